@@ -1,0 +1,214 @@
+/*
+ * qsim.h -- C ABI of the B300 exact quantum-circuit simulator.
+ *
+ * The library holds n-qubit state vectors (2^n complex amplitudes) and
+ * N-qubit density matrices (stored as 2N-qubit vectors of 2^(2N)
+ * amplitudes) in GPU memory and updates them with hand-written sm_103a
+ * CUDA kernels.  Call names and call order follow the paper (QuEST,
+ * arXiv 1802.08032): an environment, registers created in it, gates applied
+ * one call each, and a sync that waits for the work (Sec. III,
+ * "Configuration and timing").
+ *
+ * Conventions common to every call
+ *  - Qubit q is bit q of the amplitude index (Sec. II.B.1, Eq. 1).
+ *  - Amplitudes are interleaved complex numbers (re, im), contiguous:
+ *    QS_C128 = two IEEE doubles (16 B), QS_C64 = two IEEE floats (8 B).
+ *  - A density matrix rho of N qubits lives at index j + 2^N k for the
+ *    entry rho[j][k] (row j in the low N bits, column k in the high N bits);
+ *    a gate G on qubit q is enacted as G on bit q then conj(G) on bit q+N
+ *    (Sec. II.B.1, Eq. 2).
+ *  - Every call returns QS_OK (0) or a negative QS_E_* code; the message of
+ *    the last failure on the calling thread is qsLastError().  Arguments are
+ *    validated before any work is queued, so a call that fails leaves the
+ *    register unchanged.
+ *  - Gate and channel calls are asynchronous: they are queued on the
+ *    environment's CUDA stream in call order.  Calls that return a value to
+ *    the host (calcTotalProb, calcProbOfOutcome, collapseToOutcome,
+ *    calcPurity, copyStateToHost) wait for the queued work.  syncQuESTEnv
+ *    waits for everything and reports asynchronous device errors.
+ *  - Matrices and control arrays are copied at call time; host buffers
+ *    passed in stay owned by the caller.  Register memory is owned by the
+ *    library (allocated through the allocator hook when one is set).
+ *  - Handles are plain integers; a destroyed or unknown handle gives
+ *    QS_E_HANDLE.  Calls on one environment must not race from several host
+ *    threads.
+ */
+#ifndef QSIM_H
+#define QSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } Complex;
+/* Row-major 2x2 complex matrix: m[row][column]. */
+typedef struct { Complex m[2][2]; } ComplexMatrix2;
+typedef struct { int64_t id; } QuESTEnv;
+typedef struct { int64_t id; } Qureg;
+
+/* Amplitude precision of a register. */
+enum { QS_C64 = 64, QS_C128 = 128 };
+
+/* Status codes. */
+enum {
+    QS_OK = 0,
+    QS_E_QUBIT = -1,        /* qubit index out of range                        */
+    QS_E_DUP = -2,          /* repeated qubit among targets and controls       */
+    QS_E_UNITARY = -3,      /* matrix not unitary within 1e-10                 */
+    QS_E_PROB = -4,         /* probability / outcome argument out of range     */
+    QS_E_NOT_DENSITY = -5,  /* channel or purity on a state vector            */
+    QS_E_ZERO_PROB = -6,    /* collapse onto an outcome of probability ~0      */
+    QS_E_NOMEM = -7,        /* allocation failed or memory budget exceeded     */
+    QS_E_HANDLE = -8,       /* unknown or destroyed handle                     */
+    QS_E_CUDA = -9,         /* CUDA runtime error (message in qsLastError)     */
+    QS_E_TIMEOUT = -10,     /* a bounded device or host wait ran out           */
+    QS_E_ARG = -11          /* other invalid argument (null pointer, range)    */
+};
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *qsLastError(void);
+
+/* ------------------------------------------------------------ environment */
+/* createQuESTEnv: binds the current CUDA device, creates a stream owned by
+ * the environment (Sec. III: createQuESTEnv). */
+int createQuESTEnv(QuESTEnv *out);
+/* destroyQuESTEnv: waits for queued work, frees every register of the env. */
+int destroyQuESTEnv(QuESTEnv env);
+/* syncQuESTEnv: flushes every register's queued gates and waits for the
+ * stream (Sec. III: syncQuESTEnv closes the timed region).  Returns
+ * QS_E_CUDA on an asynchronous device error. */
+int syncQuESTEnv(QuESTEnv env);
+/* setEnvOption: runtime options (values are integers).
+ *   "fusion"        0 = one kernel pass per gate, 1 = queue gates and apply
+ *                   them in shared-memory tiles at flush time (default 1)
+ *   "tile_qubits"   k of a fused tile, 0 = automatic
+ *   "max_fused_ops" cap on operations per fused pass (0 = automatic)
+ *   "budget_bytes"  cap on the register memory of this env (0 = none)
+ * Unknown keys give QS_E_ARG. */
+int setEnvOption(QuESTEnv env, const char *key, int64_t value);
+/* getEnvOption: reads an option back. */
+int getEnvOption(QuESTEnv env, const char *key, int64_t *value);
+/* setAllocator: device allocations of later registers go through
+ * alloc(bytes, ctx) / release(ptr, ctx); null functions restore the built-in
+ * cudaMalloc / cudaFree.  alloc must return 256-byte aligned device memory
+ * usable on the env's stream, or null on failure (QS_E_NOMEM). */
+int setAllocator(QuESTEnv env, void *(*alloc)(size_t bytes, void *ctx),
+                 void (*release)(void *ptr, void *ctx), void *ctx);
+/* setStream: later work of the env goes to this cudaStream_t (owned by the
+ * caller, must outlive its use); null restores the env's own stream.  Queued
+ * work is flushed to the old stream first. */
+int setStream(QuESTEnv env, void *cudaStream);
+
+/* -------------------------------------------------------------- registers */
+/* createQureg: n-qubit state vector (1 <= n <= 36 within memory), returned
+ * in |0...0> (Sec. II.B.1: 2^n complex amplitudes; Sec. III: createQureg). */
+int createQureg(int numQubits, int precision, QuESTEnv env, Qureg *out);
+/* createDensityQureg: N-qubit density matrix held as a 2N-qubit vector
+ * (Sec. II.B.1, Eq. 2), returned in |0><0|. */
+int createDensityQureg(int numQubits, int precision, QuESTEnv env, Qureg *out);
+int destroyQureg(Qureg q);
+/* initZeroState: |0...0> (or |0><0|) (Sec. III: initZeroState). */
+int initZeroState(Qureg q);
+/* initPlusState: |+>^n (or |+><+|^N). */
+int initPlusState(Qureg q);
+/* copyStateToHost / setAmps: read or write `count` amplitudes starting at
+ * flat index `start` (direct amplitude access, Sec. II.B.1).  For a
+ * density matrix the flat index is j + 2^N k.  QS_C64 registers are
+ * converted to / from double. */
+int copyStateToHost(Qureg q, Complex *dst, int64_t start, int64_t count);
+int setAmps(Qureg q, const Complex *src, int64_t start, int64_t count);
+int getNumQubits(Qureg q, int *out);
+int getNumAmps(Qureg q, int64_t *out);
+/* getQuregInfo: any output pointer may be null.  devicePtr is the register's
+ * amplitude array (valid until destroyQureg; the caller must sync first). */
+int getQuregInfo(Qureg q, int *numQubits, int *isDensity, int *precision,
+                 void **devicePtr);
+
+/* ------------------------------------------------------------------ gates */
+/* Single-target gates: the pass of Eq. 1 over amplitude pairs differing in
+ * bit `target`.  On a density matrix each is applied as U rho U^dagger
+ * (Eq. 2). */
+int hadamard(Qureg q, int target);
+int pauliX(Qureg q, int target);
+int sqrtX(Qureg q, int target);     /* [[1+i, 1-i], [1-i, 1+i]] / 2          */
+int sqrtY(Qureg q, int target);     /* (1+i)/2 [[1, -1], [1, 1]]              */
+int tGate(Qureg q, int target);     /* diag(1, exp(i pi/4)), the pi/8 gate    */
+int phaseShift(Qureg q, int target, double angle);  /* diag(1, exp(i angle)) */
+/* compactUnitary: [[alpha, -conj(beta)], [beta, conj(alpha)]] with
+ * |alpha|^2 + |beta|^2 = 1 (within 1e-10, else QS_E_UNITARY). */
+int compactUnitary(Qureg q, int target, Complex alpha, Complex beta);
+/* unitary: any 2x2 unitary (max |U U^dagger - I| <= 1e-10). */
+int unitary(Qureg q, int target, ComplexMatrix2 u);
+/* Controlled gates (Eq. 1 generalised to control bits, Sec. II.B.1): the
+ * pair update happens only where every control bit is 1. */
+int controlledNot(Qureg q, int control, int target);
+int controlledUnitary(Qureg q, int control, int target, ComplexMatrix2 u);
+int multiControlledUnitary(Qureg q, const int *controls, int numControls,
+                           int target, ComplexMatrix2 u);
+/* controlledPhaseFlip (CZ): negates amplitudes with both bits set. */
+int controlledPhaseFlip(Qureg q, int qubit1, int qubit2);
+/* multiControlledPhaseFlip: negates amplitudes whose index has every listed
+ * bit set (1 <= numControls <= numQubits). */
+int multiControlledPhaseFlip(Qureg q, const int *controls, int numControls);
+
+/* --------------------------------------------------------------- channels */
+/* Density matrices only (QS_E_NOT_DENSITY otherwise).  The paper names
+ * dephasing and depolarising noise (abstract; Sec. II.B.1) without formulas;
+ * this library's reading:
+ *   mixDephasing(p):    rho -> (1-p) rho + p Z rho Z,  0 <= p <= 1/2
+ *   mixDepolarising(p): rho -> (1-p) rho + p/3 (X rho X + Y rho Y + Z rho Z),
+ *                       0 <= p <= 3/4 */
+int mixDephasing(Qureg q, int target, double prob);
+int mixDepolarising(Qureg q, int target, double prob);
+
+/* ------------------------------------------------------------- reductions */
+/* Results are accumulated in FP64 on the GPU in a fixed order (repeatable
+ * bit for bit on one GPU).  State vector: sum |a|^2; density matrix: the
+ * trace sum_j Re rho[j][j]. */
+int calcTotalProb(Qureg q, double *out);
+/* Probability that `qubit` reads `outcome` (0 or 1). */
+int calcProbOfOutcome(Qureg q, int qubit, int outcome, double *out);
+/* collapseToOutcome: projects `qubit` onto `outcome` and renormalises (scale
+ * 1/sqrt(p), or 1/p for a density matrix, in FP64).  Writes p to probOut
+ * (may be null).  p < 1e-13 (QS_C128) or 1e-6 (QS_C64) gives
+ * QS_E_ZERO_PROB and leaves the register unchanged. */
+int collapseToOutcome(Qureg q, int qubit, int outcome, double *probOut);
+/* calcPurity: Tr(rho^2) = sum_n |rho'_n|^2 of a density matrix. */
+int calcPurity(Qureg q, double *out);
+
+/* ------------------------------------------------------------ bulk calls */
+/* One operation of a gate list; the same operations as the calls above. */
+enum {
+    QS_OP_H = 1, QS_OP_X = 2, QS_OP_SQRTX = 3, QS_OP_SQRTY = 4, QS_OP_T = 5,
+    QS_OP_PHASE = 6,        /* params[0] = angle                               */
+    QS_OP_COMPACT = 7,      /* params = alpha.re, alpha.im, beta.re, beta.im   */
+    QS_OP_UNITARY = 8,      /* params = u00 u01 u10 u11 as (re, im)            */
+    QS_OP_CNOT = 9,         /* controls[0], target                             */
+    QS_OP_CUNITARY = 10,    /* controls[0..numControls), target, params as U   */
+    QS_OP_CZ = 11,          /* target and target2                              */
+    QS_OP_MCPF = 12,        /* controls[0..numControls)                        */
+    QS_OP_DEPHASE = 13,     /* target, params[0] = p                           */
+    QS_OP_DEPOL = 14        /* target, params[0] = p                           */
+};
+#define QS_MAX_OP_CONTROLS 8
+typedef struct {
+    int32_t kind;
+    int32_t target;
+    int32_t target2;
+    int32_t numControls;
+    int32_t controls[QS_MAX_OP_CONTROLS];
+    double params[8];
+} QSOp;
+
+/* applyCircuit: validates every op first (QS_E_* naming the first bad op's
+ * index in qsLastError, nothing applied), then applies them in order, as if
+ * by the individual calls. */
+int applyCircuit(Qureg q, const QSOp *ops, int64_t numOps);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSIM_H */

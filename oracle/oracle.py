@@ -12,6 +12,7 @@ prints no matrices, these are the textbook ones):
   H = [[1, 1], [1, -1]] / sqrt(2)            T = diag(1, exp(i pi/4))
   sqrt(X) = [[1+i, 1-i], [1-i, 1+i]] / 2      sqrt(Y) = (1+i)/2 [[1, -1], [1, 1]]
   X = [[0, 1], [1, 0]]                        Z = diag(1, -1)
+  phaseShift(phi) = diag(1, exp(i phi))
   compactUnitary(alpha, beta) = [[alpha, -conj(beta)], [beta, conj(alpha)]]
 Noise channels (the paper names dephasing and depolarising noise, Sec. I
 and II.B.1, without formulas; readings):
@@ -70,6 +71,8 @@ def gate_matrix(kind, params=()):
         return _FIXED[kind]
     if kind == "COMPACT":
         return compact_matrix(*params)
+    if kind == "PHASE":
+        return np.array([[1, 0], [0, np.exp(1j * params[0])]], dtype=np.complex128)
     if kind in ("UNITARY", "CUNITARY"):
         return params_matrix(params)
     raise ValueError(f"oracle: no matrix for {kind}")
@@ -166,7 +169,7 @@ class State:
 
     def apply(self, op):
         k = op.kind
-        if k in ("H", "T", "SX", "SY", "X", "COMPACT", "UNITARY"):
+        if k in ("H", "T", "SX", "SY", "X", "PHASE", "COMPACT", "UNITARY"):
             self.gate(op.targets[0], gate_matrix(k, op.params))
         elif k in ("CNOT", "CUNITARY"):
             self.gate(op.targets[0], gate_matrix(k, op.params), op.controls)

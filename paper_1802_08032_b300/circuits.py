@@ -32,12 +32,12 @@ from typing import List, NamedTuple, Sequence, Tuple
 MASK64 = (1 << 64) - 1
 
 # Gate kinds.  Matrices are NOT defined here: each consumer defines them.
-H, SQRT_X, SQRT_Y, T_GATE = "H", "SX", "SY", "T"
+H, SQRT_X, SQRT_Y, T_GATE, PHASE = "H", "SX", "SY", "T", "PHASE"
 CZ, CNOT, X_GATE = "CZ", "CNOT", "X"
 COMPACT, UNITARY, CUNITARY, MCPF = "COMPACT", "UNITARY", "CUNITARY", "MCPF"
 DEPHASE, DEPOL = "DEPHASE", "DEPOL"
 
-KINDS = (H, SQRT_X, SQRT_Y, T_GATE, CZ, CNOT, X_GATE, COMPACT, UNITARY,
+KINDS = (H, SQRT_X, SQRT_Y, T_GATE, PHASE, CZ, CNOT, X_GATE, COMPACT, UNITARY,
          CUNITARY, MCPF, DEPHASE, DEPOL)
 CHANNELS = (DEPHASE, DEPOL)
 

@@ -1,0 +1,688 @@
+// C-ABI entry points (declared in qsim.h): handle tables, argument
+// validation, register memory, and dispatch to the kernel layer.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "runtime.h"
+
+using namespace qs;
+
+namespace {
+
+thread_local std::string t_err;
+std::mutex g_mu;
+std::unordered_map<int64_t, Env*> g_envs;
+std::unordered_map<int64_t, Reg*> g_regs;
+int64_t g_next_id = 1;
+
+template <class F>
+int guarded(F&& f) {
+  try {
+    f();
+    return QS_OK;
+  } catch (const Error& e) {
+    t_err = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    t_err = "host allocation failed";
+    return QS_E_NOMEM;
+  } catch (const std::exception& e) {
+    t_err = e.what();
+    return QS_E_ARG;
+  }
+}
+
+Env& env_of(QuESTEnv e) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_envs.find(e.id);
+  if (it == g_envs.end()) fail(QS_E_HANDLE, "unknown environment handle " + std::to_string(e.id));
+  return *it->second;
+}
+
+Reg& reg_of(Qureg q) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_regs.find(q.id);
+  if (it == g_regs.end()) fail(QS_E_HANDLE, "unknown register handle " + std::to_string(q.id));
+  return *it->second;
+}
+
+void need(const void* p, const char* what) {
+  if (!p) fail(QS_E_ARG, std::string("null pointer: ") + what);
+}
+
+void check_qubit(const Reg& r, int q, const char* what) {
+  if (q < 0 || q >= r.n)
+    fail(QS_E_QUBIT, std::string(what) + " qubit " + std::to_string(q) + " out of range [0, " +
+                         std::to_string(r.n) + ")");
+}
+
+// Target plus controls: all in range and pairwise distinct.
+uint64_t check_targets(const Reg& r, int target, const int* ctrls, int nc) {
+  if (target >= 0) check_qubit(r, target, "target");
+  uint64_t mask = 0;
+  for (int k = 0; k < nc; ++k) {
+    check_qubit(r, ctrls[k], "control");
+    const uint64_t b = uint64_t(1) << ctrls[k];
+    if ((mask & b) || ctrls[k] == target)
+      fail(QS_E_DUP, "qubit " + std::to_string(ctrls[k]) + " repeated among target and controls");
+    mask |= b;
+  }
+  return mask;
+}
+
+void check_unitary(const double* m) {
+  // m: row-major u00 u01 u10 u11 as (re, im); max |U U^dagger - I| <= 1e-10.
+  double worst = 0;
+  for (int rr = 0; rr < 2; ++rr)
+    for (int cc = 0; cc < 2; ++cc) {
+      double re = 0, im = 0;
+      for (int s = 0; s < 2; ++s) {
+        const double ar = m[2 * (2 * rr + s)], ai = m[2 * (2 * rr + s) + 1];
+        const double br = m[2 * (2 * cc + s)], bi = -m[2 * (2 * cc + s) + 1];
+        re += ar * br - ai * bi;
+        im += ar * bi + ai * br;
+      }
+      worst = std::max(worst, std::hypot(re - (rr == cc ? 1.0 : 0.0), im));
+    }
+  if (!(worst <= 1e-10)) fail(QS_E_UNITARY, "matrix is not unitary (max |UU^dagger - I| = " +
+                                                std::to_string(worst) + ")");
+}
+
+GateOp make_op(OpK k, int t, uint64_t cmask) {
+  GateOp op{};
+  op.k = k;
+  op.t = t;
+  op.cmask = cmask;
+  return op;
+}
+
+void apply(Reg& r, const GateOp& op) {
+  if (r.env->fusion) r.queue.push_back(op);
+  else launch_op(*r.env, r, op);
+}
+
+void* dev_alloc(Env& env, size_t bytes) {
+  if (env.budget > 0 && env.used + int64_t(bytes) > env.budget)
+    fail(QS_E_NOMEM, "memory budget exceeded: " + std::to_string(env.used + bytes) + " > " +
+                         std::to_string(env.budget) + " bytes");
+  void* p = nullptr;
+  if (env.alloc) {
+    p = env.alloc(bytes, env.actx);
+    if (!p) fail(QS_E_NOMEM, "allocator hook returned null for " + std::to_string(bytes) + " bytes");
+  } else {
+    const cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      fail(QS_E_NOMEM, "cudaMalloc(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    }
+  }
+  env.used += int64_t(bytes);
+  return p;
+}
+
+void dev_free(Env& env, void* p, size_t bytes) {
+  if (!p) return;
+  if (env.release) env.release(p, env.actx);
+  else cudaFree(p);
+  env.used -= int64_t(bytes);
+}
+
+void ensure_stage(Env& env) {
+  if (env.d_stage) return;
+  env.stage_amps = int64_t(1) << 22;  // 64 MiB of double2
+  QS_CUDA(cudaMalloc(&env.d_stage, size_t(env.stage_amps) * sizeof(double2)));
+}
+
+void init_zero(Reg& r) {
+  r.queue.clear();
+  const size_t amp = r.prec == QS_C128 ? sizeof(double2) : sizeof(float2);
+  QS_CUDA(cudaMemsetAsync(r.d, 0, size_t(r.dim) * amp, r.env->stream));
+  if (r.prec == QS_C128) {
+    static const double one[2] = {1.0, 0.0};
+    QS_CUDA(cudaMemcpyAsync(r.d, one, sizeof(one), cudaMemcpyHostToDevice, r.env->stream));
+  } else {
+    static const float one[2] = {1.0f, 0.0f};
+    QS_CUDA(cudaMemcpyAsync(r.d, one, sizeof(one), cudaMemcpyHostToDevice, r.env->stream));
+  }
+}
+
+int create_reg(int n, int prec, QuESTEnv e, Qureg* out, bool density) {
+  return guarded([&] {
+    need(out, "out");
+    Env& env = env_of(e);
+    if (prec != QS_C64 && prec != QS_C128) fail(QS_E_ARG, "precision must be QS_C64 or QS_C128");
+    const int nq = density ? 2 * n : n;
+    if (n < 1 || nq > 40) fail(QS_E_QUBIT, "unsupported qubit count " + std::to_string(n));
+    QS_CUDA(cudaSetDevice(env.device));
+    auto* r = new Reg();
+    r->env = &env;
+    r->n = n;
+    r->density = density;
+    r->nq = nq;
+    r->prec = prec;
+    r->dim = int64_t(1) << nq;
+    r->bytes = size_t(r->dim) * (prec == QS_C128 ? 16 : 8);
+    try {
+      r->d = dev_alloc(env, r->bytes);
+      init_zero(*r);
+    } catch (...) {
+      if (r->d) dev_free(env, r->d, r->bytes);
+      delete r;
+      throw;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    r->id = g_next_id++;
+    g_regs[r->id] = r;
+    env.regs.push_back(r->id);
+    out->id = r->id;
+  });
+}
+
+void destroy_reg_locked(Reg* r) {
+  Env& env = *r->env;
+  cudaStreamSynchronize(env.stream);
+  dev_free(env, r->d, r->bytes);
+  env.regs.erase(std::remove(env.regs.begin(), env.regs.end(), r->id), env.regs.end());
+  delete r;
+}
+
+// Converts one bulk-call op into validated internal ops.
+void convert_op(const Reg& r, const QSOp& o, std::vector<GateOp>& out) {
+  const int nc = o.numControls;
+  if (nc < 0 || nc > QS_MAX_OP_CONTROLS) fail(QS_E_ARG, "numControls out of range");
+  switch (o.kind) {
+    case QS_OP_H: check_qubit(r, o.target, "target"); out.push_back(make_op(OpK::H, o.target, 0)); return;
+    case QS_OP_X: check_qubit(r, o.target, "target"); out.push_back(make_op(OpK::X, o.target, 0)); return;
+    case QS_OP_SQRTX: check_qubit(r, o.target, "target"); out.push_back(make_op(OpK::SX, o.target, 0)); return;
+    case QS_OP_SQRTY: check_qubit(r, o.target, "target"); out.push_back(make_op(OpK::SY, o.target, 0)); return;
+    case QS_OP_T:
+    case QS_OP_PHASE: {
+      check_qubit(r, o.target, "target");
+      const double ang = o.kind == QS_OP_T ? M_PI / 4 : o.params[0];
+      GateOp op = make_op(OpK::PHASE, o.target, 0);
+      op.m[0] = o.kind == QS_OP_T ? std::sqrt(0.5) : std::cos(ang);
+      op.m[1] = o.kind == QS_OP_T ? std::sqrt(0.5) : std::sin(ang);
+      out.push_back(op);
+      return;
+    }
+    case QS_OP_COMPACT: {
+      check_qubit(r, o.target, "target");
+      const double ar = o.params[0], ai = o.params[1], br = o.params[2], bi = o.params[3];
+      const double nrm = ar * ar + ai * ai + br * br + bi * bi;
+      if (!(std::fabs(nrm - 1.0) <= 1e-10))
+        fail(QS_E_UNITARY, "compactUnitary: |alpha|^2 + |beta|^2 = " + std::to_string(nrm));
+      GateOp op = make_op(OpK::GEN, o.target, 0);
+      // [[alpha, -conj(beta)], [beta, conj(alpha)]]
+      const double m[8] = {ar, ai, -br, bi, br, bi, ar, -ai};
+      std::memcpy(op.m, m, sizeof(m));
+      out.push_back(op);
+      return;
+    }
+    case QS_OP_UNITARY:
+    case QS_OP_CUNITARY:
+    case QS_OP_CNOT: {
+      const int ncu = o.kind == QS_OP_UNITARY ? 0 : (o.kind == QS_OP_CNOT ? 1 : nc);
+      if (o.kind == QS_OP_CNOT && nc != 1 && nc != 0) fail(QS_E_ARG, "CNOT takes one control");
+      const uint64_t cm = check_targets(r, o.target, o.controls, ncu);
+      if (o.kind == QS_OP_CNOT) {
+        out.push_back(make_op(OpK::X, o.target, cm));
+        return;
+      }
+      check_unitary(o.params);
+      GateOp op = make_op(OpK::GEN, o.target, cm);
+      std::memcpy(op.m, o.params, sizeof(op.m));
+      out.push_back(op);
+      return;
+    }
+    case QS_OP_CZ: {
+      const int c[1] = {o.target2};
+      const uint64_t cm = check_targets(r, o.target, c, 1);
+      out.push_back(make_op(OpK::SIGN, -1, cm | (uint64_t(1) << o.target)));
+      return;
+    }
+    case QS_OP_MCPF: {
+      if (nc < 1) fail(QS_E_ARG, "multiControlledPhaseFlip needs at least one qubit");
+      const uint64_t cm = check_targets(r, -1, o.controls, nc);
+      out.push_back(make_op(OpK::SIGN, -1, cm));
+      return;
+    }
+    case QS_OP_DEPHASE:
+    case QS_OP_DEPOL: {
+      if (!r.density) fail(QS_E_NOT_DENSITY, "noise channel on a state vector");
+      check_qubit(r, o.target, "target");
+      const double p = o.params[0];
+      const double pmax = o.kind == QS_OP_DEPHASE ? 0.5 : 0.75;
+      if (!(p >= 0.0 && p <= pmax))
+        fail(QS_E_PROB, "channel probability " + std::to_string(p) + " outside [0, " +
+                            std::to_string(pmax) + "]");
+      GateOp op = make_op(o.kind == QS_OP_DEPHASE ? OpK::DEPHASE : OpK::DEPOL, o.target, 0);
+      op.m[0] = p;
+      out.push_back(op);
+      return;
+    }
+    default: fail(QS_E_ARG, "unknown op kind " + std::to_string(o.kind));
+  }
+}
+
+int one_op(Qureg q, const QSOp& o) {
+  return guarded([&] {
+    Reg& r = reg_of(q);
+    std::vector<GateOp> ops;
+    convert_op(r, o, ops);
+    for (auto& op : ops) apply(r, op);
+  });
+}
+
+QSOp blank(int kind, int target) {
+  QSOp o;
+  std::memset(&o, 0, sizeof(o));
+  o.kind = kind;
+  o.target = target;
+  return o;
+}
+
+void mat_params(const ComplexMatrix2& u, double* p) {
+  for (int rr = 0; rr < 2; ++rr)
+    for (int cc = 0; cc < 2; ++cc) {
+      p[2 * (2 * rr + cc)] = u.m[rr][cc].re;
+      p[2 * (2 * rr + cc) + 1] = u.m[rr][cc].im;
+    }
+}
+
+}  // namespace
+
+namespace qs {
+void flush(Reg& r);  // fused.cu
+}
+
+extern "C" {
+
+const char* qsLastError(void) { return t_err.c_str(); }
+
+int createQuESTEnv(QuESTEnv* out) {
+  return guarded([&] {
+    need(out, "out");
+    auto* env = new Env();
+    try {
+      QS_CUDA(cudaGetDevice(&env->device));
+      QS_CUDA(cudaDeviceGetAttribute(&env->sms, cudaDevAttrMultiProcessorCount, env->device));
+      QS_CUDA(cudaStreamCreateWithFlags(&env->own, cudaStreamNonBlocking));
+      env->stream = env->own;
+      QS_CUDA(cudaMalloc(&env->d_partial, sizeof(double) * 4096));
+      QS_CUDA(cudaMalloc(&env->d_result, sizeof(double) * 64));
+      QS_CUDA(cudaMallocHost(&env->h_result, sizeof(double) * 64));
+    } catch (...) {
+      if (env->own) cudaStreamDestroy(env->own);
+      if (env->d_partial) cudaFree(env->d_partial);
+      if (env->d_result) cudaFree(env->d_result);
+      delete env;
+      throw;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    env->id = g_next_id++;
+    g_envs[env->id] = env;
+    out->id = env->id;
+  });
+}
+
+int destroyQuESTEnv(QuESTEnv e) {
+  return guarded([&] {
+    Env& env = env_of(e);
+    cudaStreamSynchronize(env.stream);
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (int64_t id : std::vector<int64_t>(env.regs)) {
+      auto it = g_regs.find(id);
+      if (it != g_regs.end()) {
+        destroy_reg_locked(it->second);
+        g_regs.erase(it);
+      }
+    }
+    cudaFree(env.d_partial);
+    cudaFree(env.d_result);
+    cudaFreeHost(env.h_result);
+    if (env.d_stage) cudaFree(env.d_stage);
+    cudaStreamDestroy(env.own);
+    g_envs.erase(env.id);
+    delete &env;
+  });
+}
+
+int syncQuESTEnv(QuESTEnv e) {
+  return guarded([&] {
+    Env& env = env_of(e);
+    std::vector<Reg*> regs;
+    {
+      std::lock_guard<std::mutex> lk(g_mu);
+      for (int64_t id : env.regs) regs.push_back(g_regs.at(id));
+    }
+    for (Reg* r : regs) flush(*r);
+    QS_CUDA(cudaStreamSynchronize(env.stream));
+    QS_CUDA(cudaGetLastError());
+  });
+}
+
+int setEnvOption(QuESTEnv e, const char* key, int64_t value) {
+  return guarded([&] {
+    Env& env = env_of(e);
+    need(key, "key");
+    const std::string k(key);
+    if (k == "fusion") {
+      if (value != 0 && value != 1) fail(QS_E_ARG, "fusion must be 0 or 1");
+      if (!value) {
+        std::lock_guard<std::mutex> lk(g_mu);
+        for (int64_t id : env.regs) flush(*g_regs.at(id));
+      }
+      env.fusion = value;
+    } else if (k == "tile_qubits") {
+      if (value != 0 && (value < 5 || value > 13)) fail(QS_E_ARG, "tile_qubits must be 0 or 5..13");
+      env.tile_qubits = value;
+    } else if (k == "max_fused_ops") {
+      if (value < 0) fail(QS_E_ARG, "max_fused_ops must be >= 0");
+      env.max_fused_ops = value;
+    } else if (k == "budget_bytes") {
+      if (value < 0) fail(QS_E_ARG, "budget_bytes must be >= 0");
+      env.budget = value;
+    } else {
+      fail(QS_E_ARG, "unknown option " + k);
+    }
+  });
+}
+
+int getEnvOption(QuESTEnv e, const char* key, int64_t* value) {
+  return guarded([&] {
+    Env& env = env_of(e);
+    need(key, "key");
+    need(value, "value");
+    const std::string k(key);
+    if (k == "fusion") *value = env.fusion;
+    else if (k == "tile_qubits") *value = env.tile_qubits;
+    else if (k == "max_fused_ops") *value = env.max_fused_ops;
+    else if (k == "budget_bytes") *value = env.budget;
+    else if (k == "used_bytes") *value = env.used;
+    else fail(QS_E_ARG, "unknown option " + k);
+  });
+}
+
+int setAllocator(QuESTEnv e, void* (*alloc)(size_t, void*), void (*release)(void*, void*), void* ctx) {
+  return guarded([&] {
+    Env& env = env_of(e);
+    if ((alloc == nullptr) != (release == nullptr))
+      fail(QS_E_ARG, "alloc and release must both be set or both be null");
+    env.alloc = alloc;
+    env.release = release;
+    env.actx = ctx;
+  });
+}
+
+int setStream(QuESTEnv e, void* stream) {
+  return guarded([&] {
+    Env& env = env_of(e);
+    {
+      std::lock_guard<std::mutex> lk(g_mu);
+      for (int64_t id : env.regs) flush(*g_regs.at(id));
+    }
+    cudaStream_t next = stream ? static_cast<cudaStream_t>(stream) : env.own;
+    if (next != env.stream) {
+      // order the new stream after everything queued on the old one
+      cudaEvent_t ev;
+      QS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      QS_CUDA(cudaEventRecord(ev, env.stream));
+      QS_CUDA(cudaStreamWaitEvent(next, ev, 0));
+      QS_CUDA(cudaEventDestroy(ev));
+    }
+    env.stream = next;
+  });
+}
+
+int createQureg(int n, int prec, QuESTEnv e, Qureg* out) { return create_reg(n, prec, e, out, false); }
+int createDensityQureg(int n, int prec, QuESTEnv e, Qureg* out) { return create_reg(n, prec, e, out, true); }
+
+int destroyQureg(Qureg q) {
+  return guarded([&] {
+    Reg& r = reg_of(q);
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_regs.erase(r.id);
+    destroy_reg_locked(&r);
+  });
+}
+
+int initZeroState(Qureg q) {
+  return guarded([&] { init_zero(reg_of(q)); });
+}
+
+int initPlusState(Qureg q) {
+  return guarded([&] {
+    Reg& r = reg_of(q);
+    r.queue.clear();
+    // |+>^n: every amplitude 2^(-n/2); |+><+|^N: every entry 2^(-N).
+    const double v = r.density ? std::ldexp(1.0, -r.n) : 1.0 / std::sqrt(double(r.dim));
+    launch_fill(*r.env, r, v, 0.0);
+  });
+}
+
+int copyStateToHost(Qureg q, Complex* dst, int64_t start, int64_t count) {
+  return guarded([&] {
+    Reg& r = reg_of(q);
+    if (count == 0) return;
+    need(dst, "dst");
+    if (start < 0 || count < 0 || start > r.dim || count > r.dim - start)
+      fail(QS_E_ARG, "amplitude range out of bounds");
+    flush(r);
+    Env& env = *r.env;
+    if (r.prec == QS_C128) {
+      QS_CUDA(cudaMemcpyAsync(dst, static_cast<double2*>(r.d) + start, size_t(count) * 16,
+                              cudaMemcpyDeviceToHost, env.stream));
+      QS_CUDA(cudaStreamSynchronize(env.stream));
+      return;
+    }
+    ensure_stage(env);
+    for (int64_t off = 0; off < count; off += env.stage_amps) {
+      const int64_t c = std::min(env.stage_amps, count - off);
+      launch_convert(env, static_cast<float2*>(r.d) + start + off, env.d_stage, c, true);
+      QS_CUDA(cudaMemcpyAsync(dst + off, env.d_stage, size_t(c) * 16, cudaMemcpyDeviceToHost, env.stream));
+      QS_CUDA(cudaStreamSynchronize(env.stream));
+    }
+  });
+}
+
+int setAmps(Qureg q, const Complex* src, int64_t start, int64_t count) {
+  return guarded([&] {
+    Reg& r = reg_of(q);
+    if (count == 0) return;
+    need(src, "src");
+    if (start < 0 || count < 0 || start > r.dim || count > r.dim - start)
+      fail(QS_E_ARG, "amplitude range out of bounds");
+    flush(r);
+    Env& env = *r.env;
+    if (r.prec == QS_C128) {
+      QS_CUDA(cudaMemcpyAsync(static_cast<double2*>(r.d) + start, src, size_t(count) * 16,
+                              cudaMemcpyHostToDevice, env.stream));
+      QS_CUDA(cudaStreamSynchronize(env.stream));
+      return;
+    }
+    ensure_stage(env);
+    for (int64_t off = 0; off < count; off += env.stage_amps) {
+      const int64_t c = std::min(env.stage_amps, count - off);
+      QS_CUDA(cudaMemcpyAsync(env.d_stage, src + off, size_t(c) * 16, cudaMemcpyHostToDevice, env.stream));
+      launch_convert(env, env.d_stage, static_cast<float2*>(r.d) + start + off, c, false);
+      QS_CUDA(cudaStreamSynchronize(env.stream));
+    }
+  });
+}
+
+int getNumQubits(Qureg q, int* out) {
+  return guarded([&] {
+    need(out, "out");
+    *out = reg_of(q).n;
+  });
+}
+
+int getNumAmps(Qureg q, int64_t* out) {
+  return guarded([&] {
+    need(out, "out");
+    *out = reg_of(q).dim;
+  });
+}
+
+int getQuregInfo(Qureg q, int* numQubits, int* isDensity, int* precision, void** devicePtr) {
+  return guarded([&] {
+    Reg& r = reg_of(q);
+    if (numQubits) *numQubits = r.n;
+    if (isDensity) *isDensity = r.density ? 1 : 0;
+    if (precision) *precision = r.prec;
+    if (devicePtr) *devicePtr = r.d;
+  });
+}
+
+int hadamard(Qureg q, int t) { return one_op(q, blank(QS_OP_H, t)); }
+int pauliX(Qureg q, int t) { return one_op(q, blank(QS_OP_X, t)); }
+int sqrtX(Qureg q, int t) { return one_op(q, blank(QS_OP_SQRTX, t)); }
+int sqrtY(Qureg q, int t) { return one_op(q, blank(QS_OP_SQRTY, t)); }
+int tGate(Qureg q, int t) { return one_op(q, blank(QS_OP_T, t)); }
+
+int phaseShift(Qureg q, int t, double angle) {
+  QSOp o = blank(QS_OP_PHASE, t);
+  o.params[0] = angle;
+  return one_op(q, o);
+}
+
+int compactUnitary(Qureg q, int t, Complex alpha, Complex beta) {
+  QSOp o = blank(QS_OP_COMPACT, t);
+  o.params[0] = alpha.re;
+  o.params[1] = alpha.im;
+  o.params[2] = beta.re;
+  o.params[3] = beta.im;
+  return one_op(q, o);
+}
+
+int unitary(Qureg q, int t, ComplexMatrix2 u) {
+  QSOp o = blank(QS_OP_UNITARY, t);
+  mat_params(u, o.params);
+  return one_op(q, o);
+}
+
+int controlledNot(Qureg q, int c, int t) {
+  QSOp o = blank(QS_OP_CNOT, t);
+  o.numControls = 1;
+  o.controls[0] = c;
+  return one_op(q, o);
+}
+
+int controlledUnitary(Qureg q, int c, int t, ComplexMatrix2 u) {
+  QSOp o = blank(QS_OP_CUNITARY, t);
+  o.numControls = 1;
+  o.controls[0] = c;
+  mat_params(u, o.params);
+  return one_op(q, o);
+}
+
+int multiControlledUnitary(Qureg q, const int* ctrls, int nc, int t, ComplexMatrix2 u) {
+  return guarded([&] {
+    Reg& r = reg_of(q);
+    if (nc < 0 || nc >= r.n) fail(QS_E_ARG, "numControls out of range");
+    if (nc > 0) need(ctrls, "controls");
+    const uint64_t cm = check_targets(r, t, ctrls, nc);
+    double p[8];
+    mat_params(u, p);
+    check_unitary(p);
+    GateOp op = make_op(OpK::GEN, t, cm);
+    std::memcpy(op.m, p, sizeof(p));
+    apply(r, op);
+  });
+}
+
+int controlledPhaseFlip(Qureg q, int a, int b) {
+  QSOp o = blank(QS_OP_CZ, a);
+  o.target2 = b;
+  return one_op(q, o);
+}
+
+int multiControlledPhaseFlip(Qureg q, const int* ctrls, int nc) {
+  return guarded([&] {
+    Reg& r = reg_of(q);
+    if (nc < 1 || nc > r.n) fail(QS_E_ARG, "numControls must be in [1, numQubits]");
+    need(ctrls, "controls");
+    const uint64_t cm = check_targets(r, -1, ctrls, nc);
+    apply(r, make_op(OpK::SIGN, -1, cm));
+  });
+}
+
+int mixDephasing(Qureg q, int t, double p) {
+  QSOp o = blank(QS_OP_DEPHASE, t);
+  o.params[0] = p;
+  return one_op(q, o);
+}
+
+int mixDepolarising(Qureg q, int t, double p) {
+  QSOp o = blank(QS_OP_DEPOL, t);
+  o.params[0] = p;
+  return one_op(q, o);
+}
+
+int calcTotalProb(Qureg q, double* out) {
+  return guarded([&] {
+    need(out, "out");
+    Reg& r = reg_of(q);
+    *out = reduce_total(*r.env, r);
+  });
+}
+
+int calcProbOfOutcome(Qureg q, int qubit, int outcome, double* out) {
+  return guarded([&] {
+    need(out, "out");
+    Reg& r = reg_of(q);
+    check_qubit(r, qubit, "measured");
+    if (outcome != 0 && outcome != 1) fail(QS_E_PROB, "outcome must be 0 or 1");
+    *out = reduce_outcome(*r.env, r, qubit, outcome);
+  });
+}
+
+int collapseToOutcome(Qureg q, int qubit, int outcome, double* probOut) {
+  return guarded([&] {
+    Reg& r = reg_of(q);
+    check_qubit(r, qubit, "measured");
+    if (outcome != 0 && outcome != 1) fail(QS_E_PROB, "outcome must be 0 or 1");
+    const double p = reduce_outcome(*r.env, r, qubit, outcome);
+    const double pmin = r.prec == QS_C128 ? 1e-13 : 1e-6;
+    if (!(p >= pmin))
+      fail(QS_E_ZERO_PROB, "outcome probability " + std::to_string(p) + " below " + std::to_string(pmin));
+    launch_collapse(*r.env, r, qubit, outcome, r.density ? 1.0 / p : 1.0 / std::sqrt(p));
+    if (probOut) *probOut = p;
+  });
+}
+
+int calcPurity(Qureg q, double* out) {
+  return guarded([&] {
+    need(out, "out");
+    Reg& r = reg_of(q);
+    if (!r.density) fail(QS_E_NOT_DENSITY, "purity of a state vector");
+    *out = reduce_purity(*r.env, r);
+  });
+}
+
+int applyCircuit(Qureg q, const QSOp* ops, int64_t n) {
+  return guarded([&] {
+    Reg& r = reg_of(q);
+    if (n < 0) fail(QS_E_ARG, "numOps < 0");
+    if (n > 0) need(ops, "ops");
+    std::vector<GateOp> conv;
+    conv.reserve(size_t(n));
+    for (int64_t i = 0; i < n; ++i) {
+      try {
+        convert_op(r, ops[i], conv);
+      } catch (Error& e) {
+        e.msg = "op " + std::to_string(i) + ": " + e.msg;
+        throw;
+      }
+    }
+    for (auto& op : conv) apply(r, op);
+  });
+}
+
+}  // extern "C"

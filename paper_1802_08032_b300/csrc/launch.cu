@@ -1,0 +1,257 @@
+// Kernel launches of the one-pass-per-gate path, reductions and utilities.
+#include <algorithm>
+#include <cmath>
+
+#include "pass_kernels.cuh"
+#include "reduce_kernels.cuh"
+#include "runtime.h"
+
+namespace qs {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kUnroll = 4;
+
+int grid_for(const Env& env, int64_t items, int per_thread) {
+  const int64_t want = (items + int64_t(kThreads) * per_thread - 1) / (int64_t(kThreads) * per_thread);
+  const int64_t cap = int64_t(env.sms) * 8;
+  return int(std::max<int64_t>(1, std::min(want, cap)));
+}
+
+// Fixed-bit spec from (position, value) pairs.
+Fixed make_fixed(std::vector<std::pair<int, int>> bits) {
+  std::sort(bits.begin(), bits.end());
+  Fixed f{};
+  f.n = int(bits.size());
+  f.vals = 0;
+  for (int k = 0; k < f.n; ++k) {
+    f.pos[k] = uint8_t(bits[k].first);
+    if (bits[k].second) f.vals |= uint64_t(1) << k;
+  }
+  return f;
+}
+
+std::vector<std::pair<int, int>> ctrl_bits(uint64_t mask, int value) {
+  std::vector<std::pair<int, int>> v;
+  for (int q = 0; q < 64; ++q)
+    if ((mask >> q) & 1) v.push_back({q, value});
+  return v;
+}
+
+template <typename R>
+Mat2<R> to_mat(const GateOp& op) {
+  Mat2<R> g{};
+  if (op.k == OpK::GEN) {
+    for (int e = 0; e < 4; ++e) {
+      g.re[e] = R(op.m[2 * e]);
+      g.im[e] = R(op.m[2 * e + 1]);
+    }
+  } else if (op.k == OpK::H) {
+    g.re[0] = R(1.0 / std::sqrt(2.0));
+  }
+  return g;
+}
+
+template <typename R, int K>
+void sv_pair(Env& env, Reg& r, const GateOp& op) {
+  auto bits = ctrl_bits(op.cmask, 1);
+  bits.push_back({op.t, 0});
+  const Fixed fx = make_fixed(bits);
+  const int64_t nsel = r.dim >> fx.n;
+  k_sv_pair<R, K, kUnroll><<<grid_for(env, nsel, kUnroll), kThreads, 0, env.stream>>>(
+      static_cast<cvec<R>*>(r.d), nsel, int64_t(1) << op.t, fx, to_mat<R>(op));
+}
+
+template <typename R, int K>
+void dm_pair(Env& env, Reg& r, const GateOp& op) {
+  const int N = r.n;
+  const Fixed fx = make_fixed({{op.t, 0}, {op.t + N, 0}});
+  const int64_t nsel = r.dim >> 2;
+  k_dm_gate<R, K, 2><<<grid_for(env, nsel, 2), kThreads, 0, env.stream>>>(
+      static_cast<cvec<R>*>(r.d), nsel, int64_t(1) << op.t, int64_t(1) << (op.t + N), op.cmask,
+      op.cmask << N, fx, to_mat<R>(op));
+}
+
+template <typename R>
+void launch_typed(Env& env, Reg& r, const GateOp& op) {
+  cvec<R>* a = static_cast<cvec<R>*>(r.d);
+  if (!r.density) {
+    switch (op.k) {
+      case OpK::GEN: sv_pair<R, PK_GEN>(env, r, op); return;
+      case OpK::H: sv_pair<R, PK_H>(env, r, op); return;
+      case OpK::SX: sv_pair<R, PK_SX>(env, r, op); return;
+      case OpK::SY: sv_pair<R, PK_SY>(env, r, op); return;
+      case OpK::X: sv_pair<R, PK_X>(env, r, op); return;
+      case OpK::PHASE: {
+        auto bits = ctrl_bits(op.cmask, 1);
+        bits.push_back({op.t, 1});
+        const Fixed fx = make_fixed(bits);
+        const int64_t nsel = r.dim >> fx.n;
+        k_sv_diag<R, DK_PHASE, kUnroll><<<grid_for(env, nsel, kUnroll), kThreads, 0, env.stream>>>(
+            a, nsel, fx, R(op.m[0]), R(op.m[1]));
+        return;
+      }
+      case OpK::SIGN: {
+        const Fixed fx = make_fixed(ctrl_bits(op.cmask, 1));
+        const int64_t nsel = r.dim >> fx.n;
+        k_sv_diag<R, DK_SIGN, kUnroll><<<grid_for(env, nsel, kUnroll), kThreads, 0, env.stream>>>(
+            a, nsel, fx, R(0), R(0));
+        return;
+      }
+      default: fail(QS_E_NOT_DENSITY, "channel on a state vector");
+    }
+  }
+  const int N = r.n;
+  switch (op.k) {
+    case OpK::GEN: dm_pair<R, PK_GEN>(env, r, op); return;
+    case OpK::H: dm_pair<R, PK_H>(env, r, op); return;
+    case OpK::SX: dm_pair<R, PK_SX>(env, r, op); return;
+    case OpK::SY: dm_pair<R, PK_SY>(env, r, op); return;
+    case OpK::X: dm_pair<R, PK_X>(env, r, op); return;
+    case OpK::PHASE:
+      k_dm_diag<R, DD_PHASE><<<grid_for(env, r.dim, 1), kThreads, 0, env.stream>>>(
+          a, r.dim, N, op.cmask, op.t, R(op.m[0]), R(op.m[1]));
+      return;
+    case OpK::SIGN:
+      k_dm_diag<R, DD_SIGN><<<grid_for(env, r.dim, 1), kThreads, 0, env.stream>>>(
+          a, r.dim, N, op.cmask, 0, R(0), R(0));
+      return;
+    case OpK::DEPHASE:
+      k_dm_diag<R, DD_DEPHASE><<<grid_for(env, r.dim, 1), kThreads, 0, env.stream>>>(
+          a, r.dim, N, 0, op.t, R(1.0 - 2.0 * op.m[0]), R(0));
+      return;
+    case OpK::DEPOL: {
+      const double p = op.m[0];
+      const Fixed fx = make_fixed({{op.t, 0}, {op.t + N, 0}});
+      const int64_t nsel = r.dim >> 2;
+      k_dm_depol<R, 2><<<grid_for(env, nsel, 2), kThreads, 0, env.stream>>>(
+          a, nsel, int64_t(1) << op.t, int64_t(1) << (op.t + N), fx, R(1.0 - 2.0 * p / 3.0),
+          R(2.0 * p / 3.0), R(1.0 - 4.0 * p / 3.0));
+      return;
+    }
+  }
+}
+
+void check_launch() { QS_CUDA(cudaGetLastError()); }
+
+template <typename R>
+void sumsq(Env& env, const Reg& r, const Fixed& fx, int64_t nsel) {
+  const int blocks = int(std::max<int64_t>(
+      1, std::min<int64_t>(kRedMaxBlocks, (nsel + kRedThreads * 4 - 1) / (kRedThreads * 4))));
+  k_sumsq<R, 4><<<blocks, kRedThreads, 0, env.stream>>>(static_cast<const cvec<R>*>(r.d), nsel, fx,
+                                                        env.d_partial);
+  k_sum_partials<<<1, 1024, 0, env.stream>>>(env.d_partial, blocks, env.d_result);
+}
+
+template <typename R>
+void sumdiag(Env& env, const Reg& r, int q, int o) {
+  const int64_t d = int64_t(1) << r.n;
+  const int blocks = int(std::max<int64_t>(
+      1, std::min<int64_t>(kRedMaxBlocks, (d + kRedThreads - 1) / kRedThreads)));
+  k_sumdiag<R><<<blocks, kRedThreads, 0, env.stream>>>(static_cast<const cvec<R>*>(r.d), r.n, q, o,
+                                                       env.d_partial);
+  k_sum_partials<<<1, 1024, 0, env.stream>>>(env.d_partial, blocks, env.d_result);
+}
+
+double fetch_result(Env& env) {
+  check_launch();
+  QS_CUDA(cudaMemcpyAsync(env.h_result, env.d_result, sizeof(double), cudaMemcpyDeviceToHost,
+                          env.stream));
+  QS_CUDA(cudaStreamSynchronize(env.stream));
+  return env.h_result[0];
+}
+
+}  // namespace
+
+void launch_op(Env& env, Reg& r, const GateOp& op) {
+  if (r.prec == QS_C128) launch_typed<double>(env, r, op);
+  else launch_typed<float>(env, r, op);
+  check_launch();
+}
+
+double reduce_total(Env& env, Reg& r) {
+  flush(r);
+  if (r.density) {
+    if (r.prec == QS_C128) sumdiag<double>(env, r, -1, 0);
+    else sumdiag<float>(env, r, -1, 0);
+  } else {
+    const Fixed fx = make_fixed({});
+    if (r.prec == QS_C128) sumsq<double>(env, r, fx, r.dim);
+    else sumsq<float>(env, r, fx, r.dim);
+  }
+  return fetch_result(env);
+}
+
+double reduce_outcome(Env& env, Reg& r, int q, int o) {
+  flush(r);
+  if (r.density) {
+    if (r.prec == QS_C128) sumdiag<double>(env, r, q, o);
+    else sumdiag<float>(env, r, q, o);
+  } else {
+    const Fixed fx = make_fixed({{q, o}});
+    if (r.prec == QS_C128) sumsq<double>(env, r, fx, r.dim >> 1);
+    else sumsq<float>(env, r, fx, r.dim >> 1);
+  }
+  return fetch_result(env);
+}
+
+double reduce_purity(Env& env, Reg& r) {
+  flush(r);
+  const Fixed fx = make_fixed({});
+  if (r.prec == QS_C128) sumsq<double>(env, r, fx, r.dim);
+  else sumsq<float>(env, r, fx, r.dim);
+  return fetch_result(env);
+}
+
+void launch_collapse(Env& env, Reg& r, int q, int o, double scale) {
+  const int g = grid_for(env, r.dim, 1);
+  if (r.density) {
+    if (r.prec == QS_C128)
+      k_collapse_dm<double><<<g, kThreads, 0, env.stream>>>(static_cast<double2*>(r.d), r.dim, r.n, q, o, scale);
+    else
+      k_collapse_dm<float><<<g, kThreads, 0, env.stream>>>(static_cast<float2*>(r.d), r.dim, r.n, q, o, scale);
+  } else {
+    if (r.prec == QS_C128)
+      k_collapse_sv<double><<<g, kThreads, 0, env.stream>>>(static_cast<double2*>(r.d), r.dim, q, o, scale);
+    else
+      k_collapse_sv<float><<<g, kThreads, 0, env.stream>>>(static_cast<float2*>(r.d), r.dim, q, o, scale);
+  }
+  check_launch();
+}
+
+void launch_fill(Env& env, Reg& r, double re, double im) {
+  const int g = grid_for(env, r.dim, 1);
+  if (r.prec == QS_C128)
+    k_fill<double><<<g, kThreads, 0, env.stream>>>(static_cast<double2*>(r.d), r.dim, re, im);
+  else
+    k_fill<float><<<g, kThreads, 0, env.stream>>>(static_cast<float2*>(r.d), r.dim, float(re), float(im));
+  check_launch();
+}
+
+__global__ void k_f2d(const float2* __restrict__ s, double2* __restrict__ d, int64_t count) {
+  const int64_t nthr = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; n < count; n += nthr) {
+    const float2 v = s[n];
+    d[n] = make_double2(double(v.x), double(v.y));
+  }
+}
+
+__global__ void k_d2f(const double2* __restrict__ s, float2* __restrict__ d, int64_t count) {
+  const int64_t nthr = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; n < count; n += nthr) {
+    const double2 v = s[n];
+    d[n] = make_float2(float(v.x), float(v.y));
+  }
+}
+
+void launch_convert(Env& env, const void* src, void* dst, int64_t count, bool to_double) {
+  const int g = grid_for(env, count, 1);
+  if (to_double)
+    k_f2d<<<g, kThreads, 0, env.stream>>>(static_cast<const float2*>(src), static_cast<double2*>(dst), count);
+  else
+    k_d2f<<<g, kThreads, 0, env.stream>>>(static_cast<const double2*>(src), static_cast<float2*>(dst), count);
+  check_launch();
+}
+
+}  // namespace qs

@@ -1,0 +1,99 @@
+// Host-side runtime structures of the simulator library (environment,
+// registers, validated operations).  Internal: not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "qsim.h"
+
+namespace qs {
+
+// A validated operation in the library's internal form.
+enum class OpK : int32_t {
+  GEN = 0,   // general 2x2 on t (m = re/im row-major: re0 im0 re1 im1 ...)
+  H = 1,
+  SX = 2,
+  SY = 3,
+  X = 4,
+  PHASE = 5,    // diag(1, e^{i phi}) on t: m[0] = cos phi, m[1] = sin phi
+  SIGN = 6,     // negate where every bit of cmask is set (t unused)
+  DEPHASE = 7,  // density matrix only, p in m[0]
+  DEPOL = 8     // density matrix only, p in m[0]
+};
+
+struct GateOp {
+  OpK k;
+  int t;            // target qubit (logical), -1 for SIGN
+  uint64_t cmask;   // control bits (logical qubits); SIGN: the flipped set
+  double m[8];
+};
+
+struct Error {
+  int code;
+  std::string msg;
+};
+[[noreturn]] inline void fail(int code, const std::string& msg) { throw Error{code, msg}; }
+
+#define QS_CUDA(call)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      ::qs::fail(QS_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+struct Env;
+
+struct Reg {
+  int64_t id = 0;
+  Env* env = nullptr;
+  int n = 0;          // logical qubits
+  bool density = false;
+  int nq = 0;         // qubits of the stored vector (n, or 2n for a density matrix)
+  int prec = QS_C128;
+  int64_t dim = 0;    // 2^nq amplitudes
+  void* d = nullptr;  // amplitudes (double2 or float2)
+  size_t bytes = 0;
+  std::vector<GateOp> queue;  // gates waiting for a fused flush
+};
+
+struct Env {
+  int64_t id = 0;
+  int device = 0;
+  int sms = 148;
+  cudaStream_t own = nullptr;
+  cudaStream_t stream = nullptr;
+  // options
+  int64_t fusion = 1;
+  int64_t tile_qubits = 0;
+  int64_t max_fused_ops = 0;
+  int64_t budget = 0;
+  int64_t used = 0;
+  // allocator hook
+  void* (*alloc)(size_t, void*) = nullptr;
+  void (*release)(void*, void*) = nullptr;
+  void* actx = nullptr;
+  // scratch: reduction partials and results (device), pinned result copy
+  double* d_partial = nullptr;
+  double* d_result = nullptr;
+  double* h_result = nullptr;
+  // staging buffer for complex64 <-> complex128 copies
+  double2* d_stage = nullptr;
+  int64_t stage_amps = 0;
+  std::vector<int64_t> regs;
+};
+
+// Entry points of the kernel layer (implemented in the .cu files).
+void launch_op(Env& env, Reg& r, const GateOp& op);
+void flush(Reg& r);
+double reduce_total(Env& env, Reg& r);
+double reduce_outcome(Env& env, Reg& r, int q, int o);
+double reduce_purity(Env& env, Reg& r);
+void launch_collapse(Env& env, Reg& r, int q, int o, double scale);
+void launch_fill(Env& env, Reg& r, double re, double im);
+void launch_convert(Env& env, const void* src, void* dst, int64_t count, bool to_double);
+
+}  // namespace qs

@@ -1,0 +1,260 @@
+"""GPU path vs the CPU oracle, element by element, through the C ABI."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1802_08032_b300 import circuits as C
+from gpu_helpers import (AMP_TOL, PROB_TOL, fsum_abs2, gpu_state, rand_density_vec, rand_state,
+                         single_ops)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Q():
+    from paper_1802_08032_b300 import qsim
+    return qsim
+
+
+@pytest.fixture(scope="module")
+def env(Q):
+    e = Q.createQuESTEnv()
+    yield e
+    Q.destroyQuESTEnv(e)
+
+
+@pytest.mark.parametrize("prec", [128, 64])
+@pytest.mark.parametrize("fusion", [0, 1])
+def test_every_gate_every_target(Q, env, prec, fusion):
+    n = 9
+    psi = rand_state(n, 11)
+    for op in single_ops(n, seed=3):
+        ref = O.State(n, amps=psi)
+        ref.apply(op)
+        got = gpu_state(Q, env, n, [op], prec, fusion=fusion, init=psi)
+        err = np.max(np.abs(got - ref.a))
+        assert err <= AMP_TOL[prec] * (1 if prec == 128 else 0.1), (op, err)
+
+
+@pytest.mark.parametrize("prec", [128, 64])
+@pytest.mark.parametrize("fusion", [0, 1])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 11, 14])
+def test_random_circuits(Q, env, prec, fusion, n):
+    ops = C.random_circuit(n, 12, 100 + n, extras=n >= 3)
+    ref = O.run_circuit(n, ops)
+    got = gpu_state(Q, env, n, ops, prec, fusion=fusion)
+    assert np.max(np.abs(got - ref.a)) <= AMP_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [128, 64])
+def test_twelve_qubit_depth20_workload(Q, env, prec):
+    """12-qubit state vector, depth-20 random circuit, then calcTotalProb and
+    calcProbOfOutcome on qubit 0."""
+    ops = C.workload_12q()
+    ref = O.run_circuit(12, ops)
+    Q.setEnvOption(env, "fusion", 1)
+    q = Q.createQureg(12, prec, env)
+    Q.applyCircuit(q, ops)
+    tot = Q.calcTotalProb(q)
+    p0, p1 = Q.calcProbOfOutcome(q, 0, 0), Q.calcProbOfOutcome(q, 0, 1)
+    got = Q.copyStateToHost(q)
+    Q.destroyQureg(q)
+    assert np.max(np.abs(got - ref.a)) <= AMP_TOL[prec]
+    if prec == 128:
+        assert abs(tot - ref.total_prob()) <= PROB_TOL
+        assert abs(p0 - ref.prob_outcome(0, 0)) <= PROB_TOL
+        assert abs(p1 - ref.prob_outcome(0, 1)) <= PROB_TOL
+    else:
+        # FP64 reduction of the GPU's own complex64 amplitudes
+        assert abs(tot - fsum_abs2(got)) <= PROB_TOL
+        sel = (np.arange(got.size) & 1) == 0
+        assert abs(p0 - fsum_abs2(got[sel])) <= PROB_TOL
+        assert abs(p0 - ref.prob_outcome(0, 0)) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", [128, 64])
+def test_twenty_qubit_circuit(Q, env, prec):
+    ops = C.random_circuit(20, 16, 2020, extras=True)
+    ref = O.run_circuit(20, ops)
+    got = gpu_state(Q, env, 20, ops, prec)
+    assert np.max(np.abs(got - ref.a)) <= AMP_TOL[prec]
+
+
+# ----------------------------------------------------------- density matrix
+@pytest.mark.parametrize("prec", [128, 64])
+@pytest.mark.parametrize("fusion", [0, 1])
+def test_density_every_gate_and_channel(Q, env, prec, fusion):
+    N = 4
+    rho = rand_density_vec(N, 5)
+    ops = single_ops(N, seed=9)
+    for t in range(N):
+        ops += [C.Op("DEPHASE", (t,), (), (0.13,)), C.Op("DEPOL", (t,), (), (0.21,)),
+                C.Op("PHASE", (t,), (), (0.7,))]
+    for op in ops:
+        ref = O.State(N, density=True, amps=rho)
+        ref.apply(op)
+        got = gpu_state(Q, env, N, [op], prec, density=True, fusion=fusion, init=rho)
+        err = np.max(np.abs(got - ref.a))
+        assert err <= AMP_TOL[prec] * (1 if prec == 128 else 0.1), (op, err)
+
+
+@pytest.mark.parametrize("prec", [128, 64])
+@pytest.mark.parametrize("fusion", [0, 1])
+@pytest.mark.parametrize("N", [1, 3, 6])
+def test_noisy_density_circuit(Q, env, prec, fusion, N):
+    ops = C.random_density_circuit(N, 10, 14 + N, 0.01, 0.005)
+    ref = O.run_circuit(N, ops, density=True)
+    Q.setEnvOption(env, "fusion", fusion)
+    q = Q.createDensityQureg(N, prec, env)
+    Q.applyCircuit(q, ops)
+    tr, pur = Q.calcTotalProb(q), Q.calcPurity(q)
+    probs = [Q.calcProbOfOutcome(q, t, 1) for t in range(N)]
+    got = Q.copyStateToHost(q)
+    Q.destroyQureg(q)
+    assert np.max(np.abs(got - ref.a)) <= AMP_TOL[prec]
+    if prec == 128:
+        assert abs(tr - ref.total_prob()) <= PROB_TOL
+        assert abs(pur - ref.purity()) <= PROB_TOL
+        for t in range(N):
+            assert abs(probs[t] - ref.prob_outcome(t, 1)) <= PROB_TOL
+    else:
+        d = 1 << N
+        diag = got[np.arange(d) * (d + 1)].real
+        assert abs(tr - float(np.sum(diag.astype(np.float64)))) <= PROB_TOL
+        assert abs(pur - fsum_abs2(got)) <= PROB_TOL
+        assert abs(tr - 1) <= 1e-5
+
+
+# --------------------------------------------------------------- reductions
+@pytest.mark.parametrize("prec", [128, 64])
+def test_collapse_state_vector(Q, env, prec):
+    n = 10
+    ops = C.random_circuit(n, 8, 77, extras=True)
+    for qubit, outcome in [(0, 0), (4, 1), (9, 1)]:
+        ref = O.run_circuit(n, ops)
+        pref = ref.collapse(qubit, outcome)
+        Q.setEnvOption(env, "fusion", 1)
+        q = Q.createQureg(n, prec, env)
+        Q.applyCircuit(q, ops)
+        p = Q.collapseToOutcome(q, qubit, outcome)
+        got = Q.copyStateToHost(q)
+        tot = Q.calcTotalProb(q)
+        Q.destroyQureg(q)
+        assert abs(p - pref) <= (PROB_TOL if prec == 128 else 1e-5)
+        assert np.max(np.abs(got - ref.a)) <= AMP_TOL[prec]
+        assert abs(tot - 1) <= (1e-13 if prec == 128 else 1e-5)
+
+
+@pytest.mark.parametrize("prec", [128, 64])
+def test_collapse_density(Q, env, prec):
+    N = 4
+    ops = C.random_density_circuit(N, 6, 8, 0.01, 0.005)
+    ref = O.run_circuit(N, ops, density=True)
+    pref = ref.collapse(2, 1)
+    q = Q.createDensityQureg(N, prec, env)
+    Q.applyCircuit(q, ops)
+    p = Q.collapseToOutcome(q, 2, 1)
+    got = Q.copyStateToHost(q)
+    Q.destroyQureg(q)
+    assert abs(p - pref) <= (PROB_TOL if prec == 128 else 1e-5)
+    assert np.max(np.abs(got - ref.a)) <= AMP_TOL[prec]
+
+
+def test_uniform_state_closed_forms(Q, env):
+    n = 16
+    q = Q.createQureg(n, 128, env)
+    Q.initPlusState(q)
+    for t in (0, 7, 15):
+        assert abs(Q.calcProbOfOutcome(q, t, 0) - 0.5) <= PROB_TOL
+    p = Q.collapseToOutcome(q, 5, 1)
+    a = Q.copyStateToHost(q)
+    Q.destroyQureg(q)
+    assert abs(p - 0.5) <= PROB_TOL
+    kept = ((np.arange(1 << n) >> 5) & 1) == 1
+    assert np.max(np.abs(a[kept] - np.sqrt(2) * 2 ** (-n / 2))) <= 1e-15
+    assert np.all(a[~kept] == 0)
+
+
+# ------------------------------------------------------------ edge cases
+def test_amplitude_ranges_and_ragged_copies(Q, env):
+    n = 13
+    psi = rand_state(n, 4)
+    q = Q.createQureg(n, 128, env)
+    Q.setAmps(q, psi[:1000], 0)
+    Q.setAmps(q, psi[1000:], 1000)
+    assert np.array_equal(Q.copyStateToHost(q), psi)
+    assert np.array_equal(Q.copyStateToHost(q, 4095, 17), psi[4095:4112])
+    assert Q.copyStateToHost(q, 5, 0).size == 0
+    Q.destroyQureg(q)
+    q = Q.createQureg(n, 64, env)
+    Q.setAmps(q, psi)
+    got = Q.copyStateToHost(q)
+    assert np.max(np.abs(got - psi)) <= 1e-7
+    Q.destroyQureg(q)
+
+
+def test_errors_leave_state_unchanged(Q, env):
+    n = 6
+    psi = rand_state(n, 8)
+    q = Q.createQureg(n, 128, env)
+    Q.setAmps(q, psi)
+    bad = [
+        (lambda: Q.hadamard(q, n), "QS_E_QUBIT"),
+        (lambda: Q.hadamard(q, -1), "QS_E_QUBIT"),
+        (lambda: Q.controlledNot(q, 2, 2), "QS_E_DUP"),
+        (lambda: Q.multiControlledPhaseFlip(q, [1, 3, 1]), "QS_E_DUP"),
+        (lambda: Q.unitary(q, 0, [[1, 1], [0, 1]]), "QS_E_UNITARY"),
+        (lambda: Q.compactUnitary(q, 0, 0.5, 0.5), "QS_E_UNITARY"),
+        (lambda: Q.mixDephasing(q, 0, 0.1), "QS_E_NOT_DENSITY"),
+        (lambda: Q.calcPurity(q), "QS_E_NOT_DENSITY"),
+        (lambda: Q.calcProbOfOutcome(q, 0, 2), "QS_E_PROB"),
+        (lambda: Q.applyCircuit(q, [C.Op("H", (0,)), C.Op("H", (9,))]), "QS_E_QUBIT"),
+        (lambda: Q.copyStateToHost(q, 60, 10), "QS_E_ARG"),
+    ]
+    for f, name in bad:
+        with pytest.raises(Q.QSimError) as e:
+            f()
+        assert e.value.name == name
+    assert np.array_equal(Q.copyStateToHost(q), psi)
+    Q.destroyQureg(q)
+    with pytest.raises(Q.QSimError) as e:
+        Q.hadamard(q, 0)
+    assert e.value.name == "QS_E_HANDLE"
+    d = Q.createDensityQureg(2, 128, env)
+    for f in (lambda: Q.mixDephasing(d, 0, 0.51), lambda: Q.mixDepolarising(d, 1, 0.76)):
+        with pytest.raises(Q.QSimError) as e:
+            f()
+        assert e.value.name == "QS_E_PROB"
+    Q.destroyQureg(d)
+
+
+def test_zero_probability_collapse_is_refused(Q, env):
+    q = Q.createQureg(5, 128, env)
+    with pytest.raises(Q.QSimError) as e:
+        Q.collapseToOutcome(q, 3, 1)
+    assert e.value.name == "QS_E_ZERO_PROB"
+    a = Q.copyStateToHost(q)
+    assert a[0] == 1 and np.all(a[1:] == 0)
+    Q.destroyQureg(q)
+
+
+def test_budget_and_torch_allocator(Q):
+    import torch
+    e = Q.createQuESTEnv()
+    Q.setEnvOption(e, "budget_bytes", 1 << 20)
+    with pytest.raises(Q.QSimError) as err:
+        Q.createQureg(17, 128, e)          # 2 MiB > 1 MiB
+    assert err.value.name == "QS_E_NOMEM"
+    Q.setEnvOption(e, "budget_bytes", 0)
+    Q.use_torch_allocator(e)
+    before = torch.cuda.memory_allocated()
+    q = Q.createQureg(20, 128, e)
+    assert torch.cuda.memory_allocated() - before >= 16 << 20
+    Q.hadamard(q, 3)
+    assert abs(Q.calcProbOfOutcome(q, 3, 1) - 0.5) <= PROB_TOL
+    s = torch.cuda.Stream()
+    Q.setStream(e, s)
+    Q.hadamard(q, 3)
+    assert abs(Q.calcProbOfOutcome(q, 3, 0) - 1.0) <= PROB_TOL
+    Q.destroyQureg(q)
+    Q.destroyQuESTEnv(e)
