@@ -87,9 +87,19 @@ int syncQuESTEnv(QuESTEnv env);
  *   "tile_qubits"   k of a fused tile, 0 = automatic
  *   "max_fused_ops" cap on operations per fused pass (0 = automatic)
  *   "budget_bytes"  cap on the register memory of this env (0 = none)
+ *   "arith"         complex128 arithmetic of fused passes: 0 = IEEE FP64
+ *                   (default), 1 = double-float (each real a float pair
+ *                   hi + lo on the FP32 pipes; a few units of 2^-48 of error
+ *                   per update instead of 2^-53).  Single-gate passes,
+ *                   reductions and measurement always use FP64.
+ *   "profile"       1 = time every kernel launch with CUDA events (see
+ *                   getKernelStats), 0 = off (default)
  * Unknown keys give QS_E_ARG. */
 int setEnvOption(QuESTEnv env, const char *key, int64_t value);
-/* getEnvOption: reads an option back. */
+/* getEnvOption: reads an option back, or a counter of the env:
+ *   "used_bytes" register memory held, "launches" kernels launched,
+ *   "fused_passes" fused-tile passes launched, "fused_vops" vector
+ *   operations those passes applied. */
 int getEnvOption(QuESTEnv env, const char *key, int64_t *value);
 /* setAllocator: device allocations of later registers go through
  * alloc(bytes, ctx) / release(ptr, ctx); null functions restore the built-in
@@ -207,6 +217,24 @@ typedef struct {
  * index in qsLastError, nothing applied), then applies them in order, as if
  * by the individual calls. */
 int applyCircuit(Qureg q, const QSOp *ops, int64_t numOps);
+
+/* ---------------------------------------------------------- kernel stats */
+/* Per-kernel-class timing, for roofline reporting.  With option "profile"
+ * set to 1, every kernel launch of the env is bracketed by CUDA events on
+ * the env's stream and charged to its class (a name such as
+ * "sv_pair_gen_c128").  getKernelStats waits for the stream, then fills up
+ * to maxOut entries and writes the number of classes to *count.  Bytes and
+ * flops are algorithmic: the amplitudes a launch must read and write and
+ * the floating-point operations its arithmetic needs (FMA = 2). */
+typedef struct {
+    char name[48];
+    int64_t launches;
+    double total_ms;
+    double bytes;
+    double flops;
+} QSKernelStat;
+int getKernelStats(QuESTEnv env, QSKernelStat *out, int maxOut, int *count);
+int resetKernelStats(QuESTEnv env);
 
 #ifdef __cplusplus
 }

@@ -343,6 +343,8 @@ int destroyQuESTEnv(QuESTEnv e) {
         g_regs.erase(it);
       }
     }
+    env.prof.reset();
+    for (cudaEvent_t ev : env.prof.pool) cudaEventDestroy(ev);
     cudaFree(env.d_partial);
     cudaFree(env.d_result);
     cudaFreeHost(env.h_result);
@@ -388,6 +390,16 @@ int setEnvOption(QuESTEnv e, const char* key, int64_t value) {
     } else if (k == "budget_bytes") {
       if (value < 0) fail(QS_E_ARG, "budget_bytes must be >= 0");
       env.budget = value;
+    } else if (k == "arith") {
+      if (value != 0 && value != 1) fail(QS_E_ARG, "arith must be 0 (FP64) or 1 (double-float)");
+      {
+        std::lock_guard<std::mutex> lk(g_mu);
+        for (int64_t id : env.regs) flush(*g_regs.at(id));
+      }
+      env.arith = value;
+    } else if (k == "profile") {
+      if (value != 0 && value != 1) fail(QS_E_ARG, "profile must be 0 or 1");
+      env.profile = value;
     } else {
       fail(QS_E_ARG, "unknown option " + k);
     }
@@ -405,6 +417,11 @@ int getEnvOption(QuESTEnv e, const char* key, int64_t* value) {
     else if (k == "max_fused_ops") *value = env.max_fused_ops;
     else if (k == "budget_bytes") *value = env.budget;
     else if (k == "used_bytes") *value = env.used;
+    else if (k == "profile") *value = env.profile;
+    else if (k == "arith") *value = env.arith;
+    else if (k == "launches") *value = env.launches;
+    else if (k == "fused_passes") *value = env.fused_passes;
+    else if (k == "fused_vops") *value = env.fused_vops;
     else fail(QS_E_ARG, "unknown option " + k);
   });
 }
@@ -663,6 +680,34 @@ int calcPurity(Qureg q, double* out) {
     Reg& r = reg_of(q);
     if (!r.density) fail(QS_E_NOT_DENSITY, "purity of a state vector");
     *out = reduce_purity(*r.env, r);
+  });
+}
+
+int getKernelStats(QuESTEnv e, QSKernelStat* out, int maxOut, int* count) {
+  return guarded([&] {
+    Env& env = env_of(e);
+    need(count, "count");
+    if (maxOut > 0) need(out, "out");
+    QS_CUDA(cudaStreamSynchronize(env.stream));
+    env.prof.collect();
+    *count = int(env.prof.stats.size());
+    for (int i = 0; i < maxOut && i < *count; ++i) {
+      const KStat& k = env.prof.stats[i];
+      std::memset(&out[i], 0, sizeof(QSKernelStat));
+      std::strncpy(out[i].name, k.name.c_str(), sizeof(out[i].name) - 1);
+      out[i].launches = k.launches;
+      out[i].total_ms = k.ms;
+      out[i].bytes = k.bytes;
+      out[i].flops = k.flops;
+    }
+  });
+}
+
+int resetKernelStats(QuESTEnv e) {
+  return guarded([&] {
+    Env& env = env_of(e);
+    QS_CUDA(cudaStreamSynchronize(env.stream));
+    env.prof.reset();
   });
 }
 

@@ -53,12 +53,28 @@ Mat2<R> to_mat(const GateOp& op) {
   return g;
 }
 
+// Floating-point operations of one pair update (FMA counted as 2).
+constexpr double kPairFlops[5] = {28, 8, 12, 12, 0};  // GEN, H, SX, SY, X
+const char* kPairName[5] = {"gen", "h", "sx", "sy", "x"};
+
+template <typename R>
+std::string kname(const char* base, const char* kind = nullptr) {
+  std::string s(base);
+  if (kind) s += std::string("_") + kind;
+  return s + (sizeof(R) == 8 ? "_c128" : "_c64");
+}
+
+template <typename R>
+constexpr double amp_bytes() { return 2.0 * sizeof(R); }
+
 template <typename R, int K>
 void sv_pair(Env& env, Reg& r, const GateOp& op) {
   auto bits = ctrl_bits(op.cmask, 1);
   bits.push_back({op.t, 0});
   const Fixed fx = make_fixed(bits);
   const int64_t nsel = r.dim >> fx.n;
+  KTimer kt(env, kname<R>("sv_pair", kPairName[K]).c_str(), double(nsel) * 4 * amp_bytes<R>(),
+            double(nsel) * kPairFlops[K]);
   k_sv_pair<R, K, kUnroll><<<grid_for(env, nsel, kUnroll), kThreads, 0, env.stream>>>(
       static_cast<cvec<R>*>(r.d), nsel, int64_t(1) << op.t, fx, to_mat<R>(op));
 }
@@ -68,6 +84,8 @@ void dm_pair(Env& env, Reg& r, const GateOp& op) {
   const int N = r.n;
   const Fixed fx = make_fixed({{op.t, 0}, {op.t + N, 0}});
   const int64_t nsel = r.dim >> 2;
+  KTimer kt(env, kname<R>("dm_quad", kPairName[K]).c_str(), double(nsel) * 8 * amp_bytes<R>(),
+            double(nsel) * 4 * kPairFlops[K]);
   k_dm_gate<R, K, 2><<<grid_for(env, nsel, 2), kThreads, 0, env.stream>>>(
       static_cast<cvec<R>*>(r.d), nsel, int64_t(1) << op.t, int64_t(1) << (op.t + N), op.cmask,
       op.cmask << N, fx, to_mat<R>(op));
@@ -88,6 +106,7 @@ void launch_typed(Env& env, Reg& r, const GateOp& op) {
         bits.push_back({op.t, 1});
         const Fixed fx = make_fixed(bits);
         const int64_t nsel = r.dim >> fx.n;
+        KTimer kt(env, kname<R>("sv_phase").c_str(), double(nsel) * 2 * amp_bytes<R>(), double(nsel) * 6);
         k_sv_diag<R, DK_PHASE, kUnroll><<<grid_for(env, nsel, kUnroll), kThreads, 0, env.stream>>>(
             a, nsel, fx, R(op.m[0]), R(op.m[1]));
         return;
@@ -95,6 +114,7 @@ void launch_typed(Env& env, Reg& r, const GateOp& op) {
       case OpK::SIGN: {
         const Fixed fx = make_fixed(ctrl_bits(op.cmask, 1));
         const int64_t nsel = r.dim >> fx.n;
+        KTimer kt(env, kname<R>("sv_sign").c_str(), double(nsel) * 2 * amp_bytes<R>(), 0);
         k_sv_diag<R, DK_SIGN, kUnroll><<<grid_for(env, nsel, kUnroll), kThreads, 0, env.stream>>>(
             a, nsel, fx, R(0), R(0));
         return;
@@ -109,22 +129,30 @@ void launch_typed(Env& env, Reg& r, const GateOp& op) {
     case OpK::SX: dm_pair<R, PK_SX>(env, r, op); return;
     case OpK::SY: dm_pair<R, PK_SY>(env, r, op); return;
     case OpK::X: dm_pair<R, PK_X>(env, r, op); return;
-    case OpK::PHASE:
+    case OpK::PHASE: {
+      KTimer kt(env, kname<R>("dm_phase").c_str(), double(r.dim) * amp_bytes<R>(), double(r.dim) * 3);
       k_dm_diag<R, DD_PHASE><<<grid_for(env, r.dim, 1), kThreads, 0, env.stream>>>(
           a, r.dim, N, op.cmask, op.t, R(op.m[0]), R(op.m[1]));
       return;
-    case OpK::SIGN:
+    }
+    case OpK::SIGN: {
+      const double f = std::ldexp(1.0, -__builtin_popcountll(op.cmask));
+      KTimer kt(env, kname<R>("dm_sign").c_str(), double(r.dim) * 4 * f * (1 - f) * amp_bytes<R>(), 0);
       k_dm_diag<R, DD_SIGN><<<grid_for(env, r.dim, 1), kThreads, 0, env.stream>>>(
           a, r.dim, N, op.cmask, 0, R(0), R(0));
       return;
-    case OpK::DEPHASE:
+    }
+    case OpK::DEPHASE: {
+      KTimer kt(env, kname<R>("dm_dephase").c_str(), double(r.dim) * amp_bytes<R>(), double(r.dim));
       k_dm_diag<R, DD_DEPHASE><<<grid_for(env, r.dim, 1), kThreads, 0, env.stream>>>(
           a, r.dim, N, 0, op.t, R(1.0 - 2.0 * op.m[0]), R(0));
       return;
+    }
     case OpK::DEPOL: {
       const double p = op.m[0];
       const Fixed fx = make_fixed({{op.t, 0}, {op.t + N, 0}});
       const int64_t nsel = r.dim >> 2;
+      KTimer kt(env, kname<R>("dm_depol").c_str(), double(nsel) * 8 * amp_bytes<R>(), double(nsel) * 16);
       k_dm_depol<R, 2><<<grid_for(env, nsel, 2), kThreads, 0, env.stream>>>(
           a, nsel, int64_t(1) << op.t, int64_t(1) << (op.t + N), fx, R(1.0 - 2.0 * p / 3.0),
           R(2.0 * p / 3.0), R(1.0 - 4.0 * p / 3.0));
@@ -139,6 +167,7 @@ template <typename R>
 void sumsq(Env& env, const Reg& r, const Fixed& fx, int64_t nsel) {
   const int blocks = int(std::max<int64_t>(
       1, std::min<int64_t>(kRedMaxBlocks, (nsel + kRedThreads * 4 - 1) / (kRedThreads * 4))));
+  KTimer kt(env, kname<R>("reduce_sumsq").c_str(), double(nsel) * amp_bytes<R>(), double(nsel) * 4, 2);
   k_sumsq<R, 4><<<blocks, kRedThreads, 0, env.stream>>>(static_cast<const cvec<R>*>(r.d), nsel, fx,
                                                         env.d_partial);
   k_sum_partials<<<1, 1024, 0, env.stream>>>(env.d_partial, blocks, env.d_result);
@@ -149,6 +178,7 @@ void sumdiag(Env& env, const Reg& r, int q, int o) {
   const int64_t d = int64_t(1) << r.n;
   const int blocks = int(std::max<int64_t>(
       1, std::min<int64_t>(kRedMaxBlocks, (d + kRedThreads - 1) / kRedThreads)));
+  KTimer kt(env, kname<R>("reduce_diag").c_str(), double(d) * amp_bytes<R>(), double(d), 2);
   k_sumdiag<R><<<blocks, kRedThreads, 0, env.stream>>>(static_cast<const cvec<R>*>(r.d), r.n, q, o,
                                                        env.d_partial);
   k_sum_partials<<<1, 1024, 0, env.stream>>>(env.d_partial, blocks, env.d_result);
@@ -206,6 +236,9 @@ double reduce_purity(Env& env, Reg& r) {
 
 void launch_collapse(Env& env, Reg& r, int q, int o, double scale) {
   const int g = grid_for(env, r.dim, 1);
+  const double keep = r.density ? 0.25 : 0.5;
+  KTimer kt(env, r.prec == QS_C128 ? "collapse_c128" : "collapse_c64",
+            double(r.dim) * (1 + keep) * (r.prec == QS_C128 ? 16 : 8), double(r.dim) * keep * 2);
   if (r.density) {
     if (r.prec == QS_C128)
       k_collapse_dm<double><<<g, kThreads, 0, env.stream>>>(static_cast<double2*>(r.d), r.dim, r.n, q, o, scale);
@@ -222,6 +255,7 @@ void launch_collapse(Env& env, Reg& r, int q, int o, double scale) {
 
 void launch_fill(Env& env, Reg& r, double re, double im) {
   const int g = grid_for(env, r.dim, 1);
+  KTimer kt(env, r.prec == QS_C128 ? "fill_c128" : "fill_c64", double(r.dim) * (r.prec == QS_C128 ? 16 : 8), 0);
   if (r.prec == QS_C128)
     k_fill<double><<<g, kThreads, 0, env.stream>>>(static_cast<double2*>(r.d), r.dim, re, im);
   else
@@ -247,6 +281,7 @@ __global__ void k_d2f(const double2* __restrict__ s, float2* __restrict__ d, int
 
 void launch_convert(Env& env, const void* src, void* dst, int64_t count, bool to_double) {
   const int g = grid_for(env, count, 1);
+  KTimer kt(env, "convert", double(count) * 24, 0);
   if (to_double)
     k_f2d<<<g, kThreads, 0, env.stream>>>(static_cast<const float2*>(src), static_cast<double2*>(dst), count);
   else

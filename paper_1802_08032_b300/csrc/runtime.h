@@ -47,6 +47,26 @@ struct Error {
 
 struct Env;
 
+// Per-kernel-class event timing (option "profile").
+struct KStat {
+  std::string name;
+  int64_t launches = 0;
+  double ms = 0, bytes = 0, flops = 0;
+};
+struct KPending {
+  int cls;
+  cudaEvent_t a, b;
+};
+struct Profiler {
+  std::vector<KStat> stats;
+  std::vector<KPending> pending;
+  std::vector<cudaEvent_t> pool;
+  int class_of(const std::string& name);
+  cudaEvent_t event();
+  void collect();  // caller has synchronised the stream
+  void reset();
+};
+
 struct Reg {
   int64_t id = 0;
   Env* env = nullptr;
@@ -72,6 +92,13 @@ struct Env {
   int64_t max_fused_ops = 0;
   int64_t budget = 0;
   int64_t used = 0;
+  int64_t profile = 0;
+  int64_t arith = 0;         // complex128 arithmetic of fused passes: 0 = IEEE FP64, 1 = double-float
+  Profiler prof;
+  // counters (readable through getEnvOption)
+  int64_t launches = 0;      // kernel launches issued
+  int64_t fused_passes = 0;  // fused-tile passes launched
+  int64_t fused_vops = 0;    // vector operations applied by fused passes
   // allocator hook
   void* (*alloc)(size_t, void*) = nullptr;
   void (*release)(void*, void*) = nullptr;
@@ -84,6 +111,21 @@ struct Env {
   double2* d_stage = nullptr;
   int64_t stage_amps = 0;
   std::vector<int64_t> regs;
+};
+
+// Brackets one kernel launch with events when profiling is on: construct
+// right before the launch, destroy right after it.  Counts launches always.
+class KTimer {
+ public:
+  KTimer(Env& env, const char* name, double bytes, double flops, int nlaunch = 1);
+  ~KTimer();
+  KTimer(const KTimer&) = delete;
+  KTimer& operator=(const KTimer&) = delete;
+
+ private:
+  Env& env_;
+  int cls_ = -1;
+  cudaEvent_t a_ = nullptr;
 };
 
 // Entry points of the kernel layer (implemented in the .cu files).

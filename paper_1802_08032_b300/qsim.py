@@ -61,6 +61,12 @@ class QSOp(ctypes.Structure):
                 ("params", ctypes.c_double * 8)]
 
 
+class QSKernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double),
+                ("flops", ctypes.c_double)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -105,6 +111,8 @@ SIGNATURES = {
     "collapseToOutcome": [Qureg, _I, _I, _P(_D)],
     "calcPurity": [Qureg, _P(_D)],
     "applyCircuit": [Qureg, _P(QSOp), _I64],
+    "getKernelStats": [QuESTEnv, _P(QSKernelStat), _I, _P(_I)],
+    "resetKernelStats": [QuESTEnv],
 }
 EXTRA_SIGNATURES: dict = {}
 
@@ -367,3 +375,18 @@ def applyCircuit(q, ops):
     else:
         arr, n = to_qsops(ops)
     _check(LIB.applyCircuit(q, arr, n))
+
+
+# ------------------------------------------------------------ kernel stats
+def getKernelStats(env) -> list:
+    """[{name, launches, total_ms, bytes, flops}] per kernel class."""
+    cnt = ctypes.c_int()
+    _check(LIB.getKernelStats(env, None, 0, ctypes.byref(cnt)))
+    arr = (QSKernelStat * max(1, cnt.value))()
+    _check(LIB.getKernelStats(env, arr, cnt.value, ctypes.byref(cnt)))
+    return [{"name": a.name.decode(), "launches": a.launches, "total_ms": a.total_ms,
+             "bytes": a.bytes, "flops": a.flops} for a in arr[:cnt.value]]
+
+
+def resetKernelStats(env):
+    _check(LIB.resetKernelStats(env))
