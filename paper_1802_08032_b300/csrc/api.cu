@@ -345,6 +345,7 @@ int destroyQuESTEnv(QuESTEnv e) {
     }
     env.prof.reset();
     for (cudaEvent_t ev : env.prof.pool) cudaEventDestroy(ev);
+    free_fused_buffers(env);
     cudaFree(env.d_partial);
     cudaFree(env.d_result);
     cudaFreeHost(env.h_result);

@@ -1,13 +1,410 @@
-// Flush of a register's queued gates.
+// Flush of a register's queued gates: fusion planner and fused-tile launch.
+//
+// Planner.  Gates are first expanded into vector operations on the stored
+// 2^nq vector (a density-matrix gate G on qubit t becomes G on bit t and
+// conj(G) on bit t+N, Eq. 2).  Each operation has X bits (where it mixes
+// amplitudes: the target of a pair update, both bits of a depolarising
+// quad) and Z bits (where it only reads the index: controls, the bits of
+// diagonal operations).  A pass takes operations in order while their X
+// bits fit in the k tile qubits; an operation that does not fit is
+// deferred, and a later operation may move ahead of deferred ones only if
+// it commutes with all of them (no X bit of either touches a bit of the
+// other).  Passes repeat until the queue is empty.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "fused_kernel.cuh"
 #include "runtime.h"
 
 namespace qs {
 
+namespace {
+
+struct VOp {
+  FKind kind;
+  bool conj = false;
+  int b0 = -1, b1 = -1;  // pair target (b0); DEPOL row/column; DEPH the two compared bits
+  uint64_t cond = 0;     // bits that must all be 1 (controls; PHASE/SIGN diagonal support)
+  double c[8] = {};
+
+  uint64_t xmask() const {
+    if (kind <= FK_X) return uint64_t(1) << b0;
+    if (kind == FK_DEPOL) return (uint64_t(1) << b0) | (uint64_t(1) << b1);
+    return 0;
+  }
+  uint64_t zmask() const {
+    uint64_t z = cond;
+    if (kind == FK_DEPH) z |= (uint64_t(1) << b0) | (uint64_t(1) << b1);
+    return z;
+  }
+};
+
+VOp pair_op(OpK k, int bit, uint64_t cond, const double* m, bool conj) {
+  VOp v;
+  v.kind = FKind(int(k));  // GEN..X share the numbering
+  v.b0 = bit;
+  v.cond = cond;
+  v.conj = conj;
+  if (k == OpK::GEN) std::memcpy(v.c, m, sizeof(v.c));
+  if (cond != 0 && (k == OpK::H || k == OpK::SX || k == OpK::SY)) {
+    // the engine applies these unscaled (a global factor), which a control
+    // would break: use the explicit matrix instead
+    const double h = std::sqrt(0.5);
+    const double H[8] = {h, 0, h, 0, h, 0, -h, 0};
+    const double SX[8] = {0.5, 0.5, 0.5, -0.5, 0.5, -0.5, 0.5, 0.5};
+    const double SY[8] = {0.5, 0.5, -0.5, -0.5, 0.5, 0.5, 0.5, 0.5};
+    const double* src = k == OpK::H ? H : (k == OpK::SX ? SX : SY);
+    for (int e = 0; e < 8; ++e) v.c[e] = src[e];
+    v.kind = FK_GEN;
+  }
+  return v;
+}
+
+void expand(const Reg& r, const GateOp& op, std::vector<VOp>& out) {
+  const int N = r.n;
+  switch (op.k) {
+    case OpK::GEN: case OpK::H: case OpK::SX: case OpK::SY: case OpK::X:
+      out.push_back(pair_op(op.k, op.t, op.cmask, op.m, false));
+      if (r.density) out.push_back(pair_op(op.k, op.t + N, op.cmask << N, op.m, true));
+      return;
+    case OpK::PHASE: {
+      VOp v;
+      v.kind = FK_PHASE;
+      v.cond = op.cmask | (uint64_t(1) << op.t);
+      v.c[0] = op.m[0];
+      v.c[1] = op.m[1];
+      out.push_back(v);
+      if (r.density) {  // column factor e^{-i phi}
+        v.cond <<= N;
+        v.c[1] = -op.m[1];
+        out.push_back(v);
+      }
+      return;
+    }
+    case OpK::SIGN: {
+      VOp v;
+      v.kind = FK_SIGN;
+      v.cond = op.cmask;
+      out.push_back(v);
+      if (r.density) {
+        v.cond <<= N;
+        out.push_back(v);
+      }
+      return;
+    }
+    case OpK::DEPHASE: {
+      VOp v;
+      v.kind = FK_DEPH;
+      v.b0 = op.t;
+      v.b1 = op.t + N;
+      v.c[0] = 1.0 - 2.0 * op.m[0];
+      out.push_back(v);
+      return;
+    }
+    case OpK::DEPOL: {
+      const double p = op.m[0];
+      VOp v;
+      v.kind = FK_DEPOL;
+      v.b0 = op.t;
+      v.b1 = op.t + N;
+      v.c[0] = 1.0 - 2.0 * p / 3.0;
+      v.c[1] = 2.0 * p / 3.0;
+      v.c[2] = 1.0 - 4.0 * p / 3.0;
+      out.push_back(v);
+      return;
+    }
+  }
+}
+
+// Appends FK_SCALE operations carrying the scalar factors that the engine's
+// unscaled H / sqrt(X) / sqrt(Y) leave out: one at the end of the pass, and
+// one earlier whenever the pending growth reaches 2^40.
+void add_scales(std::vector<VOp>& ops) {
+  std::vector<VOp> out;
+  out.reserve(ops.size() + 2);
+  double f = 1.0, growth = 0.0;
+  auto flush_scale = [&] {
+    if (f == 1.0) return;
+    VOp s;
+    s.kind = FK_SCALE;
+    s.c[0] = f;
+    out.push_back(s);
+    f = 1.0;
+    growth = 0.0;
+  };
+  for (const VOp& v : ops) {
+    out.push_back(v);
+    if (v.kind == FK_H) {
+      f *= std::sqrt(0.5);
+      growth += 0.5;
+    } else if (v.kind == FK_SX || v.kind == FK_SY) {
+      f *= 0.5;
+      growth += 1.0;
+    }
+    if (growth >= 40.0) flush_scale();
+  }
+  flush_scale();
+  ops.swap(out);
+}
+
+struct Pass {
+  std::vector<int> q;  // tile qubits, ascending
+  std::vector<VOp> ops;
+};
+
+int popc(uint64_t x) { return __builtin_popcountll(x); }
+
+std::vector<Pass> plan(const std::vector<VOp>& ops, int nq, int k, int L, int64_t max_ops) {
+  std::vector<Pass> passes;
+  std::vector<VOp> rem = ops;
+  const uint64_t low = (uint64_t(1) << L) - 1;
+  while (!rem.empty()) {
+    Pass p;
+    uint64_t tile = low, bx = 0, ball = 0;
+    std::vector<VOp> deferred;
+    for (const VOp& v : rem) {
+      const uint64_t x = v.xmask(), z = v.zmask();
+      const bool commutes = (x & ball) == 0 && ((x | z) & bx) == 0;
+      const bool fits = popc(tile | x) <= k;
+      const bool room = int64_t(p.ops.size()) < max_ops;
+      if (commutes && fits && room) {
+        tile |= x;
+        p.ops.push_back(v);
+      } else {
+        deferred.push_back(v);
+        bx |= x;
+        ball |= x | z;
+      }
+    }
+    // pad the tile to exactly k qubits with the lowest unused ones
+    for (int b = 0; b < nq && popc(tile) < k; ++b) tile |= uint64_t(1) << b;
+    for (int b = 0; b < nq; ++b)
+      if ((tile >> b) & 1) p.q.push_back(b);
+    add_scales(p.ops);
+    passes.push_back(std::move(p));
+    rem.swap(deferred);
+  }
+  return passes;
+}
+
+// Coefficient form of the kernel's arithmetic.
+enum class Arith { F32, F64, DF };
+
+void set_coeffs(FOp& f, const double* c, Arith a) {
+  for (int e = 0; e < 8; ++e) {
+    if (a == Arith::F64) {
+      f.c.d[e] = c[e];
+    } else {
+      const float hi = float(c[e]);
+      f.c.f[e] = hi;
+      if (a == Arith::DF) f.c.f[8 + e] = float(c[e] - double(hi));
+    }
+  }
+}
+
+// Device-side op encoding for one pass: stages of R register bits.  Stage op
+// ranges are relative to the pass's first op.
+void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fops,
+                 std::vector<FStage>& fst) {
+  const int32_t first = int32_t(fops.size());
+  int lpos[64];
+  for (int i = 0; i < 64; ++i) lpos[i] = -1;
+  for (int i = 0; i < int(p.q.size()); ++i) lpos[p.q[i]] = i;
+  auto local_mask = [&](uint64_t x) {
+    uint32_t m = 0;
+    for (int b = 0; b < 64; ++b)
+      if ((x >> b) & 1) m |= 1u << lpos[b];
+    return m;
+  };
+
+  size_t i = 0;
+  while (i < p.ops.size()) {
+    // grow the stage's register set while the X bits fit in R
+    uint32_t P = 0;
+    size_t j = i;
+    while (j < p.ops.size()) {
+      const uint32_t need = local_mask(p.ops[j].xmask());
+      if (popc(P | need) > R) break;
+      P |= need;
+      ++j;
+    }
+    // pad with the highest unused local bits (keeps low bits on lanes)
+    for (int b = k - 1; b >= 0 && popc(P) < R; --b) P |= 1u << b;
+    FStage st{};
+    int idx[32];
+    int n = 0;
+    for (int b = 0; b < k; ++b)
+      if ((P >> b) & 1) {
+        idx[b] = n;
+        st.pbits[n++] = uint8_t(b);
+      }
+    st.op_begin = int32_t(fops.size()) - first;
+    for (size_t o = i; o < j; ++o) {
+      const VOp& v = p.ops[o];
+      FOp f{};
+      f.kind = v.kind;
+      f.conj = v.conj ? 1 : 0;
+      if (v.kind <= FK_X || v.kind == FK_DEPOL) f.i0 = uint8_t(idx[lpos[v.b0]]);
+      if (v.kind == FK_DEPOL) f.i1 = uint8_t(idx[lpos[v.b1]]);
+      for (int b = 0; b < 64; ++b) {
+        if (!((v.cond >> b) & 1)) continue;
+        if (lpos[b] < 0) f.gmask |= uint64_t(1) << b;
+        else if ((P >> lpos[b]) & 1) f.rmask |= 1u << idx[lpos[b]];
+        else f.lmask |= 1u << lpos[b];
+      }
+      if (v.kind == FK_DEPH) {
+        auto src = [&](int bit, uint8_t& s, uint8_t& pos) {
+          if (lpos[bit] < 0) { s = BS_GLOBAL; pos = uint8_t(bit); }
+          else if ((P >> lpos[bit]) & 1) { s = BS_REG; pos = uint8_t(idx[lpos[bit]]); }
+          else { s = BS_LOCAL; pos = uint8_t(lpos[bit]); }
+        };
+        src(v.b0, f.asrc, f.apos);
+        src(v.b1, f.bsrc, f.bpos);
+      }
+      set_coeffs(f, v.c, arith);
+      fops.push_back(f);
+    }
+    st.op_end = int32_t(fops.size()) - first;
+    fst.push_back(st);
+    i = j;
+  }
+}
+
+double vop_flops(const VOp& v, int nq) {
+  const double dim = std::ldexp(1.0, nq), f = std::ldexp(1.0, -popc(v.cond));
+  static const double pair_flops[5] = {28, 4, 8, 8, 0};  // H, sqrt(X), sqrt(Y) unscaled
+  if (v.kind <= FK_X) return dim / 2 * f * pair_flops[v.kind];
+  if (v.kind == FK_PHASE) return dim * f * 6;
+  if (v.kind == FK_SCALE) return dim * 2;
+  if (v.kind == FK_DEPH) return dim / 2 * 2;
+  if (v.kind == FK_DEPOL) return dim / 4 * 16;
+  return 0;
+}
+
+template <class A, int R>
+void launch_pass(Env& env, Reg& r, const FPass& fp, const FOp* d_ops, const FStage* d_st,
+                 double flops, const char* name) {
+  const size_t smem = fused_smem_bytes<A>(fp.k, fp.L, fp.op_count, fp.stage_end - fp.stage_begin);
+  static bool attr_set = false;
+  if (!attr_set) {
+    QS_CUDA(cudaFuncSetAttribute(k_fused<A, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024));
+    attr_set = true;
+  }
+  const int threads = 1 << (fp.k - R);
+  const int64_t grid = std::min<int64_t>(fp.ntiles, int64_t(env.sms) * 2);
+  const double bytes = std::ldexp(2.0 * sizeof(typename A::Store), r.nq);
+  KTimer kt(env, name, bytes, flops);
+  k_fused<A, R><<<int(grid), threads, smem, env.stream>>>(static_cast<typename A::Store*>(r.d), fp,
+                                                          d_ops, d_st);
+}
+
+// Grows the env's op / stage staging (pinned host + device) to fit.
+void ensure_fused_buffers(Env& env, size_t nops, size_t nst) {
+  if (env.fcopied) QS_CUDA(cudaEventSynchronize(env.fcopied));  // staging free to overwrite
+  if (nops * sizeof(FOp) > env.fops_cap) {
+    if (env.d_fops) { cudaFree(env.d_fops); cudaFreeHost(env.h_fops); env.d_fops = env.h_fops = nullptr; }
+    env.fops_cap = std::max(nops, size_t(4096)) * sizeof(FOp);
+    QS_CUDA(cudaMalloc(&env.d_fops, env.fops_cap));
+    QS_CUDA(cudaMallocHost(&env.h_fops, env.fops_cap));
+  }
+  if (nst * sizeof(FStage) > env.fst_cap) {
+    if (env.d_fst) { cudaFree(env.d_fst); cudaFreeHost(env.h_fst); env.d_fst = env.h_fst = nullptr; }
+    env.fst_cap = std::max(nst, size_t(1024)) * sizeof(FStage);
+    QS_CUDA(cudaMalloc(&env.d_fst, env.fst_cap));
+    QS_CUDA(cudaMallocHost(&env.h_fst, env.fst_cap));
+  }
+  if (!env.fcopied) QS_CUDA(cudaEventCreateWithFlags(&env.fcopied, cudaEventDisableTiming));
+}
+
+// Tile parameters per precision: R register bits, maximum k, low qubits L.
+struct TileCfg {
+  int R, kmax, L;
+};
+TileCfg tile_cfg(const Reg& r) { return r.prec == QS_C128 ? TileCfg{4, 12, 3} : TileCfg{5, 13, 4}; }
+
+}  // namespace
+
+bool fusable(const Reg& r) {
+  const TileCfg c = tile_cfg(r);
+  return r.nq >= c.R + 5;
+}
+
+void free_fused_buffers(Env& env) {
+  if (env.fcopied) cudaEventSynchronize(env.fcopied);
+  if (env.d_fops) { cudaFree(env.d_fops); cudaFreeHost(env.h_fops); }
+  if (env.d_fst) { cudaFree(env.d_fst); cudaFreeHost(env.h_fst); }
+  if (env.fcopied) cudaEventDestroy(env.fcopied);
+  env.d_fops = env.h_fops = env.d_fst = env.h_fst = nullptr;
+  env.fops_cap = env.fst_cap = 0;
+  env.fcopied = nullptr;
+}
+
 void flush(Reg& r) {
   if (r.queue.empty()) return;
-  std::vector<GateOp> ops;
-  ops.swap(r.queue);
-  for (const GateOp& op : ops) launch_op(*r.env, r, op);
+  std::vector<GateOp> q;
+  q.swap(r.queue);
+  Env& env = *r.env;
+  if (!fusable(r)) {
+    for (const GateOp& op : q) launch_op(env, r, op);
+    return;
+  }
+  const TileCfg cfg = tile_cfg(r);
+  int k = std::min(cfg.kmax, r.nq);
+  if (env.tile_qubits > 0) k = std::min<int>(int(env.tile_qubits), r.nq);
+  k = std::max(k, cfg.R + 5);
+  k = std::min(k, cfg.R + 8);
+  const int L = std::min(cfg.L, k);
+  const bool df = r.prec == QS_C128 && env.arith == 1;
+  const Arith arith = r.prec == QS_C64 ? Arith::F32 : (df ? Arith::DF : Arith::F64);
+
+  std::vector<VOp> vops;
+  vops.reserve(q.size() * 2);
+  for (const GateOp& op : q) expand(r, op, vops);
+  const int64_t cap = env.max_fused_ops > 0 ? std::min<int64_t>(env.max_fused_ops, kMaxPassOps)
+                                            : kMaxPassOps;
+  const std::vector<Pass> passes = plan(vops, r.nq, k, L, cap);
+
+  std::vector<FOp> fops;
+  std::vector<FStage> fst;
+  std::vector<FPass> fps;
+  std::vector<double> flops;
+  for (const Pass& p : passes) {
+    FPass fp{};
+    fp.k = k;
+    fp.L = L;
+    fp.nq = r.nq;
+    fp.ntiles = int64_t(1) << (r.nq - k);
+    for (int i = 0; i < k; ++i) fp.q[i] = uint8_t(p.q[i]);
+    fp.stage_begin = int(fst.size());
+    fp.op_begin = int(fops.size());
+    encode_pass(p, cfg.R, k, arith, fops, fst);
+    fp.stage_end = int(fst.size());
+    fp.op_count = int(fops.size()) - fp.op_begin;
+    fps.push_back(fp);
+    double fl = 0;
+    for (const VOp& v : p.ops) fl += vop_flops(v, r.nq);
+    flops.push_back(fl);
+  }
+  ensure_fused_buffers(env, fops.size(), fst.size());
+  std::memcpy(env.h_fops, fops.data(), fops.size() * sizeof(FOp));
+  std::memcpy(env.h_fst, fst.data(), fst.size() * sizeof(FStage));
+  QS_CUDA(cudaMemcpyAsync(env.d_fops, env.h_fops, fops.size() * sizeof(FOp), cudaMemcpyHostToDevice, env.stream));
+  QS_CUDA(cudaMemcpyAsync(env.d_fst, env.h_fst, fst.size() * sizeof(FStage), cudaMemcpyHostToDevice, env.stream));
+  QS_CUDA(cudaEventRecord(env.fcopied, env.stream));
+  env.fused_passes += int64_t(fps.size());
+  env.fused_vops += int64_t(vops.size());
+  const FOp* d_ops = static_cast<const FOp*>(env.d_fops);
+  const FStage* d_st = static_cast<const FStage*>(env.d_fst);
+  for (size_t i = 0; i < fps.size(); ++i) {
+    if (arith == Arith::DF)
+      launch_pass<DFArith, 4>(env, r, fps[i], d_ops, d_st, flops[i], "fused_c128_df");
+    else if (arith == Arith::F64)
+      launch_pass<PlainArith<double>, 4>(env, r, fps[i], d_ops, d_st, flops[i], "fused_c128");
+    else
+      launch_pass<PlainArith<float>, 5>(env, r, fps[i], d_ops, d_st, flops[i], "fused_c64");
+  }
+  QS_CUDA(cudaGetLastError());
 }
 
 }  // namespace qs

@@ -1,0 +1,447 @@
+// Fused tile kernel: one HBM round trip applies a whole pass of operations.
+//
+// A pass fixes k "tile qubits" Q (always the L lowest qubits, for
+// contiguous 2^L-amplitude chunks, plus k-L others).  For every assignment
+// of the remaining bits (one tile) the 2^k amplitudes are loaded into shared
+// memory, every operation of the pass is applied, and the tile is written
+// back.  Non-diagonal operations must act on tile qubits; diagonal ones and
+// controls may sit anywhere (outside the tile they are a per-tile
+// predicate).
+//
+// Inside a tile the pass is split into stages.  A stage names R "register
+// bits" of the local index; each thread holds the 2^R amplitudes that
+// differ only in those bits, applies the stage's operations in registers,
+// and writes them back to shared memory.  Pair updates (Eq. 1) on a
+// register bit, and quad updates on two register bits, need no further
+// shared-memory traffic.  The pass's operation list is copied into shared
+// memory once per CTA, so decoding an operation costs shared-memory
+// broadcasts only.
+#pragma once
+#include "common.cuh"
+#include "dfloat.cuh"
+#include "pass_kernels.cuh"
+
+namespace qs {
+
+// Vector-level operations of the fused engine.
+enum FKind : uint8_t {
+  FK_GEN = 0, FK_H = 1, FK_SX = 2, FK_SY = 3, FK_X = 4,   // pair ops (PairKind order)
+  FK_PHASE = 5,   // multiply by (c0, c1) where the condition holds
+  FK_SIGN = 6,    // negate where the condition holds
+  FK_DEPH = 7,    // scale by c0 where bit A != bit B
+  FK_DEPOL = 8,   // depolarising quad on register bits (i0 = row bit, i1 = column bit)
+  FK_SCALE = 9    // multiply every amplitude by the real c0
+};
+// In this engine H, sqrt(X) and sqrt(Y) are applied WITHOUT their scalar
+// factors (1/sqrt(2), 1/2, 1/2): H -> [[1, 1], [1, -1]], sqrt(X) ->
+// [[1+i, 1-i], [1-i, 1+i]], sqrt(Y) -> (1+i) [[1, -1], [1, 1]].  Those
+// gates are uncontrolled, so the dropped factor is one scalar for the whole
+// vector; the planner emits an FK_SCALE with the accumulated product at the
+// end of each pass (and earlier if it would leave the float exponent range).
+
+// Where a single bit of the amplitude index comes from, within a stage.
+enum BitSrc : uint8_t { BS_REG = 0, BS_LOCAL = 1, BS_GLOBAL = 2 };
+
+// One operation as applied in one stage (all masks pre-split by the host).
+// Coefficients (matrix re/im row-major; PHASE cos, sin; DEPH factor; DEPOL
+// keep, move, off; SCALE factor) are stored in the form the kernel's
+// arithmetic uses: doubles (FP64), floats (FP32), or float pairs hi[0..7]
+// lo[8..15] (double-float).
+struct FOp {
+  uint8_t kind;
+  uint8_t conj;     // pair ops: apply conj(G)
+  uint8_t i0, i1;   // register-bit indices (pair target; DEPOL row/column)
+  uint8_t asrc, apos, bsrc, bpos;  // DEPH bit sources
+  uint32_t rmask;   // condition bits among the register bits (bit i = register bit i)
+  uint32_t lmask;   // condition bits among the other local bits (local positions)
+  uint64_t gmask;   // condition bits outside the tile (global positions)
+  union {
+    double d[8];
+    float f[16];
+  } c;
+};
+static_assert(sizeof(FOp) == 88, "FOp layout");
+
+struct FStage {
+  uint8_t pbits[8];          // local positions of the register bits (R used)
+  int32_t op_begin, op_end;  // relative to the pass's first op
+};
+
+struct FPass {
+  int k, L, nq;
+  int stage_begin, stage_end;  // indices into the stage array
+  int op_begin, op_count;      // the pass's ops in the op array
+  int64_t ntiles;
+  uint8_t q[24];               // tile qubits, ascending; q[i] = i for i < L
+};
+
+constexpr int kMaxPassOps = 256;
+
+// ------------------------------------------------------------- arithmetic
+// Plain arithmetic on the storage type (complex64: FP32, complex128: FP64).
+template <typename R>
+struct PlainArith {
+  using Store = cvec<R>;
+  using Cplx = cvec<R>;
+  __device__ static R cf(const FOp& op, int e) {
+    if constexpr (sizeof(R) == 8) return op.c.d[e];
+    else return op.c.f[e];
+  }
+  __device__ static Cplx from_store(const Store& s) { return s; }
+  __device__ static Store to_store(const Cplx& c) { return c; }
+  template <int K, bool CONJ>
+  __device__ static void pair_t(Cplx& x, Cplx& y, const FOp& op) {
+    if constexpr (K == PK_GEN) {
+      Mat2<R> g;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        g.re[e] = cf(op, 2 * e);
+        g.im[e] = cf(op, 2 * e + 1);
+      }
+      pair_apply<R, K, CONJ>(x, y, g);
+    } else if constexpr (K == PK_H) {  // unscaled: (x + y, x - y)
+      const Cplx u = x;
+      x.x = u.x + y.x; x.y = u.y + y.y;
+      y.x = u.x - y.x; y.y = u.y - y.y;
+    } else if constexpr (K == PK_SX) {  // unscaled: (u + i v, u - i v), u = x + y, v = x - y
+      const R ur = x.x + y.x, ui = x.y + y.y, vr = x.x - y.x, vi = x.y - y.y;
+      if constexpr (!CONJ) {
+        x.x = ur - vi; x.y = ui + vr; y.x = ur + vi; y.y = ui - vr;
+      } else {
+        x.x = ur + vi; x.y = ui - vr; y.x = ur - vi; y.y = ui + vr;
+      }
+    } else if constexpr (K == PK_SY) {  // unscaled: ((1+i) d, (1+i) s), d = x - y, s = x + y
+      const R dr = x.x - y.x, di = x.y - y.y, sr = x.x + y.x, si = x.y + y.y;
+      if constexpr (!CONJ) {
+        x.x = dr - di; x.y = dr + di; y.x = sr - si; y.y = sr + si;
+      } else {
+        x.x = dr + di; x.y = di - dr; y.x = sr + si; y.y = si - sr;
+      }
+    } else if constexpr (K == PK_X) {
+      const Cplx t = x;
+      x = y;
+      y = t;
+    }
+  }
+  __device__ static Cplx phase(const Cplx& v, const FOp& op) {
+    const R c = cf(op, 0), s = cf(op, 1);
+    Cplx w;
+    w.x = c * v.x - s * v.y;
+    w.y = s * v.x + c * v.y;
+    return w;
+  }
+  __device__ static Cplx negate(const Cplx& v) {
+    Cplx w;
+    w.x = neg_bits(v.x);
+    w.y = neg_bits(v.y);
+    return w;
+  }
+  __device__ static Cplx scale(const Cplx& v, const FOp& op, int e) {
+    const R f = cf(op, e);
+    Cplx w;
+    w.x = v.x * f;
+    w.y = v.y * f;
+    return w;
+  }
+  __device__ static Cplx axpby(const Cplx& a, const Cplx& b, const FOp& op) {
+    const R keep = cf(op, 0), move = cf(op, 1);
+    Cplx w;
+    w.x = keep * a.x + move * b.x;
+    w.y = keep * a.y + move * b.y;
+    return w;
+  }
+};
+
+// Double-float arithmetic for complex128 storage: each real part is an
+// unevaluated sum hi + lo of two floats (dfloat.cuh), computed on the FP32
+// pipes.
+struct DFArith {
+  using Store = double2;
+  using Cplx = dfc;
+  __device__ static df cf(const FOp& op, int e) { return df{op.c.f[e], op.c.f[8 + e]}; }
+  __device__ static Cplx from_store(const Store& s) { return dfc{df_from_double(s.x), df_from_double(s.y)}; }
+  __device__ static Store to_store(const Cplx& c) { return make_double2(df_to_double(c.re), df_to_double(c.im)); }
+  template <int K, bool CONJ>
+  __device__ static void pair_t(Cplx& x, Cplx& y, const FOp& op) {
+    if constexpr (K == PK_GEN) {
+      df g[4][2];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        g[e][0] = cf(op, 2 * e);
+        g[e][1] = CONJ ? df_neg(cf(op, 2 * e + 1)) : cf(op, 2 * e + 1);
+      }
+      const dfc nx = dfc_mac2(g[0][0], g[0][1], x, g[1][0], g[1][1], y);
+      const dfc ny = dfc_mac2(g[2][0], g[2][1], x, g[3][0], g[3][1], y);
+      x = nx;
+      y = ny;
+    } else if constexpr (K == PK_H) {  // unscaled
+      const dfc u = dfc_add(x, y), v = dfc_sub(x, y);
+      x = u;
+      y = v;
+    } else if constexpr (K == PK_SX) {
+      // unscaled: x' = u + i v, y' = u - i v with u = x + y, v = x - y
+      const dfc u = dfc_add(x, y), v = dfc_sub(x, y);
+      if constexpr (!CONJ) {
+        x = dfc{df_sub(u.re, v.im), df_add(u.im, v.re)};
+        y = dfc{df_add(u.re, v.im), df_sub(u.im, v.re)};
+      } else {
+        x = dfc{df_add(u.re, v.im), df_sub(u.im, v.re)};
+        y = dfc{df_sub(u.re, v.im), df_add(u.im, v.re)};
+      }
+    } else if constexpr (K == PK_SY) {
+      // unscaled: x' = (1 + i)(x - y), y' = (1 + i)(x + y)  (conj: 1 - i)
+      const dfc d = dfc_sub(x, y), s = dfc_add(x, y);
+      if constexpr (!CONJ) {
+        x = dfc{df_sub(d.re, d.im), df_add(d.re, d.im)};
+        y = dfc{df_sub(s.re, s.im), df_add(s.re, s.im)};
+      } else {
+        x = dfc{df_add(d.re, d.im), df_sub(d.im, d.re)};
+        y = dfc{df_add(s.re, s.im), df_sub(s.im, s.re)};
+      }
+    } else if constexpr (K == PK_X) {
+      const dfc t = x;
+      x = y;
+      y = t;
+    }
+  }
+  __device__ static Cplx phase(const Cplx& v, const FOp& op) { return dfc_mul(v, cf(op, 0), cf(op, 1)); }
+  __device__ static Cplx negate(const Cplx& v) { return dfc{df_neg(v.re), df_neg(v.im)}; }
+  __device__ static Cplx scale(const Cplx& v, const FOp& op, int e) {
+    const df f = cf(op, e);
+    return dfc{df_mul(v.re, f), df_mul(v.im, f)};
+  }
+  __device__ static Cplx axpby(const Cplx& a, const Cplx& b, const FOp& op) {
+    const df keep = cf(op, 0), move = cf(op, 1);
+    return dfc{df_add(df_mul(a.re, keep), df_mul(b.re, move)),
+               df_add(df_mul(a.im, keep), df_mul(b.im, move))};
+  }
+};
+
+// ------------------------------------------------------------ register ops
+template <class A, int R, int K, bool CONJ, bool MASKED, int I>
+__device__ __forceinline__ void pair_on_bit(typename A::Cplx (&v)[1 << R], uint32_t rmask,
+                                            const FOp& op) {
+#pragma unroll
+  for (int j = 0; j < (1 << R); ++j) {
+    if (j & (1 << I)) continue;
+    if (MASKED && (uint32_t(j) & rmask) != rmask) continue;
+    A::template pair_t<K, CONJ>(v[j], v[j | (1 << I)], op);
+  }
+}
+
+template <class A, int R, int K, bool CONJ, bool MASKED>
+__device__ __forceinline__ void pair_dispatch_bit(typename A::Cplx (&v)[1 << R], int i,
+                                                  uint32_t rmask, const FOp& op) {
+  switch (i) {
+    case 0: pair_on_bit<A, R, K, CONJ, MASKED, 0>(v, rmask, op); break;
+    case 1: if constexpr (R > 1) pair_on_bit<A, R, K, CONJ, MASKED, 1>(v, rmask, op); break;
+    case 2: if constexpr (R > 2) pair_on_bit<A, R, K, CONJ, MASKED, 2>(v, rmask, op); break;
+    case 3: if constexpr (R > 3) pair_on_bit<A, R, K, CONJ, MASKED, 3>(v, rmask, op); break;
+    case 4: if constexpr (R > 4) pair_on_bit<A, R, K, CONJ, MASKED, 4>(v, rmask, op); break;
+    default: break;
+  }
+}
+
+template <class A, int R, int K>
+__device__ __forceinline__ void pair_dispatch(typename A::Cplx (&v)[1 << R], const FOp& op) {
+  if (op.rmask == 0) {
+    if (op.conj) pair_dispatch_bit<A, R, K, true, false>(v, op.i0, 0u, op);
+    else pair_dispatch_bit<A, R, K, false, false>(v, op.i0, 0u, op);
+  } else {
+    if (op.conj) pair_dispatch_bit<A, R, K, true, true>(v, op.i0, op.rmask, op);
+    else pair_dispatch_bit<A, R, K, false, true>(v, op.i0, op.rmask, op);
+  }
+}
+
+template <class A, int R, int I0, int I1>
+__device__ __forceinline__ void depol_on_bits(typename A::Cplx (&v)[1 << R], const FOp& op) {
+#pragma unroll
+  for (int j = 0; j < (1 << R); ++j) {
+    if (j & ((1 << I0) | (1 << I1))) continue;
+    const int a = j, b = j | (1 << I0), c = j | (1 << I1), d = j | (1 << I0) | (1 << I1);
+    const typename A::Cplx d0 = v[a], d1 = v[d];
+    v[a] = A::axpby(d0, d1, op);
+    v[d] = A::axpby(d1, d0, op);
+    v[b] = A::scale(v[b], op, 2);
+    v[c] = A::scale(v[c], op, 2);
+  }
+}
+
+template <class A, int R>
+__device__ __forceinline__ void depol_dispatch(typename A::Cplx (&v)[1 << R], const FOp& op) {
+  const int lo = op.i0 < op.i1 ? op.i0 : op.i1, hi = op.i0 < op.i1 ? op.i1 : op.i0;
+  switch (lo * 8 + hi) {
+#define QS_DEPOL_CASE(a, b) \
+  case a * 8 + b: if constexpr (R > b) depol_on_bits<A, R, a, b>(v, op); break;
+    QS_DEPOL_CASE(0, 1) QS_DEPOL_CASE(0, 2) QS_DEPOL_CASE(0, 3) QS_DEPOL_CASE(0, 4)
+    QS_DEPOL_CASE(1, 2) QS_DEPOL_CASE(1, 3) QS_DEPOL_CASE(1, 4)
+    QS_DEPOL_CASE(2, 3) QS_DEPOL_CASE(2, 4)
+    QS_DEPOL_CASE(3, 4)
+#undef QS_DEPOL_CASE
+    default: break;
+  }
+}
+
+__device__ __forceinline__ int bit_value(uint8_t src, uint8_t pos, int j, uint32_t tlocal,
+                                         uint64_t tglobal) {
+  if (src == BS_REG) return (j >> pos) & 1;
+  if (src == BS_LOCAL) return int((tlocal >> pos) & 1u);
+  return int((tglobal >> pos) & 1u);
+}
+
+// Applies one operation to the thread's 2^R register amplitudes.
+// tlocal: this thread's local index with the register bits zero;
+// tglobal: the tile's global base (tile bits zero).
+template <class A, int R>
+__device__ __forceinline__ void apply_op(typename A::Cplx (&v)[1 << R], const FOp& op,
+                                         uint32_t tlocal, uint64_t tglobal) {
+  if ((tlocal & op.lmask) != op.lmask) return;
+  if ((tglobal & op.gmask) != op.gmask) return;
+  switch (op.kind) {
+    case FK_GEN: pair_dispatch<A, R, PK_GEN>(v, op); break;
+    case FK_H: pair_dispatch<A, R, PK_H>(v, op); break;
+    case FK_SX: pair_dispatch<A, R, PK_SX>(v, op); break;
+    case FK_SY: pair_dispatch<A, R, PK_SY>(v, op); break;
+    case FK_X: pair_dispatch<A, R, PK_X>(v, op); break;
+    case FK_PHASE:
+#pragma unroll
+      for (int j = 0; j < (1 << R); ++j)
+        if ((uint32_t(j) & op.rmask) == op.rmask) v[j] = A::phase(v[j], op);
+      break;
+    case FK_SIGN:
+#pragma unroll
+      for (int j = 0; j < (1 << R); ++j)
+        if ((uint32_t(j) & op.rmask) == op.rmask) v[j] = A::negate(v[j]);
+      break;
+    case FK_DEPH:
+#pragma unroll
+      for (int j = 0; j < (1 << R); ++j)
+        if (bit_value(op.asrc, op.apos, j, tlocal, tglobal) !=
+            bit_value(op.bsrc, op.bpos, j, tlocal, tglobal))
+          v[j] = A::scale(v[j], op, 0);
+      break;
+    case FK_DEPOL: depol_dispatch<A, R>(v, op); break;
+    case FK_SCALE:
+#pragma unroll
+      for (int j = 0; j < (1 << R); ++j) v[j] = A::scale(v[j], op, 0);
+      break;
+    default: break;
+  }
+}
+
+// Shared-memory bytes of a pass launch.
+template <class A>
+__host__ __device__ inline size_t fused_smem_bytes(int k, int L, int nops, int nstages) {
+  return sizeof(typename A::Cplx) * (size_t(1) << k) + sizeof(int64_t) * (size_t(1) << (k - L)) +
+         sizeof(FOp) * size_t(nops) + sizeof(FStage) * size_t(nstages);
+}
+
+// ------------------------------------------------------------------ kernel
+constexpr int kFusedThreads = 256;
+
+template <class A, int R>
+__global__ void __launch_bounds__(kFusedThreads, 2)
+    k_fused(typename A::Store* __restrict__ g, const __grid_constant__ FPass P,
+            const FOp* __restrict__ ops, const FStage* __restrict__ stages) {
+  using Cplx = typename A::Cplx;
+  using Store = typename A::Store;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int k = P.k, L = P.L;
+  const int ntile = 1 << k;
+  const int nchunk = 1 << (k - L);
+  const int nst = P.stage_end - P.stage_begin;
+  Cplx* tile = reinterpret_cast<Cplx*>(smem_raw);
+  int64_t* choff = reinterpret_cast<int64_t*>(smem_raw + sizeof(Cplx) * ntile);
+  FOp* sops = reinterpret_cast<FOp*>(choff + nchunk);
+  FStage* sst = reinterpret_cast<FStage*>(sops + P.op_count);
+
+  for (int c = threadIdx.x; c < nchunk; c += blockDim.x) {
+    int64_t off = 0;
+    for (int i = 0; i < k - L; ++i)
+      if ((c >> i) & 1) off |= int64_t(1) << P.q[L + i];
+    choff[c] = off;
+  }
+  {  // the pass's op and stage lists (8-byte words)
+    const uint64_t* src = reinterpret_cast<const uint64_t*>(ops + P.op_begin);
+    uint64_t* dst = reinterpret_cast<uint64_t*>(sops);
+    const int nw = P.op_count * int(sizeof(FOp) / 8);
+    for (int w = threadIdx.x; w < nw; w += blockDim.x) dst[w] = src[w];
+    const uint64_t* ss = reinterpret_cast<const uint64_t*>(stages + P.stage_begin);
+    uint64_t* sd = reinterpret_cast<uint64_t*>(sst);
+    const int ns = nst * int(sizeof(FStage) / 8);
+    for (int w = threadIdx.x; w < ns; w += blockDim.x) sd[w] = ss[w];
+  }
+  __syncthreads();
+  const int lmask_low = (1 << L) - 1;
+
+  for (int64_t tau = blockIdx.x; tau < P.ntiles; tau += gridDim.x) {
+    // global base of the tile: the bits of tau in the non-tile positions
+    int64_t base = tau;
+    for (int i = 0; i < k; ++i) {
+      const int p = P.q[i];
+      base = ((base >> p) << (p + 1)) | (base & ((int64_t(1) << p) - 1));
+    }
+    // load: 8 independent loads in flight per thread (2^R >= 16 per thread)
+    for (int l0 = threadIdx.x; l0 < ntile; l0 += blockDim.x * 8) {
+      Store t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int l = l0 + u * blockDim.x;
+        t[u] = g[base + choff[l >> L] + (l & lmask_low)];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) tile[l0 + u * blockDim.x] = A::from_store(t[u]);
+    }
+    __syncthreads();
+    for (int s = 0; s < nst; ++s) {
+      const FStage& st = sst[s];
+      uint32_t poff[R];
+      uint32_t pm = 0;
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        poff[i] = 1u << st.pbits[i];
+        pm |= poff[i];
+      }
+      // tlocal: deposit threadIdx into the local positions not in pm
+      uint32_t tlocal = 0;
+      {
+        int pos = 0;
+        for (int b = 0; b < k; ++b) {
+          if (pm & (1u << b)) continue;
+          tlocal |= uint32_t((threadIdx.x >> pos) & 1) << b;
+          ++pos;
+        }
+      }
+      Cplx v[1 << R];
+#pragma unroll
+      for (int j = 0; j < (1 << R); ++j) {
+        uint32_t off = 0;
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+          if (j & (1 << i)) off |= poff[i];
+        v[j] = tile[tlocal | off];
+      }
+      for (int o = st.op_begin; o < st.op_end; ++o) apply_op<A, R>(v, sops[o], tlocal, uint64_t(base));
+#pragma unroll
+      for (int j = 0; j < (1 << R); ++j) {
+        uint32_t off = 0;
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+          if (j & (1 << i)) off |= poff[i];
+        tile[tlocal | off] = v[j];
+      }
+      __syncthreads();
+    }
+    // store
+    for (int l0 = threadIdx.x; l0 < ntile; l0 += blockDim.x * 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int l = l0 + u * blockDim.x;
+        g[base + choff[l >> L] + (l & lmask_low)] = A::to_store(tile[l]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace qs

@@ -110,6 +110,14 @@ struct Env {
   // staging buffer for complex64 <-> complex128 copies
   double2* d_stage = nullptr;
   int64_t stage_amps = 0;
+  // fused-pass op and stage lists: pinned staging and device copies
+  void* h_fops = nullptr;
+  void* d_fops = nullptr;
+  size_t fops_cap = 0;
+  void* h_fst = nullptr;
+  void* d_fst = nullptr;
+  size_t fst_cap = 0;
+  cudaEvent_t fcopied = nullptr;
   std::vector<int64_t> regs;
 };
 
@@ -131,6 +139,7 @@ class KTimer {
 // Entry points of the kernel layer (implemented in the .cu files).
 void launch_op(Env& env, Reg& r, const GateOp& op);
 void flush(Reg& r);
+void free_fused_buffers(Env& env);
 double reduce_total(Env& env, Reg& r);
 double reduce_outcome(Env& env, Reg& r, int q, int o);
 double reduce_purity(Env& env, Reg& r);
