@@ -1,0 +1,394 @@
+"""Benchmark: seeded random circuits on B300, gates/s and achieved HBM GB/s.
+
+Default workload (one "step"): a 30-qubit complex128 state vector (16 GiB),
+|0...0> initialisation, the 1259-gate depth-40 random circuit (H, CZ,
+sqrt(X), sqrt(Y), T, Haar compactUnitary, 3-control phase flip per layer),
+then calcTotalProb and calcProbOfOutcome(qubit 0) returned to the host.
+value = gates/s of the whole job (sum over ranks).  The state (16 GiB) is
+far larger than L2 (126 MB), so no L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--prec 128|64] [--arith fp64|df] [--qubits n] [--no-variants]
+
+Multi-GPU: replicas only (every rank simulates its own register; no data
+exchange), launched by torchrun; the time is the max over ranks.
+--impl reference times the CPU oracle on the host cores instead (bounded
+sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1802_08032_b300 import circuits as C  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6400.0
+FP64_NOMINAL_TFLOPS = 1.25   # B300 dense FP64 (non-tensor), nominal
+FP32_NOMINAL_TFLOPS = 75.0   # B300 FP32: 148 SMs x 128 lanes x 2 x ~2.0 GHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", type=int, default=128, choices=[64, 128])
+    ap.add_argument("--arith", default="fp64", choices=["fp64", "df"],
+                    help="complex128 arithmetic of fused passes")
+    ap.add_argument("--qubits", type=int, default=30)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--cpu-gates", type=int, default=10,
+                    help="gates in the bounded CPU-oracle sample")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def cpu_oracle_sample(n, ops, ngates):
+    """Times the CPU oracle on a bounded sample: `ngates` gates spread evenly
+    over the circuit, applied to an n-qubit state (allocation and |0>
+    excluded from the timing, as in the paper's methodology)."""
+    from oracle import oracle as O
+    stride = max(1, len(ops) // ngates)
+    sample = ops[::stride][:ngates]
+    st, secs = O.timed_run(n, sample)
+    del st
+    return {"value": len(sample) / secs, "unit": "gates/s", "cores": O.num_threads(),
+            "kind": "oracle",
+            "sample": f"{len(sample)} gates (every {stride}th of the {len(ops)}-gate circuit) on a "
+                      f"{n}-qubit complex128 state vector, FP64 C oracle, OpenMP over "
+                      f"{O.num_threads()} host threads, {secs:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    n = args.qubits
+    ops = C.workload_30q(n)
+    vals = []
+    for _ in range(args.warmup + args.steps):
+        r = cpu_oracle_sample(n, ops, args.cpu_gates)
+        vals.append(r["value"])
+    timed = vals[args.warmup:]
+    v = len(timed) / sum(1.0 / x for x in timed)
+    line = {"metric": "gates/s (30q random circuit)", "value": v, "unit": "gates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * args.cpu_gates / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"{n}-qubit complex128 state vector, seeded depth-40 random "
+                                   "circuit (bounded CPU sample)", "qubits": n},
+            "cpu_baseline": {"value": v, "unit": "gates/s", "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def roofline(stats):
+    hbm_peak, peak_src = peaks()
+    dom = max(stats, key=lambda s: s["total_ms"]) if stats else None
+    if not dom or dom["total_ms"] <= 0:
+        return None
+    per_launch_ms = dom["total_ms"] / dom["launches"]
+    gbs = dom["bytes"] / dom["launches"] / (per_launch_ms / 1e3) / 1e9
+    tflops = dom["flops"] / dom["launches"] / (per_launch_ms / 1e3) / 1e12
+    fp64 = dom["name"].endswith("c128")
+    alu_peak = FP64_NOMINAL_TFLOPS if fp64 else FP32_NOMINAL_TFLOPS
+    if gbs / hbm_peak >= tflops / alu_peak:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": gbs / hbm_peak, "traffic": None,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        roof = {"bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": tflops / alu_peak, "traffic": None,
+                "peak_source": ("nominal B300 FP64 1.25 TFLOP/s" if fp64 else
+                                "nominal B300 FP32 (148 SMs x 128 lanes x 2 x 2 GHz)"),
+                "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak}
+    roof.update({"kernel": dom["name"], "launch_ms": per_launch_ms,
+                 "bytes_per_launch": dom["bytes"] / dom["launches"],
+                 "flops_per_launch": dom["flops"] / dom["launches"]})
+    return roof
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    from paper_1802_08032_b300 import qsim as Q
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t[0])
+
+    n, prec = args.qubits, args.prec
+    ops = C.workload_30q(n)
+    ngates = len(ops)
+    env = Q.createQuESTEnv()
+    Q.setEnvOption(env, "arith", 1 if args.arith == "df" else 0)
+    stream = torch.cuda.Stream()
+    Q.setStream(env, stream)
+    q = Q.createQureg(n, prec, env)
+    # the gate list lives in pinned host memory (the step's host input)
+    arr, nops = Q.to_qsops(ops)
+    raw = bytes(arr)
+    pinned = torch.empty(len(raw), dtype=torch.uint8, pin_memory=True)
+    ctypes.memmove(pinned.data_ptr(), raw, len(raw))
+    qsops = (ctypes.cast(pinned.data_ptr(), ctypes.POINTER(Q.QSOp)), nops)
+    h2d, d2h = len(raw), 2 * 8
+
+    def step():
+        Q.initZeroState(q)
+        Q.applyCircuit(q, qsops)
+        return Q.calcTotalProb(q), Q.calcProbOfOutcome(q, 0, 0)
+
+    for _ in range(args.warmup):
+        step()
+    Q.resetKernelStats(env)
+    Q.setEnvOption(env, "profile", 1)
+    l0 = Q.getEnvOption(env, "launches")
+    p0 = Q.getEnvOption(env, "fused_passes")
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        res = step()
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    dev_ms = max_over_ranks(e0.elapsed_time(e1))
+    launches = Q.getEnvOption(env, "launches") - l0
+    passes = (Q.getEnvOption(env, "fused_passes") - p0) / args.steps
+    stats = Q.getKernelStats(env)
+    Q.setEnvOption(env, "profile", 0)
+
+    # e2e: host wall clock around the same public-API step (gate list in from
+    # pinned host memory, probabilities out), no profiling events
+    step()
+    barrier()
+    te = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - te)
+
+    total_gates = ngates * args.steps * world
+    dtype = "f32" if prec == 64 else ("df64 (f32 pairs)" if args.arith == "df" else "f64")
+    line = {
+        "metric": "gates/s (30q random circuit)", "value": total_gates / (dev_ms / 1e3),
+        "unit": "gates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dev_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": {"workload": f"{n}-qubit complex{prec} state vector, seeded depth-40 random "
+                               f"circuit ({ngates} gates) + calcTotalProb + calcProbOfOutcome",
+                   "qubits": n, "precision": f"complex{prec}", "arith": args.arith,
+                   "gates_per_step": ngates, "parallelism": f"replicas x{world}",
+                   "l2": "state 2^n amplitudes >> 126 MB L2, no flush",
+                   "fused_passes_per_step": passes},
+        "roofline": roofline(stats),
+        "e2e": {"value": total_gates / e2e_s, "unit": "gates/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "result": {"total_prob": res[0], "prob_q0_0": res[1]},
+        "kernels": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in s.items()}
+                    for s in sorted(stats, key=lambda s: -s["total_ms"])[:6]],
+    }
+    Q.destroyQureg(q)
+    if rank == 0 and world == 1 and not args.no_variants:
+        line["variants"] = variants(Q, env, torch, stream)
+    if rank == 0 and world == 1:
+        try:
+            line["cpu_baseline"] = cpu_oracle_sample(n, ops, args.cpu_gates)
+        except Exception as e:  # host without room for the sample
+            line["cpu_baseline"] = {"value": None, "unavailable": str(e)}
+    Q.destroyQuESTEnv(env)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def timed(torch, stream, fn, reps):
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def variants(Q, env, torch, stream):
+    """Other configurations of the same metric, measured outside the timed
+    region: complex64 and double-float complex128 at 30 qubits, the 14-qubit
+    noisy density matrix, and single-gate pass bandwidth by target bit."""
+    out = {}
+    ops = C.workload_30q(30)
+
+    def sv(prec, arith):
+        def run_variant():
+            Q.setEnvOption(env, "arith", arith)
+            q = Q.createQureg(30, prec, env)
+
+            def run():
+                Q.initZeroState(q)
+                Q.applyCircuit(q, ops)
+                Q.calcTotalProb(q)
+
+            try:
+                ms = timed(torch, stream, run, 2)
+            finally:
+                Q.destroyQureg(q)
+                Q.setEnvOption(env, "arith", 0)
+            return {"gates_per_s": len(ops) / ms * 1e3, "ms_per_circuit": ms}
+        return run_variant
+
+    def sweep():
+        # single-gate passes (fusion off), algorithmic GB/s by target bit
+        Q.setEnvOption(env, "fusion", 0)
+        res = {}
+        try:
+            for prec in (64, 128):
+                reg = Q.createQureg(30, prec, env)
+                S = 16 if prec == 128 else 8
+                try:
+                    for name, fn, frac in (
+                            ("H", lambda t: Q.hadamard(reg, t), 1.0),
+                            ("T", lambda t: Q.tGate(reg, t), 0.5),
+                            ("CZ", lambda t: Q.controlledPhaseFlip(reg, t, (t + 1) % 30), 0.25)):
+                        row = []
+                        for t in range(30):
+                            ms = timed(torch, stream, lambda: fn(t), 2)
+                            row.append(round(2 * frac * (1 << 30) * S / ms / 1e6, 1))
+                        res[f"{name}_c{prec}_GBps_by_target"] = row
+                finally:
+                    Q.destroyQureg(reg)
+        finally:
+            Q.setEnvOption(env, "fusion", 1)
+        return res
+
+    def dm14():
+        dops = C.workload_dm14()
+        d = Q.createDensityQureg(14, 128, env)
+
+        def run():
+            Q.initZeroState(d)
+            Q.applyCircuit(d, dops)
+            Q.calcTotalProb(d)
+            Q.calcPurity(d)
+
+        try:
+            ms = timed(torch, stream, run, 2)
+        finally:
+            Q.destroyQureg(d)
+        return {"ops_per_s": len(dops) / ms * 1e3, "ms_per_circuit": ms, "ops": len(dops)}
+
+    for name, fn in (("sv30_c64", sv(64, 0)), ("sv30_c128_df", sv(128, 1)),
+                     ("single_gate_sweep", sweep), ("dm14_c128", dm14)):
+        try:
+            out[name] = fn()
+        except Exception as e:
+            out[name] = {"error": str(e)}
+    return out
+
+
+if __name__ == "__main__":
+    main()

@@ -258,3 +258,72 @@ def test_budget_and_torch_allocator(Q):
     assert abs(Q.calcProbOfOutcome(q, 3, 0) - 1.0) <= PROB_TOL
     Q.destroyQureg(q)
     Q.destroyQuESTEnv(e)
+
+
+# ------------------------------------------------ double-float arithmetic
+@pytest.fixture
+def df_env(Q, env):
+    Q.setEnvOption(env, "arith", 1)
+    yield env
+    Q.setEnvOption(env, "arith", 0)
+
+
+def test_double_float_every_gate(Q, df_env):
+    n = 10
+    psi = rand_state(n, 12)
+    for op in single_ops(n, seed=5):
+        ref = O.State(n, amps=psi)
+        ref.apply(op)
+        got = gpu_state(Q, df_env, n, [op], 128, fusion=1, init=psi)
+        assert np.max(np.abs(got - ref.a)) <= 1e-13, op
+
+
+@pytest.mark.parametrize("n", [9, 12, 16, 21])
+def test_double_float_random_circuits(Q, df_env, n):
+    ops = C.random_circuit(n, 24, 300 + n, extras=True)
+    ref = O.run_circuit(n, ops)
+    got = gpu_state(Q, df_env, n, ops, 128, fusion=1)
+    assert np.max(np.abs(got - ref.a)) <= AMP_TOL[128]
+
+
+@pytest.mark.parametrize("N", [5, 7])
+def test_double_float_noisy_density(Q, df_env, N):
+    ops = C.random_density_circuit(N, 10, 40 + N, 0.01, 0.005)
+    ref = O.run_circuit(N, ops, density=True)
+    q = Q.createDensityQureg(N, 128, df_env)
+    Q.applyCircuit(q, ops)
+    tr, pur = Q.calcTotalProb(q), Q.calcPurity(q)
+    got = Q.copyStateToHost(q)
+    Q.destroyQureg(q)
+    assert np.max(np.abs(got - ref.a)) <= AMP_TOL[128]
+    assert abs(tr - ref.total_prob()) <= PROB_TOL
+    assert abs(pur - ref.purity()) <= PROB_TOL
+
+
+def test_double_float_tiny_and_large_magnitudes(Q, df_env):
+    """Amplitudes spanning many binades (down to 1e-30) convert and update
+    within the absolute tolerance."""
+    n = 10
+    rng = np.random.default_rng(3)
+    mags = 10.0 ** rng.uniform(-30, 0, size=1 << n)
+    psi = mags * np.exp(1j * rng.uniform(0, 2 * np.pi, size=1 << n))
+    psi /= np.linalg.norm(psi)
+    ops = C.random_circuit(n, 6, 9, extras=True)
+    ref = O.State(n, amps=psi).run(ops)
+    got = gpu_state(Q, df_env, n, ops, 128, fusion=1, init=psi)
+    assert np.max(np.abs(got - ref.a)) <= 1e-13
+
+
+# ------------------------------------------------------- fused-pass counts
+def test_fusion_cuts_passes_per_layer(Q, env):
+    """A depth-40 layer has ~31 gates; fused tiles need far fewer HBM passes."""
+    n = 24
+    ops = C.random_circuit(n, 40, 8032, extras=True)
+    Q.setEnvOption(env, "fusion", 1)
+    q = Q.createQureg(n, 64, env)
+    p0 = Q.getEnvOption(env, "fused_passes")
+    Q.applyCircuit(q, ops)
+    Q.syncQuESTEnv(env)
+    passes = Q.getEnvOption(env, "fused_passes") - p0
+    Q.destroyQureg(q)
+    assert len(ops) / passes >= 4.0, (len(ops), passes)
