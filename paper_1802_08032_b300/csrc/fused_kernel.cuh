@@ -244,13 +244,8 @@ __device__ __forceinline__ void pair_dispatch_bit(typename A::Cplx (&v)[1 << R],
 
 template <class A, int R, int K>
 __device__ __forceinline__ void pair_dispatch(typename A::Cplx (&v)[1 << R], const FOp& op) {
-  if (op.rmask == 0) {
-    if (op.conj) pair_dispatch_bit<A, R, K, true, false>(v, op.i0, 0u, op);
-    else pair_dispatch_bit<A, R, K, false, false>(v, op.i0, 0u, op);
-  } else {
-    if (op.conj) pair_dispatch_bit<A, R, K, true, true>(v, op.i0, op.rmask, op);
-    else pair_dispatch_bit<A, R, K, false, true>(v, op.i0, op.rmask, op);
-  }
+  if (op.conj) pair_dispatch_bit<A, R, K, true, true>(v, op.i0, op.rmask, op);
+  else pair_dispatch_bit<A, R, K, false, true>(v, op.i0, op.rmask, op);
 }
 
 template <class A, int R, int I0, int I1>
