@@ -218,6 +218,34 @@ typedef struct {
  * by the individual calls. */
 int applyCircuit(Qureg q, const QSOp *ops, int64_t numOps);
 
+/* ------------------------------------------------- allocation-free norm */
+/* calcTotalProbNoAlloc: sum over j of |amps[j]|^2 in FP64, for callers that
+ * cannot allocate device memory (a host framework that owns the whole device
+ * through its own pool, a plug-in handed fixed buffers, code that must not
+ * trigger an allocation's implicit synchronisation).  It needs no
+ * environment and calls no allocator: its scratch is a fixed array of 65536
+ * doubles (512 KiB) in the library's own device memory, held by every GPU
+ * that loads the library until the process exits.  The paper has no
+ * counterpart; this is a library convenience.
+ *   amps       device pointer to numAmps interleaved complex amplitudes
+ *              (double2 for QS_C128, float2 for QS_C64), owned by the caller
+ *   precision  QS_C64 or QS_C128
+ *   numAmps    1 .. 2^30 (one scratch slot per 16384 amplitudes); larger
+ *              arrays are rejected with QS_E_ARG and a message
+ *   out        device pointer to one double, owned by the caller; written
+ *              when the call's kernels run
+ *   stream     cudaStream_t the work is queued on (null = legacy default);
+ *              the call returns without waiting
+ * The first call on a device looks up the scratch array's device address
+ * with that device current; make that first call before any stream capture.
+ * All calls share the one scratch array: calls whose kernels overlap on the
+ * GPU (different streams, or several host threads) race and give wrong
+ * sums; serialise them.  Every scratch slot a call reads is written by that
+ * call first, so stale contents from earlier calls do not matter.  The
+ * result equals calcTotalProb's up to FP64 summation order. */
+int calcTotalProbNoAlloc(const void *amps, int precision, int64_t numAmps, double *out,
+                         void *stream);
+
 /* ---------------------------------------------------------- kernel stats */
 /* Per-kernel-class timing, for roofline reporting.  With option "profile"
  * set to 1, every kernel launch of the env is bracketed by CUDA events on

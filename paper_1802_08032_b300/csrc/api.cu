@@ -298,7 +298,7 @@ void mat_params(const ComplexMatrix2& u, double* p) {
 }  // namespace
 
 namespace qs {
-void flush(Reg& r);  // fused.cu
+void set_last_error(const std::string& msg) { t_err = msg; }
 }
 
 extern "C" {

@@ -136,6 +136,9 @@ class KTimer {
   cudaEvent_t a_ = nullptr;
 };
 
+// Message returned by qsLastError on this thread (api.cu).
+void set_last_error(const std::string& msg);
+
 // Entry points of the kernel layer (implemented in the .cu files).
 void launch_op(Env& env, Reg& r, const GateOp& op);
 void flush(Reg& r);

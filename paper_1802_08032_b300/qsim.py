@@ -114,7 +114,9 @@ SIGNATURES = {
     "getKernelStats": [QuESTEnv, _P(QSKernelStat), _I, _P(_I)],
     "resetKernelStats": [QuESTEnv],
 }
-EXTRA_SIGNATURES: dict = {}
+EXTRA_SIGNATURES: dict = {
+    "calcTotalProbNoAlloc": [_VP, _I, _I64, _VP, _VP],
+}
 
 
 def _load():
@@ -390,3 +392,18 @@ def getKernelStats(env) -> list:
 
 def resetKernelStats(env):
     _check(LIB.resetKernelStats(env))
+
+
+# ------------------------------------------------- allocation-free norm
+def calcTotalProbNoAlloc(amps_ptr: int, precision: int, num_amps: int, out_ptr: int,
+                         stream=None):
+    """Queues sum |amps|^2 (FP64) into the device double at out_ptr, with no
+    device allocation (for callers that cannot allocate).  amps_ptr and
+    out_ptr are device addresses owned by the caller; stream is a cudaStream_t
+    as int, a torch.cuda.Stream, or None (legacy default stream).  The call
+    does not wait for the result."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    _check(LIB.calcTotalProbNoAlloc(ctypes.c_void_p(amps_ptr), int(precision), int(num_amps),
+                                    ctypes.c_void_p(out_ptr),
+                                    ctypes.c_void_p(stream) if stream else None))
