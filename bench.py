@@ -36,6 +36,12 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6400.0
 FP64_NOMINAL_TFLOPS = 1.25   # B300 dense FP64 (non-tensor), nominal
 FP32_NOMINAL_TFLOPS = 75.0   # B300 FP32: 148 SMs x 128 lanes x 2 x ~2.0 GHz
+# DRAM bytes (read + write) per amplitude per launch, from one ncu capture of
+# the kernel as built (profiles/<kernel>_*_ncu_full.md); scaled by the
+# amplitudes a launch processes.  Entries are removed when a kernel changes.
+MEASURED_TRAFFIC_PER_AMP = {
+    "fused_c128": 2.088e9 / (1 << 26),   # profiles/fused_c128_fp64_sv26_ncu_full.md
+}
 
 
 def parse():
@@ -162,7 +168,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def roofline(stats):
+def roofline(stats, amps_per_launch=None):
     hbm_peak, peak_src = peaks()
     dom = max(stats, key=lambda s: s["total_ms"]) if stats else None
     if not dom or dom["total_ms"] <= 0:
@@ -182,6 +188,10 @@ def roofline(stats):
                 "peak_source": ("nominal B300 FP64 1.25 TFLOP/s" if fp64 else
                                 "nominal B300 FP32 (148 SMs x 128 lanes x 2 x 2 GHz)"),
                 "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak}
+    per_amp = MEASURED_TRAFFIC_PER_AMP.get(dom["name"])
+    if per_amp is not None and amps_per_launch:
+        roof["traffic"] = per_amp * amps_per_launch
+        roof["traffic_source"] = "ncu dram bytes of a 26-qubit capture, scaled by amplitudes"
     roof.update({"kernel": dom["name"], "launch_ms": per_launch_ms,
                  "bytes_per_launch": dom["bytes"] / dom["launches"],
                  "flops_per_launch": dom["flops"] / dom["launches"]})
@@ -279,7 +289,7 @@ def main():
                    "gates_per_step": ngates, "parallelism": f"replicas x{world}",
                    "l2": "state 2^n amplitudes >> 126 MB L2, no flush",
                    "fused_passes_per_step": passes},
-        "roofline": roofline(stats),
+        "roofline": roofline(stats, 1 << n),
         "e2e": {"value": total_gates / e2e_s, "unit": "gates/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
