@@ -218,6 +218,37 @@ typedef struct {
  * by the individual calls. */
 int applyCircuit(Qureg q, const QSOp *ops, int64_t numOps);
 
+/* ------------------------------------------------------------- batches */
+/* Many independent state vectors advanced together (a batched form of the
+ * per-gate pass of Eq. 1; the paper runs one register at a time).
+ * createBatch: takes `count` distinct state-vector registers of one env and
+ * one precision (each >= 4 qubits for QS_C128, >= 5 for QS_C64) with their
+ * queued gates, which it consumes.  Each register is planned into fused
+ * passes exactly as a single-register flush would plan it (tile size
+ * tileQubits, 0 = default), the passes of all registers are grouped into
+ * waves (wave w = pass w of every register), and the launches plus one FP64
+ * norm per register are captured into a CUDA graph on the env's stream.
+ * One replay (runBatch) starts every register from |0...0> and applies its
+ * whole circuit; registers of up to 2^k amplitudes never leave shared memory
+ * within a pass.  The registers must outlive the batch; their amplitudes
+ * after a replay are read with copyStateToHost as usual.
+ * runBatch: queues one replay (asynchronous).
+ * getBatchNorms: waits, then writes count doubles: sum |a|^2 per register
+ *   after the last replay, accumulated in FP64.
+ * getBatchInfo: tile size requested (0 = default), total passes, waves,
+ *   algorithmic bytes and flops of one replay (any pointer may be null).
+ * tuneBatch: autotuner: re-plans and times `replays` replays for every
+ *   candidate tile size (5..13), keeps the fastest; writes it to *chosen.
+ * destroyBatch: frees the batch (not the registers). */
+typedef struct { int64_t id; } QSBatch;
+int createBatch(QuESTEnv env, const Qureg *regs, int count, int tileQubits, QSBatch *out);
+int runBatch(QSBatch batch);
+int getBatchNorms(QSBatch batch, double *out);
+int getBatchInfo(QSBatch batch, int *tileQubits, int64_t *passes, int *waves, double *bytes,
+                 double *flops);
+int tuneBatch(QSBatch batch, const int *candidates, int numCandidates, int replays, int *chosen);
+int destroyBatch(QSBatch batch);
+
 /* ------------------------------------------------- allocation-free norm */
 /* calcTotalProbNoAlloc: sum over j of |amps[j]|^2 in FP64, for callers that
  * cannot allocate device memory (a host framework that owns the whole device

@@ -299,6 +299,9 @@ void mat_params(const ComplexMatrix2& u, double* p) {
 
 namespace qs {
 void set_last_error(const std::string& msg) { t_err = msg; }
+int guarded_call(const std::function<void()>& f) { return guarded(f); }
+Env& lookup_env(int64_t id) { return env_of(QuESTEnv{id}); }
+Reg& lookup_reg(int64_t id) { return reg_of(Qureg{id}); }
 }
 
 extern "C" {

@@ -15,6 +15,7 @@
 #include <cstring>
 
 #include "fused_kernel.cuh"
+#include "plan.h"
 #include "runtime.h"
 
 namespace qs {
@@ -188,9 +189,6 @@ std::vector<Pass> plan(const std::vector<VOp>& ops, int nq, int k, int L, int64_
   return passes;
 }
 
-// Coefficient form of the kernel's arithmetic.
-enum class Arith { F32, F64, DF };
-
 void set_coeffs(FOp& f, const double* c, Arith a) {
   for (int e = 0; e < 8; ++e) {
     if (a == Arith::F64) {
@@ -317,17 +315,18 @@ void ensure_fused_buffers(Env& env, size_t nops, size_t nst) {
   if (!env.fcopied) QS_CUDA(cudaEventCreateWithFlags(&env.fcopied, cudaEventDisableTiming));
 }
 
-// Tile parameters per precision: R register bits, maximum k, low qubits L.
-struct TileCfg {
-  int R, kmax, L;
-};
-TileCfg tile_cfg(const Reg& r) { return r.prec == QS_C128 ? TileCfg{4, 12, 3} : TileCfg{5, 13, 4}; }
-
 }  // namespace
+
+TileCfg tile_cfg(const Reg& r) { return r.prec == QS_C128 ? TileCfg{4, 12, 3} : TileCfg{5, 13, 4}; }
 
 bool fusable(const Reg& r) {
   const TileCfg c = tile_cfg(r);
-  return r.nq >= c.R + 5;
+  return r.nq >= c.R;  // a tile of 2^nq amplitudes worked by 2^(nq-R) threads
+}
+
+Arith arith_of(const Reg& r) {
+  if (r.prec == QS_C64) return Arith::F32;
+  return r.env->arith == 1 ? Arith::DF : Arith::F64;
 }
 
 void free_fused_buffers(Env& env) {
@@ -340,6 +339,48 @@ void free_fused_buffers(Env& env) {
   env.fcopied = nullptr;
 }
 
+void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, RegPlan& out) {
+  const Env& env = *r.env;
+  const TileCfg cfg = tile_cfg(r);
+  int k = std::min(cfg.kmax, r.nq);
+  if (k_req > 0) k = std::min(k_req, r.nq);
+  else if (env.tile_qubits > 0) k = std::min<int>(int(env.tile_qubits), r.nq);
+  k = std::max(k, std::min(cfg.R + 5, r.nq));
+  k = std::min(k, cfg.R + 8);
+  const int L = std::min(cfg.L, k);
+  out = RegPlan{};
+  out.k = k;
+  out.L = L;
+  out.R = cfg.R;
+  out.arith = arith_of(r);
+
+  std::vector<VOp> vops;
+  vops.reserve(q.size() * 2);
+  for (const GateOp& op : q) expand(r, op, vops);
+  out.vops = int64_t(vops.size());
+  const int64_t cap = env.max_fused_ops > 0 ? std::min<int64_t>(env.max_fused_ops, kMaxPassOps)
+                                            : kMaxPassOps;
+  const std::vector<Pass> passes = plan(vops, r.nq, k, L, cap);
+  for (const Pass& p : passes) {
+    FPass fp{};
+    fp.k = k;
+    fp.L = L;
+    fp.nq = r.nq;
+    fp.ntiles = int64_t(1) << (r.nq - k);
+    fp.amps = r.d;
+    for (int i = 0; i < k; ++i) fp.q[i] = uint8_t(p.q[i]);
+    fp.stage_begin = int(out.fst.size());
+    fp.op_begin = int(out.fops.size());
+    encode_pass(p, cfg.R, k, out.arith, out.fops, out.fst);
+    fp.stage_end = int(out.fst.size());
+    fp.op_count = int(out.fops.size()) - fp.op_begin;
+    out.fps.push_back(fp);
+    double fl = 0;
+    for (const VOp& v : p.ops) fl += vop_flops(v, r.nq);
+    out.flops.push_back(fl);
+  }
+}
+
 void flush(Reg& r) {
   if (r.queue.empty()) return;
   std::vector<GateOp> q;
@@ -349,60 +390,25 @@ void flush(Reg& r) {
     for (const GateOp& op : q) launch_op(env, r, op);
     return;
   }
-  const TileCfg cfg = tile_cfg(r);
-  int k = std::min(cfg.kmax, r.nq);
-  if (env.tile_qubits > 0) k = std::min<int>(int(env.tile_qubits), r.nq);
-  k = std::max(k, cfg.R + 5);
-  k = std::min(k, cfg.R + 8);
-  const int L = std::min(cfg.L, k);
-  const bool df = r.prec == QS_C128 && env.arith == 1;
-  const Arith arith = r.prec == QS_C64 ? Arith::F32 : (df ? Arith::DF : Arith::F64);
-
-  std::vector<VOp> vops;
-  vops.reserve(q.size() * 2);
-  for (const GateOp& op : q) expand(r, op, vops);
-  const int64_t cap = env.max_fused_ops > 0 ? std::min<int64_t>(env.max_fused_ops, kMaxPassOps)
-                                            : kMaxPassOps;
-  const std::vector<Pass> passes = plan(vops, r.nq, k, L, cap);
-
-  std::vector<FOp> fops;
-  std::vector<FStage> fst;
-  std::vector<FPass> fps;
-  std::vector<double> flops;
-  for (const Pass& p : passes) {
-    FPass fp{};
-    fp.k = k;
-    fp.L = L;
-    fp.nq = r.nq;
-    fp.ntiles = int64_t(1) << (r.nq - k);
-    for (int i = 0; i < k; ++i) fp.q[i] = uint8_t(p.q[i]);
-    fp.stage_begin = int(fst.size());
-    fp.op_begin = int(fops.size());
-    encode_pass(p, cfg.R, k, arith, fops, fst);
-    fp.stage_end = int(fst.size());
-    fp.op_count = int(fops.size()) - fp.op_begin;
-    fps.push_back(fp);
-    double fl = 0;
-    for (const VOp& v : p.ops) fl += vop_flops(v, r.nq);
-    flops.push_back(fl);
-  }
-  ensure_fused_buffers(env, fops.size(), fst.size());
-  std::memcpy(env.h_fops, fops.data(), fops.size() * sizeof(FOp));
-  std::memcpy(env.h_fst, fst.data(), fst.size() * sizeof(FStage));
-  QS_CUDA(cudaMemcpyAsync(env.d_fops, env.h_fops, fops.size() * sizeof(FOp), cudaMemcpyHostToDevice, env.stream));
-  QS_CUDA(cudaMemcpyAsync(env.d_fst, env.h_fst, fst.size() * sizeof(FStage), cudaMemcpyHostToDevice, env.stream));
+  RegPlan pl;
+  build_plan(r, q, 0, pl);
+  ensure_fused_buffers(env, pl.fops.size(), pl.fst.size());
+  std::memcpy(env.h_fops, pl.fops.data(), pl.fops.size() * sizeof(FOp));
+  std::memcpy(env.h_fst, pl.fst.data(), pl.fst.size() * sizeof(FStage));
+  QS_CUDA(cudaMemcpyAsync(env.d_fops, env.h_fops, pl.fops.size() * sizeof(FOp), cudaMemcpyHostToDevice, env.stream));
+  QS_CUDA(cudaMemcpyAsync(env.d_fst, env.h_fst, pl.fst.size() * sizeof(FStage), cudaMemcpyHostToDevice, env.stream));
   QS_CUDA(cudaEventRecord(env.fcopied, env.stream));
-  env.fused_passes += int64_t(fps.size());
-  env.fused_vops += int64_t(vops.size());
+  env.fused_passes += int64_t(pl.fps.size());
+  env.fused_vops += pl.vops;
   const FOp* d_ops = static_cast<const FOp*>(env.d_fops);
   const FStage* d_st = static_cast<const FStage*>(env.d_fst);
-  for (size_t i = 0; i < fps.size(); ++i) {
-    if (arith == Arith::DF)
-      launch_pass<DFArith, 4>(env, r, fps[i], d_ops, d_st, flops[i], "fused_c128_df");
-    else if (arith == Arith::F64)
-      launch_pass<PlainArith<double>, 4>(env, r, fps[i], d_ops, d_st, flops[i], "fused_c128");
+  for (size_t i = 0; i < pl.fps.size(); ++i) {
+    if (pl.arith == Arith::DF)
+      launch_pass<DFArith, 4>(env, r, pl.fps[i], d_ops, d_st, pl.flops[i], "fused_c128_df");
+    else if (pl.arith == Arith::F64)
+      launch_pass<PlainArith<double>, 4>(env, r, pl.fps[i], d_ops, d_st, pl.flops[i], "fused_c128");
     else
-      launch_pass<PlainArith<float>, 5>(env, r, fps[i], d_ops, d_st, flops[i], "fused_c64");
+      launch_pass<PlainArith<float>, 5>(env, r, pl.fps[i], d_ops, d_st, pl.flops[i], "fused_c64");
   }
   QS_CUDA(cudaGetLastError());
 }

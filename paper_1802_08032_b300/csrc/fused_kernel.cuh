@@ -71,8 +71,18 @@ struct FPass {
   int k, L, nq;
   int stage_begin, stage_end;  // indices into the stage array
   int op_begin, op_count;      // the pass's ops in the op array
+  int init;                    // 1: the register starts in |0...0> (tiles are generated, not loaded)
+  int pad_;
   int64_t ntiles;
+  void* amps;                  // register amplitudes (batched launches; null = kernel argument)
   uint8_t q[24];               // tile qubits, ascending; q[i] = i for i < L
+};
+
+// One unit of a batched launch: tile `tile` of pass `pass`.
+struct BItem {
+  int32_t pass;
+  int32_t pad_;
+  int64_t tile;
 };
 
 constexpr int kMaxPassOps = 256;
@@ -334,62 +344,96 @@ __host__ __device__ inline size_t fused_smem_bytes(int k, int L, int nops, int n
 // ------------------------------------------------------------------ kernel
 constexpr int kFusedThreads = 256;
 
-template <class A, int R>
-__global__ void __launch_bounds__(kFusedThreads, 2)
-    k_fused(typename A::Store* __restrict__ g, const __grid_constant__ FPass P,
-            const FOp* __restrict__ ops, const FStage* __restrict__ stages) {
-  using Cplx = typename A::Cplx;
-  using Store = typename A::Store;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int k = P.k, L = P.L;
-  const int ntile = 1 << k;
-  const int nchunk = 1 << (k - L);
-  const int nst = P.stage_end - P.stage_begin;
-  Cplx* tile = reinterpret_cast<Cplx*>(smem_raw);
-  int64_t* choff = reinterpret_cast<int64_t*>(smem_raw + sizeof(Cplx) * ntile);
-  FOp* sops = reinterpret_cast<FOp*>(choff + nchunk);
-  FStage* sst = reinterpret_cast<FStage*>(sops + P.op_count);
+// Shared-memory layout of a pass: tile, chunk offsets, op list, stage list.
+template <class A>
+struct PassSmem {
+  typename A::Cplx* tile;
+  int64_t* choff;
+  FOp* ops;
+  FStage* st;
+};
 
+template <class A>
+__device__ __forceinline__ PassSmem<A> pass_smem(unsigned char* raw, int kmax, int Lmin, int opmax) {
+  PassSmem<A> m;
+  m.tile = reinterpret_cast<typename A::Cplx*>(raw);
+  m.choff = reinterpret_cast<int64_t*>(raw + sizeof(typename A::Cplx) * (size_t(1) << kmax));
+  m.ops = reinterpret_cast<FOp*>(m.choff + (1 << (kmax - Lmin)));
+  m.st = reinterpret_cast<FStage*>(m.ops + opmax);
+  return m;
+}
+
+// Copies a pass's chunk-offset table, op list and stage list into shared
+// memory (all threads; caller synchronises).
+template <class A>
+__device__ __forceinline__ void load_pass(const FPass& P, const FOp* __restrict__ ops,
+                                          const FStage* __restrict__ stages, PassSmem<A>& m) {
+  const int nchunk = 1 << (P.k - P.L);
   for (int c = threadIdx.x; c < nchunk; c += blockDim.x) {
     int64_t off = 0;
-    for (int i = 0; i < k - L; ++i)
-      if ((c >> i) & 1) off |= int64_t(1) << P.q[L + i];
-    choff[c] = off;
+    for (int i = 0; i < P.k - P.L; ++i)
+      if ((c >> i) & 1) off |= int64_t(1) << P.q[P.L + i];
+    m.choff[c] = off;
   }
-  {  // the pass's op and stage lists (8-byte words)
-    const uint64_t* src = reinterpret_cast<const uint64_t*>(ops + P.op_begin);
-    uint64_t* dst = reinterpret_cast<uint64_t*>(sops);
-    const int nw = P.op_count * int(sizeof(FOp) / 8);
-    for (int w = threadIdx.x; w < nw; w += blockDim.x) dst[w] = src[w];
-    const uint64_t* ss = reinterpret_cast<const uint64_t*>(stages + P.stage_begin);
-    uint64_t* sd = reinterpret_cast<uint64_t*>(sst);
-    const int ns = nst * int(sizeof(FStage) / 8);
-    for (int w = threadIdx.x; w < ns; w += blockDim.x) sd[w] = ss[w];
-  }
-  __syncthreads();
-  const int lmask_low = (1 << L) - 1;
+  const uint64_t* src = reinterpret_cast<const uint64_t*>(ops + P.op_begin);
+  uint64_t* dst = reinterpret_cast<uint64_t*>(m.ops);
+  const int nw = P.op_count * int(sizeof(FOp) / 8);
+  for (int w = threadIdx.x; w < nw; w += blockDim.x) dst[w] = src[w];
+  const uint64_t* ss = reinterpret_cast<const uint64_t*>(stages + P.stage_begin);
+  uint64_t* sd = reinterpret_cast<uint64_t*>(m.st);
+  const int ns = (P.stage_end - P.stage_begin) * int(sizeof(FStage) / 8);
+  for (int w = threadIdx.x; w < ns; w += blockDim.x) sd[w] = ss[w];
+}
 
-  for (int64_t tau = blockIdx.x; tau < P.ntiles; tau += gridDim.x) {
-    // global base of the tile: the bits of tau in the non-tile positions
-    int64_t base = tau;
-    for (int i = 0; i < k; ++i) {
-      const int p = P.q[i];
-      base = ((base >> p) << (p + 1)) | (base & ((int64_t(1) << p) - 1));
+// Applies pass P to tile tau of the register g: load (or generate |0...0>),
+// run the stages, store.  2^(k-R) threads work on the stages; all threads of
+// the block take part in loads, stores and barriers.  GENERAL = false is the
+// single-register launch, where blockDim = 2^(k-R) and no pass generates
+// |0...0>, so those checks compile away.
+template <class A, int R, bool GENERAL>
+__device__ __forceinline__ void process_tile(typename A::Store* __restrict__ g, const FPass& P,
+                                             int64_t tau, PassSmem<A>& m) {
+  using Cplx = typename A::Cplx;
+  using Store = typename A::Store;
+  const int k = P.k, L = P.L;
+  const int ntile = 1 << k;
+  const int lmask_low = (1 << L) - 1;
+  const int nst = P.stage_end - P.stage_begin;
+  const int active = 1 << (k - R);
+  // global base of the tile: the bits of tau in the non-tile positions
+  int64_t base = tau;
+  for (int i = 0; i < k; ++i) {
+    const int p = P.q[i];
+    base = ((base >> p) << (p + 1)) | (base & ((int64_t(1) << p) - 1));
+  }
+  if (GENERAL && P.init) {
+    for (int l = threadIdx.x; l < ntile; l += blockDim.x) {
+      Store z;
+      z.x = 0;
+      z.y = 0;
+      if (base == 0 && l == 0) z.x = 1;
+      m.tile[l] = A::from_store(z);
     }
-    // load: 8 independent loads in flight per thread (2^R >= 16 per thread)
+  } else {
+    // load: 8 independent loads in flight per thread
     for (int l0 = threadIdx.x; l0 < ntile; l0 += blockDim.x * 8) {
       Store t[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int l = l0 + u * blockDim.x;
-        t[u] = g[base + choff[l >> L] + (l & lmask_low)];
+        if (!GENERAL || l < ntile) t[u] = g[base + m.choff[l >> L] + (l & lmask_low)];
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) tile[l0 + u * blockDim.x] = A::from_store(t[u]);
+      for (int u = 0; u < 8; ++u) {
+        const int l = l0 + u * blockDim.x;
+        if (!GENERAL || l < ntile) m.tile[l] = A::from_store(t[u]);
+      }
     }
-    __syncthreads();
-    for (int s = 0; s < nst; ++s) {
-      const FStage& st = sst[s];
+  }
+  __syncthreads();
+  for (int s = 0; s < nst; ++s) {
+    if (!GENERAL || int(threadIdx.x) < active) {
+      const FStage& st = m.st[s];
       uint32_t poff[R];
       uint32_t pm = 0;
 #pragma unroll
@@ -414,28 +458,64 @@ __global__ void __launch_bounds__(kFusedThreads, 2)
 #pragma unroll
         for (int i = 0; i < R; ++i)
           if (j & (1 << i)) off |= poff[i];
-        v[j] = tile[tlocal | off];
+        v[j] = m.tile[tlocal | off];
       }
-      for (int o = st.op_begin; o < st.op_end; ++o) apply_op<A, R>(v, sops[o], tlocal, uint64_t(base));
+      for (int o = st.op_begin; o < st.op_end; ++o) apply_op<A, R>(v, m.ops[o], tlocal, uint64_t(base));
 #pragma unroll
       for (int j = 0; j < (1 << R); ++j) {
         uint32_t off = 0;
 #pragma unroll
         for (int i = 0; i < R; ++i)
           if (j & (1 << i)) off |= poff[i];
-        tile[tlocal | off] = v[j];
-      }
-      __syncthreads();
-    }
-    // store
-    for (int l0 = threadIdx.x; l0 < ntile; l0 += blockDim.x * 8) {
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int l = l0 + u * blockDim.x;
-        g[base + choff[l >> L] + (l & lmask_low)] = A::to_store(tile[l]);
+        m.tile[tlocal | off] = v[j];
       }
     }
     __syncthreads();
+  }
+  // store
+  for (int l0 = threadIdx.x; l0 < ntile; l0 += blockDim.x * 8) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int l = l0 + u * blockDim.x;
+      if (!GENERAL || l < ntile) g[base + m.choff[l >> L] + (l & lmask_low)] = A::to_store(m.tile[l]);
+    }
+  }
+  __syncthreads();
+}
+
+// One pass over every tile of one register.
+template <class A, int R>
+__global__ void __launch_bounds__(kFusedThreads, 2)
+    k_fused(typename A::Store* __restrict__ g, const __grid_constant__ FPass P,
+            const FOp* __restrict__ ops, const FStage* __restrict__ stages) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PassSmem<A> m = pass_smem<A>(smem_raw, P.k, P.L, P.op_count);
+  load_pass<A>(P, ops, stages, m);
+  __syncthreads();
+  for (int64_t tau = blockIdx.x; tau < P.ntiles; tau += gridDim.x) process_tile<A, R, false>(g, P, tau, m);
+}
+
+// Batched: the work items of one wave (tiles of passes of many registers,
+// each pass with its own register pointer).  Shared memory is laid out for
+// the largest tile (kmax, Lmin) and op list (opmax) of the wave.
+template <class A, int R>
+__global__ void __launch_bounds__(kFusedThreads, 2)
+    k_fused_batch(const BItem* __restrict__ items, int nitems, const FPass* __restrict__ passes,
+                  const FOp* __restrict__ ops, const FStage* __restrict__ stages, int kmax, int Lmin,
+                  int opmax) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PassSmem<A> m = pass_smem<A>(smem_raw, kmax, Lmin, opmax);
+  int cur = -1;
+  FPass P;
+  for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+    const BItem it = items[i];
+    if (it.pass != cur) {
+      cur = it.pass;
+      P = passes[cur];
+      load_pass<A>(P, ops, stages, m);
+      __syncthreads();
+    }
+    process_tile<A, R, true>(static_cast<typename A::Store*>(P.amps), P, it.tile, m);
   }
 }
 

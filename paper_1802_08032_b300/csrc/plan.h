@@ -1,0 +1,37 @@
+// Fusion plan of one register's queued gates (internal; fused.cu).
+#pragma once
+#include <vector>
+
+#include "fused_kernel.cuh"
+#include "runtime.h"
+
+namespace qs {
+
+// Coefficient form of the kernel's arithmetic.
+enum class Arith { F32, F64, DF };
+
+// The passes of one register: device-ready descriptors whose op and stage
+// indices are relative to this plan's own arrays.
+struct RegPlan {
+  int k = 0, L = 0, R = 0;
+  Arith arith = Arith::F64;
+  std::vector<FPass> fps;
+  std::vector<FOp> fops;
+  std::vector<FStage> fst;
+  std::vector<double> flops;  // algorithmic flops per pass
+  int64_t vops = 0;           // vector operations planned
+};
+
+// Tile parameters per precision: R register bits, maximum k, low qubits L.
+struct TileCfg {
+  int R, kmax, L;
+};
+TileCfg tile_cfg(const Reg& r);
+bool fusable(const Reg& r);
+Arith arith_of(const Reg& r);
+
+// Plans q for register r with tile size k (0 = the library default / the
+// env's tile_qubits option).
+void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, RegPlan& out);
+
+}  // namespace qs

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <functional>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -138,6 +139,11 @@ class KTimer {
 
 // Message returned by qsLastError on this thread (api.cu).
 void set_last_error(const std::string& msg);
+// Runs f, mapping exceptions to a status code and qsLastError (api.cu).
+int guarded_call(const std::function<void()>& f);
+// Handle lookups (api.cu); fail with QS_E_HANDLE when unknown.
+Env& lookup_env(int64_t id);
+Reg& lookup_reg(int64_t id);
 
 // Entry points of the kernel layer (implemented in the .cu files).
 void launch_op(Env& env, Reg& r, const GateOp& op);

@@ -61,6 +61,10 @@ class QSOp(ctypes.Structure):
                 ("params", ctypes.c_double * 8)]
 
 
+class QSBatch(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64)]
+
+
 class QSKernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64),
                 ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double),
@@ -116,6 +120,12 @@ SIGNATURES = {
 }
 EXTRA_SIGNATURES: dict = {
     "calcTotalProbNoAlloc": [_VP, _I, _I64, _VP, _VP],
+    "createBatch": [QuESTEnv, _P(Qureg), _I, _I, _P(QSBatch)],
+    "runBatch": [QSBatch],
+    "getBatchNorms": [QSBatch, _P(_D)],
+    "getBatchInfo": [QSBatch, _P(_I), _P(_I64), _P(_I), _P(_D), _P(_D)],
+    "tuneBatch": [QSBatch, _P(_I), _I, _I, _P(_I)],
+    "destroyBatch": [QSBatch],
 }
 
 
@@ -407,3 +417,43 @@ def calcTotalProbNoAlloc(amps_ptr: int, precision: int, num_amps: int, out_ptr: 
     _check(LIB.calcTotalProbNoAlloc(ctypes.c_void_p(amps_ptr), int(precision), int(num_amps),
                                     ctypes.c_void_p(out_ptr),
                                     ctypes.c_void_p(stream) if stream else None))
+
+
+# ------------------------------------------------------------- batches
+def createBatch(env, regs, tileQubits: int = 0) -> QSBatch:
+    arr = (Qureg * len(regs))(*[Qureg(r.id) for r in regs])
+    b = QSBatch()
+    _check(LIB.createBatch(env, arr, len(regs), int(tileQubits), ctypes.byref(b)))
+    b.count = len(regs)
+    return b
+
+
+def runBatch(b):
+    _check(LIB.runBatch(b))
+
+
+def getBatchNorms(b, count=None):
+    import numpy as np
+    n = count if count is not None else b.count
+    out = np.empty(n, dtype=np.float64)
+    _check(LIB.getBatchNorms(b, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
+
+
+def getBatchInfo(b) -> dict:
+    k, p, w, by, fl = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+    _check(LIB.getBatchInfo(b, ctypes.byref(k), ctypes.byref(p), ctypes.byref(w), ctypes.byref(by),
+                            ctypes.byref(fl)))
+    return {"tileQubits": k.value, "passes": p.value, "waves": w.value, "bytes": by.value,
+            "flops": fl.value}
+
+
+def tuneBatch(b, candidates, replays: int = 2) -> int:
+    arr, n = _ints(candidates)
+    c = ctypes.c_int()
+    _check(LIB.tuneBatch(b, arr, n, int(replays), ctypes.byref(c)))
+    return c.value
+
+
+def destroyBatch(b):
+    _check(LIB.destroyBatch(b))
