@@ -467,5 +467,68 @@ def batch_variant(Q, env, torch, stream, count=4096, depth=30):
             "plain_c128_subset": f"{len(sub)} of the same registers, one at a time, one kernel per gate"}
 
 
+def serve_trace(rate, count, seed0=5000, arrival_seed=55, max_sv=28, max_dm=13):
+    """Serving workload: Poisson arrivals at `rate` req/s (exponential gaps
+    from their own SplitMix64 stream), request i seeded 5000 + i: type
+    uniform over {state vector c64, state vector c128, density matrix c128};
+    state vectors n ~ U{10..28}, density matrices N ~ U{6..13} with
+    dephasing 0.01 after every gate; depth ~ U{10..50}."""
+    import math
+    arr = C.SplitMix64(arrival_seed)
+    t, trace = 0.0, []
+    for i in range(count):
+        t += -math.log(1.0 - arr.uniform()) / rate
+        rng = C.SplitMix64(seed0 + i)
+        kind = rng.below(3)
+        depth = 10 + rng.below(41)
+        if kind == 2:
+            N = 6 + rng.below(max_dm - 5)
+            ops = C.with_noise(C.random_circuit(N, depth, seed0 + i), 0.01, 0.0)
+            trace.append((t, True, N, 128, ops))
+        else:
+            n = 10 + rng.below(max_sv - 9)
+            trace.append((t, False, n, 64 if kind == 0 else 128,
+                          C.random_circuit(n, depth, seed0 + i)))
+    return trace
+
+
+def run_trace(Q, env, trace, slots, fusion, force_c128=False):
+    """Submits each request at its arrival time, collects every result;
+    returns latency percentiles and throughput."""
+    import numpy as np
+    srv = Q.serveCreate(env, slots=slots, budgetBytes=150 * 10 ** 9, fusion=fusion)
+    prepared = [(t, dens, n, 128 if force_c128 else prec, Q.to_qsops(ops))
+                for (t, dens, n, prec, ops) in trace]
+    tickets = []
+    try:
+        t0 = time.perf_counter()
+        for (t, dens, n, prec, qs) in prepared:
+            wait = t - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            tickets.append(Q.serveSubmit(srv, qs, n, prec, dens))
+        res = [Q.servePoll(srv, tk, timeoutUs=600_000_000) for tk in tickets]
+        wall = time.perf_counter() - t0
+    finally:
+        Q.serveDestroy(srv)
+    lat = np.array([r["latencyUs"] for r in res]) / 1e3
+    bad = sum(r["status"] != 0 for r in res)
+    return {"requests": len(res), "failed": int(bad), "circuits_per_s": len(res) / wall,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_queued_ms": float(np.mean([r["queuedUs"] for r in res]) / 1e3),
+            "slots_used": len({r["slot"] for r in res})}
+
+
+def serve_sweep(Q, env, rates, per_rate, slots=16, baseline=True):
+    out = {}
+    for rate in rates:
+        trace = serve_trace(rate, per_rate)
+        row = {"served": run_trace(Q, env, trace, slots, 1)}
+        if baseline:
+            row["plain_c128_one_at_a_time"] = run_trace(Q, env, trace, 1, 0, force_c128=True)
+        out[f"{rate}_req_per_s"] = row
+    return out
+
+
 if __name__ == "__main__":
     main()

@@ -249,6 +249,52 @@ int getBatchInfo(QSBatch batch, int *tileQubits, int64_t *passes, int *waves, do
 int tuneBatch(QSBatch batch, const int *candidates, int numCandidates, int replays, int *chosen);
 int destroyBatch(QSBatch batch);
 
+/* ------------------------------------------------------------- serving */
+/* A request loop: circuits submitted at any time run as soon as a slot and
+ * memory are free, concurrently with the ones already on the GPU (the paper
+ * runs one circuit per process; this is a library extension).
+ * serveCreate: `slots` execution slots (1..64), each with its own CUDA
+ *   stream and scratch; registers live within `budgetBytes` (2^n x 8 or 16
+ *   bytes each, density matrices 2^(2N)); `fusion` as the env option.  A
+ *   scheduler thread admits requests in arrival order while a slot is free
+ *   and the next request fits the budget.  Register memory comes from the
+ *   device's stream-ordered pool (its release threshold is raised so freed
+ *   blocks stay cached).  complex128 arithmetic and tile size follow the
+ *   env's options at creation.
+ * serveSubmit: validates and queues one request, returns its ticket.  The
+ *   op list is copied; outAmps (optional host buffer for the first outCount
+ *   final amplitudes, flat index as copyStateToHost) must stay valid until
+ *   the result is collected.  A request larger than the budget gives
+ *   QS_E_NOMEM; an invalid circuit gives its QS_E_* code (nothing queued).
+ * servePoll: waits up to timeoutUs microseconds for the ticket's result;
+ *   QS_E_TIMEOUT if it is not finished (the ticket stays valid), otherwise
+ *   fills *out and retires the ticket.
+ * serveDestroy: stops admitting, waits for the requests on the GPU, cancels
+ *   the queued ones, frees the slots. */
+typedef struct { int64_t id; } QSServer;
+typedef struct {
+    int32_t isDensity;      /* 0: state vector, 1: density matrix            */
+    int32_t precision;      /* QS_C64 or QS_C128                             */
+    int32_t numQubits;
+    int32_t measureQubit;   /* qubit whose outcome-0 probability is returned */
+    const QSOp *ops;
+    int64_t numOps;
+    Complex *outAmps;       /* optional, may be null                         */
+    int64_t outCount;
+} QSRequest;
+typedef struct {
+    int32_t status;         /* QS_OK or the request's error                  */
+    int32_t slot;           /* slot that ran it                              */
+    double totalProb;       /* calcTotalProb of the final state (FP64)       */
+    double probOutcome0;    /* calcProbOfOutcome(measureQubit, 0)            */
+    double queuedUs;        /* submit -> admitted                            */
+    double latencyUs;       /* submit -> results ready                       */
+} QSResult;
+int serveCreate(QuESTEnv env, int slots, int64_t budgetBytes, int fusion, QSServer *out);
+int serveSubmit(QSServer server, const QSRequest *req, int64_t *ticket);
+int servePoll(QSServer server, int64_t ticket, QSResult *out, int64_t timeoutUs);
+int serveDestroy(QSServer server);
+
 /* ------------------------------------------------- allocation-free norm */
 /* calcTotalProbNoAlloc: sum over j of |amps[j]|^2 in FP64, for callers that
  * cannot allocate device memory (a host framework that owns the whole device

@@ -302,6 +302,16 @@ void set_last_error(const std::string& msg) { t_err = msg; }
 int guarded_call(const std::function<void()>& f) { return guarded(f); }
 Env& lookup_env(int64_t id) { return env_of(QuESTEnv{id}); }
 Reg& lookup_reg(int64_t id) { return reg_of(Qureg{id}); }
+void convert_ops(const Reg& r, const QSOp* ops, int64_t n, std::vector<GateOp>& out) {
+  for (int64_t i = 0; i < n; ++i) {
+    try {
+      convert_op(r, ops[i], out);
+    } catch (Error& e) {
+      e.msg = "op " + std::to_string(i) + ": " + e.msg;
+      throw;
+    }
+  }
+}
 }
 
 extern "C" {

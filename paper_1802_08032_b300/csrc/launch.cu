@@ -164,24 +164,24 @@ void launch_typed(Env& env, Reg& r, const GateOp& op) {
 void check_launch() { QS_CUDA(cudaGetLastError()); }
 
 template <typename R>
-void sumsq(Env& env, const Reg& r, const Fixed& fx, int64_t nsel) {
+void sumsq(Env& env, const Reg& r, const Fixed& fx, int64_t nsel, double* out) {
   const int blocks = int(std::max<int64_t>(
       1, std::min<int64_t>(kRedMaxBlocks, (nsel + kRedThreads * 4 - 1) / (kRedThreads * 4))));
   KTimer kt(env, kname<R>("reduce_sumsq").c_str(), double(nsel) * amp_bytes<R>(), double(nsel) * 4, 2);
   k_sumsq<R, 4><<<blocks, kRedThreads, 0, env.stream>>>(static_cast<const cvec<R>*>(r.d), nsel, fx,
                                                         env.d_partial);
-  k_sum_partials<<<1, 1024, 0, env.stream>>>(env.d_partial, blocks, env.d_result);
+  k_sum_partials<<<1, 1024, 0, env.stream>>>(env.d_partial, blocks, out);
 }
 
 template <typename R>
-void sumdiag(Env& env, const Reg& r, int q, int o) {
+void sumdiag(Env& env, const Reg& r, int q, int o, double* out) {
   const int64_t d = int64_t(1) << r.n;
   const int blocks = int(std::max<int64_t>(
       1, std::min<int64_t>(kRedMaxBlocks, (d + kRedThreads - 1) / kRedThreads)));
   KTimer kt(env, kname<R>("reduce_diag").c_str(), double(d) * amp_bytes<R>(), double(d), 2);
   k_sumdiag<R><<<blocks, kRedThreads, 0, env.stream>>>(static_cast<const cvec<R>*>(r.d), r.n, q, o,
                                                        env.d_partial);
-  k_sum_partials<<<1, 1024, 0, env.stream>>>(env.d_partial, blocks, env.d_result);
+  k_sum_partials<<<1, 1024, 0, env.stream>>>(env.d_partial, blocks, out);
 }
 
 double fetch_result(Env& env) {
@@ -200,37 +200,47 @@ void launch_op(Env& env, Reg& r, const GateOp& op) {
   check_launch();
 }
 
-double reduce_total(Env& env, Reg& r) {
+void queue_total(Env& env, Reg& r, double* out) {
   flush(r);
   if (r.density) {
-    if (r.prec == QS_C128) sumdiag<double>(env, r, -1, 0);
-    else sumdiag<float>(env, r, -1, 0);
+    if (r.prec == QS_C128) sumdiag<double>(env, r, -1, 0, out);
+    else sumdiag<float>(env, r, -1, 0, out);
   } else {
     const Fixed fx = make_fixed({});
-    if (r.prec == QS_C128) sumsq<double>(env, r, fx, r.dim);
-    else sumsq<float>(env, r, fx, r.dim);
+    if (r.prec == QS_C128) sumsq<double>(env, r, fx, r.dim, out);
+    else sumsq<float>(env, r, fx, r.dim, out);
   }
+  check_launch();
+}
+
+void queue_outcome(Env& env, Reg& r, int q, int o, double* out) {
+  flush(r);
+  if (r.density) {
+    if (r.prec == QS_C128) sumdiag<double>(env, r, q, o, out);
+    else sumdiag<float>(env, r, q, o, out);
+  } else {
+    const Fixed fx = make_fixed({{q, o}});
+    if (r.prec == QS_C128) sumsq<double>(env, r, fx, r.dim >> 1, out);
+    else sumsq<float>(env, r, fx, r.dim >> 1, out);
+  }
+  check_launch();
+}
+
+double reduce_total(Env& env, Reg& r) {
+  queue_total(env, r, env.d_result);
   return fetch_result(env);
 }
 
 double reduce_outcome(Env& env, Reg& r, int q, int o) {
-  flush(r);
-  if (r.density) {
-    if (r.prec == QS_C128) sumdiag<double>(env, r, q, o);
-    else sumdiag<float>(env, r, q, o);
-  } else {
-    const Fixed fx = make_fixed({{q, o}});
-    if (r.prec == QS_C128) sumsq<double>(env, r, fx, r.dim >> 1);
-    else sumsq<float>(env, r, fx, r.dim >> 1);
-  }
+  queue_outcome(env, r, q, o, env.d_result);
   return fetch_result(env);
 }
 
 double reduce_purity(Env& env, Reg& r) {
   flush(r);
   const Fixed fx = make_fixed({});
-  if (r.prec == QS_C128) sumsq<double>(env, r, fx, r.dim);
-  else sumsq<float>(env, r, fx, r.dim);
+  if (r.prec == QS_C128) sumsq<double>(env, r, fx, r.dim, env.d_result);
+  else sumsq<float>(env, r, fx, r.dim, env.d_result);
   return fetch_result(env);
 }
 

@@ -144,12 +144,18 @@ int guarded_call(const std::function<void()>& f);
 // Handle lookups (api.cu); fail with QS_E_HANDLE when unknown.
 Env& lookup_env(int64_t id);
 Reg& lookup_reg(int64_t id);
+// Validates bulk-call ops for a register of r's shape into internal ops
+// (api.cu); fails with the first bad op's code.
+void convert_ops(const Reg& r, const QSOp* ops, int64_t n, std::vector<GateOp>& out);
 
 // Entry points of the kernel layer (implemented in the .cu files).
 void launch_op(Env& env, Reg& r, const GateOp& op);
 void flush(Reg& r);
 void free_fused_buffers(Env& env);
 double reduce_total(Env& env, Reg& r);
+// Queue a reduction into the device double *out without waiting (serving).
+void queue_total(Env& env, Reg& r, double* out);
+void queue_outcome(Env& env, Reg& r, int q, int o, double* out);
 double reduce_outcome(Env& env, Reg& r, int q, int o);
 double reduce_purity(Env& env, Reg& r);
 void launch_collapse(Env& env, Reg& r, int q, int o, double scale);

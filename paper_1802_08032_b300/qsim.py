@@ -65,6 +65,23 @@ class QSBatch(ctypes.Structure):
     _fields_ = [("id", ctypes.c_int64)]
 
 
+class QSServer(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64)]
+
+
+class QSRequest(ctypes.Structure):
+    _fields_ = [("isDensity", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("numQubits", ctypes.c_int32), ("measureQubit", ctypes.c_int32),
+                ("ops", ctypes.c_void_p), ("numOps", ctypes.c_int64),
+                ("outAmps", ctypes.c_void_p), ("outCount", ctypes.c_int64)]
+
+
+class QSResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("slot", ctypes.c_int32),
+                ("totalProb", ctypes.c_double), ("probOutcome0", ctypes.c_double),
+                ("queuedUs", ctypes.c_double), ("latencyUs", ctypes.c_double)]
+
+
 class QSKernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64),
                 ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double),
@@ -126,6 +143,10 @@ EXTRA_SIGNATURES: dict = {
     "getBatchInfo": [QSBatch, _P(_I), _P(_I64), _P(_I), _P(_D), _P(_D)],
     "tuneBatch": [QSBatch, _P(_I), _I, _I, _P(_I)],
     "destroyBatch": [QSBatch],
+    "serveCreate": [QuESTEnv, _I, _I64, _I, _P(QSServer)],
+    "serveSubmit": [QSServer, _P(QSRequest), _P(_I64)],
+    "servePoll": [QSServer, _I64, _P(QSResult), _I64],
+    "serveDestroy": [QSServer],
 }
 
 
@@ -457,3 +478,42 @@ def tuneBatch(b, candidates, replays: int = 2) -> int:
 
 def destroyBatch(b):
     _check(LIB.destroyBatch(b))
+
+
+# ------------------------------------------------------------- serving
+def serveCreate(env, slots: int, budgetBytes: int, fusion: int = 1) -> QSServer:
+    s = QSServer()
+    _check(LIB.serveCreate(env, int(slots), int(budgetBytes), int(fusion), ctypes.byref(s)))
+    s._keep = {}
+    return s
+
+
+def serveSubmit(server, ops, numQubits: int, precision: int = QS_C64, isDensity: bool = False,
+                measureQubit: int = 0, outAmps=None) -> int:
+    """Queues one circuit; ops is a gate list or a to_qsops() pair.  outAmps:
+    optional numpy complex128 array that receives the first outAmps.size
+    final amplitudes (kept alive until servePoll returns the result)."""
+    arr, n = ops if (isinstance(ops, tuple) and len(ops) == 2 and isinstance(ops[1], int)) \
+        else to_qsops(ops)
+    r = QSRequest(int(bool(isDensity)), int(precision), int(numQubits), int(measureQubit),
+                  ctypes.cast(arr, ctypes.c_void_p), int(n),
+                  outAmps.ctypes.data if outAmps is not None else None,
+                  int(outAmps.size) if outAmps is not None else 0)
+    t = ctypes.c_int64()
+    _check(LIB.serveSubmit(server, ctypes.byref(r), ctypes.byref(t)))
+    if outAmps is not None:
+        server._keep[t.value] = outAmps
+    return t.value
+
+
+def servePoll(server, ticket: int, timeoutUs: int = 60_000_000) -> dict:
+    res = QSResult()
+    _check(LIB.servePoll(server, int(ticket), ctypes.byref(res), int(timeoutUs)))
+    server._keep.pop(ticket, None)
+    return {"status": res.status, "slot": res.slot, "totalProb": res.totalProb,
+            "probOutcome0": res.probOutcome0, "queuedUs": res.queuedUs,
+            "latencyUs": res.latencyUs}
+
+
+def serveDestroy(server):
+    _check(LIB.serveDestroy(server))
