@@ -1,0 +1,122 @@
+"""Full-size parity: the GPU path at the benchmark configurations' sizes
+against expected values the CPU oracle wrote (tests/golden/make_golden.py):
+sampled amplitudes, reductions and outcome probabilities."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1802_08032_b300 import circuits as C
+from gpu_helpers import AMP_TOL, PROB_TOL
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def golden(name):
+    path = os.path.join(GOLDEN, name)
+    if not os.path.exists(path):
+        pytest.skip(f"{name} not generated yet")
+    with open(path) as f:
+        return json.load(f)
+
+
+def as_complex(pairs):
+    a = np.array(pairs, dtype=np.float64)
+    return a[:, 0] + 1j * a[:, 1]
+
+
+@pytest.fixture(scope="module")
+def Q():
+    from paper_1802_08032_b300 import qsim
+    return qsim
+
+
+@pytest.fixture(scope="module")
+def env(Q):
+    e = Q.createQuESTEnv()
+    yield e
+    Q.destroyQuESTEnv(e)
+
+
+def sample(Q, q, idx):
+    return np.array([Q.copyStateToHost(q, int(i), 1)[0] for i in idx])
+
+
+@pytest.mark.parametrize("arith", [0, 1])
+def test_density_matrix_14_qubits(Q, env, arith):
+    g = golden("dm14_depth20.json")
+    ops = C.workload_dm14(14)
+    assert C.stream_hash(ops) == g["hash"]
+    Q.setEnvOption(env, "arith", arith)
+    try:
+        d = Q.createDensityQureg(14, 128, env)
+        Q.applyCircuit(d, ops)
+        tr, pur = Q.calcTotalProb(d), Q.calcPurity(d)
+        probs = [Q.calcProbOfOutcome(d, q, 1) for q in range(14)]
+        got = sample(Q, d, g["indices"])
+        n = 1 << 14
+        diag = sample(Q, d, [j + n * j for j in g["diag_rows"]])
+        Q.destroyQureg(d)
+    finally:
+        Q.setEnvOption(env, "arith", 0)
+    assert abs(tr - g["trace"]) <= PROB_TOL
+    assert abs(pur - g["purity"]) <= PROB_TOL
+    assert np.max(np.abs(np.array(probs) - g["prob_outcome_1"])) <= PROB_TOL
+    assert np.max(np.abs(got - as_complex(g["amps"]))) <= AMP_TOL[128]
+    assert np.max(np.abs(diag - as_complex(g["diag"]))) <= AMP_TOL[128]
+
+
+def shifted(ops, k):
+    return [C.Op(o.kind, tuple(t + k for t in o.targets), tuple(c + k for c in o.controls), o.params)
+            for o in ops]
+
+
+def test_33_qubit_product_state(Q, env):
+    """33 qubits (2^33 amplitudes, 128 GiB complex128): a 30-qubit circuit on
+    qubits 0..29 and a 3-qubit circuit on 30..32; every sampled amplitude is
+    the product of the two factors' amplitudes (64-bit indices throughout)."""
+    g = golden("sv33_product_factors.json")
+    low = C.random_circuit(30, 12, 3330, extras=True)
+    high = C.random_circuit(3, 12, 3333, extras=True)
+    assert C.stream_hash(low) == g["hash_low"] and C.stream_hash(high) == g["hash_high"]
+    Q.setEnvOption(env, "arith", 1)          # double-float keeps the 33-qubit run short
+    try:
+        q = Q.createQureg(33, 128, env)
+        Q.applyCircuit(q, low + shifted(high, 30))
+        tot = Q.calcTotalProb(q)
+        probs_hi = [Q.calcProbOfOutcome(q, 30 + k, 1) for k in range(3)]
+        lo_idx = g["low_indices"][:512]
+        lo_amp = as_complex(g["low_amps"])[:512]
+        hi_amp = as_complex(g["high_amps"])
+        idx = [(j << 30) + i for j in range(8) for i in lo_idx]
+        got = sample(Q, q, idx)
+        Q.destroyQureg(q)
+    finally:
+        Q.setEnvOption(env, "arith", 0)
+    want = np.array([hi_amp[j] * a for j in range(8) for a in lo_amp])
+    assert np.max(np.abs(got - want)) <= AMP_TOL[128]
+    assert abs(tot - g["low_total_prob"]) <= PROB_TOL
+    assert np.max(np.abs(np.array(probs_hi) - g["high_prob_outcome_1"])) <= PROB_TOL
+
+
+@pytest.mark.parametrize("prec,arith", [(128, 0), (128, 1), (64, 0)])
+def test_30_qubit_depth40_workload(Q, env, prec, arith):
+    g = golden("sv30_depth40.json")
+    ops = C.workload_30q(30)
+    assert C.stream_hash(ops) == g["hash"]
+    Q.setEnvOption(env, "arith", arith)
+    try:
+        q = Q.createQureg(30, prec, env)
+        Q.applyCircuit(q, ops)
+        tot = Q.calcTotalProb(q)
+        probs = [Q.calcProbOfOutcome(q, k, 1) for k in range(30)]
+        got = sample(Q, q, g["indices"])
+        Q.destroyQureg(q)
+    finally:
+        Q.setEnvOption(env, "arith", 0)
+    assert np.max(np.abs(got - as_complex(g["amps"]))) <= AMP_TOL[prec]
+    tol = PROB_TOL if prec == 128 else 1e-5
+    assert abs(tot - g["total_prob"]) <= tol
+    assert np.max(np.abs(np.array(probs) - g["prob_outcome_1"])) <= tol
