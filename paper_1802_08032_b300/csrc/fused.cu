@@ -12,6 +12,7 @@
 // other).  Passes repeat until the queue is empty.
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 
 #include "fused_kernel.cuh"
@@ -118,18 +119,21 @@ void expand(const Reg& r, const GateOp& op, std::vector<VOp>& out) {
   }
 }
 
-// Appends FK_SCALE operations carrying the scalar factors that the engine's
-// unscaled H / sqrt(X) / sqrt(Y) leave out: one at the end of the pass, and
-// one earlier whenever the pending growth reaches 2^40.
+// Appends FK_SCALE operations carrying the factors that the engine's
+// unscaled H / sqrt(X) / sqrt(Y) leave out (1/sqrt 2, (1+i)/2, and (1-i)/2
+// for conjugated column updates): one at the end of the pass, and one
+// earlier whenever the pending magnitude growth reaches 2^40.
 void add_scales(std::vector<VOp>& ops) {
   std::vector<VOp> out;
   out.reserve(ops.size() + 2);
-  double f = 1.0, growth = 0.0;
+  std::complex<double> f(1.0, 0.0);
+  double growth = 0.0;
   auto flush_scale = [&] {
-    if (f == 1.0) return;
+    if (f == std::complex<double>(1.0, 0.0)) return;
     VOp s;
     s.kind = FK_SCALE;
-    s.c[0] = f;
+    s.c[0] = f.real();
+    s.c[1] = f.imag();
     out.push_back(s);
     f = 1.0;
     growth = 0.0;
@@ -140,8 +144,8 @@ void add_scales(std::vector<VOp>& ops) {
       f *= std::sqrt(0.5);
       growth += 0.5;
     } else if (v.kind == FK_SX || v.kind == FK_SY) {
-      f *= 0.5;
-      growth += 1.0;
+      f *= std::complex<double>(0.5, v.conj ? -0.5 : 0.5);
+      growth += 0.5;
     }
     if (growth >= 40.0) flush_scale();
   }
@@ -271,10 +275,10 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
 
 double vop_flops(const VOp& v, int nq) {
   const double dim = std::ldexp(1.0, nq), f = std::ldexp(1.0, -popc(v.cond));
-  static const double pair_flops[5] = {28, 4, 8, 8, 0};  // H, sqrt(X), sqrt(Y) unscaled
+  static const double pair_flops[5] = {28, 4, 4, 4, 0};  // H, sqrt(X), sqrt(Y) unscaled
   if (v.kind <= FK_X) return dim / 2 * f * pair_flops[v.kind];
   if (v.kind == FK_PHASE) return dim * f * 6;
-  if (v.kind == FK_SCALE) return dim * 2;
+  if (v.kind == FK_SCALE) return dim * 6;
   if (v.kind == FK_DEPH) return dim / 2 * 2;
   if (v.kind == FK_DEPOL) return dim / 4 * 16;
   return 0;

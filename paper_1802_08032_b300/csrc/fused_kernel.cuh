@@ -30,14 +30,16 @@ enum FKind : uint8_t {
   FK_SIGN = 6,    // negate where the condition holds
   FK_DEPH = 7,    // scale by c0 where bit A != bit B
   FK_DEPOL = 8,   // depolarising quad on register bits (i0 = row bit, i1 = column bit)
-  FK_SCALE = 9    // multiply every amplitude by the real c0
+  FK_SCALE = 9    // multiply every amplitude by the complex (c0, c1)
 };
 // In this engine H, sqrt(X) and sqrt(Y) are applied WITHOUT their scalar
-// factors (1/sqrt(2), 1/2, 1/2): H -> [[1, 1], [1, -1]], sqrt(X) ->
-// [[1+i, 1-i], [1-i, 1+i]], sqrt(Y) -> (1+i) [[1, -1], [1, 1]].  Those
-// gates are uncontrolled, so the dropped factor is one scalar for the whole
-// vector; the planner emits an FK_SCALE with the accumulated product at the
-// end of each pass (and earlier if it would leave the float exponent range).
+// factors: H = (1/sqrt 2) [[1, 1], [1, -1]], sqrt(X) = ((1+i)/2) [[1, -i], [-i, 1]],
+// sqrt(Y) = ((1+i)/2) [[1, -1], [1, 1]]; the bracketed matrices need additions
+// only.  Those gates are uncontrolled, so the dropped factors multiply the
+// whole vector; the planner emits an FK_SCALE with their accumulated complex
+// product at the end of each pass (and earlier if the growth would leave the
+// float exponent range).  The conjugated forms (density-matrix column
+// updates) drop the conjugate factors: [[1, i], [i, 1]] and (1-i)/2.
 
 // Where a single bit of the amplitude index comes from, within a stage.
 enum BitSrc : uint8_t { BS_REG = 0, BS_LOCAL = 1, BS_GLOBAL = 2 };
@@ -113,20 +115,17 @@ struct PlainArith {
       const Cplx u = x;
       x.x = u.x + y.x; x.y = u.y + y.y;
       y.x = u.x - y.x; y.y = u.y - y.y;
-    } else if constexpr (K == PK_SX) {  // unscaled: (u + i v, u - i v), u = x + y, v = x - y
-      const R ur = x.x + y.x, ui = x.y + y.y, vr = x.x - y.x, vi = x.y - y.y;
+    } else if constexpr (K == PK_SX) {  // [[1, -i], [-i, 1]]  (conj: [[1, i], [i, 1]])
+      const Cplx u = x;
       if constexpr (!CONJ) {
-        x.x = ur - vi; x.y = ui + vr; y.x = ur + vi; y.y = ui - vr;
+        x.x = u.x + y.y; x.y = u.y - y.x; y.x = y.x + u.y; y.y = y.y - u.x;
       } else {
-        x.x = ur + vi; x.y = ui - vr; y.x = ur - vi; y.y = ui + vr;
+        x.x = u.x - y.y; x.y = u.y + y.x; y.x = y.x - u.y; y.y = y.y + u.x;
       }
-    } else if constexpr (K == PK_SY) {  // unscaled: ((1+i) d, (1+i) s), d = x - y, s = x + y
-      const R dr = x.x - y.x, di = x.y - y.y, sr = x.x + y.x, si = x.y + y.y;
-      if constexpr (!CONJ) {
-        x.x = dr - di; x.y = dr + di; y.x = sr - si; y.y = sr + si;
-      } else {
-        x.x = dr + di; x.y = di - dr; y.x = sr + si; y.y = si - sr;
-      }
+    } else if constexpr (K == PK_SY) {  // [[1, -1], [1, 1]] (real)
+      const Cplx u = x;
+      x.x = u.x - y.x; x.y = u.y - y.y;
+      y.x = u.x + y.x; y.y = u.y + y.y;
     } else if constexpr (K == PK_X) {
       const Cplx t = x;
       x = y;
@@ -188,26 +187,19 @@ struct DFArith {
       const dfc u = dfc_add(x, y), v = dfc_sub(x, y);
       x = u;
       y = v;
-    } else if constexpr (K == PK_SX) {
-      // unscaled: x' = u + i v, y' = u - i v with u = x + y, v = x - y
-      const dfc u = dfc_add(x, y), v = dfc_sub(x, y);
+    } else if constexpr (K == PK_SX) {  // [[1, -i], [-i, 1]]  (conj: [[1, i], [i, 1]])
+      const dfc u = x;
       if constexpr (!CONJ) {
-        x = dfc{df_sub(u.re, v.im), df_add(u.im, v.re)};
-        y = dfc{df_add(u.re, v.im), df_sub(u.im, v.re)};
+        x = dfc{df_add(u.re, y.im), df_sub(u.im, y.re)};
+        y = dfc{df_add(y.re, u.im), df_sub(y.im, u.re)};
       } else {
-        x = dfc{df_add(u.re, v.im), df_sub(u.im, v.re)};
-        y = dfc{df_sub(u.re, v.im), df_add(u.im, v.re)};
+        x = dfc{df_sub(u.re, y.im), df_add(u.im, y.re)};
+        y = dfc{df_sub(y.re, u.im), df_add(y.im, u.re)};
       }
-    } else if constexpr (K == PK_SY) {
-      // unscaled: x' = (1 + i)(x - y), y' = (1 + i)(x + y)  (conj: 1 - i)
-      const dfc d = dfc_sub(x, y), s = dfc_add(x, y);
-      if constexpr (!CONJ) {
-        x = dfc{df_sub(d.re, d.im), df_add(d.re, d.im)};
-        y = dfc{df_sub(s.re, s.im), df_add(s.re, s.im)};
-      } else {
-        x = dfc{df_add(d.re, d.im), df_sub(d.im, d.re)};
-        y = dfc{df_add(s.re, s.im), df_sub(s.im, s.re)};
-      }
+    } else if constexpr (K == PK_SY) {  // [[1, -1], [1, 1]]
+      const dfc u = x;
+      x = dfc_sub(u, y);
+      y = dfc_add(u, y);
     } else if constexpr (K == PK_X) {
       const dfc t = x;
       x = y;
@@ -328,7 +320,7 @@ __device__ __forceinline__ void apply_op(typename A::Cplx (&v)[1 << R], const FO
     case FK_DEPOL: depol_dispatch<A, R>(v, op); break;
     case FK_SCALE:
 #pragma unroll
-      for (int j = 0; j < (1 << R); ++j) v[j] = A::scale(v[j], op, 0);
+      for (int j = 0; j < (1 << R); ++j) v[j] = A::phase(v[j], op);
       break;
     default: break;
   }
