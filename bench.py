@@ -36,6 +36,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6400.0
 FP64_NOMINAL_TFLOPS = 1.25   # B300 dense FP64 (non-tensor), nominal
 FP32_NOMINAL_TFLOPS = 75.0   # B300 FP32: 148 SMs x 128 lanes x 2 x ~2.0 GHz
+FP32_ISSUE_TINSTR = 148 * 128 * 2.032e9 / 1e12   # FP32 instructions/s at the 2032 MHz max clock
 # DRAM bytes (read + write) per amplitude per launch, from one ncu capture of
 # the kernel as built (profiles/<kernel>_*_ncu_full.md); scaled by the
 # amplitudes a launch processes.  Entries are removed when a kernel changes.
@@ -169,24 +170,37 @@ def run_reference(args):
 
 
 def roofline(stats, amps_per_launch=None):
+    """Roofline of the kernel class with the most time: HBM bytes per second
+    against the measured copy bandwidth, and arithmetic instructions per
+    second against the issue peak of its precision; the larger fraction
+    names the bound."""
     hbm_peak, peak_src = peaks()
     dom = max(stats, key=lambda s: s["total_ms"]) if stats else None
     if not dom or dom["total_ms"] <= 0:
         return None
     per_launch_ms = dom["total_ms"] / dom["launches"]
-    gbs = dom["bytes"] / dom["launches"] / (per_launch_ms / 1e3) / 1e9
-    tflops = dom["flops"] / dom["launches"] / (per_launch_ms / 1e3) / 1e12
+    secs = per_launch_ms / 1e3
+    gbs = dom["bytes"] / dom["launches"] / secs / 1e9
     fp64 = dom["name"].endswith("c128")
-    alu_peak = FP64_NOMINAL_TFLOPS if fp64 else FP32_NOMINAL_TFLOPS
-    if gbs / hbm_peak >= tflops / alu_peak:
+    if dom.get("alu_ops"):
+        alu = dom["alu_ops"] / dom["launches"] / secs / 1e12
+        alu_peak = FP64_NOMINAL_TFLOPS / 2 if fp64 else FP32_ISSUE_TINSTR
+        alu_unit = "T FP64 instr/s" if fp64 else "T FP32 instr/s"
+        alu_src = ("nominal B300 FP64 1.25 TFLOP/s = 0.625 T instructions/s (FMA = 1)" if fp64 else
+                   "148 SMs x 128 FP32 lanes x 2.032 GHz = 38.5 T instructions/s")
+    else:
+        alu = dom["flops"] / dom["launches"] / secs / 1e12
+        alu_peak = FP64_NOMINAL_TFLOPS if fp64 else FP32_NOMINAL_TFLOPS
+        alu_unit = "TFLOP/s"
+        alu_src = "nominal B300 FP64 1.25 TFLOP/s" if fp64 else "nominal B300 FP32 75 TFLOP/s"
+    if gbs / hbm_peak >= alu / alu_peak:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": gbs / hbm_peak, "traffic": None,
-                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"}
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                "alu_achieved": alu, "alu_unit": alu_unit, "alu_frac": alu / alu_peak}
     else:
-        roof = {"bound": "alu", "achieved": tflops, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": tflops / alu_peak, "traffic": None,
-                "peak_source": ("nominal B300 FP64 1.25 TFLOP/s" if fp64 else
-                                "nominal B300 FP32 (148 SMs x 128 lanes x 2 x 2 GHz)"),
+        roof = {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": alu_unit,
+                "frac": alu / alu_peak, "traffic": None, "peak_source": alu_src,
                 "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak}
     per_amp = MEASURED_TRAFFIC_PER_AMP.get(dom["name"])
     if per_amp is not None and amps_per_launch:
@@ -194,7 +208,8 @@ def roofline(stats, amps_per_launch=None):
         roof["traffic_source"] = "ncu dram bytes of a 26-qubit capture, scaled by amplitudes"
     roof.update({"kernel": dom["name"], "launch_ms": per_launch_ms,
                  "bytes_per_launch": dom["bytes"] / dom["launches"],
-                 "flops_per_launch": dom["flops"] / dom["launches"]})
+                 "flops_per_launch": dom["flops"] / dom["launches"],
+                 "alu_ops_per_launch": dom.get("alu_ops", 0) / dom["launches"]})
     return roof
 
 

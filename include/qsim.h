@@ -330,13 +330,17 @@ int calcTotalProbNoAlloc(const void *amps, int precision, int64_t numAmps, doubl
  * "sv_pair_gen_c128").  getKernelStats waits for the stream, then fills up
  * to maxOut entries and writes the number of classes to *count.  Bytes and
  * flops are algorithmic: the amplitudes a launch must read and write and
- * the floating-point operations its arithmetic needs (FMA = 2). */
+ * the floating-point operations its arithmetic needs (FMA = 2).  alu_ops
+ * (fused passes and batches; 0 elsewhere) counts the arithmetic
+ * instructions that arithmetic issues, each add, multiply or FMA once, in
+ * the kernel's own precision (double-float counted in FP32 instructions). */
 typedef struct {
     char name[48];
     int64_t launches;
     double total_ms;
     double bytes;
     double flops;
+    double alu_ops;
 } QSKernelStat;
 int getKernelStats(QuESTEnv env, QSKernelStat *out, int maxOut, int *count);
 int resetKernelStats(QuESTEnv env);

@@ -713,6 +713,7 @@ int getKernelStats(QuESTEnv e, QSKernelStat* out, int maxOut, int* count) {
       out[i].total_ms = k.ms;
       out[i].bytes = k.bytes;
       out[i].flops = k.flops;
+      out[i].alu_ops = k.alu;
     }
   });
 }

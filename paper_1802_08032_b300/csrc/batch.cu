@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kNormThreads) k_batch_norms(const NormDesc* __
 struct Wave {
   int first_item = 0, nitems = 0;
   int kmax = 0, Lmin = 64, opmax = 0, stmax = 0;
-  double bytes = 0, flops = 0;
+  double bytes = 0, flops = 0, alu = 0;
 };
 
 struct Batch {
@@ -87,7 +87,7 @@ struct Batch {
   double* h_out = nullptr;
   std::vector<Wave> waves;
   int64_t passes = 0;
-  double bytes = 0, flops = 0;
+  double bytes = 0, flops = 0, alu = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -164,6 +164,7 @@ void build(Batch& b) {
   b.passes = 0;
   b.bytes = 0;
   b.flops = 0;
+  b.alu = 0;
   for (size_t r = 0; r < b.regs.size(); ++r) {
     const RegPlan& pl = plans[r];
     const int op0 = int(ops.size()), st0 = int(st.size());
@@ -201,10 +202,12 @@ void build(Batch& b) {
       const double amps = std::ldexp(1.0, fp.nq);
       wave.bytes += amps * S * (fp.init ? 1.0 : 2.0);
       wave.flops += plans[r].flops[w];
+      wave.alu += plans[r].alu[w];
     }
     wave.nitems = int(items.size()) - wave.first_item;
     b.bytes += wave.bytes;
     b.flops += wave.flops;
+    b.alu += wave.alu;
     b.waves.push_back(wave);
   }
   std::vector<NormDesc> nd;
@@ -252,7 +255,7 @@ Batch& batch_of(QSBatch h) {
 }
 
 void run(Batch& b) {
-  KTimer kt(*b.env, "batch_graph", b.bytes, b.flops, int(b.waves.size()) + 1);
+  KTimer kt(*b.env, "batch_graph", b.bytes, b.flops, int(b.waves.size()) + 1, b.alu);
   QS_CUDA(cudaGraphLaunch(b.exec, b.env->stream));
 }
 

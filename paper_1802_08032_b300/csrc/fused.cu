@@ -284,9 +284,27 @@ double vop_flops(const VOp& v, int nq) {
   return 0;
 }
 
+// Arithmetic instructions (add, multiply, FMA: 1 each) one vector op issues,
+// in the precision of the kernel's arithmetic.  Plain FP32/FP64 per pair:
+// general 16, H / sqrt(X) / sqrt(Y) 4; per touched amplitude: phase 4,
+// dephasing 2; per quad: depolarising 12; per amplitude: scale 4.
+// Double-float: df add 11, df multiply 7, four-term df dot product 43.
+double vop_alu(const VOp& v, int nq, Arith a) {
+  const double dim = std::ldexp(1.0, nq), f = std::ldexp(1.0, -popc(v.cond));
+  const bool d = a == Arith::DF;
+  static const double plain_pair[5] = {16, 4, 4, 4, 0};
+  static const double df_pair[5] = {172, 44, 44, 44, 0};
+  if (v.kind <= FK_X) return dim / 2 * f * (d ? df_pair[v.kind] : plain_pair[v.kind]);
+  if (v.kind == FK_PHASE) return dim * f * (d ? 50 : 4);
+  if (v.kind == FK_SCALE) return dim * (d ? 50 : 4);
+  if (v.kind == FK_DEPH) return dim / 2 * (d ? 14 : 2);
+  if (v.kind == FK_DEPOL) return dim / 4 * (d ? 156 : 12);
+  return 0;
+}
+
 template <class A, int R>
 void launch_pass(Env& env, Reg& r, const FPass& fp, const FOp* d_ops, const FStage* d_st,
-                 double flops, const char* name) {
+                 double flops, double alu, const char* name) {
   const size_t smem = fused_smem_bytes<A>(fp.k, fp.L, fp.op_count, fp.stage_end - fp.stage_begin);
   static bool attr_set = false;
   if (!attr_set) {
@@ -296,7 +314,7 @@ void launch_pass(Env& env, Reg& r, const FPass& fp, const FOp* d_ops, const FSta
   const int threads = 1 << (fp.k - R);
   const int64_t grid = std::min<int64_t>(fp.ntiles, int64_t(env.sms) * 2);
   const double bytes = std::ldexp(2.0 * sizeof(typename A::Store), r.nq);
-  KTimer kt(env, name, bytes, flops);
+  KTimer kt(env, name, bytes, flops, 1, alu);
   k_fused<A, R><<<int(grid), threads, smem, env.stream>>>(static_cast<typename A::Store*>(r.d), fp,
                                                           d_ops, d_st);
 }
@@ -380,8 +398,13 @@ void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, RegPlan& 
     fp.op_count = int(out.fops.size()) - fp.op_begin;
     out.fps.push_back(fp);
     double fl = 0;
-    for (const VOp& v : p.ops) fl += vop_flops(v, r.nq);
+    double al = 0;
+    for (const VOp& v : p.ops) {
+      fl += vop_flops(v, r.nq);
+      al += vop_alu(v, r.nq, out.arith);
+    }
     out.flops.push_back(fl);
+    out.alu.push_back(al);
   }
 }
 
@@ -408,11 +431,11 @@ void flush(Reg& r) {
   const FStage* d_st = static_cast<const FStage*>(env.d_fst);
   for (size_t i = 0; i < pl.fps.size(); ++i) {
     if (pl.arith == Arith::DF)
-      launch_pass<DFArith, 4>(env, r, pl.fps[i], d_ops, d_st, pl.flops[i], "fused_c128_df");
+      launch_pass<DFArith, 4>(env, r, pl.fps[i], d_ops, d_st, pl.flops[i], pl.alu[i], "fused_c128_df");
     else if (pl.arith == Arith::F64)
-      launch_pass<PlainArith<double>, 4>(env, r, pl.fps[i], d_ops, d_st, pl.flops[i], "fused_c128");
+      launch_pass<PlainArith<double>, 4>(env, r, pl.fps[i], d_ops, d_st, pl.flops[i], pl.alu[i], "fused_c128");
     else
-      launch_pass<PlainArith<float>, 5>(env, r, pl.fps[i], d_ops, d_st, pl.flops[i], "fused_c64");
+      launch_pass<PlainArith<float>, 5>(env, r, pl.fps[i], d_ops, d_st, pl.flops[i], pl.alu[i], "fused_c64");
   }
   QS_CUDA(cudaGetLastError());
 }

@@ -19,6 +19,7 @@ struct RegPlan {
   std::vector<FOp> fops;
   std::vector<FStage> fst;
   std::vector<double> flops;  // algorithmic flops per pass
+  std::vector<double> alu;    // arithmetic instructions per pass (kernel precision)
   int64_t vops = 0;           // vector operations planned
 };
 

@@ -36,7 +36,8 @@ void Profiler::reset() {
   stats.clear();
 }
 
-KTimer::KTimer(Env& env, const char* name, double bytes, double flops, int nlaunch) : env_(env) {
+KTimer::KTimer(Env& env, const char* name, double bytes, double flops, int nlaunch, double alu)
+    : env_(env) {
   env.launches += nlaunch;
   if (!env.profile) return;
   cls_ = env.prof.class_of(name);
@@ -44,6 +45,7 @@ KTimer::KTimer(Env& env, const char* name, double bytes, double flops, int nlaun
   s.launches += 1;
   s.bytes += bytes;
   s.flops += flops;
+  s.alu += alu;
   a_ = env.prof.event();
   cudaEventRecord(a_, env.stream);
 }

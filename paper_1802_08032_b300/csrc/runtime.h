@@ -52,7 +52,7 @@ struct Env;
 struct KStat {
   std::string name;
   int64_t launches = 0;
-  double ms = 0, bytes = 0, flops = 0;
+  double ms = 0, bytes = 0, flops = 0, alu = 0;
 };
 struct KPending {
   int cls;
@@ -126,7 +126,7 @@ struct Env {
 // right before the launch, destroy right after it.  Counts launches always.
 class KTimer {
  public:
-  KTimer(Env& env, const char* name, double bytes, double flops, int nlaunch = 1);
+  KTimer(Env& env, const char* name, double bytes, double flops, int nlaunch = 1, double alu = 0);
   ~KTimer();
   KTimer(const KTimer&) = delete;
   KTimer& operator=(const KTimer&) = delete;

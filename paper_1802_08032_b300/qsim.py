@@ -85,7 +85,7 @@ class QSResult(ctypes.Structure):
 class QSKernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64),
                 ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double),
-                ("flops", ctypes.c_double)]
+                ("flops", ctypes.c_double), ("alu_ops", ctypes.c_double)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -418,7 +418,7 @@ def getKernelStats(env) -> list:
     arr = (QSKernelStat * max(1, cnt.value))()
     _check(LIB.getKernelStats(env, arr, cnt.value, ctypes.byref(cnt)))
     return [{"name": a.name.decode(), "launches": a.launches, "total_ms": a.total_ms,
-             "bytes": a.bytes, "flops": a.flops} for a in arr[:cnt.value]]
+             "bytes": a.bytes, "flops": a.flops, "alu_ops": a.alu_ops} for a in arr[:cnt.value]]
 
 
 def resetKernelStats(env):
