@@ -244,10 +244,14 @@ __device__ __forceinline__ void pair_dispatch_bit(typename A::Cplx (&v)[1 << R],
   }
 }
 
-template <class A, int R, int K>
+// MASKED: the op may carry control bits among the register bits (only the
+// general matrix and X do; the planner turns a controlled H / sqrt(X) /
+// sqrt(Y) into a general matrix), so the per-pair test is compiled in only
+// where it can be needed.
+template <class A, int R, int K, bool MASKED>
 __device__ __forceinline__ void pair_dispatch(typename A::Cplx (&v)[1 << R], const FOp& op) {
-  if (op.conj) pair_dispatch_bit<A, R, K, true, true>(v, op.i0, op.rmask, op);
-  else pair_dispatch_bit<A, R, K, false, true>(v, op.i0, op.rmask, op);
+  if (op.conj) pair_dispatch_bit<A, R, K, true, MASKED>(v, op.i0, op.rmask, op);
+  else pair_dispatch_bit<A, R, K, false, MASKED>(v, op.i0, op.rmask, op);
 }
 
 template <class A, int R, int I0, int I1>
@@ -295,11 +299,11 @@ __device__ __forceinline__ void apply_op(typename A::Cplx (&v)[1 << R], const FO
   if ((tlocal & op.lmask) != op.lmask) return;
   if ((tglobal & op.gmask) != op.gmask) return;
   switch (op.kind) {
-    case FK_GEN: pair_dispatch<A, R, PK_GEN>(v, op); break;
-    case FK_H: pair_dispatch<A, R, PK_H>(v, op); break;
-    case FK_SX: pair_dispatch<A, R, PK_SX>(v, op); break;
-    case FK_SY: pair_dispatch<A, R, PK_SY>(v, op); break;
-    case FK_X: pair_dispatch<A, R, PK_X>(v, op); break;
+    case FK_GEN: pair_dispatch<A, R, PK_GEN, true>(v, op); break;
+    case FK_H: pair_dispatch<A, R, PK_H, false>(v, op); break;
+    case FK_SX: pair_dispatch<A, R, PK_SX, false>(v, op); break;
+    case FK_SY: pair_dispatch<A, R, PK_SY, false>(v, op); break;
+    case FK_X: pair_dispatch<A, R, PK_X, true>(v, op); break;
     case FK_PHASE:
 #pragma unroll
       for (int j = 0; j < (1 << R); ++j)
@@ -406,6 +410,25 @@ __device__ __forceinline__ void process_tile(typename A::Store* __restrict__ g, 
       if (base == 0 && l == 0) z.x = 1;
       m.tile[l] = A::from_store(z);
     }
+  } else if constexpr (sizeof(Store) == 8) {
+    // complex64: two amplitudes per 16-byte access (chunks of 2^L >= 2
+    // contiguous amplitudes start at even indices)
+    const int npair = ntile >> 1;
+    const float4* g4 = reinterpret_cast<const float4*>(g);
+    float4* t4 = reinterpret_cast<float4*>(m.tile);
+    for (int e0 = threadIdx.x; e0 < npair; e0 += blockDim.x * 8) {
+      float4 t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int l = 2 * (e0 + u * blockDim.x);
+        if (!GENERAL || l < ntile) t[u] = g4[(base + m.choff[l >> L] + (l & lmask_low)) >> 1];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (!GENERAL || e < npair) t4[e] = t[u];
+      }
+    }
   } else {
     // load: 8 independent loads in flight per thread
     for (int l0 = threadIdx.x; l0 < ntile; l0 += blockDim.x * 8) {
@@ -433,15 +456,14 @@ __device__ __forceinline__ void process_tile(typename A::Store* __restrict__ g, 
         poff[i] = 1u << st.pbits[i];
         pm |= poff[i];
       }
-      // tlocal: deposit threadIdx into the local positions not in pm
-      uint32_t tlocal = 0;
-      {
-        int pos = 0;
-        for (int b = 0; b < k; ++b) {
-          if (pm & (1u << b)) continue;
-          tlocal |= uint32_t((threadIdx.x >> pos) & 1) << b;
-          ++pos;
-        }
+      // tlocal: threadIdx with a zero bit inserted at each register-bit
+      // position (positions ascending), i.e. its bits spread over the local
+      // positions not in pm
+      uint32_t tlocal = threadIdx.x;
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const uint32_t p = st.pbits[i];
+        tlocal = ((tlocal >> p) << (p + 1)) | (tlocal & ((1u << p) - 1u));
       }
       Cplx v[1 << R];
 #pragma unroll
@@ -465,11 +487,24 @@ __device__ __forceinline__ void process_tile(typename A::Store* __restrict__ g, 
     __syncthreads();
   }
   // store
-  for (int l0 = threadIdx.x; l0 < ntile; l0 += blockDim.x * 8) {
+  if constexpr (sizeof(Store) == 8) {
+    const int npair = ntile >> 1;
+    float4* g4 = reinterpret_cast<float4*>(g);
+    const float4* t4 = reinterpret_cast<const float4*>(m.tile);
+    for (int e0 = threadIdx.x; e0 < npair; e0 += blockDim.x * 8) {
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int l = l0 + u * blockDim.x;
-      if (!GENERAL || l < ntile) g[base + m.choff[l >> L] + (l & lmask_low)] = A::to_store(m.tile[l]);
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (!GENERAL || e < npair) g4[(base + m.choff[(2 * e) >> L] + ((2 * e) & lmask_low)) >> 1] = t4[e];
+      }
+    }
+  } else {
+    for (int l0 = threadIdx.x; l0 < ntile; l0 += blockDim.x * 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int l = l0 + u * blockDim.x;
+        if (!GENERAL || l < ntile) g[base + m.choff[l >> L] + (l & lmask_low)] = A::to_store(m.tile[l]);
+      }
     }
   }
   __syncthreads();
