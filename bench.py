@@ -171,6 +171,23 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def job_max(x, world, device):
+    """Largest value of x over the ranks of the job (the job's time is its
+    slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0])
+
+
+def job_throughput(units_per_rank, world, seconds_max):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (replicas: every rank runs the same workload)."""
+    return units_per_rank * world / seconds_max
+
+
 def roofline(stats, amps_per_launch=None):
     """Roofline of the kernel class with the most time: HBM bytes per second
     against the measured copy bandwidth, and arithmetic instructions per
@@ -234,10 +251,7 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t[0])
+        return job_max(x, world, "cuda")
 
     n, prec = args.qubits, args.prec
     ops = C.workload_30q(n)
@@ -293,7 +307,7 @@ def main():
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - te)
 
-    total_gates = ngates * args.steps * world
+    total_gates = ngates * args.steps * world  # = job_throughput(...) x time
     dtype = "f32" if prec == 64 else ("df64 (f32 pairs)" if args.arith == "df" else "f64")
     line = {
         "metric": "gates/s (30q random circuit)", "value": total_gates / (dev_ms / 1e3),

@@ -265,6 +265,21 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
         src(v.b1, f.bsrc, f.bpos);
       }
       set_coeffs(f, v.c, arith);
+      if (v.kind == FK_PHASE || v.kind == FK_SIGN) {
+        uint32_t touch = 0;  // register amplitudes j whose index has every rmask bit
+        for (int j = 0; j < (1 << R); ++j)
+          if ((uint32_t(j) & f.rmask) == f.rmask) touch |= 1u << j;
+        f.c.u[15] = touch;
+      }
+      // consecutive sign flips under the same thread / tile condition compose
+      // into one (the product of sign operators is their XOR)
+      if (v.kind == FK_SIGN && int32_t(fops.size()) - first > st.op_begin) {
+        FOp& prev = fops.back();
+        if (prev.kind == FK_SIGN && prev.lmask == f.lmask && prev.gmask == f.gmask) {
+          prev.c.u[15] ^= f.c.u[15];
+          continue;
+        }
+      }
       fops.push_back(f);
     }
     st.op_end = int32_t(fops.size()) - first;

@@ -60,6 +60,7 @@ struct FOp {
   union {
     double d[8];
     float f[16];
+    uint32_t u[16];  // PHASE / SIGN: u[15] = the register amplitudes j the op touches
   } c;
 };
 static_assert(sizeof(FOp) == 88, "FOp layout");
@@ -283,6 +284,19 @@ __device__ __forceinline__ void depol_dispatch(typename A::Cplx (&v)[1 << R], co
   }
 }
 
+// Mask of register indices j with bit i clear, as a bit set over j (R <= 5).
+__constant__ uint32_t c_bit_clear[5] = {0x55555555u, 0x33333333u, 0x0F0F0F0Fu, 0x00FF00FFu,
+                                        0x0000FFFFu};
+
+// True when the set `f` of register indices is NOT invariant under toggling
+// index bit i, i.e. a diagonal op with support f does not commute with a
+// pair update on register bit i.
+__device__ __forceinline__ bool depends_on_bit(uint32_t f, int i) {
+  const uint32_t m = c_bit_clear[i];
+  const int s = 1 << i;
+  return ((((f >> s) & m) | ((f & m) << s)) != f);
+}
+
 __device__ __forceinline__ int bit_value(uint8_t src, uint8_t pos, int j, uint32_t tlocal,
                                          uint64_t tglobal) {
   if (src == BS_REG) return (j >> pos) & 1;
@@ -304,16 +318,20 @@ __device__ __forceinline__ void apply_op(typename A::Cplx (&v)[1 << R], const FO
     case FK_SX: pair_dispatch<A, R, PK_SX, false>(v, op); break;
     case FK_SY: pair_dispatch<A, R, PK_SY, false>(v, op); break;
     case FK_X: pair_dispatch<A, R, PK_X, true>(v, op); break;
-    case FK_PHASE:
+    case FK_PHASE: {
+      const uint32_t touch = op.c.u[15];
 #pragma unroll
       for (int j = 0; j < (1 << R); ++j)
-        if ((uint32_t(j) & op.rmask) == op.rmask) v[j] = A::phase(v[j], op);
+        if ((touch >> j) & 1u) v[j] = A::phase(v[j], op);
       break;
-    case FK_SIGN:
+    }
+    case FK_SIGN: {
+      const uint32_t touch = op.c.u[15];
 #pragma unroll
       for (int j = 0; j < (1 << R); ++j)
-        if ((uint32_t(j) & op.rmask) == op.rmask) v[j] = A::negate(v[j]);
+        if ((touch >> j) & 1u) v[j] = A::negate(v[j]);
       break;
+    }
     case FK_DEPH:
 #pragma unroll
       for (int j = 0; j < (1 << R); ++j)
@@ -474,7 +492,33 @@ __device__ __forceinline__ void process_tile(typename A::Store* __restrict__ g, 
           if (j & (1 << i)) off |= poff[i];
         v[j] = m.tile[tlocal | off];
       }
-      for (int o = st.op_begin; o < st.op_end; ++o) apply_op<A, R>(v, m.ops[o], tlocal, uint64_t(base));
+      // Sign flips (CZ, multi-controlled phase flips) commute with every
+      // diagonal op, and with a pair update on register bit i whenever the
+      // flipped set is symmetric under toggling bit i; so they are collected
+      // as a per-thread mask over the register amplitudes and applied only
+      // before an op they do not commute with, or at the end of the stage.
+      uint32_t flips = 0;
+      for (int o = st.op_begin; o < st.op_end; ++o) {
+        const FOp& op = m.ops[o];
+        if (op.kind == FK_SIGN) {
+          if ((tlocal & op.lmask) == op.lmask && (uint64_t(base) & op.gmask) == op.gmask)
+            flips ^= op.c.u[15];
+          continue;
+        }
+        if (flips && (op.kind <= FK_X || op.kind == FK_DEPOL) &&
+            (depends_on_bit(flips, op.i0) || (op.kind == FK_DEPOL && depends_on_bit(flips, op.i1)))) {
+#pragma unroll
+          for (int j = 0; j < (1 << R); ++j)
+            if ((flips >> j) & 1u) v[j] = A::negate(v[j]);
+          flips = 0;
+        }
+        apply_op<A, R>(v, op, tlocal, uint64_t(base));
+      }
+      if (flips) {
+#pragma unroll
+        for (int j = 0; j < (1 << R); ++j)
+          if ((flips >> j) & 1u) v[j] = A::negate(v[j]);
+      }
 #pragma unroll
       for (int j = 0; j < (1 << R); ++j) {
         uint32_t off = 0;
