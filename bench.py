@@ -424,7 +424,8 @@ def variants(Q, env, torch, stream):
 
     for name, fn in (("sv30_c64", sv(64, 0)), ("sv30_c128_df", sv(128, 1)),
                      ("single_gate_sweep", sweep), ("dm14_c128", dm14),
-                     ("batch4096_c64", lambda: batch_variant(Q, env, torch, stream))):
+                     ("batch4096_c64", lambda: batch_variant(Q, env, torch, stream)),
+                     ("serving", lambda: serve_sweep(Q, env, [10, 100], 60))):
         try:
             out[name] = fn()
         except Exception as e:
