@@ -105,6 +105,7 @@ def lib():
             "orc_total_prob_dm": [P, I], "orc_prob_outcome_dm": [P, I, I, I],
             "orc_purity_dm": [P, I],
             "orc_collapse_sv": [P, I, I, I, D], "orc_collapse_dm": [P, I, I, I, D],
+            "orc_apply_multi": [P, I, P, I, U64, P], "orc_apply_dm_multi": [P, I, P, I, U64, P],
             "orc_num_threads": [],
         }
         for name, args in sig.items():
@@ -162,6 +163,18 @@ class State:
         else:
             lib().orc_phase_flip(_ptr(self.a), self.n, _mask(qubits))
 
+    def multi(self, targets, U, controls=()):
+        """Dense 2^m x 2^m gate U on `targets` (bit k of U's index is
+        targets[k]), restricted to the controls."""
+        m = len(targets)
+        U = _cmat(U)
+        assert U.size == 4 ** m and 1 <= m <= 6
+        t = (ctypes.c_int * m)(*targets)
+        if self.density:
+            lib().orc_apply_dm_multi(_ptr(self.a), self.n, t, m, _mask(controls), U.ctypes.data)
+        else:
+            lib().orc_apply_multi(_ptr(self.a), self.n, t, m, _mask(controls), U.ctypes.data)
+
     def kraus(self, q, ops):
         assert self.density
         K = _cmat(np.stack(ops))
@@ -181,6 +194,10 @@ class State:
             self.kraus(op.targets[0], kraus_dephasing(op.params[0]))
         elif k == "DEPOL":
             self.kraus(op.targets[0], kraus_depolarising(op.params[0]))
+        elif k == "MULTI":
+            m = len(op.targets)
+            v = np.array(op.params, dtype=np.float64).reshape(-1, 2)
+            self.multi(op.targets, (v[:, 0] + 1j * v[:, 1]).reshape(1 << m, 1 << m), op.controls)
         else:
             raise ValueError(f"oracle: unknown op {k}")
 

@@ -213,3 +213,50 @@ int orc_num_threads(void) {
     return 1;
 #endif
 }
+
+/*
+ * m-target gate U (2^m x 2^m, row-major; bit k of the block index is qubit
+ * t[k]) on the amplitudes whose bits in ctrl_mask are all 1: for every base
+ * index with the target bits 0, the 2^m amplitudes a[base + sum_k bit_k(l)
+ * 2^t[k]] (l = 0..2^m-1) are replaced by U times them.  This is Eq. 1 with
+ * the pair replaced by a block of 2^m amplitudes (the paper's multi-qubit
+ * generalisation, Sec. II.B.1).
+ */
+void orc_apply_multi(cplx *a, int nq, const int *t, int m, uint64_t ctrl_mask, const cplx *U) {
+    const int64_t dim = (int64_t)1 << nq;
+    const int64_t bs = (int64_t)1 << m;
+    uint64_t tmask = 0;
+    for (int k = 0; k < m; ++k) tmask |= (uint64_t)1 << t[k];
+#pragma omp parallel for schedule(static)
+    for (int64_t base = 0; base < dim; ++base) {
+        if ((uint64_t)base & tmask) continue;
+        if (((uint64_t)base & ctrl_mask) != ctrl_mask) continue;
+        cplx v[64], w[64];
+        int64_t idx[64];
+        for (int64_t l = 0; l < bs; ++l) {
+            int64_t off = 0;
+            for (int k = 0; k < m; ++k)
+                if ((l >> k) & 1) off += (int64_t)1 << t[k];
+            idx[l] = base + off;
+            v[l] = a[idx[l]];
+        }
+        for (int64_t r = 0; r < bs; ++r) {
+            cplx s = 0;
+            for (int64_t c = 0; c < bs; ++c) s += U[r * bs + c] * v[c];
+            w[r] = s;
+        }
+        for (int64_t l = 0; l < bs; ++l) a[idx[l]] = w[l];
+    }
+}
+
+/* Density matrix: U on the row bits t, then conj(U) on the column bits t+N
+ * (Eq. 2; the paper states the rule holds for multi-qubit gates). */
+void orc_apply_dm_multi(cplx *rho, int N, const int *t, int m, uint64_t ctrl_mask, const cplx *U) {
+    const int64_t bs = (int64_t)1 << m;
+    cplx Uc[64 * 64];
+    int tc[8];
+    for (int64_t e = 0; e < bs * bs; ++e) Uc[e] = conj(U[e]);
+    for (int k = 0; k < m; ++k) tc[k] = t[k] + N;
+    orc_apply_multi(rho, 2 * N, t, m, ctrl_mask, U);
+    orc_apply_multi(rho, 2 * N, tc, m, ctrl_mask << N, Uc);
+}

@@ -287,3 +287,78 @@ def test_collapse_dm():
     assert abs(p - np.trace(P @ rho).real) < 1e-15
     assert np.max(np.abs(s.matrix() - ref)) < 1e-15
     assert abs(s.total_prob() - 1) < 1e-15 and abs(s.prob_outcome(1, 0) - 1) < 1e-15
+
+
+# ---------------------------------------------------------------- multi-qubit
+def rand_unitary_n(d, rng=RNG):
+    z = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
+    q, r = np.linalg.qr(z)
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+def dense_multi(n, targets, U, ctrls=()):
+    """Full matrix from the definition: <i|M|j> = U[sub(i), sub(j)] when i and
+    j agree outside the targets and the controls of j are all 1, where sub
+    collects the target bits (bit k = targets[k])."""
+    dim = 1 << n
+    tmask = sum(1 << t for t in targets)
+    cmask = sum(1 << c for c in ctrls)
+    sub = [sum(((i >> t) & 1) << k for k, t in enumerate(targets)) for i in range(dim)]
+    M = np.zeros((dim, dim), dtype=np.complex128)
+    for j in range(dim):
+        if (j & cmask) != cmask:
+            M[j, j] = 1
+            continue
+        for i in range(dim):
+            if (i & ~tmask) == (j & ~tmask):
+                M[i, j] = U[sub[i], sub[j]]
+    return M
+
+
+def test_multi_of_kronecker_product_equals_single_gates():
+    n = 6
+    A, B = rand_unitary(), rand_unitary()
+    for t0, t1 in [(0, 1), (4, 2), (5, 0)]:
+        psi = rand_state(n)
+        s = O.State(n, amps=psi)
+        s.multi((t0, t1), np.kron(B, A))          # bit 0 of U's index is t0
+        r = O.State(n, amps=psi)
+        r.gate(t0, A)
+        r.gate(t1, B)
+        assert np.max(np.abs(s.a - r.a)) < 1e-14
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4])
+def test_multi_matches_dense_definition(m):
+    n = 6
+    for trial in range(3):
+        targets = tuple(int(x) for x in RNG.choice(n, size=m, replace=False))
+        others = [q for q in range(n) if q not in targets]
+        ctrls = tuple(int(x) for x in RNG.choice(others, size=min(trial, len(others)), replace=False))
+        U = rand_unitary_n(1 << m)
+        psi = rand_state(n)
+        s = O.State(n, amps=psi)
+        s.multi(targets, U, ctrls)
+        assert np.max(np.abs(s.a - dense_multi(n, targets, U, ctrls) @ psi)) < 1e-14
+
+
+def test_multi_permutation_is_exact():
+    """The 2-qubit SWAP as a dense matrix is an exact permutation."""
+    n = 5
+    SWAP = np.eye(4, dtype=np.complex128)[[0, 2, 1, 3]]
+    psi = rand_state(n)
+    s = O.State(n, amps=psi)
+    s.multi((1, 3), SWAP)
+    perm = [(j & ~0b1010) | (((j >> 1) & 1) << 3) | (((j >> 3) & 1) << 1) for j in range(1 << n)]
+    assert np.array_equal(s.a, psi[perm])
+
+
+def test_dm_multi_matches_u_rho_udagger():
+    N = 3
+    for targets, ctrls in [((0, 2), ()), ((2, 1), (0,)), ((1,), (2,))]:
+        U = rand_unitary_n(1 << len(targets))
+        rho = rand_density(N)
+        s = O.State(N, density=True, amps=vec(rho))
+        s.multi(targets, U, ctrls)
+        Uf = dense_multi(N, targets, U, ctrls)
+        assert np.max(np.abs(s.matrix() - Uf @ rho @ Uf.conj().T)) < 1e-14
