@@ -425,7 +425,8 @@ def variants(Q, env, torch, stream):
     for name, fn in (("sv30_c64", sv(64, 0)), ("sv30_c128_df", sv(128, 1)),
                      ("single_gate_sweep", sweep), ("dm14_c128", dm14),
                      ("batch4096_c64", lambda: batch_variant(Q, env, torch, stream)),
-                     ("serving", lambda: serve_sweep(Q, env, [10, 100], 60))):
+                     ("serving", lambda: serve_sweep(Q, env, [10, 100], 60)),
+                     ("multi_target_passes", lambda: multi_sweep(Q, env, torch, stream))):
         try:
             out[name] = fn()
         except Exception as e:
@@ -497,6 +498,29 @@ def batch_variant(Q, env, torch, stream, count=4096, depth=30):
             "norm_max_dev": float(np.max(np.abs(norms - 1))),
             "plain_c128_circuits_per_s": len(sub) / ms_plain * 1e3,
             "plain_c128_subset": f"{len(sub)} of the same registers, one at a time, one kernel per gate"}
+
+
+def multi_sweep(Q, env, torch, stream, n=30):
+    """One dense 2^m x 2^m gate (targets 7..7+m-1) as a single pass over a
+    30-qubit register: algorithmic GB/s (read + write of every amplitude)."""
+    import numpy as np
+    out = {}
+    Q.setEnvOption(env, "fusion", 0)
+    try:
+        for prec in (64, 128):
+            q = Q.createQureg(n, prec, env)
+            S = 16 if prec == 128 else 8
+            try:
+                for m in range(1, 6):
+                    U = np.linalg.qr(np.random.default_rng(m).normal(size=(1 << m, 1 << m)) + 0j)[0]
+                    tg = tuple(range(7, 7 + m))
+                    ms = timed(torch, stream, lambda: Q.multiQubitUnitary(q, tg, U), 2)
+                    out[f"c{prec}_m{m}"] = {"ms": ms, "GBps": 2 * (1 << n) * S / ms / 1e6}
+            finally:
+                Q.destroyQureg(q)
+    finally:
+        Q.setEnvOption(env, "fusion", 1)
+    return out
 
 
 def serve_trace(rate, count, seed0=5000, arrival_seed=55, max_sv=28, max_dm=13):

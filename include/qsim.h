@@ -46,6 +46,8 @@ extern "C" {
 typedef struct { double re, im; } Complex;
 /* Row-major 2x2 complex matrix: m[row][column]. */
 typedef struct { Complex m[2][2]; } ComplexMatrix2;
+/* Row-major 4x4 complex matrix (two-qubit gates). */
+typedef struct { Complex m[4][4]; } ComplexMatrix4;
 typedef struct { int64_t id; } QuESTEnv;
 typedef struct { int64_t id; } Qureg;
 
@@ -158,6 +160,20 @@ int controlledNot(Qureg q, int control, int target);
 int controlledUnitary(Qureg q, int control, int target, ComplexMatrix2 u);
 int multiControlledUnitary(Qureg q, const int *controls, int numControls,
                            int target, ComplexMatrix2 u);
+/* Multi-target gates: a dense 2^m x 2^m unitary on m = numTargets qubits
+ * (1..5), the block of 2^m amplitudes differing in the target bits taking
+ * the place of Eq. 1's pair; the paper notes the density-matrix rule of
+ * Eq. 2 holds also for multi-qubit gates (Sec. II.B.1).  Bit k of the
+ * matrix's row / column index is qubit targets[k] (targets[0] is the least
+ * significant).  `u` is row-major (u[row * 2^m + column]), copied at call
+ * time, unitary within 1e-10 (QS_E_UNITARY otherwise).  Targets and
+ * controls must be distinct (QS_E_DUP).  These gates run as their own pass;
+ * queued single-target gates before and after them are fused as usual. */
+int multiQubitUnitary(Qureg q, const int *targets, int numTargets, const Complex *u);
+int multiControlledMultiQubitUnitary(Qureg q, const int *controls, int numControls,
+                                     const int *targets, int numTargets, const Complex *u);
+/* twoQubitUnitary: u.m[row][column], bit 0 of the index is target1. */
+int twoQubitUnitary(Qureg q, int target1, int target2, ComplexMatrix4 u);
 /* controlledPhaseFlip (CZ): negates amplitudes with both bits set. */
 int controlledPhaseFlip(Qureg q, int qubit1, int qubit2);
 /* multiControlledPhaseFlip: negates amplitudes whose index has every listed

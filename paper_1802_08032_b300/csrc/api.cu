@@ -628,6 +628,67 @@ int multiControlledUnitary(Qureg q, const int* ctrls, int nc, int t, ComplexMatr
   });
 }
 
+int multiControlledMultiQubitUnitary(Qureg q, const int* ctrls, int nc, const int* targets, int nt,
+                                     const Complex* u) {
+  return guarded([&] {
+    Reg& r = reg_of(q);
+    if (nt < 1 || nt > 5) fail(QS_E_ARG, "numTargets must be in 1..5");
+    need(targets, "targets");
+    need(u, "matrix");
+    if (nc < 0 || nc > r.n - nt) fail(QS_E_ARG, "numControls out of range");
+    if (nc > 0) need(ctrls, "controls");
+    uint64_t tmask = 0;
+    for (int k = 0; k < nt; ++k) {
+      check_qubit(r, targets[k], "target");
+      const uint64_t b = uint64_t(1) << targets[k];
+      if (tmask & b) fail(QS_E_DUP, "target " + std::to_string(targets[k]) + " repeated");
+      tmask |= b;
+    }
+    uint64_t cmask = 0;
+    for (int k = 0; k < nc; ++k) {
+      check_qubit(r, ctrls[k], "control");
+      const uint64_t b = uint64_t(1) << ctrls[k];
+      if ((cmask | tmask) & b) fail(QS_E_DUP, "qubit " + std::to_string(ctrls[k]) + " repeated among targets and controls");
+      cmask |= b;
+    }
+    const int d = 1 << nt;
+    auto mat = std::make_shared<std::vector<double>>(size_t(2 * d * d));
+    for (int e = 0; e < d * d; ++e) {
+      (*mat)[2 * e] = u[e].re;
+      (*mat)[2 * e + 1] = u[e].im;
+    }
+    // max |U U^dagger - I| <= 1e-10
+    double worst = 0;
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j) {
+        double re = 0, im = 0;
+        for (int s = 0; s < d; ++s) {
+          const double ar = u[i * d + s].re, ai = u[i * d + s].im;
+          const double br = u[j * d + s].re, bi = -u[j * d + s].im;
+          re += ar * br - ai * bi;
+          im += ar * bi + ai * br;
+        }
+        worst = std::max(worst, std::hypot(re - (i == j ? 1.0 : 0.0), im));
+      }
+    if (!(worst <= 1e-10))
+      fail(QS_E_UNITARY, "matrix is not unitary (max |UU^dagger - I| = " + std::to_string(worst) + ")");
+    GateOp op = make_op(OpK::MULTI, targets[0], cmask);
+    op.nt = nt;
+    for (int k = 0; k < nt; ++k) op.tg[k] = uint8_t(targets[k]);
+    op.big = mat;
+    apply(r, op);
+  });
+}
+
+int multiQubitUnitary(Qureg q, const int* targets, int nt, const Complex* u) {
+  return multiControlledMultiQubitUnitary(q, nullptr, 0, targets, nt, u);
+}
+
+int twoQubitUnitary(Qureg q, int t1, int t2, ComplexMatrix4 u) {
+  const int t[2] = {t1, t2};
+  return multiControlledMultiQubitUnitary(q, nullptr, 0, t, 2, &u.m[0][0]);
+}
+
 int controlledPhaseFlip(Qureg q, int a, int b) {
   QSOp o = blank(QS_OP_CZ, a);
   o.target2 = b;

@@ -291,6 +291,9 @@ int createBatch(QuESTEnv e, const Qureg* regs, int count, int tileQubits, QSBatc
         b->reg_ids.push_back(r.id);
       }
       b->arith = arith_of(*b->regs[0]);
+      for (Reg* r : b->regs)
+        for (const GateOp& op : r->queue)
+          if (op.k == OpK::MULTI) fail(QS_E_ARG, "batches take single-target gates only");
       for (Reg* r : b->regs) {
         b->circuits.push_back(r->queue);
         r->queue.clear();

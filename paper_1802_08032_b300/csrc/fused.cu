@@ -104,6 +104,8 @@ void expand(const Reg& r, const GateOp& op, std::vector<VOp>& out) {
       out.push_back(v);
       return;
     }
+    case OpK::MULTI:
+      fail(QS_E_ARG, "multi-target gates are not planned into fused passes");
     case OpK::DEPOL: {
       const double p = op.m[0];
       VOp v;
@@ -432,25 +434,69 @@ void flush(Reg& r) {
     for (const GateOp& op : q) launch_op(env, r, op);
     return;
   }
-  RegPlan pl;
-  build_plan(r, q, 0, pl);
-  ensure_fused_buffers(env, pl.fops.size(), pl.fst.size());
-  std::memcpy(env.h_fops, pl.fops.data(), pl.fops.size() * sizeof(FOp));
-  std::memcpy(env.h_fst, pl.fst.data(), pl.fst.size() * sizeof(FStage));
-  QS_CUDA(cudaMemcpyAsync(env.d_fops, env.h_fops, pl.fops.size() * sizeof(FOp), cudaMemcpyHostToDevice, env.stream));
-  QS_CUDA(cudaMemcpyAsync(env.d_fst, env.h_fst, pl.fst.size() * sizeof(FStage), cudaMemcpyHostToDevice, env.stream));
-  QS_CUDA(cudaEventRecord(env.fcopied, env.stream));
-  env.fused_passes += int64_t(pl.fps.size());
-  env.fused_vops += pl.vops;
-  const FOp* d_ops = static_cast<const FOp*>(env.d_fops);
-  const FStage* d_st = static_cast<const FStage*>(env.d_fst);
-  for (size_t i = 0; i < pl.fps.size(); ++i) {
-    if (pl.arith == Arith::DF)
-      launch_pass<DFArith, 4>(env, r, pl.fps[i], d_ops, d_st, pl.flops[i], pl.alu[i], "fused_c128_df");
-    else if (pl.arith == Arith::F64)
-      launch_pass<PlainArith<double>, 4>(env, r, pl.fps[i], d_ops, d_st, pl.flops[i], pl.alu[i], "fused_c128");
-    else
-      launch_pass<PlainArith<float>, 5>(env, r, pl.fps[i], d_ops, d_st, pl.flops[i], pl.alu[i], "fused_c64");
+  // Multi-target gates run as their own passes; the gates between them form
+  // fused segments.  All segments' op lists go up in one copy.
+  std::vector<RegPlan> plans;
+  std::vector<int> after;  // index into q of the multi-target gate following each plan, or -1
+  std::vector<GateOp> seg;
+  auto close = [&](int next) {
+    if (!seg.empty()) {
+      plans.emplace_back();
+      build_plan(r, seg, 0, plans.back());
+      after.push_back(next);
+      seg.clear();
+    } else if (next >= 0) {
+      plans.emplace_back();  // empty plan: only the multi-target gate
+      after.push_back(next);
+    }
+  };
+  for (size_t i = 0; i < q.size(); ++i) {
+    if (q[i].k == OpK::MULTI) close(int(i));
+    else seg.push_back(q[i]);
+  }
+  close(-1);
+  size_t nops = 0, nst = 0;
+  for (const RegPlan& pl : plans) {
+    nops += pl.fops.size();
+    nst += pl.fst.size();
+  }
+  std::vector<size_t> op0, st0;
+  if (nops > 0) {
+    ensure_fused_buffers(env, nops, nst);
+    FOp* hops = static_cast<FOp*>(env.h_fops);
+    FStage* hst = static_cast<FStage*>(env.h_fst);
+    size_t o = 0, s = 0;
+    for (const RegPlan& pl : plans) {
+      op0.push_back(o);
+      st0.push_back(s);
+      std::memcpy(hops + o, pl.fops.data(), pl.fops.size() * sizeof(FOp));
+      std::memcpy(hst + s, pl.fst.data(), pl.fst.size() * sizeof(FStage));
+      o += pl.fops.size();
+      s += pl.fst.size();
+    }
+    QS_CUDA(cudaMemcpyAsync(env.d_fops, env.h_fops, nops * sizeof(FOp), cudaMemcpyHostToDevice, env.stream));
+    QS_CUDA(cudaMemcpyAsync(env.d_fst, env.h_fst, nst * sizeof(FStage), cudaMemcpyHostToDevice, env.stream));
+    QS_CUDA(cudaEventRecord(env.fcopied, env.stream));
+  }
+  for (size_t pi = 0; pi < plans.size(); ++pi) {
+    const RegPlan& pl = plans[pi];
+    env.fused_passes += int64_t(pl.fps.size());
+    env.fused_vops += pl.vops;
+    for (size_t i = 0; i < pl.fps.size(); ++i) {
+      FPass fp = pl.fps[i];
+      fp.op_begin += int(op0[pi]);
+      fp.stage_begin += int(st0[pi]);
+      fp.stage_end += int(st0[pi]);
+      const FOp* d_ops = static_cast<const FOp*>(env.d_fops);
+      const FStage* d_st = static_cast<const FStage*>(env.d_fst);
+      if (pl.arith == Arith::DF)
+        launch_pass<DFArith, 4>(env, r, fp, d_ops, d_st, pl.flops[i], pl.alu[i], "fused_c128_df");
+      else if (pl.arith == Arith::F64)
+        launch_pass<PlainArith<double>, 4>(env, r, fp, d_ops, d_st, pl.flops[i], pl.alu[i], "fused_c128");
+      else
+        launch_pass<PlainArith<float>, 5>(env, r, fp, d_ops, d_st, pl.flops[i], pl.alu[i], "fused_c64");
+    }
+    if (after[pi] >= 0) launch_op(env, r, q[size_t(after[pi])]);
   }
   QS_CUDA(cudaGetLastError());
 }

@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "multi_kernels.cuh"
 #include "pass_kernels.cuh"
 #include "reduce_kernels.cuh"
 #include "runtime.h"
@@ -91,9 +92,48 @@ void dm_pair(Env& env, Reg& r, const GateOp& op) {
       op.cmask << N, fx, to_mat<R>(op));
 }
 
+// One multi-target pass over the vector: targets t (shifted by `shift`),
+// controls cmask, matrix (conjugated when conj).
+template <typename R, int M>
+void multi_pass(Env& env, Reg& r, const GateOp& op, int shift, uint64_t cmask, bool conj) {
+  MultiParams<R, M> p{};
+  std::vector<std::pair<int, int>> bits = ctrl_bits(cmask, 1);
+  for (int k = 0; k < M; ++k) {
+    p.t[k] = uint8_t(op.tg[k] + shift);
+    bits.push_back({op.tg[k] + shift, 0});
+  }
+  const std::vector<double>& u = *op.big;
+  for (int e = 0; e < (1 << (2 * M)); ++e) {
+    p.u[e].x = R(u[2 * e]);
+    p.u[e].y = R(conj ? -u[2 * e + 1] : u[2 * e + 1]);
+  }
+  const Fixed fx = make_fixed(bits);
+  const int64_t nsel = r.dim >> fx.n;
+  KTimer kt(env, kname<R>("sv_multi").c_str(), double(nsel) * 2 * (1 << M) * amp_bytes<R>(),
+            double(nsel) * (1 << (2 * M)) * 8);
+  k_sv_multi<R, M><<<grid_for(env, nsel, 1), kThreads, 0, env.stream>>>(static_cast<cvec<R>*>(r.d), nsel,
+                                                                        fx, p);
+}
+
+template <typename R, int M>
+void multi_op(Env& env, Reg& r, const GateOp& op) {
+  multi_pass<R, M>(env, r, op, 0, op.cmask, false);
+  if (r.density) multi_pass<R, M>(env, r, op, r.n, op.cmask << r.n, true);
+}
+
 template <typename R>
 void launch_typed(Env& env, Reg& r, const GateOp& op) {
   cvec<R>* a = static_cast<cvec<R>*>(r.d);
+  if (op.k == OpK::MULTI) {
+    switch (op.nt) {
+      case 1: multi_op<R, 1>(env, r, op); return;
+      case 2: multi_op<R, 2>(env, r, op); return;
+      case 3: multi_op<R, 3>(env, r, op); return;
+      case 4: multi_op<R, 4>(env, r, op); return;
+      case 5: multi_op<R, 5>(env, r, op); return;
+      default: fail(QS_E_ARG, "1..5 targets supported");
+    }
+  }
   if (!r.density) {
     switch (op.k) {
       case OpK::GEN: sv_pair<R, PK_GEN>(env, r, op); return;

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <functional>
+#include <memory>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -23,7 +24,8 @@ enum class OpK : int32_t {
   PHASE = 5,    // diag(1, e^{i phi}) on t: m[0] = cos phi, m[1] = sin phi
   SIGN = 6,     // negate where every bit of cmask is set (t unused)
   DEPHASE = 7,  // density matrix only, p in m[0]
-  DEPOL = 8     // density matrix only, p in m[0]
+  DEPOL = 8,    // density matrix only, p in m[0]
+  MULTI = 9     // dense 2^nt x 2^nt matrix on targets tg[0..nt) (matrix in big)
 };
 
 struct GateOp {
@@ -31,6 +33,9 @@ struct GateOp {
   int t;            // target qubit (logical), -1 for SIGN
   uint64_t cmask;   // control bits (logical qubits); SIGN: the flipped set
   double m[8];
+  int nt = 0;       // MULTI: number of targets
+  uint8_t tg[8] = {};
+  std::shared_ptr<const std::vector<double>> big;  // MULTI: row-major (re, im) matrix
 };
 
 struct Error {

@@ -46,6 +46,10 @@ class ComplexMatrix2(ctypes.Structure):
     _fields_ = [("m", (Complex * 2) * 2)]
 
 
+class ComplexMatrix4(ctypes.Structure):
+    _fields_ = [("m", (Complex * 4) * 4)]
+
+
 class QuESTEnv(ctypes.Structure):
     _fields_ = [("id", ctypes.c_int64)]
 
@@ -124,6 +128,9 @@ SIGNATURES = {
     "controlledUnitary": [Qureg, _I, _I, ComplexMatrix2],
     "multiControlledUnitary": [Qureg, _P(_I), _I, _I, ComplexMatrix2],
     "controlledPhaseFlip": [Qureg, _I, _I],
+    "multiQubitUnitary": [Qureg, _P(_I), _I, _P(Complex)],
+    "multiControlledMultiQubitUnitary": [Qureg, _P(_I), _I, _P(_I), _I, _P(Complex)],
+    "twoQubitUnitary": [Qureg, _I, _I, ComplexMatrix4],
     "multiControlledPhaseFlip": [Qureg, _P(_I), _I],
     "mixDephasing": [Qureg, _I, _D],
     "mixDepolarising": [Qureg, _I, _D],
@@ -343,6 +350,34 @@ def multiControlledUnitary(q, controls: Sequence[int], t, u):
 
 
 def controlledPhaseFlip(q, a, b): _check(LIB.controlledPhaseFlip(q, a, b))
+
+
+def _cmatrix(u):
+    import numpy as np
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.complex128).reshape(-1))
+    arr = (Complex * u.size)(*[Complex(z.real, z.imag) for z in u])
+    return arr
+
+
+def multiQubitUnitary(q, targets: Sequence[int], u):
+    """u: 2^m x 2^m unitary (bit k of its index is targets[k])."""
+    t, n = _ints(targets)
+    _check(LIB.multiQubitUnitary(q, t, n, _cmatrix(u)))
+
+
+def multiControlledMultiQubitUnitary(q, controls: Sequence[int], targets: Sequence[int], u):
+    c, nc = _ints(controls)
+    t, nt = _ints(targets)
+    _check(LIB.multiControlledMultiQubitUnitary(q, c, nc, t, nt, _cmatrix(u)))
+
+
+def twoQubitUnitary(q, t1, t2, u):
+    m = ComplexMatrix4()
+    for r in range(4):
+        for c in range(4):
+            z = complex(u[r][c])
+            m.m[r][c] = Complex(z.real, z.imag)
+    _check(LIB.twoQubitUnitary(q, t1, t2, m))
 
 
 def multiControlledPhaseFlip(q, controls: Sequence[int]):

@@ -1,0 +1,121 @@
+"""Multi-target (dense 2^m x 2^m) gates on the GPU against the CPU oracle."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1802_08032_b300 import circuits as C
+from gpu_helpers import AMP_TOL, gpu_state, rand_density_vec, rand_state
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Q():
+    from paper_1802_08032_b300 import qsim
+    return qsim
+
+
+@pytest.fixture(scope="module")
+def env(Q):
+    e = Q.createQuESTEnv()
+    yield e
+    Q.destroyQuESTEnv(e)
+
+
+def rand_u(d, seed):
+    rng = np.random.default_rng(seed)
+    z = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
+    q, r = np.linalg.qr(z)
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+def cases(n, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for m in range(1, 6):
+        for nc in (0, 1, 2):
+            if m + nc > n:
+                continue
+            qs = [int(x) for x in rng.permutation(n)[:m + nc]]
+            out.append((tuple(qs[:m]), tuple(qs[m:]), rand_u(1 << m, seed + 10 * m + nc)))
+    return out
+
+
+@pytest.mark.parametrize("prec", [128, 64])
+@pytest.mark.parametrize("fusion", [0, 1])
+def test_multi_target_state_vector(Q, env, prec, fusion):
+    n = 10
+    psi = rand_state(n, 3)
+    Q.setEnvOption(env, "fusion", fusion)
+    for targets, ctrls, U in cases(n, 100 + prec):
+        ref = O.State(n, amps=psi)
+        ref.multi(targets, U, ctrls)
+        q = Q.createQureg(n, prec, env)
+        Q.setAmps(q, psi)
+        Q.multiControlledMultiQubitUnitary(q, ctrls, targets, U)
+        got = Q.copyStateToHost(q)
+        Q.destroyQureg(q)
+        assert np.max(np.abs(got - ref.a)) <= AMP_TOL[prec] * (1 if prec == 128 else 0.1), \
+            (targets, ctrls)
+
+
+@pytest.mark.parametrize("prec", [128, 64])
+def test_multi_target_density_matrix(Q, env, prec):
+    N = 4
+    rho = rand_density_vec(N, 6)
+    for targets, ctrls, U in cases(N, 7)[:8]:
+        ref = O.State(N, density=True, amps=rho)
+        ref.multi(targets, U, ctrls)
+        d = Q.createDensityQureg(N, prec, env)
+        Q.setAmps(d, rho)
+        Q.multiControlledMultiQubitUnitary(d, ctrls, targets, U)
+        got = Q.copyStateToHost(d)
+        Q.destroyQureg(d)
+        assert np.max(np.abs(got - ref.a)) <= AMP_TOL[prec] * (1 if prec == 128 else 0.1)
+
+
+@pytest.mark.parametrize("prec", [128, 64])
+def test_multi_between_fused_segments(Q, env, prec):
+    """Fused single-target gates before, between and after multi-target gates."""
+    n = 12
+    ops = C.random_circuit(n, 8, 5, extras=True)
+    U2, U3 = rand_u(4, 1), rand_u(8, 2)
+    ref = O.State(n)
+    Q.setEnvOption(env, "fusion", 1)
+    q = Q.createQureg(n, prec, env)
+    for i, chunk in enumerate((ops[:40], ops[40:90], ops[90:])):
+        ref.run(chunk)
+        Q.applyCircuit(q, chunk)
+        if i == 0:
+            ref.multi((3, 9), U2)
+            Q.twoQubitUnitary(q, 3, 9, U2)
+        elif i == 1:
+            ref.multi((11, 0, 6), U3, (4,))
+            Q.multiControlledMultiQubitUnitary(q, (4,), (11, 0, 6), U3)
+    got = Q.copyStateToHost(q)
+    Q.destroyQureg(q)
+    assert np.max(np.abs(got - ref.a)) <= AMP_TOL[prec]
+
+
+def test_multi_target_errors(Q, env):
+    q = Q.createQureg(6, 128, env)
+    psi = Q.copyStateToHost(q)
+    bad = [
+        (lambda: Q.multiQubitUnitary(q, (1, 1), np.eye(4)), "QS_E_DUP"),
+        (lambda: Q.multiControlledMultiQubitUnitary(q, (2,), (2, 3), np.eye(4)), "QS_E_DUP"),
+        (lambda: Q.multiQubitUnitary(q, (0, 1), 2 * np.eye(4)), "QS_E_UNITARY"),
+        (lambda: Q.multiQubitUnitary(q, (0, 7), np.eye(4)), "QS_E_QUBIT"),
+        (lambda: Q.multiQubitUnitary(q, tuple(range(6)), np.eye(64)), "QS_E_ARG"),
+    ]
+    for f, name in bad:
+        with pytest.raises(Q.QSimError) as e:
+            f()
+        assert e.value.name == name
+    assert np.array_equal(Q.copyStateToHost(q), psi)
+    a = Q.createQureg(10, 64, env)
+    Q.multiQubitUnitary(a, (0, 1), np.eye(4))
+    with pytest.raises(Q.QSimError) as e:
+        Q.createBatch(env, [a])
+    assert e.value.name == "QS_E_ARG"
+    Q.destroyQureg(a)
+    Q.destroyQureg(q)
