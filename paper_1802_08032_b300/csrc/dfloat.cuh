@@ -124,3 +124,81 @@ __device__ __forceinline__ double f2d_exact(float f) {
 __device__ __forceinline__ double df_to_double(df a) { return __dadd_rn(f2d_exact(a.hi), f2d_exact(a.lo)); }
 
 }  // namespace qs
+
+// ------------------------------------------------------------------------
+// Packed complex double-float: hi = (re.hi, im.hi), lo = (re.lo, im.lo).
+// The same error-free transformations, applied to the real and imaginary
+// parts at once with the paired FP32 instructions of sm_100+ (one add /
+// multiply / FMA on two floats per lane; each half rounds exactly as the
+// scalar instruction would).
+namespace qs {
+
+struct dfc2 {
+  float2 hi, lo;
+};
+
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b with one rounding: (-1) * b is exact, the FMA rounds once.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+__device__ __forceinline__ dfc2 two_sum2(float2 a, float2 b) {
+  const float2 s = add2(a, b);
+  const float2 bb = sub2(s, a);
+  return dfc2{s, add2(sub2(a, sub2(s, bb)), sub2(b, bb))};
+}
+
+__device__ __forceinline__ dfc2 two_diff2(float2 a, float2 b) {
+  const float2 s = sub2(a, b);
+  const float2 bb = sub2(s, a);
+  return dfc2{s, sub2(sub2(a, sub2(s, bb)), add2(b, bb))};
+}
+
+__device__ __forceinline__ dfc2 fast_two_sum2(float2 a, float2 b) {
+  const float2 s = add2(a, b);
+  return dfc2{s, sub2(b, sub2(s, a))};
+}
+
+__device__ __forceinline__ dfc2 dfc2_add(dfc2 a, dfc2 b) {
+  const dfc2 s = two_sum2(a.hi, b.hi);
+  return fast_two_sum2(s.hi, add2(s.lo, add2(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ dfc2 dfc2_sub(dfc2 a, dfc2 b) {
+  const dfc2 s = two_diff2(a.hi, b.hi);
+  return fast_two_sum2(s.hi, add2(s.lo, sub2(a.lo, b.lo)));
+}
+
+// Element-wise product with a packed df factor c = (c0, c1) (each half its
+// own df number): (a.re * c0, a.im * c1).
+__device__ __forceinline__ dfc2 dfc2_mulv(dfc2 a, float2 chi, float2 clo) {
+  const float2 p = mul2(a.hi, chi);
+  const float2 np = mul2(a.hi, f2(-chi.x, -chi.y));  // -p exactly
+  float2 e = fma2(a.hi, chi, np);
+  e = fma2(a.hi, clo, e);
+  e = fma2(a.lo, chi, e);
+  return fast_two_sum2(p, e);
+}
+
+// Multiplication by i: (re, im) -> (-im, re), a swap and a sign.
+__device__ __forceinline__ dfc2 dfc2_swap(dfc2 a) { return dfc2{f2(a.hi.y, a.hi.x), f2(a.lo.y, a.lo.x)}; }
+
+// (cr + i ci) * v for a complex df factor: cr (re, im) + ci (-im, re).
+__device__ __forceinline__ dfc2 dfc2_cmul(dfc2 v, df cr, df ci) {
+  const dfc2 a = dfc2_mulv(v, f2(cr.hi, cr.hi), f2(cr.lo, cr.lo));
+  const dfc2 b = dfc2_mulv(dfc2_swap(v), f2(-ci.hi, ci.hi), f2(-ci.lo, ci.lo));
+  return dfc2_add(a, b);
+}
+
+__device__ __forceinline__ dfc2 dfc2_from_double2(double2 s) {
+  const df r = df_from_double(s.x), i = df_from_double(s.y);
+  return dfc2{f2(r.hi, i.hi), f2(r.lo, i.lo)};
+}
+
+__device__ __forceinline__ double2 dfc2_to_double2(dfc2 a) {
+  return make_double2(df_to_double(df{a.hi.x, a.lo.x}), df_to_double(df{a.hi.y, a.lo.y}));
+}
+
+}  // namespace qs

@@ -125,31 +125,48 @@ void expand(const Reg& r, const GateOp& op, std::vector<VOp>& out) {
 // unscaled H / sqrt(X) / sqrt(Y) leave out (1/sqrt 2, (1+i)/2, and (1-i)/2
 // for conjugated column updates): one at the end of the pass, and one
 // earlier whenever the pending magnitude growth reaches 2^40.
+// The product of e dropped factors, p of them (1+i)/2 and q of them (1-i)/2,
+// is 2^(-e/2) e^{i pi (p-q)/4}; it is formed directly (at most one rounding,
+// in 1/sqrt 2) rather than by e successive multiplications.
+std::complex<double> dropped_factor(int e, int p, int q) {
+  const int k = ((p - q) % 8 + 8) % 8;
+  const double s = std::sqrt(0.5);
+  const double mag = std::ldexp(1.0, -(e / 2));
+  // e^{i pi k / 4} with exact components for even k
+  static const int re_sign[8] = {1, 1, 0, -1, -1, -1, 0, 1};
+  static const int im_sign[8] = {0, 1, 1, 1, 0, -1, -1, -1};
+  const bool odd_e = e & 1, odd_k = k & 1;
+  // |component| of the unit phase is 1 (even k, nonzero) or 1/sqrt 2 (odd k)
+  double c = mag;
+  if (odd_e && odd_k) c *= 0.5;
+  else if (odd_e || odd_k) c *= s;
+  return {re_sign[k] * c, im_sign[k] * c};
+}
+
 void add_scales(std::vector<VOp>& ops) {
   std::vector<VOp> out;
   out.reserve(ops.size() + 2);
-  std::complex<double> f(1.0, 0.0);
-  double growth = 0.0;
+  int e = 0, p = 0, q = 0;
   auto flush_scale = [&] {
-    if (f == std::complex<double>(1.0, 0.0)) return;
+    if (e == 0) return;
+    const std::complex<double> f = dropped_factor(e, p, q);
     VOp s;
     s.kind = FK_SCALE;
     s.c[0] = f.real();
     s.c[1] = f.imag();
     out.push_back(s);
-    f = 1.0;
-    growth = 0.0;
+    e = p = q = 0;
   };
   for (const VOp& v : ops) {
     out.push_back(v);
     if (v.kind == FK_H) {
-      f *= std::sqrt(0.5);
-      growth += 0.5;
+      ++e;
     } else if (v.kind == FK_SX || v.kind == FK_SY) {
-      f *= std::complex<double>(0.5, v.conj ? -0.5 : 0.5);
-      growth += 0.5;
+      ++e;
+      if (v.conj) ++q;
+      else ++p;
     }
-    if (growth >= 40.0) flush_scale();
+    if (e >= 80) flush_scale();  // growth 2^(e/2) stays within the float range
   }
   flush_scale();
   ops.swap(out);
@@ -305,17 +322,19 @@ double vop_flops(const VOp& v, int nq) {
 // in the precision of the kernel's arithmetic.  Plain FP32/FP64 per pair:
 // general 16, H / sqrt(X) / sqrt(Y) 4; per touched amplitude: phase 4,
 // dephasing 2; per quad: depolarising 12; per amplitude: scale 4.
-// Double-float: df add 11, df multiply 7, four-term df dot product 43.
+// Double-float (packed: one instruction covers the real and imaginary
+// parts): complex df add 11, multiply by a df factor 8, complex df product
+// 27; in FP32-lane terms each packed instruction counts twice.
 double vop_alu(const VOp& v, int nq, Arith a) {
   const double dim = std::ldexp(1.0, nq), f = std::ldexp(1.0, -popc(v.cond));
   const bool d = a == Arith::DF;
   static const double plain_pair[5] = {16, 4, 4, 4, 0};
-  static const double df_pair[5] = {172, 44, 44, 44, 0};
+  static const double df_pair[5] = {2 * 130, 2 * 22, 2 * 22, 2 * 22, 0};
   if (v.kind <= FK_X) return dim / 2 * f * (d ? df_pair[v.kind] : plain_pair[v.kind]);
-  if (v.kind == FK_PHASE) return dim * f * (d ? 50 : 4);
-  if (v.kind == FK_SCALE) return dim * (d ? 50 : 4);
-  if (v.kind == FK_DEPH) return dim / 2 * (d ? 14 : 2);
-  if (v.kind == FK_DEPOL) return dim / 4 * (d ? 156 : 12);
+  if (v.kind == FK_PHASE) return dim * f * (d ? 2 * 27 : 4);
+  if (v.kind == FK_SCALE) return dim * (d ? 2 * 27 : 4);
+  if (v.kind == FK_DEPH) return dim / 2 * (d ? 2 * 8 : 2);
+  if (v.kind == FK_DEPOL) return dim / 4 * (d ? 2 * (2 * 27 + 2 * 8) : 12);
   return 0;
 }
 

@@ -163,14 +163,22 @@ struct PlainArith {
 };
 
 // Double-float arithmetic for complex128 storage: each real part is an
-// unevaluated sum hi + lo of two floats (dfloat.cuh), computed on the FP32
-// pipes.
+// unevaluated sum hi + lo of two floats (dfloat.cuh), held packed as
+// hi = (re.hi, im.hi), lo = (re.lo, im.lo) so that the real and imaginary
+// parts go through the paired FP32 instructions together.
 struct DFArith {
   using Store = double2;
-  using Cplx = dfc;
+  using Cplx = dfc2;
   __device__ static df cf(const FOp& op, int e) { return df{op.c.f[e], op.c.f[8 + e]}; }
-  __device__ static Cplx from_store(const Store& s) { return dfc{df_from_double(s.x), df_from_double(s.y)}; }
-  __device__ static Store to_store(const Cplx& c) { return make_double2(df_to_double(c.re), df_to_double(c.im)); }
+  __device__ static Cplx from_store(const Store& s) { return dfc2_from_double2(s); }
+  __device__ static Store to_store(const Cplx& c) { return dfc2_to_double2(c); }
+  // multiply by -i: (re, im) -> (im, -re);  by +i: (re, im) -> (-im, re)
+  __device__ static dfc2 mul_minus_i(const dfc2& a) {
+    return dfc2{f2(a.hi.y, -a.hi.x), f2(a.lo.y, -a.lo.x)};
+  }
+  __device__ static dfc2 mul_plus_i(const dfc2& a) {
+    return dfc2{f2(-a.hi.y, a.hi.x), f2(-a.lo.y, a.lo.x)};
+  }
   template <int K, bool CONJ>
   __device__ static void pair_t(Cplx& x, Cplx& y, const FOp& op) {
     if constexpr (K == PK_GEN) {
@@ -180,43 +188,45 @@ struct DFArith {
         g[e][0] = cf(op, 2 * e);
         g[e][1] = CONJ ? df_neg(cf(op, 2 * e + 1)) : cf(op, 2 * e + 1);
       }
-      const dfc nx = dfc_mac2(g[0][0], g[0][1], x, g[1][0], g[1][1], y);
-      const dfc ny = dfc_mac2(g[2][0], g[2][1], x, g[3][0], g[3][1], y);
+      const dfc2 nx = dfc2_add(dfc2_cmul(x, g[0][0], g[0][1]), dfc2_cmul(y, g[1][0], g[1][1]));
+      const dfc2 ny = dfc2_add(dfc2_cmul(x, g[2][0], g[2][1]), dfc2_cmul(y, g[3][0], g[3][1]));
       x = nx;
       y = ny;
     } else if constexpr (K == PK_H) {  // unscaled
-      const dfc u = dfc_add(x, y), v = dfc_sub(x, y);
+      const dfc2 u = dfc2_add(x, y), v = dfc2_sub(x, y);
       x = u;
       y = v;
     } else if constexpr (K == PK_SX) {  // [[1, -i], [-i, 1]]  (conj: [[1, i], [i, 1]])
-      const dfc u = x;
+      const dfc2 u = x;
       if constexpr (!CONJ) {
-        x = dfc{df_add(u.re, y.im), df_sub(u.im, y.re)};
-        y = dfc{df_add(y.re, u.im), df_sub(y.im, u.re)};
+        x = dfc2_add(u, mul_minus_i(y));
+        y = dfc2_add(y, mul_minus_i(u));
       } else {
-        x = dfc{df_sub(u.re, y.im), df_add(u.im, y.re)};
-        y = dfc{df_sub(y.re, u.im), df_add(y.im, u.re)};
+        x = dfc2_add(u, mul_plus_i(y));
+        y = dfc2_add(y, mul_plus_i(u));
       }
     } else if constexpr (K == PK_SY) {  // [[1, -1], [1, 1]]
-      const dfc u = x;
-      x = dfc_sub(u, y);
-      y = dfc_add(u, y);
+      const dfc2 u = x;
+      x = dfc2_sub(u, y);
+      y = dfc2_add(u, y);
     } else if constexpr (K == PK_X) {
-      const dfc t = x;
+      const dfc2 t = x;
       x = y;
       y = t;
     }
   }
-  __device__ static Cplx phase(const Cplx& v, const FOp& op) { return dfc_mul(v, cf(op, 0), cf(op, 1)); }
-  __device__ static Cplx negate(const Cplx& v) { return dfc{df_neg(v.re), df_neg(v.im)}; }
+  __device__ static Cplx phase(const Cplx& v, const FOp& op) { return dfc2_cmul(v, cf(op, 0), cf(op, 1)); }
+  __device__ static Cplx negate(const Cplx& v) {
+    return dfc2{mul2(v.hi, f2(-1.f, -1.f)), mul2(v.lo, f2(-1.f, -1.f))};
+  }
   __device__ static Cplx scale(const Cplx& v, const FOp& op, int e) {
     const df f = cf(op, e);
-    return dfc{df_mul(v.re, f), df_mul(v.im, f)};
+    return dfc2_mulv(v, f2(f.hi, f.hi), f2(f.lo, f.lo));
   }
   __device__ static Cplx axpby(const Cplx& a, const Cplx& b, const FOp& op) {
     const df keep = cf(op, 0), move = cf(op, 1);
-    return dfc{df_add(df_mul(a.re, keep), df_mul(b.re, move)),
-               df_add(df_mul(a.im, keep), df_mul(b.im, move))};
+    return dfc2_add(dfc2_mulv(a, f2(keep.hi, keep.hi), f2(keep.lo, keep.lo)),
+                    dfc2_mulv(b, f2(move.hi, move.hi), f2(move.lo, move.lo)));
   }
 };
 
