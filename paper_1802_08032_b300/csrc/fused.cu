@@ -123,8 +123,10 @@ void expand(const Reg& r, const GateOp& op, std::vector<VOp>& out) {
 
 // Appends FK_SCALE operations carrying the factors that the engine's
 // unscaled H / sqrt(X) / sqrt(Y) leave out (1/sqrt 2, (1+i)/2, and (1-i)/2
-// for conjugated column updates): one at the end of the pass, and one
-// earlier whenever the pending magnitude growth reaches 2^40.
+// for conjugated column updates).  Every operation is linear, so the factor
+// is carried across the passes of a plan and applied once, in its last
+// pass, or earlier whenever the pending magnitude growth 2^(e/2) reaches the
+// arithmetic's limit (2^40 for float exponents, 2^500 for FP64).
 // The product of e dropped factors, p of them (1+i)/2 and q of them (1-i)/2,
 // is 2^(-e/2) e^{i pi (p-q)/4}; it is formed directly (at most one rounding,
 // in 1/sqrt 2) rather than by e successive multiplications.
@@ -143,10 +145,15 @@ std::complex<double> dropped_factor(int e, int p, int q) {
   return {re_sign[k] * c, im_sign[k] * c};
 }
 
-void add_scales(std::vector<VOp>& ops) {
+struct ScaleState {
+  int e = 0, p = 0, q = 0;
+  int limit = 80;
+};
+
+void add_scales(std::vector<VOp>& ops, ScaleState& st, bool last) {
   std::vector<VOp> out;
   out.reserve(ops.size() + 2);
-  int e = 0, p = 0, q = 0;
+  int &e = st.e, &p = st.p, &q = st.q;
   auto flush_scale = [&] {
     if (e == 0) return;
     const std::complex<double> f = dropped_factor(e, p, q);
@@ -166,9 +173,9 @@ void add_scales(std::vector<VOp>& ops) {
       if (v.conj) ++q;
       else ++p;
     }
-    if (e >= 80) flush_scale();  // growth 2^(e/2) stays within the float range
+    if (e >= st.limit) flush_scale();
   }
-  flush_scale();
+  if (last) flush_scale();
   ops.swap(out);
 }
 
@@ -179,9 +186,12 @@ struct Pass {
 
 int popc(uint64_t x) { return __builtin_popcountll(x); }
 
-std::vector<Pass> plan(const std::vector<VOp>& ops, int nq, int k, int L, int64_t max_ops) {
+std::vector<Pass> plan(const std::vector<VOp>& ops, int nq, int k, int L, int64_t max_ops,
+                       int scale_limit) {
   std::vector<Pass> passes;
   std::vector<VOp> rem = ops;
+  ScaleState scale;
+  scale.limit = scale_limit;
   const uint64_t low = (uint64_t(1) << L) - 1;
   while (!rem.empty()) {
     Pass p;
@@ -205,7 +215,7 @@ std::vector<Pass> plan(const std::vector<VOp>& ops, int nq, int k, int L, int64_
     for (int b = 0; b < nq && popc(tile) < k; ++b) tile |= uint64_t(1) << b;
     for (int b = 0; b < nq; ++b)
       if ((tile >> b) & 1) p.q.push_back(b);
-    add_scales(p.ops);
+    add_scales(p.ops, scale, deferred.empty());
     passes.push_back(std::move(p));
     rem.swap(deferred);
   }
@@ -239,14 +249,27 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
     return m;
   };
 
+  // With FP64 (or double-float) arithmetic a stage boundary costs little
+  // next to the arithmetic, while a phase on a bit that is not a register
+  // bit runs on half-idle lanes; so there the bits a phase conditions on are
+  // made register bits too.
+  const bool phase_in_regs = arith != Arith::F32;
+  auto needed = [&](const VOp& v) {
+    uint32_t need = local_mask(v.xmask());
+    if (phase_in_regs && v.kind == FK_PHASE) {
+      const uint32_t c = local_mask(v.cond);
+      if (popc(c) <= R) need |= c;
+    }
+    return need;
+  };
   size_t i = 0;
   while (i < p.ops.size()) {
-    // grow the stage's register set while the X bits fit in R
+    // grow the stage's register set while the needed bits fit in R
     uint32_t P = 0;
     size_t j = i;
     while (j < p.ops.size()) {
-      const uint32_t need = local_mask(p.ops[j].xmask());
-      if (popc(P | need) > R) break;
+      const uint32_t need = needed(p.ops[j]);
+      if (j > i && popc(P | need) > R) break;
       P |= need;
       ++j;
     }
@@ -289,6 +312,14 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
         for (int j = 0; j < (1 << R); ++j)
           if ((uint32_t(j) & f.rmask) == f.rmask) touch |= 1u << j;
         f.c.u[15] = touch;
+      }
+      if (v.kind == FK_PHASE) {  // touched-set form: generic, all, or one register bit i0
+        f.i1 = PH_MASK;
+        if (f.rmask == 0) f.i1 = PH_ALL;
+        else if (popc(f.rmask) == 1) {
+          f.i1 = PH_BIT;
+          f.i0 = uint8_t(__builtin_ctz(f.rmask));
+        }
       }
       // consecutive sign flips under the same thread / tile condition compose
       // into one (the product of sign operators is their XOR)
@@ -418,7 +449,7 @@ void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, RegPlan& 
   out.vops = int64_t(vops.size());
   const int64_t cap = env.max_fused_ops > 0 ? std::min<int64_t>(env.max_fused_ops, kMaxPassOps)
                                             : kMaxPassOps;
-  const std::vector<Pass> passes = plan(vops, r.nq, k, L, cap);
+  const std::vector<Pass> passes = plan(vops, r.nq, k, L, cap, out.arith == Arith::F64 ? 1000 : 80);
   for (const Pass& p : passes) {
     FPass fp{};
     fp.k = k;

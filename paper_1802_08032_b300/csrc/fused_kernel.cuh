@@ -41,6 +41,10 @@ enum FKind : uint8_t {
 // float exponent range).  The conjugated forms (density-matrix column
 // updates) drop the conjugate factors: [[1, i], [i, 1]] and (1-i)/2.
 
+// FK_PHASE touched-set forms (FOp::i1): the register amplitudes j in the
+// mask c.u[15]; all of them; or those with register bit i0 set.
+enum PhaseForm : uint8_t { PH_MASK = 0, PH_ALL = 1, PH_BIT = 2 };
+
 // Where a single bit of the amplitude index comes from, within a stage.
 enum BitSrc : uint8_t { BS_REG = 0, BS_LOCAL = 1, BS_GLOBAL = 2 };
 
@@ -265,6 +269,37 @@ __device__ __forceinline__ void pair_dispatch(typename A::Cplx (&v)[1 << R], con
   else pair_dispatch_bit<A, R, K, false, MASKED>(v, op.i0, op.rmask, op);
 }
 
+// Phase on the amplitudes with register bit I set: a compile-time set, so no
+// lane issues a predicated-off multiply.
+template <class A, int R, int I>
+__device__ __forceinline__ void phase_on_bit(typename A::Cplx (&v)[1 << R], const FOp& op) {
+#pragma unroll
+  for (int j = 0; j < (1 << R); ++j)
+    if (j & (1 << I)) v[j] = A::phase(v[j], op);
+}
+
+template <class A, int R>
+__device__ __forceinline__ void phase_dispatch(typename A::Cplx (&v)[1 << R], const FOp& op) {
+  if (op.i1 == PH_BIT) {
+    switch (op.i0) {
+      case 0: phase_on_bit<A, R, 0>(v, op); break;
+      case 1: if constexpr (R > 1) phase_on_bit<A, R, 1>(v, op); break;
+      case 2: if constexpr (R > 2) phase_on_bit<A, R, 2>(v, op); break;
+      case 3: if constexpr (R > 3) phase_on_bit<A, R, 3>(v, op); break;
+      case 4: if constexpr (R > 4) phase_on_bit<A, R, 4>(v, op); break;
+      default: break;
+    }
+  } else if (op.i1 == PH_ALL) {
+#pragma unroll
+    for (int j = 0; j < (1 << R); ++j) v[j] = A::phase(v[j], op);
+  } else {
+    const uint32_t touch = op.c.u[15];
+#pragma unroll
+    for (int j = 0; j < (1 << R); ++j)
+      if ((touch >> j) & 1u) v[j] = A::phase(v[j], op);
+  }
+}
+
 template <class A, int R, int I0, int I1>
 __device__ __forceinline__ void depol_on_bits(typename A::Cplx (&v)[1 << R], const FOp& op) {
 #pragma unroll
@@ -328,13 +363,7 @@ __device__ __forceinline__ void apply_op(typename A::Cplx (&v)[1 << R], const FO
     case FK_SX: pair_dispatch<A, R, PK_SX, false>(v, op); break;
     case FK_SY: pair_dispatch<A, R, PK_SY, false>(v, op); break;
     case FK_X: pair_dispatch<A, R, PK_X, true>(v, op); break;
-    case FK_PHASE: {
-      const uint32_t touch = op.c.u[15];
-#pragma unroll
-      for (int j = 0; j < (1 << R); ++j)
-        if ((touch >> j) & 1u) v[j] = A::phase(v[j], op);
-      break;
-    }
+    case FK_PHASE: phase_dispatch<A, R>(v, op); break;
     case FK_SIGN: {
       const uint32_t touch = op.c.u[15];
 #pragma unroll
