@@ -234,6 +234,27 @@ void set_coeffs(FOp& f, const double* c, Arith a) {
   }
 }
 
+// Kernel dispatch code of an encoded op (kind, conjugation, control form,
+// register bit).
+int dispatch_code(const FOp& f) {
+  const bool c = f.conj != 0;
+  switch (f.kind) {
+    case FK_GEN: return (c ? FC_GEN_C : FC_GEN) * 8 + f.i0;
+    case FK_H: return FC_H * 8 + f.i0;         // uncontrolled; conj(H) = H
+    case FK_SX: return (c ? FC_SX_C : FC_SX) * 8 + f.i0;
+    case FK_SY: return FC_SY * 8 + f.i0;       // real
+    case FK_X: return FC_X * 8 + f.i0;
+    case FK_PHASE:
+      if (f.rmask == 0) return FC_PHASE_ALL * 8;
+      if (popc(f.rmask) == 1) return FC_PHASE_BIT * 8 + __builtin_ctz(f.rmask);
+      return FC_PHASE_MASK * 8;
+    case FK_SIGN: return FC_SIGN * 8;
+    case FK_DEPH: return FC_DEPH * 8;
+    case FK_DEPOL: return FC_DEPOL * 8;
+    default: return FC_SCALE * 8;
+  }
+}
+
 // Device-side op encoding for one pass: stages of R register bits.  Stage op
 // ranges are relative to the pass's first op.
 void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fops,
@@ -284,6 +305,7 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
         st.pbits[n++] = uint8_t(b);
       }
     st.op_begin = int32_t(fops.size()) - first;
+    bool sign_seen = false;
     for (size_t o = i; o < j; ++o) {
       const VOp& v = p.ops[o];
       FOp f{};
@@ -294,7 +316,7 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
       for (int b = 0; b < 64; ++b) {
         if (!((v.cond >> b) & 1)) continue;
         if (lpos[b] < 0) f.gmask |= uint64_t(1) << b;
-        else if ((P >> lpos[b]) & 1) f.rmask |= 1u << idx[lpos[b]];
+        else if ((P >> lpos[b]) & 1) f.rmask |= uint8_t(1u << idx[lpos[b]]);
         else f.lmask |= 1u << lpos[b];
       }
       if (v.kind == FK_DEPH) {
@@ -313,14 +335,11 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
           if ((uint32_t(j) & f.rmask) == f.rmask) touch |= 1u << j;
         f.c.u[15] = touch;
       }
-      if (v.kind == FK_PHASE) {  // touched-set form: generic, all, or one register bit i0
-        f.i1 = PH_MASK;
-        if (f.rmask == 0) f.i1 = PH_ALL;
-        else if (popc(f.rmask) == 1) {
-          f.i1 = PH_BIT;
-          f.i0 = uint8_t(__builtin_ctz(f.rmask));
-        }
-      }
+      f.code = uint16_t(dispatch_code(f));
+      if (f.lmask != 0 || f.gmask != 0) f.flags |= FF_COND;
+      if (sign_seen && (v.kind <= FK_X || v.kind == FK_DEPOL)) f.flags |= FF_FLIP;
+      if (v.kind == FK_DEPOL) f.flags |= FF_TWO;
+      if (v.kind == FK_SIGN) sign_seen = true;
       // consecutive sign flips under the same thread / tile condition compose
       // into one (the product of sign operators is their XOR)
       if (v.kind == FK_SIGN && int32_t(fops.size()) - first > st.op_begin) {

@@ -41,12 +41,24 @@ enum FKind : uint8_t {
 // float exponent range).  The conjugated forms (density-matrix column
 // updates) drop the conjugate factors: [[1, i], [i, 1]] and (1-i)/2.
 
-// FK_PHASE touched-set forms (FOp::i1): the register amplitudes j in the
-// mask c.u[15]; all of them; or those with register bit i0 set.
-enum PhaseForm : uint8_t { PH_MASK = 0, PH_ALL = 1, PH_BIT = 2 };
-
 // Where a single bit of the amplitude index comes from, within a stage.
 enum BitSrc : uint8_t { BS_REG = 0, BS_LOCAL = 1, BS_GLOBAL = 2 };
+
+// Kernel dispatch of an operation: code = family * 8 + register bit, so
+// that kind, conjugation and target bit come from one word.  The general
+// matrix and X test register-bit controls per pair (compiling uncontrolled
+// copies of them as well costs the kernel registers it does not have).
+enum FFamily : uint8_t {
+  FC_GEN = 0, FC_GEN_C = 1, FC_H = 2, FC_SX = 3, FC_SX_C = 4, FC_SY = 5, FC_X = 6,
+  FC_PHASE_BIT = 7, FC_PHASE_ALL = 8, FC_PHASE_MASK = 9,
+  FC_SIGN = 10, FC_DEPH = 11, FC_DEPOL = 12, FC_SCALE = 13
+};
+// FOp::flags
+enum : uint8_t {
+  FF_COND = 1,  // lmask or gmask set: a per-thread / per-tile predicate
+  FF_FLIP = 2,  // a sign flip precedes the op in its stage: check pending flips
+  FF_TWO = 4    // the op moves amplitudes along register bits i0 and i1
+};
 
 // One operation as applied in one stage (all masks pre-split by the host).
 // Coefficients (matrix re/im row-major; PHASE cos, sin; DEPH factor; DEPOL
@@ -58,7 +70,9 @@ struct FOp {
   uint8_t conj;     // pair ops: apply conj(G)
   uint8_t i0, i1;   // register-bit indices (pair target; DEPOL row/column)
   uint8_t asrc, apos, bsrc, bpos;  // DEPH bit sources
-  uint32_t rmask;   // condition bits among the register bits (bit i = register bit i)
+  uint16_t code;    // FFamily * 8 + register bit
+  uint8_t flags;    // FF_*
+  uint8_t rmask;    // condition bits among the register bits (bit i = register bit i)
   uint32_t lmask;   // condition bits among the other local bits (local positions)
   uint64_t gmask;   // condition bits outside the tile (global positions)
   union {
@@ -246,29 +260,6 @@ __device__ __forceinline__ void pair_on_bit(typename A::Cplx (&v)[1 << R], uint3
   }
 }
 
-template <class A, int R, int K, bool CONJ, bool MASKED>
-__device__ __forceinline__ void pair_dispatch_bit(typename A::Cplx (&v)[1 << R], int i,
-                                                  uint32_t rmask, const FOp& op) {
-  switch (i) {
-    case 0: pair_on_bit<A, R, K, CONJ, MASKED, 0>(v, rmask, op); break;
-    case 1: if constexpr (R > 1) pair_on_bit<A, R, K, CONJ, MASKED, 1>(v, rmask, op); break;
-    case 2: if constexpr (R > 2) pair_on_bit<A, R, K, CONJ, MASKED, 2>(v, rmask, op); break;
-    case 3: if constexpr (R > 3) pair_on_bit<A, R, K, CONJ, MASKED, 3>(v, rmask, op); break;
-    case 4: if constexpr (R > 4) pair_on_bit<A, R, K, CONJ, MASKED, 4>(v, rmask, op); break;
-    default: break;
-  }
-}
-
-// MASKED: the op may carry control bits among the register bits (only the
-// general matrix and X do; the planner turns a controlled H / sqrt(X) /
-// sqrt(Y) into a general matrix), so the per-pair test is compiled in only
-// where it can be needed.
-template <class A, int R, int K, bool MASKED>
-__device__ __forceinline__ void pair_dispatch(typename A::Cplx (&v)[1 << R], const FOp& op) {
-  if (op.conj) pair_dispatch_bit<A, R, K, true, MASKED>(v, op.i0, op.rmask, op);
-  else pair_dispatch_bit<A, R, K, false, MASKED>(v, op.i0, op.rmask, op);
-}
-
 // Phase on the amplitudes with register bit I set: a compile-time set, so no
 // lane issues a predicated-off multiply.
 template <class A, int R, int I>
@@ -276,28 +267,6 @@ __device__ __forceinline__ void phase_on_bit(typename A::Cplx (&v)[1 << R], cons
 #pragma unroll
   for (int j = 0; j < (1 << R); ++j)
     if (j & (1 << I)) v[j] = A::phase(v[j], op);
-}
-
-template <class A, int R>
-__device__ __forceinline__ void phase_dispatch(typename A::Cplx (&v)[1 << R], const FOp& op) {
-  if (op.i1 == PH_BIT) {
-    switch (op.i0) {
-      case 0: phase_on_bit<A, R, 0>(v, op); break;
-      case 1: if constexpr (R > 1) phase_on_bit<A, R, 1>(v, op); break;
-      case 2: if constexpr (R > 2) phase_on_bit<A, R, 2>(v, op); break;
-      case 3: if constexpr (R > 3) phase_on_bit<A, R, 3>(v, op); break;
-      case 4: if constexpr (R > 4) phase_on_bit<A, R, 4>(v, op); break;
-      default: break;
-    }
-  } else if (op.i1 == PH_ALL) {
-#pragma unroll
-    for (int j = 0; j < (1 << R); ++j) v[j] = A::phase(v[j], op);
-  } else {
-    const uint32_t touch = op.c.u[15];
-#pragma unroll
-    for (int j = 0; j < (1 << R); ++j)
-      if ((touch >> j) & 1u) v[j] = A::phase(v[j], op);
-  }
 }
 
 template <class A, int R, int I0, int I1>
@@ -349,37 +318,57 @@ __device__ __forceinline__ int bit_value(uint8_t src, uint8_t pos, int j, uint32
   return int((tglobal >> pos) & 1u);
 }
 
-// Applies one operation to the thread's 2^R register amplitudes.
-// tlocal: this thread's local index with the register bits zero;
-// tglobal: the tile's global base (tile bits zero).
+// Applies one operation (dispatch code `code`, register controls `rmask`)
+// to the thread's 2^R register amplitudes; sign flips only update the
+// pending mask `flips`.  tlocal: this thread's local index with the register
+// bits zero; tglobal: the tile's global base (tile bits zero).
 template <class A, int R>
-__device__ __forceinline__ void apply_op(typename A::Cplx (&v)[1 << R], const FOp& op,
-                                         uint32_t tlocal, uint64_t tglobal) {
-  if ((tlocal & op.lmask) != op.lmask) return;
-  if ((tglobal & op.gmask) != op.gmask) return;
-  switch (op.kind) {
-    case FK_GEN: pair_dispatch<A, R, PK_GEN, true>(v, op); break;
-    case FK_H: pair_dispatch<A, R, PK_H, false>(v, op); break;
-    case FK_SX: pair_dispatch<A, R, PK_SX, false>(v, op); break;
-    case FK_SY: pair_dispatch<A, R, PK_SY, false>(v, op); break;
-    case FK_X: pair_dispatch<A, R, PK_X, true>(v, op); break;
-    case FK_PHASE: phase_dispatch<A, R>(v, op); break;
-    case FK_SIGN: {
+__device__ __forceinline__ void run_op(typename A::Cplx (&v)[1 << R], const FOp& op, uint32_t code,
+                                       uint32_t rmask, uint32_t tlocal, uint64_t tglobal,
+                                       uint32_t& flips) {
+#define QS_BIT_CASES(FAM, ...)                                                        \
+  case FAM: {                                                                         \
+    switch (code & 7u) {                                                              \
+      case 0: { constexpr int I = 0; __VA_ARGS__; } break;                            \
+      case 1: if constexpr (R > 1) { constexpr int I = 1; __VA_ARGS__; } break;       \
+      case 2: if constexpr (R > 2) { constexpr int I = 2; __VA_ARGS__; } break;       \
+      case 3: if constexpr (R > 3) { constexpr int I = 3; __VA_ARGS__; } break;       \
+      case 4: if constexpr (R > 4) { constexpr int I = 4; __VA_ARGS__; } break;       \
+      default: break;                                                                 \
+    }                                                                                 \
+    break;                                                                            \
+  }
+  switch (code >> 3) {
+    QS_BIT_CASES(FC_GEN, (pair_on_bit<A, R, PK_GEN, false, true, I>(v, rmask, op)))
+    QS_BIT_CASES(FC_GEN_C, (pair_on_bit<A, R, PK_GEN, true, true, I>(v, rmask, op)))
+    QS_BIT_CASES(FC_H, (pair_on_bit<A, R, PK_H, false, false, I>(v, rmask, op)))
+    QS_BIT_CASES(FC_SX, (pair_on_bit<A, R, PK_SX, false, false, I>(v, rmask, op)))
+    QS_BIT_CASES(FC_SX_C, (pair_on_bit<A, R, PK_SX, true, false, I>(v, rmask, op)))
+    QS_BIT_CASES(FC_SY, (pair_on_bit<A, R, PK_SY, false, false, I>(v, rmask, op)))
+    QS_BIT_CASES(FC_X, (pair_on_bit<A, R, PK_X, false, true, I>(v, rmask, op)))
+    QS_BIT_CASES(FC_PHASE_BIT, (phase_on_bit<A, R, I>(v, op)))
+#undef QS_BIT_CASES
+    case FC_PHASE_ALL:
+#pragma unroll
+      for (int j = 0; j < (1 << R); ++j) v[j] = A::phase(v[j], op);
+      break;
+    case FC_PHASE_MASK: {
       const uint32_t touch = op.c.u[15];
 #pragma unroll
       for (int j = 0; j < (1 << R); ++j)
-        if ((touch >> j) & 1u) v[j] = A::negate(v[j]);
+        if ((touch >> j) & 1u) v[j] = A::phase(v[j], op);
       break;
     }
-    case FK_DEPH:
+    case FC_SIGN: flips ^= op.c.u[15]; break;
+    case FC_DEPH:
 #pragma unroll
       for (int j = 0; j < (1 << R); ++j)
         if (bit_value(op.asrc, op.apos, j, tlocal, tglobal) !=
             bit_value(op.bsrc, op.bpos, j, tlocal, tglobal))
           v[j] = A::scale(v[j], op, 0);
       break;
-    case FK_DEPOL: depol_dispatch<A, R>(v, op); break;
-    case FK_SCALE:
+    case FC_DEPOL: depol_dispatch<A, R>(v, op); break;
+    case FC_SCALE:
 #pragma unroll
       for (int j = 0; j < (1 << R); ++j) v[j] = A::phase(v[j], op);
       break;
@@ -539,19 +528,27 @@ __device__ __forceinline__ void process_tile(typename A::Store* __restrict__ g, 
       uint32_t flips = 0;
       for (int o = st.op_begin; o < st.op_end; ++o) {
         const FOp& op = m.ops[o];
-        if (op.kind == FK_SIGN) {
-          if ((tlocal & op.lmask) == op.lmask && (uint64_t(base) & op.gmask) == op.gmask)
-            flips ^= op.c.u[15];
+        // code, flags and rmask share one word; kind, conj, i0, i1 another
+        const uint32_t w = *reinterpret_cast<const uint32_t*>(&op.code);
+        const uint32_t flags = (w >> 16) & 0xFFu;
+        if ((flags & FF_COND) &&
+            ((tlocal & op.lmask) != op.lmask || (uint64_t(base) & op.gmask) != op.gmask))
+          continue;
+        if ((flags & FF_FLIP) && flips) {
+          const uint32_t w0 = *reinterpret_cast<const uint32_t*>(&op);
+          if (depends_on_bit(flips, (w0 >> 16) & 0xFFu) ||
+              ((flags & FF_TWO) && depends_on_bit(flips, w0 >> 24))) {
+#pragma unroll
+            for (int j = 0; j < (1 << R); ++j)
+              if ((flips >> j) & 1u) v[j] = A::negate(v[j]);
+            flips = 0;
+          }
+        }
+        if ((w & 0xFFFFu) == FC_SIGN * 8) {
+          flips ^= op.c.u[15];
           continue;
         }
-        if (flips && (op.kind <= FK_X || op.kind == FK_DEPOL) &&
-            (depends_on_bit(flips, op.i0) || (op.kind == FK_DEPOL && depends_on_bit(flips, op.i1)))) {
-#pragma unroll
-          for (int j = 0; j < (1 << R); ++j)
-            if ((flips >> j) & 1u) v[j] = A::negate(v[j]);
-          flips = 0;
-        }
-        apply_op<A, R>(v, op, tlocal, uint64_t(base));
+        run_op<A, R>(v, op, w & 0xFFFFu, op.rmask, tlocal, uint64_t(base), flips);
       }
       if (flips) {
 #pragma unroll
