@@ -236,22 +236,29 @@ void set_coeffs(FOp& f, const double* c, Arith a) {
 
 // Kernel dispatch code of an encoded op (kind, conjugation, control form,
 // register bit).
+// Slot of the register-bit pair (a, b), a != b < 5 (see FFamily).
+int pair_slot(int a, int b) {
+  const int lo = std::min(a, b), hi = std::max(a, b);
+  return lo * 4 - lo * (lo - 1) / 2 + (hi - lo - 1);
+}
+
 int dispatch_code(const FOp& f) {
   const bool c = f.conj != 0;
+  const int S = kCodeSlots;
   switch (f.kind) {
-    case FK_GEN: return (c ? FC_GEN_C : FC_GEN) * 8 + f.i0;
-    case FK_H: return FC_H * 8 + f.i0;         // uncontrolled; conj(H) = H
-    case FK_SX: return (c ? FC_SX_C : FC_SX) * 8 + f.i0;
-    case FK_SY: return FC_SY * 8 + f.i0;       // real
-    case FK_X: return FC_X * 8 + f.i0;
+    case FK_GEN: return (c ? FC_GEN_C : FC_GEN) * S + f.i0;
+    case FK_H: return FC_H * S + f.i0;         // uncontrolled; conj(H) = H
+    case FK_SX: return (c ? FC_SX_C : FC_SX) * S + f.i0;
+    case FK_SY: return FC_SY * S + f.i0;       // real
+    case FK_X: return FC_X * S + f.i0;
     case FK_PHASE:
-      if (f.rmask == 0) return FC_PHASE_ALL * 8;
-      if (popc(f.rmask) == 1) return FC_PHASE_BIT * 8 + __builtin_ctz(f.rmask);
-      return FC_PHASE_MASK * 8;
-    case FK_SIGN: return FC_SIGN * 8;
-    case FK_DEPH: return FC_DEPH * 8;
-    case FK_DEPOL: return FC_DEPOL * 8;
-    default: return FC_SCALE * 8;
+      if (f.rmask == 0) return FC_PHASE_ALL * S;
+      if (popc(f.rmask) == 1) return FC_PHASE_BIT * S + __builtin_ctz(f.rmask);
+      return FC_PHASE_MASK * S;
+    case FK_SIGN: return FC_SIGN * S;
+    case FK_DEPH: return FC_DEPH * S;
+    case FK_DEPOL: return FC_DEPOL * S + pair_slot(f.i0, f.i1);
+    default: return FC_SCALE * S;
   }
 }
 
@@ -339,12 +346,13 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
       if (f.lmask != 0 || f.gmask != 0) f.flags |= FF_COND;
       if (sign_seen && (v.kind <= FK_X || v.kind == FK_DEPOL)) f.flags |= FF_FLIP;
       if (v.kind == FK_DEPOL) f.flags |= FF_TWO;
-      if (v.kind == FK_SIGN) sign_seen = true;
-      // consecutive sign flips under the same thread / tile condition compose
-      // into one (the product of sign operators is their XOR)
-      if (v.kind == FK_SIGN && int32_t(fops.size()) - first > st.op_begin) {
+      const bool deferred_sign = v.kind == FK_SIGN;
+      if (deferred_sign) sign_seen = true;
+      // consecutive pending sign flips under the same thread / tile condition
+      // compose into one (the product of sign operators is their XOR)
+      if (deferred_sign && int32_t(fops.size()) - first > st.op_begin) {
         FOp& prev = fops.back();
-        if (prev.kind == FK_SIGN && prev.lmask == f.lmask && prev.gmask == f.gmask) {
+        if (prev.code == f.code && prev.lmask == f.lmask && prev.gmask == f.gmask) {
           prev.c.u[15] ^= f.c.u[15];
           continue;
         }

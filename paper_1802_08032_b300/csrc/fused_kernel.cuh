@@ -44,15 +44,19 @@ enum FKind : uint8_t {
 // Where a single bit of the amplitude index comes from, within a stage.
 enum BitSrc : uint8_t { BS_REG = 0, BS_LOCAL = 1, BS_GLOBAL = 2 };
 
-// Kernel dispatch of an operation: code = family * 8 + register bit, so
-// that kind, conjugation and target bit come from one word.  The general
+// Kernel dispatch of an operation: code = family * 16 + slot, where the slot
+// is the target register bit, or the index of a register-bit pair (a, b),
+// a < b, in the order (0,1) (0,2) (0,3) (0,4) (1,2) (1,3) (1,4) (2,3) (2,4)
+// (3,4); so kind, conjugation and bits come from one word.  The general
 // matrix and X test register-bit controls per pair (compiling uncontrolled
 // copies of them as well costs the kernel registers it does not have).
+// Sign flips only update a pending mask (see process_tile).
 enum FFamily : uint8_t {
   FC_GEN = 0, FC_GEN_C = 1, FC_H = 2, FC_SX = 3, FC_SX_C = 4, FC_SY = 5, FC_X = 6,
   FC_PHASE_BIT = 7, FC_PHASE_ALL = 8, FC_PHASE_MASK = 9,
   FC_SIGN = 10, FC_DEPH = 11, FC_DEPOL = 12, FC_SCALE = 13
 };
+constexpr int kCodeSlots = 16;
 // FOp::flags
 enum : uint8_t {
   FF_COND = 1,  // lmask or gmask set: a per-thread / per-tile predicate
@@ -70,7 +74,7 @@ struct FOp {
   uint8_t conj;     // pair ops: apply conj(G)
   uint8_t i0, i1;   // register-bit indices (pair target; DEPOL row/column)
   uint8_t asrc, apos, bsrc, bpos;  // DEPH bit sources
-  uint16_t code;    // FFamily * 8 + register bit
+  uint16_t code;    // FFamily * kCodeSlots + slot
   uint8_t flags;    // FF_*
   uint8_t rmask;    // condition bits among the register bits (bit i = register bit i)
   uint32_t lmask;   // condition bits among the other local bits (local positions)
@@ -130,6 +134,25 @@ struct PlainArith {
         g.im[e] = cf(op, 2 * e + 1);
       }
       pair_apply<R, K, CONJ>(x, y, g);
+    } else if constexpr (sizeof(R) == 4 && (K == PK_H || K == PK_SX || K == PK_SY)) {
+      // FP32: each real butterfly (a, b) -> (a + b, b - a) or (a - b, a + b)
+      // is computed in place, the second output from the first by one FMA
+      // with an exact factor 2 (b - a = 2b - (a + b)).  Both outputs then
+      // stay in the inputs' registers, which saves a register move per
+      // output; the second output carries one extra rounding of |a + b|.
+      if constexpr (K == PK_H) {  // unscaled: (x + y, x - y)
+        x.x = x.x + y.x; y.x = fmaf(y.x, -2.f, x.x);
+        x.y = x.y + y.y; y.y = fmaf(y.y, -2.f, x.y);
+      } else if constexpr (K == PK_SY) {  // [[1, -1], [1, 1]]: (x - y, x + y)
+        x.x = x.x - y.x; y.x = fmaf(y.x, 2.f, x.x);
+        x.y = x.y - y.y; y.y = fmaf(y.y, 2.f, x.y);
+      } else if constexpr (!CONJ) {  // [[1, -i], [-i, 1]]
+        x.x = x.x + y.y; y.y = fmaf(y.y, 2.f, -x.x);   // y.im - x.re
+        x.y = x.y - y.x; y.x = fmaf(y.x, 2.f, x.y);    // y.re + x.im
+      } else {  // [[1, i], [i, 1]]
+        x.x = x.x - y.y; y.y = fmaf(y.y, 2.f, x.x);    // y.im + x.re
+        x.y = x.y + y.x; y.x = fmaf(y.x, 2.f, -x.y);   // y.re - x.im
+      }
     } else if constexpr (K == PK_H) {  // unscaled: (x + y, x - y)
       const Cplx u = x;
       x.x = u.x + y.x; x.y = u.y + y.y;
@@ -158,10 +181,18 @@ struct PlainArith {
     w.y = s * v.x + c * v.y;
     return w;
   }
+  // FP64: flip the sign bits (integer pipe; the FP64 pipe is the bottleneck).
+  // FP32: multiply by -1 (exact; full-rate FMA pipe instead of the busier
+  // integer pipe).
   __device__ static Cplx negate(const Cplx& v) {
     Cplx w;
-    w.x = neg_bits(v.x);
-    w.y = neg_bits(v.y);
+    if constexpr (sizeof(R) == 4) {
+      w.x = __fmul_rn(v.x, -1.f);
+      w.y = __fmul_rn(v.y, -1.f);
+    } else {
+      w.x = neg_bits(v.x);
+      w.y = neg_bits(v.y);
+    }
     return w;
   }
   __device__ static Cplx scale(const Cplx& v, const FOp& op, int e) {
@@ -283,21 +314,6 @@ __device__ __forceinline__ void depol_on_bits(typename A::Cplx (&v)[1 << R], con
   }
 }
 
-template <class A, int R>
-__device__ __forceinline__ void depol_dispatch(typename A::Cplx (&v)[1 << R], const FOp& op) {
-  const int lo = op.i0 < op.i1 ? op.i0 : op.i1, hi = op.i0 < op.i1 ? op.i1 : op.i0;
-  switch (lo * 8 + hi) {
-#define QS_DEPOL_CASE(a, b) \
-  case a * 8 + b: if constexpr (R > b) depol_on_bits<A, R, a, b>(v, op); break;
-    QS_DEPOL_CASE(0, 1) QS_DEPOL_CASE(0, 2) QS_DEPOL_CASE(0, 3) QS_DEPOL_CASE(0, 4)
-    QS_DEPOL_CASE(1, 2) QS_DEPOL_CASE(1, 3) QS_DEPOL_CASE(1, 4)
-    QS_DEPOL_CASE(2, 3) QS_DEPOL_CASE(2, 4)
-    QS_DEPOL_CASE(3, 4)
-#undef QS_DEPOL_CASE
-    default: break;
-  }
-}
-
 // Mask of register indices j with bit i clear, as a bit set over j (R <= 5).
 __constant__ uint32_t c_bit_clear[5] = {0x55555555u, 0x33333333u, 0x0F0F0F0Fu, 0x00FF00FFu,
                                         0x0000FFFFu};
@@ -326,19 +342,22 @@ template <class A, int R>
 __device__ __forceinline__ void run_op(typename A::Cplx (&v)[1 << R], const FOp& op, uint32_t code,
                                        uint32_t rmask, uint32_t tlocal, uint64_t tglobal,
                                        uint32_t& flips) {
-#define QS_BIT_CASES(FAM, ...)                                                        \
-  case FAM: {                                                                         \
-    switch (code & 7u) {                                                              \
-      case 0: { constexpr int I = 0; __VA_ARGS__; } break;                            \
-      case 1: if constexpr (R > 1) { constexpr int I = 1; __VA_ARGS__; } break;       \
-      case 2: if constexpr (R > 2) { constexpr int I = 2; __VA_ARGS__; } break;       \
-      case 3: if constexpr (R > 3) { constexpr int I = 3; __VA_ARGS__; } break;       \
-      case 4: if constexpr (R > 4) { constexpr int I = 4; __VA_ARGS__; } break;       \
-      default: break;                                                                 \
-    }                                                                                 \
-    break;                                                                            \
-  }
-  switch (code >> 3) {
+#define QS_BIT_CASE(FAM, S, ...) \
+  case FAM * kCodeSlots + S: if constexpr (R > S) { constexpr int I = S; __VA_ARGS__; } break;
+#define QS_BIT_CASES(FAM, ...)                                                              \
+  QS_BIT_CASE(FAM, 0, __VA_ARGS__) QS_BIT_CASE(FAM, 1, __VA_ARGS__) QS_BIT_CASE(FAM, 2, __VA_ARGS__) \
+  QS_BIT_CASE(FAM, 3, __VA_ARGS__) QS_BIT_CASE(FAM, 4, __VA_ARGS__)
+#define QS_PAIR_CASE(FAM, S, A_, B_, ...)                                   \
+  case FAM * kCodeSlots + S:                                                 \
+    if constexpr (R > B_) { constexpr int IA = A_, IB = B_; __VA_ARGS__; } \
+    break;
+#define QS_PAIR_CASES(FAM, ...)                                                                   \
+  QS_PAIR_CASE(FAM, 0, 0, 1, __VA_ARGS__) QS_PAIR_CASE(FAM, 1, 0, 2, __VA_ARGS__)                 \
+  QS_PAIR_CASE(FAM, 2, 0, 3, __VA_ARGS__) QS_PAIR_CASE(FAM, 3, 0, 4, __VA_ARGS__)                 \
+  QS_PAIR_CASE(FAM, 4, 1, 2, __VA_ARGS__) QS_PAIR_CASE(FAM, 5, 1, 3, __VA_ARGS__)                 \
+  QS_PAIR_CASE(FAM, 6, 1, 4, __VA_ARGS__) QS_PAIR_CASE(FAM, 7, 2, 3, __VA_ARGS__)                 \
+  QS_PAIR_CASE(FAM, 8, 2, 4, __VA_ARGS__) QS_PAIR_CASE(FAM, 9, 3, 4, __VA_ARGS__)
+  switch (code) {
     QS_BIT_CASES(FC_GEN, (pair_on_bit<A, R, PK_GEN, false, true, I>(v, rmask, op)))
     QS_BIT_CASES(FC_GEN_C, (pair_on_bit<A, R, PK_GEN, true, true, I>(v, rmask, op)))
     QS_BIT_CASES(FC_H, (pair_on_bit<A, R, PK_H, false, false, I>(v, rmask, op)))
@@ -347,28 +366,31 @@ __device__ __forceinline__ void run_op(typename A::Cplx (&v)[1 << R], const FOp&
     QS_BIT_CASES(FC_SY, (pair_on_bit<A, R, PK_SY, false, false, I>(v, rmask, op)))
     QS_BIT_CASES(FC_X, (pair_on_bit<A, R, PK_X, false, true, I>(v, rmask, op)))
     QS_BIT_CASES(FC_PHASE_BIT, (phase_on_bit<A, R, I>(v, op)))
+    QS_PAIR_CASES(FC_DEPOL, (depol_on_bits<A, R, IA, IB>(v, op)))
+#undef QS_PAIR_CASES
+#undef QS_PAIR_CASE
 #undef QS_BIT_CASES
-    case FC_PHASE_ALL:
+#undef QS_BIT_CASE
+    case FC_PHASE_ALL * kCodeSlots:
 #pragma unroll
       for (int j = 0; j < (1 << R); ++j) v[j] = A::phase(v[j], op);
       break;
-    case FC_PHASE_MASK: {
+    case FC_PHASE_MASK * kCodeSlots: {
       const uint32_t touch = op.c.u[15];
 #pragma unroll
       for (int j = 0; j < (1 << R); ++j)
         if ((touch >> j) & 1u) v[j] = A::phase(v[j], op);
       break;
     }
-    case FC_SIGN: flips ^= op.c.u[15]; break;
-    case FC_DEPH:
+    case FC_SIGN * kCodeSlots: flips ^= op.c.u[15]; break;
+    case FC_DEPH * kCodeSlots:
 #pragma unroll
       for (int j = 0; j < (1 << R); ++j)
         if (bit_value(op.asrc, op.apos, j, tlocal, tglobal) !=
             bit_value(op.bsrc, op.bpos, j, tlocal, tglobal))
           v[j] = A::scale(v[j], op, 0);
       break;
-    case FC_DEPOL: depol_dispatch<A, R>(v, op); break;
-    case FC_SCALE:
+    case FC_SCALE * kCodeSlots:
 #pragma unroll
       for (int j = 0; j < (1 << R); ++j) v[j] = A::phase(v[j], op);
       break;
@@ -526,10 +548,14 @@ __device__ __forceinline__ void process_tile(typename A::Store* __restrict__ g, 
       // as a per-thread mask over the register amplitudes and applied only
       // before an op they do not commute with, or at the end of the stage.
       uint32_t flips = 0;
-      for (int o = st.op_begin; o < st.op_end; ++o) {
+      // code, flags and rmask share one word (read one op ahead); kind,
+      // conj, i0, i1 another
+      const int oe = st.op_end;
+      uint32_t wnext = st.op_begin < oe ? *reinterpret_cast<const uint32_t*>(&m.ops[st.op_begin].code) : 0u;
+      for (int o = st.op_begin; o < oe; ++o) {
         const FOp& op = m.ops[o];
-        // code, flags and rmask share one word; kind, conj, i0, i1 another
-        const uint32_t w = *reinterpret_cast<const uint32_t*>(&op.code);
+        const uint32_t w = wnext;
+        wnext = o + 1 < oe ? *reinterpret_cast<const uint32_t*>(&m.ops[o + 1].code) : 0u;
         const uint32_t flags = (w >> 16) & 0xFFu;
         if ((flags & FF_COND) &&
             ((tlocal & op.lmask) != op.lmask || (uint64_t(base) & op.gmask) != op.gmask))
@@ -544,7 +570,7 @@ __device__ __forceinline__ void process_tile(typename A::Store* __restrict__ g, 
             flips = 0;
           }
         }
-        if ((w & 0xFFFFu) == FC_SIGN * 8) {
+        if ((w & 0xFFFFu) == FC_SIGN * kCodeSlots) {
           flips ^= op.c.u[15];
           continue;
         }
