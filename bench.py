@@ -383,23 +383,35 @@ def variants(Q, env, torch, stream):
         return run_variant
 
     def sweep():
-        # single-gate passes (fusion off), algorithmic GB/s by target bit
+        # single-gate passes (fusion off), GB/s by target bit.  "GBps" counts
+        # the algorithmic bytes (touched amplitudes read + written); "sector"
+        # counts the least DRAM traffic at 32-byte sector granularity (a
+        # sector is moved when any of its amplitudes is touched), which is
+        # the whole vector for diagonal ops on the lowest bits.
         Q.setEnvOption(env, "fusion", 0)
         res = {}
         try:
             for prec in (64, 128):
                 reg = Q.createQureg(30, prec, env)
                 S = 16 if prec == 128 else 8
+                lg = (32 // S).bit_length() - 1   # amplitude-index bits inside a sector
                 try:
-                    for name, fn, frac in (
-                            ("H", lambda t: Q.hadamard(reg, t), 1.0),
-                            ("T", lambda t: Q.tGate(reg, t), 0.5),
-                            ("CZ", lambda t: Q.controlledPhaseFlip(reg, t, (t + 1) % 30), 0.25)):
-                        row = []
+                    for name, fn, cond in (
+                            ("H", lambda t: Q.hadamard(reg, t), lambda t: 0),
+                            ("T", lambda t: Q.tGate(reg, t), lambda t: 1 << t),
+                            ("CZ", lambda t: Q.controlledPhaseFlip(reg, t, (t + 1) % 30),
+                             lambda t: (1 << t) | (1 << ((t + 1) % 30)))):
+                        row, srow = [], []
                         for t in range(30):
                             ms = timed(torch, stream, lambda: fn(t), 2)
+                            c = cond(t)
+                            frac = 2.0 ** -bin(c).count("1")
+                            sfrac = 2.0 ** -bin(c >> lg).count("1")
                             row.append(round(2 * frac * (1 << 30) * S / ms / 1e6, 1))
+                            srow.append(round(2 * sfrac * (1 << 30) * S / ms / 1e6, 1))
                         res[f"{name}_c{prec}_GBps_by_target"] = row
+                        if name != "H":
+                            res[f"{name}_c{prec}_sector_GBps_by_target"] = srow
                 finally:
                     Q.destroyQureg(reg)
         finally:
