@@ -58,6 +58,8 @@ def parse():
                     help="complex128 arithmetic of fused passes")
     ap.add_argument("--qubits", type=int, default=30)
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--variants", default="",
+                    help="comma-separated variant names to run (default: all)")
     ap.add_argument("--cpu-gates", type=int, default=10,
                     help="gates in the bounded CPU-oracle sample")
     return ap.parse_args()
@@ -331,7 +333,8 @@ def main():
     }
     Q.destroyQureg(q)
     if rank == 0 and world == 1 and not args.no_variants:
-        line["variants"] = variants(Q, env, torch, stream)
+        line["variants"] = variants(Q, env, torch, stream,
+                                    [v for v in args.variants.split(",") if v])
     if rank == 0 and world == 1:
         try:
             line["cpu_baseline"] = cpu_oracle_sample(n, ops, args.cpu_gates)
@@ -357,7 +360,7 @@ def timed(torch, stream, fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def variants(Q, env, torch, stream):
+def variants(Q, env, torch, stream, only=()):
     """Other configurations of the same metric, measured outside the timed
     region: complex64 and double-float complex128 at 30 qubits, the 14-qubit
     noisy density matrix, and single-gate pass bandwidth by target bit."""
@@ -439,6 +442,8 @@ def variants(Q, env, torch, stream):
                      ("batch4096_c64", lambda: batch_variant(Q, env, torch, stream)),
                      ("serving", lambda: serve_sweep(Q, env, [10, 100], 60)),
                      ("multi_target_passes", lambda: multi_sweep(Q, env, torch, stream))):
+        if only and name not in only:
+            continue
         try:
             out[name] = fn()
         except Exception as e:

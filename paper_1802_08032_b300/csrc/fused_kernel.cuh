@@ -103,6 +103,8 @@ struct FPass {
   uint8_t q[24];               // tile qubits, ascending; q[i] = i for i < L
 };
 
+static_assert(sizeof(FPass) % 8 == 0 && sizeof(FPass) / 8 <= 256, "FPass word copy");
+
 // One unit of a batched launch: tile `tile` of pass `pass`.
 struct BItem {
   int32_t pass;
@@ -407,6 +409,12 @@ __host__ __device__ inline size_t fused_smem_bytes(int k, int L, int nops, int n
 
 // ------------------------------------------------------------------ kernel
 constexpr int kFusedThreads = 256;
+// Independent 16-byte global loads in flight per thread when a tile is
+// loaded: a 2^k tile over 256 threads is 16 of them, so the single-register
+// kernel requests the whole tile in one round trip (the register amplitudes
+// are not live yet).  The batched kernel, which holds more state, keeps 8.
+template <bool GENERAL>
+__host__ __device__ constexpr int load_depth() { return GENERAL ? 8 : 16; }
 
 // Shared-memory layout of a pass: tile, chunk offsets, op list, stage list.
 template <class A>
@@ -484,30 +492,30 @@ __device__ __forceinline__ void process_tile(typename A::Store* __restrict__ g, 
     const int npair = ntile >> 1;
     const float4* g4 = reinterpret_cast<const float4*>(g);
     float4* t4 = reinterpret_cast<float4*>(m.tile);
-    for (int e0 = threadIdx.x; e0 < npair; e0 += blockDim.x * 8) {
-      float4 t[8];
+    for (int e0 = threadIdx.x; e0 < npair; e0 += blockDim.x * load_depth<GENERAL>()) {
+      float4 t[load_depth<GENERAL>()];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < load_depth<GENERAL>(); ++u) {
         const int l = 2 * (e0 + u * blockDim.x);
         if (!GENERAL || l < ntile) t[u] = g4[(base + m.choff[l >> L] + (l & lmask_low)) >> 1];
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < load_depth<GENERAL>(); ++u) {
         const int e = e0 + u * blockDim.x;
         if (!GENERAL || e < npair) t4[e] = t[u];
       }
     }
   } else {
-    // load: 8 independent loads in flight per thread
-    for (int l0 = threadIdx.x; l0 < ntile; l0 += blockDim.x * 8) {
-      Store t[8];
+    // load: load_depth<GENERAL>() independent loads in flight per thread
+    for (int l0 = threadIdx.x; l0 < ntile; l0 += blockDim.x * load_depth<GENERAL>()) {
+      Store t[load_depth<GENERAL>()];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < load_depth<GENERAL>(); ++u) {
         const int l = l0 + u * blockDim.x;
         if (!GENERAL || l < ntile) t[u] = g[base + m.choff[l >> L] + (l & lmask_low)];
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < load_depth<GENERAL>(); ++u) {
         const int l = l0 + u * blockDim.x;
         if (!GENERAL || l < ntile) m.tile[l] = A::from_store(t[u]);
       }
@@ -637,18 +645,24 @@ __global__ void __launch_bounds__(kFusedThreads, 2)
                   const FOp* __restrict__ ops, const FStage* __restrict__ stages, int kmax, int Lmin,
                   int opmax) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  // The current pass's descriptor lives in shared memory (uniform per CTA;
+  // its qubit list is indexed at run time, which in registers would force
+  // the whole descriptor onto the stack).
+  __shared__ FPass sP;
   PassSmem<A> m = pass_smem<A>(smem_raw, kmax, Lmin, opmax);
   int cur = -1;
-  FPass P;
   for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
     const BItem it = items[i];
     if (it.pass != cur) {
       cur = it.pass;
-      P = passes[cur];
-      load_pass<A>(P, ops, stages, m);
+      if (threadIdx.x < sizeof(FPass) / 8)
+        reinterpret_cast<uint64_t*>(&sP)[threadIdx.x] =
+            reinterpret_cast<const uint64_t*>(passes + cur)[threadIdx.x];
+      __syncthreads();
+      load_pass<A>(sP, ops, stages, m);
       __syncthreads();
     }
-    process_tile<A, R, true>(static_cast<typename A::Store*>(P.amps), P, it.tile, m);
+    process_tile<A, R, true>(static_cast<typename A::Store*>(sP.amps), sP, it.tile, m);
   }
 }
 
