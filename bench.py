@@ -169,8 +169,29 @@ def run_reference(args):
                                    "circuit (bounded CPU sample)", "qubits": n},
             "cpu_baseline": {"value": v, "unit": "gates/s", "cores": r["cores"], "kind": "oracle",
                              "sample": r["sample"]},
-            "e2e": {"value": v, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": v, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "thread_scaling": oracle_thread_scaling(n - 4, C.workload_30q(n - 4), args.cpu_gates)}
     print(json.dumps(line), flush=True)
+
+
+def oracle_thread_scaling(n, ops, ngates):
+    """CPU-side context in the manner of the paper's thread-scaling figure
+    (Sec. III): the same bounded gate sample on an n-qubit state with 1, 2,
+    4, ... host threads up to all of them; gates/s and speed-up over one
+    thread."""
+    from oracle import oracle as O
+    full = O.num_threads()
+    counts = sorted({t for t in (1, 2, 4, 8, 16, 32, 64, 128) if t < full} | {full})
+    rows = []
+    try:
+        for t in counts:
+            O.set_num_threads(t)
+            rows.append({"threads": t, "gates_per_s": cpu_oracle_sample(n, ops, ngates)["value"]})
+    finally:
+        O.set_num_threads(full)
+    for r in rows:
+        r["speedup"] = r["gates_per_s"] / rows[0]["gates_per_s"]
+    return {"qubits": n, "gates": ngates, "rows": rows}
 
 
 def job_max(x, world, device):
@@ -385,40 +406,49 @@ def variants(Q, env, torch, stream, only=()):
             return {"gates_per_s": len(ops) / ms * 1e3, "ms_per_circuit": ms}
         return run_variant
 
-    def sweep():
-        # single-gate passes (fusion off), GB/s by target bit.  "GBps" counts
-        # the algorithmic bytes (touched amplitudes read + written); "sector"
-        # counts the least DRAM traffic at 32-byte sector granularity (a
-        # sector is moved when any of its amplitudes is touched), which is
-        # the whole vector for diagonal ops on the lowest bits.
+    def sweep(n, targets):
+        # single-gate passes (fusion off) on an n-qubit register, GB/s by
+        # target bit.  "GBps" counts the algorithmic bytes (touched amplitudes
+        # read + written); "sector" counts the least DRAM traffic at 32-byte
+        # sector granularity (a sector is moved when any of its amplitudes is
+        # touched), which is the whole vector for diagonal ops on the lowest
+        # bits.  U is compactUnitary with fixed Haar-random (alpha, beta);
+        # MCPF flips the sign where qubits t, t+1, t+2 are all 1.
         Q.setEnvOption(env, "fusion", 0)
+        ab = C.haar_alpha_beta(C.SplitMix64(33))
         res = {}
         try:
             for prec in (64, 128):
-                reg = Q.createQureg(30, prec, env)
+                reg = Q.createQureg(n, prec, env)
                 S = 16 if prec == 128 else 8
                 lg = (32 // S).bit_length() - 1   # amplitude-index bits inside a sector
+                kinds = (
+                    ("H", lambda t: Q.hadamard(reg, t), lambda t: 0),
+                    ("U", lambda t: Q.compactUnitary(reg, t, complex(ab[0], ab[1]),
+                                                     complex(ab[2], ab[3])), lambda t: 0),
+                    ("T", lambda t: Q.tGate(reg, t), lambda t: 1 << t),
+                    ("CZ", lambda t: Q.controlledPhaseFlip(reg, t, (t + 1) % n),
+                     lambda t: (1 << t) | (1 << ((t + 1) % n))),
+                    ("MCPF", lambda t: Q.multiControlledPhaseFlip(reg, [t, (t + 1) % n, (t + 2) % n]),
+                     lambda t: (1 << t) | (1 << ((t + 1) % n)) | (1 << ((t + 2) % n))))
                 try:
-                    for name, fn, cond in (
-                            ("H", lambda t: Q.hadamard(reg, t), lambda t: 0),
-                            ("T", lambda t: Q.tGate(reg, t), lambda t: 1 << t),
-                            ("CZ", lambda t: Q.controlledPhaseFlip(reg, t, (t + 1) % 30),
-                             lambda t: (1 << t) | (1 << ((t + 1) % 30)))):
+                    for name, fn, cond in kinds:
                         row, srow = [], []
-                        for t in range(30):
+                        for t in targets:
                             ms = timed(torch, stream, lambda: fn(t), 2)
                             c = cond(t)
                             frac = 2.0 ** -bin(c).count("1")
                             sfrac = 2.0 ** -bin(c >> lg).count("1")
-                            row.append(round(2 * frac * (1 << 30) * S / ms / 1e6, 1))
-                            srow.append(round(2 * sfrac * (1 << 30) * S / ms / 1e6, 1))
+                            row.append(round(2 * frac * (1 << n) * S / ms / 1e6, 1))
+                            srow.append(round(2 * sfrac * (1 << n) * S / ms / 1e6, 1))
                         res[f"{name}_c{prec}_GBps_by_target"] = row
-                        if name != "H":
+                        if cond(1) != 0:
                             res[f"{name}_c{prec}_sector_GBps_by_target"] = srow
                 finally:
                     Q.destroyQureg(reg)
         finally:
             Q.setEnvOption(env, "fusion", 1)
+        res["targets"] = list(targets)
         return res
 
     def dm14():
@@ -438,9 +468,12 @@ def variants(Q, env, torch, stream, only=()):
         return {"ops_per_s": len(dops) / ms * 1e3, "ms_per_circuit": ms, "ops": len(dops)}
 
     for name, fn in (("sv30_c64", sv(64, 0)), ("sv30_c128_df", sv(128, 1)),
-                     ("single_gate_sweep", sweep), ("dm14_c128", dm14),
+                     ("single_gate_sweep", lambda: sweep(30, range(30))),
+                     ("single_gate_sweep_33q", lambda: sweep(33, [0, 1, 2, 4, 8, 16, 24, 32])),
+                     ("dm14_c128", dm14),
                      ("batch4096_c64", lambda: batch_variant(Q, env, torch, stream)),
-                     ("serving", lambda: serve_sweep(Q, env, [10, 100], 60)),
+                     ("serving", lambda: serve_sweep(Q, env, [10, 30, 100, 300, 1000, 2000], 60,
+                                                     baseline_rates=(10, 100))),
                      ("multi_target_passes", lambda: multi_sweep(Q, env, torch, stream))):
         if only and name not in only:
             continue
@@ -543,9 +576,10 @@ def multi_sweep(Q, env, torch, stream, n=30):
 def serve_trace(rate, count, seed0=5000, arrival_seed=55, max_sv=28, max_dm=13):
     """Serving workload: Poisson arrivals at `rate` req/s (exponential gaps
     from their own SplitMix64 stream), request i seeded 5000 + i: type
-    uniform over {state vector c64, state vector c128, density matrix c128};
+    uniform over {state vector c64, state vector c128, density matrix};
     state vectors n ~ U{10..28}, density matrices N ~ U{6..13} with
-    dephasing 0.01 after every gate; depth ~ U{10..50}."""
+    dephasing 0.01 after every gate; depth ~ U{10..50}.  A density matrix's
+    precision (complex64 or complex128, uniform) is the request's last draw."""
     import math
     arr = C.SplitMix64(arrival_seed)
     t, trace = 0.0, []
@@ -557,7 +591,7 @@ def serve_trace(rate, count, seed0=5000, arrival_seed=55, max_sv=28, max_dm=13):
         if kind == 2:
             N = 6 + rng.below(max_dm - 5)
             ops = C.with_noise(C.random_circuit(N, depth, seed0 + i), 0.01, 0.0)
-            trace.append((t, True, N, 128, ops))
+            trace.append((t, True, N, 64 if rng.below(2) == 0 else 128, ops))
         else:
             n = 10 + rng.below(max_sv - 9)
             trace.append((t, False, n, 64 if kind == 0 else 128,
@@ -592,12 +626,12 @@ def run_trace(Q, env, trace, slots, fusion, force_c128=False):
             "slots_used": len({r["slot"] for r in res})}
 
 
-def serve_sweep(Q, env, rates, per_rate, slots=16, baseline=True):
+def serve_sweep(Q, env, rates, per_rate, slots=16, baseline_rates=()):
     out = {}
     for rate in rates:
         trace = serve_trace(rate, per_rate)
         row = {"served": run_trace(Q, env, trace, slots, 1)}
-        if baseline:
+        if rate in baseline_rates:
             row["plain_c128_one_at_a_time"] = run_trace(Q, env, trace, 1, 0, force_c128=True)
         out[f"{rate}_req_per_s"] = row
     return out

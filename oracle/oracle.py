@@ -106,7 +106,7 @@ def lib():
             "orc_purity_dm": [P, I],
             "orc_collapse_sv": [P, I, I, I, D], "orc_collapse_dm": [P, I, I, I, D],
             "orc_apply_multi": [P, I, P, I, U64, P], "orc_apply_dm_multi": [P, I, P, I, U64, P],
-            "orc_num_threads": [],
+            "orc_num_threads": [], "orc_set_num_threads": [I],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -150,7 +150,16 @@ class State:
             assert self.a.size == 1 << self.nq
 
     # -- gates -------------------------------------------------------------
+    def _check_qubits(self, qs):
+        # the C core does no bounds checks: reject bad qubits here
+        for q in qs:
+            if not 0 <= int(q) < self.n:
+                raise ValueError(f"oracle: qubit {q} outside an {self.n}-qubit register")
+        if len(set(int(q) for q in qs)) != len(qs):
+            raise ValueError(f"oracle: repeated qubit in {tuple(qs)}")
+
     def gate(self, q, g, controls=()):
+        self._check_qubits((q,) + tuple(controls))
         g = _cmat(g)
         if self.density:
             lib().orc_apply_dm_gate(_ptr(self.a), self.n, q, _mask(controls), g.ctypes.data)
@@ -158,6 +167,7 @@ class State:
             lib().orc_apply_gate(_ptr(self.a), self.n, q, _mask(controls), g.ctypes.data)
 
     def phase_flip(self, qubits):
+        self._check_qubits(tuple(qubits))
         if self.density:
             lib().orc_dm_phase_flip(_ptr(self.a), self.n, _mask(qubits))
         else:
@@ -166,6 +176,7 @@ class State:
     def multi(self, targets, U, controls=()):
         """Dense 2^m x 2^m gate U on `targets` (bit k of U's index is
         targets[k]), restricted to the controls."""
+        self._check_qubits(tuple(targets) + tuple(controls))
         m = len(targets)
         U = _cmat(U)
         assert U.size == 4 ** m and 1 <= m <= 6
@@ -177,6 +188,7 @@ class State:
 
     def kraus(self, q, ops):
         assert self.density
+        self._check_qubits((q,))
         K = _cmat(np.stack(ops))
         lib().orc_apply_kraus(_ptr(self.a), self.n, q, len(ops), K.ctypes.data)
 
@@ -213,6 +225,7 @@ class State:
         return lib().orc_total_prob_sv(_ptr(self.a), self.n)
 
     def prob_outcome(self, q, outcome):
+        self._check_qubits((q,))
         if self.density:
             return lib().orc_prob_outcome_dm(_ptr(self.a), self.n, q, outcome)
         return lib().orc_prob_outcome_sv(_ptr(self.a), self.n, q, outcome)
@@ -250,3 +263,8 @@ def timed_run(n, ops, density=False):
 
 def num_threads():
     return lib().orc_num_threads()
+
+
+def set_num_threads(t):
+    """Host threads of the element-wise loops (results are unchanged)."""
+    lib().orc_set_num_threads(int(t))

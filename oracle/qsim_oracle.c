@@ -214,6 +214,17 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Host threads for the element-wise loops (thread-scaling runs); results do
+ * not depend on it (each iteration writes amplitudes no other reads). */
+void orc_set_num_threads(int t) {
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    omp_set_num_threads(t > 0 ? t : 1);
+#else
+    (void)t;
+#endif
+}
+
 /*
  * m-target gate U (2^m x 2^m, row-major; bit k of the block index is qubit
  * t[k]) on the amplitudes whose bits in ctrl_mask are all 1: for every base

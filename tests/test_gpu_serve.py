@@ -26,7 +26,7 @@ def env(Q):
 def mixed_requests(count, seed):
     """(kind, n, prec, ops) like the serving workload, at sizes the oracle
     finishes quickly: state vectors 4..14 qubits (c64 or c128), density
-    matrices 2..6 qubits with dephasing 0.01."""
+    matrices 2..6 qubits (c64 or c128) with dephasing 0.01."""
     rng = C.SplitMix64(seed)
     reqs = []
     for i in range(count):
@@ -35,7 +35,7 @@ def mixed_requests(count, seed):
         if kind == 2:
             N = 2 + rng.below(5)
             ops = C.with_noise(C.random_circuit(N, depth, seed + i), 0.01, 0.0)
-            reqs.append((True, N, 128, ops))
+            reqs.append((True, N, 64 if rng.below(2) == 0 else 128, ops))
         else:
             n = 4 + rng.below(11)
             reqs.append((False, n, 64 if kind == 0 else 128,
