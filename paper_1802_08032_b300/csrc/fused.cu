@@ -270,10 +270,12 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
   int lpos[64];
   for (int i = 0; i < 64; ++i) lpos[i] = -1;
   for (int i = 0; i < int(p.q.size()); ++i) lpos[p.q[i]] = i;
+  // local positions of the tile qubits among x (bits outside the tile are
+  // not local and are skipped)
   auto local_mask = [&](uint64_t x) {
     uint32_t m = 0;
     for (int b = 0; b < 64; ++b)
-      if ((x >> b) & 1) m |= 1u << lpos[b];
+      if (((x >> b) & 1) && lpos[b] >= 0) m |= 1u << lpos[b];
     return m;
   };
 
@@ -311,6 +313,8 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
         idx[b] = n;
         st.pbits[n++] = uint8_t(b);
       }
+    // the kernel reads exactly R distinct register positions below k
+    if (n != R || (P >> k) != 0) fail(QS_E_ARG, "fused planner: stage register set is not R tile bits");
     st.op_begin = int32_t(fops.size()) - first;
     bool sign_seen = false;
     for (size_t o = i; o < j; ++o) {
@@ -406,7 +410,7 @@ void launch_pass(Env& env, Reg& r, const FPass& fp, const FOp* d_ops, const FSta
     attr_set = true;
   }
   const int threads = 1 << (fp.k - R);
-  const int64_t grid = std::min<int64_t>(fp.ntiles, int64_t(env.sms) * 2);
+  const int64_t grid = std::min<int64_t>(fp.ntiles, int64_t(env.sms) * fused_ctas_per_sm(R));
   const double bytes = std::ldexp(2.0 * sizeof(typename A::Store), r.nq);
   KTimer kt(env, name, bytes, flops, 1, alu);
   k_fused<A, R><<<int(grid), threads, smem, env.stream>>>(static_cast<typename A::Store*>(r.d), fp,

@@ -37,8 +37,9 @@ enum FKind : uint8_t {
 // sqrt(Y) = ((1+i)/2) [[1, -1], [1, 1]]; the bracketed matrices need additions
 // only.  Those gates are uncontrolled, so the dropped factors multiply the
 // whole vector; the planner emits an FK_SCALE with their accumulated complex
-// product at the end of each pass (and earlier if the growth would leave the
-// float exponent range).  The conjugated forms (density-matrix column
+// product in the last pass of a plan (every op is linear, so the factor
+// commutes with all of them), and earlier if the growth would leave the
+// arithmetic's exponent range.  The conjugated forms (density-matrix column
 // updates) drop the conjugate factors: [[1, i], [i, 1]] and (1-i)/2.
 
 // Where a single bit of the amplitude index comes from, within a stage.
@@ -409,12 +410,21 @@ __host__ __device__ inline size_t fused_smem_bytes(int k, int L, int nops, int n
 
 // ------------------------------------------------------------------ kernel
 constexpr int kFusedThreads = 256;
-// Independent 16-byte global loads in flight per thread when a tile is
-// loaded: a 2^k tile over 256 threads is 16 of them, so the single-register
-// kernel requests the whole tile in one round trip (the register amplitudes
-// are not live yet).  The batched kernel, which holds more state, keeps 8.
-template <bool GENERAL>
-__host__ __device__ constexpr int load_depth() { return GENERAL ? 8 : 16; }
+// Resident CTAs per SM of the fused kernels: 2 (128 registers a thread) for
+// R >= 4; 3 (85 registers) for R = 3, whose 8 register amplitudes leave room
+// (measured for FP64: no faster than R = 4, which is the configuration used).
+__host__ __device__ constexpr int fused_ctas_per_sm(int R) { return R <= 3 ? 3 : 2; }
+// Global accesses per thread in one round of a tile load or store.  The
+// single-register kernel runs 2^(k-R) threads on a 2^k tile, so each thread
+// owns exactly 2^R amplitudes: 2^R complex128 accesses or 2^(R-1) float4
+// accesses of two complex64.  It issues all of them at once (one round, no
+// bounds test needed: the round covers the tile exactly; the register
+// amplitudes are not live yet).  The batched kernel runs 256 threads on
+// tiles of any size with bounds tests, 8 accesses a round.
+template <class A, int R, bool GENERAL>
+__host__ __device__ constexpr int tile_access_depth() {
+  return GENERAL ? 8 : (sizeof(typename A::Store) == 8 ? (1 << (R - 1)) : (1 << R));
+}
 
 // Shared-memory layout of a pass: tile, chunk offsets, op list, stage list.
 template <class A>
@@ -472,6 +482,7 @@ __device__ __forceinline__ void process_tile(typename A::Store* __restrict__ g, 
   const int lmask_low = (1 << L) - 1;
   const int nst = P.stage_end - P.stage_begin;
   const int active = 1 << (k - R);
+  constexpr int kDepth = tile_access_depth<A, R, GENERAL>();
   // global base of the tile: the bits of tau in the non-tile positions
   int64_t base = tau;
   for (int i = 0; i < k; ++i) {
@@ -492,30 +503,30 @@ __device__ __forceinline__ void process_tile(typename A::Store* __restrict__ g, 
     const int npair = ntile >> 1;
     const float4* g4 = reinterpret_cast<const float4*>(g);
     float4* t4 = reinterpret_cast<float4*>(m.tile);
-    for (int e0 = threadIdx.x; e0 < npair; e0 += blockDim.x * load_depth<GENERAL>()) {
-      float4 t[load_depth<GENERAL>()];
+    for (int e0 = threadIdx.x; e0 < npair; e0 += blockDim.x * kDepth) {
+      float4 t[kDepth];
 #pragma unroll
-      for (int u = 0; u < load_depth<GENERAL>(); ++u) {
+      for (int u = 0; u < kDepth; ++u) {
         const int l = 2 * (e0 + u * blockDim.x);
         if (!GENERAL || l < ntile) t[u] = g4[(base + m.choff[l >> L] + (l & lmask_low)) >> 1];
       }
 #pragma unroll
-      for (int u = 0; u < load_depth<GENERAL>(); ++u) {
+      for (int u = 0; u < kDepth; ++u) {
         const int e = e0 + u * blockDim.x;
         if (!GENERAL || e < npair) t4[e] = t[u];
       }
     }
   } else {
-    // load: load_depth<GENERAL>() independent loads in flight per thread
-    for (int l0 = threadIdx.x; l0 < ntile; l0 += blockDim.x * load_depth<GENERAL>()) {
-      Store t[load_depth<GENERAL>()];
+    // load: kDepth independent loads in flight per thread
+    for (int l0 = threadIdx.x; l0 < ntile; l0 += blockDim.x * kDepth) {
+      Store t[kDepth];
 #pragma unroll
-      for (int u = 0; u < load_depth<GENERAL>(); ++u) {
+      for (int u = 0; u < kDepth; ++u) {
         const int l = l0 + u * blockDim.x;
         if (!GENERAL || l < ntile) t[u] = g[base + m.choff[l >> L] + (l & lmask_low)];
       }
 #pragma unroll
-      for (int u = 0; u < load_depth<GENERAL>(); ++u) {
+      for (int u = 0; u < kDepth; ++u) {
         const int l = l0 + u * blockDim.x;
         if (!GENERAL || l < ntile) m.tile[l] = A::from_store(t[u]);
       }
@@ -605,17 +616,17 @@ __device__ __forceinline__ void process_tile(typename A::Store* __restrict__ g, 
     const int npair = ntile >> 1;
     float4* g4 = reinterpret_cast<float4*>(g);
     const float4* t4 = reinterpret_cast<const float4*>(m.tile);
-    for (int e0 = threadIdx.x; e0 < npair; e0 += blockDim.x * 8) {
+    for (int e0 = threadIdx.x; e0 < npair; e0 += blockDim.x * kDepth) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < kDepth; ++u) {
         const int e = e0 + u * blockDim.x;
         if (!GENERAL || e < npair) g4[(base + m.choff[(2 * e) >> L] + ((2 * e) & lmask_low)) >> 1] = t4[e];
       }
     }
   } else {
-    for (int l0 = threadIdx.x; l0 < ntile; l0 += blockDim.x * 8) {
+    for (int l0 = threadIdx.x; l0 < ntile; l0 += blockDim.x * kDepth) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < kDepth; ++u) {
         const int l = l0 + u * blockDim.x;
         if (!GENERAL || l < ntile) g[base + m.choff[l >> L] + (l & lmask_low)] = A::to_store(m.tile[l]);
       }
@@ -626,7 +637,7 @@ __device__ __forceinline__ void process_tile(typename A::Store* __restrict__ g, 
 
 // One pass over every tile of one register.
 template <class A, int R>
-__global__ void __launch_bounds__(kFusedThreads, 2)
+__global__ void __launch_bounds__(kFusedThreads, fused_ctas_per_sm(R))
     k_fused(typename A::Store* __restrict__ g, const __grid_constant__ FPass P,
             const FOp* __restrict__ ops, const FStage* __restrict__ stages) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -640,7 +651,7 @@ __global__ void __launch_bounds__(kFusedThreads, 2)
 // each pass with its own register pointer).  Shared memory is laid out for
 // the largest tile (kmax, Lmin) and op list (opmax) of the wave.
 template <class A, int R>
-__global__ void __launch_bounds__(kFusedThreads, 2)
+__global__ void __launch_bounds__(kFusedThreads, fused_ctas_per_sm(R))
     k_fused_batch(const BItem* __restrict__ items, int nitems, const FPass* __restrict__ passes,
                   const FOp* __restrict__ ops, const FStage* __restrict__ stages, int kmax, int Lmin,
                   int opmax) {
