@@ -303,7 +303,14 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
       P |= need;
       ++j;
     }
-    // pad with the highest unused local bits (keeps low bits on lanes)
+    // spare register slots go first to the single bits the stage's phases
+    // condition on (a phase on a lane bit runs on half-idle lanes), then to
+    // the highest unused local bits (keeps low bits on lanes)
+    for (size_t o = i; o < j && popc(P) < R; ++o)
+      if (p.ops[o].kind == FK_PHASE) {
+        const uint32_t c = local_mask(p.ops[o].cond);
+        if (popc(c) == 1) P |= c;
+      }
     for (int b = k - 1; b >= 0 && popc(P) < R; --b) P |= 1u << b;
     FStage st{};
     int idx[32];
