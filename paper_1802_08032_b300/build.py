@@ -9,7 +9,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libqsim.so")
-SOURCES = ["api.cu", "launch.cu", "fused.cu", "profiler.cu", "noalloc.cu", "batch.cu", "serve.cu"]
+SOURCES = ["api.cu", "oplist.cpp", "launch.cu", "planner.cpp", "fused.cu", "profiler.cu", "noalloc.cu",
+           "batch.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -17,6 +17,7 @@
 #include <mutex>
 #include <unordered_map>
 
+#include "fused_kernel.cuh"
 #include "plan.h"
 #include "runtime.h"
 

@@ -1,8 +1,8 @@
-// Fusion plan of one register's queued gates (internal; fused.cu).
+// Fusion plan of one register's queued gates (internal; planner.cpp).
 #pragma once
 #include <vector>
 
-#include "fused_kernel.cuh"
+#include "fused_types.h"
 #include "runtime.h"
 
 namespace qs {

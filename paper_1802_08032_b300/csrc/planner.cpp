@@ -1,0 +1,470 @@
+// Fusion planner: gate list -> fused passes of encoded operations.
+//
+// Planner.  Gates are first expanded into vector operations on the stored
+// 2^nq vector (a density-matrix gate G on qubit t becomes G on bit t and
+// conj(G) on bit t+N, Eq. 2).  Each operation has X bits (where it mixes
+// amplitudes: the target of a pair update, both bits of a depolarising
+// quad) and Z bits (where it only reads the index: controls, the bits of
+// diagonal operations).  A pass takes operations in order while their X
+// bits fit in the k tile qubits; an operation that does not fit is
+// deferred, and a later operation may move ahead of deferred ones only if
+// it commutes with all of them (no X bit of either touches a bit of the
+// other).  Passes repeat until the queue is empty.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+
+#include "plan.h"
+#include "runtime.h"
+
+namespace qs {
+
+namespace {
+
+struct VOp {
+  FKind kind;
+  bool conj = false;
+  int b0 = -1, b1 = -1;  // pair target (b0); DEPOL row/column; DEPH the two compared bits
+  uint64_t cond = 0;     // bits that must all be 1 (controls; PHASE/SIGN diagonal support)
+  double c[8] = {};
+
+  uint64_t xmask() const {
+    if (kind <= FK_X) return uint64_t(1) << b0;
+    if (kind == FK_DEPOL) return (uint64_t(1) << b0) | (uint64_t(1) << b1);
+    return 0;
+  }
+  uint64_t zmask() const {
+    uint64_t z = cond;
+    if (kind == FK_DEPH) z |= (uint64_t(1) << b0) | (uint64_t(1) << b1);
+    return z;
+  }
+};
+
+VOp pair_op(OpK k, int bit, uint64_t cond, const double* m, bool conj) {
+  VOp v;
+  v.kind = FKind(int(k));  // GEN..X share the numbering
+  v.b0 = bit;
+  v.cond = cond;
+  v.conj = conj;
+  if (k == OpK::GEN) std::memcpy(v.c, m, sizeof(v.c));
+  if (cond != 0 && (k == OpK::H || k == OpK::SX || k == OpK::SY)) {
+    // the engine applies these unscaled (a global factor), which a control
+    // would break: use the explicit matrix instead
+    const double h = std::sqrt(0.5);
+    const double H[8] = {h, 0, h, 0, h, 0, -h, 0};
+    const double SX[8] = {0.5, 0.5, 0.5, -0.5, 0.5, -0.5, 0.5, 0.5};
+    const double SY[8] = {0.5, 0.5, -0.5, -0.5, 0.5, 0.5, 0.5, 0.5};
+    const double* src = k == OpK::H ? H : (k == OpK::SX ? SX : SY);
+    for (int e = 0; e < 8; ++e) v.c[e] = src[e];
+    v.kind = FK_GEN;
+  }
+  return v;
+}
+
+void expand(const Reg& r, const GateOp& op, std::vector<VOp>& out) {
+  const int N = r.n;
+  switch (op.k) {
+    case OpK::GEN: case OpK::H: case OpK::SX: case OpK::SY: case OpK::X:
+      out.push_back(pair_op(op.k, op.t, op.cmask, op.m, false));
+      if (r.density) out.push_back(pair_op(op.k, op.t + N, op.cmask << N, op.m, true));
+      return;
+    case OpK::PHASE: {
+      VOp v;
+      v.kind = FK_PHASE;
+      v.cond = op.cmask | (uint64_t(1) << op.t);
+      v.c[0] = op.m[0];
+      v.c[1] = op.m[1];
+      out.push_back(v);
+      if (r.density) {  // column factor e^{-i phi}
+        v.cond <<= N;
+        v.c[1] = -op.m[1];
+        out.push_back(v);
+      }
+      return;
+    }
+    case OpK::SIGN: {
+      VOp v;
+      v.kind = FK_SIGN;
+      v.cond = op.cmask;
+      out.push_back(v);
+      if (r.density) {
+        v.cond <<= N;
+        out.push_back(v);
+      }
+      return;
+    }
+    case OpK::DEPHASE: {
+      VOp v;
+      v.kind = FK_DEPH;
+      v.b0 = op.t;
+      v.b1 = op.t + N;
+      v.c[0] = 1.0 - 2.0 * op.m[0];
+      out.push_back(v);
+      return;
+    }
+    case OpK::MULTI:
+      fail(QS_E_ARG, "multi-target gates are not planned into fused passes");
+    case OpK::DEPOL: {
+      const double p = op.m[0];
+      VOp v;
+      v.kind = FK_DEPOL;
+      v.b0 = op.t;
+      v.b1 = op.t + N;
+      v.c[0] = 1.0 - 2.0 * p / 3.0;
+      v.c[1] = 2.0 * p / 3.0;
+      v.c[2] = 1.0 - 4.0 * p / 3.0;
+      out.push_back(v);
+      return;
+    }
+  }
+}
+
+// Appends FK_SCALE operations carrying the factors that the engine's
+// unscaled H / sqrt(X) / sqrt(Y) leave out (1/sqrt 2, (1+i)/2, and (1-i)/2
+// for conjugated column updates).  Every operation is linear, so the factor
+// is carried across the passes of a plan and applied once, in its last
+// pass, or earlier whenever the pending magnitude growth 2^(e/2) reaches the
+// arithmetic's limit (2^40 for float exponents, 2^500 for FP64).
+// The product of e dropped factors, p of them (1+i)/2 and q of them (1-i)/2,
+// is 2^(-e/2) e^{i pi (p-q)/4}; it is formed directly (at most one rounding,
+// in 1/sqrt 2) rather than by e successive multiplications.
+std::complex<double> dropped_factor(int e, int p, int q) {
+  const int k = ((p - q) % 8 + 8) % 8;
+  const double s = std::sqrt(0.5);
+  const double mag = std::ldexp(1.0, -(e / 2));
+  // e^{i pi k / 4} with exact components for even k
+  static const int re_sign[8] = {1, 1, 0, -1, -1, -1, 0, 1};
+  static const int im_sign[8] = {0, 1, 1, 1, 0, -1, -1, -1};
+  const bool odd_e = e & 1, odd_k = k & 1;
+  // |component| of the unit phase is 1 (even k, nonzero) or 1/sqrt 2 (odd k)
+  double c = mag;
+  if (odd_e && odd_k) c *= 0.5;
+  else if (odd_e || odd_k) c *= s;
+  return {re_sign[k] * c, im_sign[k] * c};
+}
+
+struct ScaleState {
+  int e = 0, p = 0, q = 0;
+  int limit = 80;
+};
+
+void add_scales(std::vector<VOp>& ops, ScaleState& st, bool last) {
+  std::vector<VOp> out;
+  out.reserve(ops.size() + 2);
+  int &e = st.e, &p = st.p, &q = st.q;
+  auto flush_scale = [&] {
+    if (e == 0) return;
+    const std::complex<double> f = dropped_factor(e, p, q);
+    VOp s;
+    s.kind = FK_SCALE;
+    s.c[0] = f.real();
+    s.c[1] = f.imag();
+    out.push_back(s);
+    e = p = q = 0;
+  };
+  for (const VOp& v : ops) {
+    out.push_back(v);
+    if (v.kind == FK_H) {
+      ++e;
+    } else if (v.kind == FK_SX || v.kind == FK_SY) {
+      ++e;
+      if (v.conj) ++q;
+      else ++p;
+    }
+    if (e >= st.limit) flush_scale();
+  }
+  if (last) flush_scale();
+  ops.swap(out);
+}
+
+struct Pass {
+  std::vector<int> q;  // tile qubits, ascending
+  std::vector<VOp> ops;
+};
+
+int popc(uint64_t x) { return __builtin_popcountll(x); }
+
+std::vector<Pass> plan(const std::vector<VOp>& ops, int nq, int k, int L, int64_t max_ops,
+                       int scale_limit) {
+  std::vector<Pass> passes;
+  std::vector<VOp> rem = ops;
+  ScaleState scale;
+  scale.limit = scale_limit;
+  const uint64_t low = (uint64_t(1) << L) - 1;
+  while (!rem.empty()) {
+    Pass p;
+    uint64_t tile = low, bx = 0, ball = 0;
+    std::vector<VOp> deferred;
+    for (const VOp& v : rem) {
+      const uint64_t x = v.xmask(), z = v.zmask();
+      const bool commutes = (x & ball) == 0 && ((x | z) & bx) == 0;
+      const bool fits = popc(tile | x) <= k;
+      const bool room = int64_t(p.ops.size()) < max_ops;
+      if (commutes && fits && room) {
+        tile |= x;
+        p.ops.push_back(v);
+      } else {
+        deferred.push_back(v);
+        bx |= x;
+        ball |= x | z;
+      }
+    }
+    // pad the tile to exactly k qubits with the lowest unused ones
+    for (int b = 0; b < nq && popc(tile) < k; ++b) tile |= uint64_t(1) << b;
+    for (int b = 0; b < nq; ++b)
+      if ((tile >> b) & 1) p.q.push_back(b);
+    add_scales(p.ops, scale, deferred.empty());
+    passes.push_back(std::move(p));
+    rem.swap(deferred);
+  }
+  return passes;
+}
+
+void set_coeffs(FOp& f, const double* c, Arith a) {
+  for (int e = 0; e < 8; ++e) {
+    if (a == Arith::F64) {
+      f.c.d[e] = c[e];
+    } else {
+      const float hi = float(c[e]);
+      f.c.f[e] = hi;
+      if (a == Arith::DF) f.c.f[8 + e] = float(c[e] - double(hi));
+    }
+  }
+}
+
+// Kernel dispatch code of an encoded op (kind, conjugation, control form,
+// register bit).
+// Slot of the register-bit pair (a, b), a != b < 5 (see FFamily).
+int pair_slot(int a, int b) {
+  const int lo = std::min(a, b), hi = std::max(a, b);
+  return lo * 4 - lo * (lo - 1) / 2 + (hi - lo - 1);
+}
+
+int dispatch_code(const FOp& f) {
+  const bool c = f.conj != 0;
+  const int S = kCodeSlots;
+  switch (f.kind) {
+    case FK_GEN: return (c ? FC_GEN_C : FC_GEN) * S + f.i0;
+    case FK_H: return FC_H * S + f.i0;         // uncontrolled; conj(H) = H
+    case FK_SX: return (c ? FC_SX_C : FC_SX) * S + f.i0;
+    case FK_SY: return FC_SY * S + f.i0;       // real
+    case FK_X: return FC_X * S + f.i0;
+    case FK_PHASE:
+      if (f.rmask == 0) return FC_PHASE_ALL * S;
+      if (popc(f.rmask) == 1) return FC_PHASE_BIT * S + __builtin_ctz(f.rmask);
+      return FC_PHASE_MASK * S;
+    case FK_SIGN: return FC_SIGN * S;
+    case FK_DEPH: return FC_DEPH * S;
+    case FK_DEPOL: return FC_DEPOL * S + pair_slot(f.i0, f.i1);
+    default: return FC_SCALE * S;
+  }
+}
+
+// Device-side op encoding for one pass: stages of R register bits.  Stage op
+// ranges are relative to the pass's first op.
+void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fops,
+                 std::vector<FStage>& fst) {
+  const int32_t first = int32_t(fops.size());
+  int lpos[64];
+  for (int i = 0; i < 64; ++i) lpos[i] = -1;
+  for (int i = 0; i < int(p.q.size()); ++i) lpos[p.q[i]] = i;
+  // local positions of the tile qubits among x (bits outside the tile are
+  // not local and are skipped)
+  auto local_mask = [&](uint64_t x) {
+    uint32_t m = 0;
+    for (int b = 0; b < 64; ++b)
+      if (((x >> b) & 1) && lpos[b] >= 0) m |= 1u << lpos[b];
+    return m;
+  };
+
+  // With FP64 (or double-float) arithmetic a stage boundary costs little
+  // next to the arithmetic, while a phase on a bit that is not a register
+  // bit runs on half-idle lanes; so there the bits a phase conditions on are
+  // made register bits too.
+  const bool phase_in_regs = arith != Arith::F32;
+  auto needed = [&](const VOp& v) {
+    uint32_t need = local_mask(v.xmask());
+    if (phase_in_regs && v.kind == FK_PHASE) {
+      const uint32_t c = local_mask(v.cond);
+      if (popc(c) <= R) need |= c;
+    }
+    return need;
+  };
+  size_t i = 0;
+  while (i < p.ops.size()) {
+    // grow the stage's register set while the needed bits fit in R
+    uint32_t P = 0;
+    size_t j = i;
+    while (j < p.ops.size()) {
+      const uint32_t need = needed(p.ops[j]);
+      if (j > i && popc(P | need) > R) break;
+      P |= need;
+      ++j;
+    }
+    // spare register slots go first to the single bits the stage's phases
+    // condition on (a phase on a lane bit runs on half-idle lanes), then to
+    // the highest unused local bits (keeps low bits on lanes)
+    for (size_t o = i; o < j && popc(P) < R; ++o)
+      if (p.ops[o].kind == FK_PHASE) {
+        const uint32_t c = local_mask(p.ops[o].cond);
+        if (popc(c) == 1) P |= c;
+      }
+    for (int b = k - 1; b >= 0 && popc(P) < R; --b) P |= 1u << b;
+    FStage st{};
+    int idx[32];
+    int n = 0;
+    for (int b = 0; b < k; ++b)
+      if ((P >> b) & 1) {
+        idx[b] = n;
+        st.pbits[n++] = uint8_t(b);
+      }
+    // the kernel reads exactly R distinct register positions below k
+    if (n != R || (P >> k) != 0) fail(QS_E_ARG, "fused planner: stage register set is not R tile bits");
+    st.op_begin = int32_t(fops.size()) - first;
+    bool sign_seen = false;
+    for (size_t o = i; o < j; ++o) {
+      const VOp& v = p.ops[o];
+      FOp f{};
+      f.kind = v.kind;
+      f.conj = v.conj ? 1 : 0;
+      if (v.kind <= FK_X || v.kind == FK_DEPOL) f.i0 = uint8_t(idx[lpos[v.b0]]);
+      if (v.kind == FK_DEPOL) f.i1 = uint8_t(idx[lpos[v.b1]]);
+      for (int b = 0; b < 64; ++b) {
+        if (!((v.cond >> b) & 1)) continue;
+        if (lpos[b] < 0) f.gmask |= uint64_t(1) << b;
+        else if ((P >> lpos[b]) & 1) f.rmask |= uint8_t(1u << idx[lpos[b]]);
+        else f.lmask |= 1u << lpos[b];
+      }
+      if (v.kind == FK_DEPH) {
+        auto src = [&](int bit, uint8_t& s, uint8_t& pos) {
+          if (lpos[bit] < 0) { s = BS_GLOBAL; pos = uint8_t(bit); }
+          else if ((P >> lpos[bit]) & 1) { s = BS_REG; pos = uint8_t(idx[lpos[bit]]); }
+          else { s = BS_LOCAL; pos = uint8_t(lpos[bit]); }
+        };
+        src(v.b0, f.asrc, f.apos);
+        src(v.b1, f.bsrc, f.bpos);
+      }
+      set_coeffs(f, v.c, arith);
+      if (v.kind == FK_PHASE || v.kind == FK_SIGN) {
+        uint32_t touch = 0;  // register amplitudes j whose index has every rmask bit
+        for (int j = 0; j < (1 << R); ++j)
+          if ((uint32_t(j) & f.rmask) == f.rmask) touch |= 1u << j;
+        f.c.u[15] = touch;
+      }
+      f.code = uint16_t(dispatch_code(f));
+      if (f.lmask != 0 || f.gmask != 0) f.flags |= FF_COND;
+      if (sign_seen && (v.kind <= FK_X || v.kind == FK_DEPOL)) f.flags |= FF_FLIP;
+      if (v.kind == FK_DEPOL) f.flags |= FF_TWO;
+      const bool deferred_sign = v.kind == FK_SIGN;
+      if (deferred_sign) sign_seen = true;
+      // consecutive pending sign flips under the same thread / tile condition
+      // compose into one (the product of sign operators is their XOR)
+      if (deferred_sign && int32_t(fops.size()) - first > st.op_begin) {
+        FOp& prev = fops.back();
+        if (prev.code == f.code && prev.lmask == f.lmask && prev.gmask == f.gmask) {
+          prev.c.u[15] ^= f.c.u[15];
+          continue;
+        }
+      }
+      fops.push_back(f);
+    }
+    st.op_end = int32_t(fops.size()) - first;
+    fst.push_back(st);
+    i = j;
+  }
+}
+
+double vop_flops(const VOp& v, int nq) {
+  const double dim = std::ldexp(1.0, nq), f = std::ldexp(1.0, -popc(v.cond));
+  static const double pair_flops[5] = {28, 4, 4, 4, 0};  // H, sqrt(X), sqrt(Y) unscaled
+  if (v.kind <= FK_X) return dim / 2 * f * pair_flops[v.kind];
+  if (v.kind == FK_PHASE) return dim * f * 6;
+  if (v.kind == FK_SCALE) return dim * 6;
+  if (v.kind == FK_DEPH) return dim / 2 * 2;
+  if (v.kind == FK_DEPOL) return dim / 4 * 16;
+  return 0;
+}
+
+// Arithmetic instructions (add, multiply, FMA: 1 each) one vector op issues,
+// in the precision of the kernel's arithmetic.  Plain FP32/FP64 per pair:
+// general 16, H / sqrt(X) / sqrt(Y) 4; per touched amplitude: phase 4,
+// dephasing 2; per quad: depolarising 12; per amplitude: scale 4.
+// Double-float (packed: one instruction covers the real and imaginary
+// parts): complex df add 11, multiply by a df factor 8, complex df product
+// 27; in FP32-lane terms each packed instruction counts twice.
+double vop_alu(const VOp& v, int nq, Arith a) {
+  const double dim = std::ldexp(1.0, nq), f = std::ldexp(1.0, -popc(v.cond));
+  const bool d = a == Arith::DF;
+  static const double plain_pair[5] = {16, 4, 4, 4, 0};
+  static const double df_pair[5] = {2 * 130, 2 * 22, 2 * 22, 2 * 22, 0};
+  if (v.kind <= FK_X) return dim / 2 * f * (d ? df_pair[v.kind] : plain_pair[v.kind]);
+  if (v.kind == FK_PHASE) return dim * f * (d ? 2 * 27 : 4);
+  if (v.kind == FK_SCALE) return dim * (d ? 2 * 27 : 4);
+  if (v.kind == FK_DEPH) return dim / 2 * (d ? 2 * 8 : 2);
+  if (v.kind == FK_DEPOL) return dim / 4 * (d ? 2 * (2 * 27 + 2 * 8) : 12);
+  return 0;
+}
+
+}  // namespace
+
+TileCfg tile_cfg(const Reg& r) { return r.prec == QS_C128 ? TileCfg{4, 12, 3} : TileCfg{5, 13, 4}; }
+
+bool fusable(const Reg& r) {
+  const TileCfg c = tile_cfg(r);
+  return r.nq >= c.R;  // a tile of 2^nq amplitudes worked by 2^(nq-R) threads
+}
+
+Arith arith_of(const Reg& r) {
+  if (r.prec == QS_C64) return Arith::F32;
+  return r.env->arith == 1 ? Arith::DF : Arith::F64;
+}
+
+void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, RegPlan& out) {
+  const Env& env = *r.env;
+  const TileCfg cfg = tile_cfg(r);
+  int k = std::min(cfg.kmax, r.nq);
+  if (k_req > 0) k = std::min(k_req, r.nq);
+  else if (env.tile_qubits > 0) k = std::min<int>(int(env.tile_qubits), r.nq);
+  k = std::max(k, std::min(cfg.R + 5, r.nq));
+  k = std::min(k, cfg.R + 8);
+  const int L = std::min(cfg.L, k);
+  out = RegPlan{};
+  out.k = k;
+  out.L = L;
+  out.R = cfg.R;
+  out.arith = arith_of(r);
+
+  std::vector<VOp> vops;
+  vops.reserve(q.size() * 2);
+  for (const GateOp& op : q) expand(r, op, vops);
+  out.vops = int64_t(vops.size());
+  const int64_t cap = env.max_fused_ops > 0 ? std::min<int64_t>(env.max_fused_ops, kMaxPassOps)
+                                            : kMaxPassOps;
+  const std::vector<Pass> passes = plan(vops, r.nq, k, L, cap, out.arith == Arith::F64 ? 1000 : 80);
+  for (const Pass& p : passes) {
+    FPass fp{};
+    fp.k = k;
+    fp.L = L;
+    fp.nq = r.nq;
+    fp.ntiles = int64_t(1) << (r.nq - k);
+    fp.amps = r.d;
+    for (int i = 0; i < k; ++i) fp.q[i] = uint8_t(p.q[i]);
+    fp.stage_begin = int(out.fst.size());
+    fp.op_begin = int(out.fops.size());
+    encode_pass(p, cfg.R, k, out.arith, out.fops, out.fst);
+    fp.stage_end = int(out.fst.size());
+    fp.op_count = int(out.fops.size()) - fp.op_begin;
+    out.fps.push_back(fp);
+    double fl = 0;
+    double al = 0;
+    for (const VOp& v : p.ops) {
+      fl += vop_flops(v, r.nq);
+      al += vop_alu(v, r.nq, out.arith);
+    }
+    out.flops.push_back(fl);
+    out.alu.push_back(al);
+  }
+}
+
+}  // namespace qs

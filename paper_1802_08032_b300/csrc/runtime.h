@@ -149,8 +149,17 @@ int guarded_call(const std::function<void()>& f);
 // Handle lookups (api.cu); fail with QS_E_HANDLE when unknown.
 Env& lookup_env(int64_t id);
 Reg& lookup_reg(int64_t id);
+// Validation helpers (oplist.cpp): a qubit in [0, n) (QS_E_QUBIT); a
+// target plus controls, in range and pairwise distinct (QS_E_DUP), as the
+// control mask; a unitary 2x2 matrix, row-major (re, im) (QS_E_UNITARY).
+void check_qubit(const Reg& r, int q, const char* what);
+uint64_t check_targets(const Reg& r, int target, const int* ctrls, int nc);
+void check_unitary(const double* m);
+GateOp make_op(OpK k, int t, uint64_t cmask);
+// Validates one bulk-call op, appending its internal ops (oplist.cpp).
+void convert_op(const Reg& r, const QSOp& o, std::vector<GateOp>& out);
 // Validates bulk-call ops for a register of r's shape into internal ops
-// (api.cu); fails with the first bad op's code.
+// (oplist.cpp); fails with the first bad op's code.
 void convert_ops(const Reg& r, const QSOp* ops, int64_t n, std::vector<GateOp>& out);
 
 // Entry points of the kernel layer (implemented in the .cu files).

@@ -1,0 +1,141 @@
+"""CPU tests of the fused-pass planner (host logic, no GPU).
+
+tests/planner_check.cpp is compiled with the host compiler against the
+library's planner and op-validation sources.  For each gate list it plans
+the passes, checks the invariants the fused kernel relies on (tile qubits,
+R distinct ascending register positions per stage, condition masks that
+split cleanly into register / local / global bits, dispatch codes) and
+applies the encoded passes to |0...0> on the CPU.  The result must match
+the oracle: this pins the planner and the operation encoding (unscaled
+H / sqrt(X) / sqrt(Y) with the deferred scale factor, pending sign flips,
+per-thread and per-tile conditions, the density-matrix column updates of
+Eq. 2) independently of the GPU.
+"""
+import os
+import shutil
+import subprocess
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1802_08032_b300 import circuits as C
+from paper_1802_08032_b300 import qsim as Q
+from oracle import oracle as O
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(ROOT, "paper_1802_08032_b300", "csrc")
+CUDA_INC = "/usr/local/cuda/include"
+
+
+@pytest.fixture(scope="session")
+def harness(tmp_path_factory):
+    cxx = shutil.which("g++")
+    if cxx is None or not os.path.isdir(CUDA_INC):
+        pytest.skip("host compiler or CUDA headers missing")
+    exe = str(tmp_path_factory.mktemp("planner") / "planner_check")
+    srcs = [os.path.join(HERE, "planner_check.cpp"), os.path.join(CSRC, "planner.cpp"),
+            os.path.join(CSRC, "oplist.cpp")]
+    base = [cxx, "-O1", "-std=c++17", "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-I", CUDA_INC,
+            "-o", exe, *srcs]
+    # undefined behaviour in the planner (shifts, overflows) aborts the run
+    ubsan = ["-fsanitize=undefined", "-fno-sanitize-recover=undefined"]
+    if subprocess.run(base[:1] + ubsan + base[1:], capture_output=True).returncode != 0:
+        subprocess.check_call(base)
+    return exe
+
+
+def run(exe, n, ops, density=False, prec=128, arith=0, k_req=0, emulate=True):
+    arr, cnt = Q.to_qsops(ops)
+    data = ctypes.string_at(ctypes.addressof(arr), ctypes.sizeof(QSOp) * cnt)
+    r = subprocess.run([exe, str(n), str(int(density)), str(prec), str(arith), str(k_req),
+                        str(int(emulate))], input=data, capture_output=True, timeout=120)
+    out = r.stdout
+    head, _, rest = out.partition(b"\n")
+    assert r.returncode == 0, (head.decode(), r.stderr.decode()[-2000:])
+    assert b"violations 0" in head, head
+    if not emulate:
+        return head.decode(), None
+    tag, _, body = rest.partition(b"\n")
+    assert tag == b"STATE"
+    return head.decode(), np.frombuffer(body, dtype=np.complex128)
+
+
+QSOp = Q.QSOp
+TOL = {(128, 0): 1e-12, (128, 1): 1e-12, (64, 0): 1e-5}
+
+
+def controlled_extras(n, seed):
+    """CNOT, controlled and multi-controlled unitaries, phase shifts (the
+    random layering has none of them)."""
+    rng = C.SplitMix64(seed)
+    ops = []
+    for _ in range(3 * n):
+        qs = C.distinct_qubits(rng, n, min(n, 3))
+        a = C.haar_alpha_beta(rng)
+        al, be = complex(a[0], a[1]), complex(a[2], a[3])
+        u = (al.real, al.imag, -be.real, be.imag, be.real, be.imag, al.real, -al.imag)
+        kind = rng.below(4)
+        if kind == 0 and n >= 2:
+            ops.append(C.Op("CNOT", (qs[0],), (qs[1],)))
+        elif kind == 1 and n >= 2:
+            ops.append(C.Op("CUNITARY", (qs[0],), tuple(qs[1:]), u))
+        elif kind == 2:
+            ops.append(C.Op("PHASE", (qs[0],), (), (0.3 + rng.uniform(),)))
+        else:
+            ops.append(C.Op("UNITARY", (qs[0],), (), u))
+    return ops
+
+
+@pytest.mark.parametrize("n", [1, 3, 5, 8, 11, 13, 14])
+@pytest.mark.parametrize("prec,arith", [(128, 0), (128, 1), (64, 0)])
+def test_planned_state_vector_matches_oracle(harness, n, prec, arith):
+    ops = C.random_circuit(n, 10, 100 + n, extras=n >= 3)
+    ops = ops[: len(ops) // 2] + controlled_extras(n, n) + ops[len(ops) // 2:]
+    if n < (5 if prec == 64 else 4):
+        pytest.skip("registers below R qubits (5 complex64, 4 complex128) are not fused")
+    head, psi = run(harness, n, ops, prec=prec, arith=arith)
+    ref = O.run_circuit(n, ops).a
+    assert np.max(np.abs(psi - ref)) <= TOL[(prec, arith)], head
+
+
+@pytest.mark.parametrize("n,k", [(14, 9), (13, 9), (12, 10), (14, 11)])
+@pytest.mark.parametrize("part", ["whole", "suffix"])
+def test_tile_smaller_than_register(harness, n, k, part):
+    """Qubits outside the tile: per-tile conditions, phases and flips whose
+    qubits are global, and stage register sets that must still be R tile
+    positions.  A suffix of a circuit (as a later flush of the same register
+    sees it) has phases before any other op on their qubits, so they land in
+    passes whose tile does not hold them."""
+    ops = C.random_circuit(n, 12, 7 * n + k, extras=True) + controlled_extras(n, k)
+    if part == "suffix":
+        ops = ops[len(ops) // 3:]
+    head, psi = run(harness, n, ops, k_req=k)
+    assert f" k {k} " in head, head
+    ref = O.run_circuit(n, ops).a
+    assert np.max(np.abs(psi - ref)) <= 1e-12, head
+
+
+@pytest.mark.parametrize("N", [2, 4, 6])
+@pytest.mark.parametrize("arith", [0, 1])
+def test_planned_density_matrix_matches_oracle(harness, N, arith):
+    ops = C.random_density_circuit(N, 8, 40 + N, 0.01, 0.005)
+    head, rho = run(harness, N, ops, density=True, arith=arith, k_req=0)
+    ref = O.run_circuit(N, ops, density=True).a
+    assert np.max(np.abs(rho - ref)) <= 1e-12, head
+
+
+def test_density_matrix_small_tile(harness):
+    N = 6
+    ops = C.random_density_circuit(N, 6, 77, 0.02, 0.01)
+    head, rho = run(harness, N, ops, density=True, k_req=9)
+    ref = O.run_circuit(N, ops, density=True).a
+    assert np.max(np.abs(rho - ref)) <= 1e-12, head
+
+
+@pytest.mark.parametrize("prec,arith", [(128, 0), (128, 1), (64, 0)])
+def test_30_qubit_workload_plan_invariants(harness, prec, arith):
+    head, _ = run(harness, 30, C.workload_30q(), prec=prec, arith=arith, emulate=False)
+    passes = int(head.split()[2])
+    assert 0 < passes <= 40, head
