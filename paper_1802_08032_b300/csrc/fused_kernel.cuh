@@ -108,6 +108,13 @@ struct PlainArith {
     }
     return w;
   }
+  // i v: a swap and a sign flip, no arithmetic
+  __device__ static Cplx mul_i(const Cplx& v) {
+    Cplx w;
+    w.x = neg_bits(v.y);
+    w.y = v.x;
+    return w;
+  }
   __device__ static Cplx scale(const Cplx& v, const FOp& op, int e) {
     const R f = cf(op, e);
     Cplx w;
@@ -178,6 +185,7 @@ struct DFArith {
     }
   }
   __device__ static Cplx phase(const Cplx& v, const FOp& op) { return dfc2_cmul(v, cf(op, 0), cf(op, 1)); }
+  __device__ static Cplx mul_i(const Cplx& v) { return mul_plus_i(v); }
   __device__ static Cplx negate(const Cplx& v) {
     return dfc2{mul2(v.hi, f2(-1.f, -1.f)), mul2(v.lo, f2(-1.f, -1.f))};
   }
@@ -211,6 +219,14 @@ __device__ __forceinline__ void phase_on_bit(typename A::Cplx (&v)[1 << R], cons
 #pragma unroll
   for (int j = 0; j < (1 << R); ++j)
     if (j & (1 << I)) v[j] = A::phase(v[j], op);
+}
+
+// i times the amplitudes with register bit I set.
+template <class A, int R, int I>
+__device__ __forceinline__ void muli_on_bit(typename A::Cplx (&v)[1 << R]) {
+#pragma unroll
+  for (int j = 0; j < (1 << R); ++j)
+    if (j & (1 << I)) v[j] = A::mul_i(v[j]);
 }
 
 template <class A, int R, int I0, int I1>
@@ -280,6 +296,18 @@ __device__ __forceinline__ void run_op(typename A::Cplx (&v)[1 << R], const FOp&
     QS_BIT_CASES(FC_X, (pair_on_bit<A, R, PK_X, false, true, I>(v, rmask, op)))
     QS_BIT_CASES(FC_PHASE_BIT, (phase_on_bit<A, R, I>(v, op)))
     QS_PAIR_CASES(FC_DEPOL, (depol_on_bits<A, R, IA, IB>(v, op)))
+    QS_BIT_CASES(FC_MULI_BIT, (muli_on_bit<A, R, I>(v)))
+    case FC_MULI_ALL * kCodeSlots:
+#pragma unroll
+      for (int j = 0; j < (1 << R); ++j) v[j] = A::mul_i(v[j]);
+      break;
+    case FC_MULI_MASK * kCodeSlots: {
+      const uint32_t touch = op.c.u[15];
+#pragma unroll
+      for (int j = 0; j < (1 << R); ++j)
+        if ((touch >> j) & 1u) v[j] = A::mul_i(v[j]);
+      break;
+    }
 #undef QS_PAIR_CASES
 #undef QS_PAIR_CASE
 #undef QS_BIT_CASES

@@ -12,7 +12,8 @@ enum FKind : uint8_t {
   FK_SIGN = 6,    // negate where the condition holds
   FK_DEPH = 7,    // scale by c0 where bit A != bit B
   FK_DEPOL = 8,   // depolarising quad on register bits (i0 = row bit, i1 = column bit)
-  FK_SCALE = 9    // multiply every amplitude by the complex (c0, c1)
+  FK_SCALE = 9,   // multiply every amplitude by the complex (c0, c1)
+  FK_MULI = 10    // multiply by i where the condition holds (no arithmetic)
 };
 // In this engine H, sqrt(X) and sqrt(Y) are applied WITHOUT their scalar
 // factors: H = (1/sqrt 2) [[1, 1], [1, -1]], sqrt(X) = ((1+i)/2) [[1, -i], [-i, 1]],
@@ -37,7 +38,8 @@ enum BitSrc : uint8_t { BS_REG = 0, BS_LOCAL = 1, BS_GLOBAL = 2 };
 enum FFamily : uint8_t {
   FC_GEN = 0, FC_GEN_C = 1, FC_H = 2, FC_SX = 3, FC_SX_C = 4, FC_SY = 5, FC_X = 6,
   FC_PHASE_BIT = 7, FC_PHASE_ALL = 8, FC_PHASE_MASK = 9,
-  FC_SIGN = 10, FC_DEPH = 11, FC_DEPOL = 12, FC_SCALE = 13
+  FC_SIGN = 10, FC_DEPH = 11, FC_DEPOL = 12, FC_SCALE = 13,
+  FC_MULI_BIT = 14, FC_MULI_ALL = 15, FC_MULI_MASK = 16
 };
 constexpr int kCodeSlots = 16;
 // FOp::flags
@@ -65,7 +67,7 @@ struct FOp {
   union {
     double d[8];
     float f[16];
-    uint32_t u[16];  // PHASE / SIGN: u[15] = the register amplitudes j the op touches
+    uint32_t u[16];  // PHASE / SIGN / MULI: u[15] = the register amplitudes j the op touches
   } c;
 };
 static_assert(sizeof(FOp) == 88, "FOp layout");

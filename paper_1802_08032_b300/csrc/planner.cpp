@@ -183,6 +183,76 @@ struct Pass {
   std::vector<VOp> ops;
 };
 
+// Consecutive phases on one bit merge into one operation (T^2 = S is a
+// multiplication by i, T^4 = Z a sign flip: neither needs arithmetic).  A
+// phase on a single bit commutes with every operation except those that
+// mix amplitudes along that bit (a pair update on it, a depolarising quad
+// on it), so it is carried forward to the next such operation, or to the
+// end, and emitted there.  T factors (1 + i)/sqrt 2 and their conjugates
+// (density-matrix column updates) are counted exactly as multiples k of
+// pi/4: k = 4 is a sign flip, k = 2 a multiplication by i, k = 6 both, odd k
+// one phase with components +-1/sqrt 2; any other phase joins one general
+// factor, multiplied out once.
+void merge_phases(std::vector<VOp>& ops, int nq) {
+  struct Pending {
+    int k = 0;
+    std::complex<double> g{1.0, 0.0};
+    bool general = false, any = false;
+  };
+  const double s = std::sqrt(0.5);
+  static const double ur[8] = {1, s, 0, -s, -1, -s, 0, s}, ui[8] = {0, s, 1, s, 0, -s, -1, -s};
+  std::vector<Pending> pend(static_cast<size_t>(nq));
+  std::vector<VOp> out;
+  out.reserve(ops.size());
+  auto emit = [&](int b) {
+    Pending& p = pend[size_t(b)];
+    if (!p.any) return;
+    const uint64_t bit = uint64_t(1) << b;
+    const int k = ((p.k % 8) + 8) % 8;
+    VOp v;
+    v.cond = bit;
+    if (p.general || (k & 1)) {
+      const std::complex<double> f = p.g * std::complex<double>(ur[k], ui[k]);
+      v.kind = FK_PHASE;
+      v.c[0] = p.general ? f.real() : ur[k];
+      v.c[1] = p.general ? f.imag() : ui[k];
+      out.push_back(v);
+    } else if (k == 2 || k == 6) {
+      v.kind = FK_MULI;
+      out.push_back(v);
+      if (k == 6) {
+        v.kind = FK_SIGN;
+        out.push_back(v);
+      }
+    } else if (k == 4) {
+      v.kind = FK_SIGN;
+      out.push_back(v);
+    }
+    p = Pending{};
+  };
+  for (const VOp& v : ops) {
+    if (v.kind == FK_PHASE && __builtin_popcountll(v.cond) == 1) {
+      Pending& p = pend[size_t(__builtin_ctzll(v.cond))];
+      p.any = true;
+      if (v.c[0] == s && v.c[1] == s) {
+        p.k += 1;
+      } else if (v.c[0] == s && v.c[1] == -s) {
+        p.k -= 1;
+      } else {
+        p.g *= std::complex<double>(v.c[0], v.c[1]);
+        p.general = true;
+      }
+      continue;
+    }
+    const uint64_t x = v.xmask();
+    for (int b = 0; b < nq; ++b)
+      if ((x >> b) & 1) emit(b);
+    out.push_back(v);
+  }
+  for (int b = 0; b < nq; ++b) emit(b);
+  ops.swap(out);
+}
+
 int popc(uint64_t x) { return __builtin_popcountll(x); }
 
 std::vector<Pass> plan(const std::vector<VOp>& ops, int nq, int k, int L, int64_t max_ops,
@@ -255,6 +325,10 @@ int dispatch_code(const FOp& f) {
       if (popc(f.rmask) == 1) return FC_PHASE_BIT * S + __builtin_ctz(f.rmask);
       return FC_PHASE_MASK * S;
     case FK_SIGN: return FC_SIGN * S;
+    case FK_MULI:
+      if (f.rmask == 0) return FC_MULI_ALL * S;
+      if (popc(f.rmask) == 1) return FC_MULI_BIT * S + __builtin_ctz(f.rmask);
+      return FC_MULI_MASK * S;
     case FK_DEPH: return FC_DEPH * S;
     case FK_DEPOL: return FC_DEPOL * S + pair_slot(f.i0, f.i1);
     default: return FC_SCALE * S;
@@ -346,7 +420,7 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
         src(v.b1, f.bsrc, f.bpos);
       }
       set_coeffs(f, v.c, arith);
-      if (v.kind == FK_PHASE || v.kind == FK_SIGN) {
+      if (v.kind == FK_PHASE || v.kind == FK_SIGN || v.kind == FK_MULI) {
         uint32_t touch = 0;  // register amplitudes j whose index has every rmask bit
         for (int j = 0; j < (1 << R); ++j)
           if ((uint32_t(j) & f.rmask) == f.rmask) touch |= 1u << j;
@@ -439,6 +513,7 @@ void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, RegPlan& 
   vops.reserve(q.size() * 2);
   for (const GateOp& op : q) expand(r, op, vops);
   out.vops = int64_t(vops.size());
+  merge_phases(vops, r.nq);
   const int64_t cap = env.max_fused_ops > 0 ? std::min<int64_t>(env.max_fused_ops, kMaxPassOps)
                                             : kMaxPassOps;
   const std::vector<Pass> passes = plan(vops, r.nq, k, L, cap, out.arith == Arith::F64 ? 1000 : 80);

@@ -79,18 +79,19 @@ static void check_plan(const RegPlan& pl, int nq) {
       for (int o = st.op_begin; o < st.op_end; ++o) {
         const FOp& f = pl.fops[P.op_begin + o];
         const int fam = f.code / kCodeSlots, slot = f.code % kCodeSlots;
-        CHECK(fam <= FC_SCALE, "op %d: family %d", o, fam);
+        CHECK(fam <= FC_MULI_MASK, "op %d: family %d", o, fam);
         CHECK(f.rmask < (1u << R), "op %d: rmask", o);
         CHECK((f.lmask & pm) == 0 && (f.lmask >> k) == 0, "op %d: lmask on a register / non-tile bit", o);
         CHECK((f.gmask & tile) == 0 && (nq == 64 || (f.gmask >> nq) == 0), "op %d: gmask inside the tile", o);
         CHECK(((f.flags & FF_COND) != 0) == (f.lmask != 0 || f.gmask != 0), "op %d: FF_COND", o);
-        if (fam <= FC_X || fam == FC_PHASE_BIT) CHECK(slot < R, "op %d: slot %d >= R", o, slot);
+        if (fam <= FC_X || fam == FC_PHASE_BIT || fam == FC_MULI_BIT) CHECK(slot < R, "op %d: slot %d >= R", o, slot);
         if (fam <= FC_X) {
           CHECK(f.i0 == slot && ((f.rmask >> f.i0) & 1u) == 0, "op %d: pair target", o);
           if (fam != FC_GEN && fam != FC_GEN_C && fam != FC_X) CHECK(f.rmask == 0, "op %d: controlled add-only pair", o);
         }
         if (fam == FC_PHASE_BIT) CHECK(popc64(f.rmask) == 1 && (f.rmask >> slot) == 1u, "op %d: phase bit", o);
-        if (fam == FC_PHASE_ALL) CHECK(f.rmask == 0, "op %d: phase all", o);
+        if (fam == FC_PHASE_ALL || fam == FC_MULI_ALL) CHECK(f.rmask == 0, "op %d: phase all", o);
+        if (fam == FC_MULI_BIT) CHECK(popc64(f.rmask) == 1 && (f.rmask >> slot) == 1u, "op %d: i bit", o);
         if (fam == FC_DEPOL) {
           int a, b;
           slot_pair(slot, a, b);
@@ -183,6 +184,13 @@ static std::vector<cd> emulate(const RegPlan& pl, int nq) {
                 if (fam == FC_PHASE_BIT) touch = (j >> slot) & 1;
                 if (fam == FC_PHASE_MASK) touch = (f.c.u[15] >> j) & 1u;
                 if (touch) v[j] *= ph;
+              }
+            } else if (fam == FC_MULI_BIT || fam == FC_MULI_ALL || fam == FC_MULI_MASK) {
+              for (int j = 0; j < nj; ++j) {
+                bool touch = true;
+                if (fam == FC_MULI_BIT) touch = (j >> slot) & 1;
+                if (fam == FC_MULI_MASK) touch = (f.c.u[15] >> j) & 1u;
+                if (touch) v[j] *= cd(0, 1);
               }
             } else if (fam == FC_DEPH) {
               auto bv = [&](uint8_t src, uint8_t pos, int j) -> int {
