@@ -122,12 +122,16 @@ struct PlainArith {
     w.y = v.y * f;
     return w;
   }
-  __device__ static Cplx axpby(const Cplx& a, const Cplx& b, const FOp& op) {
-    const R keep = cf(op, 0), move = cf(op, 1);
-    Cplx w;
-    w.x = keep * a.x + move * b.x;
-    w.y = keep * a.y + move * b.y;
-    return w;
+  // Depolarising mix of the diagonal pair (x, y) = (rho_00, rho_11) with
+  // move = m: (x + m (y - x), y - m (y - x)), one subtraction and two FMAs
+  // per component (keep = 1 - m is implied).
+  __device__ static void depol_mix(Cplx& x, Cplx& y, const FOp& op) {
+    const R m = cf(op, 1);
+    const R dx = y.x - x.x, dy = y.y - x.y;
+    x.x = fma(m, dx, x.x);
+    x.y = fma(m, dy, x.y);
+    y.x = fma(-m, dx, y.x);
+    y.y = fma(-m, dy, y.y);
   }
 };
 
@@ -198,6 +202,12 @@ struct DFArith {
     return dfc2_add(dfc2_mulv(a, f2(keep.hi, keep.hi), f2(keep.lo, keep.lo)),
                     dfc2_mulv(b, f2(move.hi, move.hi), f2(move.lo, move.lo)));
   }
+  // (keep x + move y, keep y + move x)
+  __device__ static void depol_mix(Cplx& x, Cplx& y, const FOp& op) {
+    const Cplx x0 = x;
+    x = axpby(x0, y, op);
+    y = axpby(y, x0, op);
+  }
 };
 
 // ------------------------------------------------------------ register ops
@@ -235,9 +245,7 @@ __device__ __forceinline__ void depol_on_bits(typename A::Cplx (&v)[1 << R], con
   for (int j = 0; j < (1 << R); ++j) {
     if (j & ((1 << I0) | (1 << I1))) continue;
     const int a = j, b = j | (1 << I0), c = j | (1 << I1), d = j | (1 << I0) | (1 << I1);
-    const typename A::Cplx d0 = v[a], d1 = v[d];
-    v[a] = A::axpby(d0, d1, op);
-    v[d] = A::axpby(d1, d0, op);
+    A::depol_mix(v[a], v[d], op);
     v[b] = A::scale(v[b], op, 2);
     v[c] = A::scale(v[c], op, 2);
   }

@@ -253,6 +253,32 @@ void merge_phases(std::vector<VOp>& ops, int nq) {
   ops.swap(out);
 }
 
+// A dephasing on qubit bits (t, t + N) only scales the entries whose row
+// and column bits differ; a depolarising quad on the same bits scales those
+// entries by its "off" factor and mixes the others.  When no operation
+// between them mixes amplitudes along either bit (every such operation
+// commutes with the diagonal dephasing), the dephasing factor folds into
+// the depolarising one and the dephasing is dropped.
+void fold_dephasing(std::vector<VOp>& ops) {
+  std::vector<bool> drop(ops.size(), false);
+  for (size_t i = 0; i < ops.size(); ++i) {
+    if (ops[i].kind != FK_DEPH) continue;
+    const uint64_t bits = (uint64_t(1) << ops[i].b0) | (uint64_t(1) << ops[i].b1);
+    for (size_t j = i + 1; j < ops.size(); ++j) {
+      if ((ops[j].xmask() & bits) == 0) continue;
+      if (ops[j].kind == FK_DEPOL && ops[j].b0 == ops[i].b0 && ops[j].b1 == ops[i].b1) {
+        ops[j].c[2] *= ops[i].c[0];
+        drop[i] = true;
+      }
+      break;
+    }
+  }
+  size_t w = 0;
+  for (size_t i = 0; i < ops.size(); ++i)
+    if (!drop[i]) ops[w++] = ops[i];
+  ops.resize(w);
+}
+
 int popc(uint64_t x) { return __builtin_popcountll(x); }
 
 std::vector<Pass> plan(const std::vector<VOp>& ops, int nq, int k, int L, int64_t max_ops,
@@ -463,7 +489,7 @@ double vop_flops(const VOp& v, int nq) {
 // Arithmetic instructions (add, multiply, FMA: 1 each) one vector op issues,
 // in the precision of the kernel's arithmetic.  Plain FP32/FP64 per pair:
 // general 16, H / sqrt(X) / sqrt(Y) 4; per touched amplitude: phase 4,
-// dephasing 2; per quad: depolarising 12; per amplitude: scale 4.
+// dephasing 2; per quad: depolarising 10; per amplitude: scale 4.
 // Double-float (packed: one instruction covers the real and imaginary
 // parts): complex df add 11, multiply by a df factor 8, complex df product
 // 27; in FP32-lane terms each packed instruction counts twice.
@@ -476,7 +502,7 @@ double vop_alu(const VOp& v, int nq, Arith a) {
   if (v.kind == FK_PHASE) return dim * f * (d ? 2 * 27 : 4);
   if (v.kind == FK_SCALE) return dim * (d ? 2 * 27 : 4);
   if (v.kind == FK_DEPH) return dim / 2 * (d ? 2 * 8 : 2);
-  if (v.kind == FK_DEPOL) return dim / 4 * (d ? 2 * (2 * 27 + 2 * 8) : 12);
+  if (v.kind == FK_DEPOL) return dim / 4 * (d ? 2 * (2 * 27 + 2 * 8) : 10);
   return 0;
 }
 
@@ -514,6 +540,7 @@ void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, RegPlan& 
   for (const GateOp& op : q) expand(r, op, vops);
   out.vops = int64_t(vops.size());
   merge_phases(vops, r.nq);
+  if (r.density) fold_dephasing(vops);
   const int64_t cap = env.max_fused_ops > 0 ? std::min<int64_t>(env.max_fused_ops, kMaxPassOps)
                                             : kMaxPassOps;
   const std::vector<Pass> passes = plan(vops, r.nq, k, L, cap, out.arith == Arith::F64 ? 1000 : 80);
