@@ -57,8 +57,12 @@ void need(const void* p, const char* what) {
 }
 
 void apply(Reg& r, const GateOp& op) {
-  if (r.env->fusion) r.queue.push_back(op);
-  else launch_op(*r.env, r, op);
+  if (r.env->fusion) {
+    r.queue.push_back(op);
+  } else {
+    launch_op(*r.env, r, op);
+    note_mixing(r, op);
+  }
 }
 
 void* dev_alloc(Env& env, size_t bytes) {
@@ -95,6 +99,7 @@ void ensure_stage(Env& env) {
 
 void init_zero(Reg& r) {
   r.queue.clear();
+  r.zero_bits = r.nq >= 64 ? ~uint64_t(0) : (uint64_t(1) << r.nq) - 1;
   const size_t amp = r.prec == QS_C128 ? sizeof(double2) : sizeof(float2);
   QS_CUDA(cudaMemsetAsync(r.d, 0, size_t(r.dim) * amp, r.env->stream));
   if (r.prec == QS_C128) {
@@ -360,6 +365,7 @@ int initPlusState(Qureg q) {
     // |+>^n: every amplitude 2^(-n/2); |+><+|^N: every entry 2^(-N).
     const double v = r.density ? std::ldexp(1.0, -r.n) : 1.0 / std::sqrt(double(r.dim));
     launch_fill(*r.env, r, v, 0.0);
+    r.zero_bits = 0;
   });
 }
 
@@ -396,6 +402,7 @@ int setAmps(Qureg q, const Complex* src, int64_t start, int64_t count) {
     if (start < 0 || count < 0 || start > r.dim || count > r.dim - start)
       fail(QS_E_ARG, "amplitude range out of bounds");
     flush(r);
+    r.zero_bits = 0;
     Env& env = *r.env;
     if (r.prec == QS_C128) {
       QS_CUDA(cudaMemcpyAsync(static_cast<double2*>(r.d) + start, src, size_t(count) * 16,
@@ -433,7 +440,10 @@ int getQuregInfo(Qureg q, int* numQubits, int* isDensity, int* precision, void**
     if (numQubits) *numQubits = r.n;
     if (isDensity) *isDensity = r.density ? 1 : 0;
     if (precision) *precision = r.prec;
-    if (devicePtr) *devicePtr = r.d;
+    if (devicePtr) {
+      *devicePtr = r.d;
+      r.zero_bits = 0;  // the caller may write the amplitudes
+    }
   });
 }
 

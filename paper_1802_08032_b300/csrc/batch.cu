@@ -153,7 +153,11 @@ void build(Batch& b) {
   std::vector<RegPlan> plans(b.regs.size());
   size_t maxp = 0;
   for (size_t r = 0; r < b.regs.size(); ++r) {
-    build_plan(*b.regs[r], b.circuits[r], b.k_req, plans[r]);
+    // every replay starts from |0...0> (the first pass generates it)
+    const int nq = b.regs[r]->nq;
+    build_plan(*b.regs[r], b.circuits[r], b.k_req, nq >= 64 ? ~uint64_t(0) : (uint64_t(1) << nq) - 1,
+               plans[r]);
+    b.regs[r]->zero_bits = 0;  // the register's contents are the batch's from now on
     if (!plans[r].fps.empty()) plans[r].fps[0].init = 1;
     maxp = std::max(maxp, plans[r].fps.size());
   }
@@ -321,7 +325,11 @@ int createBatch(QuESTEnv e, const Qureg* regs, int count, int tileQubits, QSBatc
 }
 
 int runBatch(QSBatch h) {
-  return guarded_call([&] { run(batch_of(h)); });
+  return guarded_call([&] {
+    Batch& b = batch_of(h);
+    for (Reg* r : b.regs) r->zero_bits = 0;
+    run(b);
+  });
 }
 
 int getBatchNorms(QSBatch h, double* out) {

@@ -66,7 +66,10 @@ void flush(Reg& r) {
   q.swap(r.queue);
   Env& env = *r.env;
   if (!fusable(r)) {
-    for (const GateOp& op : q) launch_op(env, r, op);
+    for (const GateOp& op : q) {
+      launch_op(env, r, op);
+      note_mixing(r, op);
+    }
     return;
   }
   // Multi-target gates run as their own passes; the gates between them form
@@ -74,16 +77,19 @@ void flush(Reg& r) {
   std::vector<RegPlan> plans;
   std::vector<int> after;  // index into q of the multi-target gate following each plan, or -1
   std::vector<GateOp> seg;
+  // the known-zero bits flow through the plans and the multi-target gates
   auto close = [&](int next) {
     if (!seg.empty()) {
       plans.emplace_back();
-      build_plan(r, seg, 0, plans.back());
+      build_plan(r, seg, 0, r.zero_bits, plans.back());
+      r.zero_bits = plans.back().zero_out;
       after.push_back(next);
       seg.clear();
     } else if (next >= 0) {
       plans.emplace_back();  // empty plan: only the multi-target gate
       after.push_back(next);
     }
+    if (next >= 0) note_mixing(r, q[size_t(next)]);
   };
   for (size_t i = 0; i < q.size(); ++i) {
     if (q[i].k == OpK::MULTI) close(int(i));

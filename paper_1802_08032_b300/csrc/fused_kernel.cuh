@@ -115,6 +115,7 @@ struct PlainArith {
     w.y = v.x;
     return w;
   }
+
   __device__ static Cplx scale(const Cplx& v, const FOp& op, int e) {
     const R f = cf(op, e);
     Cplx w;
@@ -483,11 +484,13 @@ __device__ __forceinline__ void process_tile(typename A::Store* __restrict__ g, 
     if (!GENERAL || int(threadIdx.x) < active) {
       const FStage& st = m.st[s];
       uint32_t poff[R];
-      uint32_t pm = 0;
+      uint32_t pm = 0, cpm = 0;
 #pragma unroll
       for (int i = 0; i < R; ++i) {
         poff[i] = 1u << st.pbits[i];
         pm |= poff[i];
+        // register bits in st.copy start as copies of their bit-0 half
+        if ((st.copy >> i) & 1u) cpm |= poff[i];
       }
       // tlocal: threadIdx with a zero bit inserted at each register-bit
       // position (positions ascending), i.e. its bits spread over the local
@@ -505,7 +508,7 @@ __device__ __forceinline__ void process_tile(typename A::Store* __restrict__ g, 
 #pragma unroll
         for (int i = 0; i < R; ++i)
           if (j & (1 << i)) off |= poff[i];
-        v[j] = m.tile[tlocal | off];
+        v[j] = m.tile[tlocal | (off & ~cpm)];
       }
       // Sign flips (CZ, multi-controlled phase flips) commute with every
       // diagonal op, and with a pair update on register bit i whenever the

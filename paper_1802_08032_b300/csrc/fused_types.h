@@ -73,7 +73,13 @@ struct FOp {
 static_assert(sizeof(FOp) == 88, "FOp layout");
 
 struct FStage {
-  uint8_t pbits[8];          // local positions of the register bits (R used)
+  uint8_t pbits[7];          // local positions of the register bits (R used)
+  // Register bits whose bit-1 amplitudes are loaded as copies of the bit-0
+  // ones: an H / sqrt(X) / sqrt(Y) on a bit whose bit-1 amplitudes are all
+  // 0 maps (x, 0) to (x, x) (unscaled; sqrt(X) then multiplies the copy by
+  // -i or i, as separate ops).  Every op of the stage before it leaves that
+  // bit alone, so the copy can be made when the stage loads its amplitudes.
+  uint8_t copy;
   int32_t op_begin, op_end;  // relative to the pass's first op
 };
 

@@ -21,6 +21,7 @@ struct RegPlan {
   std::vector<double> flops;  // algorithmic flops per pass
   std::vector<double> alu;    // arithmetic instructions per pass (kernel precision)
   int64_t vops = 0;           // vector operations planned
+  uint64_t zero_out = 0;      // bits known to hold only zeros after the plan
 };
 
 // Tile parameters per precision: R register bits, maximum k, low qubits L.
@@ -33,6 +34,8 @@ Arith arith_of(const Reg& r);
 
 // Plans q for register r with tile size k (0 = the library default / the
 // env's tile_qubits option).
-void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, RegPlan& out);
+// zero_in: bits known to hold only zeros before q (see Reg::zero_bits); the
+// bits still known zero after q are returned in out.zero_out.
+void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, uint64_t zero_in, RegPlan& out);
 
 }  // namespace qs

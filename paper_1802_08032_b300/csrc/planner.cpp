@@ -25,6 +25,7 @@ namespace {
 struct VOp {
   FKind kind;
   bool conj = false;
+  bool spread = false;   // H / sqrt(X) / sqrt(Y) on a bit whose bit-1 amplitudes are all 0
   int b0 = -1, b1 = -1;  // pair target (b0); DEPOL row/column; DEPH the two compared bits
   uint64_t cond = 0;     // bits that must all be 1 (controls; PHASE/SIGN diagonal support)
   double c[8] = {};
@@ -182,6 +183,54 @@ struct Pass {
   std::vector<int> q;  // tile qubits, ascending
   std::vector<VOp> ops;
 };
+
+// Bits known to hold only zeros (every amplitude with the bit set is 0, see
+// Reg::zero_bits) simplify what follows: a phase, sign flip or
+// multiplication by i conditioned on such a bit touches only zeros and is
+// dropped, as is a dephasing whose two bits are both such bits and a pair
+// update with such a bit among its controls; H, sqrt(X) and sqrt(Y) on such
+// a bit map (x, 0) to (x, x), (x, -i x) or (x, i x) (unscaled): the op is
+// marked as a copy (made when its stage loads the amplitudes) followed, for
+// sqrt(X), by a multiplication by i and (for -i) a sign flip on the bit.
+// Every operation that mixes amplitudes along a bit clears it.
+void apply_zero_bits(std::vector<VOp>& ops, uint64_t& zero) {
+  std::vector<VOp> out;
+  out.reserve(ops.size());
+  for (VOp v : ops) {
+    const uint64_t x = v.xmask();
+    if (v.kind == FK_PHASE || v.kind == FK_SIGN || v.kind == FK_MULI) {
+      if ((v.cond & zero) == 0) out.push_back(v);
+      continue;
+    }
+    if (v.kind == FK_DEPH) {
+      const uint64_t both = (uint64_t(1) << v.b0) | (uint64_t(1) << v.b1);
+      if ((zero & both) != both) out.push_back(v);
+      continue;
+    }
+    if (v.kind <= FK_X) {
+      if (v.cond & zero) continue;
+      if ((zero & x) && v.cond == 0 && (v.kind == FK_H || v.kind == FK_SX || v.kind == FK_SY)) {
+        v.spread = true;
+        zero &= ~x;
+        out.push_back(v);
+        if (v.kind == FK_SX) {
+          VOp m;
+          m.kind = FK_MULI;
+          m.cond = x;
+          out.push_back(m);
+          if (!v.conj) {
+            m.kind = FK_SIGN;
+            out.push_back(m);
+          }
+        }
+        continue;
+      }
+    }
+    zero &= ~x;
+    out.push_back(v);
+  }
+  ops.swap(out);
+}
 
 // Consecutive phases on one bit merge into one operation (T^2 = S is a
 // multiplication by i, T^4 = Z a sign flip: neither needs arithmetic).  A
@@ -425,6 +474,10 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
     bool sign_seen = false;
     for (size_t o = i; o < j; ++o) {
       const VOp& v = p.ops[o];
+      if (v.spread) {  // a copy made when the stage loads its amplitudes
+        st.copy |= uint8_t(1u << idx[lpos[v.b0]]);
+        continue;
+      }
       FOp f{};
       f.kind = v.kind;
       f.conj = v.conj ? 1 : 0;
@@ -476,6 +529,7 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
 }
 
 double vop_flops(const VOp& v, int nq) {
+  if (v.spread) return 0;
   const double dim = std::ldexp(1.0, nq), f = std::ldexp(1.0, -popc(v.cond));
   static const double pair_flops[5] = {28, 4, 4, 4, 0};  // H, sqrt(X), sqrt(Y) unscaled
   if (v.kind <= FK_X) return dim / 2 * f * pair_flops[v.kind];
@@ -494,6 +548,7 @@ double vop_flops(const VOp& v, int nq) {
 // parts): complex df add 11, multiply by a df factor 8, complex df product
 // 27; in FP32-lane terms each packed instruction counts twice.
 double vop_alu(const VOp& v, int nq, Arith a) {
+  if (v.spread) return 0;
   const double dim = std::ldexp(1.0, nq), f = std::ldexp(1.0, -popc(v.cond));
   const bool d = a == Arith::DF;
   static const double plain_pair[5] = {16, 4, 4, 4, 0};
@@ -508,6 +563,22 @@ double vop_alu(const VOp& v, int nq, Arith a) {
 
 }  // namespace
 
+void note_mixing(Reg& r, const GateOp& op) {
+  uint64_t x = 0;
+  switch (op.k) {
+    case OpK::GEN: case OpK::H: case OpK::SX: case OpK::SY: case OpK::X: case OpK::DEPOL:
+      x = uint64_t(1) << op.t;
+      break;
+    case OpK::MULTI:
+      for (int i = 0; i < op.nt; ++i) x |= uint64_t(1) << op.tg[i];
+      break;
+    default:
+      break;  // diagonal
+  }
+  if (r.density) x |= x << r.n;
+  r.zero_bits &= ~x;
+}
+
 TileCfg tile_cfg(const Reg& r) { return r.prec == QS_C128 ? TileCfg{4, 12, 3} : TileCfg{5, 13, 4}; }
 
 bool fusable(const Reg& r) {
@@ -520,7 +591,7 @@ Arith arith_of(const Reg& r) {
   return r.env->arith == 1 ? Arith::DF : Arith::F64;
 }
 
-void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, RegPlan& out) {
+void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, uint64_t zero_in, RegPlan& out) {
   const Env& env = *r.env;
   const TileCfg cfg = tile_cfg(r);
   int k = std::min(cfg.kmax, r.nq);
@@ -539,6 +610,9 @@ void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, RegPlan& 
   vops.reserve(q.size() * 2);
   for (const GateOp& op : q) expand(r, op, vops);
   out.vops = int64_t(vops.size());
+  uint64_t zero = zero_in;
+  apply_zero_bits(vops, zero);
+  out.zero_out = zero;
   merge_phases(vops, r.nq);
   if (r.density) fold_dephasing(vops);
   const int64_t cap = env.max_fused_ops > 0 ? std::min<int64_t>(env.max_fused_ops, kMaxPassOps)

@@ -84,6 +84,11 @@ struct Reg {
   void* d = nullptr;  // amplitudes (double2 or float2)
   size_t bytes = 0;
   std::vector<GateOp> queue;  // gates waiting for a fused flush
+  // Bits b of the stored index for which every amplitude with bit b set is
+  // exactly 0: the register was zeroed and nothing since has mixed
+  // amplitudes along b.  The planner turns gates on such bits into copies
+  // or drops them.  Cleared whenever amplitudes are written from outside.
+  uint64_t zero_bits = 0;
 };
 
 struct Env {
@@ -161,6 +166,10 @@ void convert_op(const Reg& r, const QSOp& o, std::vector<GateOp>& out);
 // Validates bulk-call ops for a register of r's shape into internal ops
 // (oplist.cpp); fails with the first bad op's code.
 void convert_ops(const Reg& r, const QSOp* ops, int64_t n, std::vector<GateOp>& out);
+
+// Clears the bits of r.zero_bits that op mixes (planner.cpp): call after
+// launching op outside a fused plan.
+void note_mixing(Reg& r, const GateOp& op);
 
 // Entry points of the kernel layer (implemented in the .cu files).
 void launch_op(Env& env, Reg& r, const GateOp& op);

@@ -10,7 +10,7 @@
 // writes the final 2^nq amplitudes (re, im doubles) to stdout after a line
 // "STATE".  The test compares that state with the oracle.
 //
-// usage: planner_check n density prec arith k_req emulate
+// usage: planner_check n density prec arith k_req emulate [fresh]
 #include <algorithm>
 #include <complex>
 #include <cstdio>
@@ -71,6 +71,7 @@ static void check_plan(const RegPlan& pl, int nq) {
       CHECK(st.op_begin == next && st.op_end >= st.op_begin, "pass %zu stage %d: op range", pi, s);
       next = st.op_end;
       uint32_t pm = 0;
+      CHECK((st.copy >> R) == 0, "pass %zu stage %d: copy bits", pi, s);
       for (int i = 0; i < R; ++i) {
         CHECK(st.pbits[i] < k, "pass %zu stage %d: register position %d >= k", pi, s, st.pbits[i]);
         if (i > 0) CHECK(st.pbits[i] > st.pbits[i - 1], "pass %zu stage %d: positions not ascending", pi, s);
@@ -142,7 +143,9 @@ static std::vector<cd> emulate(const RegPlan& pl, int nq) {
           };
           const int nj = 1 << R;
           cd v[32];
-          for (int j = 0; j < nj; ++j) v[j] = t[loc(j)];
+          // copy bits: their bit-1 amplitudes start as the bit-0 ones (the
+          // planner's claim that the bit-1 ones are 0 is not used: overwritten)
+          for (int j = 0; j < nj; ++j) v[j] = t[loc(j & ~int(st.copy))];
           uint32_t flips = 0;
           auto flush_flips = [&] {
             for (int j = 0; j < nj; ++j)
@@ -231,6 +234,7 @@ int main(int argc, char** argv) {
   }
   const int n = std::atoi(argv[1]), density = std::atoi(argv[2]), prec = std::atoi(argv[3]);
   const int arith = std::atoi(argv[4]), k_req = std::atoi(argv[5]), emu = std::atoi(argv[6]);
+  const int fresh = argc > 7 ? std::atoi(argv[7]) : 1;
   Env env;
   env.arith = arith;
   Reg r;
@@ -247,7 +251,8 @@ int main(int argc, char** argv) {
   try {
     std::vector<GateOp> g;
     convert_ops(r, ops.data(), int64_t(ops.size()), g);
-    build_plan(r, g, k_req, pl);
+    // a zeroed register unless told otherwise (argument 7 = 0)
+    build_plan(r, g, k_req, fresh ? (uint64_t(1) << r.nq) - 1 : 0, pl);
   } catch (const Error& e) {
     std::printf("ERROR %d %s\n", e.code, e.msg.c_str());
     return 1;
