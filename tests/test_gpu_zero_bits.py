@@ -1,0 +1,173 @@
+"""GPU tests of the known-zero tracking: gates on qubits still in |0> since the
+register was zeroed are planned as copies or dropped, so every path that
+changes amplitudes must keep that knowledge right.  Each case runs a gate
+list through the API paths that touch the tracking and compares the final
+state with the oracle."""
+import numpy as np
+import pytest
+
+from paper_1802_08032_b300 import circuits as C
+from oracle import oracle as O
+from gpu_helpers import AMP_TOL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Q():
+    from paper_1802_08032_b300 import qsim
+    return qsim
+
+
+@pytest.fixture
+def env(Q):
+    e = Q.createQuESTEnv()
+    yield e
+    Q.destroyQuESTEnv(e)
+
+
+def rand_state(n, seed):
+    rng = np.random.default_rng(seed)
+    a = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    return a / np.linalg.norm(a)
+
+
+FIRST = [C.Op("T", (2,)), C.Op("CZ", (1, 3)), C.Op("H", (1,)), C.Op("SX", (4,)), C.Op("SY", (0,)),
+         C.Op("MCPF", (), (0, 5, 6)), C.Op("T", (4,)), C.Op("CNOT", (6,), (1,)), C.Op("H", (6,))]
+
+
+@pytest.mark.parametrize("prec", [128, 64])
+def test_fresh_register(Q, env, prec):
+    n = 9
+    q = Q.createQureg(n, prec, env)
+    Q.applyCircuit(q, FIRST)
+    got = Q.copyStateToHost(q)
+    Q.destroyQureg(q)
+    assert np.max(np.abs(got - O.run_circuit(n, FIRST).a)) <= AMP_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [128, 64])
+def test_after_setamps_and_plus_state(Q, env, prec):
+    n = 9
+    q = Q.createQureg(n, prec, env)
+    psi = rand_state(n, 3)
+    Q.setAmps(q, psi)
+    Q.applyCircuit(q, FIRST)
+    got = Q.copyStateToHost(q)
+    ref = O.State(n, amps=psi).run(FIRST).a
+    assert np.max(np.abs(got - ref)) <= AMP_TOL[prec]
+    Q.initPlusState(q)
+    Q.applyCircuit(q, FIRST)
+    got = Q.copyStateToHost(q)
+    ref = O.State(n, amps=np.full(1 << n, 2 ** (-n / 2), dtype=np.complex128)).run(FIRST).a
+    Q.destroyQureg(q)
+    assert np.max(np.abs(got - ref)) <= AMP_TOL[prec]
+
+
+def test_unfused_then_fused(Q, env):
+    n = 9
+    q = Q.createQureg(n, 128, env)
+    Q.setEnvOption(env, "fusion", 0)
+    Q.hadamard(q, 2)
+    Q.sqrtX(q, 5)
+    Q.setEnvOption(env, "fusion", 1)
+    ops = [C.Op("H", (2,)), C.Op("T", (5,)), C.Op("H", (5,)), C.Op("CZ", (2, 5))] + FIRST
+    Q.applyCircuit(q, ops)
+    got = Q.copyStateToHost(q)
+    Q.destroyQureg(q)
+    ref = O.run_circuit(n, [C.Op("H", (2,)), C.Op("SX", (5,))] + ops).a
+    assert np.max(np.abs(got - ref)) <= AMP_TOL[128]
+
+
+def test_multi_target_on_fresh_qubits(Q, env):
+    n = 8
+    rng = np.random.default_rng(5)
+    m = rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4))
+    U, _ = np.linalg.qr(m)
+    q = Q.createQureg(n, 128, env)
+    Q.hadamard(q, 0)
+    Q.twoQubitUnitary(q, 3, 6, U)
+    Q.applyCircuit(q, [C.Op("H", (3,)), C.Op("T", (6,)), C.Op("SX", (6,)), C.Op("H", (7,))])
+    got = Q.copyStateToHost(q)
+    Q.destroyQureg(q)
+    ref = O.State(n)
+    ref.gate(0, O.MAT_H)
+    ref.multi((3, 6), U)
+    ref.run([C.Op("H", (3,)), C.Op("T", (6,)), C.Op("SX", (6,)), C.Op("H", (7,))])
+    assert np.max(np.abs(got - ref.a)) <= AMP_TOL[128]
+
+
+def test_collapse_then_gates_and_rezero(Q, env):
+    n = 7
+    q = Q.createQureg(n, 128, env)
+    ref = O.State(n)
+    pre = [C.Op("H", (0,)), C.Op("CNOT", (1,), (0,))]
+    Q.applyCircuit(q, pre)
+    ref.run(pre)
+    p = Q.collapseToOutcome(q, 1, 1)
+    assert abs(p - ref.collapse(1, 1)) <= 1e-13
+    post = [C.Op("H", (4,)), C.Op("T", (1,)), C.Op("SY", (1,)), C.Op("CZ", (0, 4))]
+    Q.applyCircuit(q, post)
+    ref.run(post)
+    assert np.max(np.abs(Q.copyStateToHost(q) - ref.a)) <= AMP_TOL[128]
+    Q.initZeroState(q)
+    Q.applyCircuit(q, FIRST[:6])
+    got = Q.copyStateToHost(q)
+    Q.destroyQureg(q)
+    assert np.max(np.abs(got - O.run_circuit(n, FIRST[:6]).a)) <= AMP_TOL[128]
+
+
+def test_density_matrix_fresh_and_after_plus(Q, env):
+    N = 4
+    ops = C.with_noise([C.Op("T", (1,)), C.Op("H", (1,)), C.Op("SX", (2,)), C.Op("CZ", (1, 2)),
+                        C.Op("T", (3,))], 0.02, 0.01)
+    d = Q.createDensityQureg(N, 128, env)
+    Q.applyCircuit(d, ops)
+    got = Q.copyStateToHost(d)
+    assert np.max(np.abs(got - O.run_circuit(N, ops, density=True).a)) <= AMP_TOL[128]
+    Q.initPlusState(d)
+    Q.applyCircuit(d, ops)
+    got = Q.copyStateToHost(d)
+    Q.destroyQureg(d)
+    plus = np.full(1 << (2 * N), 2.0 ** -N, dtype=np.complex128)
+    ref = O.State(N, density=True, amps=plus).run(ops).a
+    assert np.max(np.abs(got - ref)) <= AMP_TOL[128]
+
+
+def test_gates_after_batch_replay(Q, env):
+    sizes = [6, 9]
+    regs = [Q.createQureg(n, 128, env) for n in sizes]
+    circs = [C.random_circuit(n, 5, 60 + n, extras=True) for n in sizes]
+    try:
+        for q, ops in zip(regs, circs):
+            Q.applyCircuit(q, ops)
+        b = Q.createBatch(env, regs)
+        Q.runBatch(b)
+        Q.runBatch(b)
+        Q.destroyBatch(b)
+        more = [C.Op("H", (2,)), C.Op("T", (3,)), C.Op("SX", (3,))]
+        for q, n, ops in zip(regs, sizes, circs):
+            Q.applyCircuit(q, more)
+            got = Q.copyStateToHost(q)
+            assert np.max(np.abs(got - O.run_circuit(n, ops + more).a)) <= AMP_TOL[128], n
+    finally:
+        for q in regs:
+            Q.destroyQureg(q)
+
+
+def test_raw_pointer_clears_tracking(Q, env):
+    """A caller may write the amplitudes through getQuregInfo's pointer."""
+    rt = pytest.importorskip("cuda.bindings.runtime")
+    n = 6
+    q = Q.createQureg(n, 128, env)
+    ptr = Q.getQuregInfo(q)["devicePtr"]
+    Q.syncQuESTEnv(env)
+    psi = rand_state(n, 9)
+    host = np.ascontiguousarray(psi)  # interleaved (re, im) doubles, the register's layout
+    (err,) = rt.cudaMemcpy(ptr, host.ctypes.data, host.nbytes, rt.cudaMemcpyKind.cudaMemcpyHostToDevice)
+    assert int(err) == 0
+    ops = [C.Op("H", (1,)), C.Op("T", (2,)), C.Op("CZ", (2, 4))]
+    Q.applyCircuit(q, ops)
+    got = Q.copyStateToHost(q)
+    Q.destroyQureg(q)
+    assert np.max(np.abs(got - O.State(n, amps=psi).run(ops).a)) <= AMP_TOL[128]
