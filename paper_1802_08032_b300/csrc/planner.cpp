@@ -302,6 +302,78 @@ void merge_phases(std::vector<VOp>& ops, int nq) {
   ops.swap(out);
 }
 
+// The 2x2 matrix an op applies along bit b (row-major), when it is a
+// single-bit unitary acting on b alone: an uncontrolled pair update on b
+// (true matrices, with the scale factors the engine's H / sqrt(X) / sqrt(Y)
+// leave out; conjugated for density-matrix column updates) or a phase,
+// multiplication by i or sign flip conditioned on b alone.
+bool single_bit_matrix(const VOp& v, int b, std::complex<double> m[4]) {
+  using C = std::complex<double>;
+  const uint64_t bit = uint64_t(1) << b;
+  if (v.kind <= FK_SY && v.cond == 0 && v.b0 == b && !v.spread) {
+    const double s = std::sqrt(0.5);
+    if (v.kind == FK_GEN) {
+      for (int e = 0; e < 4; ++e) m[e] = C(v.c[2 * e], v.c[2 * e + 1]);
+    } else if (v.kind == FK_H) {
+      m[0] = s; m[1] = s; m[2] = s; m[3] = -s;
+    } else if (v.kind == FK_SX) {
+      m[0] = C(0.5, 0.5); m[1] = C(0.5, -0.5); m[2] = C(0.5, -0.5); m[3] = C(0.5, 0.5);
+    } else {  // sqrt(Y)
+      m[0] = C(0.5, 0.5); m[1] = C(-0.5, -0.5); m[2] = C(0.5, 0.5); m[3] = C(0.5, 0.5);
+    }
+    if (v.conj)
+      for (int e = 0; e < 4; ++e) m[e] = std::conj(m[e]);
+    return true;
+  }
+  if (v.cond == bit && (v.kind == FK_PHASE || v.kind == FK_MULI || v.kind == FK_SIGN)) {
+    m[0] = 1;
+    m[1] = 0;
+    m[2] = 0;
+    m[3] = v.kind == FK_PHASE ? C(v.c[0], v.c[1]) : (v.kind == FK_MULI ? C(0, 1) : C(-1, 0));
+    return true;
+  }
+  return false;
+}
+
+// An uncontrolled general 2x2 update absorbs the single-bit unitaries just
+// before it on its bit (every op in between leaves the bit alone, so they
+// commute): one general update costs the same as before, the absorbed ops
+// cost nothing.
+void absorb_into_general(std::vector<VOp>& ops) {
+  using C = std::complex<double>;
+  std::vector<bool> dead(ops.size(), false);
+  for (size_t i = 0; i < ops.size(); ++i) {
+    VOp& g = ops[i];
+    if (g.kind != FK_GEN || g.cond != 0) continue;
+    const int b = g.b0;
+    const uint64_t bit = uint64_t(1) << b;
+    C G[4];
+    single_bit_matrix(g, b, G);
+    bool changed = false;
+    for (size_t j = i; j-- > 0;) {
+      if (dead[j] || ((ops[j].xmask() | ops[j].zmask()) & bit) == 0) continue;
+      C M[4];
+      if (!single_bit_matrix(ops[j], b, M)) break;
+      const C P[4] = {G[0] * M[0] + G[1] * M[2], G[0] * M[1] + G[1] * M[3],
+                      G[2] * M[0] + G[3] * M[2], G[2] * M[1] + G[3] * M[3]};
+      for (int e = 0; e < 4; ++e) G[e] = P[e];
+      dead[j] = true;
+      changed = true;
+    }
+    if (changed) {
+      for (int e = 0; e < 4; ++e) {
+        g.c[2 * e] = G[e].real();
+        g.c[2 * e + 1] = G[e].imag();
+      }
+      g.conj = false;
+    }
+  }
+  size_t w = 0;
+  for (size_t i = 0; i < ops.size(); ++i)
+    if (!dead[i]) ops[w++] = ops[i];
+  ops.resize(w);
+}
+
 // A dephasing on qubit bits (t, t + N) only scales the entries whose row
 // and column bits differ; a depolarising quad on the same bits scales those
 // entries by its "off" factor and mixes the others.  When no operation
@@ -614,6 +686,7 @@ void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, uint64_t 
   apply_zero_bits(vops, zero);
   out.zero_out = zero;
   merge_phases(vops, r.nq);
+  absorb_into_general(vops);
   if (r.density) fold_dephasing(vops);
   const int64_t cap = env.max_fused_ops > 0 ? std::min<int64_t>(env.max_fused_ops, kMaxPassOps)
                                             : kMaxPassOps;
