@@ -108,6 +108,24 @@ struct PlainArith {
     }
     return w;
   }
+  // Shear along a register bit: MODE 0 (x - t y, y + t x), MODE 1
+  // (t x - y, x + t y), t = c0.
+  template <int MODE>
+  __device__ static void shear(Cplx& x, Cplx& y, const FOp& op) {
+    const R t = cf(op, 0);
+    const Cplx u = x;
+    if constexpr (MODE == 0) {
+      x.x = fma(-t, y.x, u.x);
+      x.y = fma(-t, y.y, u.y);
+      y.x = fma(t, u.x, y.x);
+      y.y = fma(t, u.y, y.y);
+    } else {
+      x.x = fma(t, u.x, -y.x);
+      x.y = fma(t, u.y, -y.y);
+      y.x = fma(t, y.x, u.x);
+      y.y = fma(t, y.y, u.y);
+    }
+  }
   // i v: a swap and a sign flip, no arithmetic
   __device__ static Cplx mul_i(const Cplx& v) {
     Cplx w;
@@ -191,6 +209,19 @@ struct DFArith {
   }
   __device__ static Cplx phase(const Cplx& v, const FOp& op) { return dfc2_cmul(v, cf(op, 0), cf(op, 1)); }
   __device__ static Cplx mul_i(const Cplx& v) { return mul_plus_i(v); }
+  template <int MODE>
+  __device__ static void shear(Cplx& x, Cplx& y, const FOp& op) {
+    const df t = cf(op, 0);
+    const float2 th = f2(t.hi, t.hi), tl = f2(t.lo, t.lo);
+    const Cplx u = x;
+    if constexpr (MODE == 0) {
+      x = dfc2_sub(u, dfc2_mulv(y, th, tl));
+      y = dfc2_add(y, dfc2_mulv(u, th, tl));
+    } else {
+      x = dfc2_sub(dfc2_mulv(u, th, tl), y);
+      y = dfc2_add(u, dfc2_mulv(y, th, tl));
+    }
+  }
   __device__ static Cplx negate(const Cplx& v) {
     return dfc2{mul2(v.hi, f2(-1.f, -1.f)), mul2(v.lo, f2(-1.f, -1.f))};
   }
@@ -230,6 +261,16 @@ __device__ __forceinline__ void phase_on_bit(typename A::Cplx (&v)[1 << R], cons
 #pragma unroll
   for (int j = 0; j < (1 << R); ++j)
     if (j & (1 << I)) v[j] = A::phase(v[j], op);
+}
+
+// Shear along register bit I (MODE as in Arith::shear).
+template <class A, int R, int I, int MODE>
+__device__ __forceinline__ void shear_on_bit(typename A::Cplx (&v)[1 << R], const FOp& op) {
+#pragma unroll
+  for (int j = 0; j < (1 << R); ++j) {
+    if (j & (1 << I)) continue;
+    A::template shear<MODE>(v[j], v[j | (1 << I)], op);
+  }
 }
 
 // i times the amplitudes with register bit I set.
@@ -306,6 +347,8 @@ __device__ __forceinline__ void run_op(typename A::Cplx (&v)[1 << R], const FOp&
     QS_BIT_CASES(FC_PHASE_BIT, (phase_on_bit<A, R, I>(v, op)))
     QS_PAIR_CASES(FC_DEPOL, (depol_on_bits<A, R, IA, IB>(v, op)))
     QS_BIT_CASES(FC_MULI_BIT, (muli_on_bit<A, R, I>(v)))
+    QS_BIT_CASES(FC_SHEAR, (shear_on_bit<A, R, I, 0>(v, op)))
+    QS_BIT_CASES(FC_SHEAR2, (shear_on_bit<A, R, I, 1>(v, op)))
     case FC_MULI_ALL * kCodeSlots:
 #pragma unroll
       for (int j = 0; j < (1 << R); ++j) v[j] = A::mul_i(v[j]);

@@ -31,7 +31,7 @@ struct VOp {
   double c[8] = {};
 
   uint64_t xmask() const {
-    if (kind <= FK_X) return uint64_t(1) << b0;
+    if (kind <= FK_X || kind == FK_SHEAR) return uint64_t(1) << b0;
     if (kind == FK_DEPOL) return (uint64_t(1) << b0) | (uint64_t(1) << b1);
     return 0;
   }
@@ -147,6 +147,8 @@ std::complex<double> dropped_factor(int e, int p, int q) {
 
 struct ScaleState {
   int e = 0, p = 0, q = 0;
+  std::complex<double> g{1.0, 0.0};  // factors left out by shears (see decompose_general)
+  int shears = 0;                    // their growth, at most sqrt 2 each
   int limit = 80;
 };
 
@@ -155,8 +157,13 @@ void add_scales(std::vector<VOp>& ops, ScaleState& st, bool last) {
   out.reserve(ops.size() + 2);
   int &e = st.e, &p = st.p, &q = st.q;
   auto flush_scale = [&] {
-    if (e == 0) return;
-    const std::complex<double> f = dropped_factor(e, p, q);
+    if (e == 0 && st.g == std::complex<double>(1.0, 0.0)) {
+      st.shears = 0;
+      return;
+    }
+    const std::complex<double> f = dropped_factor(e, p, q) * st.g;
+    st.g = 1.0;
+    st.shears = 0;
     VOp s;
     s.kind = FK_SCALE;
     s.c[0] = f.real();
@@ -172,8 +179,11 @@ void add_scales(std::vector<VOp>& ops, ScaleState& st, bool last) {
       ++e;
       if (v.conj) ++q;
       else ++p;
+    } else if (v.kind == FK_SHEAR) {
+      ++st.shears;
+      st.g *= std::complex<double>(v.c[2], v.c[3]);
     }
-    if (e >= st.limit) flush_scale();
+    if (e + st.shears >= st.limit) flush_scale();
   }
   if (last) flush_scale();
   ops.swap(out);
@@ -374,6 +384,66 @@ void absorb_into_general(std::vector<VOp>& ops) {
   ops.resize(w);
 }
 
+// An uncontrolled general 2x2 update U = [[a, b], [c, d]] factors exactly as
+// g diag(1, p1) R diag(1, p2), with unit phases g = a/|a|,
+// p1 = (c/|c|) conj(g), p2 = -(b/|b|) conj(g) and the real rotation
+// R = [[|a|, -|b|], [|b|, |a|]] = m [[1, -t], [t, 1]] (m = |a| >= |b|,
+// t = |b|/|a|) or m [[t, -1], [1, t]] (m = |b|, t = |a|/|b|).  The rotation
+// runs as a shear with one FMA per output component and g m joins the
+// factors applied once per plan; the two phases cost what half a general
+// update does and may merge with neighbouring phases.  Together: 12 FP64
+// operations per pair instead of 16.  Matrices whose factors do not
+// reproduce them to 1e-14 (not unitary to that precision, or |a| or |b| 0)
+// stay general.
+void decompose_general(std::vector<VOp>& ops) {
+  using C = std::complex<double>;
+  std::vector<VOp> out;
+  out.reserve(ops.size() + ops.size() / 2);
+  for (const VOp& v : ops) {
+    if (v.kind != FK_GEN || v.cond != 0) {
+      out.push_back(v);
+      continue;
+    }
+    C U[4];
+    single_bit_matrix(v, v.b0, U);
+    const double na = std::abs(U[0]), nb = std::abs(U[1]), nc = std::abs(U[2]);
+    if (!(na > 1e-150 && nb > 1e-150 && nc > 1e-150)) {
+      out.push_back(v);
+      continue;
+    }
+    const C g = U[0] / na, p1 = (U[2] / nc) * std::conj(g), p2 = -(U[1] / nb) * std::conj(g);
+    // reproduce U from the factors (R uses |b| for both off-diagonal magnitudes)
+    const C r01 = -g * nb * p2, r10 = g * p1 * nb, r11 = g * p1 * na * p2;
+    if (std::abs(r01 - U[1]) > 1e-14 || std::abs(r10 - U[2]) > 1e-14 || std::abs(r11 - U[3]) > 1e-14) {
+      out.push_back(v);
+      continue;
+    }
+    const uint64_t bit = uint64_t(1) << v.b0;
+    auto phase = [&](C z) {
+      if (z == C(1.0, 0.0)) return;
+      VOp ph;
+      ph.kind = FK_PHASE;
+      ph.cond = bit;
+      ph.c[0] = z.real();
+      ph.c[1] = z.imag();
+      out.push_back(ph);
+    };
+    phase(p2);
+    VOp sh;
+    sh.kind = FK_SHEAR;
+    sh.b0 = v.b0;
+    const bool by_a = na >= nb;
+    sh.c[0] = by_a ? nb / na : na / nb;  // t <= 1
+    sh.c[1] = by_a ? 0.0 : 1.0;          // form
+    const C f = g * (by_a ? na : nb);
+    sh.c[2] = f.real();
+    sh.c[3] = f.imag();
+    out.push_back(sh);
+    phase(p1);
+  }
+  ops.swap(out);
+}
+
 // A dephasing on qubit bits (t, t + N) only scales the entries whose row
 // and column bits differ; a depolarising quad on the same bits scales those
 // entries by its "off" factor and mixes the others.  When no operation
@@ -472,6 +542,7 @@ int dispatch_code(const FOp& f) {
       if (popc(f.rmask) == 1) return FC_PHASE_BIT * S + __builtin_ctz(f.rmask);
       return FC_PHASE_MASK * S;
     case FK_SIGN: return FC_SIGN * S;
+    case FK_SHEAR: return (f.i1 ? FC_SHEAR2 : FC_SHEAR) * S + f.i0;  // i1: the form
     case FK_MULI:
       if (f.rmask == 0) return FC_MULI_ALL * S;
       if (popc(f.rmask) == 1) return FC_MULI_BIT * S + __builtin_ctz(f.rmask);
@@ -553,8 +624,9 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
       FOp f{};
       f.kind = v.kind;
       f.conj = v.conj ? 1 : 0;
-      if (v.kind <= FK_X || v.kind == FK_DEPOL) f.i0 = uint8_t(idx[lpos[v.b0]]);
+      if (v.kind <= FK_X || v.kind == FK_SHEAR || v.kind == FK_DEPOL) f.i0 = uint8_t(idx[lpos[v.b0]]);
       if (v.kind == FK_DEPOL) f.i1 = uint8_t(idx[lpos[v.b1]]);
+      if (v.kind == FK_SHEAR) f.i1 = v.c[1] != 0.0 ? 1 : 0;
       for (int b = 0; b < 64; ++b) {
         if (!((v.cond >> b) & 1)) continue;
         if (lpos[b] < 0) f.gmask |= uint64_t(1) << b;
@@ -579,7 +651,7 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
       }
       f.code = uint16_t(dispatch_code(f));
       if (f.lmask != 0 || f.gmask != 0) f.flags |= FF_COND;
-      if (sign_seen && (v.kind <= FK_X || v.kind == FK_DEPOL)) f.flags |= FF_FLIP;
+      if (sign_seen && (v.kind <= FK_X || v.kind == FK_SHEAR || v.kind == FK_DEPOL)) f.flags |= FF_FLIP;
       if (v.kind == FK_DEPOL) f.flags |= FF_TWO;
       const bool deferred_sign = v.kind == FK_SIGN;
       if (deferred_sign) sign_seen = true;
@@ -605,6 +677,7 @@ double vop_flops(const VOp& v, int nq) {
   const double dim = std::ldexp(1.0, nq), f = std::ldexp(1.0, -popc(v.cond));
   static const double pair_flops[5] = {28, 4, 4, 4, 0};  // H, sqrt(X), sqrt(Y) unscaled
   if (v.kind <= FK_X) return dim / 2 * f * pair_flops[v.kind];
+  if (v.kind == FK_SHEAR) return dim / 2 * 8;
   if (v.kind == FK_PHASE) return dim * f * 6;
   if (v.kind == FK_SCALE) return dim * 6;
   if (v.kind == FK_DEPH) return dim / 2 * 2;
@@ -614,7 +687,7 @@ double vop_flops(const VOp& v, int nq) {
 
 // Arithmetic instructions (add, multiply, FMA: 1 each) one vector op issues,
 // in the precision of the kernel's arithmetic.  Plain FP32/FP64 per pair:
-// general 16, H / sqrt(X) / sqrt(Y) 4; per touched amplitude: phase 4,
+// general 16, H / sqrt(X) / sqrt(Y) / shear 4; per touched amplitude: phase 4,
 // dephasing 2; per quad: depolarising 10; per amplitude: scale 4.
 // Double-float (packed: one instruction covers the real and imaginary
 // parts): complex df add 11, multiply by a df factor 8, complex df product
@@ -626,6 +699,7 @@ double vop_alu(const VOp& v, int nq, Arith a) {
   static const double plain_pair[5] = {16, 4, 4, 4, 0};
   static const double df_pair[5] = {2 * 130, 2 * 22, 2 * 22, 2 * 22, 0};
   if (v.kind <= FK_X) return dim / 2 * f * (d ? df_pair[v.kind] : plain_pair[v.kind]);
+  if (v.kind == FK_SHEAR) return dim / 2 * (d ? 2 * 2 * (8 + 11) : 4);
   if (v.kind == FK_PHASE) return dim * f * (d ? 2 * 27 : 4);
   if (v.kind == FK_SCALE) return dim * (d ? 2 * 27 : 4);
   if (v.kind == FK_DEPH) return dim / 2 * (d ? 2 * 8 : 2);
@@ -687,6 +761,8 @@ void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, uint64_t 
   out.zero_out = zero;
   merge_phases(vops, r.nq);
   absorb_into_general(vops);
+  decompose_general(vops);
+  merge_phases(vops, r.nq);
   if (r.density) fold_dephasing(vops);
   const int64_t cap = env.max_fused_ops > 0 ? std::min<int64_t>(env.max_fused_ops, kMaxPassOps)
                                             : kMaxPassOps;

@@ -80,12 +80,15 @@ static void check_plan(const RegPlan& pl, int nq) {
       for (int o = st.op_begin; o < st.op_end; ++o) {
         const FOp& f = pl.fops[P.op_begin + o];
         const int fam = f.code / kCodeSlots, slot = f.code % kCodeSlots;
-        CHECK(fam <= FC_MULI_MASK, "op %d: family %d", o, fam);
+        CHECK(fam <= FC_SHEAR2, "op %d: family %d", o, fam);
         CHECK(f.rmask < (1u << R), "op %d: rmask", o);
         CHECK((f.lmask & pm) == 0 && (f.lmask >> k) == 0, "op %d: lmask on a register / non-tile bit", o);
         CHECK((f.gmask & tile) == 0 && (nq == 64 || (f.gmask >> nq) == 0), "op %d: gmask inside the tile", o);
         CHECK(((f.flags & FF_COND) != 0) == (f.lmask != 0 || f.gmask != 0), "op %d: FF_COND", o);
-        if (fam <= FC_X || fam == FC_PHASE_BIT || fam == FC_MULI_BIT) CHECK(slot < R, "op %d: slot %d >= R", o, slot);
+        if (fam <= FC_X || fam == FC_PHASE_BIT || fam == FC_MULI_BIT || fam == FC_SHEAR || fam == FC_SHEAR2)
+          CHECK(slot < R, "op %d: slot %d >= R", o, slot);
+        if (fam == FC_SHEAR || fam == FC_SHEAR2)
+          CHECK(f.rmask == 0 && f.lmask == 0 && f.gmask == 0 && f.i0 == slot, "op %d: shear", o);
         if (fam <= FC_X) {
           CHECK(f.i0 == slot && ((f.rmask >> f.i0) & 1u) == 0, "op %d: pair target", o);
           if (fam != FC_GEN && fam != FC_GEN_C && fam != FC_X) CHECK(f.rmask == 0, "op %d: controlled add-only pair", o);
@@ -160,7 +163,7 @@ static std::vector<cd> emulate(const RegPlan& pl, int nq) {
               flips ^= f.c.u[15];
               continue;
             }
-            if (fam <= FC_X || fam == FC_DEPOL) flush_flips();  // applying early is always exact
+            if (fam <= FC_X || fam == FC_DEPOL || fam == FC_SHEAR || fam == FC_SHEAR2) flush_flips();
             auto c = [&](int e) { return coef(f, e, pl.arith); };
             if (fam <= FC_X) {
               const int I = slot;
@@ -187,6 +190,14 @@ static std::vector<cd> emulate(const RegPlan& pl, int nq) {
                 if (fam == FC_PHASE_BIT) touch = (j >> slot) & 1;
                 if (fam == FC_PHASE_MASK) touch = (f.c.u[15] >> j) & 1u;
                 if (touch) v[j] *= ph;
+              }
+            } else if (fam == FC_SHEAR || fam == FC_SHEAR2) {
+              const double t = c(0);
+              for (int j = 0; j < nj; ++j) {
+                if ((j >> slot) & 1) continue;
+                const cd x = v[j], y = v[j | (1 << slot)];
+                v[j] = fam == FC_SHEAR ? x - t * y : t * x - y;
+                v[j | (1 << slot)] = fam == FC_SHEAR ? y + t * x : x + t * y;
               }
             } else if (fam == FC_MULI_BIT || fam == FC_MULI_ALL || fam == FC_MULI_MASK) {
               for (int j = 0; j < nj; ++j) {
