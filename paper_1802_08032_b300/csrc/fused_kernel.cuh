@@ -48,39 +48,44 @@ struct PlainArith {
       }
       pair_apply<R, K, CONJ>(x, y, g);
     } else if constexpr (sizeof(R) == 4 && (K == PK_H || K == PK_SX || K == PK_SY)) {
-      // FP32: each real butterfly (a, b) -> (a + b, b - a) or (a - b, a + b)
-      // is computed in place, the second output from the first by one FMA
-      // with an exact factor 2 (b - a = 2b - (a + b)).  Both outputs then
-      // stay in the inputs' registers, which saves a register move per
-      // output; the second output carries one extra rounding of |a + b|.
-      if constexpr (K == PK_H) {  // unscaled: (x + y, x - y)
-        x.x = x.x + y.x; y.x = fmaf(y.x, -2.f, x.x);
-        x.y = x.y + y.y; y.y = fmaf(y.y, -2.f, x.y);
-      } else if constexpr (K == PK_SY) {  // [[1, -1], [1, 1]]: (x - y, x + y)
-        x.x = x.x - y.x; y.x = fmaf(y.x, 2.f, x.x);
-        x.y = x.y - y.y; y.y = fmaf(y.y, 2.f, x.y);
+      // FP32: each real butterfly (a, b) -> (a + c b, c b - a) or
+      // (a - c b, a + c b), c = the y factor c0, is computed in place, the
+      // second output from the first by one FMA with the factor 2c
+      // (c b - a = 2c b - (a + c b)).  Both outputs then stay in the inputs'
+      // registers, which saves a register move per output; the second output
+      // carries one extra rounding of |a + c b|.
+      const R c = cf(op, 0), c2 = 2.f * c;
+      if constexpr (K == PK_H) {  // unscaled: (x + c y, x - c y)
+        x.x = fmaf(c, y.x, x.x); y.x = fmaf(y.x, -c2, x.x);
+        x.y = fmaf(c, y.y, x.y); y.y = fmaf(y.y, -c2, x.y);
+      } else if constexpr (K == PK_SY) {  // [[1, -1], [1, 1]]: (x - c y, x + c y)
+        x.x = fmaf(-c, y.x, x.x); y.x = fmaf(y.x, c2, x.x);
+        x.y = fmaf(-c, y.y, x.y); y.y = fmaf(y.y, c2, x.y);
       } else if constexpr (!CONJ) {  // [[1, -i], [-i, 1]]
-        x.x = x.x + y.y; y.y = fmaf(y.y, 2.f, -x.x);   // y.im - x.re
-        x.y = x.y - y.x; y.x = fmaf(y.x, 2.f, x.y);    // y.re + x.im
+        x.x = fmaf(c, y.y, x.x); y.y = fmaf(y.y, c2, -x.x);    // c y.im - x.re
+        x.y = fmaf(-c, y.x, x.y); y.x = fmaf(y.x, c2, x.y);    // c y.re + x.im
       } else {  // [[1, i], [i, 1]]
-        x.x = x.x - y.y; y.y = fmaf(y.y, 2.f, x.x);    // y.im + x.re
-        x.y = x.y + y.x; y.x = fmaf(y.x, 2.f, -x.y);   // y.re - x.im
+        x.x = fmaf(-c, y.y, x.x); y.y = fmaf(y.y, c2, x.x);    // c y.im + x.re
+        x.y = fmaf(c, y.x, x.y); y.x = fmaf(y.x, c2, -x.y);    // c y.re - x.im
       }
-    } else if constexpr (K == PK_H) {  // unscaled: (x + y, x - y)
+    } else if constexpr (K == PK_H) {  // unscaled: (x + c y, x - c y); FMA with c = 1 is the add
+      const R c = cf(op, 0);
       const Cplx u = x;
-      x.x = u.x + y.x; x.y = u.y + y.y;
-      y.x = u.x - y.x; y.y = u.y - y.y;
+      x.x = fma(c, y.x, u.x); x.y = fma(c, y.y, u.y);
+      y.x = fma(-c, y.x, u.x); y.y = fma(-c, y.y, u.y);
     } else if constexpr (K == PK_SX) {  // [[1, -i], [-i, 1]]  (conj: [[1, i], [i, 1]])
+      const R c = cf(op, 0);
       const Cplx u = x;
       if constexpr (!CONJ) {
-        x.x = u.x + y.y; x.y = u.y - y.x; y.x = y.x + u.y; y.y = y.y - u.x;
+        x.x = fma(c, y.y, u.x); x.y = fma(-c, y.x, u.y); y.x = fma(c, y.x, u.y); y.y = fma(c, y.y, -u.x);
       } else {
-        x.x = u.x - y.y; x.y = u.y + y.x; y.x = y.x - u.y; y.y = y.y + u.x;
+        x.x = fma(-c, y.y, u.x); x.y = fma(c, y.x, u.y); y.x = fma(c, y.x, -u.y); y.y = fma(c, y.y, u.x);
       }
     } else if constexpr (K == PK_SY) {  // [[1, -1], [1, 1]] (real)
+      const R c = cf(op, 0);
       const Cplx u = x;
-      x.x = u.x - y.x; x.y = u.y - y.y;
-      y.x = u.x + y.x; y.y = u.y + y.y;
+      x.x = fma(-c, y.x, u.x); x.y = fma(-c, y.y, u.y);
+      y.x = fma(c, y.x, u.x); y.y = fma(c, y.y, u.y);
     } else if constexpr (K == PK_X) {
       const Cplx t = x;
       x = y;
@@ -106,6 +111,14 @@ struct PlainArith {
       w.x = neg_bits(v.x);
       w.y = neg_bits(v.y);
     }
+    return w;
+  }
+  // (1 + i t) v, t = c0: the unscaled phase
+  __device__ static Cplx phase_u(const Cplx& v, const FOp& op) {
+    const R t = cf(op, 0);
+    Cplx w;
+    w.x = fma(-t, v.y, v.x);
+    w.y = fma(t, v.x, v.y);
     return w;
   }
   // Shear along a register bit: MODE 0 (x - t y, y + t x), MODE 1
@@ -209,6 +222,9 @@ struct DFArith {
   }
   __device__ static Cplx phase(const Cplx& v, const FOp& op) { return dfc2_cmul(v, cf(op, 0), cf(op, 1)); }
   __device__ static Cplx mul_i(const Cplx& v) { return mul_plus_i(v); }
+  __device__ static Cplx phase_u(const Cplx& v, const FOp& op) {
+    return dfc2_cmul(v, df{1.f, 0.f}, cf(op, 0));
+  }
   template <int MODE>
   __device__ static void shear(Cplx& x, Cplx& y, const FOp& op) {
     const df t = cf(op, 0);
@@ -261,6 +277,14 @@ __device__ __forceinline__ void phase_on_bit(typename A::Cplx (&v)[1 << R], cons
 #pragma unroll
   for (int j = 0; j < (1 << R); ++j)
     if (j & (1 << I)) v[j] = A::phase(v[j], op);
+}
+
+// Unscaled phase (1 + i t) on the amplitudes with register bit I set.
+template <class A, int R, int I>
+__device__ __forceinline__ void phaseu_on_bit(typename A::Cplx (&v)[1 << R], const FOp& op) {
+#pragma unroll
+  for (int j = 0; j < (1 << R); ++j)
+    if (j & (1 << I)) v[j] = A::phase_u(v[j], op);
 }
 
 // Shear along register bit I (MODE as in Arith::shear).
@@ -349,6 +373,11 @@ __device__ __forceinline__ void run_op(typename A::Cplx (&v)[1 << R], const FOp&
     QS_BIT_CASES(FC_MULI_BIT, (muli_on_bit<A, R, I>(v)))
     QS_BIT_CASES(FC_SHEAR, (shear_on_bit<A, R, I, 0>(v, op)))
     QS_BIT_CASES(FC_SHEAR2, (shear_on_bit<A, R, I, 1>(v, op)))
+    QS_BIT_CASES(FC_PHASEU_BIT, (phaseu_on_bit<A, R, I>(v, op)))
+    case FC_PHASEU_ALL * kCodeSlots:
+#pragma unroll
+      for (int j = 0; j < (1 << R); ++j) v[j] = A::phase_u(v[j], op);
+      break;
     case FC_MULI_ALL * kCodeSlots:
 #pragma unroll
       for (int j = 0; j < (1 << R); ++j) v[j] = A::mul_i(v[j]);

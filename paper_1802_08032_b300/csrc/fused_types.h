@@ -14,9 +14,14 @@ enum FKind : uint8_t {
   FK_DEPOL = 8,   // depolarising quad on register bits (i0 = row bit, i1 = column bit)
   FK_SCALE = 9,   // multiply every amplitude by the complex (c0, c1)
   FK_MULI = 10,   // multiply by i where the condition holds (no arithmetic)
-  FK_SHEAR = 11   // pair op: (x, y) -> (x - t y, y + t x), or (t x - y, x + t y): a real
+  FK_SHEAR = 11,  // pair op: (x, y) -> (x - t y, y + t x), or (t x - y, x + t y): a real
                   // rotation up to a factor deferred like the dropped ones (c0 = t)
+  FK_PHASEU = 12  // multiply by (1 + i t) where the condition holds (c0 = t): a phase
+                  // whose real factor the next pair update on its bit applies
 };
+// H, sqrt(X) and sqrt(Y) carry one coefficient, c0: a real factor applied to
+// their bit-1 input y (1 unless a preceding FK_PHASEU on the bit left its
+// real factor to them).
 // In this engine H, sqrt(X) and sqrt(Y) are applied WITHOUT their scalar
 // factors: H = (1/sqrt 2) [[1, 1], [1, -1]], sqrt(X) = ((1+i)/2) [[1, -i], [-i, 1]],
 // sqrt(Y) = ((1+i)/2) [[1, -1], [1, 1]]; the bracketed matrices need additions
@@ -42,7 +47,8 @@ enum FFamily : uint8_t {
   FC_PHASE_BIT = 7, FC_PHASE_ALL = 8, FC_PHASE_MASK = 9,
   FC_SIGN = 10, FC_DEPH = 11, FC_DEPOL = 12, FC_SCALE = 13,
   FC_MULI_BIT = 14, FC_MULI_ALL = 15, FC_MULI_MASK = 16,
-  FC_SHEAR = 17, FC_SHEAR2 = 18  // (x - t y, y + t x); (t x - y, x + t y)
+  FC_SHEAR = 17, FC_SHEAR2 = 18,  // (x - t y, y + t x); (t x - y, x + t y)
+  FC_PHASEU_BIT = 19, FC_PHASEU_ALL = 20
 };
 constexpr int kCodeSlots = 16;
 // FOp::flags

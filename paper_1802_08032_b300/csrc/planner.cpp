@@ -49,6 +49,7 @@ VOp pair_op(OpK k, int bit, uint64_t cond, const double* m, bool conj) {
   v.cond = cond;
   v.conj = conj;
   if (k == OpK::GEN) std::memcpy(v.c, m, sizeof(v.c));
+  if (k == OpK::H || k == OpK::SX || k == OpK::SY) v.c[0] = 1.0;  // factor on the bit-1 input
   if (cond != 0 && (k == OpK::H || k == OpK::SX || k == OpK::SY)) {
     // the engine applies these unscaled (a global factor), which a control
     // would break: use the explicit matrix instead
@@ -444,6 +445,34 @@ void decompose_general(std::vector<VOp>& ops) {
   ops.swap(out);
 }
 
+// A phase e^{i psi} = cos psi (1 + i tan psi) on a single bit: the bracket
+// costs one FMA per output component (2 per touched amplitude, against 4
+// for the complex product), and the real factor cos psi, which multiplies
+// every amplitude with the bit set, commutes with everything up to the next
+// operation that mixes amplitudes along the bit.  When that operation is an
+// uncontrolled H / sqrt(X) / sqrt(Y), it takes the factor on its bit-1 input
+// at no cost (its additions become FMAs).  Only for plain FP32 / FP64
+// arithmetic (a double-float scaled add is not free), and only for
+// |cos psi| >= 1/4, which bounds the growth.
+void unscale_phases(std::vector<VOp>& ops) {
+  for (size_t i = 0; i < ops.size(); ++i) {
+    VOp& ph = ops[i];
+    if (ph.kind != FK_PHASE || __builtin_popcountll(ph.cond) != 1 || !(std::fabs(ph.c[0]) >= 0.25)) continue;
+    const uint64_t bit = ph.cond;
+    for (size_t j = i + 1; j < ops.size(); ++j) {
+      if ((ops[j].xmask() & bit) == 0) continue;
+      VOp& p = ops[j];
+      if ((p.kind == FK_H || p.kind == FK_SX || p.kind == FK_SY) && p.cond == 0 && !p.spread) {
+        p.c[0] *= ph.c[0];
+        ph.kind = FK_PHASEU;
+        ph.c[0] = ph.c[1] / ph.c[0];
+        ph.c[1] = 0.0;
+      }
+      break;
+    }
+  }
+}
+
 // A dephasing on qubit bits (t, t + N) only scales the entries whose row
 // and column bits differ; a depolarising quad on the same bits scales those
 // entries by its "off" factor and mixes the others.  When no operation
@@ -543,6 +572,10 @@ int dispatch_code(const FOp& f) {
       return FC_PHASE_MASK * S;
     case FK_SIGN: return FC_SIGN * S;
     case FK_SHEAR: return (f.i1 ? FC_SHEAR2 : FC_SHEAR) * S + f.i0;  // i1: the form
+    case FK_PHASEU:
+      if (f.rmask == 0) return FC_PHASEU_ALL * S;
+      if (popc(f.rmask) == 1) return FC_PHASEU_BIT * S + __builtin_ctz(f.rmask);
+      fail(QS_E_ARG, "fused planner: unscaled phase on several bits");
     case FK_MULI:
       if (f.rmask == 0) return FC_MULI_ALL * S;
       if (popc(f.rmask) == 1) return FC_MULI_BIT * S + __builtin_ctz(f.rmask);
@@ -577,7 +610,7 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
   const bool phase_in_regs = arith != Arith::F32;
   auto needed = [&](const VOp& v) {
     uint32_t need = local_mask(v.xmask());
-    if (phase_in_regs && v.kind == FK_PHASE) {
+    if (phase_in_regs && (v.kind == FK_PHASE || v.kind == FK_PHASEU)) {
       const uint32_t c = local_mask(v.cond);
       if (popc(c) <= R) need |= c;
     }
@@ -598,7 +631,7 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
     // condition on (a phase on a lane bit runs on half-idle lanes), then to
     // the highest unused local bits (keeps low bits on lanes)
     for (size_t o = i; o < j && popc(P) < R; ++o)
-      if (p.ops[o].kind == FK_PHASE) {
+      if (p.ops[o].kind == FK_PHASE || p.ops[o].kind == FK_PHASEU) {
         const uint32_t c = local_mask(p.ops[o].cond);
         if (popc(c) == 1) P |= c;
       }
@@ -643,7 +676,7 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
         src(v.b1, f.bsrc, f.bpos);
       }
       set_coeffs(f, v.c, arith);
-      if (v.kind == FK_PHASE || v.kind == FK_SIGN || v.kind == FK_MULI) {
+      if (v.kind == FK_PHASE || v.kind == FK_PHASEU || v.kind == FK_SIGN || v.kind == FK_MULI) {
         uint32_t touch = 0;  // register amplitudes j whose index has every rmask bit
         for (int j = 0; j < (1 << R); ++j)
           if ((uint32_t(j) & f.rmask) == f.rmask) touch |= 1u << j;
@@ -679,6 +712,7 @@ double vop_flops(const VOp& v, int nq) {
   if (v.kind <= FK_X) return dim / 2 * f * pair_flops[v.kind];
   if (v.kind == FK_SHEAR) return dim / 2 * 8;
   if (v.kind == FK_PHASE) return dim * f * 6;
+  if (v.kind == FK_PHASEU) return dim * f * 4;
   if (v.kind == FK_SCALE) return dim * 6;
   if (v.kind == FK_DEPH) return dim / 2 * 2;
   if (v.kind == FK_DEPOL) return dim / 4 * 16;
@@ -701,6 +735,7 @@ double vop_alu(const VOp& v, int nq, Arith a) {
   if (v.kind <= FK_X) return dim / 2 * f * (d ? df_pair[v.kind] : plain_pair[v.kind]);
   if (v.kind == FK_SHEAR) return dim / 2 * (d ? 2 * 2 * (8 + 11) : 4);
   if (v.kind == FK_PHASE) return dim * f * (d ? 2 * 27 : 4);
+  if (v.kind == FK_PHASEU) return dim * f * (d ? 2 * 27 : 2);
   if (v.kind == FK_SCALE) return dim * (d ? 2 * 27 : 4);
   if (v.kind == FK_DEPH) return dim / 2 * (d ? 2 * 8 : 2);
   if (v.kind == FK_DEPOL) return dim / 4 * (d ? 2 * (2 * 27 + 2 * 8) : 10);
@@ -763,6 +798,7 @@ void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, uint64_t 
   absorb_into_general(vops);
   decompose_general(vops);
   merge_phases(vops, r.nq);
+  if (out.arith != Arith::DF) unscale_phases(vops);
   if (r.density) fold_dephasing(vops);
   const int64_t cap = env.max_fused_ops > 0 ? std::min<int64_t>(env.max_fused_ops, kMaxPassOps)
                                             : kMaxPassOps;

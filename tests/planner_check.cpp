@@ -80,12 +80,13 @@ static void check_plan(const RegPlan& pl, int nq) {
       for (int o = st.op_begin; o < st.op_end; ++o) {
         const FOp& f = pl.fops[P.op_begin + o];
         const int fam = f.code / kCodeSlots, slot = f.code % kCodeSlots;
-        CHECK(fam <= FC_SHEAR2, "op %d: family %d", o, fam);
+        CHECK(fam <= FC_PHASEU_ALL, "op %d: family %d", o, fam);
         CHECK(f.rmask < (1u << R), "op %d: rmask", o);
         CHECK((f.lmask & pm) == 0 && (f.lmask >> k) == 0, "op %d: lmask on a register / non-tile bit", o);
         CHECK((f.gmask & tile) == 0 && (nq == 64 || (f.gmask >> nq) == 0), "op %d: gmask inside the tile", o);
         CHECK(((f.flags & FF_COND) != 0) == (f.lmask != 0 || f.gmask != 0), "op %d: FF_COND", o);
-        if (fam <= FC_X || fam == FC_PHASE_BIT || fam == FC_MULI_BIT || fam == FC_SHEAR || fam == FC_SHEAR2)
+        if (fam <= FC_X || fam == FC_PHASE_BIT || fam == FC_MULI_BIT || fam == FC_SHEAR || fam == FC_SHEAR2 ||
+            fam == FC_PHASEU_BIT)
           CHECK(slot < R, "op %d: slot %d >= R", o, slot);
         if (fam == FC_SHEAR || fam == FC_SHEAR2)
           CHECK(f.rmask == 0 && f.lmask == 0 && f.gmask == 0 && f.i0 == slot, "op %d: shear", o);
@@ -176,6 +177,10 @@ static std::vector<cd> emulate(const RegPlan& pl, int nq) {
               else if (fam == FC_SX_C) { g01 = cd(0, 1); g10 = cd(0, 1); }
               else if (fam == FC_SY) { g01 = -1; g10 = 1; }
               else { g00 = 0; g01 = 1; g10 = 1; g11 = 0; }  // X
+              if (fam >= FC_H && fam <= FC_SY) {  // c0: factor on the bit-1 input
+                g01 *= c(0);
+                g11 *= c(0);
+              }
               for (int j = 0; j < nj; ++j) {
                 if ((j >> I) & 1) continue;
                 if ((uint32_t(j) & f.rmask) != f.rmask) continue;
@@ -191,6 +196,10 @@ static std::vector<cd> emulate(const RegPlan& pl, int nq) {
                 if (fam == FC_PHASE_MASK) touch = (f.c.u[15] >> j) & 1u;
                 if (touch) v[j] *= ph;
               }
+            } else if (fam == FC_PHASEU_BIT || fam == FC_PHASEU_ALL) {
+              const cd u(1.0, c(0));
+              for (int j = 0; j < nj; ++j)
+                if (fam == FC_PHASEU_ALL || ((j >> slot) & 1)) v[j] *= u;
             } else if (fam == FC_SHEAR || fam == FC_SHEAR2) {
               const double t = c(0);
               for (int j = 0; j < nj; ++j) {
