@@ -145,6 +145,68 @@ def test_collapse_state_vector(Q, env, prec):
         assert abs(tot - 1) <= (1e-13 if prec == 128 else 1e-5)
 
 
+def general_gates(n, seed):
+    """CNOT, controlled and plain general unitaries and phase shifts mixed
+    into a random circuit (the layering itself has only H, sqrt(X), sqrt(Y),
+    T, CZ, compactUnitary and multi-controlled phase flips)."""
+    rng = C.SplitMix64(seed)
+    ops = list(C.random_circuit(n, 6, seed, extras=n >= 3))
+    for _ in range(3 * n):
+        qs = C.distinct_qubits(rng, n, min(n, 3))
+        a = C.haar_alpha_beta(rng)
+        al, be = complex(a[0], a[1]), complex(a[2], a[3])
+        u = (al.real, al.imag, -be.real, be.imag, be.real, be.imag, al.real, -al.imag)
+        kind = rng.below(4)
+        at = rng.below(len(ops) + 1)
+        if kind == 0 and n >= 2:
+            op = C.Op("CNOT", (qs[0],), (qs[1],))
+        elif kind == 1 and n >= 2:
+            op = C.Op("CUNITARY", (qs[0],), tuple(qs[1:]), u)
+        elif kind == 2:
+            op = C.Op("PHASE", (qs[0],), (), (0.3 + rng.uniform(),))
+        else:
+            op = C.Op("UNITARY", (qs[0],), (), u)
+        ops.insert(at, op)
+    return ops
+
+
+@pytest.mark.parametrize("prec,arith", [(128, 0), (128, 1), (64, 0)])
+@pytest.mark.parametrize("fusion", [0, 1])
+@pytest.mark.parametrize("N", [3, 5])
+def test_density_circuit_general_gates(Q, env, prec, arith, fusion, N):
+    ops = C.with_noise(general_gates(N, 70 + N), 0.02, 0.01)
+    ref = O.run_circuit(N, ops, density=True)
+    Q.setEnvOption(env, "fusion", fusion)
+    Q.setEnvOption(env, "arith", arith)
+    try:
+        q = Q.createDensityQureg(N, prec, env)
+        Q.applyCircuit(q, ops)
+        tr = Q.calcTotalProb(q)
+        got = Q.copyStateToHost(q)
+        Q.destroyQureg(q)
+    finally:
+        Q.setEnvOption(env, "arith", 0)
+        Q.setEnvOption(env, "fusion", 1)
+    assert np.max(np.abs(got - ref.a)) <= AMP_TOL[prec]
+    assert abs(tr - ref.total_prob()) <= (PROB_TOL if prec == 128 else 1e-5)
+
+
+@pytest.mark.parametrize("prec,arith", [(128, 0), (128, 1), (64, 0)])
+@pytest.mark.parametrize("n", [6, 11, 14])
+def test_state_vector_general_gates(Q, env, prec, arith, n):
+    ops = general_gates(n, 30 + n)
+    ref = O.run_circuit(n, ops)
+    Q.setEnvOption(env, "arith", arith)
+    try:
+        q = Q.createQureg(n, prec, env)
+        Q.applyCircuit(q, ops)
+        got = Q.copyStateToHost(q)
+        Q.destroyQureg(q)
+    finally:
+        Q.setEnvOption(env, "arith", 0)
+    assert np.max(np.abs(got - ref.a)) <= AMP_TOL[prec]
+
+
 @pytest.mark.parametrize("prec", [128, 64])
 def test_collapse_density(Q, env, prec):
     N = 4

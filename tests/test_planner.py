@@ -126,6 +126,19 @@ def test_planned_density_matrix_matches_oracle(harness, N, arith):
     assert np.max(np.abs(rho - ref)) <= 1e-12, head
 
 
+@pytest.mark.parametrize("N", [3, 5])
+@pytest.mark.parametrize("arith", [0, 1])
+def test_planned_density_matrix_general_gates(harness, N, arith):
+    """General, controlled and phase gates on a density matrix: the column
+    updates carry conjugated matrices through absorption, the phase-shear-
+    phase form and the unscaled phases."""
+    gates = C.random_circuit(N, 6, 90 + N, extras=True) + controlled_extras(N, N + 1)
+    ops = C.with_noise(gates, 0.02, 0.01)
+    head, rho = run(harness, N, ops, density=True, arith=arith)
+    ref = O.run_circuit(N, ops, density=True).a
+    assert np.max(np.abs(rho - ref)) <= 1e-12, head
+
+
 def test_density_matrix_small_tile(harness):
     N = 6
     ops = C.random_density_circuit(N, 6, 77, 0.02, 0.01)
