@@ -121,17 +121,18 @@ struct PlainArith {
     w.y = fma(t, v.x, v.y);
     return w;
   }
-  // Shear along a register bit: MODE 0 (x - t y, y + t x), MODE 1
-  // (t x - y, x + t y), t = c0.
+  // Shear along a register bit: MODE 0 (x - t y, y + t' x), MODE 1
+  // (t x - y, x + t y), t = c0, t' = c4.
   template <int MODE>
   __device__ static void shear(Cplx& x, Cplx& y, const FOp& op) {
     const R t = cf(op, 0);
     const Cplx u = x;
     if constexpr (MODE == 0) {
+      const R t2 = cf(op, 4);
       x.x = fma(-t, y.x, u.x);
       x.y = fma(-t, y.y, u.y);
-      y.x = fma(t, u.x, y.x);
-      y.y = fma(t, u.y, y.y);
+      y.x = fma(t2, u.x, y.x);
+      y.y = fma(t2, u.y, y.y);
     } else {
       x.x = fma(t, u.x, -y.x);
       x.y = fma(t, u.y, -y.y);
@@ -231,8 +232,9 @@ struct DFArith {
     const float2 th = f2(t.hi, t.hi), tl = f2(t.lo, t.lo);
     const Cplx u = x;
     if constexpr (MODE == 0) {
+      const df t2 = cf(op, 4);
       x = dfc2_sub(u, dfc2_mulv(y, th, tl));
-      y = dfc2_add(y, dfc2_mulv(u, th, tl));
+      y = dfc2_add(y, dfc2_mulv(u, f2(t2.hi, t2.hi), f2(t2.lo, t2.lo)));
     } else {
       x = dfc2_sub(dfc2_mulv(u, th, tl), y);
       y = dfc2_add(u, dfc2_mulv(y, th, tl));

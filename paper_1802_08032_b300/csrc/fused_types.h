@@ -14,8 +14,9 @@ enum FKind : uint8_t {
   FK_DEPOL = 8,   // depolarising quad on register bits (i0 = row bit, i1 = column bit)
   FK_SCALE = 9,   // multiply every amplitude by the complex (c0, c1)
   FK_MULI = 10,   // multiply by i where the condition holds (no arithmetic)
-  FK_SHEAR = 11,  // pair op: (x, y) -> (x - t y, y + t x), or (t x - y, x + t y): a real
-                  // rotation up to a factor deferred like the dropped ones (c0 = t)
+  FK_SHEAR = 11,  // pair op: (x, y) -> (x - t y, y + u x), or (t x - y, x + t y): a real
+                  // rotation up to a factor deferred like the dropped ones (c0 = t, c4 = u;
+                  // u = t unless a phase's factor passes through, see the planner)
   FK_PHASEU = 12  // multiply by (1 + i t) where the condition holds (c0 = t): a phase
                   // whose real factor the next pair update on its bit applies
 };

@@ -396,7 +396,9 @@ void absorb_into_general(std::vector<VOp>& ops) {
 // operations per pair instead of 16.  Matrices whose factors do not
 // reproduce them to 1e-14 (not unitary to that precision, or |a| or |b| 0)
 // stay general.
-void decompose_general(std::vector<VOp>& ops) {
+// max_t: the largest t the first form may take (its deferred factor |a|
+// then is at least 1/sqrt(1 + max_t^2)).
+void decompose_general(std::vector<VOp>& ops, double max_t) {
   using C = std::complex<double>;
   std::vector<VOp> out;
   out.reserve(ops.size() + ops.size() / 2);
@@ -433,9 +435,10 @@ void decompose_general(std::vector<VOp>& ops) {
     VOp sh;
     sh.kind = FK_SHEAR;
     sh.b0 = v.b0;
-    const bool by_a = na >= nb;
-    sh.c[0] = by_a ? nb / na : na / nb;  // t <= 1
+    const bool by_a = na * max_t >= nb;
+    sh.c[0] = by_a ? nb / na : na / nb;  // t <= max_t (first form) or < 1
     sh.c[1] = by_a ? 0.0 : 1.0;          // form
+    sh.c[4] = sh.c[0];
     const C f = g * (by_a ? na : nb);
     sh.c[2] = f.real();
     sh.c[3] = f.imag();
@@ -447,25 +450,39 @@ void decompose_general(std::vector<VOp>& ops) {
 
 // A phase e^{i psi} = cos psi (1 + i tan psi) on a single bit: the bracket
 // costs one FMA per output component (2 per touched amplitude, against 4
-// for the complex product), and the real factor cos psi, which multiplies
-// every amplitude with the bit set, commutes with everything up to the next
-// operation that mixes amplitudes along the bit.  When that operation is an
-// uncontrolled H / sqrt(X) / sqrt(Y), it takes the factor on its bit-1 input
-// at no cost (its additions become FMAs).  Only for plain FP32 / FP64
-// arithmetic (a double-float scaled add is not free), and only for
-// |cos psi| >= 1/4, which bounds the growth.
+// for the complex product), and the real factor c = cos psi, which
+// multiplies every amplitude with the bit set, commutes with everything up
+// to the next operation that mixes amplitudes along the bit.  When that
+// operation is an uncontrolled H / sqrt(X) / sqrt(Y), it takes the factor on
+// its bit-1 input at no cost (its additions become FMAs).  A first-form
+// shear (x - t y, y + t' x) on the bit lets the factor through, also at no
+// cost: with y = c y~ it computes x - (t c) y~ and y~ + (t'/c) x, the factor
+// staying on the bit-1 half.  Only for plain FP32 / FP64 arithmetic (a
+// double-float scaled add is not free), and only for |cos psi| >= 1/4,
+// which bounds the growth.
 void unscale_phases(std::vector<VOp>& ops) {
+  std::vector<size_t> through;
   for (size_t i = 0; i < ops.size(); ++i) {
     VOp& ph = ops[i];
     if (ph.kind != FK_PHASE || __builtin_popcountll(ph.cond) != 1 || !(std::fabs(ph.c[0]) >= 0.25)) continue;
     const uint64_t bit = ph.cond;
+    through.clear();
     for (size_t j = i + 1; j < ops.size(); ++j) {
       if ((ops[j].xmask() & bit) == 0) continue;
       VOp& p = ops[j];
+      if (p.kind == FK_SHEAR && p.c[1] == 0.0) {
+        through.push_back(j);
+        continue;
+      }
       if ((p.kind == FK_H || p.kind == FK_SX || p.kind == FK_SY) && p.cond == 0 && !p.spread) {
-        p.c[0] *= ph.c[0];
+        const double c = ph.c[0];
+        for (size_t t : through) {
+          ops[t].c[0] *= c;
+          ops[t].c[4] /= c;
+        }
+        p.c[0] *= c;
         ph.kind = FK_PHASEU;
-        ph.c[0] = ph.c[1] / ph.c[0];
+        ph.c[0] = ph.c[1] / c;
         ph.c[1] = 0.0;
       }
       break;
@@ -796,7 +813,9 @@ void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, uint64_t 
   out.zero_out = zero;
   merge_phases(vops, r.nq);
   absorb_into_general(vops);
-  decompose_general(vops);
+  // FP64 defers factors down to 2^-500, so the first form (which passes a
+  // phase's factor through, see unscale_phases) may take t up to 16
+  decompose_general(vops, out.arith == Arith::F64 ? 16.0 : 1.0);
   merge_phases(vops, r.nq);
   if (out.arith != Arith::DF) unscale_phases(vops);
   if (r.density) fold_dephasing(vops);

@@ -206,7 +206,7 @@ static std::vector<cd> emulate(const RegPlan& pl, int nq) {
                 if ((j >> slot) & 1) continue;
                 const cd x = v[j], y = v[j | (1 << slot)];
                 v[j] = fam == FC_SHEAR ? x - t * y : t * x - y;
-                v[j | (1 << slot)] = fam == FC_SHEAR ? y + t * x : x + t * y;
+                v[j | (1 << slot)] = fam == FC_SHEAR ? y + c(4) * x : x + t * y;
               }
             } else if (fam == FC_MULI_BIT || fam == FC_MULI_ALL || fam == FC_MULI_MASK) {
               for (int j = 0; j < nj; ++j) {
