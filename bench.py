@@ -383,27 +383,31 @@ def timed(torch, stream, fn, reps):
 
 def variants(Q, env, torch, stream, only=()):
     """Other configurations of the same metric, measured outside the timed
-    region: complex64 and double-float complex128 at 30 qubits, the 14-qubit
-    noisy density matrix, and single-gate pass bandwidth by target bit."""
+    region: complex64 and double-float complex128 at 30 qubits, the 33-qubit
+    (128 GiB complex128, 64 GiB complex64) depth-40 circuits, the 14-qubit
+    noisy density matrix, single-gate pass bandwidth by target bit, batches,
+    serving and multi-target passes."""
     out = {}
     ops = C.workload_30q(30)
 
-    def sv(prec, arith):
+    def sv(prec, arith, n=30, reps=2):
         def run_variant():
+            circ = ops if n == 30 else C.workload_30q(n)
             Q.setEnvOption(env, "arith", arith)
-            q = Q.createQureg(30, prec, env)
+            q = Q.createQureg(n, prec, env)
 
             def run():
                 Q.initZeroState(q)
-                Q.applyCircuit(q, ops)
+                Q.applyCircuit(q, circ)
                 Q.calcTotalProb(q)
 
             try:
-                ms = timed(torch, stream, run, 2)
+                ms = timed(torch, stream, run, reps)
             finally:
                 Q.destroyQureg(q)
                 Q.setEnvOption(env, "arith", 0)
-            return {"gates_per_s": len(ops) / ms * 1e3, "ms_per_circuit": ms}
+            return {"qubits": n, "gates": len(circ), "gates_per_s": len(circ) / ms * 1e3,
+                    "ms_per_circuit": ms}
         return run_variant
 
     def sweep(n, targets):
@@ -468,6 +472,7 @@ def variants(Q, env, torch, stream, only=()):
         return {"ops_per_s": len(dops) / ms * 1e3, "ms_per_circuit": ms, "ops": len(dops)}
 
     for name, fn in (("sv30_c64", sv(64, 0)), ("sv30_c128_df", sv(128, 1)),
+                     ("sv33_c128", sv(128, 0, 33, 1)), ("sv33_c64", sv(64, 0, 33)),
                      ("single_gate_sweep", lambda: sweep(30, range(30))),
                      ("single_gate_sweep_33q", lambda: sweep(33, [0, 1, 2, 4, 8, 16, 24, 32])),
                      ("dm14_c128", dm14),
