@@ -55,12 +55,14 @@ struct PlainArith {
       // registers, which saves a register move per output; the second output
       // carries one extra rounding of |a + c b|.
       const R c = cf(op, 0), c2 = 2.f * c;
+      // real matrices: one paired FMA covers the real and imaginary parts
+      // (each half rounds as the scalar FMA would)
       if constexpr (K == PK_H) {  // unscaled: (x + c y, x - c y)
-        x.x = fmaf(c, y.x, x.x); y.x = fmaf(y.x, -c2, x.x);
-        x.y = fmaf(c, y.y, x.y); y.y = fmaf(y.y, -c2, x.y);
+        x = __ffma2_rn(make_float2(c, c), y, x);
+        y = __ffma2_rn(y, make_float2(-c2, -c2), x);
       } else if constexpr (K == PK_SY) {  // [[1, -1], [1, 1]]: (x - c y, x + c y)
-        x.x = fmaf(-c, y.x, x.x); y.x = fmaf(y.x, c2, x.x);
-        x.y = fmaf(-c, y.y, x.y); y.y = fmaf(y.y, c2, x.y);
+        x = __ffma2_rn(make_float2(-c, -c), y, x);
+        y = __ffma2_rn(y, make_float2(c2, c2), x);
       } else if constexpr (!CONJ) {  // [[1, -i], [-i, 1]]
         x.x = fmaf(c, y.y, x.x); y.y = fmaf(y.y, c2, -x.x);    // c y.im - x.re
         x.y = fmaf(-c, y.x, x.y); y.x = fmaf(y.x, c2, x.y);    // c y.re + x.im
