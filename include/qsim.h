@@ -85,7 +85,13 @@ int destroyQuESTEnv(QuESTEnv env);
 int syncQuESTEnv(QuESTEnv env);
 /* setEnvOption: runtime options (values are integers).
  *   "fusion"        0 = one kernel pass per gate, 1 = queue gates and apply
- *                   them in shared-memory tiles at flush time (default 1)
+ *                   them in shared-memory tiles at flush time (default 1).
+ *                   The flush planner rewrites the queued gates exactly
+ *                   (consecutive phases merge, gates on qubits still in |0>
+ *                   since the register was zeroed become copies or vanish,
+ *                   general 2x2 gates run as phase-rotation-phase, scalar
+ *                   factors are applied once per flush): results equal
+ *                   applying the gates one by one up to rounding.
  *   "tile_qubits"   k of a fused tile, 0 = automatic
  *   "max_fused_ops" cap on operations per fused pass (0 = automatic)
  *   "budget_bytes"  cap on the register memory of this env (0 = none)
@@ -135,7 +141,9 @@ int setAmps(Qureg q, const Complex *src, int64_t start, int64_t count);
 int getNumQubits(Qureg q, int *out);
 int getNumAmps(Qureg q, int64_t *out);
 /* getQuregInfo: any output pointer may be null.  devicePtr is the register's
- * amplitude array (valid until destroyQureg; the caller must sync first). */
+ * amplitude array (valid until destroyQureg; the caller must sync first).
+ * The caller may write amplitudes through it: asking for it makes the
+ * library drop what it knows about the register's contents. */
 int getQuregInfo(Qureg q, int *numQubits, int *isDensity, int *precision,
                  void **devicePtr);
 
