@@ -99,6 +99,7 @@ void ensure_stage(Env& env) {
 
 void init_zero(Reg& r) {
   r.queue.clear();
+  r.pend_scale = 1.0;
   r.zero_bits = r.nq >= 64 ? ~uint64_t(0) : (uint64_t(1) << r.nq) - 1;
   const size_t amp = r.prec == QS_C128 ? sizeof(double2) : sizeof(float2);
   QS_CUDA(cudaMemsetAsync(r.d, 0, size_t(r.dim) * amp, r.env->stream));
@@ -366,6 +367,7 @@ int initPlusState(Qureg q) {
     const double v = r.density ? std::ldexp(1.0, -r.n) : 1.0 / std::sqrt(double(r.dim));
     launch_fill(*r.env, r, v, 0.0);
     r.zero_bits = 0;
+    r.pend_scale = 1.0;
   });
 }
 
@@ -441,6 +443,7 @@ int getQuregInfo(Qureg q, int* numQubits, int* isDensity, int* precision, void**
     if (isDensity) *isDensity = r.density ? 1 : 0;
     if (precision) *precision = r.prec;
     if (devicePtr) {
+      flush(r);  // the amplitudes as stored must be the register's values
       *devicePtr = r.d;
       r.zero_bits = 0;  // the caller may write the amplitudes
     }

@@ -156,8 +156,9 @@ void build(Batch& b) {
     // every replay starts from |0...0> (the first pass generates it)
     const int nq = b.regs[r]->nq;
     build_plan(*b.regs[r], b.circuits[r], b.k_req, nq >= 64 ? ~uint64_t(0) : (uint64_t(1) << nq) - 1,
-               plans[r]);
+               1.0, plans[r]);
     b.regs[r]->zero_bits = 0;  // the register's contents are the batch's from now on
+    b.regs[r]->pend_scale = 1.0;
     if (!plans[r].fps.empty()) plans[r].fps[0].init = 1;
     maxp = std::max(maxp, plans[r].fps.size());
   }
@@ -327,7 +328,10 @@ int createBatch(QuESTEnv e, const Qureg* regs, int count, int tileQubits, QSBatc
 int runBatch(QSBatch h) {
   return guarded_call([&] {
     Batch& b = batch_of(h);
-    for (Reg* r : b.regs) r->zero_bits = 0;
+    for (Reg* r : b.regs) {
+      r->zero_bits = 0;
+      r->pend_scale = 1.0;
+    }
     run(b);
   });
 }

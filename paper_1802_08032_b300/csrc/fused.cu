@@ -60,8 +60,18 @@ void free_fused_buffers(Env& env) {
   env.fcopied = nullptr;
 }
 
+// Applies a pending scalar factor the fused plans did not absorb.
+void settle_scale(Reg& r) {
+  if (r.pend_scale == std::complex<double>(1.0, 0.0)) return;
+  launch_scale(*r.env, r, r.pend_scale);
+  r.pend_scale = 1.0;
+}
+
 void flush(Reg& r) {
-  if (r.queue.empty()) return;
+  if (r.queue.empty()) {
+    settle_scale(r);
+    return;
+  }
   std::vector<GateOp> q;
   q.swap(r.queue);
   Env& env = *r.env;
@@ -70,6 +80,7 @@ void flush(Reg& r) {
       launch_op(env, r, op);
       note_mixing(r, op);
     }
+    settle_scale(r);
     return;
   }
   // Multi-target gates run as their own passes; the gates between them form
@@ -81,8 +92,10 @@ void flush(Reg& r) {
   auto close = [&](int next) {
     if (!seg.empty()) {
       plans.emplace_back();
-      build_plan(r, seg, 0, r.zero_bits, plans.back());
+      // the pending factor rides on the first plan's final scale (all ops are linear)
+      build_plan(r, seg, 0, r.zero_bits, r.pend_scale, plans.back());
       r.zero_bits = plans.back().zero_out;
+      if (!plans.back().fps.empty()) r.pend_scale = 1.0;
       after.push_back(next);
       seg.clear();
     } else if (next >= 0) {
@@ -139,6 +152,7 @@ void flush(Reg& r) {
     }
     if (after[pi] >= 0) launch_op(env, r, q[size_t(after[pi])]);
   }
+  settle_scale(r);
   QS_CUDA(cudaGetLastError());
 }
 

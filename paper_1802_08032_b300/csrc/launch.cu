@@ -55,8 +55,8 @@ Mat2<R> to_mat(const GateOp& op) {
 }
 
 // Floating-point operations of one pair update (FMA counted as 2).
-constexpr double kPairFlops[5] = {28, 8, 12, 12, 0};  // GEN, H, SX, SY, X
-const char* kPairName[5] = {"gen", "h", "sx", "sy", "x"};
+constexpr double kPairFlops[8] = {28, 8, 12, 12, 0, 4, 4, 4};  // GEN, H, SX, SY, X, unscaled H, SX, SY
+const char* kPairName[8] = {"gen", "h", "sx", "sy", "x", "h", "sx", "sy"};
 
 template <typename R>
 std::string kname(const char* base, const char* kind = nullptr) {
@@ -137,9 +137,23 @@ void launch_typed(Env& env, Reg& r, const GateOp& op) {
   if (!r.density) {
     switch (op.k) {
       case OpK::GEN: sv_pair<R, PK_GEN>(env, r, op); return;
-      case OpK::H: sv_pair<R, PK_H>(env, r, op); return;
-      case OpK::SX: sv_pair<R, PK_SX>(env, r, op); return;
-      case OpK::SY: sv_pair<R, PK_SY>(env, r, op); return;
+      // uncontrolled H / sqrt(X) / sqrt(Y): unscaled, the register keeps the factor
+      case OpK::H:
+        if (op.cmask) return sv_pair<R, PK_H>(env, r, op);
+        sv_pair<R, PK_HU>(env, r, op);
+        r.pend_scale *= std::sqrt(0.5);
+        return;
+      case OpK::SX:
+      case OpK::SY:
+        if (op.cmask) {
+          if (op.k == OpK::SX) sv_pair<R, PK_SX>(env, r, op);
+          else sv_pair<R, PK_SY>(env, r, op);
+          return;
+        }
+        if (op.k == OpK::SX) sv_pair<R, PK_SXU>(env, r, op);
+        else sv_pair<R, PK_SYU>(env, r, op);
+        r.pend_scale *= std::complex<double>(0.5, 0.5);
+        return;
       case OpK::X: sv_pair<R, PK_X>(env, r, op); return;
       case OpK::PHASE: {
         auto bits = ctrl_bits(op.cmask, 1);
@@ -165,9 +179,21 @@ void launch_typed(Env& env, Reg& r, const GateOp& op) {
   const int N = r.n;
   switch (op.k) {
     case OpK::GEN: dm_pair<R, PK_GEN>(env, r, op); return;
-    case OpK::H: dm_pair<R, PK_H>(env, r, op); return;
-    case OpK::SX: dm_pair<R, PK_SX>(env, r, op); return;
-    case OpK::SY: dm_pair<R, PK_SY>(env, r, op); return;
+    // uncontrolled: unscaled row and column updates, factor |f|^2 = 1/2 kept
+    case OpK::H:
+    case OpK::SX:
+    case OpK::SY:
+      if (op.cmask) {
+        if (op.k == OpK::H) dm_pair<R, PK_H>(env, r, op);
+        else if (op.k == OpK::SX) dm_pair<R, PK_SX>(env, r, op);
+        else dm_pair<R, PK_SY>(env, r, op);
+        return;
+      }
+      if (op.k == OpK::H) dm_pair<R, PK_HU>(env, r, op);
+      else if (op.k == OpK::SX) dm_pair<R, PK_SXU>(env, r, op);
+      else dm_pair<R, PK_SYU>(env, r, op);
+      r.pend_scale *= 0.5;
+      return;
     case OpK::X: dm_pair<R, PK_X>(env, r, op); return;
     case OpK::PHASE: {
       KTimer kt(env, kname<R>("dm_phase").c_str(), double(r.dim) * amp_bytes<R>(), double(r.dim) * 3);
@@ -234,7 +260,22 @@ double fetch_result(Env& env) {
 
 }  // namespace
 
+// Unscaled passes grow the stored amplitudes by 1/|pend_scale|: settle the
+// factor before that growth nears the storage format's range.
+static void bound_pending(Env& env, Reg& r) {
+  if (std::abs(r.pend_scale) >= (r.prec == QS_C64 ? 1e-9 : 1e-100)) return;
+  launch_scale(env, r, r.pend_scale);
+  r.pend_scale = 1.0;
+}
+
+static void launch_op_impl(Env& env, Reg& r, const GateOp& op);
+
 void launch_op(Env& env, Reg& r, const GateOp& op) {
+  launch_op_impl(env, r, op);
+  bound_pending(env, r);
+}
+
+static void launch_op_impl(Env& env, Reg& r, const GateOp& op) {
   if (r.prec == QS_C128) launch_typed<double>(env, r, op);
   else launch_typed<float>(env, r, op);
   check_launch();
@@ -310,6 +351,18 @@ void launch_fill(Env& env, Reg& r, double re, double im) {
     k_fill<double><<<g, kThreads, 0, env.stream>>>(static_cast<double2*>(r.d), r.dim, re, im);
   else
     k_fill<float><<<g, kThreads, 0, env.stream>>>(static_cast<float2*>(r.d), r.dim, float(re), float(im));
+  check_launch();
+}
+
+void launch_scale(Env& env, Reg& r, std::complex<double> f) {
+  const int g = grid_for(env, r.dim, 1);
+  KTimer kt(env, r.prec == QS_C128 ? "scale_c128" : "scale_c64",
+            2.0 * double(r.dim) * (r.prec == QS_C128 ? 16 : 8), 6.0 * double(r.dim));
+  if (r.prec == QS_C128)
+    k_scale<double><<<g, kThreads, 0, env.stream>>>(static_cast<double2*>(r.d), r.dim, f.real(), f.imag());
+  else
+    k_scale<float><<<g, kThreads, 0, env.stream>>>(static_cast<float2*>(r.d), r.dim, float(f.real()),
+                                                   float(f.imag()));
   check_launch();
 }
 

@@ -14,7 +14,11 @@ namespace qs {
 // ---------------------------------------------------------------- pair ops
 // Gate classes of the paper's benchmark set (Sec. II.C) with their own
 // arithmetic, plus the general 2x2 matrix (Eq. 1).
-enum PairKind { PK_GEN = 0, PK_H = 1, PK_SX = 2, PK_SY = 3, PK_X = 4 };
+// The U forms are H, sqrt(X), sqrt(Y) without their scalar factors (1/sqrt 2,
+// (1+i)/2, and (1-i)/2 for conjugated column updates), which the register
+// then carries (Reg::pend_scale): [[1, 1], [1, -1]], [[1, -i], [-i, 1]]
+// (conj: [[1, i], [i, 1]]), [[1, -1], [1, 1]].
+enum PairKind { PK_GEN = 0, PK_H = 1, PK_SX = 2, PK_SY = 3, PK_X = 4, PK_HU = 5, PK_SXU = 6, PK_SYU = 7 };
 
 // (x, y) <- G (x, y); CONJ applies conj(G) instead (Eq. 2 column update).
 template <typename R, int K, bool CONJ>
@@ -55,6 +59,16 @@ __device__ __forceinline__ void pair_apply(cvec<R>& x, cvec<R>& y, const Mat2<R>
     }
   } else if constexpr (K == PK_X) {
     x.x = yr; x.y = yi; y.x = xr; y.y = xi;
+  } else if constexpr (K == PK_HU) {
+    x.x = xr + yr; x.y = xi + yi; y.x = xr - yr; y.y = xi - yi;
+  } else if constexpr (K == PK_SXU) {
+    if constexpr (!CONJ) {
+      x.x = xr + yi; x.y = xi - yr; y.x = yr + xi; y.y = yi - xr;
+    } else {
+      x.x = xr - yi; x.y = xi + yr; y.x = yr - xi; y.y = yi + xr;
+    }
+  } else if constexpr (K == PK_SYU) {
+    x.x = xr - yr; x.y = xi - yi; y.x = xr + yr; y.y = xi + yi;
   }
 }
 
@@ -257,6 +271,19 @@ __global__ void k_fill(cvec<R>* __restrict__ a, int64_t count, R re, R im) {
   for (int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; n < count; n += nthr) {
     cvec<R> v; v.x = re; v.y = im;
     a[n] = v;
+  }
+}
+
+// a <- a (re + i im): applies a register's pending scalar factor.
+template <typename R>
+__global__ void k_scale(cvec<R>* __restrict__ a, int64_t count, R re, R im) {
+  const int64_t nthr = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; n < count; n += nthr) {
+    const cvec<R> v = a[n];
+    cvec<R> w;
+    w.x = re * v.x - im * v.y;
+    w.y = im * v.x + re * v.y;
+    a[n] = w;
   }
 }
 

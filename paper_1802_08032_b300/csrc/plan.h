@@ -36,6 +36,9 @@ Arith arith_of(const Reg& r);
 // env's tile_qubits option).
 // zero_in: bits known to hold only zeros before q (see Reg::zero_bits); the
 // bits still known zero after q are returned in out.zero_out.
-void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, uint64_t zero_in, RegPlan& out);
+// scale_in: a scalar to apply to the whole register as well (folded into
+// the plan's final scale when the plan has passes).
+void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, uint64_t zero_in,
+                std::complex<double> scale_in, RegPlan& out);
 
 }  // namespace qs

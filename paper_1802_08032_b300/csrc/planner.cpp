@@ -519,11 +519,12 @@ void fold_dephasing(std::vector<VOp>& ops) {
 int popc(uint64_t x) { return __builtin_popcountll(x); }
 
 std::vector<Pass> plan(const std::vector<VOp>& ops, int nq, int k, int L, int64_t max_ops,
-                       int scale_limit) {
+                       int scale_limit, std::complex<double> scale_in) {
   std::vector<Pass> passes;
   std::vector<VOp> rem = ops;
   ScaleState scale;
   scale.limit = scale_limit;
+  scale.g = scale_in;
   const uint64_t low = (uint64_t(1) << L) - 1;
   while (!rem.empty()) {
     Pass p;
@@ -789,7 +790,8 @@ Arith arith_of(const Reg& r) {
   return r.env->arith == 1 ? Arith::DF : Arith::F64;
 }
 
-void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, uint64_t zero_in, RegPlan& out) {
+void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, uint64_t zero_in,
+                std::complex<double> scale_in, RegPlan& out) {
   const Env& env = *r.env;
   const TileCfg cfg = tile_cfg(r);
   int k = std::min(cfg.kmax, r.nq);
@@ -821,7 +823,8 @@ void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, uint64_t 
   if (r.density) fold_dephasing(vops);
   const int64_t cap = env.max_fused_ops > 0 ? std::min<int64_t>(env.max_fused_ops, kMaxPassOps)
                                             : kMaxPassOps;
-  const std::vector<Pass> passes = plan(vops, r.nq, k, L, cap, out.arith == Arith::F64 ? 1000 : 80);
+  const std::vector<Pass> passes =
+      plan(vops, r.nq, k, L, cap, out.arith == Arith::F64 ? 1000 : 80, scale_in);
   for (const Pass& p : passes) {
     FPass fp{};
     fp.k = k;

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <complex>
 #include <cstdint>
 #include <functional>
 #include <memory>
@@ -89,6 +90,12 @@ struct Reg {
   // amplitudes along b.  The planner turns gates on such bits into copies
   // or drops them.  Cleared whenever amplitudes are written from outside.
   uint64_t zero_bits = 0;
+  // Scalar every amplitude is to be multiplied by: the factors that unfused
+  // uncontrolled H / sqrt(X) / sqrt(Y) passes leave out (they apply the
+  // matrices without them).  Applied at the next flush (by the fused plan's
+  // final scale, or by one scaling pass), before anything reads the
+  // amplitudes.
+  std::complex<double> pend_scale{1.0, 0.0};
 };
 
 struct Env {
@@ -183,6 +190,8 @@ double reduce_outcome(Env& env, Reg& r, int q, int o);
 double reduce_purity(Env& env, Reg& r);
 void launch_collapse(Env& env, Reg& r, int q, int o, double scale);
 void launch_fill(Env& env, Reg& r, double re, double im);
+// Multiplies every amplitude by f (settles Reg::pend_scale).
+void launch_scale(Env& env, Reg& r, std::complex<double> f);
 void launch_convert(Env& env, const void* src, void* dst, int64_t count, bool to_double);
 
 }  // namespace qs

@@ -272,7 +272,7 @@ int main(int argc, char** argv) {
     std::vector<GateOp> g;
     convert_ops(r, ops.data(), int64_t(ops.size()), g);
     // a zeroed register unless told otherwise (argument 7 = 0)
-    build_plan(r, g, k_req, fresh ? (uint64_t(1) << r.nq) - 1 : 0, pl);
+    build_plan(r, g, k_req, fresh ? (uint64_t(1) << r.nq) - 1 : 0, 1.0, pl);
   } catch (const Error& e) {
     std::printf("ERROR %d %s\n", e.code, e.msg.c_str());
     return 1;

@@ -171,3 +171,54 @@ def test_raw_pointer_clears_tracking(Q, env):
     got = Q.copyStateToHost(q)
     Q.destroyQureg(q)
     assert np.max(np.abs(got - O.State(n, amps=psi).run(ops).a)) <= AMP_TOL[128]
+
+
+@pytest.mark.parametrize("prec", [128, 64])
+@pytest.mark.parametrize("density", [False, True])
+def test_unfused_pending_scale(Q, env, prec, density):
+    """Unfused uncontrolled H / sqrt(X) / sqrt(Y) passes leave their scalar
+    factors to the register; reductions, collapse, copies and a later fused
+    flush must all see the scaled values, and 600 such passes (float range:
+    the factor is settled before it underflows) stay finite."""
+    n = 3 if density else 8
+    rng = C.SplitMix64(600 + prec + density)
+    kinds = ("H", "SX", "SY", "T", "CZ")
+    ops = []
+    for _ in range(600):
+        k = kinds[rng.below(5)]
+        if k == "CZ":
+            a, b = C.distinct_qubits(rng, n, 2)
+            ops.append(C.Op("CZ", (a, b)))
+        else:
+            ops.append(C.Op(k, (rng.below(n),)))
+    Q.setEnvOption(env, "fusion", 0)
+    try:
+        q = (Q.createDensityQureg if density else Q.createQureg)(n, prec, env)
+        ref = O.State(n, density=density)
+        Q.applyCircuit(q, ops[:300])
+        ref.run(ops[:300])
+        tol = 1e-12 if prec == 128 else 1e-5
+        assert abs(Q.calcTotalProb(q) - ref.total_prob()) <= tol
+        assert abs(Q.calcProbOfOutcome(q, 1, 0) - ref.prob_outcome(1, 0)) <= tol
+        if density:
+            assert abs(Q.calcPurity(q) - ref.purity()) <= tol
+        Q.applyCircuit(q, ops[300:450])
+        ref.run(ops[300:450])
+        p = Q.collapseToOutcome(q, 0, 1)
+        assert abs(p - ref.collapse(0, 1)) <= (1e-12 if prec == 128 else 1e-5)
+        Q.applyCircuit(q, ops[450:])
+        ref.run(ops[450:])
+        got = Q.copyStateToHost(q)
+        assert np.all(np.isfinite(got))
+        assert np.max(np.abs(got - ref.a)) <= AMP_TOL[prec] * (10 if prec == 64 else 1)
+        Q.setEnvOption(env, "fusion", 1)
+        more = [C.Op("SX", (1,)), C.Op("T", (2,)), C.Op("H", (0,))]
+        Q.hadamard(q, 1)  # queued again: fused with `more` at the next copy
+        ref.gate(1, O.MAT_H)
+        Q.applyCircuit(q, more)
+        ref.run(more)
+        got = Q.copyStateToHost(q)
+        Q.destroyQureg(q)
+        assert np.max(np.abs(got - ref.a)) <= AMP_TOL[prec] * (10 if prec == 64 else 1)
+    finally:
+        Q.setEnvOption(env, "fusion", 1)
