@@ -157,16 +157,16 @@ struct PlainArith {
     w.y = v.y * f;
     return w;
   }
-  // Depolarising mix of the diagonal pair (x, y) = (rho_00, rho_11) with
-  // move = m: (x + m (y - x), y - m (y - x)), one subtraction and two FMAs
-  // per component (keep = 1 - m is implied).
+  // Depolarising mix of the diagonal pair (x, y) = (rho_00, rho_11) up to
+  // the deferred factor 1 - m: (x + r y, y + r x), r = c0, one FMA per
+  // component.
   __device__ static void depol_mix(Cplx& x, Cplx& y, const FOp& op) {
-    const R m = cf(op, 1);
-    const R dx = y.x - x.x, dy = y.y - x.y;
-    x.x = fma(m, dx, x.x);
-    x.y = fma(m, dy, x.y);
-    y.x = fma(-m, dx, y.x);
-    y.y = fma(-m, dy, y.y);
+    const R r = cf(op, 0);
+    const Cplx u = x;
+    x.x = fma(r, y.x, u.x);
+    x.y = fma(r, y.y, u.y);
+    y.x = fma(r, u.x, y.x);
+    y.y = fma(r, u.y, y.y);
   }
 };
 
@@ -249,16 +249,13 @@ struct DFArith {
     const df f = cf(op, e);
     return dfc2_mulv(v, f2(f.hi, f.hi), f2(f.lo, f.lo));
   }
-  __device__ static Cplx axpby(const Cplx& a, const Cplx& b, const FOp& op) {
-    const df keep = cf(op, 0), move = cf(op, 1);
-    return dfc2_add(dfc2_mulv(a, f2(keep.hi, keep.hi), f2(keep.lo, keep.lo)),
-                    dfc2_mulv(b, f2(move.hi, move.hi), f2(move.lo, move.lo)));
-  }
-  // (keep x + move y, keep y + move x)
+  // (x + r y, y + r x), r = c0
   __device__ static void depol_mix(Cplx& x, Cplx& y, const FOp& op) {
+    const df r = cf(op, 0);
+    const float2 rh = f2(r.hi, r.hi), rl = f2(r.lo, r.lo);
     const Cplx x0 = x;
-    x = axpby(x0, y, op);
-    y = axpby(y, x0, op);
+    x = dfc2_add(x0, dfc2_mulv(y, rh, rl));
+    y = dfc2_add(y, dfc2_mulv(x0, rh, rl));
   }
 };
 
@@ -314,11 +311,17 @@ __device__ __forceinline__ void depol_on_bits(typename A::Cplx (&v)[1 << R], con
 #pragma unroll
   for (int j = 0; j < (1 << R); ++j) {
     if (j & ((1 << I0) | (1 << I1))) continue;
-    const int a = j, b = j | (1 << I0), c = j | (1 << I1), d = j | (1 << I0) | (1 << I1);
-    A::depol_mix(v[a], v[d], op);
-    v[b] = A::scale(v[b], op, 2);
-    v[c] = A::scale(v[c], op, 2);
+    A::depol_mix(v[j], v[j | (1 << I0) | (1 << I1)], op);
   }
+}
+
+// Dephasing-form scale by c0 of the amplitudes whose register bits I0 and I1
+// differ (a compile-time half of the register amplitudes).
+template <class A, int R, int I0, int I1>
+__device__ __forceinline__ void deph_on_bits(typename A::Cplx (&v)[1 << R], const FOp& op) {
+#pragma unroll
+  for (int j = 0; j < (1 << R); ++j)
+    if (((j >> I0) ^ (j >> I1)) & 1) v[j] = A::scale(v[j], op, 0);
 }
 
 // Mask of register indices j with bit i clear, as a bit set over j (R <= 5).
@@ -374,6 +377,7 @@ __device__ __forceinline__ void run_op(typename A::Cplx (&v)[1 << R], const FOp&
     QS_BIT_CASES(FC_X, (pair_on_bit<A, R, PK_X, false, true, I>(v, rmask, op)))
     QS_BIT_CASES(FC_PHASE_BIT, (phase_on_bit<A, R, I>(v, op)))
     QS_PAIR_CASES(FC_DEPOL, (depol_on_bits<A, R, IA, IB>(v, op)))
+    QS_PAIR_CASES(FC_DEPH_PAIR, (deph_on_bits<A, R, IA, IB>(v, op)))
     QS_BIT_CASES(FC_MULI_BIT, (muli_on_bit<A, R, I>(v)))
     QS_BIT_CASES(FC_SHEAR, (shear_on_bit<A, R, I, 0>(v, op)))
     QS_BIT_CASES(FC_SHEAR2, (shear_on_bit<A, R, I, 1>(v, op)))

@@ -11,7 +11,10 @@ enum FKind : uint8_t {
   FK_PHASE = 5,   // multiply by (c0, c1) where the condition holds
   FK_SIGN = 6,    // negate where the condition holds
   FK_DEPH = 7,    // scale by c0 where bit A != bit B
-  FK_DEPOL = 8,   // depolarising quad on register bits (i0 = row bit, i1 = column bit)
+  FK_DEPOL = 8,   // depolarising quad on register bits (i0 = row bit, i1 = column bit):
+                  // the diagonal pair only, (x, y) -> (x + r y, y + r x), r = c0 (the
+                  // off-diagonal factor and the common factor 1 - m are deferred, see
+                  // the planner)
   FK_SCALE = 9,   // multiply every amplitude by the complex (c0, c1)
   FK_MULI = 10,   // multiply by i where the condition holds (no arithmetic)
   FK_SHEAR = 11,  // pair op: (x, y) -> (x - t y, y + u x), or (t x - y, x + t y): a real
@@ -49,7 +52,8 @@ enum FFamily : uint8_t {
   FC_SIGN = 10, FC_DEPH = 11, FC_DEPOL = 12, FC_SCALE = 13,
   FC_MULI_BIT = 14, FC_MULI_ALL = 15, FC_MULI_MASK = 16,
   FC_SHEAR = 17, FC_SHEAR2 = 18,  // (x - t y, y + t x); (t x - y, x + t y)
-  FC_PHASEU_BIT = 19, FC_PHASEU_ALL = 20
+  FC_PHASEU_BIT = 19, FC_PHASEU_ALL = 20,
+  FC_DEPH_PAIR = 21  // FK_DEPH whose two bits are register bits (pair slot)
 };
 constexpr int kCodeSlots = 16;
 // FOp::flags

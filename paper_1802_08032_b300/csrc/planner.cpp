@@ -490,30 +490,68 @@ void unscale_phases(std::vector<VOp>& ops) {
   }
 }
 
-// A dephasing on qubit bits (t, t + N) only scales the entries whose row
-// and column bits differ; a depolarising quad on the same bits scales those
-// entries by its "off" factor and mixes the others.  When no operation
-// between them mixes amplitudes along either bit (every such operation
-// commutes with the diagonal dephasing), the dephasing factor folds into
-// the depolarising one and the dephasing is dropped.
-void fold_dephasing(std::vector<VOp>& ops) {
-  std::vector<bool> drop(ops.size(), false);
-  for (size_t i = 0; i < ops.size(); ++i) {
-    if (ops[i].kind != FK_DEPH) continue;
-    const uint64_t bits = (uint64_t(1) << ops[i].b0) | (uint64_t(1) << ops[i].b1);
-    for (size_t j = i + 1; j < ops.size(); ++j) {
-      if ((ops[j].xmask() & bits) == 0) continue;
-      if (ops[j].kind == FK_DEPOL && ops[j].b0 == ops[i].b0 && ops[j].b1 == ops[i].b1) {
-        ops[j].c[2] *= ops[i].c[0];
-        drop[i] = true;
-      }
-      break;
+// Channels on a density matrix (Eq. 2 vectorisation: row bit t, column bit
+// t + N).  A dephasing scales the entries whose row and column bits differ
+// (the off-diagonal ones in t) by 1 - 2p; a depolarising channel scales them
+// by 1 - 4p/3 and mixes the diagonal pair (x, y) into ((1 - m) x + m y,
+// m x + (1 - m) y), m = 2p/3.  Written as
+//   (1 - m) * [ off -> (s / (1 - m)) off,  (x, y) -> (x + r y, y + r x) ],
+// r = m / (1 - m), the common factor 1 - m joins the plan's final scale and
+// the off-diagonal factor is kept per qubit, F[t]: an entrywise real scale
+// commutes with every operation that does not mix amplitudes along bit t or
+// t + N (diagonal ops; pair updates, depolarising mixes and dephasings on
+// other qubits move or mix entries with equal bits t and t + N; a
+// depolarising mix on t itself moves only diagonal entries).  So consecutive
+// channels on t multiply into F[t], which one dephasing-form op applies just
+// before the next pair update on t or t + N, or at the end of the plan.  The
+// depolarising op left in the list is the diagonal mix alone (4 FMAs a quad
+// instead of 10 operations).  Returns the common factor; a FK_SCALE carries
+// it earlier if it falls below 2^-30.
+double defer_offdiag(std::vector<VOp>& ops, int N) {
+  std::vector<double> F(size_t(N), 1.0);
+  double G = 1.0;
+  std::vector<VOp> out;
+  out.reserve(ops.size() + size_t(N));
+  auto settle = [&](int t) {
+    if (F[size_t(t)] == 1.0) return;
+    VOp d;
+    d.kind = FK_DEPH;
+    d.b0 = t;
+    d.b1 = t + N;
+    d.c[0] = F[size_t(t)];
+    out.push_back(d);
+    F[size_t(t)] = 1.0;
+  };
+  for (const VOp& v : ops) {
+    if (v.kind == FK_DEPH) {
+      F[size_t(v.b0)] *= v.c[0];
+      continue;
     }
+    if (v.kind == FK_DEPOL) {
+      const double keep = v.c[0], move = v.c[1], off = v.c[2];
+      F[size_t(v.b0)] *= off / keep;
+      G *= keep;
+      VOp d = v;
+      d.c[0] = move / keep;
+      d.c[1] = d.c[2] = 0.0;
+      out.push_back(d);
+      if (G < 0x1p-30) {
+        VOp sc;
+        sc.kind = FK_SCALE;
+        sc.c[0] = G;
+        out.push_back(sc);
+        G = 1.0;
+      }
+      continue;
+    }
+    const uint64_t x = v.xmask();
+    for (int t = 0; t < N; ++t)
+      if (((x >> t) | (x >> (t + N))) & 1) settle(t);
+    out.push_back(v);
   }
-  size_t w = 0;
-  for (size_t i = 0; i < ops.size(); ++i)
-    if (!drop[i]) ops[w++] = ops[i];
-  ops.resize(w);
+  for (int t = 0; t < N; ++t) settle(t);
+  ops.swap(out);
+  return G;
 }
 
 int popc(uint64_t x) { return __builtin_popcountll(x); }
@@ -598,7 +636,9 @@ int dispatch_code(const FOp& f) {
       if (f.rmask == 0) return FC_MULI_ALL * S;
       if (popc(f.rmask) == 1) return FC_MULI_BIT * S + __builtin_ctz(f.rmask);
       return FC_MULI_MASK * S;
-    case FK_DEPH: return FC_DEPH * S;
+    case FK_DEPH:
+      if (f.asrc == BS_REG && f.bsrc == BS_REG) return FC_DEPH_PAIR * S + pair_slot(f.apos, f.bpos);
+      return FC_DEPH * S;
     case FK_DEPOL: return FC_DEPOL * S + pair_slot(f.i0, f.i1);
     default: return FC_SCALE * S;
   }
@@ -632,6 +672,9 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
       const uint32_t c = local_mask(v.cond);
       if (popc(c) <= R) need |= c;
     }
+    // a dephasing on two register bits runs over a compile-time half of the
+    // register amplitudes
+    if (v.kind == FK_DEPH) need |= local_mask(v.zmask());
     return need;
   };
   size_t i = 0;
@@ -733,14 +776,14 @@ double vop_flops(const VOp& v, int nq) {
   if (v.kind == FK_PHASEU) return dim * f * 4;
   if (v.kind == FK_SCALE) return dim * 6;
   if (v.kind == FK_DEPH) return dim / 2 * 2;
-  if (v.kind == FK_DEPOL) return dim / 4 * 16;
+  if (v.kind == FK_DEPOL) return dim / 4 * 8;
   return 0;
 }
 
 // Arithmetic instructions (add, multiply, FMA: 1 each) one vector op issues,
 // in the precision of the kernel's arithmetic.  Plain FP32/FP64 per pair:
 // general 16, H / sqrt(X) / sqrt(Y) / shear 4; per touched amplitude: phase 4,
-// dephasing 2; per quad: depolarising 10; per amplitude: scale 4.
+// dephasing 2; per quad: depolarising 4 (diagonal mix); per amplitude: scale 4.
 // Double-float (packed: one instruction covers the real and imaginary
 // parts): complex df add 11, multiply by a df factor 8, complex df product
 // 27; in FP32-lane terms each packed instruction counts twice.
@@ -756,7 +799,7 @@ double vop_alu(const VOp& v, int nq, Arith a) {
   if (v.kind == FK_PHASEU) return dim * f * (d ? 2 * 27 : 2);
   if (v.kind == FK_SCALE) return dim * (d ? 2 * 27 : 4);
   if (v.kind == FK_DEPH) return dim / 2 * (d ? 2 * 8 : 2);
-  if (v.kind == FK_DEPOL) return dim / 4 * (d ? 2 * (2 * 27 + 2 * 8) : 10);
+  if (v.kind == FK_DEPOL) return dim / 4 * (d ? 2 * 2 * (11 + 8) : 4);
   return 0;
 }
 
@@ -820,7 +863,7 @@ void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, uint64_t 
   decompose_general(vops, out.arith == Arith::F64 ? 16.0 : 1.0);
   merge_phases(vops, r.nq);
   if (out.arith != Arith::DF) unscale_phases(vops);
-  if (r.density) fold_dephasing(vops);
+  if (r.density) scale_in *= defer_offdiag(vops, r.n);
   const int64_t cap = env.max_fused_ops > 0 ? std::min<int64_t>(env.max_fused_ops, kMaxPassOps)
                                             : kMaxPassOps;
   const std::vector<Pass> passes =

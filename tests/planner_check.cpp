@@ -80,7 +80,7 @@ static void check_plan(const RegPlan& pl, int nq) {
       for (int o = st.op_begin; o < st.op_end; ++o) {
         const FOp& f = pl.fops[P.op_begin + o];
         const int fam = f.code / kCodeSlots, slot = f.code % kCodeSlots;
-        CHECK(fam <= FC_PHASEU_ALL, "op %d: family %d", o, fam);
+        CHECK(fam <= FC_DEPH_PAIR, "op %d: family %d", o, fam);
         CHECK(f.rmask < (1u << R), "op %d: rmask", o);
         CHECK((f.lmask & pm) == 0 && (f.lmask >> k) == 0, "op %d: lmask on a register / non-tile bit", o);
         CHECK((f.gmask & tile) == 0 && (nq == 64 || (f.gmask >> nq) == 0), "op %d: gmask inside the tile", o);
@@ -102,6 +102,14 @@ static void check_plan(const RegPlan& pl, int nq) {
           slot_pair(slot, a, b);
           CHECK(b < R && std::min<int>(f.i0, f.i1) == a && std::max<int>(f.i0, f.i1) == b, "op %d: depol bits", o);
         }
+        if (fam == FC_DEPH_PAIR) {
+          int a, b;
+          slot_pair(slot, a, b);
+          CHECK(b < R && f.asrc == BS_REG && f.bsrc == BS_REG &&
+                    std::min<int>(f.apos, f.bpos) == a && std::max<int>(f.apos, f.bpos) == b,
+                "op %d: dephasing register bits", o);
+        }
+        if (fam == FC_DEPH) CHECK(f.asrc != BS_REG || f.bsrc != BS_REG, "op %d: dephasing form", o);
       }
     }
     CHECK(next == P.op_count, "pass %zu: stages cover %d of %d ops", pi, next, P.op_count);
@@ -223,17 +231,20 @@ static std::vector<cd> emulate(const RegPlan& pl, int nq) {
               };
               for (int j = 0; j < nj; ++j)
                 if (bv(f.asrc, f.apos, j) != bv(f.bsrc, f.bpos, j)) v[j] *= c(0);
-            } else if (fam == FC_DEPOL) {
+            } else if (fam == FC_DEPH_PAIR) {
+              int a, b;
+              slot_pair(slot, a, b);
+              for (int j = 0; j < nj; ++j)
+                if (((j >> a) ^ (j >> b)) & 1) v[j] *= c(0);
+            } else if (fam == FC_DEPOL) {  // the diagonal pair only: (x + r y, y + r x)
               int a, b;
               slot_pair(slot, a, b);
               for (int j = 0; j < nj; ++j) {
                 if ((j >> a) & 1 || (j >> b) & 1) continue;
-                const int ja = j | (1 << a), jb = j | (1 << b), jd = j | (1 << a) | (1 << b);
+                const int jd = j | (1 << a) | (1 << b);
                 const cd d0 = v[j], d1 = v[jd];
-                v[j] = c(0) * d0 + c(1) * d1;
-                v[jd] = c(0) * d1 + c(1) * d0;
-                v[ja] *= c(2);
-                v[jb] *= c(2);
+                v[j] = d0 + c(0) * d1;
+                v[jd] = d1 + c(0) * d0;
               }
             }
           }

@@ -152,3 +152,23 @@ def test_30_qubit_workload_plan_invariants(harness, prec, arith):
     head, _ = run(harness, 30, C.workload_30q(), prec=prec, arith=arith, emulate=False)
     passes = int(head.split()[2])
     assert 0 < passes <= 40, head
+
+
+@pytest.mark.parametrize("p_depol", [0.6, 0.75])
+@pytest.mark.parametrize("arith", [0, 1])
+def test_planned_density_matrix_heavy_noise(harness, p_depol, arith):
+    """Strong channels: the deferred common factor (1 - 2p/3 per
+    depolarising channel) passes 2^-30 and is applied mid-plan; p = 3/4
+    zeroes the off-diagonal entries (r = 1).  Runs of channels on one qubit
+    with only diagonal gates between them share one deferred off-diagonal
+    factor."""
+    N = 4
+    gates = C.random_circuit(N, 8, 500 + int(p_depol * 100), extras=True)
+    ops = C.with_noise(gates, 0.3, p_depol)
+    extra = [C.Op("T", (1,)), C.Op("CZ", (1, 2)), C.Op("DEPOL", (1,), (), (p_depol,)),
+             C.Op("DEPHASE", (1,), (), (0.2,)), C.Op("T", (1,)), C.Op("DEPOL", (1,), (), (0.1,)),
+             C.Op("SX", (1,))]
+    ops = ops[: len(ops) // 2] + extra + ops[len(ops) // 2:]
+    head, rho = run(harness, N, ops, density=True, arith=arith)
+    ref = O.run_circuit(N, ops, density=True).a
+    assert np.max(np.abs(rho - ref)) <= 1e-12, head
