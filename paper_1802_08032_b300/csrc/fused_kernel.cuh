@@ -115,9 +115,10 @@ struct PlainArith {
     }
     return w;
   }
-  // (1 + i t) v, t = c0: the unscaled phase
+  // (1 + i t) v, t = c[E]: the unscaled phase
+  template <int E = 0>
   __device__ static Cplx phase_u(const Cplx& v, const FOp& op) {
-    const R t = cf(op, 0);
+    const R t = cf(op, E);
     Cplx w;
     w.x = fma(-t, v.y, v.x);
     w.y = fma(t, v.x, v.y);
@@ -225,8 +226,9 @@ struct DFArith {
   }
   __device__ static Cplx phase(const Cplx& v, const FOp& op) { return dfc2_cmul(v, cf(op, 0), cf(op, 1)); }
   __device__ static Cplx mul_i(const Cplx& v) { return mul_plus_i(v); }
+  template <int E = 0>
   __device__ static Cplx phase_u(const Cplx& v, const FOp& op) {
-    return dfc2_cmul(v, df{1.f, 0.f}, cf(op, 0));
+    return dfc2_cmul(v, df{1.f, 0.f}, cf(op, E));
   }
   template <int MODE>
   __device__ static void shear(Cplx& x, Cplx& y, const FOp& op) {
@@ -315,6 +317,18 @@ __device__ __forceinline__ void depol_on_bits(typename A::Cplx (&v)[1 << R], con
   }
 }
 
+// Row / column phase pair on register bits I0 < I1: (1 + i c0) where only
+// I0 is set, (1 + i c1) where only I1 is set.
+template <class A, int R, int I0, int I1>
+__device__ __forceinline__ void offph_on_bits(typename A::Cplx (&v)[1 << R], const FOp& op) {
+#pragma unroll
+  for (int j = 0; j < (1 << R); ++j) {
+    const int lo = (j >> I0) & 1, hi = (j >> I1) & 1;
+    if (lo && !hi) v[j] = A::template phase_u<0>(v[j], op);
+    if (!lo && hi) v[j] = A::template phase_u<1>(v[j], op);
+  }
+}
+
 // Dephasing-form scale by c0 of the amplitudes whose register bits I0 and I1
 // differ (a compile-time half of the register amplitudes).
 template <class A, int R, int I0, int I1>
@@ -378,6 +392,7 @@ __device__ __forceinline__ void run_op(typename A::Cplx (&v)[1 << R], const FOp&
     QS_BIT_CASES(FC_PHASE_BIT, (phase_on_bit<A, R, I>(v, op)))
     QS_PAIR_CASES(FC_DEPOL, (depol_on_bits<A, R, IA, IB>(v, op)))
     QS_PAIR_CASES(FC_DEPH_PAIR, (deph_on_bits<A, R, IA, IB>(v, op)))
+    QS_PAIR_CASES(FC_OFFPH, (offph_on_bits<A, R, IA, IB>(v, op)))
     QS_BIT_CASES(FC_MULI_BIT, (muli_on_bit<A, R, I>(v)))
     QS_BIT_CASES(FC_SHEAR, (shear_on_bit<A, R, I, 0>(v, op)))
     QS_BIT_CASES(FC_SHEAR2, (shear_on_bit<A, R, I, 1>(v, op)))

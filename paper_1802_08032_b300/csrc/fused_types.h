@@ -20,8 +20,12 @@ enum FKind : uint8_t {
   FK_SHEAR = 11,  // pair op: (x, y) -> (x - t y, y + u x), or (t x - y, x + t y): a real
                   // rotation up to a factor deferred like the dropped ones (c0 = t, c4 = u;
                   // u = t unless a phase's factor passes through, see the planner)
-  FK_PHASEU = 12  // multiply by (1 + i t) where the condition holds (c0 = t): a phase
-                  // whose real factor the next pair update on its bit applies
+  FK_PHASEU = 12,  // multiply by (1 + i t) where the condition holds (c0 = t): a phase
+                   // whose real factor the next pair update on its bit applies
+  FK_OFFPH = 13    // density-matrix phase pair on register bits i0 < i1: multiply by
+                   // (1 + i c0) where bit i0 = 1, bit i1 = 0 and by (1 + i c1) where
+                   // bit i0 = 0, bit i1 = 1 (a row phase and its conjugate column
+                   // phase; the real factor is deferred with the off-diagonal ones)
 };
 // H, sqrt(X) and sqrt(Y) carry one coefficient, c0: a real factor applied to
 // their bit-1 input y (1 unless a preceding FK_PHASEU on the bit left its
@@ -53,7 +57,8 @@ enum FFamily : uint8_t {
   FC_MULI_BIT = 14, FC_MULI_ALL = 15, FC_MULI_MASK = 16,
   FC_SHEAR = 17, FC_SHEAR2 = 18,  // (x - t y, y + t x); (t x - y, x + t y)
   FC_PHASEU_BIT = 19, FC_PHASEU_ALL = 20,
-  FC_DEPH_PAIR = 21  // FK_DEPH whose two bits are register bits (pair slot)
+  FC_DEPH_PAIR = 21,  // FK_DEPH whose two bits are register bits (pair slot)
+  FC_OFFPH = 22       // pair slot
 };
 constexpr int kCodeSlots = 16;
 // FOp::flags

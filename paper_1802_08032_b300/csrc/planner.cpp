@@ -32,7 +32,9 @@ struct VOp {
 
   uint64_t xmask() const {
     if (kind <= FK_X || kind == FK_SHEAR) return uint64_t(1) << b0;
-    if (kind == FK_DEPOL) return (uint64_t(1) << b0) | (uint64_t(1) << b1);
+    // (a row / column phase pair is diagonal, but it must run on register
+    // bits: counting its bits as moved keeps them in the tile)
+    if (kind == FK_DEPOL || kind == FK_OFFPH) return (uint64_t(1) << b0) | (uint64_t(1) << b1);
     return 0;
   }
   uint64_t zmask() const {
@@ -507,6 +509,11 @@ void unscale_phases(std::vector<VOp>& ops) {
 // depolarising op left in the list is the diagonal mix alone (4 FMAs a quad
 // instead of 10 operations).  Returns the common factor; a FK_SCALE carries
 // it earlier if it falls below 2^-30.
+// A gate's phase e^{i phi} on row bit t and its conjugate on column bit t + N
+// (Eq. 2) cancel on the diagonal entries and give e^{+-i phi} on the two
+// off-diagonal halves: when nothing between them moves amplitudes along t or
+// t + N, the two phases become one op, (1 +- i tan phi) on the off-diagonal
+// entries only, and cos phi joins F[t].
 double defer_offdiag(std::vector<VOp>& ops, int N) {
   std::vector<double> F(size_t(N), 1.0);
   double G = 1.0;
@@ -522,10 +529,39 @@ double defer_offdiag(std::vector<VOp>& ops, int N) {
     out.push_back(d);
     F[size_t(t)] = 1.0;
   };
-  for (const VOp& v : ops) {
+  std::vector<bool> used(ops.size(), false);
+  for (size_t i = 0; i < ops.size(); ++i) {
+    const VOp& v = ops[i];
+    if (used[i]) continue;
     if (v.kind == FK_DEPH) {
       F[size_t(v.b0)] *= v.c[0];
       continue;
+    }
+    if (v.kind == FK_PHASE && __builtin_popcountll(v.cond) == 1 && __builtin_ctzll(v.cond) < N &&
+        std::abs(v.c[0]) >= 0.5) {
+      const int t = __builtin_ctzll(v.cond);
+      const uint64_t col = uint64_t(1) << (t + N), both = v.cond | col;
+      size_t j = i + 1;
+      for (; j < ops.size(); ++j) {
+        const VOp& w = ops[j];
+        if (!used[j] && w.kind == FK_PHASE && w.cond == col) break;
+        if (w.xmask() & both) {
+          j = ops.size();
+          break;
+        }
+      }
+      if (j < ops.size() && ops[j].c[0] == v.c[0] && ops[j].c[1] == -v.c[1]) {
+        used[j] = true;
+        F[size_t(t)] *= v.c[0];
+        VOp o;
+        o.kind = FK_OFFPH;
+        o.b0 = t;
+        o.b1 = t + N;
+        o.c[0] = v.c[1] / v.c[0];  // where row bit = 1, column bit = 0
+        o.c[1] = -o.c[0];
+        out.push_back(o);
+        continue;
+      }
     }
     if (v.kind == FK_DEPOL) {
       const double keep = v.c[0], move = v.c[1], off = v.c[2];
@@ -640,6 +676,7 @@ int dispatch_code(const FOp& f) {
       if (f.asrc == BS_REG && f.bsrc == BS_REG) return FC_DEPH_PAIR * S + pair_slot(f.apos, f.bpos);
       return FC_DEPH * S;
     case FK_DEPOL: return FC_DEPOL * S + pair_slot(f.i0, f.i1);
+    case FK_OFFPH: return FC_OFFPH * S + pair_slot(f.i0, f.i1);
     default: return FC_SCALE * S;
   }
 }
@@ -718,8 +755,9 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
       FOp f{};
       f.kind = v.kind;
       f.conj = v.conj ? 1 : 0;
-      if (v.kind <= FK_X || v.kind == FK_SHEAR || v.kind == FK_DEPOL) f.i0 = uint8_t(idx[lpos[v.b0]]);
-      if (v.kind == FK_DEPOL) f.i1 = uint8_t(idx[lpos[v.b1]]);
+      if (v.kind <= FK_X || v.kind == FK_SHEAR || v.kind == FK_DEPOL || v.kind == FK_OFFPH)
+        f.i0 = uint8_t(idx[lpos[v.b0]]);
+      if (v.kind == FK_DEPOL || v.kind == FK_OFFPH) f.i1 = uint8_t(idx[lpos[v.b1]]);
       if (v.kind == FK_SHEAR) f.i1 = v.c[1] != 0.0 ? 1 : 0;
       for (int b = 0; b < 64; ++b) {
         if (!((v.cond >> b) & 1)) continue;
@@ -737,6 +775,10 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
         src(v.b1, f.bsrc, f.bpos);
       }
       set_coeffs(f, v.c, arith);
+      if (v.kind == FK_OFFPH && f.i0 > f.i1) {  // c0 belongs to the lower register bit
+        double c[8] = {v.c[1], v.c[0]};
+        set_coeffs(f, c, arith);
+      }
       if (v.kind == FK_PHASE || v.kind == FK_PHASEU || v.kind == FK_SIGN || v.kind == FK_MULI) {
         uint32_t touch = 0;  // register amplitudes j whose index has every rmask bit
         for (int j = 0; j < (1 << R); ++j)
@@ -777,6 +819,7 @@ double vop_flops(const VOp& v, int nq) {
   if (v.kind == FK_SCALE) return dim * 6;
   if (v.kind == FK_DEPH) return dim / 2 * 2;
   if (v.kind == FK_DEPOL) return dim / 4 * 8;
+  if (v.kind == FK_OFFPH) return dim / 2 * 4;
   return 0;
 }
 
@@ -800,6 +843,7 @@ double vop_alu(const VOp& v, int nq, Arith a) {
   if (v.kind == FK_SCALE) return dim * (d ? 2 * 27 : 4);
   if (v.kind == FK_DEPH) return dim / 2 * (d ? 2 * 8 : 2);
   if (v.kind == FK_DEPOL) return dim / 4 * (d ? 2 * 2 * (11 + 8) : 4);
+  if (v.kind == FK_OFFPH) return dim / 2 * (d ? 2 * 27 : 2);
   return 0;
 }
 

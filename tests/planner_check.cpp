@@ -80,7 +80,7 @@ static void check_plan(const RegPlan& pl, int nq) {
       for (int o = st.op_begin; o < st.op_end; ++o) {
         const FOp& f = pl.fops[P.op_begin + o];
         const int fam = f.code / kCodeSlots, slot = f.code % kCodeSlots;
-        CHECK(fam <= FC_DEPH_PAIR, "op %d: family %d", o, fam);
+        CHECK(fam <= FC_OFFPH, "op %d: family %d", o, fam);
         CHECK(f.rmask < (1u << R), "op %d: rmask", o);
         CHECK((f.lmask & pm) == 0 && (f.lmask >> k) == 0, "op %d: lmask on a register / non-tile bit", o);
         CHECK((f.gmask & tile) == 0 && (nq == 64 || (f.gmask >> nq) == 0), "op %d: gmask inside the tile", o);
@@ -110,6 +110,13 @@ static void check_plan(const RegPlan& pl, int nq) {
                 "op %d: dephasing register bits", o);
         }
         if (fam == FC_DEPH) CHECK(f.asrc != BS_REG || f.bsrc != BS_REG, "op %d: dephasing form", o);
+        if (fam == FC_OFFPH) {
+          int a, b;
+          slot_pair(slot, a, b);
+          CHECK(b < R && std::min<int>(f.i0, f.i1) == a && std::max<int>(f.i0, f.i1) == b && f.rmask == 0 &&
+                    f.lmask == 0 && f.gmask == 0,
+                "op %d: row / column phase bits", o);
+        }
       }
     }
     CHECK(next == P.op_count, "pass %zu: stages cover %d of %d ops", pi, next, P.op_count);
@@ -231,6 +238,14 @@ static std::vector<cd> emulate(const RegPlan& pl, int nq) {
               };
               for (int j = 0; j < nj; ++j)
                 if (bv(f.asrc, f.apos, j) != bv(f.bsrc, f.bpos, j)) v[j] *= c(0);
+            } else if (fam == FC_OFFPH) {  // (1 + i c0) where only bit a is set, (1 + i c1) only b
+              int a, b;
+              slot_pair(slot, a, b);
+              for (int j = 0; j < nj; ++j) {
+                const int lo = (j >> a) & 1, hi = (j >> b) & 1;
+                if (lo && !hi) v[j] *= cd(1.0, c(0));
+                if (!lo && hi) v[j] *= cd(1.0, c(1));
+              }
             } else if (fam == FC_DEPH_PAIR) {
               int a, b;
               slot_pair(slot, a, b);
