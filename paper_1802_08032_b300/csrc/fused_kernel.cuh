@@ -102,13 +102,12 @@ struct PlainArith {
     return w;
   }
   // FP64: flip the sign bits (integer pipe; the FP64 pipe is the bottleneck).
-  // FP32: multiply by -1 (exact; full-rate FMA pipe instead of the busier
-  // integer pipe).
+  // FP32: multiply by -1 (exact; the FMA pipe instead of the busier integer
+  // pipe), one paired multiply for both parts.
   __device__ static Cplx negate(const Cplx& v) {
     Cplx w;
     if constexpr (sizeof(R) == 4) {
-      w.x = __fmul_rn(v.x, -1.f);
-      w.y = __fmul_rn(v.y, -1.f);
+      w = __fmul2_rn(v, make_float2(-1.f, -1.f));
     } else {
       w.x = neg_bits(v.x);
       w.y = neg_bits(v.y);
