@@ -557,7 +557,9 @@ def batch_variant(Q, env, torch, stream, count=4096, depth=30):
 
 def multi_sweep(Q, env, torch, stream, n=30):
     """One dense 2^m x 2^m gate (targets 7..7+m-1) as a single pass over a
-    30-qubit register: algorithmic GB/s (read + write of every amplitude)."""
+    30-qubit register: algorithmic GB/s (read + write of every amplitude).
+    Complex64 with m = 4, 5 runs on the tensor cores; those are also timed
+    on the CUDA cores and with the targets on the lowest bits."""
     import numpy as np
     out = {}
     Q.setEnvOption(env, "fusion", 0)
@@ -567,10 +569,22 @@ def multi_sweep(Q, env, torch, stream, n=30):
             S = 16 if prec == 128 else 8
             try:
                 for m in range(1, 6):
-                    U = np.linalg.qr(np.random.default_rng(m).normal(size=(1 << m, 1 << m)) + 0j)[0]
+                    g = np.random.default_rng(m)
+                    U = np.linalg.qr(g.normal(size=(1 << m, 1 << m)) + 1j * g.normal(size=(1 << m, 1 << m)))[0]
                     tg = tuple(range(7, 7 + m))
                     ms = timed(torch, stream, lambda: Q.multiQubitUnitary(q, tg, U), 2)
                     out[f"c{prec}_m{m}"] = {"ms": ms, "GBps": 2 * (1 << n) * S / ms / 1e6}
+                    if prec == 64 and m >= 4:
+                        # the same pass on the CUDA cores, and with the targets on the lowest bits
+                        Q.setEnvOption(env, "multi_tc", 0)
+                        try:
+                            ms = timed(torch, stream, lambda: Q.multiQubitUnitary(q, tg, U), 2)
+                        finally:
+                            Q.setEnvOption(env, "multi_tc", 1)
+                        out[f"c64_m{m}_cuda_cores"] = {"ms": ms, "GBps": 2 * (1 << n) * S / ms / 1e6}
+                        low = tuple(range(m))
+                        ms = timed(torch, stream, lambda: Q.multiQubitUnitary(q, low, U), 2)
+                        out[f"c64_m{m}_low_targets"] = {"ms": ms, "GBps": 2 * (1 << n) * S / ms / 1e6}
             finally:
                 Q.destroyQureg(q)
     finally:

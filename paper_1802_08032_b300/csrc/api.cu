@@ -202,10 +202,16 @@ int createQuESTEnv(QuESTEnv* out) {
       QS_CUDA(cudaMalloc(&env->d_partial, sizeof(double) * 4096));
       QS_CUDA(cudaMalloc(&env->d_result, sizeof(double) * 64));
       QS_CUDA(cudaMallocHost(&env->h_result, sizeof(double) * 64));
+      QS_CUDA(cudaMalloc(&env->d_status, sizeof(unsigned)));
+      QS_CUDA(cudaMemset(env->d_status, 0, sizeof(unsigned)));
+      QS_CUDA(cudaMallocHost(&env->h_status, sizeof(unsigned)));
+      *env->h_status = 0;
     } catch (...) {
       if (env->own) cudaStreamDestroy(env->own);
       if (env->d_partial) cudaFree(env->d_partial);
       if (env->d_result) cudaFree(env->d_result);
+      if (env->h_result) cudaFreeHost(env->h_result);
+      if (env->d_status) cudaFree(env->d_status);
       delete env;
       throw;
     }
@@ -234,6 +240,8 @@ int destroyQuESTEnv(QuESTEnv e) {
     cudaFree(env.d_partial);
     cudaFree(env.d_result);
     cudaFreeHost(env.h_result);
+    cudaFree(env.d_status);
+    cudaFreeHost(env.h_status);
     if (env.d_stage) cudaFree(env.d_stage);
     cudaStreamDestroy(env.own);
     g_envs.erase(env.id);
@@ -250,8 +258,10 @@ int syncQuESTEnv(QuESTEnv e) {
       for (int64_t id : env.regs) regs.push_back(g_regs.at(id));
     }
     for (Reg* r : regs) flush(*r);
+    QS_CUDA(cudaMemcpyAsync(env.h_status, env.d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, env.stream));
     QS_CUDA(cudaStreamSynchronize(env.stream));
     QS_CUDA(cudaGetLastError());
+    check_status(env);
   });
 }
 
@@ -286,6 +296,9 @@ int setEnvOption(QuESTEnv e, const char* key, int64_t value) {
     } else if (k == "profile") {
       if (value != 0 && value != 1) fail(QS_E_ARG, "profile must be 0 or 1");
       env.profile = value;
+    } else if (k == "multi_tc") {
+      if (value != 0 && value != 1) fail(QS_E_ARG, "multi_tc must be 0 or 1");
+      env.multi_tc = value;
     } else {
       fail(QS_E_ARG, "unknown option " + k);
     }
@@ -305,6 +318,7 @@ int getEnvOption(QuESTEnv e, const char* key, int64_t* value) {
     else if (k == "used_bytes") *value = env.used;
     else if (k == "profile") *value = env.profile;
     else if (k == "arith") *value = env.arith;
+    else if (k == "multi_tc") *value = env.multi_tc;
     else if (k == "launches") *value = env.launches;
     else if (k == "fused_passes") *value = env.fused_passes;
     else if (k == "fused_vops") *value = env.fused_vops;

@@ -3,6 +3,7 @@
 #include <cmath>
 
 #include "multi_kernels.cuh"
+#include "tc_multi.cuh"
 #include "pass_kernels.cuh"
 #include "reduce_kernels.cuh"
 #include "runtime.h"
@@ -92,6 +93,28 @@ void dm_pair(Env& env, Reg& r, const GateOp& op) {
       op.cmask << N, fx, to_mat<R>(op));
 }
 
+// Complex64 multi-target pass on the tensor cores (tc_multi.cuh): a
+// persistent grid of 128-thread CTAs, as many per SM as shared memory holds.
+template <int M>
+void multi_pass_tc(Env& env, Reg& r, const MultiParams<float, M>& mp, const Fixed& fx, int64_t nsel) {
+  TcParams<M> p{};
+  for (int k = 0; k < 8; ++k) p.t[k] = mp.t[k];
+  for (int e = 0; e < (1 << (2 * M)); ++e) p.u[e] = make_float2(mp.u[e].x, mp.u[e].y);
+  constexpr size_t smem = tc_smem_bytes<M>();
+  static bool attr = false;
+  if (!attr) {
+    QS_CUDA(cudaFuncSetAttribute(k_sv_multi_tc<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    attr = true;
+  }
+  const int64_t ntiles = (nsel + kTcRows - 1) / kTcRows;
+  const int per_sm = std::max(1, std::min(4, int((227 * 1024) / (smem + 1024))));
+  const int grid = int(std::min<int64_t>(ntiles, int64_t(env.sms) * per_sm));
+  // algorithmic flops: 2^m complex multiply-adds (8 flops) per amplitude
+  KTimer kt(env, "sv_multi_tc_c64", double(nsel) * 2 * (1 << M) * sizeof(float2),
+            double(nsel) * (1 << (2 * M)) * 8);
+  k_sv_multi_tc<M><<<grid, kTcRows, smem, env.stream>>>(static_cast<float2*>(r.d), nsel, fx, p, env.d_status);
+}
+
 // One multi-target pass over the vector: targets t (shifted by `shift`),
 // controls cmask, matrix (conjugated when conj).
 template <typename R, int M>
@@ -109,6 +132,12 @@ void multi_pass(Env& env, Reg& r, const GateOp& op, int shift, uint64_t cmask, b
   }
   const Fixed fx = make_fixed(bits);
   const int64_t nsel = r.dim >> fx.n;
+  if constexpr (std::is_same<R, float>::value && M >= 4) {
+    if (env.multi_tc) {
+      multi_pass_tc<M>(env, r, p, fx, nsel);
+      return;
+    }
+  }
   KTimer kt(env, kname<R>("sv_multi").c_str(), double(nsel) * 2 * (1 << M) * amp_bytes<R>(),
             double(nsel) * (1 << (2 * M)) * 8);
   k_sv_multi<R, M><<<grid_for(env, nsel, 1), kThreads, 0, env.stream>>>(static_cast<cvec<R>*>(r.d), nsel,
@@ -254,11 +283,21 @@ double fetch_result(Env& env) {
   check_launch();
   QS_CUDA(cudaMemcpyAsync(env.h_result, env.d_result, sizeof(double), cudaMemcpyDeviceToHost,
                           env.stream));
+  QS_CUDA(cudaMemcpyAsync(env.h_status, env.d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, env.stream));
   QS_CUDA(cudaStreamSynchronize(env.stream));
+  check_status(env);
   return env.h_result[0];
 }
 
 }  // namespace
+
+void check_status(Env& env) {
+  const unsigned s = *env.h_status;
+  if (s == 0) return;
+  *env.h_status = 0;
+  QS_CUDA(cudaMemsetAsync(env.d_status, 0, sizeof(unsigned), env.stream));
+  fail(QS_E_TIMEOUT, "a bounded device wait ran out (tensor-core multi-target pass); amplitudes are unreliable");
+}
 
 // Unscaled passes grow the stored amplitudes by 1/|pend_scale|: settle the
 // factor before that growth nears the storage format's range.

@@ -112,6 +112,7 @@ struct Env {
   int64_t used = 0;
   int64_t profile = 0;
   int64_t arith = 0;         // complex128 arithmetic of fused passes: 0 = IEEE FP64, 1 = double-float
+  int64_t multi_tc = 1;      // complex64 dense gates on 4-5 targets on the tensor cores (0 = CUDA cores)
   Profiler prof;
   // counters (readable through getEnvOption)
   int64_t launches = 0;      // kernel launches issued
@@ -125,6 +126,10 @@ struct Env {
   double* d_partial = nullptr;
   double* d_result = nullptr;
   double* h_result = nullptr;
+  // device status word: kernels set bits when a bounded device wait runs
+  // out; read (and cleared) at the next synchronisation, see check_status
+  unsigned* d_status = nullptr;
+  unsigned* h_status = nullptr;
   // staging buffer for complex64 <-> complex128 copies
   double2* d_stage = nullptr;
   int64_t stage_amps = 0;
@@ -153,6 +158,11 @@ class KTimer {
   int cls_ = -1;
   cudaEvent_t a_ = nullptr;
 };
+
+// Fails with QS_E_TIMEOUT (and clears the word) if a kernel reported a
+// bounded wait that ran out; h_status must have been copied from d_status
+// and the stream synchronised.
+void check_status(Env& env);
 
 // Message returned by qsLastError on this thread (api.cu).
 void set_last_error(const std::string& msg);

@@ -1,0 +1,267 @@
+// Dense multi-target gates on complex64 state vectors on the tensor cores
+// (tcgen05, sm_100-family).  A gate U on m targets maps every block of 2^m
+// amplitudes v (the amplitudes that differ only in the target bits, Eq. 1
+// with the pair replaced by a block) to U v.  For 128 blocks at a time this
+// is one real matrix product
+//     W^T = V^T B,   V^T: 128 x 2^(m+1) rows [Re v, Im v],
+//     B (2^(m+1) x 2^(m+1)) = [[Re U^T, Im U^T], [-Im U^T, Re U^T]],
+// so row b of the result is [Re (U v_b), Im (U v_b)].  The operands are
+// FP32; the tensor cores multiply TF32 (11 significant bits), so each
+// operand is split x = hi + lo with hi = x rounded to TF32 and lo = x - hi
+// (exact, at most 12 significant bits, of which TF32 keeps 11), and the
+// product is accumulated as lo*hi + hi*lo + hi*hi in FP32 (the dropped
+// lo*lo term and the lost bit of lo are about 2^-23 relative): close to
+// FP32 accuracy (measured: a few units of 1e-7 of the largest amplitude per
+// gate).
+//
+// Per CTA: 128 threads, one block (GEMM row) per thread.  Operands in
+// shared memory in the no-swizzle K-major core-matrix layout (8 rows x 16
+// bytes per core matrix; consecutive core matrices 128 bytes apart along
+// the rows, R*16 bytes apart along K), the accumulator (128 lanes x
+// 2^(m+1) FP32 columns) in tensor memory.  One thread issues the MMAs and
+// commits them to an mbarrier; every thread waits (bounded), reads its row
+// back with tcgen05.ld and scatters it.  The next tile's gather is issued
+// before the wait, so global loads overlap the MMAs and the stores.
+#pragma once
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace qs {
+
+constexpr int kTcRows = 128;  // GEMM rows (blocks) per tile = threads per CTA
+
+template <int MT>
+struct TcParams {
+  uint8_t t[8];                     // target qubits; bit k of the block index is t[k]
+  float2 u[1 << (2 * MT)];          // row-major matrix
+};
+
+// Shared-memory bytes of one CTA: A hi/lo (128 x K), B hi/lo (N x K), the
+// block offsets, the mbarrier and the tensor-memory address slot.
+template <int MT>
+__host__ __device__ constexpr size_t tc_smem_bytes() {
+  return size_t(2) * kTcRows * (2 << MT) * 4 + size_t(2) * (2 << MT) * (2 << MT) * 4 +
+         sizeof(int64_t) * (1 << MT) + 64;
+}
+
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading byte
+// offset (between core matrices along K), stride byte offset (between core
+// matrices along M / N), all in 16-byte units; bits 46-48 = 0b001; no
+// swizzle, base offset 0.
+__device__ __forceinline__ uint64_t desc(uint32_t addr, uint32_t kstride, uint32_t rstride) {
+  return uint64_t((addr >> 4) & 0x3FFFu) | (uint64_t((kstride >> 4) & 0x3FFFu) << 16) |
+         (uint64_t((rstride >> 4) & 0x3FFFu) << 32) | (uint64_t(1) << 46);
+}
+
+// Instruction descriptor, kind::tf32: FP32 accumulator, TF32 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Bounded wait for the phase with the given parity (each try_wait suspends
+// for at most a short, system-defined time).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// x rounded to the nearest TF32 value (ties away from zero); x - tf32_hi(x)
+// is exact in FP32 and has at most 12 significant bits.
+__device__ __forceinline__ float tf32_hi(float x) {
+  uint32_t h;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+  return __uint_as_float(h);
+}
+
+// Element (r, k) of an R-row K-major operand, in floats.
+template <int R>
+__device__ __forceinline__ int at(int r, int k) {
+  return (k >> 2) * (R * 4) + (r >> 3) * 32 + (r & 7) * 4 + (k & 3);
+}
+
+#define QS_R32(m, r, o)                                                                              \
+  m(r[o + 0]), m(r[o + 1]), m(r[o + 2]), m(r[o + 3]), m(r[o + 4]), m(r[o + 5]), m(r[o + 6]), m(r[o + 7]), \
+      m(r[o + 8]), m(r[o + 9]), m(r[o + 10]), m(r[o + 11]), m(r[o + 12]), m(r[o + 13]), m(r[o + 14]),     \
+      m(r[o + 15]), m(r[o + 16]), m(r[o + 17]), m(r[o + 18]), m(r[o + 19]), m(r[o + 20]), m(r[o + 21]),   \
+      m(r[o + 22]), m(r[o + 23]), m(r[o + 24]), m(r[o + 25]), m(r[o + 26]), m(r[o + 27]), m(r[o + 28]),   \
+      m(r[o + 29]), m(r[o + 30]), m(r[o + 31])
+#define QS_OUT(x) "=r"(x)
+#define QS_INOUT(x) "+r"(x)
+
+// Columns [O, O + 32) of the accumulator, this warp's 32 lanes, into
+// r[O .. O + 32).  Asynchronous: the registers hold the values only after
+// wait_ld, which takes them as operands so that no use moves above it.
+template <int O, int N>
+__device__ __forceinline__ void ld32(uint32_t taddr, uint32_t (&r)[N]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : QS_R32(QS_OUT, r, O)
+      : "r"(taddr));
+}
+
+template <int N>
+__device__ __forceinline__ void wait_ld(uint32_t (&r)[N]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" : QS_R32(QS_INOUT, r, 0)::"memory");
+  if constexpr (N > 32) asm volatile("" : QS_R32(QS_INOUT, r, 32));
+}
+
+}  // namespace tc
+
+// status: bit 0 set when a bounded wait for the tensor cores ran out (the
+// kernel then stops; the amplitudes of unfinished tiles are unchanged or
+// partly written).
+template <int MT>
+__global__ void __launch_bounds__(kTcRows) k_sv_multi_tc(float2* __restrict__ a, int64_t nsel, Fixed fx,
+                                                        const __grid_constant__ TcParams<MT> p,
+                                                        unsigned* status) {
+  constexpr int D2 = 1 << MT, KD = 2 * D2, ND = 2 * D2;
+  constexpr uint32_t kA = kTcRows * KD * 4, kB = ND * KD * 4;  // bytes of one A / B operand
+  constexpr uint32_t kIdesc = tc::idesc_tf32(kTcRows, ND);
+  extern __shared__ __align__(1024) uint8_t smem[];
+  float* sAh = reinterpret_cast<float*>(smem);
+  float* sAl = reinterpret_cast<float*>(smem + kA);
+  float* sBh = reinterpret_cast<float*>(smem + 2 * kA);
+  float* sBl = reinterpret_cast<float*>(smem + 2 * kA + kB);
+  int64_t* toff = reinterpret_cast<int64_t*>(smem + 2 * kA + 2 * kB);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * kA + 2 * kB + sizeof(int64_t) * D2);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+
+  // B = [[Re U^T, Im U^T], [-Im U^T, Re U^T]] stored N x K (row n = output
+  // column): row n < D2 gives Re w[n], row D2 + n gives Im w[n].
+  for (int e = tid; e < ND * KD; e += kTcRows) {
+    const int n = e / KD, k = e % KD;
+    const float2 u = p.u[(n & (D2 - 1)) * D2 + (k & (D2 - 1))];
+    const float v = n < D2 ? (k < D2 ? u.x : -u.y) : (k < D2 ? u.y : u.x);
+    const float h = tc::tf32_hi(v);
+    sBh[tc::at<ND>(n, k)] = h;
+    sBl[tc::at<ND>(n, k)] = v - h;
+  }
+  if (tid < D2) {
+    int64_t o = 0;
+    for (int k = 0; k < MT; ++k)
+      if ((tid >> k) & 1) o += int64_t(1) << p.t[k];
+    toff[tid] = o;
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tslot)),
+                 "r"(uint32_t(ND)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+  const uint32_t bar_a = tc::smem_u32(bar);
+  const uint32_t ah = tc::smem_u32(sAh), al = tc::smem_u32(sAl), bh = tc::smem_u32(sBh), bl = tc::smem_u32(sBl);
+
+  const int64_t ntiles = (nsel + kTcRows - 1) / kTcRows;
+  float2 v[D2];
+  int64_t tile = blockIdx.x;
+  int64_t j = 0;
+  bool live = false;
+  auto gather = [&](int64_t t) {
+    const int64_t b = t * kTcRows + tid;
+    live = b < nsel;
+    j = live ? deposit(b, fx) : 0;
+#pragma unroll
+    for (int l = 0; l < D2; ++l) v[l] = live ? a[j + toff[l]] : make_float2(0.f, 0.f);
+  };
+  if (tile < ntiles) gather(tile);
+  uint32_t parity = 0;
+  bool ok = true;
+  for (; tile < ntiles; tile += gridDim.x) {
+    // this thread's row of A = [Re v, Im v], split into TF32 hi and lo
+#pragma unroll
+    for (int kc = 0; kc < KD / 4; ++kc) {
+      float x[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int k = 4 * kc + i;
+        x[i] = k < D2 ? v[k & (D2 - 1)].x : v[k & (D2 - 1)].y;
+      }
+      const float4 h = make_float4(tc::tf32_hi(x[0]), tc::tf32_hi(x[1]), tc::tf32_hi(x[2]), tc::tf32_hi(x[3]));
+      const float4 lo = make_float4(x[0] - h.x, x[1] - h.y, x[2] - h.z, x[3] - h.w);
+      *reinterpret_cast<float4*>(&sAh[tc::at<kTcRows>(tid, 4 * kc)]) = h;
+      *reinterpret_cast<float4*>(&sAl[tc::at<kTcRows>(tid, 4 * kc)]) = lo;
+    }
+    const int64_t jcur = j;
+    const bool lcur = live;
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+      // lo*hi + hi*lo + hi*hi; K advances 8 (two core matrices) per MMA
+      const uint32_t as[3] = {al, ah, ah}, bs[3] = {bh, bl, bh};
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int kk = 0; kk < KD / 8; ++kk)
+          tc::mma_tf32(tmem, tc::desc(as[q] + kk * 2 * (kTcRows * 16), kTcRows * 16, 128),
+                       tc::desc(bs[q] + kk * 2 * (ND * 16), ND * 16, 128), kIdesc, (q | kk) != 0);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_a));
+    }
+    // next tile's amplitudes while the tensor cores work
+    if (tile + gridDim.x < ntiles) gather(tile + gridDim.x);
+    const bool done = tc::mbar_wait(bar_a, parity);
+    parity ^= 1u;
+    if (__syncthreads_or(!done)) {
+      ok = false;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    uint32_t r[ND];
+    const uint32_t trow = tmem + (uint32_t(warp * 32) << 16);
+    tc::ld32<0>(trow, r);
+    if constexpr (ND > 32) tc::ld32<32>(trow + 32u, r);
+    tc::wait_ld(r);
+    if (lcur) {
+#pragma unroll
+      for (int n = 0; n < D2; ++n) a[jcur + toff[n]] = make_float2(__uint_as_float(r[n]), __uint_as_float(r[D2 + n]));
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+  }
+  if (!ok) {
+    if (tid == 0) atomicOr(status, 1u);
+    tc::mbar_wait(bar_a, parity ^ 1u);  // the outstanding commit, bounded
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(ND)));
+}
+
+}  // namespace qs

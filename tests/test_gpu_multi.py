@@ -119,3 +119,51 @@ def test_multi_target_errors(Q, env):
     assert e.value.name == "QS_E_ARG"
     Q.destroyQureg(a)
     Q.destroyQureg(q)
+
+
+@pytest.mark.parametrize("m", [4, 5])
+@pytest.mark.parametrize("ctrls", [(), (2, 17)])
+def test_multi_target_tensor_cores(Q, env, m, ctrls):
+    """Complex64 gates on 4-5 targets run on the tensor cores (three TF32
+    products per FP32 operand pair): many 128-block tiles per CTA, targets on
+    the lowest and highest bits, with and without controls, against the
+    CUDA-core kernel and the oracle."""
+    n = 20
+    psi = rand_state(n, 40 + m)
+    targets = (0, 19, 7, 1, 12)[:m]
+    U = rand_u(1 << m, 50 + m)
+    ref = O.State(n, amps=psi)
+    ref.multi(targets, U, ctrls)
+    out = {}
+    for tc in (1, 0):
+        Q.setEnvOption(env, "multi_tc", tc)
+        q = Q.createQureg(n, 64, env)
+        Q.setAmps(q, psi)
+        Q.multiControlledMultiQubitUnitary(q, ctrls, targets, U)
+        Q.multiControlledMultiQubitUnitary(q, ctrls, targets, U.conj().T)
+        Q.multiControlledMultiQubitUnitary(q, ctrls, targets, U)
+        out[tc] = Q.copyStateToHost(q)
+        Q.destroyQureg(q)
+    Q.setEnvOption(env, "multi_tc", 1)
+    # three gates of 2^(m+1)-term FP32 sums whose products carry about 2^-23
+    # relative error each (the TF32 split): bound 5e-6 of the largest
+    # amplitude, well inside the complex64 bar of 1e-5 absolute
+    scale = np.max(np.abs(ref.a))
+    assert np.max(np.abs(out[1] - ref.a)) <= 5e-6 * scale
+    assert np.max(np.abs(out[1] - out[0])) <= 5e-6 * scale
+
+
+def test_multi_target_tensor_cores_density_matrix(Q, env):
+    N = 8
+    rho = rand_density_vec(N, 9)
+    U = rand_u(32, 77)
+    ref = O.State(N, density=True, amps=rho)
+    ref.multi((6, 0, 3, 7, 2), U, (5,))
+    d = Q.createDensityQureg(N, 64, env)
+    Q.setAmps(d, rho)
+    Q.multiControlledMultiQubitUnitary(d, (5,), (6, 0, 3, 7, 2), U)
+    got = Q.copyStateToHost(d)
+    tr = Q.calcTotalProb(d)
+    Q.destroyQureg(d)
+    assert np.max(np.abs(got - ref.a)) <= 5e-6 * np.max(np.abs(ref.a))
+    assert abs(tr - 1.0) <= 1e-5
