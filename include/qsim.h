@@ -81,7 +81,11 @@ int createQuESTEnv(QuESTEnv *out);
 int destroyQuESTEnv(QuESTEnv env);
 /* syncQuESTEnv: flushes every register's queued gates and waits for the
  * stream (Sec. III: syncQuESTEnv closes the timed region).  Returns
- * QS_E_CUDA on an asynchronous device error. */
+ * QS_E_CUDA on an asynchronous device error, QS_E_TIMEOUT when a kernel
+ * reported a bounded device wait that ran out since the last check (the
+ * tensor-core pass of multi-target gates waits on its MMAs; the affected
+ * amplitudes are unreliable).  Reductions report the same at their next
+ * result. */
 int syncQuESTEnv(QuESTEnv env);
 /* setEnvOption: runtime options (values are integers).
  *   "fusion"        0 = one kernel pass per gate, 1 = queue gates and apply
@@ -102,6 +106,11 @@ int syncQuESTEnv(QuESTEnv env);
  *                   reductions and measurement always use FP64.
  *   "profile"       1 = time every kernel launch with CUDA events (see
  *                   getKernelStats), 0 = off (default)
+ *   "multi_tc"      1 = complex64 multi-target gates on 4-5 targets run on
+ *                   the tensor cores (default; FP32 operands as TF32 hi + lo
+ *                   pairs, three products accumulated in FP32: a few units of
+ *                   1e-7 of the largest amplitude per gate), 0 = FP32 on the
+ *                   CUDA cores
  * Unknown keys give QS_E_ARG. */
 int setEnvOption(QuESTEnv env, const char *key, int64_t value);
 /* getEnvOption: reads an option back, or a counter of the env:
