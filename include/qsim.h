@@ -87,6 +87,14 @@ int destroyQuESTEnv(QuESTEnv env);
  * amplitudes are unreliable).  Reductions report the same at their next
  * result. */
 int syncQuESTEnv(QuESTEnv env);
+/* qsDiagBoundedWait: diagnostic of the device failure path.  Launches, on
+ * the env's stream, one CTA that runs the bounded wait the tensor-core
+ * multi-target pass uses (there: 1 s), on an mbarrier nothing arrives on,
+ * for timeoutUs (1..10^6) microseconds of the GPU's global timer; it then
+ * sets the device status word, so the next syncQuESTEnv (or reduction)
+ * returns QS_E_TIMEOUT and clears it.  No fault, no unbounded wait; the
+ * context stays usable.  QS_E_ARG for a timeoutUs outside the range. */
+int qsDiagBoundedWait(QuESTEnv env, int timeoutUs);
 /* setEnvOption: runtime options (values are integers).
  *   "fusion"        0 = one kernel pass per gate, 1 = queue gates and apply
  *                   them in shared-memory tiles at flush time (default 1).

@@ -265,6 +265,14 @@ int syncQuESTEnv(QuESTEnv e) {
   });
 }
 
+int qsDiagBoundedWait(QuESTEnv e, int timeoutUs) {
+  return guarded([&] {
+    Env& env = env_of(e);
+    if (timeoutUs < 1 || timeoutUs > 1000000) fail(QS_E_ARG, "timeoutUs must be in 1..1000000");
+    launch_wait_probe(env, timeoutUs);
+  });
+}
+
 int setEnvOption(QuESTEnv e, const char* key, int64_t value) {
   return guarded([&] {
     Env& env = env_of(e);

@@ -291,6 +291,11 @@ double fetch_result(Env& env) {
 
 }  // namespace
 
+void launch_wait_probe(Env& env, int timeout_us) {
+  k_wait_probe<<<1, 32, 0, env.stream>>>(env.d_status, uint64_t(timeout_us) * 1000u);
+  check_launch();
+}
+
 void check_status(Env& env) {
   const unsigned s = *env.h_status;
   if (s == 0) return;

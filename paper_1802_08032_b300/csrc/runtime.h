@@ -163,6 +163,8 @@ class KTimer {
 // bounded wait that ran out; h_status must have been copied from d_status
 // and the stream synchronised.
 void check_status(Env& env);
+// Launches the bounded-wait diagnostic kernel (tc_multi.cuh).
+void launch_wait_probe(Env& env, int timeout_us);
 
 // Message returned by qsLastError on this thread (api.cu).
 void set_last_error(const std::string& msg);

@@ -84,12 +84,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return done != 0;
 }
 
-// Bounded wait for the phase with the given parity (each try_wait suspends
-// for at most a short, system-defined time).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < (1 << 22); ++it)
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the phase with the given parity, for at most max_ns nanoseconds
+// of the global timer (each try_wait suspends for at most a short,
+// system-defined time, so the deadline is checked between tries).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t max_ns = 1000000000ull) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
-  return false;
+    if (globaltimer_ns() - t0 > max_ns) return false;
+  }
 }
 
 // x rounded to the nearest TF32 value (ties away from zero); x - tf32_hi(x)
@@ -135,9 +145,9 @@ __device__ __forceinline__ void wait_ld(uint32_t (&r)[N]) {
 
 }  // namespace tc
 
-// status: bit 0 set when a bounded wait for the tensor cores ran out (the
-// kernel then stops; the amplitudes of unfinished tiles are unchanged or
-// partly written).
+// status: bit 0 set when a wait for the tensor cores ran out (1 s of the
+// global timer; the kernel then stops; the amplitudes of unfinished tiles
+// are unchanged or partly written).
 template <int MT>
 __global__ void __launch_bounds__(kTcRows) k_sv_multi_tc(float2* __restrict__ a, int64_t nsel, Fixed fx,
                                                         const __grid_constant__ TcParams<MT> p,
@@ -262,6 +272,20 @@ __global__ void __launch_bounds__(kTcRows) k_sv_multi_tc(float2* __restrict__ a,
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(ND)));
+}
+
+// Diagnostic: the bounded wait of k_sv_multi_tc on an mbarrier that nothing
+// arrives on, so it runs out after max_ns and reports through the status
+// word exactly as the tensor-core pass would.
+__global__ void k_wait_probe(unsigned* status, uint64_t max_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  const bool done = tc::mbar_wait(tc::smem_u32(&bar), 0, max_ns);
+  if (__syncthreads_or(!done) && threadIdx.x == 0) atomicOr(status, 1u);
 }
 
 }  // namespace qs

@@ -102,6 +102,7 @@ SIGNATURES = {
     "createQuESTEnv": [_P(QuESTEnv)],
     "destroyQuESTEnv": [QuESTEnv],
     "syncQuESTEnv": [QuESTEnv],
+    "qsDiagBoundedWait": [QuESTEnv, ctypes.c_int],
     "setEnvOption": [QuESTEnv, ctypes.c_char_p, _I64],
     "getEnvOption": [QuESTEnv, ctypes.c_char_p, _P(_I64)],
     "setAllocator": [QuESTEnv, ALLOC_FN, RELEASE_FN, _VP],
@@ -211,6 +212,10 @@ def destroyQuESTEnv(env: QuESTEnv):
 
 def syncQuESTEnv(env: QuESTEnv):
     _check(LIB.syncQuESTEnv(env))
+
+
+def qsDiagBoundedWait(env: QuESTEnv, timeout_us: int):
+    _check(LIB.qsDiagBoundedWait(env, int(timeout_us)))
 
 
 def setEnvOption(env: QuESTEnv, key: str, value: int):

@@ -167,3 +167,25 @@ def test_multi_target_tensor_cores_density_matrix(Q, env):
     Q.destroyQureg(d)
     assert np.max(np.abs(got - ref.a)) <= 5e-6 * np.max(np.abs(ref.a))
     assert abs(tr - 1.0) <= 1e-5
+
+
+def test_bounded_wait_reports_timeout(Q, env):
+    """The tensor-core pass's bounded mbarrier wait, run on a barrier nothing
+    arrives on: it gives up, the status word turns the next synchronisation
+    into QS_E_TIMEOUT once, and the context stays usable."""
+    Q.qsDiagBoundedWait(env, 2000)  # 2 ms
+    with pytest.raises(Q.QSimError) as e:
+        Q.syncQuESTEnv(env)
+    assert e.value.name == "QS_E_TIMEOUT"
+    Q.syncQuESTEnv(env)  # cleared
+    Q.qsDiagBoundedWait(env, 500)
+    q = Q.createQureg(6, 64, env)
+    Q.hadamard(q, 0)
+    with pytest.raises(Q.QSimError) as e:
+        Q.calcTotalProb(q)  # a reduction reports it too
+    assert e.value.name == "QS_E_TIMEOUT"
+    assert abs(Q.calcTotalProb(q) - 1.0) < 1e-6
+    Q.destroyQureg(q)
+    with pytest.raises(Q.QSimError) as e:
+        Q.qsDiagBoundedWait(env, 0)
+    assert e.value.name == "QS_E_ARG"
