@@ -355,7 +355,7 @@ def main():
     Q.destroyQureg(q)
     if rank == 0 and world == 1 and not args.no_variants:
         line["variants"] = variants(Q, env, torch, stream,
-                                    [v for v in args.variants.split(",") if v])
+                                    [v for v in args.variants.split(",") if v], n)
     if rank == 0 and world == 1:
         try:
             line["cpu_baseline"] = cpu_oracle_sample(n, ops, args.cpu_gates)
@@ -381,12 +381,13 @@ def timed(torch, stream, fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def variants(Q, env, torch, stream, only=()):
+def variants(Q, env, torch, stream, only=(), qubits=30):
     """Other configurations of the same metric, measured outside the timed
     region: complex64 and double-float complex128 at 30 qubits, the 33-qubit
     (128 GiB complex128, 64 GiB complex64) depth-40 circuits, the 14-qubit
     noisy density matrix, single-gate pass bandwidth by target bit, batches,
-    serving and multi-target passes."""
+    serving and multi-target passes (on a register of `qubits` qubits, the
+    headline's size)."""
     out = {}
     ops = C.workload_30q(30)
 
@@ -479,7 +480,7 @@ def variants(Q, env, torch, stream, only=()):
                      ("batch4096_c64", lambda: batch_variant(Q, env, torch, stream)),
                      ("serving", lambda: serve_sweep(Q, env, [10, 30, 100, 300, 1000, 2000], 60,
                                                      baseline_rates=(10, 100))),
-                     ("multi_target_passes", lambda: multi_sweep(Q, env, torch, stream))):
+                     ("multi_target_passes", lambda: multi_sweep(Q, env, torch, stream, qubits))):
         if only and name not in only:
             continue
         try:
@@ -556,8 +557,8 @@ def batch_variant(Q, env, torch, stream, count=4096, depth=30):
 
 
 def multi_sweep(Q, env, torch, stream, n=30):
-    """One dense 2^m x 2^m gate (targets 7..7+m-1) as a single pass over a
-    30-qubit register: algorithmic GB/s (read + write of every amplitude).
+    """One dense 2^m x 2^m gate (targets 7..7+m-1) as a single pass over an
+    n-qubit register: algorithmic GB/s (read + write of every amplitude).
     Complex64 with m = 4, 5 runs on the tensor cores; those are also timed
     on the CUDA cores and with the targets on the lowest bits."""
     import numpy as np

@@ -107,7 +107,7 @@ void multi_pass_tc(Env& env, Reg& r, const MultiParams<float, M>& mp, const Fixe
     attr = true;
   }
   const int64_t ntiles = (nsel + kTcRows - 1) / kTcRows;
-  const int per_sm = std::max(1, std::min(4, int((227 * 1024) / (smem + 1024))));
+  const int per_sm = std::max(1, std::min(8, int((227 * 1024) / (smem + 1024))));
   const int grid = int(std::min<int64_t>(ntiles, int64_t(env.sms) * per_sm));
   // algorithmic flops: 2^m complex multiply-adds (8 flops) per amplitude
   KTimer kt(env, "sv_multi_tc_c64", double(nsel) * 2 * (1 << M) * sizeof(float2),
