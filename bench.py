@@ -57,6 +57,11 @@ def parse():
     ap.add_argument("--arith", default="fp64", choices=["fp64", "df"],
                     help="complex128 arithmetic of fused passes")
     ap.add_argument("--qubits", type=int, default=30)
+    ap.add_argument("--serve-requests", type=int, default=60,
+                    help="serving variant: requests per arrival rate (at most)")
+    ap.add_argument("--serve-seconds", type=float, default=0.0,
+                    help="serving variant: also cap each rate's trace at this many seconds of arrivals "
+                         "(0 = no cap); 2000 and 60 give the full-length sweep")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--variants", default="",
                     help="comma-separated variant names to run (default: all)")
@@ -355,7 +360,8 @@ def main():
     Q.destroyQureg(q)
     if rank == 0 and world == 1 and not args.no_variants:
         line["variants"] = variants(Q, env, torch, stream,
-                                    [v for v in args.variants.split(",") if v], n)
+                                    [v for v in args.variants.split(",") if v], n,
+                                    (args.serve_requests, args.serve_seconds))
     if rank == 0 and world == 1:
         try:
             line["cpu_baseline"] = cpu_oracle_sample(n, ops, args.cpu_gates)
@@ -381,7 +387,7 @@ def timed(torch, stream, fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def variants(Q, env, torch, stream, only=(), qubits=30):
+def variants(Q, env, torch, stream, only=(), qubits=30, serve=(60, 0.0)):
     """Other configurations of the same metric, measured outside the timed
     region: complex64 and double-float complex128 at 30 qubits, the 33-qubit
     (128 GiB complex128, 64 GiB complex64) depth-40 circuits, the 14-qubit
@@ -478,8 +484,8 @@ def variants(Q, env, torch, stream, only=(), qubits=30):
                      ("single_gate_sweep_33q", lambda: sweep(33, [0, 1, 2, 4, 8, 16, 24, 32])),
                      ("dm14_c128", dm14),
                      ("batch4096_c64", lambda: batch_variant(Q, env, torch, stream)),
-                     ("serving", lambda: serve_sweep(Q, env, [10, 30, 100, 300, 1000, 2000], 60,
-                                                     baseline_rates=(10, 100))),
+                     ("serving", lambda: serve_sweep(Q, env, [10, 30, 100, 300, 1000, 2000], serve[0],
+                                                     baseline_rates=(10, 100), seconds=serve[1])),
                      ("multi_target_passes", lambda: multi_sweep(Q, env, torch, stream, qubits))):
         if only and name not in only:
             continue
@@ -646,10 +652,13 @@ def run_trace(Q, env, trace, slots, fusion, force_c128=False):
             "slots_used": len({r["slot"] for r in res})}
 
 
-def serve_sweep(Q, env, rates, per_rate, slots=16, baseline_rates=()):
+def serve_sweep(Q, env, rates, per_rate, slots=16, baseline_rates=(), seconds=0.0):
+    """Per arrival rate: `per_rate` requests, or fewer if `seconds` > 0 caps
+    the trace at that many seconds of arrivals (rate x seconds requests)."""
     out = {}
     for rate in rates:
-        trace = serve_trace(rate, per_rate)
+        count = per_rate if seconds <= 0 else max(1, min(per_rate, int(rate * seconds)))
+        trace = serve_trace(rate, count)
         row = {"served": run_trace(Q, env, trace, slots, 1)}
         if rate in baseline_rates:
             row["plain_c128_one_at_a_time"] = run_trace(Q, env, trace, 1, 0, force_c128=True)
