@@ -138,12 +138,13 @@ void launch_wave(const Batch& b, const Wave& w, cudaStream_t s) {
 
 template <class A, int R>
 void set_batch_attr() {
-  static bool done = false;
-  if (!done) {
+  // once per instantiation (thread-safe static initialisation)
+  static const bool done = [] {
     QS_CUDA(cudaFuncSetAttribute(k_fused_batch<A, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  110 * 1024));
-    done = true;
-  }
+    return true;
+  }();
+  (void)done;
 }
 
 // Plans every register with tile size k_req, uploads, captures the graph.

@@ -17,11 +17,12 @@ template <class A, int R>
 void launch_pass(Env& env, Reg& r, const FPass& fp, const FOp* d_ops, const FStage* d_st,
                  double flops, double alu, const char* name) {
   const size_t smem = fused_smem_bytes<A>(fp.k, fp.L, fp.op_count, fp.stage_end - fp.stage_begin);
-  static bool attr_set = false;
-  if (!attr_set) {
+  // once per instantiation (thread-safe static initialisation)
+  static const bool attr_set = [] {
     QS_CUDA(cudaFuncSetAttribute(k_fused<A, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024));
-    attr_set = true;
-  }
+    return true;
+  }();
+  (void)attr_set;
   const int threads = 1 << (fp.k - R);
   const int64_t grid = std::min<int64_t>(fp.ntiles, int64_t(env.sms) * fused_ctas_per_sm(R));
   const double bytes = std::ldexp(2.0 * sizeof(typename A::Store), r.nq);

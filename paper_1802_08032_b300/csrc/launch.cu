@@ -105,16 +105,17 @@ void multi_pass_tc(Env& env, Reg& r, const MultiParams<float, M>& mp, const Fixe
   // in units of 256), shared memory (228 KB per SM, 1 KB reserved per CTA)
   // and tensor memory (512 columns, 2^(M+1) per CTA) allow: the persistent
   // grid must be resident all at once
-  static int per_sm = 0;
-  if (per_sm == 0) {
+  // (a function-local static: initialised once, thread-safe; the serving
+  // scheduler thread may get here first)
+  static const int per_sm = [] {
     QS_CUDA(cudaFuncSetAttribute(k_sv_multi_tc<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     cudaFuncAttributes fa{};
     QS_CUDA(cudaFuncGetAttributes(&fa, k_sv_multi_tc<M>));
     const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;
     const int by_regs = 65536 / std::max(1, regs_warp * (kTcRows / 32));
     const int by_smem = int((228 * 1024) / (smem + fa.sharedSizeBytes + 1024));
-    per_sm = std::max(1, std::min({by_regs, by_smem, 512 / (2 << M), 8}));
-  }
+    return std::max(1, std::min({by_regs, by_smem, 512 / (2 << M), 8}));
+  }();
   const int64_t ntiles = (nsel + kTcRows - 1) / kTcRows;
   const int grid = int(std::min<int64_t>(ntiles, int64_t(env.sms) * per_sm));
   // algorithmic flops: 2^m complex multiply-adds (8 flops) per amplitude
