@@ -192,6 +192,38 @@ def test_density_circuit_general_gates(Q, env, prec, arith, fusion, N):
 
 
 @pytest.mark.parametrize("prec,arith", [(128, 0), (128, 1), (64, 0)])
+@pytest.mark.parametrize("p_depol", [0.3, 0.75])
+def test_density_circuit_heavy_noise(Q, env, prec, arith, p_depol):
+    """Strong channels after every gate: the fused plan defers each qubit's
+    off-diagonal factor (applied as a register-pair dephasing before the next
+    pair update on the qubit), applies the common factor 1 - 2p/3 of each
+    depolarising channel mid-plan once it passes 2^-30, pairs a T's row and
+    column phases into one off-diagonal op, and at p = 3/4 zeroes every
+    off-diagonal entry of the qubit.  Against the unfused path and the
+    oracle, with the trace and purity."""
+    N = 6
+    ops = C.with_noise(general_gates(N, 90), 0.3, p_depol)
+    ref = O.run_circuit(N, ops, density=True)
+    Q.setEnvOption(env, "arith", arith)
+    try:
+        got = {}
+        for fusion in (1, 0):
+            Q.setEnvOption(env, "fusion", fusion)
+            q = Q.createDensityQureg(N, prec, env)
+            Q.applyCircuit(q, ops)
+            tr, pur = Q.calcTotalProb(q), Q.calcPurity(q)
+            got[fusion] = Q.copyStateToHost(q)
+            Q.destroyQureg(q)
+            assert abs(tr - ref.total_prob()) <= (PROB_TOL if prec == 128 else 1e-5)
+            assert abs(pur - ref.purity()) <= (1e-12 if prec == 128 else 1e-5)
+    finally:
+        Q.setEnvOption(env, "arith", 0)
+        Q.setEnvOption(env, "fusion", 1)
+    for fusion in (1, 0):
+        assert np.max(np.abs(got[fusion] - ref.a)) <= AMP_TOL[prec], fusion
+
+
+@pytest.mark.parametrize("prec,arith", [(128, 0), (128, 1), (64, 0)])
 @pytest.mark.parametrize("n", [6, 11, 14])
 def test_state_vector_general_gates(Q, env, prec, arith, n):
     ops = general_gates(n, 30 + n)
