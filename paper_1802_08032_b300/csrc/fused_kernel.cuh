@@ -37,6 +37,29 @@ struct PlainArith {
   }
   __device__ static Cplx from_store(const Store& s) { return s; }
   __device__ static Store to_store(const Cplx& c) { return c; }
+  // FP64 only: unscaled H / sqrt(X) / sqrt(Y) with a real factor on either
+  // input (see pair_side_on_bit)
+  static constexpr bool kSide = sizeof(R) == 8;
+  // The unscaled butterfly of K applied to (f x, y): one FMA per output
+  // component, f = c0.
+  template <int K, bool CONJ>
+  __device__ static void pair_xs(Cplx& x, Cplx& y, const FOp& op) {
+    const R f = cf(op, 0);
+    const Cplx u = x;
+    if constexpr (K == PK_H) {  // (f x + y, f x - y)
+      x.x = fma(f, u.x, y.x); x.y = fma(f, u.y, y.y);
+      y.x = fma(f, u.x, -y.x); y.y = fma(f, u.y, -y.y);
+    } else if constexpr (K == PK_SX && !CONJ) {  // (f x - i y, -i f x + y)
+      x.x = fma(f, u.x, y.y); x.y = fma(f, u.y, -y.x);
+      y.x = fma(f, u.y, y.x); y.y = fma(-f, u.x, y.y);
+    } else if constexpr (K == PK_SX) {  // (f x + i y, i f x + y)
+      x.x = fma(f, u.x, -y.y); x.y = fma(f, u.y, y.x);
+      y.x = fma(-f, u.y, y.x); y.y = fma(f, u.x, y.y);
+    } else {  // sqrt(Y): (f x - y, f x + y)
+      x.x = fma(f, u.x, -y.x); x.y = fma(f, u.y, -y.y);
+      y.x = fma(f, u.x, y.x); y.y = fma(f, u.y, y.y);
+    }
+  }
   template <int K, bool CONJ>
   __device__ static void pair_t(Cplx& x, Cplx& y, const FOp& op) {
     if constexpr (K == PK_GEN) {
@@ -178,6 +201,7 @@ struct DFArith {
   using Store = double2;
   using Cplx = dfc2;
   __device__ static df cf(const FOp& op, int e) { return df{op.c.f[e], op.c.f[8 + e]}; }
+  static constexpr bool kSide = false;
   __device__ static Cplx from_store(const Store& s) { return dfc2_from_double2(s); }
   __device__ static Store to_store(const Cplx& c) { return dfc2_to_double2(c); }
   // multiply by -i: (re, im) -> (im, -re);  by +i: (re, im) -> (-im, re)
@@ -269,6 +293,22 @@ __device__ __forceinline__ void pair_on_bit(typename A::Cplx (&v)[1 << R], uint3
     if (j & (1 << I)) continue;
     if (MASKED && (uint32_t(j) & rmask) != rmask) continue;
     A::template pair_t<K, CONJ>(v[j], v[j | (1 << I)], op);
+  }
+}
+
+// Unscaled H / sqrt(X) / sqrt(Y) on register bit I with a real factor c0 on
+// the input whose register bit J differs from its bit I: the bit-1 input y
+// where bit J is 0, the bit-0 input x where bit J is 1.  With I, J a density
+// matrix's row and column bits of one qubit these are exactly the entries
+// off the qubit's diagonal: the update applies a deferred off-diagonal
+// factor for free (the planner's channel deferral).
+template <class A, int R, int K, bool CONJ, int I, int J>
+__device__ __forceinline__ void pair_side_on_bit(typename A::Cplx (&v)[1 << R], const FOp& op) {
+#pragma unroll
+  for (int j = 0; j < (1 << R); ++j) {
+    if (j & (1 << I)) continue;
+    if (j & (1 << J)) A::template pair_xs<K, CONJ>(v[j], v[j | (1 << I)], op);
+    else A::template pair_t<K, CONJ>(v[j], v[j | (1 << I)], op);
   }
 }
 
@@ -380,7 +420,22 @@ __device__ __forceinline__ void run_op(typename A::Cplx (&v)[1 << R], const FOp&
   QS_PAIR_CASE(FAM, 4, 1, 2, __VA_ARGS__) QS_PAIR_CASE(FAM, 5, 1, 3, __VA_ARGS__)                 \
   QS_PAIR_CASE(FAM, 6, 1, 4, __VA_ARGS__) QS_PAIR_CASE(FAM, 7, 2, 3, __VA_ARGS__)                 \
   QS_PAIR_CASE(FAM, 8, 2, 4, __VA_ARGS__) QS_PAIR_CASE(FAM, 9, 3, 4, __VA_ARGS__)
+#define QS_SIDE_CASE(FAM, I_, J_, K_, C_)                                      \
+  case FAM * kCodeSlots + I_ * 4 + J_:                                          \
+    if constexpr (A::kSide && R == 4) pair_side_on_bit<A, R, K_, C_, I_, J_>(v, op); \
+    break;
+#define QS_SIDE_CASES(FAM, K_, C_)                                                                    \
+  QS_SIDE_CASE(FAM, 0, 1, K_, C_) QS_SIDE_CASE(FAM, 0, 2, K_, C_) QS_SIDE_CASE(FAM, 0, 3, K_, C_)     \
+  QS_SIDE_CASE(FAM, 1, 0, K_, C_) QS_SIDE_CASE(FAM, 1, 2, K_, C_) QS_SIDE_CASE(FAM, 1, 3, K_, C_)     \
+  QS_SIDE_CASE(FAM, 2, 0, K_, C_) QS_SIDE_CASE(FAM, 2, 1, K_, C_) QS_SIDE_CASE(FAM, 2, 3, K_, C_)     \
+  QS_SIDE_CASE(FAM, 3, 0, K_, C_) QS_SIDE_CASE(FAM, 3, 1, K_, C_) QS_SIDE_CASE(FAM, 3, 2, K_, C_)
   switch (code) {
+    QS_SIDE_CASES(FC_H_SIDE, PK_H, false)
+    QS_SIDE_CASES(FC_SX_SIDE, PK_SX, false)
+    QS_SIDE_CASES(FC_SX_C_SIDE, PK_SX, true)
+    QS_SIDE_CASES(FC_SY_SIDE, PK_SY, false)
+#undef QS_SIDE_CASES
+#undef QS_SIDE_CASE
     QS_BIT_CASES(FC_GEN, (pair_on_bit<A, R, PK_GEN, false, true, I>(v, rmask, op)))
     QS_BIT_CASES(FC_GEN_C, (pair_on_bit<A, R, PK_GEN, true, true, I>(v, rmask, op)))
     QS_BIT_CASES(FC_H, (pair_on_bit<A, R, PK_H, false, false, I>(v, rmask, op)))

@@ -58,14 +58,19 @@ enum FFamily : uint8_t {
   FC_SHEAR = 17, FC_SHEAR2 = 18,  // (x - t y, y + t x); (t x - y, x + t y)
   FC_PHASEU_BIT = 19, FC_PHASEU_ALL = 20,
   FC_DEPH_PAIR = 21,  // FK_DEPH whose two bits are register bits (pair slot)
-  FC_OFFPH = 22       // pair slot
+  FC_OFFPH = 22,      // pair slot
+  // H, sqrt(X), conjugated sqrt(X), sqrt(Y) on register bit i0 with the real
+  // factor c0 on the input whose register bit i1 differs from its bit i0
+  // (FP64 arithmetic, R = 4 only; slot = i0 * 4 + i1)
+  FC_H_SIDE = 23, FC_SX_SIDE = 24, FC_SX_C_SIDE = 25, FC_SY_SIDE = 26
 };
 constexpr int kCodeSlots = 16;
 // FOp::flags
 enum : uint8_t {
   FF_COND = 1,  // lmask or gmask set: a per-thread / per-tile predicate
   FF_FLIP = 2,  // a sign flip precedes the op in its stage: check pending flips
-  FF_TWO = 4    // the op moves amplitudes along register bits i0 and i1
+  FF_TWO = 4,   // the op moves amplitudes along register bits i0 and i1
+  FF_SIDE = 8   // H / sqrt(X) / sqrt(Y) with the side factor on register bit i1 (encoding only)
 };
 
 // One operation as applied in one stage (all masks pre-split by the host).

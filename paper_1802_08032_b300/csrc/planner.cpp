@@ -27,10 +27,13 @@ struct VOp {
   bool conj = false;
   bool spread = false;   // H / sqrt(X) / sqrt(Y) on a bit whose bit-1 amplitudes are all 0
   int b0 = -1, b1 = -1;  // pair target (b0); DEPOL row/column; DEPH the two compared bits
+  int side = -1;         // H / sqrt(X) / sqrt(Y): c0 scales the input whose bit `side` differs from its bit b0
   uint64_t cond = 0;     // bits that must all be 1 (controls; PHASE/SIGN diagonal support)
   double c[8] = {};
 
   uint64_t xmask() const {
+    // (a side factor's bit joins the tile and the register bits with b0)
+    if (side >= 0) return (uint64_t(1) << b0) | (uint64_t(1) << side);
     if (kind <= FK_X || kind == FK_SHEAR) return uint64_t(1) << b0;
     // (a row / column phase pair is diagonal, but it must run on register
     // bits: counting its bits as moved keeps them in the tile)
@@ -514,7 +517,11 @@ void unscale_phases(std::vector<VOp>& ops) {
 // off-diagonal halves: when nothing between them moves amplitudes along t or
 // t + N, the two phases become one op, (1 +- i tan phi) on the off-diagonal
 // entries only, and cos phi joins F[t].
-double defer_offdiag(std::vector<VOp>& ops, int N) {
+// With FP64 arithmetic an uncontrolled H / sqrt(X) / sqrt(Y) on t or t + N
+// (bit-1 factor 1) takes F[t] itself: its inputs off the qubit's diagonal
+// are the bit-1 one where the partner bit is 0 and the bit-0 one where it is
+// 1, and the kernel scales whichever it is inside the update's FMAs.
+double defer_offdiag(std::vector<VOp>& ops, int N, bool side_factors) {
   std::vector<double> F(size_t(N), 1.0);
   double G = 1.0;
   std::vector<VOp> out;
@@ -581,6 +588,18 @@ double defer_offdiag(std::vector<VOp>& ops, int N) {
       continue;
     }
     const uint64_t x = v.xmask();
+    if (side_factors && (v.kind == FK_H || v.kind == FK_SX || v.kind == FK_SY) && v.cond == 0 && !v.spread &&
+        v.c[0] == 1.0) {
+      const int t = v.b0 < N ? v.b0 : v.b0 - N;
+      if (F[size_t(t)] != 1.0) {
+        VOp w = v;
+        w.side = v.b0 < N ? t + N : t;
+        w.c[0] = F[size_t(t)];
+        F[size_t(t)] = 1.0;
+        out.push_back(w);
+        continue;
+      }
+    }
     for (int t = 0; t < N; ++t)
       if (((x >> t) | (x >> (t + N))) & 1) settle(t);
     out.push_back(v);
@@ -654,9 +673,15 @@ int dispatch_code(const FOp& f) {
   const int S = kCodeSlots;
   switch (f.kind) {
     case FK_GEN: return (c ? FC_GEN_C : FC_GEN) * S + f.i0;
-    case FK_H: return FC_H * S + f.i0;         // uncontrolled; conj(H) = H
-    case FK_SX: return (c ? FC_SX_C : FC_SX) * S + f.i0;
-    case FK_SY: return FC_SY * S + f.i0;       // real
+    case FK_H:  // uncontrolled; conj(H) = H
+      if (f.flags & FF_SIDE) return FC_H_SIDE * S + f.i0 * 4 + f.i1;
+      return FC_H * S + f.i0;
+    case FK_SX:
+      if (f.flags & FF_SIDE) return (c ? FC_SX_C_SIDE : FC_SX_SIDE) * S + f.i0 * 4 + f.i1;
+      return (c ? FC_SX_C : FC_SX) * S + f.i0;
+    case FK_SY:  // real
+      if (f.flags & FF_SIDE) return FC_SY_SIDE * S + f.i0 * 4 + f.i1;
+      return FC_SY * S + f.i0;
     case FK_X: return FC_X * S + f.i0;
     case FK_PHASE:
       if (f.rmask == 0) return FC_PHASE_ALL * S;
@@ -758,6 +783,10 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
       if (v.kind <= FK_X || v.kind == FK_SHEAR || v.kind == FK_DEPOL || v.kind == FK_OFFPH)
         f.i0 = uint8_t(idx[lpos[v.b0]]);
       if (v.kind == FK_DEPOL || v.kind == FK_OFFPH) f.i1 = uint8_t(idx[lpos[v.b1]]);
+      if (v.side >= 0) {
+        f.i1 = uint8_t(idx[lpos[v.side]]);
+        f.flags |= FF_SIDE;
+      }
       if (v.kind == FK_SHEAR) f.i1 = v.c[1] != 0.0 ? 1 : 0;
       for (int b = 0; b < 64; ++b) {
         if (!((v.cond >> b) & 1)) continue;
@@ -907,7 +936,8 @@ void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, uint64_t 
   decompose_general(vops, out.arith == Arith::F64 ? 16.0 : 1.0);
   merge_phases(vops, r.nq);
   if (out.arith != Arith::DF) unscale_phases(vops);
-  if (r.density) scale_in *= defer_offdiag(vops, r.n);
+  // (side factors need R = 4 register slots: i0 * 4 + i1)
+  if (r.density) scale_in *= defer_offdiag(vops, r.n, out.arith == Arith::F64 && cfg.R == 4);
   const int64_t cap = env.max_fused_ops > 0 ? std::min<int64_t>(env.max_fused_ops, kMaxPassOps)
                                             : kMaxPassOps;
   const std::vector<Pass> passes =

@@ -80,7 +80,11 @@ static void check_plan(const RegPlan& pl, int nq) {
       for (int o = st.op_begin; o < st.op_end; ++o) {
         const FOp& f = pl.fops[P.op_begin + o];
         const int fam = f.code / kCodeSlots, slot = f.code % kCodeSlots;
-        CHECK(fam <= FC_OFFPH, "op %d: family %d", o, fam);
+        CHECK(fam <= FC_SY_SIDE, "op %d: family %d", o, fam);
+        if (fam >= FC_H_SIDE && fam <= FC_SY_SIDE)
+          CHECK(R == 4 && slot / 4 != slot % 4 && f.i0 == slot / 4 && f.i1 == slot % 4 && f.rmask == 0 &&
+                    f.lmask == 0 && f.gmask == 0 && ((f.flags & FF_SIDE) != 0),
+                "op %d: side-factor pair update", o);
         CHECK(f.rmask < (1u << R), "op %d: rmask", o);
         CHECK((f.lmask & pm) == 0 && (f.lmask >> k) == 0, "op %d: lmask on a register / non-tile bit", o);
         CHECK((f.gmask & tile) == 0 && (nq == 64 || (f.gmask >> nq) == 0), "op %d: gmask inside the tile", o);
@@ -179,7 +183,8 @@ static std::vector<cd> emulate(const RegPlan& pl, int nq) {
               flips ^= f.c.u[15];
               continue;
             }
-            if (fam <= FC_X || fam == FC_DEPOL || fam == FC_SHEAR || fam == FC_SHEAR2) flush_flips();
+            const bool side = fam >= FC_H_SIDE && fam <= FC_SY_SIDE;
+            if (fam <= FC_X || fam == FC_DEPOL || fam == FC_SHEAR || fam == FC_SHEAR2 || side) flush_flips();
             auto c = [&](int e) { return coef(f, e, pl.arith); };
             if (fam <= FC_X) {
               const int I = slot;
@@ -238,6 +243,20 @@ static std::vector<cd> emulate(const RegPlan& pl, int nq) {
               };
               for (int j = 0; j < nj; ++j)
                 if (bv(f.asrc, f.apos, j) != bv(f.bsrc, f.bpos, j)) v[j] *= c(0);
+            } else if (side) {  // unscaled H / sqrt(X) / sqrt(Y) on bit I, c0 on the input whose bit J != bit I
+              const int I = slot / 4, J = slot % 4;
+              cd g01(1, 0), g10(1, 0), g11(-1, 0);  // H
+              if (fam == FC_SX_SIDE) { g01 = cd(0, -1); g10 = cd(0, -1); g11 = 1; }
+              if (fam == FC_SX_C_SIDE) { g01 = cd(0, 1); g10 = cd(0, 1); g11 = 1; }
+              if (fam == FC_SY_SIDE) { g01 = -1; g10 = 1; g11 = 1; }
+              for (int j = 0; j < nj; ++j) {
+                if ((j >> I) & 1) continue;
+                cd x = v[j], y = v[j | (1 << I)];
+                if ((j >> J) & 1) x *= c(0);
+                else y *= c(0);
+                v[j] = x + g01 * y;
+                v[j | (1 << I)] = g10 * x + g11 * y;
+              }
             } else if (fam == FC_OFFPH) {  // (1 + i c0) where only bit a is set, (1 + i c1) only b
               int a, b;
               slot_pair(slot, a, b);
