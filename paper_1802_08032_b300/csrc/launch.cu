@@ -94,23 +94,19 @@ void dm_pair(Env& env, Reg& r, const GateOp& op) {
 }
 
 // Complex64 multi-target pass on the tensor cores (tc_multi.cuh): a
-// persistent grid of 128-thread CTAs, as many per SM as shared memory holds.
-template <int M>
-void multi_pass_tc(Env& env, Reg& r, const MultiParams<float, M>& mp, const Fixed& fx, int64_t nsel) {
-  TcParams<M> p{};
-  for (int k = 0; k < 8; ++k) p.t[k] = mp.t[k];
-  for (int e = 0; e < (1 << (2 * M)); ++e) p.u[e] = make_float2(mp.u[e].x, mp.u[e].y);
+// persistent grid of 128-thread CTAs, as many per SM as can be resident.
+template <int M, bool COAL>
+void launch_tc(Env& env, Reg& r, const TcParams<M>& p, const Fixed& fx, int64_t nsel) {
   constexpr size_t smem = tc_smem_bytes<M>();
   // resident CTAs per SM, the least of what registers (allocated per warp
   // in units of 256), shared memory (228 KB per SM, 1 KB reserved per CTA)
   // and tensor memory (512 columns, 2^(M+1) per CTA) allow: the persistent
-  // grid must be resident all at once
-  // (a function-local static: initialised once, thread-safe; the serving
-  // scheduler thread may get here first)
+  // grid must be resident all at once (a function-local static: initialised
+  // once, thread-safe; the serving scheduler thread may get here first)
   static const int per_sm = [] {
-    QS_CUDA(cudaFuncSetAttribute(k_sv_multi_tc<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    QS_CUDA(cudaFuncSetAttribute(k_sv_multi_tc<M, COAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     cudaFuncAttributes fa{};
-    QS_CUDA(cudaFuncGetAttributes(&fa, k_sv_multi_tc<M>));
+    QS_CUDA(cudaFuncGetAttributes(&fa, k_sv_multi_tc<M, COAL>));
     const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;
     const int by_regs = 65536 / std::max(1, regs_warp * (kTcRows / 32));
     const int by_smem = int((228 * 1024) / (smem + fa.sharedSizeBytes + 1024));
@@ -121,7 +117,36 @@ void multi_pass_tc(Env& env, Reg& r, const MultiParams<float, M>& mp, const Fixe
   // algorithmic flops: 2^m complex multiply-adds (8 flops) per amplitude
   KTimer kt(env, "sv_multi_tc_c64", double(nsel) * 2 * (1 << M) * sizeof(float2),
             double(nsel) * (1 << (2 * M)) * 8);
-  k_sv_multi_tc<M><<<grid, kTcRows, smem, env.stream>>>(static_cast<float2*>(r.d), nsel, fx, p, env.d_status);
+  k_sv_multi_tc<M, COAL><<<grid, kTcRows, smem, env.stream>>>(static_cast<float2*>(r.d), nsel, fx, p,
+                                                               env.d_status);
+}
+
+template <int M>
+void multi_pass_tc(Env& env, Reg& r, const MultiParams<float, M>& mp, const Fixed& fx, int64_t nsel) {
+  TcParams<M> p{};
+  for (int k = 0; k < 8; ++k) p.t[k] = mp.t[k];
+  for (int e = 0; e < (1 << (2 * M)); ++e) p.u[e] = make_float2(mp.u[e].x, mp.u[e].y);
+  int tmin = 64;
+  for (int k = 0; k < M; ++k) tmin = std::min(tmin, int(mp.t[k]));
+  // targets among the five lowest qubits: a thread's block would be runs of
+  // contiguous amplitudes, so load the tile in address order instead; the
+  // enumeration takes the 7 lowest free qubits and the targets, ascending
+  if (tmin < 5 && nsel >= kTcRows) {
+    uint64_t fixed = 0;
+    for (int k = 0; k < fx.n; ++k) fixed |= uint64_t(1) << fx.pos[k];
+    std::vector<std::pair<int, int>> en;  // (qubit, role)
+    for (int q = 0, j = 0; q < r.nq && j < 7; ++q)
+      if (!((fixed >> q) & 1)) en.push_back({q, j++});
+    for (int k = 0; k < M; ++k) en.push_back({int(mp.t[k]), 0x80 | k});
+    std::sort(en.begin(), en.end());
+    for (size_t k = 0; k < en.size(); ++k) {
+      p.pos[k] = uint8_t(en[k].first);
+      p.role[k] = uint8_t(en[k].second);
+    }
+    launch_tc<M, true>(env, r, p, fx, nsel);
+  } else {
+    launch_tc<M, false>(env, r, p, fx, nsel);
+  }
 }
 
 // One multi-target pass over the vector: targets t (shifted by `shift`),

@@ -34,15 +34,22 @@ constexpr int kTcRows = 128;  // GEMM rows (blocks) per tile = threads per CTA
 template <int MT>
 struct TcParams {
   uint8_t t[8];                     // target qubits; bit k of the block index is t[k]
+  // coalesced mode: a tile's 128 x 2^m amplitudes enumerated in address
+  // order, bit k of the enumeration index at qubit pos[k] (the 7 lowest
+  // free qubits and the targets, ascending); role[k] = 0x80 | u for target
+  // t[u], else the block-index bit it carries
+  uint8_t pos[16];
+  uint8_t role[16];
   float2 u[1 << (2 * MT)];          // row-major matrix
 };
 
 // Shared-memory bytes of one CTA: A hi/lo (128 x K), B hi/lo (N x K), the
-// block offsets, the mbarrier and the tensor-memory address slot.
+// block offsets, the coalesced mode's per-index offsets, rows and columns,
+// the mbarrier and the tensor-memory address slot.
 template <int MT>
 __host__ __device__ constexpr size_t tc_smem_bytes() {
   return size_t(2) * kTcRows * (2 << MT) * 4 + size_t(2) * (2 << MT) * (2 << MT) * 4 +
-         sizeof(int64_t) * (1 << MT) + 64;
+         2 * sizeof(int64_t) * (1 << MT) + 2 * (1 << MT) + 64;
 }
 
 namespace tc {
@@ -148,7 +155,13 @@ __device__ __forceinline__ void wait_ld(uint32_t (&r)[N]) {
 // status: bit 0 set when a wait for the tensor cores ran out (1 s of the
 // global timer; the kernel then stops; the amplitudes of unfinished tiles
 // are unchanged or partly written).
-template <int MT>
+// COAL: targets among the lowest qubits, where one thread's block is a few
+// contiguous runs and a warp's per-block loads would not coalesce: the CTA
+// loads the tile in address order into a row-swizzled staging buffer (the
+// A lo area) and each thread then reads its block from it; results go back
+// the same way through the A hi area (free once the MMAs are done).
+// Requires nsel >= 128 (seven free qubits).
+template <int MT, bool COAL>
 __global__ void __launch_bounds__(kTcRows) k_sv_multi_tc(float2* __restrict__ a, int64_t nsel, Fixed fx,
                                                         const __grid_constant__ TcParams<MT> p,
                                                         unsigned* status) {
@@ -161,9 +174,26 @@ __global__ void __launch_bounds__(kTcRows) k_sv_multi_tc(float2* __restrict__ a,
   float* sBh = reinterpret_cast<float*>(smem + 2 * kA);
   float* sBl = reinterpret_cast<float*>(smem + 2 * kA + kB);
   int64_t* toff = reinterpret_cast<int64_t*>(smem + 2 * kA + 2 * kB);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * kA + 2 * kB + sizeof(int64_t) * D2);
+  int64_t* ioff = toff + D2;
+  uint8_t* irow = reinterpret_cast<uint8_t*>(ioff + D2);
+  uint8_t* il = irow + D2;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * kA + 2 * kB + 2 * sizeof(int64_t) * D2 + 2 * D2 + 8 -
+                                              ((2 * D2) % 8));
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
+  // coalesced mode: this thread's part (enumeration bits 0..6) of every
+  // element's address, block row and column
+  int64_t tdep = 0;
+  int trow = 0, tl = 0;  // (distinct names: the tensor-memory row address is tmem_row)
+  if constexpr (COAL) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      if (!((tid >> k) & 1)) continue;
+      tdep += int64_t(1) << p.pos[k];
+      if (p.role[k] & 0x80) tl |= 1 << (p.role[k] & 0x7F);
+      else trow |= 1 << p.role[k];
+    }
+  }
 
   // B = [[Re U^T, Im U^T], [-Im U^T, Re U^T]] stored N x K (row n = output
   // column): row n < D2 gives Re w[n], row D2 + n gives Im w[n].
@@ -180,6 +210,20 @@ __global__ void __launch_bounds__(kTcRows) k_sv_multi_tc(float2* __restrict__ a,
     for (int k = 0; k < MT; ++k)
       if ((tid >> k) & 1) o += int64_t(1) << p.t[k];
     toff[tid] = o;
+    if constexpr (COAL) {  // enumeration bits 7..7+m-1 from the element index i = tid
+      int64_t d = 0;
+      int rw = 0, cl = 0;
+      for (int k = 0; k < MT; ++k) {
+        if (!((tid >> k) & 1)) continue;
+        const uint8_t r = p.role[7 + k];
+        d += int64_t(1) << p.pos[7 + k];
+        if (r & 0x80) cl |= 1 << (r & 0x7F);
+        else rw |= 1 << r;
+      }
+      ioff[tid] = d;
+      irow[tid] = uint8_t(rw);
+      il[tid] = uint8_t(cl);
+    }
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(bar)));
@@ -198,22 +242,44 @@ __global__ void __launch_bounds__(kTcRows) k_sv_multi_tc(float2* __restrict__ a,
   const uint32_t ah = tc::smem_u32(sAh), al = tc::smem_u32(sAl), bh = tc::smem_u32(sBh), bl = tc::smem_u32(sBl);
 
   const int64_t ntiles = (nsel + kTcRows - 1) / kTcRows;
+  // row mode: v = this thread's block; coalesced mode: v = elements
+  // tdep + ioff[i] of the tile (index i), base = the tile's first address
   float2 v[D2];
   int64_t tile = blockIdx.x;
   int64_t j = 0;
   bool live = false;
+  float2* stage = reinterpret_cast<float2*>(sAl);   // coalesced mode: 128 x 2^m, row-swizzled
+  float2* stage2 = reinterpret_cast<float2*>(sAh);  // coalesced mode: results
+  auto sidx = [](int row, int l) { return row * D2 + (l ^ (row & (D2 - 1))); };
   auto gather = [&](int64_t t) {
-    const int64_t b = t * kTcRows + tid;
-    live = b < nsel;
-    j = live ? deposit(b, fx) : 0;
+    if constexpr (COAL) {
+      j = deposit(t * kTcRows, fx);
 #pragma unroll
-    for (int l = 0; l < D2; ++l) v[l] = live ? a[j + toff[l]] : make_float2(0.f, 0.f);
+      for (int i = 0; i < D2; ++i)
+        v[i] = t * kTcRows + (trow | irow[i]) < nsel ? a[j + tdep + ioff[i]] : make_float2(0.f, 0.f);
+    } else {
+      const int64_t b = t * kTcRows + tid;
+      live = b < nsel;
+      j = live ? deposit(b, fx) : 0;
+#pragma unroll
+      for (int l = 0; l < D2; ++l) v[l] = live ? a[j + toff[l]] : make_float2(0.f, 0.f);
+    }
   };
   if (tile < ntiles) gather(tile);
   uint32_t parity = 0;
   bool ok = true;
   for (; tile < ntiles; tile += gridDim.x) {
-    // this thread's row of A = [Re v, Im v], split into TF32 hi and lo
+    if constexpr (COAL) {
+      // elements to the staging buffer, then this thread's block back out
+#pragma unroll
+      for (int i = 0; i < D2; ++i) stage[sidx(trow | irow[i], tl | il[i])] = v[i];
+      __syncthreads();
+#pragma unroll
+      for (int l = 0; l < D2; ++l) v[l] = stage[sidx(tid, l)];
+    }
+    // this thread's row of A = [Re v, Im v], split into TF32 hi and lo (in
+    // coalesced mode lo only after every thread has read the staging area)
+    float4 lo4[KD / 4];
 #pragma unroll
     for (int kc = 0; kc < KD / 4; ++kc) {
       float x[4];
@@ -223,9 +289,14 @@ __global__ void __launch_bounds__(kTcRows) k_sv_multi_tc(float2* __restrict__ a,
         x[i] = k < D2 ? v[k & (D2 - 1)].x : v[k & (D2 - 1)].y;
       }
       const float4 h = make_float4(tc::tf32_hi(x[0]), tc::tf32_hi(x[1]), tc::tf32_hi(x[2]), tc::tf32_hi(x[3]));
-      const float4 lo = make_float4(x[0] - h.x, x[1] - h.y, x[2] - h.z, x[3] - h.w);
+      lo4[kc] = make_float4(x[0] - h.x, x[1] - h.y, x[2] - h.z, x[3] - h.w);
       *reinterpret_cast<float4*>(&sAh[tc::at<kTcRows>(tid, 4 * kc)]) = h;
-      *reinterpret_cast<float4*>(&sAl[tc::at<kTcRows>(tid, 4 * kc)]) = lo;
+      if constexpr (!COAL) *reinterpret_cast<float4*>(&sAl[tc::at<kTcRows>(tid, 4 * kc)]) = lo4[kc];
+    }
+    if constexpr (COAL) {
+      __syncthreads();
+#pragma unroll
+      for (int kc = 0; kc < KD / 4; ++kc) *reinterpret_cast<float4*>(&sAl[tc::at<kTcRows>(tid, 4 * kc)]) = lo4[kc];
     }
     const int64_t jcur = j;
     const bool lcur = live;
@@ -254,15 +325,30 @@ __global__ void __launch_bounds__(kTcRows) k_sv_multi_tc(float2* __restrict__ a,
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
     uint32_t r[ND];
-    const uint32_t trow = tmem + (uint32_t(warp * 32) << 16);
-    tc::ld32<0>(trow, r);
-    if constexpr (ND > 32) tc::ld32<32>(trow + 32u, r);
+    const uint32_t tmem_row = tmem + (uint32_t(warp * 32) << 16);
+    tc::ld32<0>(tmem_row, r);
+    if constexpr (ND > 32) tc::ld32<32>(tmem_row + 32u, r);
     tc::wait_ld(r);
-    if (lcur) {
+    if constexpr (COAL) {
+      // this thread's block to the results area, then elements out in
+      // address order
 #pragma unroll
-      for (int n = 0; n < D2; ++n) a[jcur + toff[n]] = make_float2(__uint_as_float(r[n]), __uint_as_float(r[D2 + n]));
+      for (int n = 0; n < D2; ++n) stage2[sidx(tid, n)] = make_float2(__uint_as_float(r[n]), __uint_as_float(r[D2 + n]));
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < D2; ++i) {
+        const int row = trow | irow[i];
+        if (tile * kTcRows + row < nsel) a[jcur + tdep + ioff[i]] = stage2[sidx(row, tl | il[i])];
+      }
+    } else {
+      if (lcur) {
+#pragma unroll
+        for (int n = 0; n < D2; ++n)
+          a[jcur + toff[n]] = make_float2(__uint_as_float(r[n]), __uint_as_float(r[D2 + n]));
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
   }
   if (!ok) {
     if (tid == 0) atomicOr(status, 1u);

@@ -122,15 +122,18 @@ def test_multi_target_errors(Q, env):
 
 
 @pytest.mark.parametrize("m", [4, 5])
-@pytest.mark.parametrize("ctrls", [(), (2, 17)])
-def test_multi_target_tensor_cores(Q, env, m, ctrls):
+@pytest.mark.parametrize("ctrls", [(), (5, 17)])
+@pytest.mark.parametrize("tset", [(0, 19, 7, 1, 12), (0, 1, 2, 3, 4), (9, 10, 11, 12, 13)])
+def test_multi_target_tensor_cores(Q, env, m, ctrls, tset):
     """Complex64 gates on 4-5 targets run on the tensor cores (three TF32
-    products per FP32 operand pair): many 128-block tiles per CTA, targets on
-    the lowest and highest bits, with and without controls, against the
-    CUDA-core kernel and the oracle."""
+    products per FP32 operand pair): many 128-block tiles per CTA, targets
+    mixed low and high or all among the lowest qubits (tiles loaded in
+    address order through shared memory) or all above them (one block per
+    thread), with and without controls, against the CUDA-core kernel and the
+    oracle."""
     n = 20
     psi = rand_state(n, 40 + m)
-    targets = (0, 19, 7, 1, 12)[:m]
+    targets = tset[:m]
     U = rand_u(1 << m, 50 + m)
     ref = O.State(n, amps=psi)
     ref.multi(targets, U, ctrls)
