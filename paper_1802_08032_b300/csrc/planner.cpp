@@ -548,15 +548,19 @@ double defer_offdiag(std::vector<VOp>& ops, int N, bool side_factors) {
         std::abs(v.c[0]) >= 0.5) {
       const int t = __builtin_ctzll(v.cond);
       const uint64_t col = uint64_t(1) << (t + N), both = v.cond | col;
+      // (the two are normally adjacent; the search is capped so that a long
+      // run of unrelated ops keeps planning linear)
       size_t j = i + 1;
-      for (; j < ops.size(); ++j) {
+      const size_t jmax = std::min(ops.size(), i + 64);
+      for (; j < jmax; ++j) {
         const VOp& w = ops[j];
         if (!used[j] && w.kind == FK_PHASE && w.cond == col) break;
         if (w.xmask() & both) {
-          j = ops.size();
+          j = jmax;
           break;
         }
       }
+      if (j == jmax) j = ops.size();
       if (j < ops.size() && ops[j].c[0] == v.c[0] && ops[j].c[1] == -v.c[1]) {
         used[j] = true;
         F[size_t(t)] *= v.c[0];

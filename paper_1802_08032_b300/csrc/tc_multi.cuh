@@ -177,14 +177,15 @@ __global__ void __launch_bounds__(kTcRows) k_sv_multi_tc(float2* __restrict__ a,
   int64_t* ioff = toff + D2;
   uint8_t* irow = reinterpret_cast<uint8_t*>(ioff + D2);
   uint8_t* il = irow + D2;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * kA + 2 * kB + 2 * sizeof(int64_t) * D2 + 2 * D2 + 8 -
-                                              ((2 * D2) % 8));
+  constexpr uint32_t kBar = (2 * kA + 2 * kB + 18 * D2 + 7) / 8 * 8;  // after toff, ioff, irow, il
+  static_assert(kBar + 16 <= tc_smem_bytes<MT>(), "shared-memory layout");
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kBar);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
   // coalesced mode: this thread's part (enumeration bits 0..6) of every
-  // element's address, block row and column
+  // element's address (tdep), block row (trow) and column (tl)
   int64_t tdep = 0;
-  int trow = 0, tl = 0;  // (distinct names: the tensor-memory row address is tmem_row)
+  int trow = 0, tl = 0;
   if constexpr (COAL) {
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
