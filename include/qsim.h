@@ -102,8 +102,12 @@ int qsDiagBoundedWait(QuESTEnv env, int timeoutUs);
  *                   (consecutive phases merge, gates on qubits still in |0>
  *                   since the register was zeroed become copies or vanish,
  *                   general 2x2 gates run as phase-rotation-phase, scalar
- *                   factors are applied once per flush): results equal
- *                   applying the gates one by one up to rounding.
+ *                   factors are applied once per flush; on a density matrix
+ *                   the channels' off-diagonal factors are deferred per
+ *                   qubit and applied with the next gate on it, and a
+ *                   gate's row and column phases act on the off-diagonal
+ *                   entries only): results equal applying the gates one by
+ *                   one up to rounding.
  *   "tile_qubits"   k of a fused tile, 0 = automatic
  *   "max_fused_ops" cap on operations per fused pass (0 = automatic)
  *   "budget_bytes"  cap on the register memory of this env (0 = none)
