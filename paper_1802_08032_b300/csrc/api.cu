@@ -100,6 +100,7 @@ void ensure_stage(Env& env) {
 void init_zero(Reg& r) {
   r.queue.clear();
   r.pend_scale = 1.0;
+  r.reset_qscale();
   r.zero_bits = r.nq >= 64 ? ~uint64_t(0) : (uint64_t(1) << r.nq) - 1;
   const size_t amp = r.prec == QS_C128 ? sizeof(double2) : sizeof(float2);
   QS_CUDA(cudaMemsetAsync(r.d, 0, size_t(r.dim) * amp, r.env->stream));
@@ -390,6 +391,7 @@ int initPlusState(Qureg q) {
     launch_fill(*r.env, r, v, 0.0);
     r.zero_bits = 0;
     r.pend_scale = 1.0;
+    r.reset_qscale();
   });
 }
 

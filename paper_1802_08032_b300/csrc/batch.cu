@@ -160,6 +160,7 @@ void build(Batch& b) {
                1.0, plans[r]);
     b.regs[r]->zero_bits = 0;  // the register's contents are the batch's from now on
     b.regs[r]->pend_scale = 1.0;
+    b.regs[r]->reset_qscale();
     if (!plans[r].fps.empty()) plans[r].fps[0].init = 1;
     maxp = std::max(maxp, plans[r].fps.size());
   }
@@ -332,6 +333,7 @@ int runBatch(QSBatch h) {
     for (Reg* r : b.regs) {
       r->zero_bits = 0;
       r->pend_scale = 1.0;
+      r->reset_qscale();
     }
     run(b);
   });

@@ -69,6 +69,8 @@ void settle_scale(Reg& r) {
 }
 
 void flush(Reg& r) {
+  // deferred per-qubit factors of unfused phases first (the plans assume none)
+  if (!r.density) settle_qscales(r);
   if (r.queue.empty()) {
     settle_scale(r);
     return;
@@ -81,6 +83,7 @@ void flush(Reg& r) {
       launch_op(env, r, op);
       note_mixing(r, op);
     }
+    if (!r.density) settle_qscales(r);
     settle_scale(r);
     return;
   }
@@ -153,7 +156,7 @@ void flush(Reg& r) {
     }
     if (after[pi] >= 0) launch_op(env, r, q[size_t(after[pi])]);
   }
-  settle_scale(r);
+  settle_scale(r);  // (multi-target gates settle their own targets' factors; nothing else adds one here)
   QS_CUDA(cudaGetLastError());
 }
 

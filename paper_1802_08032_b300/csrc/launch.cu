@@ -42,7 +42,7 @@ std::vector<std::pair<int, int>> ctrl_bits(uint64_t mask, int value) {
 }
 
 template <typename R>
-Mat2<R> to_mat(const GateOp& op) {
+Mat2<R> to_mat(const GateOp& op, double yscale = 1.0) {
   Mat2<R> g{};
   if (op.k == OpK::GEN) {
     for (int e = 0; e < 4; ++e) {
@@ -52,6 +52,15 @@ Mat2<R> to_mat(const GateOp& op) {
   } else if (op.k == OpK::H) {
     g.re[0] = R(1.0 / std::sqrt(2.0));
   }
+  return g;
+}
+
+// The unscaled H / sqrt(X) / sqrt(Y) kernels' argument: the factor on the
+// bit-1 input.
+template <typename R>
+Mat2<R> yscale_mat(double c) {
+  Mat2<R> g{};
+  g.re[0] = R(c);
   return g;
 }
 
@@ -70,7 +79,7 @@ template <typename R>
 constexpr double amp_bytes() { return 2.0 * sizeof(R); }
 
 template <typename R, int K>
-void sv_pair(Env& env, Reg& r, const GateOp& op) {
+void sv_pair(Env& env, Reg& r, const GateOp& op, const Mat2<R>& g) {
   auto bits = ctrl_bits(op.cmask, 1);
   bits.push_back({op.t, 0});
   const Fixed fx = make_fixed(bits);
@@ -78,7 +87,23 @@ void sv_pair(Env& env, Reg& r, const GateOp& op) {
   KTimer kt(env, kname<R>("sv_pair", kPairName[K]).c_str(), double(nsel) * 4 * amp_bytes<R>(),
             double(nsel) * kPairFlops[K]);
   k_sv_pair<R, K, kUnroll><<<grid_for(env, nsel, kUnroll), kThreads, 0, env.stream>>>(
-      static_cast<cvec<R>*>(r.d), nsel, int64_t(1) << op.t, fx, to_mat<R>(op));
+      static_cast<cvec<R>*>(r.d), nsel, int64_t(1) << op.t, fx, g);
+}
+template <typename R, int K>
+void sv_pair(Env& env, Reg& r, const GateOp& op) {
+  sv_pair<R, K>(env, r, op, to_mat<R>(op));
+}
+
+// Applies the real factor Reg::qscale[t] keeps for qubit t's bit-1 half.
+template <typename R>
+void settle_qscale(Env& env, Reg& r, int t) {
+  if (r.qscale[t] == 1.0) return;
+  const Fixed fx = make_fixed({{t, 1}});
+  const int64_t nsel = r.dim >> 1;
+  KTimer kt(env, kname<R>("sv_qscale").c_str(), double(nsel) * 2 * amp_bytes<R>(), double(nsel) * 6);
+  k_sv_diag<R, DK_PHASE, kUnroll><<<grid_for(env, nsel, kUnroll), kThreads, 0, env.stream>>>(
+      static_cast<cvec<R>*>(r.d), nsel, fx, R(r.qscale[t]), R(0));
+  r.qscale[t] = 1.0;
 }
 
 template <typename R, int K>
@@ -88,9 +113,11 @@ void dm_pair(Env& env, Reg& r, const GateOp& op) {
   const int64_t nsel = r.dim >> 2;
   KTimer kt(env, kname<R>("dm_quad", kPairName[K]).c_str(), double(nsel) * 8 * amp_bytes<R>(),
             double(nsel) * 4 * kPairFlops[K]);
+  // (the unscaled kinds take their bit-1 factor, here 1, in g.re[0])
+  const Mat2<R> g = K >= PK_HU ? yscale_mat<R>(1.0) : to_mat<R>(op);
   k_dm_gate<R, K, 2><<<grid_for(env, nsel, 2), kThreads, 0, env.stream>>>(
       static_cast<cvec<R>*>(r.d), nsel, int64_t(1) << op.t, int64_t(1) << (op.t + N), op.cmask,
-      op.cmask << N, fx, to_mat<R>(op));
+      op.cmask << N, fx, g);
 }
 
 // Complex64 multi-target pass on the tensor cores (tc_multi.cuh): a
@@ -180,6 +207,7 @@ void multi_pass(Env& env, Reg& r, const GateOp& op, int shift, uint64_t cmask, b
 
 template <typename R, int M>
 void multi_op(Env& env, Reg& r, const GateOp& op) {
+  for (int k = 0; k < M; ++k) settle_qscale<R>(env, r, op.tg[k]);
   multi_pass<R, M>(env, r, op, 0, op.cmask, false);
   if (r.density) multi_pass<R, M>(env, r, op, r.n, op.cmask << r.n, true);
 }
@@ -198,31 +226,56 @@ void launch_typed(Env& env, Reg& r, const GateOp& op) {
     }
   }
   if (!r.density) {
+    // a pair update on target t needs t's deferred bit-1 factor applied first,
+    // unless it takes it as its bit-1 input factor (uncontrolled H / sqrt(X) /
+    // sqrt(Y) below)
+    const bool absorbs = op.cmask == 0 && (op.k == OpK::H || op.k == OpK::SX || op.k == OpK::SY);
+    if ((op.k == OpK::GEN || op.k == OpK::X || op.k == OpK::H || op.k == OpK::SX || op.k == OpK::SY) &&
+        !absorbs)
+      settle_qscale<R>(env, r, op.t);
     switch (op.k) {
       case OpK::GEN: sv_pair<R, PK_GEN>(env, r, op); return;
-      // uncontrolled H / sqrt(X) / sqrt(Y): unscaled, the register keeps the factor
+      // uncontrolled H / sqrt(X) / sqrt(Y): unscaled, the register keeps the
+      // scalar factor; the bit-1 input takes the qubit's deferred factor
       case OpK::H:
-        if (op.cmask) return sv_pair<R, PK_H>(env, r, op);
-        sv_pair<R, PK_HU>(env, r, op);
-        r.pend_scale *= std::sqrt(0.5);
-        return;
       case OpK::SX:
-      case OpK::SY:
+      case OpK::SY: {
         if (op.cmask) {
-          if (op.k == OpK::SX) sv_pair<R, PK_SX>(env, r, op);
+          if (op.k == OpK::H) sv_pair<R, PK_H>(env, r, op);
+          else if (op.k == OpK::SX) sv_pair<R, PK_SX>(env, r, op);
           else sv_pair<R, PK_SY>(env, r, op);
           return;
         }
-        if (op.k == OpK::SX) sv_pair<R, PK_SXU>(env, r, op);
-        else sv_pair<R, PK_SYU>(env, r, op);
-        r.pend_scale *= std::complex<double>(0.5, 0.5);
+        const Mat2<R> g = yscale_mat<R>(r.qscale[op.t]);
+        r.qscale[op.t] = 1.0;
+        if (op.k == OpK::H) {
+          sv_pair<R, PK_HU>(env, r, op, g);
+          r.pend_scale *= std::sqrt(0.5);
+        } else {
+          if (op.k == OpK::SX) sv_pair<R, PK_SXU>(env, r, op, g);
+          else sv_pair<R, PK_SYU>(env, r, op, g);
+          r.pend_scale *= std::complex<double>(0.5, 0.5);
+        }
         return;
+      }
       case OpK::X: sv_pair<R, PK_X>(env, r, op); return;
       case OpK::PHASE: {
         auto bits = ctrl_bits(op.cmask, 1);
         bits.push_back({op.t, 1});
         const Fixed fx = make_fixed(bits);
         const int64_t nsel = r.dim >> fx.n;
+        // complex128, uncontrolled: (1 + i tan phi) on the bit-1 half (2 FP64
+        // FMAs instead of 4 operations, the FP64 pipe being the bound); cos phi
+        // joins the qubit's deferred factor (a diagonal factor commutes with
+        // every op that does not target the qubit)
+        if (sizeof(R) == 8 && op.cmask == 0 && std::abs(op.m[0]) >= 0.5) {
+          KTimer kt(env, kname<R>("sv_phase").c_str(), double(nsel) * 2 * amp_bytes<R>(), double(nsel) * 4);
+          k_sv_diag<R, DK_PHASEU, kUnroll><<<grid_for(env, nsel, kUnroll), kThreads, 0, env.stream>>>(
+              a, nsel, fx, R(1), R(op.m[1] / op.m[0]));
+          r.qscale[op.t] *= op.m[0];
+          if (std::abs(r.qscale[op.t]) < 1e-100) settle_qscale<R>(env, r, op.t);
+          return;
+        }
         KTimer kt(env, kname<R>("sv_phase").c_str(), double(nsel) * 2 * amp_bytes<R>(), double(nsel) * 6);
         k_sv_diag<R, DK_PHASE, kUnroll><<<grid_for(env, nsel, kUnroll), kThreads, 0, env.stream>>>(
             a, nsel, fx, R(op.m[0]), R(op.m[1]));
@@ -328,6 +381,14 @@ double fetch_result(Env& env) {
 void launch_wait_probe(Env& env, int timeout_us) {
   k_wait_probe<<<1, 32, 0, env.stream>>>(env.d_status, uint64_t(timeout_us) * 1000u);
   check_launch();
+}
+
+void settle_qscales(Reg& r) {
+  for (int t = 0; t < r.nq; ++t) {
+    if (r.qscale[t] == 1.0) continue;
+    if (r.prec == QS_C128) settle_qscale<double>(*r.env, r, t);
+    else settle_qscale<float>(*r.env, r, t);
+  }
 }
 
 void check_status(Env& env) {

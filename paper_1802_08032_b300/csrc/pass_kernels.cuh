@@ -59,16 +59,19 @@ __device__ __forceinline__ void pair_apply(cvec<R>& x, cvec<R>& y, const Mat2<R>
     }
   } else if constexpr (K == PK_X) {
     x.x = yr; x.y = yi; y.x = xr; y.y = xi;
-  } else if constexpr (K == PK_HU) {
-    x.x = xr + yr; x.y = xi + yi; y.x = xr - yr; y.y = xi - yi;
+  } else if constexpr (K == PK_HU) {  // unscaled, bit-1 input times c = g.re[0] (FMA: free)
+    const R c = g.re[0];
+    x.x = fma(c, yr, xr); x.y = fma(c, yi, xi); y.x = fma(-c, yr, xr); y.y = fma(-c, yi, xi);
   } else if constexpr (K == PK_SXU) {
+    const R c = g.re[0];
     if constexpr (!CONJ) {
-      x.x = xr + yi; x.y = xi - yr; y.x = yr + xi; y.y = yi - xr;
+      x.x = fma(c, yi, xr); x.y = fma(-c, yr, xi); y.x = fma(c, yr, xi); y.y = fma(c, yi, -xr);
     } else {
-      x.x = xr - yi; x.y = xi + yr; y.x = yr - xi; y.y = yi + xr;
+      x.x = fma(-c, yi, xr); x.y = fma(c, yr, xi); y.x = fma(c, yr, -xi); y.y = fma(c, yi, xr);
     }
   } else if constexpr (K == PK_SYU) {
-    x.x = xr - yr; x.y = xi - yi; y.x = xr + yr; y.y = xi + yi;
+    const R c = g.re[0];
+    x.x = fma(-c, yr, xr); x.y = fma(-c, yi, xi); y.x = fma(c, yr, xr); y.y = fma(c, yi, xi);
   }
 }
 
@@ -101,7 +104,9 @@ __global__ void __launch_bounds__(256) k_sv_pair(cvec<R>* __restrict__ a, int64_
 // Diagonal state-vector gates on the selected amplitudes (all fixed bits 1):
 // PHASE multiplies by (c, s) = exp(i phi); SIGN negates (CZ, multi-controlled
 // phase flip).
-enum DiagKind { DK_PHASE = 0, DK_SIGN = 1 };
+// DK_PHASE: times (c + i s); DK_SIGN: negate; DK_PHASEU: times (1 + i s), a
+// phase whose real factor c the caller keeps (2 FMAs instead of 4 operations).
+enum DiagKind { DK_PHASE = 0, DK_SIGN = 1, DK_PHASEU = 2 };
 
 template <typename R, int K, int UNROLL>
 __global__ void __launch_bounds__(256) k_sv_diag(cvec<R>* __restrict__ a, int64_t nsel,
@@ -123,6 +128,9 @@ __global__ void __launch_bounds__(256) k_sv_diag(cvec<R>* __restrict__ a, int64_
       cvec<R> v = x[u];
       if constexpr (K == DK_SIGN) {
         v.x = neg_bits(v.x); v.y = neg_bits(v.y);
+      } else if constexpr (K == DK_PHASEU) {
+        v.x = fma(-s, x[u].y, x[u].x);
+        v.y = fma(s, x[u].x, x[u].y);
       } else {
         v.x = c * x[u].x - s * x[u].y;
         v.y = s * x[u].x + c * x[u].y;

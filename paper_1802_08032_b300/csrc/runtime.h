@@ -96,6 +96,18 @@ struct Reg {
   // final scale, or by one scaling pass), before anything reads the
   // amplitudes.
   std::complex<double> pend_scale{1.0, 0.0};
+  // Per qubit t: a real factor every amplitude with bit t set is to be
+  // multiplied by (state vectors, unfused complex128 phases: the cos phi of a
+  // phase applied as 1 + i tan phi).  Taken by the next uncontrolled H /
+  // sqrt(X) / sqrt(Y) on t as its bit-1 input factor, applied before any
+  // other update targeting t and at every flush.
+  double qscale[64];
+  Reg() {
+    for (double& q : qscale) q = 1.0;
+  }
+  void reset_qscale() {
+    for (double& q : qscale) q = 1.0;
+  }
 };
 
 struct Env {
@@ -204,6 +216,8 @@ void launch_collapse(Env& env, Reg& r, int q, int o, double scale);
 void launch_fill(Env& env, Reg& r, double re, double im);
 // Multiplies every amplitude by f (settles Reg::pend_scale).
 void launch_scale(Env& env, Reg& r, std::complex<double> f);
+// Applies every pending Reg::qscale factor (launch.cu).
+void settle_qscales(Reg& r);
 void launch_convert(Env& env, const void* src, void* dst, int64_t count, bool to_double);
 
 }  // namespace qs

@@ -222,3 +222,52 @@ def test_unfused_pending_scale(Q, env, prec, density):
         assert np.max(np.abs(got - ref.a)) <= AMP_TOL[prec] * (10 if prec == 64 else 1)
     finally:
         Q.setEnvOption(env, "fusion", 1)
+
+
+def test_unfused_phase_factor_per_qubit(Q, env):
+    """Unfused complex128 phases run as 1 + i tan(phi) and leave cos(phi) as a
+    factor on the qubit's bit-1 half: the next uncontrolled H / sqrt(X) /
+    sqrt(Y) on the qubit takes it, a general, controlled or multi-target
+    update on the qubit and every read apply it first, gates that only use
+    the qubit as a control or are diagonal leave it pending."""
+    n = 9
+    rng = np.random.default_rng(12)
+    m = rng.normal(size=(8, 8)) + 1j * rng.normal(size=(8, 8))
+    U3, _ = np.linalg.qr(m)
+    a = complex(0.6, 0.0)
+    b = complex(0.0, 0.8)
+    seq = [
+        [C.Op("T", (1,)), C.Op("T", (1,)), C.Op("T", (1,)), C.Op("SX", (1,))],        # taken by sqrt(X)
+        [C.Op("T", (2,)), C.Op("CNOT", (5,), (2,)), C.Op("CZ", (2, 3)), C.Op("H", (2,))],  # control, diagonal, then H
+        [C.Op("T", (3,)), C.Op("COMPACT", (3,), (), (a.real, a.imag, b.real, b.imag))],  # general: applied first
+        [C.Op("T", (4,)), C.Op("CUNITARY", (4,), (0,), (0.6, 0, 0, -0.8, 0, -0.8, 0.6, 0))],  # controlled update on it
+        [C.Op("T", (6,)), C.Op("PHASE", (6,), (), (0.7,)), C.Op("SY", (6,))],
+        [C.Op("T", (7,))] * 5 + [C.Op("T", (0,))],                                      # left pending until the read
+    ]
+    Q.setEnvOption(env, "fusion", 0)
+    try:
+        q = Q.createQureg(n, 128, env)
+        ref = O.State(n)
+        for ops in seq:
+            Q.applyCircuit(q, ops)
+            ref.run(ops)
+        Q.multiControlledMultiQubitUnitary(q, (), (7, 8, 0), U3)  # targets with pending factors
+        ref.multi((7, 8, 0), U3)
+        Q.applyCircuit(q, [C.Op("T", (5,)), C.Op("T", (8,))])
+        ref.run([C.Op("T", (5,)), C.Op("T", (8,))])
+        assert abs(Q.calcProbOfOutcome(q, 5, 1) - ref.prob_outcome(5, 1)) <= 1e-13
+        Q.applyCircuit(q, [C.Op("T", (5,))] * 400 + [C.Op("H", (5,))])  # the factor is bounded
+        ref.run([C.Op("T", (5,))] * 400 + [C.Op("H", (5,))])
+        p = Q.collapseToOutcome(q, 8, 0)
+        assert abs(p - ref.collapse(8, 0)) <= 1e-13
+        Q.applyCircuit(q, [C.Op("T", (2,))])
+        ref.run([C.Op("T", (2,))])
+        Q.setEnvOption(env, "fusion", 1)  # queued from here: the flush plans with the factors applied
+        more = [C.Op("SX", (2,)), C.Op("T", (6,)), C.Op("CZ", (2, 6)), C.Op("H", (6,))]
+        Q.applyCircuit(q, more)
+        ref.run(more)
+        got = Q.copyStateToHost(q)
+        Q.destroyQureg(q)
+        assert np.max(np.abs(got - ref.a)) <= AMP_TOL[128]
+    finally:
+        Q.setEnvOption(env, "fusion", 1)
