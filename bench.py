@@ -484,9 +484,11 @@ def variants(Q, env, torch, stream, only=(), qubits=30, serve=(60, 0.0)):
                      ("single_gate_sweep_33q", lambda: sweep(33, [0, 1, 2, 4, 8, 16, 24, 32])),
                      ("dm14_c128", dm14),
                      ("batch4096_c64", lambda: batch_variant(Q, env, torch, stream)),
+                     ("multi_target_passes", lambda: multi_sweep(Q, env, torch, stream, qubits)),
+                     # last: after a serving sweep's many large allocations the process's later
+                     # registers measured up to 15 % slower in latency-bound passes
                      ("serving", lambda: serve_sweep(Q, env, [10, 30, 100, 300, 1000, 2000], serve[0],
-                                                     baseline_rates=(10, 100), seconds=serve[1])),
-                     ("multi_target_passes", lambda: multi_sweep(Q, env, torch, stream, qubits))):
+                                                     baseline_rates=(10, 100), seconds=serve[1]))):
         if only and name not in only:
             continue
         try:

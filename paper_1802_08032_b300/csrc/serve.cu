@@ -72,6 +72,10 @@ struct Server {
   bool stop = false;
   std::thread th;
   int64_t next_ticket = 1;
+  // the device's default pool: its release threshold before the server
+  // raised it (restored, and the cached blocks released, when it stops)
+  cudaMemPool_t pool = nullptr;
+  uint64_t pool_threshold = 0;
 };
 
 std::mutex g_smu;
@@ -240,7 +244,9 @@ int serveCreate(QuESTEnv env, int slots, int64_t budgetBytes, int fusion, QSServ
       QS_CUDA(cudaSetDevice(S->device));
       cudaMemPool_t pool;
       QS_CUDA(cudaDeviceGetDefaultMemPool(&pool, S->device));
-      uint64_t keep = ~uint64_t(0);  // keep freed blocks cached in the pool
+      QS_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &S->pool_threshold));
+      S->pool = pool;
+      uint64_t keep = ~uint64_t(0);  // keep freed blocks cached in the pool while serving
       QS_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
       for (int i = 0; i < slots; ++i) {
         auto* s = new Slot();
@@ -348,6 +354,13 @@ int serveDestroy(QSServer h) {
       delete s;
     }
     for (auto& kv : S->tickets) delete kv.second;
+    // give the pool's cached blocks back and restore its threshold: the
+    // server's setting must not outlive it
+    if (S->pool) {
+      cudaDeviceSynchronize();
+      cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &S->pool_threshold);
+      cudaMemPoolTrimTo(S->pool, 0);
+    }
     {
       std::lock_guard<std::mutex> lk(g_smu);
       g_servers.erase(S->id);
