@@ -65,8 +65,9 @@ Mat2<R> yscale_mat(double c) {
 }
 
 // Floating-point operations of one pair update (FMA counted as 2).
-constexpr double kPairFlops[8] = {28, 8, 12, 12, 0, 4, 4, 4};  // GEN, H, SX, SY, X, unscaled H, SX, SY
-const char* kPairName[8] = {"gen", "h", "sx", "sy", "x", "h", "sx", "sy"};
+// GEN, H, SX, SY, X, unscaled H, SX, SY, phase-shear (two forms)
+constexpr double kPairFlops[10] = {28, 8, 12, 12, 0, 4, 4, 4, 12, 12};
+const char* kPairName[10] = {"gen", "h", "sx", "sy", "x", "h", "sx", "sy", "gen", "gen"};
 
 template <typename R>
 std::string kname(const char* base, const char* kind = nullptr) {
@@ -94,16 +95,64 @@ void sv_pair(Env& env, Reg& r, const GateOp& op) {
   sv_pair<R, K>(env, r, op, to_mat<R>(op));
 }
 
-// Applies the real factor Reg::qscale[t] keeps for qubit t's bit-1 half.
+// Applies the factor Reg::qscale[t] keeps for qubit t's bit-1 half.
 template <typename R>
 void settle_qscale(Env& env, Reg& r, int t) {
-  if (r.qscale[t] == 1.0) return;
+  if (r.qscale[t] == std::complex<double>(1.0, 0.0)) return;
   const Fixed fx = make_fixed({{t, 1}});
   const int64_t nsel = r.dim >> 1;
   KTimer kt(env, kname<R>("sv_qscale").c_str(), double(nsel) * 2 * amp_bytes<R>(), double(nsel) * 6);
   k_sv_diag<R, DK_PHASE, kUnroll><<<grid_for(env, nsel, kUnroll), kThreads, 0, env.stream>>>(
-      static_cast<cvec<R>*>(r.d), nsel, fx, R(r.qscale[t]), R(0));
+      static_cast<cvec<R>*>(r.d), nsel, fx, R(r.qscale[t].real()), R(r.qscale[t].imag()));
   r.qscale[t] = 1.0;
+}
+
+// Complex128 uncontrolled general update U on target t whose pending factor
+// is w = s e^{i theta}: U' = U diag(1, e^{i theta}) (unitary) acts on
+// (x, s y).  U' = g diag(1, p1) R diag(1, p2) (the fused planner's
+// factorisation: g = a/|a|, p1 = (c/|c|) conj(g), p2 = -(b/|b|) conj(g),
+// R = |a| [[1, -t], [t, 1]], t = |b|/|a|); p2 = cos (1 + i tan) runs as
+// 1 + i tan, or, when |sin| > |cos|, p2 = sin (cot + i) as cot + i; the
+// real factor f (cos or sin) times s is carried through the shear
+// (x - t c y~, y~ + (t/c) x, c = f s), so the pass is 6 FMAs a pair; g |a|
+// joins the register's scalar and c p1 becomes t's pending factor.  Returns
+// false (nothing launched) when U' does not take that form: |a|, |b| or
+// |c| near 0, t > 16, or factors that do not reproduce U' to 1e-14.
+template <typename R>
+bool phase_shear(Env& env, Reg& r, const GateOp& op, const std::complex<double> (&U)[4], double s) {
+  using C = std::complex<double>;
+  const double na = std::abs(U[0]), nb = std::abs(U[1]), nc = std::abs(U[2]);
+  if (!(na > 1e-150 && nb > 1e-150 && nc > 1e-150) || nb > 16.0 * na) return false;
+  const C g = U[0] / na, p1 = (U[2] / nc) * std::conj(g), p2 = -(U[1] / nb) * std::conj(g);
+  const C r01 = -g * nb * p2, r10 = g * p1 * nb, r11 = g * p1 * na * p2;
+  if (std::abs(r01 - U[1]) > 1e-14 || std::abs(r10 - U[2]) > 1e-14 || std::abs(r11 - U[3]) > 1e-14) return false;
+  const bool by_cos = std::abs(p2.real()) >= std::abs(p2.imag());
+  const double f = by_cos ? p2.real() : p2.imag();
+  const double t = nb / na, c = f * s;
+  Mat2<R> m{};
+  m.re[0] = R(by_cos ? p2.imag() / p2.real() : p2.real() / p2.imag());
+  m.re[1] = R(t * c);
+  m.re[2] = R(t / c);
+  if (by_cos) sv_pair<R, PK_PSP>(env, r, op, m);
+  else sv_pair<R, PK_PSP2>(env, r, op, m);
+  r.pend_scale *= g * na;
+  r.qscale[op.t] = c * p1;
+  return true;
+}
+
+// The 2x2 matrix of an uncontrolled H / sqrt(X) / sqrt(Y) / general op.
+inline void op_matrix(const GateOp& op, std::complex<double> (&U)[4]) {
+  using C = std::complex<double>;
+  const double s = std::sqrt(0.5);
+  if (op.k == OpK::GEN) {
+    for (int e = 0; e < 4; ++e) U[e] = C(op.m[2 * e], op.m[2 * e + 1]);
+  } else if (op.k == OpK::H) {
+    U[0] = s; U[1] = s; U[2] = s; U[3] = -s;
+  } else if (op.k == OpK::SX) {
+    U[0] = C(0.5, 0.5); U[1] = C(0.5, -0.5); U[2] = C(0.5, -0.5); U[3] = C(0.5, 0.5);
+  } else {  // sqrt(Y)
+    U[0] = C(0.5, 0.5); U[1] = C(-0.5, -0.5); U[2] = C(0.5, 0.5); U[3] = C(0.5, 0.5);
+  }
 }
 
 template <typename R, int K>
@@ -229,10 +278,35 @@ void launch_typed(Env& env, Reg& r, const GateOp& op) {
     // a pair update on target t needs t's deferred bit-1 factor applied first,
     // unless it takes it as its bit-1 input factor (uncontrolled H / sqrt(X) /
     // sqrt(Y) below)
-    const bool absorbs = op.cmask == 0 && (op.k == OpK::H || op.k == OpK::SX || op.k == OpK::SY);
-    if ((op.k == OpK::GEN || op.k == OpK::X || op.k == OpK::H || op.k == OpK::SX || op.k == OpK::SY) &&
-        !absorbs)
-      settle_qscale<R>(env, r, op.t);
+    const bool real_pending = r.qscale[op.t].imag() == 0.0;
+    const bool hsxsy = op.k == OpK::H || op.k == OpK::SX || op.k == OpK::SY;
+    // complex128, uncontrolled general update (or H / sqrt(X) / sqrt(Y) meeting a
+    // complex pending factor): phase-shear with the pending factor folded in
+    const bool ps_path = sizeof(R) == 8 && op.cmask == 0 && (op.k == OpK::GEN || (hsxsy && !real_pending));
+    // uncontrolled H / sqrt(X) / sqrt(Y) with a real pending factor: its bit-1 input factor
+    const bool yscale_path = op.cmask == 0 && hsxsy && real_pending;
+    if ((op.k == OpK::GEN || op.k == OpK::X || hsxsy) && !ps_path && !yscale_path) settle_qscale<R>(env, r, op.t);
+    if (ps_path) {
+      std::complex<double> U[4];
+      op_matrix(op, U);
+      const std::complex<double> w = r.qscale[op.t];
+      const double sw = std::abs(w);
+      std::complex<double> Up[4] = {U[0], U[1] * (w / sw), U[2], U[3] * (w / sw)};
+      if (!phase_shear<R>(env, r, op, Up, sw)) {
+        U[1] *= w;
+        U[3] *= w;
+        GateOp g = op;  // the plain general update of U diag(1, w)
+        g.k = OpK::GEN;
+        for (int e = 0; e < 4; ++e) {
+          g.m[2 * e] = U[e].real();
+          g.m[2 * e + 1] = U[e].imag();
+        }
+        sv_pair<R, PK_GEN>(env, r, g);
+        r.qscale[op.t] = 1.0;
+      }
+      if (std::abs(r.qscale[op.t]) < 1e-100) settle_qscale<R>(env, r, op.t);
+      return;
+    }
     switch (op.k) {
       case OpK::GEN: sv_pair<R, PK_GEN>(env, r, op); return;
       // uncontrolled H / sqrt(X) / sqrt(Y): unscaled, the register keeps the
@@ -246,7 +320,7 @@ void launch_typed(Env& env, Reg& r, const GateOp& op) {
           else sv_pair<R, PK_SY>(env, r, op);
           return;
         }
-        const Mat2<R> g = yscale_mat<R>(r.qscale[op.t]);
+        const Mat2<R> g = yscale_mat<R>(r.qscale[op.t].real());
         r.qscale[op.t] = 1.0;
         if (op.k == OpK::H) {
           sv_pair<R, PK_HU>(env, r, op, g);

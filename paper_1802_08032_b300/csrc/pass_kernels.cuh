@@ -18,7 +18,8 @@ namespace qs {
 // (1+i)/2, and (1-i)/2 for conjugated column updates), which the register
 // then carries (Reg::pend_scale): [[1, 1], [1, -1]], [[1, -i], [-i, 1]]
 // (conj: [[1, i], [i, 1]]), [[1, -1], [1, 1]].
-enum PairKind { PK_GEN = 0, PK_H = 1, PK_SX = 2, PK_SY = 3, PK_X = 4, PK_HU = 5, PK_SXU = 6, PK_SYU = 7 };
+enum PairKind { PK_GEN = 0, PK_H = 1, PK_SX = 2, PK_SY = 3, PK_X = 4, PK_HU = 5, PK_SXU = 6, PK_SYU = 7,
+                PK_PSP = 8, PK_PSP2 = 9 };
 
 // (x, y) <- G (x, y); CONJ applies conj(G) instead (Eq. 2 column update).
 template <typename R, int K, bool CONJ>
@@ -72,6 +73,15 @@ __device__ __forceinline__ void pair_apply(cvec<R>& x, cvec<R>& y, const Mat2<R>
   } else if constexpr (K == PK_SYU) {
     const R c = g.re[0];
     x.x = fma(-c, yr, xr); x.y = fma(-c, yi, xi); y.x = fma(c, yr, xr); y.y = fma(c, yi, xi);
+  } else if constexpr (K == PK_PSP || K == PK_PSP2) {
+    // a general update as phase-shear with deferred factors (launch.cu):
+    // y~ = (1 + i t2) y (PSP) or (t2 + i) y (PSP2), then (x - a1 y~, y~ + a2 x);
+    // g.re = {t2, a1, a2}
+    const R t2 = g.re[0], a1 = g.re[1], a2 = g.re[2];
+    const R zr = K == PK_PSP ? fma(-t2, yi, yr) : fma(t2, yr, -yi);
+    const R zi = K == PK_PSP ? fma(t2, yr, yi) : fma(t2, yi, yr);
+    x.x = fma(-a1, zr, xr); x.y = fma(-a1, zi, xi);
+    y.x = fma(a2, xr, zr); y.y = fma(a2, xi, zi);
   }
 }
 

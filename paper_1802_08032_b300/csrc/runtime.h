@@ -96,17 +96,19 @@ struct Reg {
   // final scale, or by one scaling pass), before anything reads the
   // amplitudes.
   std::complex<double> pend_scale{1.0, 0.0};
-  // Per qubit t: a real factor every amplitude with bit t set is to be
-  // multiplied by (state vectors, unfused complex128 phases: the cos phi of a
-  // phase applied as 1 + i tan phi).  Taken by the next uncontrolled H /
-  // sqrt(X) / sqrt(Y) on t as its bit-1 input factor, applied before any
-  // other update targeting t and at every flush.
-  double qscale[64];
+  // Per qubit t: a factor every amplitude with bit t set is to be multiplied
+  // by (state vectors, unfused complex128 gates: the cos phi of a phase
+  // applied as 1 + i tan phi, the output phase of a general update run as
+  // phase-shear).  A real one is taken by the next uncontrolled H / sqrt(X)
+  // / sqrt(Y) on t as its bit-1 input factor, any by the next uncontrolled
+  // general update on t (folded into its matrix); applied before any other
+  // update targeting t and at every flush.
+  std::complex<double> qscale[64];
   Reg() {
-    for (double& q : qscale) q = 1.0;
+    for (std::complex<double>& q : qscale) q = 1.0;
   }
   void reset_qscale() {
-    for (double& q : qscale) q = 1.0;
+    for (std::complex<double>& q : qscale) q = 1.0;
   }
 };
 

@@ -271,3 +271,65 @@ def test_unfused_phase_factor_per_qubit(Q, env):
         assert np.max(np.abs(got - ref.a)) <= AMP_TOL[128]
     finally:
         Q.setEnvOption(env, "fusion", 1)
+
+
+def test_unfused_general_updates_phase_shear(Q, env):
+    """Unfused complex128 uncontrolled general updates run as phase-shear:
+    the qubit's pending factor folds into the matrix, the output phase stays
+    pending.  Chains of general updates, H / sqrt(X) / sqrt(Y) meeting a
+    complex pending factor, X, controlled and multi-target updates that apply
+    it first, uses as a control, reads, and a switch back to fused flushes."""
+    n = 8
+    rng = C.SplitMix64(77)
+
+    def haar():
+        a = C.haar_alpha_beta(rng)
+        return C.Op("COMPACT", (rng.below(n),), (), tuple(a))
+
+    ops = []
+    for _ in range(120):
+        k = rng.below(8)
+        q = rng.below(n)
+        if k <= 2:
+            ops.append(haar())
+        elif k == 3:
+            ops.append(C.Op(("H", "SX", "SY")[rng.below(3)], (q,)))
+        elif k == 4:
+            ops.append(C.Op("T", (q,)))
+        elif k == 5:
+            c = (q + 1 + rng.below(n - 1)) % n
+            ops.append(C.Op("CNOT", (q,), (c,)))
+        elif k == 6:
+            ops.append(C.Op("X", (q,)))
+        else:
+            a, b = C.distinct_qubits(rng, n, 2)
+            ops.append(C.Op("CZ", (a, b)))
+    same = C.Op("COMPACT", (3,), (), tuple(C.haar_alpha_beta(rng)))
+    chain = [same] * 300 + [C.Op("SX", (3,)), C.Op("H", (3,))]
+    g = np.random.default_rng(4)
+    U2 = np.linalg.qr(g.normal(size=(4, 4)) + 1j * g.normal(size=(4, 4)))[0]
+    Q.setEnvOption(env, "fusion", 0)
+    try:
+        q = Q.createQureg(n, 128, env)
+        ref = O.State(n)
+        Q.applyCircuit(q, ops[:60])
+        ref.run(ops[:60])
+        assert abs(Q.calcTotalProb(q) - 1.0) <= 1e-13
+        Q.applyCircuit(q, ops[60:] + chain)
+        ref.run(ops[60:] + chain)
+        Q.applyCircuit(q, [same, C.Op("T", (3,)), same])
+        ref.run([same, C.Op("T", (3,)), same])
+        Q.multiControlledMultiQubitUnitary(q, (5,), (3, 0), U2)
+        ref.multi((3, 0), U2, (5,))
+        assert abs(Q.calcProbOfOutcome(q, 3, 1) - ref.prob_outcome(3, 1)) <= 1e-13
+        Q.applyCircuit(q, [same, C.Op("CNOT", (1,), (3,))])
+        ref.run([same, C.Op("CNOT", (1,), (3,))])
+        Q.setEnvOption(env, "fusion", 1)
+        tail = [C.Op("SY", (3,)), C.Op("T", (1,)), C.Op("CZ", (1, 3))]
+        Q.applyCircuit(q, tail)
+        ref.run(tail)
+        got = Q.copyStateToHost(q)
+        Q.destroyQureg(q)
+        assert np.max(np.abs(got - ref.a)) <= AMP_TOL[128]
+    finally:
+        Q.setEnvOption(env, "fusion", 1)
