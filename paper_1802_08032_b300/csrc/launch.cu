@@ -474,9 +474,12 @@ void check_status(Env& env) {
 }
 
 // Unscaled passes grow the stored amplitudes by 1/|pend_scale|: settle the
-// factor before that growth nears the storage format's range.
+// factor before that growth nears the storage format's range.  Unitary
+// updates keep the stored vector's norm at 1/|pend_scale|, so no stored
+// amplitude exceeds it: 1e18 for complex64 (float range 3.4e38), 1e100 for
+// complex128; precision is relative and does not depend on the scale.
 static void bound_pending(Env& env, Reg& r) {
-  if (std::abs(r.pend_scale) >= (r.prec == QS_C64 ? 1e-9 : 1e-100)) return;
+  if (std::abs(r.pend_scale) >= (r.prec == QS_C64 ? 1e-18 : 1e-100)) return;
   launch_scale(env, r, r.pend_scale);
   r.pend_scale = 1.0;
 }
