@@ -154,9 +154,14 @@ void flush(Reg& r) {
       else
         launch_pass<PlainArith<float>, 5>(env, r, fp, d_ops, d_st, pl.flops[i], pl.alu[i], "fused_c64");
     }
-    if (after[pi] >= 0) launch_op(env, r, q[size_t(after[pi])]);
+    if (after[pi] >= 0) {
+      launch_op(env, r, q[size_t(after[pi])]);
+      // (a one-target gate runs as a pair update and may leave a per-qubit
+      // factor; the next plan and every read assume none)
+      if (!r.density) settle_qscales(r);
+    }
   }
-  settle_scale(r);  // (multi-target gates settle their own targets' factors; nothing else adds one here)
+  settle_scale(r);
   QS_CUDA(cudaGetLastError());
 }
 

@@ -265,6 +265,17 @@ template <typename R>
 void launch_typed(Env& env, Reg& r, const GateOp& op) {
   cvec<R>* a = static_cast<cvec<R>*>(r.d);
   if (op.k == OpK::MULTI) {
+    if (op.nt == 1) {  // a 2x2 update: the single-target path (pair kernels, phase-shear)
+      GateOp g = op;
+      g.k = OpK::GEN;
+      g.t = op.tg[0];
+      g.nt = 0;
+      const std::vector<double>& u = *op.big;
+      for (int e = 0; e < 8; ++e) g.m[e] = u[size_t(e)];
+      g.big.reset();
+      launch_typed<R>(env, r, g);
+      return;
+    }
     switch (op.nt) {
       case 1: multi_op<R, 1>(env, r, op); return;
       case 2: multi_op<R, 2>(env, r, op); return;
