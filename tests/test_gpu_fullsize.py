@@ -123,3 +123,26 @@ def test_30_qubit_depth40_workload(Q, env, prec, arith):
     tol = (PROB_TOL if arith == 0 else DF_PROB_TOL) if prec == 128 else 1e-5
     assert abs(tot - g["total_prob"]) <= tol
     assert np.max(np.abs(np.array(probs) - g["prob_outcome_1"])) <= tol
+
+
+@pytest.mark.parametrize("prec", [128, 64])
+def test_30_qubit_depth40_workload_unfused(Q, env, prec):
+    """The same 30-qubit circuit one kernel per gate: unscaled H / sqrt(X) /
+    sqrt(Y) with the register's scalar, (1 + i tan) phases and phase-shear
+    general updates with per-qubit factors, at full size."""
+    g = golden("sv30_depth40.json")
+    ops = C.workload_30q(30)
+    Q.setEnvOption(env, "fusion", 0)
+    try:
+        q = Q.createQureg(30, prec, env)
+        Q.applyCircuit(q, ops)
+        tot = Q.calcTotalProb(q)
+        probs = [Q.calcProbOfOutcome(q, k, 1) for k in range(0, 30, 3)]
+        got = sample(Q, q, g["indices"])
+        Q.destroyQureg(q)
+    finally:
+        Q.setEnvOption(env, "fusion", 1)
+    assert np.max(np.abs(got - as_complex(g["amps"]))) <= AMP_TOL[prec]
+    tol = PROB_TOL if prec == 128 else 1e-5
+    assert abs(tot - g["total_prob"]) <= tol
+    assert np.max(np.abs(np.array(probs) - np.array(g["prob_outcome_1"])[0:30:3])) <= tol
