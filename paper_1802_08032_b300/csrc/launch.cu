@@ -79,6 +79,25 @@ std::string kname(const char* base, const char* kind = nullptr) {
 template <typename R>
 constexpr double amp_bytes() { return 2.0 * sizeof(R); }
 
+// A diagonal update on the nsel amplitudes selected by fx.  Where the
+// selected amplitudes come in runs (every fixed bit at position >= 1), a
+// thread takes two consecutive ones with one index computation: for
+// complex64 one 16-byte access (lanes stay contiguous; measured: a 3-control
+// phase flip 4755 -> 5236 GB/s), for complex128 only for phases (two 16-byte
+// accesses per thread half-fill each sector per instruction, which cost
+// sign flips more than the saved index work: CZ 5756 -> 5545 GB/s).
+template <typename R, int K>
+void launch_diag(Env& env, cvec<R>* a, int64_t nsel, const Fixed& fx, R c, R s) {
+  const int low = fx.n > 0 ? fx.pos[0] : 64;  // the lowest fixed bit (positions sorted)
+  const bool aligned = (reinterpret_cast<uintptr_t>(a) & 15u) == 0;
+  const int V = aligned && low >= 1 && (sizeof(R) == 4 || K != DK_SIGN) ? 2 : 1;
+  if (V == 2)
+    k_sv_diag_v<R, K, 2, kUnroll><<<grid_for(env, nsel / 2, kUnroll), kThreads, 0, env.stream>>>(a, nsel / 2, fx,
+                                                                                                   c, s);
+  else
+    k_sv_diag<R, K, kUnroll><<<grid_for(env, nsel, kUnroll), kThreads, 0, env.stream>>>(a, nsel, fx, c, s);
+}
+
 template <typename R, int K>
 void sv_pair(Env& env, Reg& r, const GateOp& op, const Mat2<R>& g) {
   auto bits = ctrl_bits(op.cmask, 1);
@@ -102,8 +121,8 @@ void settle_qscale(Env& env, Reg& r, int t) {
   const Fixed fx = make_fixed({{t, 1}});
   const int64_t nsel = r.dim >> 1;
   KTimer kt(env, kname<R>("sv_qscale").c_str(), double(nsel) * 2 * amp_bytes<R>(), double(nsel) * 6);
-  k_sv_diag<R, DK_PHASE, kUnroll><<<grid_for(env, nsel, kUnroll), kThreads, 0, env.stream>>>(
-      static_cast<cvec<R>*>(r.d), nsel, fx, R(r.qscale[t].real()), R(r.qscale[t].imag()));
+  launch_diag<R, DK_PHASE>(env, static_cast<cvec<R>*>(r.d), nsel, fx, R(r.qscale[t].real()),
+                           R(r.qscale[t].imag()));
   r.qscale[t] = 1.0;
 }
 
@@ -355,23 +374,20 @@ void launch_typed(Env& env, Reg& r, const GateOp& op) {
         // every op that does not target the qubit)
         if (sizeof(R) == 8 && op.cmask == 0 && std::abs(op.m[0]) >= 0.5) {
           KTimer kt(env, kname<R>("sv_phase").c_str(), double(nsel) * 2 * amp_bytes<R>(), double(nsel) * 4);
-          k_sv_diag<R, DK_PHASEU, kUnroll><<<grid_for(env, nsel, kUnroll), kThreads, 0, env.stream>>>(
-              a, nsel, fx, R(1), R(op.m[1] / op.m[0]));
+          launch_diag<R, DK_PHASEU>(env, a, nsel, fx, R(1), R(op.m[1] / op.m[0]));
           r.qscale[op.t] *= op.m[0];
           if (std::abs(r.qscale[op.t]) < 1e-100) settle_qscale<R>(env, r, op.t);
           return;
         }
         KTimer kt(env, kname<R>("sv_phase").c_str(), double(nsel) * 2 * amp_bytes<R>(), double(nsel) * 6);
-        k_sv_diag<R, DK_PHASE, kUnroll><<<grid_for(env, nsel, kUnroll), kThreads, 0, env.stream>>>(
-            a, nsel, fx, R(op.m[0]), R(op.m[1]));
+        launch_diag<R, DK_PHASE>(env, a, nsel, fx, R(op.m[0]), R(op.m[1]));
         return;
       }
       case OpK::SIGN: {
         const Fixed fx = make_fixed(ctrl_bits(op.cmask, 1));
         const int64_t nsel = r.dim >> fx.n;
         KTimer kt(env, kname<R>("sv_sign").c_str(), double(nsel) * 2 * amp_bytes<R>(), 0);
-        k_sv_diag<R, DK_SIGN, kUnroll><<<grid_for(env, nsel, kUnroll), kThreads, 0, env.stream>>>(
-            a, nsel, fx, R(0), R(0));
+        launch_diag<R, DK_SIGN>(env, a, nsel, fx, R(0), R(0));
         return;
       }
       default: fail(QS_E_NOT_DENSITY, "channel on a state vector");

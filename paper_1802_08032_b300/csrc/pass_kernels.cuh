@@ -150,6 +150,64 @@ __global__ void __launch_bounds__(256) k_sv_diag(cvec<R>* __restrict__ a, int64_
   }
 }
 
+// The same diagonal update on groups of V consecutive selected amplitudes
+// (valid when every fixed bit is at position >= log2 V, so that deposit(g V)
+// starts a run of V selected amplitudes): one index computation per V
+// amplitudes and 16-byte vector accesses for complex64.
+template <typename R, int K, int V, int UNROLL>
+__global__ void __launch_bounds__(256) k_sv_diag_v(cvec<R>* __restrict__ a, int64_t ngroups,
+                                                   Fixed fx, R c, R s) {
+  const int64_t nthr = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; base < ngroups;
+       base += nthr * UNROLL) {
+    int64_t j[UNROLL];
+    cvec<R> x[UNROLL][V];
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) {
+      const int64_t g = base + u * nthr;
+      j[u] = g < ngroups ? deposit(g * V, fx) : -1;
+      if (j[u] < 0) continue;
+      if constexpr (sizeof(R) == 4 && V >= 2) {
+#pragma unroll
+        for (int w = 0; w < V; w += 2) {
+          const float4 q = *reinterpret_cast<const float4*>(a + j[u] + w);
+          x[u][w] = cvec<R>{q.x, q.y};
+          x[u][w + 1] = cvec<R>{q.z, q.w};
+        }
+      } else {
+#pragma unroll
+        for (int w = 0; w < V; ++w) x[u][w] = a[j[u] + w];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) {
+      if (j[u] < 0) continue;
+      cvec<R> v[V];
+#pragma unroll
+      for (int w = 0; w < V; ++w) {
+        const cvec<R> y = x[u][w];
+        if constexpr (K == DK_SIGN) {
+          v[w].x = neg_bits(y.x); v[w].y = neg_bits(y.y);
+        } else if constexpr (K == DK_PHASEU) {
+          v[w].x = fma(-s, y.y, y.x);
+          v[w].y = fma(s, y.x, y.y);
+        } else {
+          v[w].x = c * y.x - s * y.y;
+          v[w].y = s * y.x + c * y.y;
+        }
+      }
+      if constexpr (sizeof(R) == 4 && V >= 2) {
+#pragma unroll
+        for (int w = 0; w < V; w += 2)
+          *reinterpret_cast<float4*>(a + j[u] + w) = make_float4(v[w].x, v[w].y, v[w + 1].x, v[w + 1].y);
+      } else {
+#pragma unroll
+        for (int w = 0; w < V; ++w) a[j[u] + w] = v[w];
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------- density matrix
 // Quad pass of Eq. 2: for a quad base j (bits t and t+N zero) the four
 // entries v[r][c] = a[j + r 2^t + c 2^(t+N)] (r = row bit, c = column bit).
