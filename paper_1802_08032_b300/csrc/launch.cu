@@ -308,7 +308,8 @@ void launch_typed(Env& env, Reg& r, const GateOp& op) {
     // a pair update on target t needs t's deferred bit-1 factor applied first,
     // unless it takes it as its bit-1 input factor (uncontrolled H / sqrt(X) /
     // sqrt(Y) below)
-    const bool real_pending = r.qscale[op.t].imag() == 0.0;
+    // (sign flips have no target: op.t = -1)
+    const bool real_pending = op.t < 0 || r.qscale[op.t].imag() == 0.0;
     const bool hsxsy = op.k == OpK::H || op.k == OpK::SX || op.k == OpK::SY;
     // complex128, uncontrolled general update (or H / sqrt(X) / sqrt(Y) meeting a
     // complex pending factor): phase-shear with the pending factor folded in
