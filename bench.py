@@ -481,7 +481,7 @@ def variants(Q, env, torch, stream, only=(), qubits=30, serve=(60, 0.0)):
     for name, fn in (("sv30_c64", sv(64, 0)), ("sv30_c128_df", sv(128, 1)),
                      ("sv33_c128", sv(128, 0, 33, 1)), ("sv33_c64", sv(64, 0, 33)),
                      ("single_gate_sweep", lambda: sweep(30, range(30))),
-                     ("single_gate_sweep_33q", lambda: sweep(33, [0, 1, 2, 4, 8, 16, 24, 32])),
+                     ("single_gate_sweep_33q", lambda: sweep(33, range(33))),
                      ("dm14_c128", dm14),
                      ("batch4096_c64", lambda: batch_variant(Q, env, torch, stream)),
                      ("multi_target_passes", lambda: multi_sweep(Q, env, torch, stream, qubits)),
