@@ -567,8 +567,9 @@ def batch_variant(Q, env, torch, stream, count=4096, depth=30):
 def multi_sweep(Q, env, torch, stream, n=30):
     """One dense 2^m x 2^m gate (targets 7..7+m-1) as a single pass over an
     n-qubit register: algorithmic GB/s (read + write of every amplitude).
-    Complex64 with m = 4, 5 runs on the tensor cores; those are also timed
-    on the CUDA cores and with the targets on the lowest bits."""
+    Complex64 with m = 4, 5 picks the tensor cores or the CUDA cores by the
+    targets' positions; both are also timed forced, with these targets and
+    with the targets on the lowest bits."""
     import numpy as np
     out = {}
     Q.setEnvOption(env, "fusion", 0)
@@ -585,13 +586,17 @@ def multi_sweep(Q, env, torch, stream, n=30):
                     out[f"c{prec}_m{m}"] = {"ms": ms, "GBps": 2 * (1 << n) * S / ms / 1e6}
                     if prec == 64 and m >= 4:
                         # the same pass on the CUDA cores, and with the targets on the lowest bits
-                        Q.setEnvOption(env, "multi_tc", 0)
+                        low = tuple(range(m))
                         try:
-                            ms = timed(torch, stream, lambda: Q.multiQubitUnitary(q, tg, U), 2)
+                            for mode, name in ((0, "cuda_cores"), (2, "tensor_cores")):
+                                Q.setEnvOption(env, "multi_tc", mode)
+                                ms = timed(torch, stream, lambda: Q.multiQubitUnitary(q, tg, U), 2)
+                                out[f"c64_m{m}_{name}"] = {"ms": ms, "GBps": 2 * (1 << n) * S / ms / 1e6}
+                                ms = timed(torch, stream, lambda: Q.multiQubitUnitary(q, low, U), 2)
+                                out[f"c64_m{m}_low_targets_{name}"] = {"ms": ms,
+                                                                       "GBps": 2 * (1 << n) * S / ms / 1e6}
                         finally:
                             Q.setEnvOption(env, "multi_tc", 1)
-                        out[f"c64_m{m}_cuda_cores"] = {"ms": ms, "GBps": 2 * (1 << n) * S / ms / 1e6}
-                        low = tuple(range(m))
                         ms = timed(torch, stream, lambda: Q.multiQubitUnitary(q, low, U), 2)
                         out[f"c64_m{m}_low_targets"] = {"ms": ms, "GBps": 2 * (1 << n) * S / ms / 1e6}
             finally:

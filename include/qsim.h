@@ -118,11 +118,14 @@ int qsDiagBoundedWait(QuESTEnv env, int timeoutUs);
  *                   reductions and measurement always use FP64.
  *   "profile"       1 = time every kernel launch with CUDA events (see
  *                   getKernelStats), 0 = off (default)
- *   "multi_tc"      1 = complex64 multi-target gates on 4-5 targets run on
- *                   the tensor cores (default; FP32 operands as TF32 hi + lo
+ *   "multi_tc"      where complex64 multi-target gates on 4-5 targets run:
+ *                   2 = on the tensor cores (FP32 operands as TF32 hi + lo
  *                   pairs, three products accumulated in FP32: a few units of
  *                   1e-7 of the largest amplitude per gate), 0 = FP32 on the
- *                   CUDA cores
+ *                   CUDA cores, 1 = by shape (default): 5 targets, or 4 with
+ *                   one below qubit 5, on the tensor cores; 4 targets all at
+ *                   qubit 5 or above on the CUDA cores (paired FP32 FMAs,
+ *                   faster there)
  * Unknown keys give QS_E_ARG. */
 int setEnvOption(QuESTEnv env, const char *key, int64_t value);
 /* getEnvOption: reads an option back, or a counter of the env:

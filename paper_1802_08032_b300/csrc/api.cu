@@ -306,7 +306,7 @@ int setEnvOption(QuESTEnv e, const char* key, int64_t value) {
       if (value != 0 && value != 1) fail(QS_E_ARG, "profile must be 0 or 1");
       env.profile = value;
     } else if (k == "multi_tc") {
-      if (value != 0 && value != 1) fail(QS_E_ARG, "multi_tc must be 0 or 1");
+      if (value < 0 || value > 2) fail(QS_E_ARG, "multi_tc must be 0, 1 or 2");
       env.multi_tc = value;
     } else {
       fail(QS_E_ARG, "unknown option " + k);

@@ -262,13 +262,28 @@ void multi_pass(Env& env, Reg& r, const GateOp& op, int shift, uint64_t cmask, b
   const Fixed fx = make_fixed(bits);
   const int64_t nsel = r.dim >> fx.n;
   if constexpr (std::is_same<R, float>::value && M >= 4) {
-    if (env.multi_tc) {
+    // by shape: the paired-FMA CUDA-core pass is faster at 4 targets when a
+    // thread's block has no run of contiguous amplitudes (all targets at
+    // qubit 5 or above); 5 targets, or runs, go to the tensor cores
+    int tmin = 64;
+    for (int k = 0; k < M; ++k) tmin = std::min(tmin, int(p.t[k]));
+    if (env.multi_tc == 2 || (env.multi_tc == 1 && (M == 5 || (tmin < 5 && nsel >= kTcRows)))) {
       multi_pass_tc<M>(env, r, p, fx, nsel);
       return;
     }
   }
   KTimer kt(env, kname<R>("sv_multi").c_str(), double(nsel) * 2 * (1 << M) * amp_bytes<R>(),
             double(nsel) * (1 << (2 * M)) * 8);
+  // complex64 on up to 4 targets with paired FP32 FMAs; at 5 targets the
+  // duplicated matrix (16 KB of parameters) is fetched into registers entry by
+  // entry, slower than the scalar kernel whose FMAs read it as operands
+  if constexpr (std::is_same<R, float>::value && M <= 4) {
+    MultiParamsF2<M> q{};
+    for (int k = 0; k < 8; ++k) q.t[k] = p.t[k];
+    for (int e = 0; e < (1 << (2 * M)); ++e) q.u[e] = make_float4(p.u[e].x, p.u[e].x, p.u[e].y, p.u[e].y);
+    k_sv_multi_f2<M><<<grid_for(env, nsel, 1), kThreads, 0, env.stream>>>(static_cast<float2*>(r.d), nsel, fx, q);
+    return;
+  }
   k_sv_multi<R, M><<<grid_for(env, nsel, 1), kThreads, 0, env.stream>>>(static_cast<cvec<R>*>(r.d), nsel,
                                                                         fx, p);
 }

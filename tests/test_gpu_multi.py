@@ -125,12 +125,12 @@ def test_multi_target_errors(Q, env):
 @pytest.mark.parametrize("ctrls", [(), (5, 17)])
 @pytest.mark.parametrize("tset", [(0, 19, 7, 1, 12), (0, 1, 2, 3, 4), (9, 10, 11, 12, 13)])
 def test_multi_target_tensor_cores(Q, env, m, ctrls, tset):
-    """Complex64 gates on 4-5 targets run on the tensor cores (three TF32
-    products per FP32 operand pair): many 128-block tiles per CTA, targets
-    mixed low and high or all among the lowest qubits (tiles loaded in
-    address order through shared memory) or all above them (one block per
-    thread), with and without controls, against the CUDA-core kernel and the
-    oracle."""
+    """Complex64 gates on 4-5 targets on the tensor cores (three TF32
+    products per FP32 operand pair; forced, and chosen by shape): many
+    128-block tiles per CTA, targets mixed low and high or all among the
+    lowest qubits (tiles loaded in address order through shared memory) or
+    all above them (one block per thread), with and without controls, against
+    the CUDA-core kernel and the oracle."""
     n = 20
     psi = rand_state(n, 40 + m)
     targets = tset[:m]
@@ -138,7 +138,7 @@ def test_multi_target_tensor_cores(Q, env, m, ctrls, tset):
     ref = O.State(n, amps=psi)
     ref.multi(targets, U, ctrls)
     out = {}
-    for tc in (1, 0):
+    for tc in (2, 1, 0):
         Q.setEnvOption(env, "multi_tc", tc)
         q = Q.createQureg(n, 64, env)
         Q.setAmps(q, psi)
@@ -152,8 +152,9 @@ def test_multi_target_tensor_cores(Q, env, m, ctrls, tset):
     # relative error each (the TF32 split): bound 5e-6 of the largest
     # amplitude, well inside the complex64 bar of 1e-5 absolute
     scale = np.max(np.abs(ref.a))
-    assert np.max(np.abs(out[1] - ref.a)) <= 5e-6 * scale
-    assert np.max(np.abs(out[1] - out[0])) <= 5e-6 * scale
+    for tc in (2, 1):
+        assert np.max(np.abs(out[tc] - ref.a)) <= 5e-6 * scale
+        assert np.max(np.abs(out[tc] - out[0])) <= 5e-6 * scale
 
 
 def test_multi_target_tensor_cores_density_matrix(Q, env):
