@@ -357,23 +357,29 @@ def multiControlledUnitary(q, controls: Sequence[int], t, u):
 def controlledPhaseFlip(q, a, b): _check(LIB.controlledPhaseFlip(q, a, b))
 
 
-def _cmatrix(u):
+def _cmatrix(u, m: int):
+    """A 2^m x 2^m matrix as contiguous complex128 (the layout of Complex,
+    re then im) and a pointer into it, without a copy when u already is one;
+    the caller keeps the array alive for the call."""
     import numpy as np
-    u = np.ascontiguousarray(np.asarray(u, dtype=np.complex128).reshape(-1))
-    arr = (Complex * u.size)(*[Complex(z.real, z.imag) for z in u])
-    return arr
+    a = np.ascontiguousarray(np.asarray(u, dtype=np.complex128).reshape(-1))
+    if m < 0 or a.size != 1 << (2 * m):
+        raise ValueError(f"matrix has {a.size} entries; {m} targets need {1 << (2 * max(m, 0))}")
+    return a, a.ctypes.data_as(ctypes.POINTER(Complex))
 
 
 def multiQubitUnitary(q, targets: Sequence[int], u):
     """u: 2^m x 2^m unitary (bit k of its index is targets[k])."""
     t, n = _ints(targets)
-    _check(LIB.multiQubitUnitary(q, t, n, _cmatrix(u)))
+    a, p = _cmatrix(u, n)
+    _check(LIB.multiQubitUnitary(q, t, n, p))
 
 
 def multiControlledMultiQubitUnitary(q, controls: Sequence[int], targets: Sequence[int], u):
     c, nc = _ints(controls)
     t, nt = _ints(targets)
-    _check(LIB.multiControlledMultiQubitUnitary(q, c, nc, t, nt, _cmatrix(u)))
+    a, p = _cmatrix(u, nt)
+    _check(LIB.multiControlledMultiQubitUnitary(q, c, nc, t, nt, p))
 
 
 def twoQubitUnitary(q, t1, t2, u):

@@ -69,3 +69,20 @@ def test_status_codes_match_header():
         assert re.search(rf"{name}\s*=\s*{code}\b", src), name
     for name, code in qsim.OP_CODES.items():
         assert re.search(rf"QS_OP_\w+\s*=\s*{code}\b", src)
+
+
+def test_matrix_marshalling_is_the_complex_layout():
+    """Multi-target matrices go to the library as a pointer into contiguous
+    complex128 (re, im per entry: the layout of Complex), row-major, sized
+    4^m for m targets; other sizes are refused before the call."""
+    import numpy as np
+    from paper_1802_08032_b300 import qsim as Q
+    u = (np.arange(16) + 1j * (100 + np.arange(16))).reshape(4, 4)
+    a, p = Q._cmatrix(u, 2)
+    for e in range(16):
+        assert (p[e].re, p[e].im) == (u.reshape(-1)[e].real, u.reshape(-1)[e].imag)
+    a, p = Q._cmatrix(u.T, 2)  # a transposed view is copied into row-major order
+    assert (p[1].re, p[1].im) == (u[1, 0].real, u[1, 0].imag)
+    for m in (1, 3):
+        with pytest.raises(ValueError):
+            Q._cmatrix(u, m)
