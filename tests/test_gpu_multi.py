@@ -193,3 +193,71 @@ def test_bounded_wait_reports_timeout(Q, env):
     with pytest.raises(Q.QSimError) as e:
         Q.qsDiagBoundedWait(env, 0)
     assert e.value.name == "QS_E_ARG"
+
+
+_FACTOR_A = {}
+
+
+def remap(ops, phys):
+    """A gate list on qubits 0..len(phys)-1 moved onto the physical qubits phys."""
+    return [C.Op(o.kind, tuple(phys[t] for t in o.targets), tuple(phys[c] for c in o.controls), o.params)
+            for o in ops]
+
+
+def gather_bits(idx, phys):
+    """The bits of idx at the positions phys, packed in order (bit k = idx bit phys[k])."""
+    out = np.zeros(len(idx), dtype=np.int64)
+    for k, p in enumerate(phys):
+        out |= ((idx >> p) & 1) << k
+    return out
+
+
+@pytest.mark.parametrize("prec", [128, 64])
+@pytest.mark.parametrize("m,targets,ctrls", [
+    (5, (0, 19, 7, 1, 12), (5, 17)),   # targets mixed low and high, two controls
+    (5, (0, 1, 2, 3, 4), (9,)),         # all among the lowest qubits
+    (5, (25, 26, 27, 28, 29), ()),      # all at the top
+    (4, (25, 26, 27, 28), (3,)),        # complex64: the paired-FMA CUDA-core pass
+    (4, (1, 0, 3, 2), ()),              # complex64: the tensor cores in address order
+])
+def test_multi_target_30_qubits(Q, env, prec, m, targets, ctrls):
+    """A dense gate on a 30-qubit register (16 GiB complex128, 8 GiB
+    complex64: 2^25 or more blocks, 64-bit indices) prepared as a product
+    state: a seeded circuit on the 23-25 qubits A outside the gate, and one
+    on the qubits B of the gate's targets and controls, then the gate.  The
+    result is still a product, so each sampled amplitude is the oracle's
+    factor-A amplitude times its factor-B amplitude (each factor run on its
+    own, 2^25 amplitudes at most)."""
+    n = 30
+    B = sorted(set(targets) | set(ctrls))
+    A = [q for q in range(n) if q not in B]
+    loc = {p: k for k, p in enumerate(B)}
+    U = rand_u(1 << m, 300 + m)
+    ops_a = C.random_circuit(len(A), 4, 3000 + len(A), extras=True)
+    ops_b = C.random_circuit(len(B), 6, 3100 + len(B), extras=True)
+    key = tuple(A)
+    if key not in _FACTOR_A:
+        _FACTOR_A[key] = O.run_circuit(len(A), ops_a).a.copy()
+    fa = _FACTOR_A[key]
+    sb = O.run_circuit(len(B), ops_b)
+    sb.multi(tuple(loc[t] for t in targets), U, tuple(loc[c] for c in ctrls))
+    q = Q.createQureg(n, prec, env)
+    try:
+        Q.applyCircuit(q, remap(ops_a, A) + remap(ops_b, B))
+        Q.multiControlledMultiQubitUnitary(q, ctrls, targets, U)
+        idx = np.array(C.sample_indices(n, 2048, 77 + m), dtype=np.int64)
+        got = np.array([Q.copyStateToHost(q, int(i), 1)[0] for i in idx])
+        tot = Q.calcTotalProb(q)
+    finally:
+        Q.destroyQureg(q)
+    want = fa[gather_bits(idx, A)] * sb.a[gather_bits(idx, B)]
+    scale = np.max(np.abs(want))
+    if prec == 128:
+        assert np.max(np.abs(got - want)) <= AMP_TOL[128]
+        assert np.max(np.abs(got - want)) <= 1e-10 * scale
+        assert abs(tot - 1.0) <= 1e-12
+    else:
+        # the complex64 bar of 1e-5, taken relative to the largest sampled
+        # amplitude (30-qubit amplitudes are ~1e-4, far below the absolute bar)
+        assert np.max(np.abs(got - want)) <= 1e-5 * scale
+        assert abs(tot - 1.0) <= 1e-5
