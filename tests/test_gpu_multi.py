@@ -261,3 +261,49 @@ def test_multi_target_30_qubits(Q, env, prec, m, targets, ctrls):
         # amplitude (30-qubit amplitudes are ~1e-4, far below the absolute bar)
         assert np.max(np.abs(got - want)) <= 1e-5 * scale
         assert abs(tot - 1.0) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", [128, 64])
+@pytest.mark.parametrize("m,targets,ctrls", [
+    (5, (0, 9, 3, 1, 12), (5,)),   # targets mixed low and high in the row bits, one control
+    (4, (10, 11, 12, 13), ()),     # the top row bits (their columns are the top vector bits)
+])
+def test_multi_target_density_matrix_14_qubits(Q, env, prec, m, targets, ctrls):
+    """A dense gate on a noisy 14-qubit density matrix (2^28 amplitudes: 4 GiB
+    complex128) prepared as a product rho_A (x) rho_B: a seeded noisy circuit
+    on the qubits A outside the gate, one on the gate's qubits B, then the
+    gate (U on the row bits, conj(U) on the column bits, Eq. 2).  Element
+    (row, column) is rho_A(row_A, column_A) rho_B(row_B, column_B), each factor
+    run by the oracle on its own."""
+    N = 14
+    B = sorted(set(targets) | set(ctrls))
+    A = [q for q in range(N) if q not in B]
+    loc = {p: k for k, p in enumerate(B)}
+    U = rand_u(1 << m, 400 + m)
+    ops_a = C.with_noise(C.random_circuit(len(A), 4, 1400 + len(A), extras=True), 0.01, 0.005)
+    ops_b = C.with_noise(C.random_circuit(len(B), 6, 1500 + len(B), extras=True), 0.01, 0.005)
+    sa = O.run_circuit(len(A), ops_a, density=True)
+    sb = O.run_circuit(len(B), ops_b, density=True)
+    sb.multi(tuple(loc[t] for t in targets), U, tuple(loc[c] for c in ctrls))
+    d = Q.createDensityQureg(N, prec, env)
+    try:
+        Q.applyCircuit(d, remap(ops_a, A) + remap(ops_b, B))
+        Q.multiControlledMultiQubitUnitary(d, ctrls, targets, U)
+        idx = np.array(C.sample_indices(2 * N, 2048, 91 + m), dtype=np.int64)
+        got = np.array([Q.copyStateToHost(d, int(i), 1)[0] for i in idx])
+        tr = Q.calcTotalProb(d)
+    finally:
+        Q.destroyQureg(d)
+    # vector index = row + 2^N column: factor X's element sits at its row bits
+    # (positions X) and its column bits (positions X + N)
+    ia = gather_bits(idx, A + [q + N for q in A])
+    ib = gather_bits(idx, B + [q + N for q in B])
+    want = sa.a[ia] * sb.a[ib]
+    scale = np.max(np.abs(want))
+    if prec == 128:
+        assert np.max(np.abs(got - want)) <= AMP_TOL[128]
+        assert np.max(np.abs(got - want)) <= 1e-10 * scale
+        assert abs(tr - 1.0) <= 1e-12
+    else:
+        assert np.max(np.abs(got - want)) <= 1e-5 * scale
+        assert abs(tr - 1.0) <= 1e-5
