@@ -584,6 +584,14 @@ def multi_sweep(Q, env, torch, stream, n=30):
                     tg = tuple(range(7, 7 + m))
                     ms = timed(torch, stream, lambda: Q.multiQubitUnitary(q, tg, U), 2)
                     out[f"c{prec}_m{m}"] = {"ms": ms, "GBps": 2 * (1 << n) * S / ms / 1e6}
+                    if prec == 128 and m >= 2:
+                        # complex128 in double-float arithmetic (FP32 pipes)
+                        Q.setEnvOption(env, "arith", 1)
+                        try:
+                            ms = timed(torch, stream, lambda: Q.multiQubitUnitary(q, tg, U), 2)
+                        finally:
+                            Q.setEnvOption(env, "arith", 0)
+                        out[f"c128_df_m{m}"] = {"ms": ms, "GBps": 2 * (1 << n) * S / ms / 1e6}
                     if prec == 64 and m >= 4:
                         # the same pass on the CUDA cores, and with the targets on the lowest bits
                         low = tuple(range(m))

@@ -111,11 +111,13 @@ int qsDiagBoundedWait(QuESTEnv env, int timeoutUs);
  *   "tile_qubits"   k of a fused tile, 0 = automatic
  *   "max_fused_ops" cap on operations per fused pass (0 = automatic)
  *   "budget_bytes"  cap on the register memory of this env (0 = none)
- *   "arith"         complex128 arithmetic of fused passes: 0 = IEEE FP64
- *                   (default), 1 = double-float (each real a float pair
- *                   hi + lo on the FP32 pipes; a few units of 2^-48 of error
- *                   per update instead of 2^-53).  Single-gate passes,
- *                   reductions and measurement always use FP64.
+ *   "arith"         complex128 arithmetic of fused passes and multi-target
+ *                   passes: 0 = IEEE FP64 (default), 1 = double-float (each
+ *                   real a float pair hi + lo on the FP32 pipes; a few units
+ *                   of 2^-48 of error per update instead of 2^-53; a
+ *                   multi-target pass on m targets up to 2^m units of 2^-48
+ *                   of the norm).  Single-gate passes, reductions and
+ *                   measurement always use FP64.
  *   "profile"       1 = time every kernel launch with CUDA events (see
  *                   getKernelStats), 0 = off (default)
  *   "multi_tc"      where complex64 multi-target gates on 4-5 targets run:

@@ -277,6 +277,20 @@ void multi_pass(Env& env, Reg& r, const GateOp& op, int shift, uint64_t cmask, b
   // complex64 on up to 4 targets with paired FP32 FMAs; at 5 targets the
   // duplicated matrix (16 KB of parameters) is fetched into registers entry by
   // entry, slower than the scalar kernel whose FMAs read it as operands
+  if constexpr (std::is_same<R, double>::value) {
+    if (env.arith == 1) {  // double-float on the FP32 pipes
+      MultiParamsDF<M> q{};
+      for (int k = 0; k < 8; ++k) q.t[k] = p.t[k];
+      for (int e = 0; e < (1 << (2 * M)); ++e) {
+        const double re = u[2 * e], im = conj ? -u[2 * e + 1] : u[2 * e + 1];
+        const float rh = float(re), ih = float(im);
+        q.u[e] = make_float4(rh, float(re - double(rh)), ih, float(im - double(ih)));
+      }
+      k_sv_multi_df<M><<<grid_for(env, nsel, 1), kThreads, 0, env.stream>>>(static_cast<double2*>(r.d), nsel,
+                                                                             fx, q);
+      return;
+    }
+  }
   if constexpr (std::is_same<R, float>::value && M <= 4) {
     MultiParamsF2<M> q{};
     for (int k = 0; k < 8; ++k) q.t[k] = p.t[k];

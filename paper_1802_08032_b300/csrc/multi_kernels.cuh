@@ -3,6 +3,7 @@
 // notes the density-matrix rule holds for multi-qubit gates, Sec. II.B.1).
 #pragma once
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace qs {
 
@@ -94,6 +95,74 @@ __global__ void __launch_bounds__(256) k_sv_multi_f2(float2* __restrict__ a, int
         Q = __ffma2_rn(make_float2(g.z, g.w), v[c], Q);
       }
       a[j + off(r)] = make_float2(P.x - Q.y, P.y + Q.x);
+    }
+  }
+}
+
+// Complex128 matrix entries as double-float pairs: u[e] = (Re hi, Re lo,
+// Im hi, Im lo) of entry e.
+template <int M>
+struct MultiParamsDF {
+  uint8_t t[8];
+  float4 u[1 << (2 * M)];
+};
+
+// k_sv_multi for complex128 amplitudes in double-float arithmetic on the
+// FP32 pipes (env option "arith" 1).  Each amplitude is split into a
+// packed pair hi = (Re hi, Im hi), lo = (Re lo, Im lo); per row, P = sum_c
+// Re(g_c) v_c and Q = sum_c Im(g_c) v_c as in k_sv_multi_f2, each product
+// formed exactly (p = g_hi v_hi, its rounding error by an FMA, plus the two
+// cross terms g_hi v_lo + g_lo v_hi), the high parts summed by error-free
+// two-sums and every low part accumulated in float; then (P.x - Q.y,
+// P.y + Q.x) by one double-float addition.  Error: about 2^M units of 2^-48
+// of the block's norm per gate (the low-part sum), far below 1e-12.
+template <int M>
+__global__ void __launch_bounds__(256) k_sv_multi_df(double2* __restrict__ a, int64_t nsel, Fixed fx,
+                                                     const __grid_constant__ MultiParamsDF<M> p) {
+  constexpr int B = 1 << M;
+  const int64_t nthr = int64_t(gridDim.x) * blockDim.x;
+  auto off = [&](int l) {
+    int64_t o = 0;
+#pragma unroll
+    for (int k = 0; k < M; ++k)
+      if ((l >> k) & 1) o += int64_t(1) << p.t[k];
+    return o;
+  };
+  // accumulates g v (g a real double-float, broadcast to both halves) into
+  // the high sum S and the low sum E
+  auto mac = [](float2& S, float2& E, const dfc2& v, float gh, float gl, bool first) {
+    const float2 G = f2(gh, gh);
+    const float2 p = mul2(v.hi, G);
+    const float2 np = mul2(v.hi, f2(-gh, -gh));  // -p exactly
+    float2 e = fma2(v.hi, G, np);
+    e = fma2(v.hi, f2(gl, gl), e);
+    e = fma2(v.lo, G, e);
+    if (first) {
+      S = p;
+      E = e;
+    } else {
+      const dfc2 t = two_sum2(S, p);
+      S = t.hi;
+      E = add2(E, add2(t.lo, e));
+    }
+  };
+  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < nsel; idx += nthr) {
+    const int64_t j = deposit(idx, fx);
+    dfc2 v[B];
+#pragma unroll
+    for (int l = 0; l < B; ++l) v[l] = dfc2_from_double2(a[j + off(l)]);
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+      float2 Ps, Pe, Qs, Qe;
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        const float4 g = p.u[r * B + c];
+        mac(Ps, Pe, v[c], g.x, g.y, c == 0);
+        mac(Qs, Qe, v[c], g.z, g.w, c == 0);
+      }
+      const dfc2 P = fast_two_sum2(Ps, Pe), Q = fast_two_sum2(Qs, Qe);
+      const dfc2 iQ{f2(-Q.hi.y, Q.hi.x), f2(-Q.lo.y, Q.lo.x)};  // i Q
+      a[j + off(r)] = dfc2_to_double2(dfc2_add(P, iQ));
     }
   }
 }

@@ -41,37 +41,47 @@ def cases(n, seed):
     return out
 
 
-@pytest.mark.parametrize("prec", [128, 64])
+@pytest.mark.parametrize("prec,arith", [(128, 0), (128, 1), (64, 0)])
 @pytest.mark.parametrize("fusion", [0, 1])
-def test_multi_target_state_vector(Q, env, prec, fusion):
+def test_multi_target_state_vector(Q, env, prec, arith, fusion):
+    """arith 1: complex128 multi-target passes in double-float arithmetic."""
     n = 10
     psi = rand_state(n, 3)
     Q.setEnvOption(env, "fusion", fusion)
-    for targets, ctrls, U in cases(n, 100 + prec):
-        ref = O.State(n, amps=psi)
-        ref.multi(targets, U, ctrls)
-        q = Q.createQureg(n, prec, env)
-        Q.setAmps(q, psi)
-        Q.multiControlledMultiQubitUnitary(q, ctrls, targets, U)
-        got = Q.copyStateToHost(q)
-        Q.destroyQureg(q)
-        assert np.max(np.abs(got - ref.a)) <= AMP_TOL[prec] * (1 if prec == 128 else 0.1), \
-            (targets, ctrls)
+    Q.setEnvOption(env, "arith", arith)
+    try:
+        for targets, ctrls, U in cases(n, 100 + prec):
+            ref = O.State(n, amps=psi)
+            ref.multi(targets, U, ctrls)
+            q = Q.createQureg(n, prec, env)
+            Q.setAmps(q, psi)
+            Q.multiControlledMultiQubitUnitary(q, ctrls, targets, U)
+            got = Q.copyStateToHost(q)
+            Q.destroyQureg(q)
+            assert np.max(np.abs(got - ref.a)) <= AMP_TOL[prec] * (1 if prec == 128 else 0.1), \
+                (targets, ctrls)
+    finally:
+        Q.setEnvOption(env, "arith", 0)
+        Q.setEnvOption(env, "fusion", 1)
 
 
-@pytest.mark.parametrize("prec", [128, 64])
-def test_multi_target_density_matrix(Q, env, prec):
+@pytest.mark.parametrize("prec,arith", [(128, 0), (128, 1), (64, 0)])
+def test_multi_target_density_matrix(Q, env, prec, arith):
     N = 4
     rho = rand_density_vec(N, 6)
-    for targets, ctrls, U in cases(N, 7)[:8]:
-        ref = O.State(N, density=True, amps=rho)
-        ref.multi(targets, U, ctrls)
-        d = Q.createDensityQureg(N, prec, env)
-        Q.setAmps(d, rho)
-        Q.multiControlledMultiQubitUnitary(d, ctrls, targets, U)
-        got = Q.copyStateToHost(d)
-        Q.destroyQureg(d)
-        assert np.max(np.abs(got - ref.a)) <= AMP_TOL[prec] * (1 if prec == 128 else 0.1)
+    Q.setEnvOption(env, "arith", arith)
+    try:
+        for targets, ctrls, U in cases(N, 7)[:8]:
+            ref = O.State(N, density=True, amps=rho)
+            ref.multi(targets, U, ctrls)
+            d = Q.createDensityQureg(N, prec, env)
+            Q.setAmps(d, rho)
+            Q.multiControlledMultiQubitUnitary(d, ctrls, targets, U)
+            got = Q.copyStateToHost(d)
+            Q.destroyQureg(d)
+            assert np.max(np.abs(got - ref.a)) <= AMP_TOL[prec] * (1 if prec == 128 else 0.1)
+    finally:
+        Q.setEnvOption(env, "arith", 0)
 
 
 @pytest.mark.parametrize("prec", [128, 64])
@@ -212,7 +222,7 @@ def gather_bits(idx, phys):
     return out
 
 
-@pytest.mark.parametrize("prec", [128, 64])
+@pytest.mark.parametrize("prec,arith", [(128, 0), (128, 1), (64, 0)])
 @pytest.mark.parametrize("m,targets,ctrls", [
     (5, (0, 19, 7, 1, 12), (5, 17)),   # targets mixed low and high, two controls
     (5, (0, 1, 2, 3, 4), (9,)),         # all among the lowest qubits
@@ -220,7 +230,7 @@ def gather_bits(idx, phys):
     (4, (25, 26, 27, 28), (3,)),        # complex64: the paired-FMA CUDA-core pass
     (4, (1, 0, 3, 2), ()),              # complex64: the tensor cores in address order
 ])
-def test_multi_target_30_qubits(Q, env, prec, m, targets, ctrls):
+def test_multi_target_30_qubits(Q, env, prec, arith, m, targets, ctrls):
     """A dense gate on a 30-qubit register (16 GiB complex128, 8 GiB
     complex64: 2^25 or more blocks, 64-bit indices) prepared as a product
     state: a seeded circuit on the 23-25 qubits A outside the gate, and one
@@ -242,6 +252,7 @@ def test_multi_target_30_qubits(Q, env, prec, m, targets, ctrls):
     sb = O.run_circuit(len(B), ops_b)
     sb.multi(tuple(loc[t] for t in targets), U, tuple(loc[c] for c in ctrls))
     q = Q.createQureg(n, prec, env)
+    Q.setEnvOption(env, "arith", arith)
     try:
         Q.applyCircuit(q, remap(ops_a, A) + remap(ops_b, B))
         Q.multiControlledMultiQubitUnitary(q, ctrls, targets, U)
@@ -249,6 +260,7 @@ def test_multi_target_30_qubits(Q, env, prec, m, targets, ctrls):
         got = np.array([Q.copyStateToHost(q, int(i), 1)[0] for i in idx])
         tot = Q.calcTotalProb(q)
     finally:
+        Q.setEnvOption(env, "arith", 0)
         Q.destroyQureg(q)
     want = fa[gather_bits(idx, A)] * sb.a[gather_bits(idx, B)]
     scale = np.max(np.abs(want))
