@@ -584,6 +584,12 @@ def multi_sweep(Q, env, torch, stream, n=30):
                     tg = tuple(range(7, 7 + m))
                     ms = timed(torch, stream, lambda: Q.multiQubitUnitary(q, tg, U), 2)
                     out[f"c{prec}_m{m}"] = {"ms": ms, "GBps": 2 * (1 << n) * S / ms / 1e6}
+                    if m in (2, 3) or (prec == 128 and m >= 4):
+                        # the same gate on the lowest qubits (contiguous runs
+                        # in every block); complex64 m = 4, 5 below
+                        low = tuple(range(m))
+                        ms = timed(torch, stream, lambda: Q.multiQubitUnitary(q, low, U), 2)
+                        out[f"c{prec}_m{m}_low_targets"] = {"ms": ms, "GBps": 2 * (1 << n) * S / ms / 1e6}
                     if prec == 128 and m >= 2:
                         # complex128 in double-float arithmetic (FP32 pipes)
                         Q.setEnvOption(env, "arith", 1)

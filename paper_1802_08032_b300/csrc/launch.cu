@@ -244,6 +244,71 @@ void multi_pass_tc(Env& env, Reg& r, const MultiParams<float, M>& mp, const Fixe
   }
 }
 
+// The tiled complex64 pass (k_sv_multi_f2_tile): false (nothing launched)
+// when fewer than 8 qubits are neither target nor control.
+template <int M>
+bool multi_pass_tile(Env& env, Reg& r, const MultiParams<float, M>& mp, uint64_t cmask) {
+  uint64_t tmask = 0;
+  for (int k = 0; k < M; ++k) tmask |= uint64_t(1) << mp.t[k];
+  std::vector<int> fq;  // the 8 lowest free qubits
+  for (int q = 0; q < r.nq && int(fq.size()) < 8; ++q)
+    if (!((tmask >> q) & 1) && !((cmask >> q) & 1)) fq.push_back(q);
+  if (fq.size() < 8) return false;
+  std::vector<int> L;  // local qubits, ascending
+  for (int q = 0; q < r.nq; ++q)
+    if (((tmask >> q) & 1) || std::find(fq.begin(), fq.end(), q) != fq.end()) L.push_back(q);
+  auto local_of = [&](int q) { return int(std::find(L.begin(), L.end(), q) - L.begin()); };
+  MultiTileParams<M> p{};
+  for (int k = 0; k < M + 8; ++k) p.lpos[k] = uint8_t(L[size_t(k)]);
+  for (int j = 0; j < 8; ++j) p.fpos[j] = uint8_t(local_of(fq[size_t(j)]));
+  // bank bits: a half-warp's 16 blocks differ in block-index bits 0..3; give
+  // each of their local bits at position >= 4 a bank bit the others lack
+  uint32_t used = 0;
+  for (int j = 0; j < 4; ++j)
+    if (p.fpos[j] < 4) used |= 1u << p.fpos[j];
+  for (int j = 0; j < 4; ++j)
+    if (p.fpos[j] >= 4) {
+      int e = 0;
+      while ((used >> e) & 1u) ++e;
+      p.swz[p.fpos[j]] = uint8_t(1u << e);
+      used |= 1u << e;
+    }
+  auto slot = [&](uint32_t x) {
+    uint32_t s = x;
+    for (int k = 4; k < M + 8; ++k)
+      if ((x >> k) & 1u) s ^= p.swz[k];
+    return uint16_t(s);
+  };
+  for (int i = 0; i < (1 << M); ++i) {
+    int64_t g = 0;
+    for (int k = 0; k < M; ++k)
+      if ((i >> k) & 1) g += int64_t(1) << L[size_t(8 + k)];
+    p.goff_hi[i] = g;
+    p.sm_hi[i] = slot(uint32_t(i) << 8);
+    uint32_t lam = 0;
+    for (int k = 0; k < M; ++k)
+      if ((i >> k) & 1) lam |= 1u << local_of(mp.t[k]);
+    p.sm_l[i] = slot(lam);
+  }
+  for (int e = 0; e < (1 << (2 * M)); ++e)
+    p.u[e] = make_float4(mp.u[e].x, mp.u[e].x, mp.u[e].y, mp.u[e].y);
+  std::vector<std::pair<int, int>> bits = ctrl_bits(cmask, 1);
+  for (int q : L) bits.push_back({q, 0});
+  const Fixed fx = make_fixed(bits);
+  const int64_t ntiles = r.dim >> fx.n;
+  // one wave of resident CTAs (each prefetches its next tile)
+  static const int per_sm = [] {
+    int nb = 0;
+    QS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sv_multi_f2_tile<M>, 256, 0));
+    return std::max(1, nb);
+  }();
+  const int grid = int(std::min<int64_t>(ntiles, int64_t(env.sms) * per_sm));
+  KTimer kt(env, "sv_multi_c64", double(ntiles) * 256 * 2 * (1 << M) * sizeof(float2),
+            double(ntiles) * 256 * (1 << (2 * M)) * 8);
+  k_sv_multi_f2_tile<M><<<grid, 256, 0, env.stream>>>(static_cast<float2*>(r.d), ntiles, fx, p);
+  return true;
+}
+
 // One multi-target pass over the vector: targets t (shifted by `shift`),
 // controls cmask, matrix (conjugated when conj).
 template <typename R, int M>
@@ -261,15 +326,21 @@ void multi_pass(Env& env, Reg& r, const GateOp& op, int shift, uint64_t cmask, b
   }
   const Fixed fx = make_fixed(bits);
   const int64_t nsel = r.dim >> fx.n;
-  if constexpr (std::is_same<R, float>::value && M >= 4) {
-    // by shape: the paired-FMA CUDA-core pass is faster at 4 targets when a
-    // thread's block has no run of contiguous amplitudes (all targets at
-    // qubit 5 or above); 5 targets, or runs, go to the tensor cores
+  if constexpr (std::is_same<R, float>::value) {
+    // by shape: 5 targets on the tensor cores; up to 4 on the CUDA cores
+    // (paired FMAs), at 3-4 through shared-memory tiles when a target is
+    // among the five lowest qubits (a thread's block would be short
+    // contiguous runs)
     int tmin = 64;
     for (int k = 0; k < M; ++k) tmin = std::min(tmin, int(p.t[k]));
-    if (env.multi_tc == 2 || (env.multi_tc == 1 && (M == 5 || (tmin < 5 && nsel >= kTcRows)))) {
-      multi_pass_tc<M>(env, r, p, fx, nsel);
-      return;
+    if constexpr (M >= 4) {
+      if (env.multi_tc == 2 || (env.multi_tc == 1 && M == 5)) {
+        multi_pass_tc<M>(env, r, p, fx, nsel);
+        return;
+      }
+    }
+    if constexpr (M >= 3 && M <= 4) {  // (at 2 targets the per-block loads do as well)
+      if (tmin < 5 && multi_pass_tile<M>(env, r, p, cmask)) return;
     }
   }
   KTimer kt(env, kname<R>("sv_multi").c_str(), double(nsel) * 2 * (1 << M) * amp_bytes<R>(),

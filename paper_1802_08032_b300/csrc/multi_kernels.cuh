@@ -99,6 +99,93 @@ __global__ void __launch_bounds__(256) k_sv_multi_f2(float2* __restrict__ a, int
   }
 }
 
+// Tables of k_sv_multi_f2_tile.  A tile is every combination of the M
+// targets and the 8 lowest free qubits (neither target nor control): local
+// index bit k is qubit lpos[k] (ascending), so the lowest local bits are the
+// lowest qubits and a warp's 32 consecutive local indices are (without
+// controls among qubits 0..4) 32 consecutive amplitudes.  Shared-memory slot
+// of local index x: x ^ sw(x), sw XOR-linear with sw(bit k) = swz[k] (bits
+// 0..3 unchanged), chosen so that the 16 blocks a half-warp works on fall in
+// 16 different bank pairs; both access patterns then split into per-thread
+// and per-element parts (the bits are disjoint, so OR = XOR).
+template <int M>
+struct MultiTileParams {
+  float4 u[1 << (2 * M)];      // matrix entries duplicated (re, re, im, im)
+  int64_t goff_hi[1 << M];     // global offset of local index 256 i
+  uint16_t sm_hi[1 << M];      // slot part of local index 256 i
+  uint16_t sm_l[1 << M];       // slot part of block element l (the target bits)
+  uint8_t lpos[16];            // qubit of local bit k, k < M + 8
+  uint8_t fpos[8];             // local bit of block-index bit j (the free local bits)
+  uint8_t swz[16];             // swizzle of local bit k
+};
+
+// k_sv_multi_f2 for a target among the lowest qubits, where one thread's
+// block is a few short runs of contiguous amplitudes and per-block loads do
+// not coalesce: a CTA loads a tile in address order into shared memory
+// (2^M coalesced accesses a thread), each thread updates one block there
+// (256 blocks a tile), and the tile is stored in address order.
+template <int M>
+__global__ void __launch_bounds__(256, M >= 4 ? 2 : 4) k_sv_multi_f2_tile(float2* __restrict__ a, int64_t ntiles, Fixed fx,
+                                                          const __grid_constant__ MultiTileParams<M> p) {
+  constexpr int B = 1 << M;
+  __shared__ float2 tile[256 * B];
+  const uint32_t t = threadIdx.x;
+  int64_t goff_t = 0;
+  uint32_t sm_t = t, lam_b = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if ((t >> k) & 1u) {
+      goff_t += int64_t(1) << p.lpos[k];
+      sm_t ^= p.swz[k];
+      lam_b |= 1u << p.fpos[k];
+    }
+  uint32_t sm_b = lam_b;
+#pragma unroll
+  for (int k = 0; k < M + 8; ++k)
+    if ((lam_b >> k) & 1u) sm_b ^= p.swz[k];
+  int64_t tau = blockIdx.x;
+  if (tau >= ntiles) return;
+  int64_t base = deposit(tau, fx) + goff_t;
+  float2 x[B];
+#pragma unroll
+  for (int i = 0; i < B; ++i) x[i] = a[base + p.goff_hi[i]];
+  for (;;) {
+#pragma unroll
+    for (int i = 0; i < B; ++i) tile[sm_t ^ p.sm_hi[i]] = x[i];
+    __syncthreads();
+    // the next tile's loads go out before this tile's arithmetic and stores
+    // (the condition is uniform over the CTA)
+    const int64_t tau_n = tau + gridDim.x;
+    int64_t base_n = 0;
+    if (tau_n < ntiles) {
+      base_n = deposit(tau_n, fx) + goff_t;
+#pragma unroll
+      for (int i = 0; i < B; ++i) x[i] = a[base_n + p.goff_hi[i]];
+    }
+    float2 v[B];
+#pragma unroll
+    for (int l = 0; l < B; ++l) v[l] = tile[sm_b ^ p.sm_l[l]];
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+      float2 P = make_float2(0.f, 0.f), Q = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        const float4 g = p.u[r * B + c];
+        P = __ffma2_rn(make_float2(g.x, g.y), v[c], P);
+        Q = __ffma2_rn(make_float2(g.z, g.w), v[c], Q);
+      }
+      tile[sm_b ^ p.sm_l[r]] = make_float2(P.x - Q.y, P.y + Q.x);  // this thread's own slots
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < B; ++i) a[base + p.goff_hi[i]] = tile[sm_t ^ p.sm_hi[i]];
+    if (tau_n >= ntiles) break;
+    __syncthreads();  // the next tile reuses the buffer
+    tau = tau_n;
+    base = base_n;
+  }
+}
+
 // Complex128 matrix entries as double-float pairs: u[e] = (Re hi, Re lo,
 // Im hi, Im lo) of entry e.
 template <int M>

@@ -228,7 +228,8 @@ def gather_bits(idx, phys):
     (5, (0, 1, 2, 3, 4), (9,)),         # all among the lowest qubits
     (5, (25, 26, 27, 28, 29), ()),      # all at the top
     (4, (25, 26, 27, 28), (3,)),        # complex64: the paired-FMA CUDA-core pass
-    (4, (1, 0, 3, 2), ()),              # complex64: the tensor cores in address order
+    (4, (1, 0, 3, 2), ()),              # complex64: shared-memory tiles in address order
+    (3, (2, 0, 4), (1,)),               # the same with a control among the lowest qubits
 ])
 def test_multi_target_30_qubits(Q, env, prec, arith, m, targets, ctrls):
     """A dense gate on a 30-qubit register (16 GiB complex128, 8 GiB
