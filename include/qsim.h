@@ -124,10 +124,10 @@ int qsDiagBoundedWait(QuESTEnv env, int timeoutUs);
  *                   2 = on the tensor cores (FP32 operands as TF32 hi + lo
  *                   pairs, three products accumulated in FP32: a few units of
  *                   1e-7 of the largest amplitude per gate), 0 = FP32 on the
- *                   CUDA cores, 1 = by shape (default): 5 targets, or 4 with
- *                   one below qubit 5, on the tensor cores; 4 targets all at
- *                   qubit 5 or above on the CUDA cores (paired FP32 FMAs,
- *                   faster there)
+ *                   CUDA cores, 1 = by shape (default): 5 targets on the
+ *                   tensor cores, 4 on the CUDA cores (paired FP32 FMAs,
+ *                   faster there; through shared-memory tiles when a target
+ *                   is below qubit 5)
  * Unknown keys give QS_E_ARG. */
 int setEnvOption(QuESTEnv env, const char *key, int64_t value);
 /* getEnvOption: reads an option back, or a counter of the env:

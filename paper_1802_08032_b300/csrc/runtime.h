@@ -126,7 +126,7 @@ struct Env {
   int64_t used = 0;
   int64_t profile = 0;
   int64_t arith = 0;         // complex128 arithmetic of fused passes: 0 = IEEE FP64, 1 = double-float
-  int64_t multi_tc = 1;      // complex64 dense gates on 4-5 targets: 0 CUDA cores, 1 either (by shape), 2 tensor cores
+  int64_t multi_tc = 1;      // complex64 dense gates on 4-5 targets: 0 CUDA cores, 1 by shape (5 on the tensor cores), 2 tensor cores
   Profiler prof;
   // counters (readable through getEnvOption)
   int64_t launches = 0;      // kernel launches issued
