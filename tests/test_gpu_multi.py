@@ -320,3 +320,37 @@ def test_multi_target_density_matrix_14_qubits(Q, env, prec, m, targets, ctrls):
     else:
         assert np.max(np.abs(got - want)) <= 1e-5 * scale
         assert abs(tr - 1.0) <= 1e-5
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_multi_target_random_placements(Q, env, mode):
+    """Complex64 gates on 2-5 targets at seeded random positions, most with a
+    target among the five lowest qubits and some with controls there too
+    (every table the shared-memory tile and tensor-core paths derive from
+    the positions), on 16 qubits, each against the oracle."""
+    n = 16
+    rng = np.random.default_rng(500 + mode)
+    psi = rand_state(n, 61)
+    Q.setEnvOption(env, "multi_tc", mode)
+    try:
+        for case in range(24):
+            m = int(rng.integers(2, 6))
+            nc = int(rng.integers(0, 3))
+            low = rng.permutation(6)[: int(rng.integers(1, min(m, 3) + 1))]
+            rest = [q for q in rng.permutation(n) if q not in low]
+            qs = [int(q) for q in low] + [int(q) for q in rest]
+            targets, ctrls = tuple(qs[:m]), tuple(qs[m:m + nc])
+            if case % 3 == 0 and nc > 0:  # a control among the lowest qubits
+                ctrls = (targets[0],) + ctrls[1:]
+                targets = (qs[m + nc],) + targets[1:]
+            U = rand_u(1 << m, 700 + 31 * mode + case)
+            ref = O.State(n, amps=psi)
+            ref.multi(targets, U, ctrls)
+            q = Q.createQureg(n, 64, env)
+            Q.setAmps(q, psi)
+            Q.multiControlledMultiQubitUnitary(q, ctrls, targets, U)
+            got = Q.copyStateToHost(q)
+            Q.destroyQureg(q)
+            assert np.max(np.abs(got - ref.a)) <= 5e-6 * np.max(np.abs(ref.a)), (m, targets, ctrls)
+    finally:
+        Q.setEnvOption(env, "multi_tc", 1)
