@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--variants", default="",
                     help="comma-separated variant names to run (default: all)")
-    ap.add_argument("--cpu-gates", type=int, default=10,
+    ap.add_argument("--cpu-gates", type=int, default=40,
                     help="gates in the bounded CPU-oracle sample")
     return ap.parse_args()
 
