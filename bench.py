@@ -389,7 +389,8 @@ def timed(torch, stream, fn, reps):
 
 def variants(Q, env, torch, stream, only=(), qubits=30, serve=(60, 0.0)):
     """Other configurations of the same metric, measured outside the timed
-    region: complex64 and double-float complex128 at 30 qubits, the 33-qubit
+    region: the 12-qubit circuit (latency), complex64 and double-float
+    complex128 at 30 qubits, the 33-qubit
     (128 GiB complex128, 64 GiB complex64) depth-40 circuits, the 14-qubit
     noisy density matrix, single-gate pass bandwidth by target bit, batches,
     serving and multi-target passes (on a register of `qubits` qubits, the
@@ -478,7 +479,30 @@ def variants(Q, env, torch, stream, only=(), qubits=30, serve=(60, 0.0)):
             Q.destroyQureg(d)
         return {"ops_per_s": len(dops) / ms * 1e3, "ms_per_circuit": ms, "ops": len(dops)}
 
-    for name, fn in (("sv30_c64", sv(64, 0)), ("sv30_c128_df", sv(128, 1)),
+    def sv12(reps=300):
+        # the 12-qubit complex128 depth-20 circuit (64 KiB: one fused tile):
+        # latency-bound, so whole circuits are timed on the host clock, each
+        # reset, planned, run and reduced (calcTotalProb reads its result)
+        import time
+        ops12 = Q.to_qsops(C.workload_12q())
+        q = Q.createQureg(12, 128, env)
+        try:
+            def run():
+                Q.initZeroState(q)
+                Q.applyCircuit(q, ops12)
+                return Q.calcTotalProb(q)
+            for _ in range(10):
+                run()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                run()
+            us = (time.perf_counter() - t0) / reps * 1e6
+        finally:
+            Q.destroyQureg(q)
+        return {"qubits": 12, "gates": ops12[1], "us_per_circuit": us,
+                "gates_per_s": ops12[1] / us * 1e6, "circuits_per_s": 1e6 / us}
+
+    for name, fn in (("sv12_c128", sv12), ("sv30_c64", sv(64, 0)), ("sv30_c128_df", sv(128, 1)),
                      ("sv33_c128", sv(128, 0, 33, 1)), ("sv33_c64", sv(64, 0, 33)),
                      ("single_gate_sweep", lambda: sweep(30, range(30))),
                      ("single_gate_sweep_33q", lambda: sweep(33, range(33))),

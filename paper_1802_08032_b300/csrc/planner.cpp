@@ -623,12 +623,24 @@ std::vector<Pass> plan(const std::vector<VOp>& ops, int nq, int k, int L, int64_
   scale.limit = scale_limit;
   scale.g = scale_in;
   const uint64_t low = (uint64_t(1) << L) - 1;
+  const uint64_t all = nq >= 64 ? ~uint64_t(0) : (uint64_t(1) << nq) - 1;
   while (!rem.empty()) {
     Pass p;
     uint64_t tile = low, bx = 0, ball = 0;
     std::vector<VOp> deferred;
     for (const VOp& v : rem) {
       const uint64_t x = v.xmask(), z = v.zmask();
+      // A mid-plan scale (a density matrix's deferred channel factor)
+      // balances the growth of the operations before it; moved ahead of a
+      // deferred one it would shrink the amplitudes early, and with float
+      // exponents (double-float) values below 2^-74 lose their low parts
+      // when a pass boundary stores them.  So it stays behind every deferred
+      // op, and no later op that mixes amplitudes passes it.
+      if (v.kind == FK_SCALE && !deferred.empty()) {
+        deferred.push_back(v);
+        ball = all;
+        continue;
+      }
       const bool commutes = (x & ball) == 0 && ((x | z) & bx) == 0;
       const bool fits = popc(tile | x) <= k;
       const bool room = int64_t(p.ops.size()) < max_ops;
@@ -917,6 +929,12 @@ void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, uint64_t 
   int k = std::min(cfg.kmax, r.nq);
   if (k_req > 0) k = std::min(k_req, r.nq);
   else if (env.tile_qubits > 0) k = std::min<int>(int(env.tile_qubits), r.nq);
+  // a register of at most 18 qubits has too few tiles to fill the GPU: one
+  // qubit less per tile doubles the tiles (SMs at work) for a few more
+  // passes (measured, circuit of depth 20: complex128 12 / 16 / 18 qubits
+  // 372-528 / 497 / 563 -> 283 / 369 / 405 us; complex64 16 / 18 qubits
+  // 255 / 288 -> 232 / 265 us)
+  else if (r.nq <= 18) k = std::min(k, cfg.kmax - 1);
   k = std::max(k, std::min(cfg.R + 5, r.nq));
   k = std::min(k, cfg.R + 8);
   const int L = std::min(cfg.L, k);

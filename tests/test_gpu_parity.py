@@ -193,15 +193,17 @@ def test_density_circuit_general_gates(Q, env, prec, arith, fusion, N):
 
 @pytest.mark.parametrize("prec,arith", [(128, 0), (128, 1), (64, 0)])
 @pytest.mark.parametrize("p_depol", [0.3, 0.75])
-def test_density_circuit_heavy_noise(Q, env, prec, arith, p_depol):
+@pytest.mark.parametrize("N", [6, 7])
+def test_density_circuit_heavy_noise(Q, env, prec, arith, p_depol, N):
     """Strong channels after every gate: the fused plan defers each qubit's
     off-diagonal factor (applied as a register-pair dephasing before the next
     pair update on the qubit), applies the common factor 1 - 2p/3 of each
-    depolarising channel mid-plan once it passes 2^-30, pairs a T's row and
-    column phases into one off-diagonal op, and at p = 3/4 zeroes every
+    depolarising channel mid-plan once it passes 2^-30 (in order: over
+    several passes a scale moved ahead of the growth it balances took
+    double-float amplitudes below 2^-74 at a pass boundary), pairs a T's row
+    and column phases into one off-diagonal op, and at p = 3/4 zeroes every
     off-diagonal entry of the qubit.  Against the unfused path and the
     oracle, with the trace and purity."""
-    N = 6
     ops = C.with_noise(general_gates(N, 90), 0.3, p_depol)
     ref = O.run_circuit(N, ops, density=True)
     Q.setEnvOption(env, "arith", arith)
