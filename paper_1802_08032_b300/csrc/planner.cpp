@@ -734,8 +734,10 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
   // not local and are skipped)
   auto local_mask = [&](uint64_t x) {
     uint32_t m = 0;
-    for (int b = 0; b < 64; ++b)
-      if (((x >> b) & 1) && lpos[b] >= 0) m |= 1u << lpos[b];
+    for (; x; x &= x - 1) {
+      const int b = __builtin_ctzll(x);
+      if (lpos[b] >= 0) m |= 1u << lpos[b];
+    }
     return m;
   };
 
@@ -804,8 +806,8 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
         f.flags |= FF_SIDE;
       }
       if (v.kind == FK_SHEAR) f.i1 = v.c[1] != 0.0 ? 1 : 0;
-      for (int b = 0; b < 64; ++b) {
-        if (!((v.cond >> b) & 1)) continue;
+      for (uint64_t cb = v.cond; cb; cb &= cb - 1) {
+        const int b = __builtin_ctzll(cb);
         if (lpos[b] < 0) f.gmask |= uint64_t(1) << b;
         else if ((P >> lpos[b]) & 1) f.rmask |= uint8_t(1u << idx[lpos[b]]);
         else f.lmask |= 1u << lpos[b];
