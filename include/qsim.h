@@ -355,16 +355,24 @@ int serveDestroy(QSServer server);
  * that loads the library until the process exits.  The paper has no
  * counterpart; this is a library convenience.
  *   amps       device pointer to numAmps interleaved complex amplitudes
- *              (double2 for QS_C128, float2 for QS_C64), owned by the caller
+ *              (double2 for QS_C128, float2 for QS_C64), owned by the caller,
+ *              aligned to one amplitude (16 / 8 bytes; else QS_E_ARG).  For a
+ *              state vector the result is the total probability; for a
+ *              density matrix's 2^(2N) stored entries it is the purity
+ *              Tr rho^2, not the trace (use calcTotalProb for Tr rho)
  *   precision  QS_C64 or QS_C128
  *   numAmps    1 .. 2^30 (one scratch slot per 16384 amplitudes); larger
  *              arrays are rejected with QS_E_ARG and a message
- *   out        device pointer to one double, owned by the caller; written
- *              when the call's kernels run
+ *   out        device pointer to one double, owned by the caller, 8-byte
+ *              aligned (else QS_E_ARG); written when the call's kernels run
  *   stream     cudaStream_t the work is queued on (null = legacy default);
  *              the call returns without waiting
  * The first call on a device looks up the scratch array's device address
  * with that device current; make that first call before any stream capture.
+ * The address is kept until the process exits: after cudaDeviceReset on a
+ * device, do not call this entry point on that device again.  A CUDA error
+ * left pending by earlier work is reported (QS_E_CUDA) without being cleared,
+ * and nothing is launched.
  * All calls share the one scratch array: calls whose kernels overlap on the
  * GPU (different streams, or several host threads) race and give wrong
  * sums; serialise them.  Every scratch slot a call reads is written by that

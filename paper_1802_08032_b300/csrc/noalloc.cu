@@ -88,6 +88,14 @@ int calcTotalProbNoAlloc(const void* amps, int precision, int64_t numAmps, doubl
   if (!amps || !out) return na_fail(QS_E_ARG, "null amplitude or output pointer");
   if (precision != QS_C64 && precision != QS_C128)
     return na_fail(QS_E_ARG, "precision must be QS_C64 or QS_C128");
+  // the kernels read 16-byte (complex128) or 8-byte (complex64) amplitudes
+  // and write one double: a misaligned pointer would fault on the device
+  const uintptr_t amp_align = precision == QS_C128 ? 16 : 8;
+  if (reinterpret_cast<uintptr_t>(amps) % amp_align != 0)
+    return na_fail(QS_E_ARG, "amps is not aligned to " + std::to_string(amp_align) +
+                                 " bytes (one amplitude)");
+  if (reinterpret_cast<uintptr_t>(out) % 8 != 0)
+    return na_fail(QS_E_ARG, "out is not aligned to 8 bytes (one double)");
   if (numAmps < 1 || numAmps > kNaMaxAmps)
     return na_fail(QS_E_ARG, "numAmps " + std::to_string(numAmps) + " outside [1, " +
                                  std::to_string(kNaMaxAmps) +
@@ -100,7 +108,9 @@ int calcTotalProbNoAlloc(const void* amps, int precision, int64_t numAmps, doubl
   double* scratch = nullptr;
   {
     // first call on this device: device address of the scratch array, taken
-    // with the device current (the host-side name is not a device address)
+    // with the device current (the host-side name is not a device address).
+    // The address is kept for the life of the process; cudaDeviceReset
+    // unloads the module and invalidates it.
     std::lock_guard<std::mutex> lk(g_na_mu);
     if (!g_na_ptr[dev]) {
       void* p = nullptr;
@@ -111,6 +121,13 @@ int calcTotalProbNoAlloc(const void* amps, int precision, int64_t numAmps, doubl
     }
     scratch = g_na_ptr[dev];
   }
+  // An error left pending by earlier, unrelated work belongs to its owner:
+  // report it without clearing it and launch nothing, so that the error
+  // checked after the launches below is this call's own.
+  e = cudaPeekAtLastError();
+  if (e != cudaSuccess)
+    return na_fail(QS_E_CUDA, std::string("a CUDA error from earlier work is pending (not cleared): ") +
+                                  cudaGetErrorString(e));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int blocks = int((numAmps + kNaChunk - 1) / kNaChunk);
   // every partial the final kernel reads is written by this call first, so

@@ -76,3 +76,29 @@ def gpu_state(Q, env, n, ops, prec, density=False, fusion=1, init=None):
 
 def fsum_abs2(v):
     return math.fsum((v.real ** 2).tolist() + (v.imag ** 2).tolist())
+
+
+def inverse(ops):
+    """C-dagger of a gate list: the inverse of each gate, in reverse order.
+    sqrt(X) and sqrt(Y) are principal square roots, (1/2)[[1+i, 1-i], [1-i, 1+i]]
+    and ((1+i)/2)[[1, -1], [1, 1]]; their inverses are the conjugate
+    transposes.  compactUnitary(a, b) = [[a, -b*], [b, a*]] has the inverse
+    compactUnitary(a*, -b)."""
+    sx_dag = (0.5, -0.5, 0.5, 0.5, 0.5, 0.5, 0.5, -0.5)
+    sy_dag = (0.5, -0.5, 0.5, -0.5, -0.5, 0.5, 0.5, -0.5)
+    out = []
+    for o in reversed(ops):
+        if o.kind in (C.H, C.CZ, C.MCPF):
+            out.append(o)
+        elif o.kind == C.T_GATE:
+            out.append(C.Op(C.PHASE, o.targets, (), (-np.pi / 4,)))
+        elif o.kind == C.SQRT_X:
+            out.append(C.Op(C.UNITARY, o.targets, (), sx_dag))
+        elif o.kind == C.SQRT_Y:
+            out.append(C.Op(C.UNITARY, o.targets, (), sy_dag))
+        elif o.kind == C.COMPACT:
+            ar, ai, br, bi = o.params
+            out.append(C.Op(C.COMPACT, o.targets, (), (ar, -ai, -br, -bi)))
+        else:
+            raise AssertionError(o.kind)
+    return out

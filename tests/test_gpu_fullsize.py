@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from paper_1802_08032_b300 import circuits as C
-from gpu_helpers import AMP_TOL, DF_PROB_TOL, PROB_TOL
+from gpu_helpers import AMP_TOL, DF_PROB_TOL, PROB_TOL, inverse
 
 pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
@@ -73,20 +73,24 @@ def shifted(ops, k):
             for o in ops]
 
 
-def test_33_qubit_product_state(Q, env):
-    """33 qubits (2^33 amplitudes, 128 GiB complex128): a 30-qubit circuit on
-    qubits 0..29 and a 3-qubit circuit on 30..32; every sampled amplitude is
-    the product of the two factors' amplitudes (64-bit indices throughout)."""
+@pytest.mark.parametrize("prec,arith", [(128, 0), (128, 1), (64, 0)])
+def test_33_qubit_product_state(Q, env, prec, arith):
+    """33 qubits (2^33 amplitudes: 128 GiB complex128, 64 GiB complex64): a
+    30-qubit circuit on qubits 0..29 and a 3-qubit circuit on 30..32; every
+    sampled amplitude is the product of the two factors' amplitudes (64-bit
+    indices throughout).  Runs the IEEE-FP64 and complex64 fused kernels as
+    well as the double-float one."""
     g = golden("sv33_product_factors.json")
     low = C.random_circuit(30, 12, 3330, extras=True)
     high = C.random_circuit(3, 12, 3333, extras=True)
     assert C.stream_hash(low) == g["hash_low"] and C.stream_hash(high) == g["hash_high"]
-    Q.setEnvOption(env, "arith", 1)          # double-float keeps the 33-qubit run short
+    Q.setEnvOption(env, "arith", arith)
     try:
-        q = Q.createQureg(33, 128, env)
+        q = Q.createQureg(33, prec, env)
         Q.applyCircuit(q, low + shifted(high, 30))
         tot = Q.calcTotalProb(q)
         probs_hi = [Q.calcProbOfOutcome(q, 30 + k, 1) for k in range(3)]
+        probs_lo = [Q.calcProbOfOutcome(q, k, 1) for k in (0, 13, 29)]
         lo_idx = g["low_indices"][:512]
         lo_amp = as_complex(g["low_amps"])[:512]
         hi_amp = as_complex(g["high_amps"])
@@ -96,9 +100,35 @@ def test_33_qubit_product_state(Q, env):
     finally:
         Q.setEnvOption(env, "arith", 0)
     want = np.array([hi_amp[j] * a for j in range(8) for a in lo_amp])
-    assert np.max(np.abs(got - want)) <= AMP_TOL[128]
-    assert abs(tot - g["low_total_prob"]) <= PROB_TOL
-    assert np.max(np.abs(np.array(probs_hi) - g["high_prob_outcome_1"])) <= PROB_TOL
+    assert np.max(np.abs(got - want)) <= AMP_TOL[prec]
+    tol = PROB_TOL if prec == 128 else 1e-5
+    assert abs(tot - g["low_total_prob"]) <= tol
+    assert np.max(np.abs(np.array(probs_hi) - g["high_prob_outcome_1"])) <= tol
+    assert np.max(np.abs(np.array(probs_lo) - np.array(g["low_prob_outcome_1"])[[0, 13, 29]])) <= tol
+
+
+@pytest.mark.parametrize("prec", [128, 64])
+def test_33_qubit_mirror_circuit(Q, env, prec):
+    """33-qubit depth-40 workload C followed by C-dagger returns |0...0>
+    (no host oracle: the 128 GiB state does not fit a host).  Pins the
+    full-size 64-bit index paths of the fused kernels (IEEE FP64 and
+    complex64) by a closed form."""
+    ops = C.workload_30q(33)
+    q = Q.createQureg(33, prec, env)
+    try:
+        Q.applyCircuit(q, ops + inverse(ops))
+        tot = Q.calcTotalProb(q)
+        probs = [Q.calcProbOfOutcome(q, k, 1) for k in range(33)]
+        head = Q.copyStateToHost(q, 0, 64)
+        tail = Q.copyStateToHost(q, (1 << 33) - 64, 64)
+    finally:
+        Q.destroyQureg(q)
+    tol = AMP_TOL[prec]
+    assert abs(head[0] - 1) <= tol
+    assert np.max(np.abs(head[1:])) <= tol and np.max(np.abs(tail)) <= tol
+    ptol = PROB_TOL if prec == 128 else 1e-5
+    assert abs(tot - 1) <= ptol
+    assert max(probs) <= ptol
 
 
 @pytest.mark.parametrize("prec,arith", [(128, 0), (128, 1), (64, 0)])

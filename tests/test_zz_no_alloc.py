@@ -6,6 +6,8 @@ buffers): it takes caller-owned device input and output and keeps its scratch
 in a fixed array inside the library.  This file is collected last, so a run
 that stops at the first failure has run every other test before it.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -65,7 +67,40 @@ def test_no_alloc_norm_rejects_bad_sizes():
     with pytest.raises(Q.QSimError) as e:
         Q.calcTotalProbNoAlloc(amps.data_ptr(), 32, 64, out.data_ptr())
     assert e.value.name == "QS_E_ARG"
+    # misaligned pointers are refused on the host, before anything launches
+    for aptr, prec, optr in ((amps.data_ptr() + 8, 128, out.data_ptr()),
+                             (amps.data_ptr() + 4, 64, out.data_ptr()),
+                             (amps.data_ptr(), 128, out.data_ptr() + 4)):
+        with pytest.raises(Q.QSimError) as e:
+            Q.calcTotalProbNoAlloc(aptr, prec, 8, optr)
+        assert e.value.name == "QS_E_ARG"
     amps[3] = 0.6 + 0.8j
     Q.calcTotalProbNoAlloc(amps.data_ptr(), 128, 64, out.data_ptr())
     torch.cuda.synchronize()
     assert abs(float(out[0]) - 1.0) <= PROB_TOL
+
+
+@pytest.mark.parametrize("prec", [128, 64])
+def test_no_alloc_norm_ragged_last_chunk(prec):
+    """Several CTAs with a partial last chunk (3 * 16384 + 5 amplitudes) on a
+    caller-filled array, against an exact host sum of the same values."""
+    import torch
+    from paper_1802_08032_b300 import qsim as Q
+    n = 3 * 16384 + 5
+    rng = np.random.default_rng(9)
+    v = (rng.normal(size=n) + 1j * rng.normal(size=n)) * 1e-2
+    dt = torch.complex128 if prec == 128 else torch.complex64
+    amps = torch.from_numpy(v).to(dt).cuda()
+    host = amps.cpu().numpy().astype(np.complex128)
+    want = math.fsum((host.real ** 2).tolist() + (host.imag ** 2).tolist())
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        Q.calcTotalProbNoAlloc(amps.data_ptr(), prec, n, out.data_ptr())
+        torch.cuda.synchronize()
+        assert abs(float(out[0]) - want) <= PROB_TOL * max(1.0, want)
+    # the same values in the first 3 * 16384 only: the tail's share is gone
+    Q.calcTotalProbNoAlloc(amps.data_ptr(), prec, 3 * 16384, out.data_ptr())
+    torch.cuda.synchronize()
+    head = host[:3 * 16384]
+    want_head = math.fsum((head.real ** 2).tolist() + (head.imag ** 2).tolist())
+    assert abs(float(out[0]) - want_head) <= PROB_TOL * max(1.0, want_head)
