@@ -63,6 +63,9 @@ def parse():
                     help="serving variant: also cap each rate's trace at this many seconds of arrivals "
                          "(0 = no cap); 2000 and 60 give the full-length sweep")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--jit", type=int, default=1, choices=[0, 1, 2],
+                    help="fused passes: 0 interpreting kernel, 1 runtime-compiled kernels "
+                         "(compiled in the warm-up), 2 compiled in the background")
     ap.add_argument("--variants", default="",
                     help="comma-separated variant names to run (default: all)")
     ap.add_argument("--cpu-gates", type=int, default=40,
@@ -286,6 +289,9 @@ def main():
     ngates = len(ops)
     env = Q.createQuESTEnv()
     Q.setEnvOption(env, "arith", 1 if args.arith == "df" else 0)
+    # fused passes as runtime-compiled kernels, compiled during the warm-up
+    # (the first step waits for them; timed steps reuse the cached kernels)
+    Q.setEnvOption(env, "jit", args.jit)
     stream = torch.cuda.Stream()
     Q.setStream(env, stream)
     q = Q.createQureg(n, prec, env)
@@ -347,7 +353,10 @@ def main():
                    "qubits": n, "precision": f"complex{prec}", "arith": args.arith,
                    "gates_per_step": ngates, "parallelism": f"replicas x{world}",
                    "l2": "state 2^n amplitudes >> 126 MB L2, no flush",
-                   "fused_passes_per_step": passes},
+                   "fused_passes_per_step": passes,
+                   "jit": {"mode": args.jit, "kernels": Q.getEnvOption(env, "jit_ready"),
+                           "compile_ms_total": Q.getEnvOption(env, "jit_compile_ms"),
+                           "launches": Q.getEnvOption(env, "jit_launches")}},
         "roofline": roofline(stats, 1 << n),
         "e2e": {"value": total_gates / e2e_s, "unit": "gates/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},

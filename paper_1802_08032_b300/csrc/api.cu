@@ -9,6 +9,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "jit_runtime.h"
 #include "runtime.h"
 
 using namespace qs;
@@ -308,6 +309,15 @@ int setEnvOption(QuESTEnv e, const char* key, int64_t value) {
     } else if (k == "multi_tc") {
       if (value < 0 || value > 2) fail(QS_E_ARG, "multi_tc must be 0, 1 or 2");
       env.multi_tc = value;
+    } else if (k == "jit") {
+      if (value < 0 || value > 2) fail(QS_E_ARG, "jit must be 0 (off), 1 (compile and wait) or 2 (background)");
+      env.jit = value;
+    } else if (k == "jit_min_qubits") {
+      if (value < 1 || value > 64) fail(QS_E_ARG, "jit_min_qubits must be in 1..64");
+      env.jit_min_qubits = value;
+    } else if (k == "jit_ctas") {
+      if (value < 1 || value > 4) fail(QS_E_ARG, "jit_ctas must be in 1..4");
+      env.jit_ctas = value;
     } else {
       fail(QS_E_ARG, "unknown option " + k);
     }
@@ -328,6 +338,15 @@ int getEnvOption(QuESTEnv e, const char* key, int64_t* value) {
     else if (k == "profile") *value = env.profile;
     else if (k == "arith") *value = env.arith;
     else if (k == "multi_tc") *value = env.multi_tc;
+    else if (k == "jit") *value = env.jit;
+    else if (k == "jit_min_qubits") *value = env.jit_min_qubits;
+    else if (k == "jit_ctas") *value = env.jit_ctas;
+    else if (k == "jit_launches") *value = env.jit_launches;
+    else if (k == "jit_rejected") *value = env.jit_rejected;
+    else if (k == "jit_ready") *value = jit_stats().ready;
+    else if (k == "jit_pending") *value = jit_stats().pending;
+    else if (k == "jit_failed") *value = jit_stats().failed;
+    else if (k == "jit_compile_ms") *value = int64_t(jit_stats().compile_s * 1e3);
     else if (k == "launches") *value = env.launches;
     else if (k == "fused_passes") *value = env.fused_passes;
     else if (k == "fused_vops") *value = env.fused_vops;

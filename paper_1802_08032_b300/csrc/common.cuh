@@ -1,7 +1,9 @@
 // Shared device definitions of the simulator kernels.
 #pragma once
+#ifndef __CUDACC_RTC__
 #include <cstdint>
 #include <cuda_runtime.h>
+#endif
 
 namespace qs {
 

@@ -17,8 +17,10 @@
 // with one FP64 addition.  Magnitudes below 2^-126 (hi) or 2^-74 (lo part)
 // are flushed to zero: an absolute error below 1e-22 per amplitude.
 #pragma once
+#ifndef __CUDACC_RTC__
 #include <cstdint>
 #include <cuda_runtime.h>
+#endif
 
 namespace qs {
 

@@ -6,6 +6,7 @@
 #include <cstring>
 
 #include "fused_kernel.cuh"
+#include "jit_runtime.h"
 #include "plan.h"
 #include "runtime.h"
 
@@ -147,6 +148,11 @@ void flush(Reg& r) {
       fp.stage_end += int(st0[pi]);
       const FOp* d_ops = static_cast<const FOp*>(env.d_fops);
       const FStage* d_st = static_cast<const FStage*>(env.d_fst);
+      // the pass as its own compiled kernel when one is ready (jit.cpp)
+      const int R = pl.arith == Arith::F32 ? 5 : 4;
+      const char* name = pl.arith == Arith::DF ? "fused_c128_df" : pl.arith == Arith::F64 ? "fused_c128" : "fused_c64";
+      if (jit_try_launch(env, r, pl.fps[i], pl.fst.data(), pl.fops.data(), pl.arith, R, pl.flops[i], pl.alu[i], name))
+        continue;
       if (pl.arith == Arith::DF)
         launch_pass<DFArith, 4>(env, r, fp, d_ops, d_st, pl.flops[i], pl.alu[i], "fused_c128_df");
       else if (pl.arith == Arith::F64)

@@ -1,7 +1,9 @@
 // Encoding of fused-pass operations, shared by the host planner and the
 // fused tile kernel (plain C++: no device code).
 #pragma once
+#ifndef __CUDACC_RTC__
 #include <cstdint>
+#endif
 
 namespace qs {
 

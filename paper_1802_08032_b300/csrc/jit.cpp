@@ -1,0 +1,255 @@
+// Runtime compilation and cache of the generated pass kernels (see jit.h).
+//
+// A kernel is compiled by NVRTC for sm_103a straight to a cubin, loaded as
+// a context-independent CUDA library and kept for the life of the process,
+// keyed by its source text (which spells out the whole pass structure, so
+// equal text means an equal kernel).  Compilation runs on a small pool of
+// host threads: with the "jit" option 2 (asynchronous) a flush launches the
+// interpreting kernel for any pass whose kernel is not ready yet and queues
+// its compilation; with 1 (synchronous) the flush waits for the compile.
+#include <nvrtc.h>
+
+#include <algorithm>
+#include <cmath>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+
+#include "jit.h"
+#include "jit_runtime.h"
+#include "runtime.h"
+
+namespace qs {
+
+// Headers embedded at build time (generated jit_headers.inc: an array of
+// {name, text} pairs of the device headers the generated source includes).
+namespace {
+struct EmbeddedHeader {
+  const char* name;
+  const char* text;
+};
+#include "jit_headers.inc"
+}  // namespace
+
+int jit_header_count() { return int(sizeof(kJitHeaders) / sizeof(kJitHeaders[0])); }
+const char* jit_header_name(int i) { return kJitHeaders[i].name; }
+const char* jit_header_text(int i) { return kJitHeaders[i].text; }
+
+namespace {
+
+enum JitState : int { JS_QUEUED = 0, JS_READY = 1, JS_FAILED = 2 };
+
+struct JitEntry {
+  std::string src;
+  int device = 0;
+  size_t smem = 0;
+  std::atomic<int> state{JS_QUEUED};
+  cudaLibrary_t lib = nullptr;
+  cudaKernel_t kern = nullptr;
+  double compile_s = 0;
+  std::string log;
+};
+
+class JitCache {
+ public:
+  static JitCache& get() {
+    static JitCache c;
+    return c;
+  }
+  ~JitCache() {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      stop_ = true;
+      queue_.clear();
+    }
+    cv_.notify_all();
+    for (std::thread& t : workers_)
+      if (t.joinable()) t.join();
+  }
+
+  // The entry of this source, created (and queued for compilation) if new.
+  std::shared_ptr<JitEntry> find_or_queue(const std::string& src, int device, size_t smem, bool& created) {
+    std::lock_guard<std::mutex> lk(mu_);
+    auto it = map_.find(src);
+    created = false;
+    if (it != map_.end()) return it->second;
+    auto e = std::make_shared<JitEntry>();
+    e->src = src;
+    e->device = device;
+    e->smem = smem;
+    map_.emplace(src, e);
+    queue_.push_back(e);
+    created = true;
+    start_workers_locked();
+    cv_.notify_one();
+    return e;
+  }
+
+  // Waits until e is compiled (or failed).
+  void wait(const std::shared_ptr<JitEntry>& e) {
+    std::unique_lock<std::mutex> lk(mu_);
+    done_cv_.wait(lk, [&] { return e->state.load() != JS_QUEUED || stop_; });
+  }
+
+  JitStats stats() {
+    std::lock_guard<std::mutex> lk(mu_);
+    JitStats s{};
+    for (auto& kv : map_) {
+      const int st = kv.second->state.load();
+      if (st == JS_READY) {
+        ++s.ready;
+        s.compile_s += kv.second->compile_s;
+      } else if (st == JS_FAILED) {
+        ++s.failed;
+      } else {
+        ++s.pending;
+      }
+    }
+    return s;
+  }
+
+  std::string first_failure() {
+    std::lock_guard<std::mutex> lk(mu_);
+    for (auto& kv : map_)
+      if (kv.second->state.load() == JS_FAILED) return kv.second->log;
+    return {};
+  }
+
+ private:
+  void start_workers_locked() {
+    if (!workers_.empty()) return;
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const unsigned n = std::min(16u, std::max(2u, hw / 2));
+    for (unsigned i = 0; i < n; ++i) workers_.emplace_back([this] { run(); });
+  }
+
+  void run() {
+    for (;;) {
+      std::shared_ptr<JitEntry> e;
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [&] { return stop_ || !queue_.empty(); });
+        if (stop_) return;
+        e = queue_.front();
+        queue_.pop_front();
+      }
+      compile(*e);
+      {
+        std::lock_guard<std::mutex> lk(mu_);
+      }
+      done_cv_.notify_all();
+    }
+  }
+
+  static void compile(JitEntry& e) {
+    const auto t0 = std::chrono::steady_clock::now();
+    std::string log;
+    std::vector<char> cubin;
+    const bool ok = jit_compile_cubin(e.src, cubin, log);
+    if (ok) {
+      cudaError_t err = cudaSetDevice(e.device);
+      if (err == cudaSuccess)
+        err = cudaLibraryLoadData(&e.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+      if (err == cudaSuccess) err = cudaLibraryGetKernel(&e.kern, e.lib, "qs_pass");
+      if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(reinterpret_cast<const void*>(e.kern),
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(e.smem));
+      if (err != cudaSuccess) {
+        e.log = std::string("load: ") + cudaGetErrorString(err);
+        e.state.store(JS_FAILED);
+        return;
+      }
+      e.compile_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      e.state.store(JS_READY);
+    } else {
+      e.log = log;
+      e.state.store(JS_FAILED);
+    }
+  }
+
+  std::mutex mu_;
+  std::condition_variable cv_, done_cv_;
+  bool stop_ = false;
+  std::deque<std::shared_ptr<JitEntry>> queue_;
+  std::unordered_map<std::string, std::shared_ptr<JitEntry>> map_;
+  std::vector<std::thread> workers_;
+};
+
+}  // namespace
+
+bool jit_compile_cubin(const std::string& src, std::vector<char>& cubin, std::string& log) {
+  const int nh = jit_header_count();
+  std::vector<const char*> hdr(static_cast<size_t>(nh)), names(static_cast<size_t>(nh));
+  for (int i = 0; i < nh; ++i) {
+    hdr[size_t(i)] = jit_header_text(i);
+    names[size_t(i)] = jit_header_name(i);
+  }
+  nvrtcProgram prog;
+  if (nvrtcCreateProgram(&prog, src.c_str(), "qs_pass.cu", nh, hdr.data(), names.data()) != NVRTC_SUCCESS) {
+    log = "nvrtcCreateProgram failed";
+    return false;
+  }
+  const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-default-device", "-lineinfo"};
+  const nvrtcResult r = nvrtcCompileProgram(prog, 4, opts);
+  size_t ls = 0;
+  nvrtcGetProgramLogSize(prog, &ls);
+  if (ls > 1) {
+    log.resize(ls);
+    nvrtcGetProgramLog(prog, &log[0]);
+  }
+  bool ok = r == NVRTC_SUCCESS;
+  if (ok) {
+    size_t cs = 0;
+    ok = nvrtcGetCUBINSize(prog, &cs) == NVRTC_SUCCESS && cs > 0;
+    if (ok) {
+      cubin.resize(cs);
+      ok = nvrtcGetCUBIN(prog, cubin.data()) == NVRTC_SUCCESS;
+    }
+  } else {
+    log = std::string(nvrtcGetErrorString(r)) + ": " + log;
+  }
+  nvrtcDestroyProgram(&prog);
+  return ok;
+}
+
+bool jit_try_launch(Env& env, Reg& r, const FPass& fp, const FStage* st, const FOp* ops, Arith arith, int R,
+                    double flops, double alu, const char* name) {
+  if (env.jit == 0 || r.nq < env.jit_min_qubits || fp.init) return false;
+  if (fp.op_count <= 0 || fp.op_count > kMaxPassOps) return false;
+  const JitShape sh{arith, R, int(env.jit_ctas)};
+  std::string src;
+  try {
+    src = jit_source(fp, st, ops, sh);
+  } catch (const Error&) {
+    ++env.jit_rejected;
+    return false;
+  }
+  const size_t smem = jit_smem_bytes(fp, arith);
+  bool created = false;
+  std::shared_ptr<JitEntry> e = JitCache::get().find_or_queue(src, env.device, smem, created);
+  if (env.jit == 1 && e->state.load() == JS_QUEUED) JitCache::get().wait(e);
+  if (e->state.load() != JS_READY) return false;
+  // parameters: g, ntiles, then the pass's FOp records (constant bank)
+  void* g = r.d;
+  long long ntiles = fp.ntiles;
+  const FOp* popv = ops + fp.op_begin;
+  void* args[3] = {&g, &ntiles, const_cast<FOp*>(popv)};
+  const int threads = 1 << (fp.k - R);
+  const int64_t grid = std::min<int64_t>(fp.ntiles, int64_t(env.sms) * env.jit_ctas);
+  const double bytes = std::ldexp(2.0 * (arith == Arith::F32 ? 8.0 : 16.0), r.nq);
+  KTimer kt(env, name, bytes, flops, 1, alu);
+  QS_CUDA(cudaLaunchKernel(reinterpret_cast<const void*>(e->kern), dim3(unsigned(grid)), dim3(unsigned(threads)),
+                           args, smem, env.stream));
+  ++env.jit_launches;
+  return true;
+}
+
+JitStats jit_stats() { return JitCache::get().stats(); }
+std::string jit_first_failure() { return JitCache::get().first_failure(); }
+
+}  // namespace qs

@@ -1,0 +1,50 @@
+// Pass kernels compiled at run time for one fused pass's operation list.
+//
+// The fused tile kernel (fused_kernel.cuh) interprets a pass: every thread
+// decodes every operation (dispatch word, condition masks, pending sign
+// flips) before its arithmetic, which for complex64 costs more instructions
+// than the arithmetic itself.  A pass's structure (tile qubits, stages,
+// operation kinds, register bits, condition masks) is fixed once planned, so
+// this module writes a kernel with that structure spelled out in straight-
+// line code, compiles it with NVRTC for sm_103a and caches it by its source
+// text.  Coefficients stay kernel parameters (the pass's FOp array, read from
+// the constant bank), so a circuit rerun with other angles reuses the
+// kernels.  The arithmetic is the same inline code as the interpreter's
+// (fused_arith.cuh), applied in the same order; sign flips, which commute
+// exactly with what they are moved past, are applied where they occur.
+#pragma once
+#include <cstdint>
+#include <string>
+
+#include "fused_types.h"
+#include "plan.h"
+
+namespace qs {
+
+// Parameters of one generated pass kernel.
+struct JitShape {
+  Arith arith;
+  int R;
+  int ctas;  // resident CTAs per SM the kernel is compiled for (__launch_bounds__)
+};
+
+// CUDA source of the pass kernel `qs_pass` for pass fp of a plan whose
+// stage and op arrays are st and ops (fp's indices relative to them).
+// Kernel signature: (Store* g, long long ntiles, const __grid_constant__
+// JitOps P) with P holding fp.op_count FOp records.  Throws Error
+// (QS_E_ARG) if the pass uses a form the generator does not know.
+std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const JitShape& sh);
+
+// Bytes of the kernel's parameter block after the two scalar arguments.
+inline size_t jit_param_bytes(const FPass& fp) { return sizeof(FOp) * size_t(fp.op_count); }
+
+// Shared-memory bytes of a generated pass kernel.
+size_t jit_smem_bytes(const FPass& fp, Arith a);
+
+// Headers the generated source includes, as (name, contents) pairs embedded
+// at build time; used by the NVRTC compile.
+int jit_header_count();
+const char* jit_header_name(int i);
+const char* jit_header_text(int i);
+
+}  // namespace qs

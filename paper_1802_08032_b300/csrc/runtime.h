@@ -127,11 +127,19 @@ struct Env {
   int64_t profile = 0;
   int64_t arith = 0;         // complex128 arithmetic of fused passes: 0 = IEEE FP64, 1 = double-float
   int64_t multi_tc = 1;      // complex64 dense gates on 4-5 targets: 0 CUDA cores, 1 by shape (5 on the tensor cores), 2 tensor cores
+  // fused passes as runtime-compiled kernels (jit.cpp): 0 off, 1 compile and
+  // wait, 2 compile in the background (interpreting kernel until ready);
+  // registers of at least jit_min_qubits stored qubits; CTAs per SM
+  int64_t jit = 2;
+  int64_t jit_min_qubits = 20;
+  int64_t jit_ctas = 2;
   Profiler prof;
   // counters (readable through getEnvOption)
   int64_t launches = 0;      // kernel launches issued
   int64_t fused_passes = 0;  // fused-tile passes launched
   int64_t fused_vops = 0;    // vector operations applied by fused passes
+  int64_t jit_launches = 0;  // fused passes launched as runtime-compiled kernels
+  int64_t jit_rejected = 0;  // passes the kernel generator could not express
   // allocator hook
   void* (*alloc)(size_t, void*) = nullptr;
   void (*release)(void*, void*) = nullptr;

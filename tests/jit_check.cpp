@@ -1,0 +1,96 @@
+// Host-side check of the runtime-compiled pass kernels (test
+// infrastructure; built by tests/test_jit.py with the host compiler against
+// the library's planner, op validation and kernel generator, no GPU
+// involved).
+//
+// Reads QSOp records from stdin, plans them for a register of the given
+// shape, generates the pass kernel of every pass and compiles it with NVRTC
+// for sm_103a.  Prints "JIT passes P compiled C distinct D seconds S" and,
+// for a failure, the compiler log.  With a file name as argument 7 the
+// source of the first pass is written there.
+//
+// usage: jit_check n density prec arith k_req ctas [source_out]
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "jit.h"
+#include "jit_runtime.h"
+#include "plan.h"
+#include "runtime.h"
+
+using namespace qs;
+
+// jit.cpp's launch path (never called here) times launches with KTimer,
+// which lives in the CUDA part of the library
+namespace qs {
+KTimer::KTimer(Env& env, const char*, double, double, int, double) : env_(env) {}
+KTimer::~KTimer() {}
+}  // namespace qs
+
+int main(int argc, char** argv) {
+  if (argc < 7) {
+    std::fprintf(stderr, "usage: jit_check n density prec arith k_req ctas [source_out]\n");
+    return 2;
+  }
+  const int n = std::atoi(argv[1]), density = std::atoi(argv[2]), prec = std::atoi(argv[3]);
+  const int arith = std::atoi(argv[4]), k_req = std::atoi(argv[5]), ctas = std::atoi(argv[6]);
+  Env env;
+  env.arith = arith;
+  Reg r;
+  r.env = &env;
+  r.n = n;
+  r.density = density != 0;
+  r.nq = density ? 2 * n : n;
+  r.prec = prec;
+  r.dim = int64_t(1) << r.nq;
+  std::vector<QSOp> ops;
+  QSOp o;
+  while (std::fread(&o, sizeof(o), 1, stdin) == 1) ops.push_back(o);
+  RegPlan pl;
+  try {
+    std::vector<GateOp> g;
+    convert_ops(r, ops.data(), int64_t(ops.size()), g);
+    build_plan(r, g, k_req, (uint64_t(1) << r.nq) - 1, 1.0, pl);
+  } catch (const Error& e) {
+    std::printf("ERROR %d %s\n", e.code, e.msg.c_str());
+    return 1;
+  }
+  const int R = pl.arith == Arith::F32 ? 5 : 4;
+  std::set<std::string> distinct;
+  int compiled = 0;
+  double secs = 0;
+  for (size_t i = 0; i < pl.fps.size(); ++i) {
+    std::string src;
+    try {
+      src = jit_source(pl.fps[i], pl.fst.data(), pl.fops.data(), JitShape{pl.arith, R, ctas});
+    } catch (const Error& e) {
+      std::printf("GENFAIL pass %zu: %s\n", i, e.msg.c_str());
+      return 3;
+    }
+    if (i == 0 && argc > 7) {
+      FILE* f = std::fopen(argv[7], "w");
+      if (f) {
+        std::fputs(src.c_str(), f);
+        std::fclose(f);
+      }
+    }
+    if (!distinct.insert(src).second) continue;
+    std::vector<char> cubin;
+    std::string log;
+    const auto t0 = std::chrono::steady_clock::now();
+    const bool ok = jit_compile_cubin(src, cubin, log);
+    secs += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (!ok) {
+      std::printf("COMPILEFAIL pass %zu\n%s\n", i, log.c_str());
+      return 4;
+    }
+    ++compiled;
+  }
+  std::printf("JIT passes %zu compiled %d distinct %zu seconds %.3f\n", pl.fps.size(), compiled, distinct.size(),
+              secs);
+  return 0;
+}
