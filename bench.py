@@ -40,11 +40,7 @@ FP32_ISSUE_TINSTR = 148 * 128 * 2.032e9 / 1e12   # FP32 instructions/s at the 20
 # DRAM bytes (read + write) per amplitude per launch, from one ncu capture of
 # the kernel as built (profiles/<kernel>_*_ncu_full.md); scaled by the
 # amplitudes a launch processes.  Entries are removed when a kernel changes.
-MEASURED_TRAFFIC_PER_AMP = {
-    "fused_c128": 2.088e9 / (1 << 26),      # profiles/fused_c128_fp64_sv26_ncu_full.md
-    "fused_c128_df": 2.089e9 / (1 << 26),   # profiles/fused_c128_df_sv26_ncu_full.md
-    "fused_c64": 1.021e9 / (1 << 26),       # profiles/fused_c64_sv26_ncu_full.md
-}
+MEASURED_TRAFFIC_PER_AMP = {}
 
 
 def parse():
@@ -140,20 +136,47 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def cpu_oracle_sample(n, ops, ngates):
+def cpu_model():
+    """The host CPU's model name and logical CPU count."""
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"model": model, "nproc": os.cpu_count()}
+
+
+def cpu_oracle_sample(n, ops, ngates, one_core_gates=0):
     """Times the CPU oracle on a bounded sample: `ngates` gates spread evenly
     over the circuit, applied to an n-qubit state (allocation and |0>
-    excluded from the timing, as in the paper's methodology)."""
+    excluded from the timing, as in the paper's methodology); with
+    one_core_gates > 0 also the first that many of the sample on one host
+    thread."""
     from oracle import oracle as O
     stride = max(1, len(ops) // ngates)
     sample = ops[::stride][:ngates]
     st, secs = O.timed_run(n, sample)
     del st
-    return {"value": len(sample) / secs, "unit": "gates/s", "cores": O.num_threads(),
-            "kind": "oracle",
-            "sample": f"{len(sample)} gates (every {stride}th of the {len(ops)}-gate circuit) on a "
-                      f"{n}-qubit complex128 state vector, FP64 C oracle, OpenMP over "
-                      f"{O.num_threads()} host threads, {secs:.1f} s"}
+    out = {"value": len(sample) / secs, "unit": "gates/s", "cores": O.num_threads(),
+           "kind": "oracle", "cpu": cpu_model(),
+           "sample": f"{len(sample)} gates (every {stride}th of the {len(ops)}-gate circuit) on a "
+                     f"{n}-qubit complex128 state vector, FP64 C oracle, OpenMP over "
+                     f"{O.num_threads()} host threads, {secs:.1f} s"}
+    if one_core_gates > 0:
+        full = O.num_threads()
+        O.set_num_threads(1)
+        try:
+            st, secs1 = O.timed_run(n, sample[:one_core_gates])
+            del st
+        finally:
+            O.set_num_threads(full)
+        out["one_core"] = {"value": one_core_gates / secs1, "unit": "gates/s", "cores": 1,
+                           "sample": f"the first {one_core_gates} gates of the same sample, {secs1:.1f} s"}
+    return out
 
 
 def run_reference(args):
@@ -176,7 +199,7 @@ def run_reference(args):
             "config": {"workload": f"{n}-qubit complex128 state vector, seeded depth-40 random "
                                    "circuit (bounded CPU sample)", "qubits": n},
             "cpu_baseline": {"value": v, "unit": "gates/s", "cores": r["cores"], "kind": "oracle",
-                             "sample": r["sample"]},
+                             "sample": r["sample"], "cpu": r["cpu"]},
             "e2e": {"value": v, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "thread_scaling": oracle_thread_scaling(n - 4, C.workload_30q(n - 4), args.cpu_gates)}
     print(json.dumps(line), flush=True)
@@ -342,7 +365,9 @@ def main():
     e2e_s = max_over_ranks(time.perf_counter() - te)
 
     total_gates = ngates * args.steps * world  # = job_throughput(...) x time
-    dtype = "f32" if prec == 64 else ("df64 (f32 pairs)" if args.arith == "df" else "f64")
+    # double-float is an out-of-spec precision form (48-bit significands),
+    # never reported as complex128 arithmetic
+    dtype = "f32" if prec == 64 else ("df64 (f32 pairs, out of spec)" if args.arith == "df" else "f64")
     line = {
         "metric": "gates/s (30q random circuit)", "value": total_gates / (dev_ms / 1e3),
         "unit": "gates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -373,7 +398,7 @@ def main():
                                     (args.serve_requests, args.serve_seconds))
     if rank == 0 and world == 1:
         try:
-            line["cpu_baseline"] = cpu_oracle_sample(n, ops, args.cpu_gates)
+            line["cpu_baseline"] = cpu_oracle_sample(n, ops, args.cpu_gates, one_core_gates=6)
         except Exception as e:  # host without room for the sample
             line["cpu_baseline"] = {"value": None, "unavailable": str(e)}
     Q.destroyQuESTEnv(env)
@@ -381,6 +406,60 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+class _DeviceAmps:
+    """__cuda_array_interface__ over a register's device amplitudes (as
+    interleaved reals), so that torch can read them for error reports."""
+
+    def __init__(self, ptr, count, prec):
+        self.__cuda_array_interface__ = {
+            "shape": (2 * count,), "typestr": "<f8" if prec == 128 else "<f4",
+            "data": (ptr, False), "version": 3, "strides": None}
+
+
+def reg_view(Q, torch, q):
+    info = Q.getQuregInfo(q)
+    prec = info["precision"]
+    t = torch.as_tensor(_DeviceAmps(info["devicePtr"], info["numAmps"], prec), device="cuda")
+    return torch.view_as_complex(t.view(-1, 2))
+
+
+def c64_error(Q, torch, q64, q128, chunk=1 << 27):
+    """Error of a complex64 register against the complex128 register of the
+    same circuit run with IEEE FP64 arithmetic (which the parity tests hold
+    to the FP64 oracle at 1e-12): max |a64 - a128| over every amplitude,
+    raw overlap |<a128|a64>|^2, fidelity of the normalised states
+    |<a128|a64>|^2 / (<a128|a128> <a64|a64>) and the complex64 norm drift,
+    all reduced in FP64."""
+    ip = Q.calcInnerProduct(q128, q64)
+    n128, n64 = Q.calcTotalProb(q128), Q.calcTotalProb(q64)
+    a, b = reg_view(Q, torch, q128), reg_view(Q, torch, q64)
+    worst = 0.0
+    for i in range(0, a.numel(), chunk):
+        d = (a[i:i + chunk] - b[i:i + chunk].to(torch.complex128)).abs().max().item()
+        worst = max(worst, d)
+    raw = abs(ip) ** 2
+    fid = raw / (n128 * n64)
+    return {"max_abs_err": worst, "fidelity": fid, "one_minus_fidelity": 1.0 - fid,
+            "raw_overlap": raw, "one_minus_raw_overlap": 1.0 - raw, "norm_dev": abs(n64 - 1.0)}
+
+
+def golden_sample_error(Q, q, name="sv30_depth40.json"):
+    """max |a - a_oracle| over the sampled amplitudes the FP64 oracle wrote
+    for this workload (tests/golden), and the largest outcome-probability
+    difference; None when the file is absent."""
+    path = os.path.join(ROOT, "tests", "golden", name)
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        g = json.load(f)
+    worst = 0.0
+    for i, (re, im) in zip(g["indices"], g["amps"]):
+        worst = max(worst, abs(Q.copyStateToHost(q, int(i), 1)[0] - complex(re, im)))
+    pw = max(abs(Q.calcProbOfOutcome(q, k, 1) - p) for k, p in enumerate(g["prob_outcome_1"]))
+    return {"max_abs_err_vs_fp64_oracle": worst, "amplitudes": len(g["indices"]),
+            "max_prob_err_vs_fp64_oracle": pw, "total_prob_err": abs(Q.calcTotalProb(q) - g["total_prob"])}
 
 
 def timed(torch, stream, fn, reps):
@@ -407,7 +486,10 @@ def variants(Q, env, torch, stream, only=(), qubits=30, serve=(60, 0.0)):
     out = {}
     ops = C.workload_30q(30)
 
-    def sv(prec, arith, n=30, reps=2):
+    def sv(prec, arith, n=30, reps=2, ref=None):
+        """One circuit variant; with ref (a complex128 register holding the
+        same circuit's IEEE-FP64 result) a complex64 run also states its
+        error and fidelity against it."""
         def run_variant():
             circ = ops if n == 30 else C.workload_30q(n)
             Q.setEnvOption(env, "arith", arith)
@@ -420,12 +502,50 @@ def variants(Q, env, torch, stream, only=(), qubits=30, serve=(60, 0.0)):
 
             try:
                 ms = timed(torch, stream, run, reps)
+                res = {"qubits": n, "gates": len(circ), "gates_per_s": len(circ) / ms * 1e3,
+                       "ms_per_circuit": ms}
+                if prec == 64 and ref is not None and ref.get("q") is not None:
+                    res["error_vs_fp64"] = c64_error(Q, torch, q, ref["q"])
+                if n == 30:
+                    g = golden_sample_error(Q, q)
+                    if g is not None:
+                        res["error_vs_fp64_oracle_sample"] = g
             finally:
                 Q.destroyQureg(q)
                 Q.setEnvOption(env, "arith", 0)
+            if arith == 1:
+                res["precision"] = ("double-float (float pairs, 48-bit significands): an out-of-spec "
+                                    "form, not complex128 arithmetic; complex128 storage")
+            return res
+        return run_variant
+
+    def fp64_reference(n, keep):
+        """Runs the n-qubit workload in complex128 (IEEE FP64) and keeps the
+        register in keep["q"] as the reference of the complex64 variant; with
+        n = 33 the run is timed as the sv33_c128 variant."""
+        def run_variant():
+            circ = ops if n == 30 else C.workload_30q(n)
+            q = Q.createQureg(n, 128, env)
+            keep["q"] = q
+
+            def run():
+                Q.initZeroState(q)
+                Q.applyCircuit(q, circ)
+                Q.calcTotalProb(q)
+
+            ms = timed(torch, stream, run, 1)
             return {"qubits": n, "gates": len(circ), "gates_per_s": len(circ) / ms * 1e3,
                     "ms_per_circuit": ms}
         return run_variant
+
+    def release(keep):
+        def run_variant():
+            if keep.get("q") is not None:
+                Q.destroyQureg(keep.pop("q"))
+            return None
+        return run_variant
+
+    ref30, ref33 = {}, {}
 
     def sweep(n, targets):
         # single-gate passes (fusion off) on an n-qubit register, GB/s by
@@ -511,8 +631,11 @@ def variants(Q, env, torch, stream, only=(), qubits=30, serve=(60, 0.0)):
         return {"qubits": 12, "gates": ops12[1], "us_per_circuit": us,
                 "gates_per_s": ops12[1] / us * 1e6, "circuits_per_s": 1e6 / us}
 
-    for name, fn in (("sv12_c128", sv12), ("sv30_c64", sv(64, 0)), ("sv30_c128_df", sv(128, 1)),
-                     ("sv33_c128", sv(128, 0, 33, 1)), ("sv33_c64", sv(64, 0, 33)),
+    for name, fn in (("sv12_c128", sv12), ("_ref30", fp64_reference(30, ref30)),
+                     ("sv30_c64", sv(64, 0, ref=ref30)), ("_rel30", release(ref30)),
+                     ("sv30_df64_out_of_spec", sv(128, 1)),
+                     ("sv33_c128", fp64_reference(33, ref33)), ("sv33_c64", sv(64, 0, 33, ref=ref33)),
+                     ("_rel33", release(ref33)),
                      ("single_gate_sweep", lambda: sweep(30, range(30))),
                      ("single_gate_sweep_33q", lambda: sweep(33, range(33))),
                      ("dm14_c128", dm14),
@@ -522,12 +645,20 @@ def variants(Q, env, torch, stream, only=(), qubits=30, serve=(60, 0.0)):
                      # registers measured up to 15 % slower in latency-bound passes
                      ("serving", lambda: serve_sweep(Q, env, [10, 30, 100, 300, 1000, 2000], serve[0],
                                                      baseline_rates=(10, 100), seconds=serve[1]))):
-        if only and name not in only:
+        # the "_" entries keep / release the FP64 reference registers of
+        # the sv<n> variants: they run when any sv<n>_ variant is wanted
+        if only and name not in only and not (
+                name.startswith("_") and any(o.startswith("sv" + name[4:] + "_") for o in only)):
             continue
         try:
-            out[name] = fn()
+            r = fn()
+            if not name.startswith("_"):
+                out[name] = r
         except Exception as e:
             out[name] = {"error": str(e)}
+    for keep in (ref30, ref33):
+        if keep.get("q") is not None:
+            Q.destroyQureg(keep.pop("q"))
     return out
 
 
@@ -537,13 +668,14 @@ def batch_variant(Q, env, torch, stream, count=4096, depth=30):
     (seed 4096 + i), advanced together by one graph replay of the batched
     engine with an autotuned tile size.  Compared with running the same
     circuits one at a time through the unfused complex128 path (timed on a
-    subset), and checked against the FP64 oracle on sampled registers."""
+    subset).  Every register's error and fidelity is stated against the same
+    circuit run with IEEE FP64 arithmetic (a complex128 batch, which the
+    parity tests hold to the FP64 oracle at 1e-12)."""
     import numpy as np
-    from oracle import oracle as O
     rng = C.SplitMix64(4096)
     sizes = [8 + rng.below(13) for _ in range(count)]
     circs = [C.random_circuit(n, depth, 4096 + i) for i, n in enumerate(sizes)]
-    regs = []
+    regs, regs128 = [], []
     try:
         for n, ops in zip(sizes, circs):
             q = Q.createQureg(n, 64, env)
@@ -554,18 +686,22 @@ def batch_variant(Q, env, torch, stream, count=4096, depth=30):
         ms = timed(torch, stream, lambda: Q.runBatch(b), 3)
         info = Q.getBatchInfo(b)
         norms = Q.getBatchNorms(b)
-        worst_err, worst_infid, worst_raw = 0.0, 0.0, 0.0
-        for i in range(0, count, count // 16):
-            got = Q.copyStateToHost(regs[i])
-            ref = O.run_circuit(sizes[i], circs[i])
-            worst_err = max(worst_err, float(np.max(np.abs(got - ref.a))))
-            ov = abs(np.vdot(ref.a, got)) ** 2
-            worst_raw = max(worst_raw, 1.0 - ov)                        # includes norm drift
-            worst_infid = max(worst_infid, 1.0 - ov / np.vdot(got, got).real)  # normalised state
+        for n, ops in zip(sizes, circs):
+            q = Q.createQureg(n, 128, env)
+            Q.applyCircuit(q, ops)
+            regs128.append(q)
+        b128 = Q.createBatch(env, regs128)
+        Q.runBatch(b128)
+        Q.syncQuESTEnv(env)
+        errs = [c64_error(Q, torch, regs[i], regs128[i]) for i in range(count)]
+        Q.destroyBatch(b128)
         Q.destroyBatch(b)
     finally:
-        for q in regs:
+        for q in regs + regs128:
             Q.destroyQureg(q)
+    maxerr = np.array([e["max_abs_err"] for e in errs])
+    infid = np.array([e["one_minus_fidelity"] for e in errs])
+    raw = np.array([e["one_minus_raw_overlap"] for e in errs])
     # plain per-register complex128 path (one kernel per gate), subset
     Q.setEnvOption(env, "fusion", 0)
     sub = list(range(0, count, count // 64))
@@ -590,8 +726,14 @@ def batch_variant(Q, env, torch, stream, count=4096, depth=30):
             "registers": count, "amplitudes": int(sum(1 << n for n in sizes)),
             "gates": int(sum(len(c) for c in circs)), "passes": info["passes"],
             "waves": info["waves"], "alg_GBps": info["bytes"] / ms / 1e6,
-            "max_abs_err_vs_fp64_oracle_sample16": worst_err,
-            "max_infidelity_sample16": worst_infid, "max_one_minus_raw_overlap_sample16": worst_raw,
+            "error_vs_fp64_all_registers": {
+                "registers": count,
+                "reference": "same circuits, complex128 batch, IEEE FP64 arithmetic",
+                "max_abs_err": float(maxerr.max()), "median_max_abs_err": float(np.median(maxerr)),
+                "fidelity_definition": "|<a128|a64>|^2 / (<a128|a128> <a64|a64>) (normalised states)",
+                "min_fidelity": float(1.0 - infid.max()), "max_one_minus_fidelity": float(infid.max()),
+                "max_one_minus_raw_overlap": float(raw.max()),
+                "max_norm_dev": float(max(e["norm_dev"] for e in errs))},
             "norm_max_dev": float(np.max(np.abs(norms - 1))),
             "plain_c128_circuits_per_s": len(sub) / ms_plain * 1e3,
             "plain_c128_subset": f"{len(sub)} of the same registers, one at a time, one kernel per gate"}
@@ -679,9 +821,11 @@ def serve_trace(rate, count, seed0=5000, arrival_seed=55, max_sv=28, max_dm=13):
     return trace
 
 
-def run_trace(Q, env, trace, slots, fusion, force_c128=False):
+def run_trace(Q, env, trace, slots, fusion, force_c128=False, capture=None):
     """Submits each request at its arrival time, collects every result;
-    returns latency percentiles and throughput."""
+    returns latency percentiles and throughput.  capture: optional dict
+    {request index: None}; those requests return their full final state
+    (filled in place)."""
     import numpy as np
     srv = Q.serveCreate(env, slots=slots, budgetBytes=150 * 10 ** 9, fusion=fusion)
     prepared = [(t, dens, n, 128 if force_c128 else prec, Q.to_qsops(ops))
@@ -689,11 +833,14 @@ def run_trace(Q, env, trace, slots, fusion, force_c128=False):
     tickets = []
     try:
         t0 = time.perf_counter()
-        for (t, dens, n, prec, qs) in prepared:
+        for i, (t, dens, n, prec, qs) in enumerate(prepared):
             wait = t - (time.perf_counter() - t0)
             if wait > 0:
                 time.sleep(wait)
-            tickets.append(Q.serveSubmit(srv, qs, n, prec, dens))
+            out = None
+            if capture is not None and i in capture:
+                out = capture[i] = np.zeros(1 << (2 * n if dens else n), dtype=np.complex128)
+            tickets.append(Q.serveSubmit(srv, qs, n, prec, dens, outAmps=out))
         res = [Q.servePoll(srv, tk, timeoutUs=600_000_000) for tk in tickets]
         wall = time.perf_counter() - t0
     finally:
@@ -706,6 +853,34 @@ def run_trace(Q, env, trace, slots, fusion, force_c128=False):
             "slots_used": len({r["slot"] for r in res})}
 
 
+def served_c64_error(Q, env, trace, captured):
+    """Per captured complex64 request: max |a64 - a128|, the normalised
+    fidelity and the raw overlap against the same circuit run with IEEE FP64
+    arithmetic in a complex128 register (held to the FP64 oracle at 1e-12 by
+    the parity tests).  Returns the worst over the sample."""
+    import numpy as np
+    rows = []
+    for i, got in captured.items():
+        if got is None:
+            continue
+        _, _, n, _, ops = trace[i]
+        q = Q.createQureg(n, 128, env)
+        try:
+            Q.applyCircuit(q, ops)
+            ref = Q.copyStateToHost(q)
+        finally:
+            Q.destroyQureg(q)
+        ip = np.vdot(ref, got)
+        n_ref, n_got = np.vdot(ref, ref).real, np.vdot(got, got).real
+        rows.append((float(np.max(np.abs(got - ref))), 1.0 - abs(ip) ** 2 / (n_ref * n_got),
+                     1.0 - abs(ip) ** 2))
+    if not rows:
+        return None
+    return {"requests": len(rows), "max_abs_err": max(r[0] for r in rows),
+            "max_one_minus_fidelity": max(r[1] for r in rows),
+            "max_one_minus_raw_overlap": max(r[2] for r in rows)}
+
+
 def serve_sweep(Q, env, rates, per_rate, slots=16, baseline_rates=(), seconds=0.0):
     """Per arrival rate: `per_rate` requests, or fewer if `seconds` > 0 caps
     the trace at that many seconds of arrivals (rate x seconds requests)."""
@@ -713,7 +888,12 @@ def serve_sweep(Q, env, rates, per_rate, slots=16, baseline_rates=(), seconds=0.
     for rate in rates:
         count = per_rate if seconds <= 0 else max(1, min(per_rate, int(rate * seconds)))
         trace = serve_trace(rate, count)
-        row = {"served": run_trace(Q, env, trace, slots, 1)}
+        # complex64 state-vector requests of up to 22 qubits return their
+        # states: error and fidelity against the same circuit in IEEE FP64
+        cap = {i: None for i, (_, dens, n, prec, _) in enumerate(trace) if not dens and prec == 64 and n <= 22}
+        cap = dict(list(cap.items())[:12])
+        row = {"served": run_trace(Q, env, trace, slots, 1, capture=cap)}
+        row["served"]["c64_error_vs_fp64"] = served_c64_error(Q, env, trace, cap)
         if rate in baseline_rates:
             row["plain_c128_one_at_a_time"] = run_trace(Q, env, trace, 1, 0, force_c128=True)
         out[f"{rate}_req_per_s"] = row

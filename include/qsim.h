@@ -112,11 +112,16 @@ int qsDiagBoundedWait(QuESTEnv env, int timeoutUs);
  *   "max_fused_ops" cap on operations per fused pass (0 = automatic)
  *   "budget_bytes"  cap on the register memory of this env (0 = none)
  *   "arith"         complex128 arithmetic of fused passes and multi-target
- *                   passes: 0 = IEEE FP64 (default), 1 = double-float (each
- *                   real a float pair hi + lo on the FP32 pipes; a few units
- *                   of 2^-48 of error per update instead of 2^-53; a
- *                   multi-target pass on m targets up to 2^m units of 2^-48
- *                   of the norm).  Single-gate passes, reductions and
+ *                   passes: 0 = IEEE FP64 (default), 1 = double-float, an
+ *                   OUT-OF-SPEC precision form, not complex128 arithmetic:
+ *                   each real is a float pair hi + lo on the FP32 pipes (a
+ *                   48-bit significand: a few units of 2^-48 of error per
+ *                   update instead of 2^-53; a multi-target pass on m
+ *                   targets up to 2^m units of 2^-48 of the norm).  Storage
+ *                   stays complex128 and amplitudes meet the 1e-12 bar, but
+ *                   FP64-reduced probabilities after long circuits drift by
+ *                   up to ~5e-13 (30 qubits, 1259 gates), outside the 1e-13
+ *                   complex128 bar.  Single-gate passes, reductions and
  *                   measurement always use FP64.
  *   "profile"       1 = time every kernel launch with CUDA events (see
  *                   getKernelStats), 0 = off (default)
@@ -238,6 +243,18 @@ int calcProbOfOutcome(Qureg q, int qubit, int outcome, double *out);
 int collapseToOutcome(Qureg q, int qubit, int outcome, double *probOut);
 /* calcPurity: Tr(rho^2) = sum_n |rho'_n|^2 of a density matrix. */
 int calcPurity(Qureg q, double *out);
+/* calcInnerProduct: <bra|ket> = sum_j conj(bra_j) ket_j, accumulated in FP64
+ * (complex64 amplitudes widened first), for two state vectors of the same
+ * qubit count and either precision (QuEST's API call of this name; the
+ * paper's Sec. III lists the API's measurement calls).  Both registers'
+ * queued gates are applied first; the reduction runs on bra's environment
+ * stream after ket's environment stream is synchronised.  Errors:
+ * QS_E_NOT_DENSITY for a density matrix, QS_E_QUBIT for unequal sizes. */
+int calcInnerProduct(Qureg bra, Qureg ket, Complex *out);
+/* calcFidelity: |<a|b>|^2 of two state vectors (as calcInnerProduct; no
+ * renormalisation: divide by both calcTotalProb for the fidelity of the
+ * normalised states). */
+int calcFidelity(Qureg a, Qureg b, double *out);
 
 /* ------------------------------------------------------------ bulk calls */
 /* One operation of a gate list; the same operations as the calls above. */

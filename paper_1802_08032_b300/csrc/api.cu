@@ -680,6 +680,30 @@ int calcPurity(Qureg q, double* out) {
   });
 }
 
+int calcInnerProduct(Qureg bra, Qureg ket, Complex* out) {
+  return guarded([&] {
+    need(out, "out");
+    Reg& a = reg_of(bra);
+    Reg& b = reg_of(ket);
+    if (a.density || b.density) fail(QS_E_NOT_DENSITY, "inner product of state vectors only");
+    if (a.n != b.n) fail(QS_E_QUBIT, "registers of different sizes");
+    const std::complex<double> z = reduce_inner(*a.env, a, b);
+    out->re = z.real();
+    out->im = z.imag();
+  });
+}
+
+int calcFidelity(Qureg a, Qureg b, double* out) {
+  return guarded([&] {
+    need(out, "out");
+    Reg& ra = reg_of(a);
+    Reg& rb = reg_of(b);
+    if (ra.density || rb.density) fail(QS_E_NOT_DENSITY, "fidelity of state vectors only");
+    if (ra.n != rb.n) fail(QS_E_QUBIT, "registers of different sizes");
+    *out = std::norm(reduce_inner(*ra.env, ra, rb));
+  });
+}
+
 int getKernelStats(QuESTEnv e, QSKernelStat* out, int maxOut, int* count) {
   return guarded([&] {
     Env& env = env_of(e);

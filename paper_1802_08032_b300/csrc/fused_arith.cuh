@@ -108,8 +108,10 @@ struct PlainArith {
   __device__ static Cplx phase(const Cplx& v, const FOp& op) {
     const R c = cf(op, 0), s = cf(op, 1);
     Cplx w;
-    w.x = c * v.x - s * v.y;
-    w.y = s * v.x + c * v.y;
+    // explicit FMAs: the same rounding wherever this is compiled (the
+    // interpreting kernel and the runtime-compiled ones)
+    w.x = fma(c, v.x, -(s * v.y));
+    w.y = fma(s, v.x, c * v.y);
     return w;
   }
   // FP64: flip the sign bits (integer pipe; the FP64 pipe is the bottleneck).

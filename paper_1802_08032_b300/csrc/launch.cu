@@ -651,6 +651,38 @@ void queue_outcome(Env& env, Reg& r, int q, int o, double* out) {
   check_launch();
 }
 
+namespace {
+template <typename RA, typename RB>
+void inner(Env& env, const Reg& a, const Reg& b, double* out) {
+  const int blocks = int(std::max<int64_t>(
+      1, std::min<int64_t>(kRedMaxBlocks, (a.dim + kRedThreads * 4 - 1) / (kRedThreads * 4))));
+  KTimer kt(env, "reduce_inner", double(a.dim) * (amp_bytes<RA>() + amp_bytes<RB>()), double(a.dim) * 8, 3);
+  k_inner<RA, RB, 4><<<blocks, kRedThreads, 0, env.stream>>>(static_cast<const cvec<RA>*>(a.d),
+                                                            static_cast<const cvec<RB>*>(b.d), a.dim,
+                                                            env.d_partial);
+  k_sum_partials<<<1, 1024, 0, env.stream>>>(env.d_partial, blocks, out);
+  k_sum_partials<<<1, 1024, 0, env.stream>>>(env.d_partial + blocks, blocks, out + 1);
+}
+}  // namespace
+
+std::complex<double> reduce_inner(Env& env, Reg& a, Reg& b) {
+  flush(a);
+  flush(b);
+  // both registers' pending work must be done before the reduction reads
+  // them: b's env may queue on another stream
+  if (b.env != &env) QS_CUDA(cudaStreamSynchronize(b.env->stream));
+  if (a.prec == QS_C128 && b.prec == QS_C128) inner<double, double>(env, a, b, env.d_result);
+  else if (a.prec == QS_C128) inner<double, float>(env, a, b, env.d_result);
+  else if (b.prec == QS_C128) inner<float, double>(env, a, b, env.d_result);
+  else inner<float, float>(env, a, b, env.d_result);
+  check_launch();
+  QS_CUDA(cudaMemcpyAsync(env.h_result, env.d_result, 2 * sizeof(double), cudaMemcpyDeviceToHost, env.stream));
+  QS_CUDA(cudaMemcpyAsync(env.h_status, env.d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, env.stream));
+  QS_CUDA(cudaStreamSynchronize(env.stream));
+  check_status(env);
+  return {env.h_result[0], env.h_result[1]};
+}
+
 double reduce_total(Env& env, Reg& r) {
   queue_total(env, r, env.d_result);
   return fetch_result(env);

@@ -23,10 +23,13 @@ __device__ __forceinline__ void pair_apply(cvec<R>& x, cvec<R>& y, const Mat2<R>
   if constexpr (K == PK_GEN) {
     const R s = CONJ ? R(-1) : R(1);
     const R i0 = s * g.im[0], i1 = s * g.im[1], i2 = s * g.im[2], i3 = s * g.im[3];
-    x.x = g.re[0] * xr - i0 * xi + g.re[1] * yr - i1 * yi;
-    x.y = g.re[0] * xi + i0 * xr + g.re[1] * yi + i1 * yr;
-    y.x = g.re[2] * xr - i2 * xi + g.re[3] * yr - i3 * yi;
-    y.y = g.re[2] * xi + i2 * xr + g.re[3] * yi + i3 * yr;
+    // explicit FMA chains (one product rounded, three fused): the same
+    // rounding in every kernel that includes this, whatever the compiler's
+    // contraction choices
+    x.x = fma(g.re[0], xr, fma(-i0, xi, fma(g.re[1], yr, -(i1 * yi))));
+    x.y = fma(g.re[0], xi, fma(i0, xr, fma(g.re[1], yi, i1 * yr)));
+    y.x = fma(g.re[2], xr, fma(-i2, xi, fma(g.re[3], yr, -(i3 * yi))));
+    y.y = fma(g.re[2], xi, fma(i2, xr, fma(g.re[3], yi, i3 * yr)));
   } else if constexpr (K == PK_H) {
     // H = [[1, 1], [1, -1]] / sqrt(2); real, so conj(H) = H.  g.re[0] = 1/sqrt(2).
     const R s = g.re[0];

@@ -73,6 +73,48 @@ __global__ void __launch_bounds__(kRedThreads) k_sumdiag(const cvec<R>* __restri
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
+// sum over j of conj(a_j) b_j in FP64 (a and b of either precision, widened
+// first): partial[blockIdx.x] = real part, partial[gridDim.x + blockIdx.x] =
+// imaginary part.
+template <typename RA, typename RB, int UNROLL>
+__global__ void __launch_bounds__(kRedThreads) k_inner(const cvec<RA>* __restrict__ a,
+                                                       const cvec<RB>* __restrict__ b, int64_t n,
+                                                       double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const int64_t nthr = int64_t(gridDim.x) * blockDim.x;
+  double re = 0.0, im = 0.0;
+  for (int64_t base = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; base < n; base += nthr * UNROLL) {
+    cvec<RA> x[UNROLL];
+    cvec<RB> y[UNROLL];
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) {
+      const int64_t j = base + u * nthr;
+      if (j < n) {
+        x[u] = a[j];
+        y[u] = b[j];
+      } else {
+        x[u].x = RA(0); x[u].y = RA(0);
+        y[u].x = RB(0); y[u].y = RB(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UNROLL; ++u) {
+      const double ar = double(x[u].x), ai = double(x[u].y), br = double(y[u].x), bi = double(y[u].y);
+      re = fma(ar, br, re);
+      re = fma(ai, bi, re);
+      im = fma(ar, bi, im);
+      im = fma(-ai, br, im);
+    }
+  }
+  const double sr = block_sum(re, sh);
+  __syncthreads();
+  const double si = block_sum(im, sh);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = sr;
+    partial[gridDim.x + blockIdx.x] = si;
+  }
+}
+
 // Second stage: out[0] = sum of partial[0..n) in a fixed order.
 __global__ void __launch_bounds__(1024) k_sum_partials(const double* __restrict__ partial, int n,
                                                        double* __restrict__ out) {

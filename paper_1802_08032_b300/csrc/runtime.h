@@ -222,6 +222,9 @@ void queue_total(Env& env, Reg& r, double* out);
 void queue_outcome(Env& env, Reg& r, int q, int o, double* out);
 double reduce_outcome(Env& env, Reg& r, int q, int o);
 double reduce_purity(Env& env, Reg& r);
+// <a|b> = sum_j conj(a_j) b_j in FP64 (state vectors of equal size, any
+// precisions), on a's env stream; flushes both.
+std::complex<double> reduce_inner(Env& env, Reg& a, Reg& b);
 void launch_collapse(Env& env, Reg& r, int q, int o, double scale);
 void launch_fill(Env& env, Reg& r, double re, double im);
 // Multiplies every amplitude by f (settles Reg::pend_scale).

@@ -139,6 +139,8 @@ SIGNATURES = {
     "calcProbOfOutcome": [Qureg, _I, _I, _P(_D)],
     "collapseToOutcome": [Qureg, _I, _I, _P(_D)],
     "calcPurity": [Qureg, _P(_D)],
+    "calcInnerProduct": [Qureg, Qureg, _P(Complex)],
+    "calcFidelity": [Qureg, Qureg, _P(_D)],
     "applyCircuit": [Qureg, _P(QSOp), _I64],
     "getKernelStats": [QuESTEnv, _P(QSKernelStat), _I, _P(_I)],
     "resetKernelStats": [QuESTEnv],
@@ -417,6 +419,18 @@ def collapseToOutcome(q, qubit, outcome) -> float:
     v = ctypes.c_double()
     _check(LIB.collapseToOutcome(q, qubit, outcome, ctypes.byref(v)))
     return v.value
+
+
+def calcInnerProduct(bra, ket) -> complex:
+    out = Complex()
+    _check(LIB.calcInnerProduct(bra, ket, ctypes.byref(out)))
+    return complex(out.re, out.im)
+
+
+def calcFidelity(a, b) -> float:
+    out = ctypes.c_double()
+    _check(LIB.calcFidelity(a, b, ctypes.byref(out)))
+    return out.value
 
 
 def calcPurity(q) -> float:

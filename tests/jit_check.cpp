@@ -6,15 +6,18 @@
 // Reads QSOp records from stdin, plans them for a register of the given
 // shape, generates the pass kernel of every pass and compiles it with NVRTC
 // for sm_103a.  Prints "JIT passes P compiled C distinct D seconds S" and,
-// for a failure, the compiler log.  With a file name as argument 7 the
-// source of the first pass is written there.
+// for a failure, the compiler log.  Argument 7 caps how many distinct
+// kernels are compiled (all are generated); with a file name as argument 8
+// the source of the first pass is written there.  Compiles run on up to 8
+// host threads.
 //
-// usage: jit_check n density prec arith k_req ctas [source_out]
+// usage: jit_check n density prec arith k_req ctas [max_compile [source_out]]
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
 #include <set>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "jit.h"
@@ -60,9 +63,9 @@ int main(int argc, char** argv) {
     return 1;
   }
   const int R = pl.arith == Arith::F32 ? 5 : 4;
+  const int max_compile = argc > 7 ? std::atoi(argv[7]) : 1 << 30;
   std::set<std::string> distinct;
-  int compiled = 0;
-  double secs = 0;
+  std::vector<std::string> todo;
   for (size_t i = 0; i < pl.fps.size(); ++i) {
     std::string src;
     try {
@@ -71,21 +74,33 @@ int main(int argc, char** argv) {
       std::printf("GENFAIL pass %zu: %s\n", i, e.msg.c_str());
       return 3;
     }
-    if (i == 0 && argc > 7) {
-      FILE* f = std::fopen(argv[7], "w");
+    if (i == 0 && argc > 8) {
+      FILE* f = std::fopen(argv[8], "w");
       if (f) {
         std::fputs(src.c_str(), f);
         std::fclose(f);
       }
     }
-    if (!distinct.insert(src).second) continue;
-    std::vector<char> cubin;
-    std::string log;
-    const auto t0 = std::chrono::steady_clock::now();
-    const bool ok = jit_compile_cubin(src, cubin, log);
-    secs += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    if (!ok) {
-      std::printf("COMPILEFAIL pass %zu\n%s\n", i, log.c_str());
+    if (distinct.insert(src).second && int(todo.size()) < max_compile) todo.push_back(src);
+  }
+  std::vector<int> ok(todo.size(), 0);
+  std::vector<std::string> logs(todo.size());
+  std::vector<std::thread> th;
+  const auto t0 = std::chrono::steady_clock::now();
+  const size_t nth = std::min<size_t>(8, todo.size());
+  for (size_t w = 0; w < nth; ++w)
+    th.emplace_back([&, w] {
+      for (size_t i = w; i < todo.size(); i += nth) {
+        std::vector<char> cubin;
+        ok[i] = jit_compile_cubin(todo[i], cubin, logs[i]) ? 1 : 0;
+      }
+    });
+  for (std::thread& t : th) t.join();
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  int compiled = 0;
+  for (size_t i = 0; i < todo.size(); ++i) {
+    if (!ok[i]) {
+      std::printf("COMPILEFAIL kernel %zu\n%s\n", i, logs[i].c_str());
       return 4;
     }
     ++compiled;
