@@ -59,6 +59,7 @@ def parse():
                     help="serving variant: also cap each rate's trace at this many seconds of arrivals "
                          "(0 = no cap); 2000 and 60 give the full-length sweep")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg (profiling runs)")
     ap.add_argument("--jit", type=int, default=1, choices=[0, 1, 2],
                     help="fused passes: 0 interpreting kernel, 1 runtime-compiled kernels "
                          "(compiled in the warm-up), 2 compiled in the background")
@@ -396,7 +397,7 @@ def main():
         line["variants"] = variants(Q, env, torch, stream,
                                     [v for v in args.variants.split(",") if v], n,
                                     (args.serve_requests, args.serve_seconds))
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_cpu:
         try:
             line["cpu_baseline"] = cpu_oracle_sample(n, ops, args.cpu_gates, one_core_gates=6)
         except Exception as e:  # host without room for the sample
@@ -421,7 +422,8 @@ class _DeviceAmps:
 def reg_view(Q, torch, q):
     info = Q.getQuregInfo(q)
     prec = info["precision"]
-    t = torch.as_tensor(_DeviceAmps(info["devicePtr"], info["numAmps"], prec), device="cuda")
+    count = 1 << (info["numQubits"] * (2 if info["isDensity"] else 1))
+    t = torch.as_tensor(_DeviceAmps(info["devicePtr"], count, prec), device="cuda")
     return torch.view_as_complex(t.view(-1, 2))
 
 
@@ -682,7 +684,10 @@ def batch_variant(Q, env, torch, stream, count=4096, depth=30):
             Q.applyCircuit(q, ops)
             regs.append(q)
         b = Q.createBatch(env, regs)
-        k = Q.tuneBatch(b, [9, 10, 11, 12, 13], replays=1)
+        # tile size and fusion depth tuned together (tiles below 10 act as 10
+        # on registers of 10 or more qubits: a complex64 tile holds at least
+        # 2^(R + 5) amplitudes, R = 5)
+        k, depth = Q.tuneBatchJoint(b, [8, 10, 11, 12, 13], [0, 32, 64, 128], replays=1)
         ms = timed(torch, stream, lambda: Q.runBatch(b), 3)
         info = Q.getBatchInfo(b)
         norms = Q.getBatchNorms(b)
@@ -723,6 +728,8 @@ def batch_variant(Q, env, torch, stream, count=4096, depth=30):
     finally:
         Q.setEnvOption(env, "fusion", 1)
     return {"circuits_per_s": count / ms * 1e3, "ms_per_batch": ms, "tile_qubits": k,
+            "fusion_depth": depth or "planner default (256 ops per pass)",
+            "tuned_over": {"tile_qubits": [8, 10, 11, 12, 13], "fusion_depth": [0, 32, 64, 128]},
             "registers": count, "amplitudes": int(sum(1 << n for n in sizes)),
             "gates": int(sum(len(c) for c in circs)), "passes": info["passes"],
             "waves": info["waves"], "alg_GBps": info["bytes"] / ms / 1e6,

@@ -133,6 +133,21 @@ int qsDiagBoundedWait(QuESTEnv env, int timeoutUs);
  *                   tensor cores, 4 on the CUDA cores (paired FP32 FMAs,
  *                   faster there; through shared-memory tiles when a target
  *                   is below qubit 5)
+ *   "jit"           fused passes of registers of at least "jit_min_qubits"
+ *                   stored qubits (default 20) as kernels generated for the
+ *                   pass and compiled at run time (NVRTC, sm_103a), cached
+ *                   for the process by the pass's structure (coefficients
+ *                   are kernel parameters, so other angles reuse them):
+ *                   0 = never (the interpreting fused kernel), 1 = compile
+ *                   on first use and wait, 2 = compile in the background and
+ *                   use the interpreting kernel until ready (default).  Both
+ *                   kernels give bit-identical amplitudes.  Applies to
+ *                   complex64 and double-float passes; IEEE-FP64 passes
+ *                   only with "jit_fp64" = 1.  "jit_ctas": resident CTAs per
+ *                   SM the generated kernels are built for (1..4, default 2).
+ *                   Read-only counters: "jit_launches", "jit_rejected",
+ *                   "jit_ready", "jit_pending", "jit_failed",
+ *                   "jit_compile_ms".
  * Unknown keys give QS_E_ARG. */
 int setEnvOption(QuESTEnv env, const char *key, int64_t value);
 /* getEnvOption: reads an option back, or a counter of the env:
@@ -306,6 +321,13 @@ int applyCircuit(Qureg q, const QSOp *ops, int64_t numOps);
  *   algorithmic bytes and flops of one replay (any pointer may be null).
  * tuneBatch: autotuner: re-plans and times `replays` replays for every
  *   candidate tile size (5..13), keeps the fastest; writes it to *chosen.
+ *   A tile has at least 2^(R+5) amplitudes where the register has as many
+ *   (R = 5 register bits for QS_C64, 4 for QS_C128), so candidates below
+ *   R + 5 act as R + 5 on such registers and as the register itself on
+ *   smaller ones.
+ * tuneBatchJoint: the same over every pair of a candidate tile size and a
+ *   candidate fusion depth (the cap on operations per fused pass, 0 = the
+ *   planner's default, else 1..256); writes the fastest pair.
  * destroyBatch: frees the batch (not the registers). */
 typedef struct { int64_t id; } QSBatch;
 int createBatch(QuESTEnv env, const Qureg *regs, int count, int tileQubits, QSBatch *out);
@@ -314,6 +336,8 @@ int getBatchNorms(QSBatch batch, double *out);
 int getBatchInfo(QSBatch batch, int *tileQubits, int64_t *passes, int *waves, double *bytes,
                  double *flops);
 int tuneBatch(QSBatch batch, const int *candidates, int numCandidates, int replays, int *chosen);
+int tuneBatchJoint(QSBatch batch, const int *tileCandidates, int numTile, const int *depthCandidates,
+                   int numDepth, int replays, int *chosenTile, int *chosenDepth);
 int destroyBatch(QSBatch batch);
 
 /* ------------------------------------------------------------- serving */

@@ -315,6 +315,9 @@ int setEnvOption(QuESTEnv e, const char* key, int64_t value) {
     } else if (k == "jit_min_qubits") {
       if (value < 1 || value > 64) fail(QS_E_ARG, "jit_min_qubits must be in 1..64");
       env.jit_min_qubits = value;
+    } else if (k == "jit_fp64") {
+      if (value != 0 && value != 1) fail(QS_E_ARG, "jit_fp64 must be 0 or 1");
+      env.jit_fp64 = value;
     } else if (k == "jit_ctas") {
       if (value < 1 || value > 4) fail(QS_E_ARG, "jit_ctas must be in 1..4");
       env.jit_ctas = value;
@@ -341,6 +344,7 @@ int getEnvOption(QuESTEnv e, const char* key, int64_t* value) {
     else if (k == "jit") *value = env.jit;
     else if (k == "jit_min_qubits") *value = env.jit_min_qubits;
     else if (k == "jit_ctas") *value = env.jit_ctas;
+    else if (k == "jit_fp64") *value = env.jit_fp64;
     else if (k == "jit_launches") *value = env.jit_launches;
     else if (k == "jit_rejected") *value = env.jit_rejected;
     else if (k == "jit_ready") *value = jit_stats().ready;

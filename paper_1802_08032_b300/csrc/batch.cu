@@ -78,6 +78,7 @@ struct Batch {
   int prec = QS_C64;
   Arith arith = Arith::F32;
   int k_req = 0;
+  int max_ops = 0;  // cap on operations per fused pass (0 = the planner's default)
   // device data of the current plan
   FPass* d_passes = nullptr;
   FOp* d_ops = nullptr;
@@ -153,6 +154,13 @@ void build(Batch& b) {
   Env& env = *b.env;
   std::vector<RegPlan> plans(b.regs.size());
   size_t maxp = 0;
+  // the batch's own fusion depth for its plans (the env's option otherwise)
+  struct DepthScope {
+    Env& e;
+    int64_t saved;
+    DepthScope(Env& env_, int64_t d) : e(env_), saved(env_.max_fused_ops) { e.max_fused_ops = d; }
+    ~DepthScope() { e.max_fused_ops = saved; }
+  } depth_scope(env, b.max_ops > 0 ? b.max_ops : env.max_fused_ops);
   for (size_t r = 0; r < b.regs.size(); ++r) {
     // every replay starts from |0...0> (the first pass generates it)
     const int nq = b.regs[r]->nq;
@@ -404,6 +412,63 @@ int tuneBatch(QSBatch h, const int* candidates, int numCandidates, int replays, 
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (chosen) *chosen = best_k;
+  });
+}
+
+int tuneBatchJoint(QSBatch h, const int* tileCandidates, int numTile, const int* depthCandidates, int numDepth,
+                   int replays, int* chosenTile, int* chosenDepth) {
+  return guarded_call([&] {
+    Batch& b = batch_of(h);
+    if (!tileCandidates || numTile < 1 || !depthCandidates || numDepth < 1)
+      fail(QS_E_ARG, "no candidates");
+    if (replays < 1) fail(QS_E_ARG, "replays must be >= 1");
+    for (int i = 0; i < numTile; ++i)
+      if (tileCandidates[i] < 5 || tileCandidates[i] > 13) fail(QS_E_ARG, "candidate tile sizes must be 5..13");
+    for (int i = 0; i < numDepth; ++i)
+      if (depthCandidates[i] < 0 || depthCandidates[i] > kMaxPassOps)
+        fail(QS_E_ARG, "candidate depths must be 0 (default) or 1.." + std::to_string(kMaxPassOps));
+    Env& env = *b.env;
+    cudaEvent_t e0, e1;
+    QS_CUDA(cudaEventCreate(&e0));
+    QS_CUDA(cudaEventCreate(&e1));
+    const int64_t prof = env.profile;
+    env.profile = 0;
+    float best = 1e30f;
+    int best_k = b.k_req, best_d = b.max_ops;
+    try {
+      for (int i = 0; i < numTile; ++i) {
+        for (int j = 0; j < numDepth; ++j) {
+          b.k_req = tileCandidates[i];
+          b.max_ops = depthCandidates[j];
+          build(b);
+          QS_CUDA(cudaGraphLaunch(b.exec, env.stream));  // warm-up
+          QS_CUDA(cudaEventRecord(e0, env.stream));
+          for (int r = 0; r < replays; ++r) QS_CUDA(cudaGraphLaunch(b.exec, env.stream));
+          QS_CUDA(cudaEventRecord(e1, env.stream));
+          QS_CUDA(cudaEventSynchronize(e1));
+          float ms = 0;
+          QS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          if (ms < best) {
+            best = ms;
+            best_k = b.k_req;
+            best_d = b.max_ops;
+          }
+        }
+      }
+      b.k_req = best_k;
+      b.max_ops = best_d;
+      build(b);
+    } catch (...) {
+      env.profile = prof;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      throw;
+    }
+    env.profile = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (chosenTile) *chosenTile = best_k;
+    if (chosenDepth) *chosenDepth = best_d;
   });
 }
 

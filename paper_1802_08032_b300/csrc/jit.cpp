@@ -220,6 +220,7 @@ bool jit_compile_cubin(const std::string& src, std::vector<char>& cubin, std::st
 bool jit_try_launch(Env& env, Reg& r, const FPass& fp, const FStage* st, const FOp* ops, Arith arith, int R,
                     double flops, double alu, const char* name) {
   if (env.jit == 0 || r.nq < env.jit_min_qubits || fp.init) return false;
+  if (arith == Arith::F64 && env.jit_fp64 == 0) return false;
   if (fp.op_count <= 0 || fp.op_count > kMaxPassOps) return false;
   const JitShape sh{arith, R, int(env.jit_ctas)};
   std::string src;

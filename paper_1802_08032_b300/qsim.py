@@ -152,6 +152,7 @@ EXTRA_SIGNATURES: dict = {
     "getBatchNorms": [QSBatch, _P(_D)],
     "getBatchInfo": [QSBatch, _P(_I), _P(_I64), _P(_I), _P(_D), _P(_D)],
     "tuneBatch": [QSBatch, _P(_I), _I, _I, _P(_I)],
+    "tuneBatchJoint": [QSBatch, _P(_I), _I, _P(_I), _I, _I, _P(_I), _P(_I)],
     "destroyBatch": [QSBatch],
     "serveCreate": [QuESTEnv, _I, _I64, _I, _P(QSServer)],
     "serveSubmit": [QSServer, _P(QSRequest), _P(_I64)],
@@ -534,6 +535,14 @@ def tuneBatch(b, candidates, replays: int = 2) -> int:
     c = ctypes.c_int()
     _check(LIB.tuneBatch(b, arr, n, int(replays), ctypes.byref(c)))
     return c.value
+
+
+def tuneBatchJoint(b, tiles, depths, replays: int = 1):
+    """Times every (tile size, fusion depth) pair; returns the fastest."""
+    ta, da = _ints(tiles), _ints(depths)
+    ck, cd = ctypes.c_int(), ctypes.c_int()
+    _check(LIB.tuneBatchJoint(b, ta[0], ta[1], da[0], da[1], int(replays), ctypes.byref(ck), ctypes.byref(cd)))
+    return ck.value, cd.value
 
 
 def destroyBatch(b):

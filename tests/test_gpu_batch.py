@@ -102,6 +102,33 @@ def test_batch_tuner_and_info(Q, env):
             Q.destroyQureg(q)
 
 
+def test_batch_joint_tuner(Q, env):
+    """Tile size and fusion depth tuned together: the chosen pair is one of
+    the candidates, the batch is re-planned with it (a depth cap of 8 ops
+    per pass gives more passes than the default), and every register still
+    matches the oracle."""
+    sizes = [6, 9, 12, 14, 17]
+    regs, circs = make_regs(Q, env, sizes, 64, 56)
+    try:
+        b = Q.createBatch(env, regs)
+        p_default = Q.getBatchInfo(b)["passes"]
+        k, d = Q.tuneBatchJoint(b, [8], [8], replays=1)
+        assert (k, d) == (8, 8) and Q.getBatchInfo(b)["passes"] > p_default
+        k, d = Q.tuneBatchJoint(b, [10, 13], [0, 16, 64], replays=1)
+        assert k in (10, 13) and d in (0, 16, 64)
+        Q.runBatch(b)
+        for q, n, ops in zip(regs, sizes, circs):
+            ref = O.run_circuit(n, ops)
+            assert np.max(np.abs(Q.copyStateToHost(q) - ref.a)) <= AMP_TOL[64]
+        with pytest.raises(Q.QSimError) as e:
+            Q.tuneBatchJoint(b, [10], [300])
+        assert e.value.name == "QS_E_ARG"
+        Q.destroyBatch(b)
+    finally:
+        for q in regs:
+            Q.destroyQureg(q)
+
+
 def test_batch_argument_errors(Q, env):
     a = Q.createQureg(10, 64, env)
     c = Q.createQureg(10, 128, env)

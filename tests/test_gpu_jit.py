@@ -52,6 +52,7 @@ def run_both(Q, env, n, ops, prec, arith=0, density=False, tile=0, min_q=None):
     launched generated kernels and none failed."""
     Q.setEnvOption(env, "arith", arith)
     Q.setEnvOption(env, "tile_qubits", tile)
+    Q.setEnvOption(env, "jit_fp64", 1)
     if min_q is not None:
         Q.setEnvOption(env, "jit_min_qubits", min_q)
     try:
@@ -63,6 +64,7 @@ def run_both(Q, env, n, ops, prec, arith=0, density=False, tile=0, min_q=None):
         launched = Q.getEnvOption(env, "jit_launches") - l0
     finally:
         Q.setEnvOption(env, "jit", 2)
+        Q.setEnvOption(env, "jit_fp64", 0)
         Q.setEnvOption(env, "arith", 0)
         Q.setEnvOption(env, "tile_qubits", 0)
         Q.setEnvOption(env, "jit_min_qubits", 20)
