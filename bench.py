@@ -60,6 +60,10 @@ def parse():
                          "(0 = no cap); 2000 and 60 give the full-length sweep")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg (profiling runs)")
+    ap.add_argument("--jit-tma", type=int, default=None, choices=[0, 1],
+                    help="generated pass kernels move tiles by bulk copies, double-buffered")
+    ap.add_argument("--jit-ctas", type=int, default=None, help="resident CTAs per SM of generated kernels")
+    ap.add_argument("--tile-qubits", type=int, default=None, help="fused tile size k (0 = automatic)")
     ap.add_argument("--jit", type=int, default=1, choices=[0, 1, 2],
                     help="fused passes: 0 interpreting kernel, 1 runtime-compiled kernels "
                          "(compiled in the warm-up), 2 compiled in the background")
@@ -316,6 +320,9 @@ def main():
     # fused passes as runtime-compiled kernels, compiled during the warm-up
     # (the first step waits for them; timed steps reuse the cached kernels)
     Q.setEnvOption(env, "jit", args.jit)
+    for opt, val in (("jit_tma", args.jit_tma), ("jit_ctas", args.jit_ctas), ("tile_qubits", args.tile_qubits)):
+        if val is not None:
+            Q.setEnvOption(env, opt, val)
     stream = torch.cuda.Stream()
     Q.setStream(env, stream)
     q = Q.createQureg(n, prec, env)
@@ -380,7 +387,10 @@ def main():
                    "gates_per_step": ngates, "parallelism": f"replicas x{world}",
                    "l2": "state 2^n amplitudes >> 126 MB L2, no flush",
                    "fused_passes_per_step": passes,
+                   "tile_qubits": Q.getEnvOption(env, "tile_qubits"),
                    "jit": {"mode": args.jit, "kernels": Q.getEnvOption(env, "jit_ready"),
+                           "bulk_copy_pipeline": Q.getEnvOption(env, "jit_tma"),
+                           "ctas_per_sm": Q.getEnvOption(env, "jit_ctas"),
                            "compile_ms_total": Q.getEnvOption(env, "jit_compile_ms"),
                            "launches": Q.getEnvOption(env, "jit_launches")}},
         "roofline": roofline(stats, 1 << n),

@@ -148,6 +148,12 @@ int qsDiagBoundedWait(QuESTEnv env, int timeoutUs);
  *                   Read-only counters: "jit_launches", "jit_rejected",
  *                   "jit_ready", "jit_pending", "jit_failed",
  *                   "jit_compile_ms".
+ *   "plan_cache"    1 (default) = a flush of a gate list that equals one of
+ *                   the env's 16 most recently planned lists (same gates and
+ *                   parameters, register shape, precision, options, known-
+ *                   zero bits and pending scalar) reuses its plan instead of
+ *                   planning again; 0 = always plan (and drop the cache).
+ *                   Counter: "plan_cache_hits".
  * Unknown keys give QS_E_ARG. */
 int setEnvOption(QuESTEnv env, const char *key, int64_t value);
 /* getEnvOption: reads an option back, or a counter of the env:

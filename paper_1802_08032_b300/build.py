@@ -13,7 +13,7 @@ SOURCES = ["api.cu", "oplist.cpp", "launch.cu", "planner.cpp", "fused.cu", "prof
            "batch.cu", "serve.cu", "jit.cpp", "jit_gen.cpp"]
 # device headers the runtime-compiled pass kernels include (embedded in the
 # library for NVRTC)
-JIT_HEADERS = ["common.cuh", "dfloat.cuh", "fused_types.h", "pair_arith.cuh", "fused_arith.cuh"]
+JIT_HEADERS = ["common.cuh", "dfloat.cuh", "fused_types.h", "pair_arith.cuh", "fused_arith.cuh", "mbarrier.cuh"]
 GEN = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

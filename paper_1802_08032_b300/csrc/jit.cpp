@@ -222,7 +222,8 @@ bool jit_try_launch(Env& env, Reg& r, const FPass& fp, const FStage* st, const F
   if (env.jit == 0 || r.nq < env.jit_min_qubits || fp.init) return false;
   if (arith == Arith::F64 && env.jit_fp64 == 0) return false;
   if (fp.op_count <= 0 || fp.op_count > kMaxPassOps) return false;
-  const JitShape sh{arith, R, int(env.jit_ctas)};
+  JitShape sh{arith, R, int(env.jit_ctas)};
+  sh.tma = env.jit_tma != 0;
   std::string src;
   try {
     src = jit_source(fp, st, ops, sh);
@@ -230,7 +231,7 @@ bool jit_try_launch(Env& env, Reg& r, const FPass& fp, const FStage* st, const F
     ++env.jit_rejected;
     return false;
   }
-  const size_t smem = jit_smem_bytes(fp, arith);
+  const size_t smem = jit_smem_bytes(fp, sh);
   bool created = false;
   std::shared_ptr<JitEntry> e = JitCache::get().find_or_queue(src, env.device, smem, created);
   if (env.jit == 1 && e->state.load() == JS_QUEUED) JitCache::get().wait(e);
@@ -238,8 +239,11 @@ bool jit_try_launch(Env& env, Reg& r, const FPass& fp, const FStage* st, const F
   // parameters: g, ntiles, then the pass's FOp records (constant bank)
   void* g = r.d;
   long long ntiles = fp.ntiles;
+  unsigned* status = env.d_status;
   const FOp* popv = ops + fp.op_begin;
-  void* args[3] = {&g, &ntiles, const_cast<FOp*>(popv)};
+  void* args_plain[3] = {&g, &ntiles, const_cast<FOp*>(popv)};
+  void* args_tma[4] = {&g, &ntiles, &status, const_cast<FOp*>(popv)};
+  void** args = sh.tma ? args_tma : args_plain;
   const int threads = 1 << (fp.k - R);
   const int64_t grid = std::min<int64_t>(fp.ntiles, int64_t(env.sms) * env.jit_ctas);
   const double bytes = std::ldexp(2.0 * (arith == Arith::F32 ? 8.0 : 16.0), r.nq);

@@ -26,20 +26,23 @@ struct JitShape {
   Arith arith;
   int R;
   int ctas;  // resident CTAs per SM the kernel is compiled for (__launch_bounds__)
+  // tiles move by bulk (TMA) copies through two shared-memory buffers, the
+  // next tile's load overlapping the current tile's work; the kernel then
+  // takes a device status word after ntiles (bit 1: a copy did not arrive
+  // within 1 s of the GPU's global timer)
+  bool tma = false;
 };
 
 // CUDA source of the pass kernel `qs_pass` for pass fp of a plan whose
 // stage and op arrays are st and ops (fp's indices relative to them).
-// Kernel signature: (Store* g, long long ntiles, const __grid_constant__
-// JitOps P) with P holding fp.op_count FOp records.  Throws Error
-// (QS_E_ARG) if the pass uses a form the generator does not know.
+// Kernel signature: (Store* g, long long ntiles, [unsigned* status,] const
+// __grid_constant__ JitOps P) with P holding fp.op_count FOp records (the
+// status word only with sh.tma).  Throws Error (QS_E_ARG) if the pass uses a
+// form the generator does not know.
 std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const JitShape& sh);
 
-// Bytes of the kernel's parameter block after the two scalar arguments.
-inline size_t jit_param_bytes(const FPass& fp) { return sizeof(FOp) * size_t(fp.op_count); }
-
 // Shared-memory bytes of a generated pass kernel.
-size_t jit_smem_bytes(const FPass& fp, Arith a);
+size_t jit_smem_bytes(const FPass& fp, const JitShape& sh);
 
 // Headers the generated source includes, as (name, contents) pairs embedded
 // at build time; used by the NVRTC compile.

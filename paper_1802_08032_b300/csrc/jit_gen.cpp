@@ -13,6 +13,7 @@
 //     stay run-time tests of the thread's local index and the tile base.
 // Host code only (no CUDA runtime calls): the CPU planner tests generate and
 // compile these sources without a GPU.
+#include <algorithm>
 #include <cstdio>
 #include <sstream>
 
@@ -130,9 +131,23 @@ std::string op_statement(const FOp& op, int o, int R, const JitShape& sh) {
   fail(QS_E_ARG, "jit: unknown op family " + std::to_string(fam));
 }
 
+// True when the set m of register amplitudes is not invariant under
+// toggling register bit i (a sign flip on m does not commute with a pair
+// update on bit i).
+bool depends_on(uint32_t m, int i, int R) {
+  if (i < 0 || i >= R) return true;
+  uint32_t moved = 0;
+  for (int j = 0; j < (1 << R); ++j)
+    if ((m >> j) & 1u) moved |= 1u << (j ^ (1 << i));
+  return moved != m;
+}
+
 }  // namespace
 
-size_t jit_smem_bytes(const FPass& fp, Arith a) { return cplx_bytes(a) * (size_t(1) << fp.k); }
+size_t jit_smem_bytes(const FPass& fp, const JitShape& sh) {
+  const size_t tile = cplx_bytes(sh.arith) * (size_t(1) << fp.k);
+  return sh.tma ? 2 * tile + 2 * sizeof(uint64_t) : tile;
+}
 
 std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const JitShape& sh) {
   const int R = sh.R, k = fp.k, L = fp.L;
@@ -141,7 +156,8 @@ std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const 
   const int T = 1 << (k - R);
   const bool pack2 = store_bytes(sh.arith) == 8;  // complex64: two amplitudes per access
   const int span_log = pack2 ? (k - R + 1) : (k - R);  // amplitudes one round of accesses covers (log2)
-  if (span_log < L) fail(QS_E_ARG, "jit: access round narrower than a chunk");
+  if (!sh.tma && span_log < L) fail(QS_E_ARG, "jit: access round narrower than a chunk");
+  if (sh.tma && (size_t(1) << L) * store_bytes(sh.arith) % 16 != 0) fail(QS_E_ARG, "jit: chunk not 16-byte sized");
   const int depth = pack2 ? (1 << (R - 1)) : (1 << R);
   const int cbits = span_log - L;  // chunk-index bits taken from the thread index
   auto deposit = [&](uint64_t c) {  // chunk index -> offset (bit i at tile qubit L + i)
@@ -150,57 +166,128 @@ std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const 
       if ((c >> i) & 1u) off |= uint64_t(1) << fp.q[L + i];
     return off;
   };
+  const int nstage = fp.stage_end - fp.stage_begin;
   std::ostringstream s;
-  s << "// fused pass: k " << k << " L " << L << " R " << R << " ops " << fp.op_count << " stages "
-    << (fp.stage_end - fp.stage_begin) << "\n";
+  s << "// fused pass: k " << k << " L " << L << " R " << R << " ops " << fp.op_count << " stages " << nstage
+    << (sh.tma ? " (bulk-copy pipeline)" : "") << "\n";
   s << "#ifdef __CUDACC_RTC__\n"
        "typedef signed char int8_t; typedef unsigned char uint8_t; typedef short int16_t;\n"
        "typedef unsigned short uint16_t; typedef int int32_t; typedef unsigned int uint32_t;\n"
        "typedef long long int64_t; typedef unsigned long long uint64_t;\n"
        "#endif\n"
-       "#include \"fused_arith.cuh\"\n"
-       "namespace qs { struct JitOps { FOp o["
-    << (fp.op_count > 0 ? fp.op_count : 1) << "]; }; }\n"
+       "#include \"fused_arith.cuh\"\n";
+  if (sh.tma) s << "#include \"mbarrier.cuh\"\n";
+  s << "namespace qs { struct JitOps { FOp o[" << (fp.op_count > 0 ? fp.op_count : 1) << "]; }; }\n"
     << "using namespace qs;\n"
     << "extern \"C\" __global__ void __launch_bounds__(" << T << ", " << sh.ctas << ")\n"
     << "qs_pass(" << store_name(sh.arith) << "* __restrict__ g, long long ntiles,\n"
+    << (sh.tma ? "        unsigned* __restrict__ status,\n" : "")
     << "        const __grid_constant__ qs::JitOps P) {\n"
     << "  using A = " << arith_name(sh.arith) << ";\n"
     << "  using Cplx = A::Cplx;\n"
-    << "  extern __shared__ __align__(16) unsigned char smem_raw[];\n"
-    << "  Cplx* __restrict__ tile = reinterpret_cast<Cplx*>(smem_raw);\n"
+    << "  using Store = A::Store;\n"
+    << "  extern __shared__ __align__(128) unsigned char smem_raw[];\n"
     << "  const uint32_t tid = threadIdx.x;\n";
-  // this thread's part of the tile offset of its accesses
-  s << "  const uint32_t lt = " << (pack2 ? "2u * tid" : "tid") << ";\n"
-    << "  int64_t toff = int64_t(lt & " << hex32((1u << L) - 1u) << ");\n";
-  for (int i = 0; i < cbits; ++i)
-    s << "  toff |= int64_t((lt >> " << (L + i) << ") & 1u) << " << int(fp.q[L + i]) << ";\n";
-  s << "  for (int64_t tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {\n"
-    << "    int64_t base = tau << " << L << ";\n";
+  // tile base: the tile index with a zero inserted at every tile qubit
+  s << "  auto tile_base = [](int64_t t) {\n    int64_t b = t << " << L << ";\n";
   for (int i = L; i < k; ++i) {
     const int p = fp.q[i];
-    s << "    base = ((base >> " << p << ") << " << (p + 1) << ") | (base & " << hex64((uint64_t(1) << p) - 1)
-      << ");\n";
+    s << "    b = ((b >> " << p << ") << " << (p + 1) << ") | (b & " << hex64((uint64_t(1) << p) - 1) << ");\n";
   }
-  // tile load: all accesses of the round in flight, then into shared memory
-  if (pack2) {
-    s << "    {\n      const float4* __restrict__ g4 = reinterpret_cast<const float4*>(g);\n"
-      << "      float4* t4 = reinterpret_cast<float4*>(tile);\n"
-      << "      const int64_t gb = base + toff;\n";
-    for (int u = 0; u < depth; ++u)
-      s << "      const float4 ld" << u << " = g4[(gb + " << hex64(deposit(uint64_t(u) << cbits)) << ") >> 1];\n";
-    for (int u = 0; u < depth; ++u) s << "      t4[tid + " << u * T << "u] = ld" << u << ";\n";
-    s << "    }\n";
+  s << "    return b;\n  };\n";
+  const int nchunk_log = k - L;
+  // warp 0 issues the copies: up to 32 lanes, no more than the CTA has
+  const int lanes_log = std::min({5, nchunk_log, k - R});
+  const std::string warp_mask = k - R >= 5 ? "0xFFFFFFFFu" : hex32((1u << (1 << (k - R))) - 1u);
+  const int per_lane = 1 << (nchunk_log - lanes_log);
+  const size_t chunk_bytes = (size_t(1) << L) * store_bytes(sh.arith);
+  const size_t tile_store_bytes = (size_t(1) << k) * store_bytes(sh.arith);
+  if (sh.tma) {
+    // Bulk-copy pipeline: two tile buffers; warp 0 copies tile t + 1 into
+    // one (2^(k-L) contiguous chunks of 2^L amplitudes, completing on that
+    // buffer's mbarrier) while the CTA works on tile t in the other, and
+    // stores a finished tile with bulk copies from shared memory.
+    s << "  Cplx* const buf0 = reinterpret_cast<Cplx*>(smem_raw);\n"
+      << "  Cplx* const buf1 = buf0 + " << (1 << k) << ";\n"
+      << "  uint64_t* const bar = reinterpret_cast<uint64_t*>(buf0 + " << (2 << k) << ");\n"
+      << "  const uint32_t lane = tid & 31u;\n"
+      << "  int64_t coff = 0;  // this lane's chunk offset (chunk c = lane + 32 u)\n";
+    for (int i = 0; i < lanes_log; ++i)
+      s << "  coff |= int64_t((lane >> " << i << ") & 1u) << " << int(fp.q[L + i]) << ";\n";
+    s << "  auto issue_load = [&](int64_t b, Cplx* dst, uint64_t* br) {\n"
+      << "    if (lane == 0) mb::arrive_expect_tx(br, " << tile_store_bytes << "u);\n"
+      << "    __syncwarp(" << warp_mask << ");\n";
+    if (lanes_log < 5) s << "    if (lane < " << (1 << lanes_log) << "u) {\n";
+    else s << "    {\n";
+    for (int u = 0; u < per_lane; ++u) {
+      const uint64_t cu = uint64_t(u) << lanes_log;
+      s << "      mb::bulk_load(reinterpret_cast<Store*>(dst) + ((lane + " << cu << "u) << " << L << "), g + b + coff + "
+        << hex64(deposit(cu)) << ", " << chunk_bytes << "u, br);\n";
+    }
+    s << "    }\n  };\n";
+    s << "  auto issue_store = [&](int64_t b, Cplx* src) {\n";
+    if (lanes_log < 5) s << "    if (lane < " << (1 << lanes_log) << "u) {\n";
+    else s << "    {\n";
+    for (int u = 0; u < per_lane; ++u) {
+      const uint64_t cu = uint64_t(u) << lanes_log;
+      s << "      mb::bulk_store(g + b + coff + " << hex64(deposit(cu)) << ", reinterpret_cast<Store*>(src) + ((lane + "
+        << cu << "u) << " << L << "), " << chunk_bytes << "u);\n";
+    }
+    s << "      mb::bulk_commit();\n    }\n  };\n";
+    s << "  if (tid == 0) {\n    mb::init(&bar[0], 1);\n    mb::init(&bar[1], 1);\n    mb::fence_init();\n  }\n"
+      << "  __syncthreads();\n"
+      << "  int64_t tau = blockIdx.x;\n"
+      << "  if (tid < 32 && tau < ntiles) issue_load(tile_base(tau), buf0, &bar[0]);\n"
+      << "  uint32_t parity = 0;  // bit i: parity of buffer i's next phase\n"
+      << "  bool pend[2] = {tau < ntiles, false};\n"
+      << "  bool ok = true;\n"
+      << "  for (int it = 0; tau < ntiles; ++it, tau += gridDim.x) {\n"
+      << "    const int cur = it & 1;\n"
+      << "    Cplx* const tile = cur ? buf1 : buf0;\n"
+      << "    const int64_t base = tile_base(tau);\n"
+      << "    const bool more = tau + int64_t(gridDim.x) < ntiles;\n"
+      << "    if (tid < 32) {\n"
+      << "      mb::bulk_wait_read();  // the other buffer's stores have read it\n"
+      << "      if (more) issue_load(tile_base(tau + gridDim.x), cur ? buf0 : buf1, &bar[cur ^ 1]);\n"
+      << "    }\n"
+      << "    pend[cur ^ 1] = more;\n"
+      << "    const bool got = mb::wait(&bar[cur], (parity >> cur) & 1u);\n"
+      << "    if (!__syncthreads_and(got)) {\n      ok = false;\n      break;\n    }\n"
+      << "    parity ^= 1u << cur;\n"
+      << "    pend[cur] = false;\n";
   } else {
-    s << "    {\n      const int64_t gb = base + toff;\n";
-    for (int u = 0; u < depth; ++u)
-      s << "      const double2 ld" << u << " = g[gb + " << hex64(deposit(uint64_t(u) << cbits)) << "];\n";
-    for (int u = 0; u < depth; ++u) s << "      tile[tid + " << u * T << "u] = A::from_store(ld" << u << ");\n";
-    s << "    }\n";
+    s << "  Cplx* __restrict__ tile = reinterpret_cast<Cplx*>(smem_raw);\n";
+    // this thread's part of the tile offset of its accesses
+    s << "  const uint32_t lt = " << (pack2 ? "2u * tid" : "tid") << ";\n"
+      << "  int64_t toff = int64_t(lt & " << hex32((1u << L) - 1u) << ");\n";
+    for (int i = 0; i < cbits; ++i)
+      s << "  toff |= int64_t((lt >> " << (L + i) << ") & 1u) << " << int(fp.q[L + i]) << ";\n";
+    s << "  for (int64_t tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {\n"
+      << "    const int64_t base = tile_base(tau);\n";
+    // tile load: all accesses of the round in flight, then into shared memory
+    if (pack2) {
+      s << "    {\n      const float4* __restrict__ g4 = reinterpret_cast<const float4*>(g);\n"
+        << "      float4* t4 = reinterpret_cast<float4*>(tile);\n"
+        << "      const int64_t gb = base + toff;\n";
+      for (int u = 0; u < depth; ++u)
+        s << "      const float4 ld" << u << " = g4[(gb + " << hex64(deposit(uint64_t(u) << cbits)) << ") >> 1];\n";
+      for (int u = 0; u < depth; ++u) s << "      t4[tid + " << u * T << "u] = ld" << u << ";\n";
+      s << "    }\n";
+    } else {
+      s << "    {\n      const int64_t gb = base + toff;\n";
+      for (int u = 0; u < depth; ++u)
+        s << "      const double2 ld" << u << " = g[gb + " << hex64(deposit(uint64_t(u) << cbits)) << "];\n";
+      for (int u = 0; u < depth; ++u) s << "      tile[tid + " << u * T << "u] = A::from_store(ld" << u << ");\n";
+      s << "    }\n";
+    }
+    s << "    __syncthreads();\n";
   }
-  s << "    __syncthreads();\n";
   for (int si = fp.stage_begin; si < fp.stage_end; ++si) {
     const FStage& S = st[si];
+    // with the bulk-copy pipeline the tile arrives and leaves in the storage
+    // format: the first stage converts on reading, the last on writing
+    const bool first_io = sh.tma && si == fp.stage_begin;
+    const bool last_io = sh.tma && si == fp.stage_end - 1;
     uint32_t poff[8] = {}, cpm = 0;
     for (int i = 0; i < R; ++i) {
       if (S.pbits[i] >= k) fail(QS_E_ARG, "jit: register position outside the tile");
@@ -219,41 +306,121 @@ std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const 
       for (int i = 0; i < R; ++i)
         if (j & (1 << i)) o |= poff[i];
       off[size_t(j)] = o;
-      s << "      v[" << j << "] = tile[tl | " << hex32(o & ~cpm) << "];\n";
+      if (first_io)
+        s << "      v[" << j << "] = A::from_store(reinterpret_cast<const Store*>(tile)[tl | " << hex32(o & ~cpm)
+          << "]);\n";
+      else
+        s << "      v[" << j << "] = tile[tl | " << hex32(o & ~cpm) << "];\n";
     }
+    // Sign flips (CZ, multi-controlled phase flips) are kept pending, as
+    // the interpreter keeps them: an unconditional compile-time mask, and
+    // per-thread booleans for flips conditioned on local or global bits
+    // (one per distinct mask, merged by XOR); each is applied just before
+    // the first op it does not commute with, or at the end of the stage.
+    // Negation is exact and commutes exactly with what it is moved past, so
+    // the results are those of applying it where it occurs.
+    uint32_t unc = 0;
+    std::vector<std::pair<uint32_t, std::string>> pend;  // (mask, bool variable)
+    int nflag = 0;
+    const std::string AR = "A, " + std::to_string(R);
+    auto apply_unc = [&]() {
+      if (unc) s << "      negate_mask<" << AR << ", " << hex32(unc) << ">(v);\n";
+      unc = 0;
+    };
+    auto apply_pend = [&](size_t i) {
+      s << "      if (" << pend[i].second << ") negate_mask<" << AR << ", " << hex32(pend[i].first) << ">(v);\n";
+    };
     for (int o = S.op_begin; o < S.op_end; ++o) {
       if (o < 0 || o >= fp.op_count) fail(QS_E_ARG, "jit: stage op range outside the pass");
       const FOp& op = ops[fp.op_begin + o];
-      const std::string stmt = op_statement(op, o, R, sh);
+      std::string cond;
       if ((op.flags & FF_COND) && (op.lmask || op.gmask)) {
-        s << "      if (";
-        if (op.lmask) s << "(tl & " << hex32(op.lmask) << ") == " << hex32(op.lmask);
-        if (op.lmask && op.gmask) s << " && ";
-        if (op.gmask) s << "((uint64_t)base & " << hex64(op.gmask) << ") == " << hex64(op.gmask);
-        s << ") " << stmt << "\n";
-      } else {
-        s << "      " << stmt << "\n";
+        if (op.lmask) cond += "(tl & " + hex32(op.lmask) + ") == " + hex32(op.lmask);
+        if (op.lmask && op.gmask) cond += " && ";
+        if (op.gmask) cond += "((uint64_t)base & " + hex64(op.gmask) + ") == " + hex64(op.gmask);
       }
+      if (op.code == FC_SIGN * kCodeSlots) {
+        const uint32_t m = op.c.u[15] & (R >= 5 ? 0xFFFFFFFFu : ((1u << (1 << R)) - 1u));
+        if (!m) continue;
+        if (cond.empty()) {
+          unc ^= m;
+          continue;
+        }
+        size_t i = 0;
+        while (i < pend.size() && pend[i].first != m) ++i;
+        if (i == pend.size()) {
+          const std::string var = "f" + std::to_string(nflag++);
+          s << "      bool " << var << " = " << cond << ";\n";
+          pend.emplace_back(m, var);
+        } else {
+          s << "      " << pend[i].second << " ^= (" << cond << ");\n";
+        }
+        continue;
+      }
+      if (op.flags & FF_FLIP) {
+        const int b0 = op.i0, b1 = (op.flags & FF_TWO) ? op.i1 : -1;
+        auto dep = [&](uint32_t m) {
+          return depends_on(m, b0, R) || (b1 >= 0 && depends_on(m, b1, R));
+        };
+        if (unc && dep(unc)) apply_unc();
+        for (size_t i = 0; i < pend.size();) {
+          if (dep(pend[i].first)) {
+            apply_pend(i);
+            pend.erase(pend.begin() + long(i));
+          } else {
+            ++i;
+          }
+        }
+      }
+      const std::string stmt = op_statement(op, o, R, sh);
+      if (!cond.empty()) s << "      if (" << cond << ") " << stmt << "\n";
+      else s << "      " << stmt << "\n";
     }
-    for (int j = 0; j < (1 << R); ++j) s << "      tile[tl | " << hex32(off[size_t(j)]) << "] = v[" << j << "];\n";
+    apply_unc();
+    for (size_t i = 0; i < pend.size(); ++i) apply_pend(i);
+    if (last_io) {
+      // (each thread writes exactly the slots it read: converting in place
+      // needs no barrier)
+      for (int j = 0; j < (1 << R); ++j)
+        s << "      reinterpret_cast<Store*>(tile)[tl | " << hex32(off[size_t(j)]) << "] = A::to_store(v[" << j
+          << "]);\n";
+    } else {
+      for (int j = 0; j < (1 << R); ++j) s << "      tile[tl | " << hex32(off[size_t(j)]) << "] = v[" << j << "];\n";
+    }
     s << "    }\n    __syncthreads();\n";
   }
-  // tile store
-  if (pack2) {
-    s << "    {\n      float4* __restrict__ g4 = reinterpret_cast<float4*>(g);\n"
-      << "      const float4* t4 = reinterpret_cast<const float4*>(tile);\n"
-      << "      const int64_t gb = base + toff;\n";
-    for (int u = 0; u < depth; ++u)
-      s << "      g4[(gb + " << hex64(deposit(uint64_t(u) << cbits)) << ") >> 1] = t4[tid + " << u * T << "u];\n";
-    s << "    }\n";
+  if (sh.tma) {
+    s << "    mb::fence_proxy_async();\n"
+      << "    __syncthreads();\n"
+      << "    if (tid < 32) issue_store(base, tile);\n"
+      << "  }\n"
+      << "  if (!ok) {\n"
+      << "    // a copy did not arrive within the bound: report it, and wait (bounded)\n"
+      << "    // for copies still in flight into this CTA's shared memory\n"
+      << "    if (tid == 0) atomicOr(status, 2u);\n"
+      << "    for (int i = 0; i < 2; ++i)\n"
+      << "      if (pend[i]) (void)mb::wait(&bar[i], (parity >> i) & 1u);\n"
+      << "  }\n"
+      << "  if (tid < 32) mb::bulk_wait();\n"
+      << "}\n";
   } else {
-    s << "    {\n      const int64_t gb = base + toff;\n";
-    for (int u = 0; u < depth; ++u)
-      s << "      g[gb + " << hex64(deposit(uint64_t(u) << cbits)) << "] = A::to_store(tile[tid + " << u * T
-        << "u]);\n";
-    s << "    }\n";
+    s << "    // tile store\n";
+    if (pack2) {
+      s << "    {\n      float4* __restrict__ g4 = reinterpret_cast<float4*>(g);\n"
+        << "      const float4* t4 = reinterpret_cast<const float4*>(tile);\n"
+        << "      const int64_t gb = base + toff;\n";
+      for (int u = 0; u < depth; ++u)
+        s << "      g4[(gb + " << hex64(deposit(uint64_t(u) << cbits)) << ") >> 1] = t4[tid + " << u * T << "u];\n";
+      s << "    }\n";
+    } else {
+      s << "    {\n      const int64_t gb = base + toff;\n";
+      for (int u = 0; u < depth; ++u)
+        s << "      g[gb + " << hex64(deposit(uint64_t(u) << cbits)) << "] = A::to_store(tile[tid + " << u * T
+          << "u]);\n";
+      s << "    }\n";
+    }
+    s << "    __syncthreads();\n  }\n}\n";
   }
-  s << "    __syncthreads();\n  }\n}\n";
   return s.str();
 }
 

@@ -598,7 +598,9 @@ void check_status(Env& env) {
   if (s == 0) return;
   *env.h_status = 0;
   QS_CUDA(cudaMemsetAsync(env.d_status, 0, sizeof(unsigned), env.stream));
-  fail(QS_E_TIMEOUT, "a bounded device wait ran out (tensor-core multi-target pass); amplitudes are unreliable");
+  fail(QS_E_TIMEOUT, std::string("a bounded device wait ran out (") +
+                         ((s & 1u) ? "tensor-core multi-target pass" : "bulk tile copy of a fused pass") +
+                         "); amplitudes are unreliable");
 }
 
 // Unscaled passes grow the stored amplitudes by 1/|pend_scale|: settle the

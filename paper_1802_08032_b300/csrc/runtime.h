@@ -133,10 +133,15 @@ struct Env {
   int64_t jit = 2;
   int64_t jit_min_qubits = 20;
   int64_t jit_ctas = 2;
+  int64_t jit_tma = 0;  // generated kernels move tiles by bulk copies, double-buffered
   // IEEE-FP64 passes are bound by the FP64 pipe, where the interpreting
   // kernel measured faster (30 qubits: 83.4 vs 88.3 ms a pass): they use
   // generated kernels only when this is 1
   int64_t jit_fp64 = 0;
+  // reuse of plans for repeated gate lists (fused.cu): on by default
+  int64_t plan_cache_on = 1;
+  int64_t plan_cache_hits = 0;
+  std::shared_ptr<void> plan_cache;
   Profiler prof;
   // counters (readable through getEnvOption)
   int64_t launches = 0;      // kernel launches issued

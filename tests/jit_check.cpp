@@ -6,12 +6,13 @@
 // Reads QSOp records from stdin, plans them for a register of the given
 // shape, generates the pass kernel of every pass and compiles it with NVRTC
 // for sm_103a.  Prints "JIT passes P compiled C distinct D seconds S" and,
-// for a failure, the compiler log.  Argument 7 caps how many distinct
-// kernels are compiled (all are generated); with a file name as argument 8
-// the source of the first pass is written there.  Compiles run on up to 8
+// for a failure, the compiler log.  tma = 1 generates the bulk-copy
+// pipeline form.  Argument 8 caps how many distinct kernels are compiled
+// (all are generated); with a file name as argument 9 the source of the
+// first pass is written there.  Compiles run on up to 8
 // host threads.
 //
-// usage: jit_check n density prec arith k_req ctas [max_compile [source_out]]
+// usage: jit_check n density prec arith k_req ctas tma [max_compile [source_out]]
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -35,12 +36,13 @@ KTimer::~KTimer() {}
 }  // namespace qs
 
 int main(int argc, char** argv) {
-  if (argc < 7) {
-    std::fprintf(stderr, "usage: jit_check n density prec arith k_req ctas [source_out]\n");
+  if (argc < 8) {
+    std::fprintf(stderr, "usage: jit_check n density prec arith k_req ctas tma [max_compile [source_out]]\n");
     return 2;
   }
   const int n = std::atoi(argv[1]), density = std::atoi(argv[2]), prec = std::atoi(argv[3]);
   const int arith = std::atoi(argv[4]), k_req = std::atoi(argv[5]), ctas = std::atoi(argv[6]);
+  const bool tma = std::atoi(argv[7]) != 0;
   Env env;
   env.arith = arith;
   Reg r;
@@ -63,19 +65,21 @@ int main(int argc, char** argv) {
     return 1;
   }
   const int R = pl.arith == Arith::F32 ? 5 : 4;
-  const int max_compile = argc > 7 ? std::atoi(argv[7]) : 1 << 30;
+  const int max_compile = argc > 8 ? std::atoi(argv[8]) : 1 << 30;
+  JitShape shape{pl.arith, R, ctas};
+  shape.tma = tma;
   std::set<std::string> distinct;
   std::vector<std::string> todo;
   for (size_t i = 0; i < pl.fps.size(); ++i) {
     std::string src;
     try {
-      src = jit_source(pl.fps[i], pl.fst.data(), pl.fops.data(), JitShape{pl.arith, R, ctas});
+      src = jit_source(pl.fps[i], pl.fst.data(), pl.fops.data(), shape);
     } catch (const Error& e) {
       std::printf("GENFAIL pass %zu: %s\n", i, e.msg.c_str());
       return 3;
     }
-    if (i == 0 && argc > 8) {
-      FILE* f = std::fopen(argv[8], "w");
+    if (i == 0 && argc > 9) {
+      FILE* f = std::fopen(argv[9], "w");
       if (f) {
         std::fputs(src.c_str(), f);
         std::fclose(f);

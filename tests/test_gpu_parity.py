@@ -423,3 +423,24 @@ def test_fusion_cuts_passes_per_layer(Q, env):
     passes = Q.getEnvOption(env, "fused_passes") - p0
     Q.destroyQureg(q)
     assert len(ops) / passes >= 4.0, (len(ops), passes)
+
+
+def test_plan_cache_reuses_identical_gate_lists(Q, env):
+    """A repeated flush of the same gate list reuses the cached plan (bit-
+    identical result); a list differing in one angle is planned anew and
+    matches the oracle."""
+    n = 14
+    ops = C.random_circuit(n, 10, 4242, extras=True)
+    a = gpu_state(Q, env, n, ops, 128)
+    h1 = Q.getEnvOption(env, "plan_cache_hits")
+    b = gpu_state(Q, env, n, ops, 128)
+    h2 = Q.getEnvOption(env, "plan_cache_hits")
+    assert h2 > h1 and np.array_equal(a, b)
+    i = next(j for j, o in enumerate(ops) if o.kind == "COMPACT")
+    ar, ai, br, bi = ops[i].params
+    c, s = np.cos(0.1), np.sin(0.1)
+    ops2 = list(ops)
+    ops2[i] = C.Op("COMPACT", ops[i].targets, (), (ar * c - ai * s, ar * s + ai * c, br, bi))
+    got = gpu_state(Q, env, n, ops2, 128)
+    assert Q.getEnvOption(env, "plan_cache_hits") == h2
+    assert np.max(np.abs(got - O.run_circuit(n, ops2).a)) <= AMP_TOL[128]
