@@ -60,8 +60,9 @@ def parse():
                          "(0 = no cap); 2000 and 60 give the full-length sweep")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg (profiling runs)")
-    ap.add_argument("--jit-tma", type=int, default=None, choices=[0, 1],
-                    help="generated pass kernels move tiles by bulk copies, double-buffered")
+    ap.add_argument("--jit-copy", type=int, default=None, choices=[0, 1, 2],
+                    help="generated pass kernels move tiles by coalesced loads (0), bulk (TMA) copies "
+                         "double-buffered (1) or async copies double-buffered (2)")
     ap.add_argument("--jit-ctas", type=int, default=None, help="resident CTAs per SM of generated kernels")
     ap.add_argument("--tile-qubits", type=int, default=None, help="fused tile size k (0 = automatic)")
     ap.add_argument("--jit", type=int, default=1, choices=[0, 1, 2],
@@ -320,7 +321,7 @@ def main():
     # fused passes as runtime-compiled kernels, compiled during the warm-up
     # (the first step waits for them; timed steps reuse the cached kernels)
     Q.setEnvOption(env, "jit", args.jit)
-    for opt, val in (("jit_tma", args.jit_tma), ("jit_ctas", args.jit_ctas), ("tile_qubits", args.tile_qubits)):
+    for opt, val in (("jit_copy", args.jit_copy), ("jit_ctas", args.jit_ctas), ("tile_qubits", args.tile_qubits)):
         if val is not None:
             Q.setEnvOption(env, opt, val)
     stream = torch.cuda.Stream()
@@ -389,7 +390,8 @@ def main():
                    "fused_passes_per_step": passes,
                    "tile_qubits": Q.getEnvOption(env, "tile_qubits"),
                    "jit": {"mode": args.jit, "kernels": Q.getEnvOption(env, "jit_ready"),
-                           "bulk_copy_pipeline": Q.getEnvOption(env, "jit_tma"),
+                           "tile_copy": ["coalesced loads", "bulk (TMA) copies, double-buffered",
+                                         "async copies, double-buffered"][Q.getEnvOption(env, "jit_copy")],
                            "ctas_per_sm": Q.getEnvOption(env, "jit_ctas"),
                            "compile_ms_total": Q.getEnvOption(env, "jit_compile_ms"),
                            "launches": Q.getEnvOption(env, "jit_launches")}},
@@ -656,7 +658,7 @@ def variants(Q, env, torch, stream, only=(), qubits=30, serve=(60, 0.0)):
                      # last: after a serving sweep's many large allocations the process's later
                      # registers measured up to 15 % slower in latency-bound passes
                      ("serving", lambda: serve_sweep(Q, env, [10, 30, 100, 300, 1000, 2000], serve[0],
-                                                     baseline_rates=(10, 100), seconds=serve[1]))):
+                                                     seconds=serve[1]))):
         # the "_" entries keep / release the FP64 reference registers of
         # the sv<n> variants: they run when any sv<n>_ variant is wanted
         if only and name not in only and not (
@@ -838,13 +840,15 @@ def serve_trace(rate, count, seed0=5000, arrival_seed=55, max_sv=28, max_dm=13):
     return trace
 
 
-def run_trace(Q, env, trace, slots, fusion, force_c128=False, capture=None):
+def run_trace(Q, env, trace, slots, fusion, force_c128=False, capture=None, max_queue_us=0):
     """Submits each request at its arrival time, collects every result;
     returns latency percentiles and throughput.  capture: optional dict
     {request index: None}; those requests return their full final state
     (filled in place)."""
     import numpy as np
     srv = Q.serveCreate(env, slots=slots, budgetBytes=150 * 10 ** 9, fusion=fusion)
+    if max_queue_us:
+        Q.serveSetOption(srv, "max_queue_us", max_queue_us)
     prepared = [(t, dens, n, 128 if force_c128 else prec, Q.to_qsops(ops))
                 for (t, dens, n, prec, ops) in trace]
     tickets = []
@@ -862,12 +866,14 @@ def run_trace(Q, env, trace, slots, fusion, force_c128=False, capture=None):
         wall = time.perf_counter() - t0
     finally:
         Q.serveDestroy(srv)
-    lat = np.array([r["latencyUs"] for r in res]) / 1e3
-    bad = sum(r["status"] != 0 for r in res)
-    return {"requests": len(res), "failed": int(bad), "circuits_per_s": len(res) / wall,
+    ok = [r for r in res if r["status"] == 0]
+    shed = sum(Q.ERRORS.get(r["status"]) == "QS_E_BUSY" for r in res)
+    lat = np.array([r["latencyUs"] for r in ok] or [0.0]) / 1e3
+    return {"requests": len(res), "completed": len(ok), "shed": int(shed),
+            "failed": int(len(res) - len(ok) - shed), "circuits_per_s": len(ok) / wall,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_queued_ms": float(np.mean([r["queuedUs"] for r in res]) / 1e3),
-            "slots_used": len({r["slot"] for r in res})}
+            "mean_queued_ms": float(np.mean([r["queuedUs"] for r in ok] or [0.0]) / 1e3),
+            "slots_used": len({r["slot"] for r in ok})}
 
 
 def served_c64_error(Q, env, trace, captured):
@@ -898,7 +904,7 @@ def served_c64_error(Q, env, trace, captured):
             "max_one_minus_raw_overlap": max(r[2] for r in rows)}
 
 
-def serve_sweep(Q, env, rates, per_rate, slots=16, baseline_rates=(), seconds=0.0):
+def serve_sweep(Q, env, rates, per_rate, slots=16, baseline_rates=None, seconds=0.0):
     """Per arrival rate: `per_rate` requests, or fewer if `seconds` > 0 caps
     the trace at that many seconds of arrivals (rate x seconds requests)."""
     out = {}
@@ -911,7 +917,10 @@ def serve_sweep(Q, env, rates, per_rate, slots=16, baseline_rates=(), seconds=0.
         cap = dict(list(cap.items())[:12])
         row = {"served": run_trace(Q, env, trace, slots, 1, capture=cap)}
         row["served"]["c64_error_vs_fp64"] = served_c64_error(Q, env, trace, cap)
-        if rate in baseline_rates:
+        # admission policy past saturation: requests that cannot start within
+        # 1 s are shed, which bounds the latency of the ones served
+        row["served_shed_after_1s"] = run_trace(Q, env, trace, slots, 1, max_queue_us=1_000_000)
+        if baseline_rates is None or rate in baseline_rates:
             row["plain_c128_one_at_a_time"] = run_trace(Q, env, trace, 1, 0, force_c128=True)
         out[f"{rate}_req_per_s"] = row
     return out

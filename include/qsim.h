@@ -67,7 +67,8 @@ enum {
     QS_E_HANDLE = -8,       /* unknown or destroyed handle                     */
     QS_E_CUDA = -9,         /* CUDA runtime error (message in qsLastError)     */
     QS_E_TIMEOUT = -10,     /* a bounded device or host wait ran out           */
-    QS_E_ARG = -11          /* other invalid argument (null pointer, range)    */
+    QS_E_ARG = -11,         /* other invalid argument (null pointer, range)    */
+    QS_E_BUSY = -12         /* refused or shed by a server's admission policy  */
 };
 
 /* Message of the last failed call on this thread ("" if none). */
@@ -366,6 +367,16 @@ int destroyBatch(QSBatch batch);
  * servePoll: waits up to timeoutUs microseconds for the ticket's result;
  *   QS_E_TIMEOUT if it is not finished (the ticket stays valid), otherwise
  *   fills *out and retires the ticket.
+ * serveSetOption: admission policy past saturation (both 0 = none, the
+ *   default: every request is queued until it runs, so latency grows without
+ *   bound once arrivals outpace the GPU):
+ *     "max_queue"     back-pressure: serveSubmit refuses a request with
+ *                     QS_E_BUSY (nothing queued) while this many wait;
+ *     "max_queue_us"  shedding: a request that has waited this long without
+ *                     being admitted is dropped; its result has status
+ *                     QS_E_BUSY.  Admitted requests then wait at most about
+ *                     this long (the scheduler checks every 50 ms at most).
+ *   Counters (serveGetOption): "queued", "shed", "refused".
  * serveDestroy: stops admitting, waits for the requests on the GPU, cancels
  *   the queued ones, frees the slots. */
 typedef struct { int64_t id; } QSServer;
@@ -390,6 +401,8 @@ typedef struct {
 int serveCreate(QuESTEnv env, int slots, int64_t budgetBytes, int fusion, QSServer *out);
 int serveSubmit(QSServer server, const QSRequest *req, int64_t *ticket);
 int servePoll(QSServer server, int64_t ticket, QSResult *out, int64_t timeoutUs);
+int serveSetOption(QSServer server, const char *key, int64_t value);
+int serveGetOption(QSServer server, const char *key, int64_t *value);
 int serveDestroy(QSServer server);
 
 /* ------------------------------------------------- allocation-free norm */

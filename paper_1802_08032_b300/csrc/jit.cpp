@@ -223,7 +223,7 @@ bool jit_try_launch(Env& env, Reg& r, const FPass& fp, const FStage* st, const F
   if (arith == Arith::F64 && env.jit_fp64 == 0) return false;
   if (fp.op_count <= 0 || fp.op_count > kMaxPassOps) return false;
   JitShape sh{arith, R, int(env.jit_ctas)};
-  sh.tma = env.jit_tma != 0;
+  sh.copy = static_cast<JitCopy>(env.jit_copy);
   std::string src;
   try {
     src = jit_source(fp, st, ops, sh);
@@ -242,8 +242,8 @@ bool jit_try_launch(Env& env, Reg& r, const FPass& fp, const FStage* st, const F
   unsigned* status = env.d_status;
   const FOp* popv = ops + fp.op_begin;
   void* args_plain[3] = {&g, &ntiles, const_cast<FOp*>(popv)};
-  void* args_tma[4] = {&g, &ntiles, &status, const_cast<FOp*>(popv)};
-  void** args = sh.tma ? args_tma : args_plain;
+  void* args_bulk[4] = {&g, &ntiles, &status, const_cast<FOp*>(popv)};
+  void** args = sh.copy == JitCopy::Bulk ? args_bulk : args_plain;
   const int threads = 1 << (fp.k - R);
   const int64_t grid = std::min<int64_t>(fp.ntiles, int64_t(env.sms) * env.jit_ctas);
   const double bytes = std::ldexp(2.0 * (arith == Arith::F32 ? 8.0 : 16.0), r.nq);

@@ -21,23 +21,28 @@
 
 namespace qs {
 
+enum class JitCopy { Plain = 0, Bulk = 1, Async = 2 };
+
 // Parameters of one generated pass kernel.
 struct JitShape {
   Arith arith;
   int R;
   int ctas;  // resident CTAs per SM the kernel is compiled for (__launch_bounds__)
-  // tiles move by bulk (TMA) copies through two shared-memory buffers, the
-  // next tile's load overlapping the current tile's work; the kernel then
-  // takes a device status word after ntiles (bit 1: a copy did not arrive
-  // within 1 s of the GPU's global timer)
-  bool tma = false;
+  // How tiles move between global and shared memory: Plain = coalesced
+  // loads and stores through registers; Bulk = bulk (TMA) copies of the
+  // tile's contiguous chunks through two shared-memory buffers, the next
+  // tile's load overlapping the current tile's work (the kernel then takes a
+  // device status word after ntiles: bit 1 = a copy did not arrive within 1 s
+  // of the GPU's global timer); Async = the same double buffering with
+  // 16-byte asynchronous copies (cp.async) in the plain access pattern.
+  JitCopy copy = JitCopy::Plain;
 };
 
 // CUDA source of the pass kernel `qs_pass` for pass fp of a plan whose
 // stage and op arrays are st and ops (fp's indices relative to them).
 // Kernel signature: (Store* g, long long ntiles, [unsigned* status,] const
 // __grid_constant__ JitOps P) with P holding fp.op_count FOp records (the
-// status word only with sh.tma).  Throws Error (QS_E_ARG) if the pass uses a
+// status word only with JitCopy::Bulk).  Throws Error (QS_E_ARG) if the pass uses a
 // form the generator does not know.
 std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const JitShape& sh);
 

@@ -146,7 +146,9 @@ bool depends_on(uint32_t m, int i, int R) {
 
 size_t jit_smem_bytes(const FPass& fp, const JitShape& sh) {
   const size_t tile = cplx_bytes(sh.arith) * (size_t(1) << fp.k);
-  return sh.tma ? 2 * tile + 2 * sizeof(uint64_t) : tile;
+  if (sh.copy == JitCopy::Bulk) return 2 * tile + 2 * sizeof(uint64_t);
+  if (sh.copy == JitCopy::Async) return 2 * tile;
+  return tile;
 }
 
 std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const JitShape& sh) {
@@ -154,10 +156,13 @@ std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const 
   if (R < 1 || R > 5 || k < R || k > 20 || L < 1 || L > k) fail(QS_E_ARG, "jit: bad tile shape");
   if (fp.init) fail(QS_E_ARG, "jit: generated tiles are not supported");
   const int T = 1 << (k - R);
+  const bool bulk = sh.copy == JitCopy::Bulk, async = sh.copy == JitCopy::Async;
+  const bool pipelined = bulk || async;  // two buffers, tiles kept in the storage format
   const bool pack2 = store_bytes(sh.arith) == 8;  // complex64: two amplitudes per access
   const int span_log = pack2 ? (k - R + 1) : (k - R);  // amplitudes one round of accesses covers (log2)
-  if (!sh.tma && span_log < L) fail(QS_E_ARG, "jit: access round narrower than a chunk");
-  if (sh.tma && (size_t(1) << L) * store_bytes(sh.arith) % 16 != 0) fail(QS_E_ARG, "jit: chunk not 16-byte sized");
+  if (!bulk && span_log < L) fail(QS_E_ARG, "jit: access round narrower than a chunk");
+  if (bulk && (R < L || (size_t(1) << L) * store_bytes(sh.arith) % 16 != 0))
+    fail(QS_E_ARG, "jit: chunks unsuited to bulk copies");
   const int depth = pack2 ? (1 << (R - 1)) : (1 << R);
   const int cbits = span_log - L;  // chunk-index bits taken from the thread index
   auto deposit = [&](uint64_t c) {  // chunk index -> offset (bit i at tile qubit L + i)
@@ -169,19 +174,19 @@ std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const 
   const int nstage = fp.stage_end - fp.stage_begin;
   std::ostringstream s;
   s << "// fused pass: k " << k << " L " << L << " R " << R << " ops " << fp.op_count << " stages " << nstage
-    << (sh.tma ? " (bulk-copy pipeline)" : "") << "\n";
+    << (bulk ? " (bulk-copy pipeline)" : async ? " (async-copy pipeline)" : "") << "\n";
   s << "#ifdef __CUDACC_RTC__\n"
        "typedef signed char int8_t; typedef unsigned char uint8_t; typedef short int16_t;\n"
        "typedef unsigned short uint16_t; typedef int int32_t; typedef unsigned int uint32_t;\n"
        "typedef long long int64_t; typedef unsigned long long uint64_t;\n"
        "#endif\n"
        "#include \"fused_arith.cuh\"\n";
-  if (sh.tma) s << "#include \"mbarrier.cuh\"\n";
+  if (pipelined) s << "#include \"mbarrier.cuh\"\n";
   s << "namespace qs { struct JitOps { FOp o[" << (fp.op_count > 0 ? fp.op_count : 1) << "]; }; }\n"
     << "using namespace qs;\n"
     << "extern \"C\" __global__ void __launch_bounds__(" << T << ", " << sh.ctas << ")\n"
     << "qs_pass(" << store_name(sh.arith) << "* __restrict__ g, long long ntiles,\n"
-    << (sh.tma ? "        unsigned* __restrict__ status,\n" : "")
+    << (bulk ? "        unsigned* __restrict__ status,\n" : "")
     << "        const __grid_constant__ qs::JitOps P) {\n"
     << "  using A = " << arith_name(sh.arith) << ";\n"
     << "  using Cplx = A::Cplx;\n"
@@ -195,49 +200,51 @@ std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const 
     s << "    b = ((b >> " << p << ") << " << (p + 1) << ") | (b & " << hex64((uint64_t(1) << p) - 1) << ");\n";
   }
   s << "    return b;\n  };\n";
-  const int nchunk_log = k - L;
-  // warp 0 issues the copies: up to 32 lanes, no more than the CTA has
-  const int lanes_log = std::min({5, nchunk_log, k - R});
-  const std::string warp_mask = k - R >= 5 ? "0xFFFFFFFFu" : hex32((1u << (1 << (k - R))) - 1u);
-  const int per_lane = 1 << (nchunk_log - lanes_log);
   const size_t chunk_bytes = (size_t(1) << L) * store_bytes(sh.arith);
   const size_t tile_store_bytes = (size_t(1) << k) * store_bytes(sh.arith);
-  if (sh.tma) {
-    // Bulk-copy pipeline: two tile buffers; warp 0 copies tile t + 1 into
-    // one (2^(k-L) contiguous chunks of 2^L amplitudes, completing on that
-    // buffer's mbarrier) while the CTA works on tile t in the other, and
-    // stores a finished tile with bulk copies from shared memory.
+  if (!bulk) {
+    // this thread's part of the tile offset of its coalesced accesses
+    s << "  const uint32_t lt = " << (pack2 ? "2u * tid" : "tid") << ";\n"
+      << "  int64_t toff = int64_t(lt & " << hex32((1u << L) - 1u) << ");\n";
+    for (int i = 0; i < cbits; ++i)
+      s << "  toff |= int64_t((lt >> " << (L + i) << ") & 1u) << " << int(fp.q[L + i]) << ";\n";
+  }
+  // (global offset, shared index) of this thread's u-th coalesced access
+  auto acc_goff = [&](int u) { return hex64(deposit(uint64_t(u) << cbits)); };
+  if (bulk) {
+    // Bulk (TMA) copies: the tile is 2^(k-L) contiguous chunks of 2^L
+    // amplitudes; thread t copies chunks t + T u (u < 2^(R-L)) in and out, so
+    // each thread only ever overwrites chunks whose stores it issued itself.
     s << "  Cplx* const buf0 = reinterpret_cast<Cplx*>(smem_raw);\n"
       << "  Cplx* const buf1 = buf0 + " << (1 << k) << ";\n"
       << "  uint64_t* const bar = reinterpret_cast<uint64_t*>(buf0 + " << (2 << k) << ");\n"
-      << "  const uint32_t lane = tid & 31u;\n"
-      << "  int64_t coff = 0;  // this lane's chunk offset (chunk c = lane + 32 u)\n";
-    for (int i = 0; i < lanes_log; ++i)
-      s << "  coff |= int64_t((lane >> " << i << ") & 1u) << " << int(fp.q[L + i]) << ";\n";
-    s << "  auto issue_load = [&](int64_t b, Cplx* dst, uint64_t* br) {\n"
-      << "    if (lane == 0) mb::arrive_expect_tx(br, " << tile_store_bytes << "u);\n"
-      << "    __syncwarp(" << warp_mask << ");\n";
-    if (lanes_log < 5) s << "    if (lane < " << (1 << lanes_log) << "u) {\n";
-    else s << "    {\n";
-    for (int u = 0; u < per_lane; ++u) {
-      const uint64_t cu = uint64_t(u) << lanes_log;
-      s << "      mb::bulk_load(reinterpret_cast<Store*>(dst) + ((lane + " << cu << "u) << " << L << "), g + b + coff + "
+      << "  int64_t coff = 0;  // this thread's chunk offset\n";
+    for (int i = 0; i < k - R; ++i)
+      s << "  coff |= int64_t((tid >> " << i << ") & 1u) << " << int(fp.q[L + i]) << ";\n";
+    const int per = 1 << (R - L);
+    s << "  auto issue_load = [&](int64_t b, Cplx* dst, uint64_t* br) {\n";
+    for (int u = 0; u < per; ++u) {
+      const uint64_t cu = uint64_t(u) << (k - R);
+      s << "    mb::bulk_load(reinterpret_cast<Store*>(dst) + ((tid + " << cu << "u) << " << L << "), g + b + coff + "
         << hex64(deposit(cu)) << ", " << chunk_bytes << "u, br);\n";
     }
-    s << "    }\n  };\n";
-    s << "  auto issue_store = [&](int64_t b, Cplx* src) {\n";
-    if (lanes_log < 5) s << "    if (lane < " << (1 << lanes_log) << "u) {\n";
-    else s << "    {\n";
-    for (int u = 0; u < per_lane; ++u) {
-      const uint64_t cu = uint64_t(u) << lanes_log;
-      s << "      mb::bulk_store(g + b + coff + " << hex64(deposit(cu)) << ", reinterpret_cast<Store*>(src) + ((lane + "
+    s << "  };\n  auto issue_store = [&](int64_t b, Cplx* src) {\n";
+    for (int u = 0; u < per; ++u) {
+      const uint64_t cu = uint64_t(u) << (k - R);
+      s << "    mb::bulk_store(g + b + coff + " << hex64(deposit(cu)) << ", reinterpret_cast<Store*>(src) + ((tid + "
         << cu << "u) << " << L << "), " << chunk_bytes << "u);\n";
     }
-    s << "      mb::bulk_commit();\n    }\n  };\n";
+    s << "    mb::bulk_commit();\n  };\n";
+    // thread 0 announces the bytes before anyone's copy can complete on the
+    // barrier (the barrier after it orders the copies behind it)
     s << "  if (tid == 0) {\n    mb::init(&bar[0], 1);\n    mb::init(&bar[1], 1);\n    mb::fence_init();\n  }\n"
       << "  __syncthreads();\n"
       << "  int64_t tau = blockIdx.x;\n"
-      << "  if (tid < 32 && tau < ntiles) issue_load(tile_base(tau), buf0, &bar[0]);\n"
+      << "  if (tau < ntiles) {\n"
+      << "    if (tid == 0) mb::arrive_expect_tx(&bar[0], " << tile_store_bytes << "u);\n"
+      << "    __syncthreads();\n"
+      << "    issue_load(tile_base(tau), buf0, &bar[0]);\n"
+      << "  }\n"
       << "  uint32_t parity = 0;  // bit i: parity of buffer i's next phase\n"
       << "  bool pend[2] = {tau < ntiles, false};\n"
       << "  bool ok = true;\n"
@@ -246,23 +253,49 @@ std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const 
       << "    Cplx* const tile = cur ? buf1 : buf0;\n"
       << "    const int64_t base = tile_base(tau);\n"
       << "    const bool more = tau + int64_t(gridDim.x) < ntiles;\n"
-      << "    if (tid < 32) {\n"
-      << "      mb::bulk_wait_read();  // the other buffer's stores have read it\n"
-      << "      if (more) issue_load(tile_base(tau + gridDim.x), cur ? buf0 : buf1, &bar[cur ^ 1]);\n"
+      << "    if (more) {\n"
+      << "      mb::bulk_wait_read();  // this thread's stores from the other buffer have read it\n"
+      << "      if (tid == 0) mb::arrive_expect_tx(&bar[cur ^ 1], " << tile_store_bytes << "u);\n"
+      << "      __syncthreads();\n"
+      << "      issue_load(tile_base(tau + gridDim.x), cur ? buf0 : buf1, &bar[cur ^ 1]);\n"
       << "    }\n"
       << "    pend[cur ^ 1] = more;\n"
       << "    const bool got = mb::wait(&bar[cur], (parity >> cur) & 1u);\n"
       << "    if (!__syncthreads_and(got)) {\n      ok = false;\n      break;\n    }\n"
       << "    parity ^= 1u << cur;\n"
       << "    pend[cur] = false;\n";
+  } else if (async) {
+    // Async copies (cp.async, 16 bytes a thread): the same coalesced
+    // accesses as the plain load, into the other buffer, one group per tile.
+    s << "  Cplx* const buf0 = reinterpret_cast<Cplx*>(smem_raw);\n"
+      << "  Cplx* const buf1 = buf0 + " << (1 << k) << ";\n"
+      << "  auto issue_load = [&](int64_t b, Cplx* dst) {\n"
+      << "    const int64_t gb = b + toff;\n";
+    for (int u = 0; u < depth; ++u) {
+      if (pack2)
+        s << "    mb::async_copy16(reinterpret_cast<float4*>(dst) + (tid + " << u * T
+          << "u), reinterpret_cast<const float4*>(g) + ((gb + " << acc_goff(u) << ") >> 1));\n";
+      else
+        s << "    mb::async_copy16(reinterpret_cast<Store*>(dst) + (tid + " << u * T << "u), g + gb + " << acc_goff(u)
+          << ");\n";
+    }
+    s << "    asm volatile(\"cp.async.commit_group;\" ::: \"memory\");\n  };\n"
+      << "  int64_t tau = blockIdx.x;\n"
+      << "  if (tau < ntiles) issue_load(tile_base(tau), buf0);\n"
+      << "  for (int it = 0; tau < ntiles; ++it, tau += gridDim.x) {\n"
+      << "    const int cur = it & 1;\n"
+      << "    Cplx* const tile = cur ? buf1 : buf0;\n"
+      << "    const int64_t base = tile_base(tau);\n"
+      << "    if (tau + int64_t(gridDim.x) < ntiles) {\n"
+      << "      issue_load(tile_base(tau + gridDim.x), cur ? buf0 : buf1);\n"
+      << "      asm volatile(\"cp.async.wait_group 1;\" ::: \"memory\");\n"
+      << "    } else {\n"
+      << "      asm volatile(\"cp.async.wait_group 0;\" ::: \"memory\");\n"
+      << "    }\n"
+      << "    __syncthreads();\n";
   } else {
-    s << "  Cplx* __restrict__ tile = reinterpret_cast<Cplx*>(smem_raw);\n";
-    // this thread's part of the tile offset of its accesses
-    s << "  const uint32_t lt = " << (pack2 ? "2u * tid" : "tid") << ";\n"
-      << "  int64_t toff = int64_t(lt & " << hex32((1u << L) - 1u) << ");\n";
-    for (int i = 0; i < cbits; ++i)
-      s << "  toff |= int64_t((lt >> " << (L + i) << ") & 1u) << " << int(fp.q[L + i]) << ";\n";
-    s << "  for (int64_t tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {\n"
+    s << "  Cplx* __restrict__ tile = reinterpret_cast<Cplx*>(smem_raw);\n"
+      << "  for (int64_t tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {\n"
       << "    const int64_t base = tile_base(tau);\n";
     // tile load: all accesses of the round in flight, then into shared memory
     if (pack2) {
@@ -270,13 +303,12 @@ std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const 
         << "      float4* t4 = reinterpret_cast<float4*>(tile);\n"
         << "      const int64_t gb = base + toff;\n";
       for (int u = 0; u < depth; ++u)
-        s << "      const float4 ld" << u << " = g4[(gb + " << hex64(deposit(uint64_t(u) << cbits)) << ") >> 1];\n";
+        s << "      const float4 ld" << u << " = g4[(gb + " << acc_goff(u) << ") >> 1];\n";
       for (int u = 0; u < depth; ++u) s << "      t4[tid + " << u * T << "u] = ld" << u << ";\n";
       s << "    }\n";
     } else {
       s << "    {\n      const int64_t gb = base + toff;\n";
-      for (int u = 0; u < depth; ++u)
-        s << "      const double2 ld" << u << " = g[gb + " << hex64(deposit(uint64_t(u) << cbits)) << "];\n";
+      for (int u = 0; u < depth; ++u) s << "      const double2 ld" << u << " = g[gb + " << acc_goff(u) << "];\n";
       for (int u = 0; u < depth; ++u) s << "      tile[tid + " << u * T << "u] = A::from_store(ld" << u << ");\n";
       s << "    }\n";
     }
@@ -284,16 +316,19 @@ std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const 
   }
   for (int si = fp.stage_begin; si < fp.stage_end; ++si) {
     const FStage& S = st[si];
-    // with the bulk-copy pipeline the tile arrives and leaves in the storage
+    // with a copy pipeline the tile arrives and leaves in the storage
     // format: the first stage converts on reading, the last on writing
-    const bool first_io = sh.tma && si == fp.stage_begin;
-    const bool last_io = sh.tma && si == fp.stage_end - 1;
+    const bool first_io = pipelined && si == fp.stage_begin;
+    const bool last_io = pipelined && si == fp.stage_end - 1;
     uint32_t poff[8] = {}, cpm = 0;
     for (int i = 0; i < R; ++i) {
       if (S.pbits[i] >= k) fail(QS_E_ARG, "jit: register position outside the tile");
       poff[i] = 1u << S.pbits[i];
       if ((S.copy >> i) & 1u) cpm |= poff[i];
     }
+    // complex64 with register bit 0 at local position 0: amplitudes j and
+    // j + 1 are neighbours in shared memory, one 16-byte access
+    const bool vec2 = pack2 && S.pbits[0] == 0 && !(cpm & 1u);
     s << "    {\n      uint32_t tl = tid;\n";
     for (int i = 0; i < R; ++i) {
       const int p = S.pbits[i];
@@ -306,11 +341,20 @@ std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const 
       for (int i = 0; i < R; ++i)
         if (j & (1 << i)) o |= poff[i];
       off[size_t(j)] = o;
-      if (first_io)
+    }
+    for (int j = 0; j < (1 << R); ++j) {
+      const uint32_t o = off[size_t(j)];
+      if (vec2) {
+        if (j & 1) continue;
+        s << "      {\n        const float4 w = *reinterpret_cast<const float4*>(tile + (tl | " << hex32(o & ~cpm)
+          << "));\n        v[" << j << "] = make_float2(w.x, w.y);\n        v[" << j + 1
+          << "] = make_float2(w.z, w.w);\n      }\n";
+      } else if (first_io) {
         s << "      v[" << j << "] = A::from_store(reinterpret_cast<const Store*>(tile)[tl | " << hex32(o & ~cpm)
           << "]);\n";
-      else
+      } else {
         s << "      v[" << j << "] = tile[tl | " << hex32(o & ~cpm) << "];\n";
+      }
     }
     // Sign flips (CZ, multi-controlled phase flips) are kept pending, as
     // the interpreter keeps them: an unconditional compile-time mask, and
@@ -378,21 +422,26 @@ std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const 
     }
     apply_unc();
     for (size_t i = 0; i < pend.size(); ++i) apply_pend(i);
-    if (last_io) {
-      // (each thread writes exactly the slots it read: converting in place
-      // needs no barrier)
-      for (int j = 0; j < (1 << R); ++j)
-        s << "      reinterpret_cast<Store*>(tile)[tl | " << hex32(off[size_t(j)]) << "] = A::to_store(v[" << j
-          << "]);\n";
-    } else {
-      for (int j = 0; j < (1 << R); ++j) s << "      tile[tl | " << hex32(off[size_t(j)]) << "] = v[" << j << "];\n";
+    // (each thread writes exactly the slots it read: converting in place
+    // needs no barrier)
+    for (int j = 0; j < (1 << R); ++j) {
+      const uint32_t o = off[size_t(j)];
+      if (vec2) {
+        if (j & 1) continue;
+        s << "      *reinterpret_cast<float4*>(tile + (tl | " << hex32(o) << ")) = make_float4(v[" << j << "].x, v["
+          << j << "].y, v[" << j + 1 << "].x, v[" << j + 1 << "].y);\n";
+      } else if (last_io) {
+        s << "      reinterpret_cast<Store*>(tile)[tl | " << hex32(o) << "] = A::to_store(v[" << j << "]);\n";
+      } else {
+        s << "      tile[tl | " << hex32(o) << "] = v[" << j << "];\n";
+      }
     }
     s << "    }\n    __syncthreads();\n";
   }
-  if (sh.tma) {
+  if (bulk) {
     s << "    mb::fence_proxy_async();\n"
       << "    __syncthreads();\n"
-      << "    if (tid < 32) issue_store(base, tile);\n"
+      << "    issue_store(base, tile);\n"
       << "  }\n"
       << "  if (!ok) {\n"
       << "    // a copy did not arrive within the bound: report it, and wait (bounded)\n"
@@ -401,26 +450,29 @@ std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const 
       << "    for (int i = 0; i < 2; ++i)\n"
       << "      if (pend[i]) (void)mb::wait(&bar[i], (parity >> i) & 1u);\n"
       << "  }\n"
-      << "  if (tid < 32) mb::bulk_wait();\n"
+      << "  mb::bulk_wait();\n"
       << "}\n";
-  } else {
-    s << "    // tile store\n";
-    if (pack2) {
-      s << "    {\n      float4* __restrict__ g4 = reinterpret_cast<float4*>(g);\n"
-        << "      const float4* t4 = reinterpret_cast<const float4*>(tile);\n"
-        << "      const int64_t gb = base + toff;\n";
-      for (int u = 0; u < depth; ++u)
-        s << "      g4[(gb + " << hex64(deposit(uint64_t(u) << cbits)) << ") >> 1] = t4[tid + " << u * T << "u];\n";
-      s << "    }\n";
-    } else {
-      s << "    {\n      const int64_t gb = base + toff;\n";
-      for (int u = 0; u < depth; ++u)
-        s << "      g[gb + " << hex64(deposit(uint64_t(u) << cbits)) << "] = A::to_store(tile[tid + " << u * T
-          << "u]);\n";
-      s << "    }\n";
-    }
-    s << "    __syncthreads();\n  }\n}\n";
+    return s.str();
   }
+  s << "    // tile store\n";
+  if (pack2) {
+    s << "    {\n      float4* __restrict__ g4 = reinterpret_cast<float4*>(g);\n"
+      << "      const float4* t4 = reinterpret_cast<const float4*>(tile);\n"
+      << "      const int64_t gb = base + toff;\n";
+    for (int u = 0; u < depth; ++u)
+      s << "      g4[(gb + " << acc_goff(u) << ") >> 1] = t4[tid + " << u * T << "u];\n";
+    s << "    }\n";
+  } else {
+    s << "    {\n      const int64_t gb = base + toff;\n";
+    for (int u = 0; u < depth; ++u) {
+      if (async)  // already in the storage format
+        s << "      g[gb + " << acc_goff(u) << "] = reinterpret_cast<const Store*>(tile)[tid + " << u * T << "u];\n";
+      else
+        s << "      g[gb + " << acc_goff(u) << "] = A::to_store(tile[tid + " << u * T << "u]);\n";
+    }
+    s << "    }\n";
+  }
+  s << "    __syncthreads();\n  }\n}\n";
   return s.str();
 }
 

@@ -1,8 +1,8 @@
-// Shared-memory barriers and bulk (TMA) copies between global and shared
-// memory, as inline PTX (sm_90 and later; used on sm_103a).  Every wait is
-// bounded by the GPU's global timer, so a copy or an arrival that never
-// comes makes the caller report an error instead of hanging.  Compiles
-// under NVRTC as well as nvcc.
+// Shared-memory barriers, bulk (TMA) copies and asynchronous copies between
+// global and shared memory, as inline PTX (sm_90 and later; used on
+// sm_103a).  Every barrier wait is bounded by the GPU's global timer, so a
+// copy or an arrival that never comes makes the caller report an error
+// instead of hanging.  Compiles under NVRTC as well as nvcc.
 #pragma once
 #ifndef __CUDACC_RTC__
 #include <cstdint>
@@ -82,6 +82,12 @@ __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.w
 
 // Waits until this thread's committed bulk stores are complete.
 __device__ __forceinline__ void bulk_wait() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// 16-byte asynchronous copy global -> shared (cp.async, cached in L2 only);
+// completes in this thread's cp.async group (commit / wait_group).
+__device__ __forceinline__ void async_copy16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
 
 // Orders this thread's earlier shared-memory accesses before later bulk
 // copies (async proxy).

@@ -133,7 +133,9 @@ struct Env {
   int64_t jit = 2;
   int64_t jit_min_qubits = 20;
   int64_t jit_ctas = 2;
-  int64_t jit_tma = 0;  // generated kernels move tiles by bulk copies, double-buffered
+  // how generated kernels move tiles: 0 coalesced loads / stores, 1 bulk
+  // (TMA) copies double-buffered, 2 asynchronous copies double-buffered
+  int64_t jit_copy = 0;
   // IEEE-FP64 passes are bound by the FP64 pipe, where the interpreting
   // kernel measured faster (30 qubits: 83.4 vs 88.3 ms a pass): they use
   // generated kernels only when this is 1

@@ -20,6 +20,7 @@
 #include <cstring>
 #include <deque>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -72,6 +73,10 @@ struct Server {
   bool stop = false;
   std::thread th;
   int64_t next_ticket = 1;
+  // admission policy (0 = none): queue length past which serveSubmit
+  // refuses, queue wait after which a request is shed
+  int64_t max_queue = 0, max_queue_us = 0;
+  int64_t shed = 0, refused = 0;
   // the device's default pool: its release threshold before the server
   // raised it (restored, and the cached blocks released, when it stops)
   cudaMemPool_t pool = nullptr;
@@ -157,6 +162,26 @@ void scheduler(Server* S) {
       S->used -= r->bytes;
       s->cur = nullptr;
       s->gpu_done.store(false);
+      S->done_cv.notify_all();
+    }
+    // shedding: requests that waited longer than the bound leave the queue
+    // with QS_E_BUSY (admitted requests then never wait longer)
+    if (S->max_queue_us > 0 && !S->queue.empty()) {
+      const Clock::time_point now = Clock::now();
+      for (auto it = S->queue.begin(); it != S->queue.end();) {
+        Request* r = *it;
+        if (us_between(r->submit, now) > double(S->max_queue_us)) {
+          r->result.status = QS_E_BUSY;
+          r->result.slot = -1;
+          r->result.queuedUs = us_between(r->submit, now);
+          r->result.latencyUs = r->result.queuedUs;
+          r->finished = true;
+          ++S->shed;
+          it = S->queue.erase(it);
+        } else {
+          ++it;
+        }
+      }
       S->done_cv.notify_all();
     }
     // admissions: arrival order, while a slot is free and the budget allows
@@ -314,6 +339,11 @@ int serveSubmit(QSServer h, const QSRequest* req, int64_t* ticket) {
         delete r;
         fail(QS_E_ARG, "server is shutting down");
       }
+      if (S.max_queue > 0 && int64_t(S.queue.size()) >= S.max_queue) {
+        ++S.refused;
+        delete r;
+        fail(QS_E_BUSY, "the server's queue is full (max_queue)");
+      }
       r->ticket = S.next_ticket++;
       S.tickets[r->ticket] = r;
       S.queue.push_back(r);
@@ -337,6 +367,35 @@ int servePoll(QSServer h, int64_t ticket, QSResult* out, int64_t timeoutUs) {
     *out = r->result;
     S.tickets.erase(it);
     delete r;
+  });
+}
+
+int serveSetOption(QSServer h, const char* key, int64_t value) {
+  return guarded_call([&] {
+    if (!key) fail(QS_E_ARG, "null key");
+    Server& S = server_of(h);
+    const std::string k(key);
+    if (value < 0) fail(QS_E_ARG, k + " must be >= 0");
+    std::lock_guard<std::mutex> lk(S.mu);
+    if (k == "max_queue") S.max_queue = value;
+    else if (k == "max_queue_us") S.max_queue_us = value;
+    else fail(QS_E_ARG, "unknown server option " + k);
+    S.cv.notify_one();
+  });
+}
+
+int serveGetOption(QSServer h, const char* key, int64_t* value) {
+  return guarded_call([&] {
+    if (!key || !value) fail(QS_E_ARG, "null pointer");
+    Server& S = server_of(h);
+    const std::string k(key);
+    std::lock_guard<std::mutex> lk(S.mu);
+    if (k == "max_queue") *value = S.max_queue;
+    else if (k == "max_queue_us") *value = S.max_queue_us;
+    else if (k == "queued") *value = int64_t(S.queue.size());
+    else if (k == "shed") *value = S.shed;
+    else if (k == "refused") *value = S.refused;
+    else fail(QS_E_ARG, "unknown server option " + k);
   });
 }
 

@@ -23,7 +23,7 @@ QS_C64, QS_C128 = 64, 128
 ERRORS = {
     0: "QS_OK", -1: "QS_E_QUBIT", -2: "QS_E_DUP", -3: "QS_E_UNITARY", -4: "QS_E_PROB",
     -5: "QS_E_NOT_DENSITY", -6: "QS_E_ZERO_PROB", -7: "QS_E_NOMEM", -8: "QS_E_HANDLE",
-    -9: "QS_E_CUDA", -10: "QS_E_TIMEOUT", -11: "QS_E_ARG",
+    -9: "QS_E_CUDA", -10: "QS_E_TIMEOUT", -11: "QS_E_ARG", -12: "QS_E_BUSY",
 }
 OP_CODES = {"H": 1, "X": 2, "SX": 3, "SY": 4, "T": 5, "PHASE": 6, "COMPACT": 7,
             "UNITARY": 8, "CNOT": 9, "CUNITARY": 10, "CZ": 11, "MCPF": 12,
@@ -157,6 +157,8 @@ EXTRA_SIGNATURES: dict = {
     "serveCreate": [QuESTEnv, _I, _I64, _I, _P(QSServer)],
     "serveSubmit": [QSServer, _P(QSRequest), _P(_I64)],
     "servePoll": [QSServer, _I64, _P(QSResult), _I64],
+    "serveSetOption": [QSServer, ctypes.c_char_p, _I64],
+    "serveGetOption": [QSServer, ctypes.c_char_p, _P(_I64)],
     "serveDestroy": [QSServer],
 }
 
@@ -582,6 +584,16 @@ def servePoll(server, ticket: int, timeoutUs: int = 60_000_000) -> dict:
     return {"status": res.status, "slot": res.slot, "totalProb": res.totalProb,
             "probOutcome0": res.probOutcome0, "queuedUs": res.queuedUs,
             "latencyUs": res.latencyUs}
+
+
+def serveSetOption(server, key: str, value: int):
+    _check(LIB.serveSetOption(server, key.encode(), int(value)))
+
+
+def serveGetOption(server, key: str) -> int:
+    v = ctypes.c_int64()
+    _check(LIB.serveGetOption(server, key.encode(), ctypes.byref(v)))
+    return v.value
 
 
 def serveDestroy(server):

@@ -6,13 +6,13 @@
 // Reads QSOp records from stdin, plans them for a register of the given
 // shape, generates the pass kernel of every pass and compiles it with NVRTC
 // for sm_103a.  Prints "JIT passes P compiled C distinct D seconds S" and,
-// for a failure, the compiler log.  tma = 1 generates the bulk-copy
-// pipeline form.  Argument 8 caps how many distinct kernels are compiled
+// for a failure, the compiler log.  copy = 1 / 2 generates the bulk-copy /
+// async-copy pipeline form.  Argument 8 caps how many distinct kernels are compiled
 // (all are generated); with a file name as argument 9 the source of the
 // first pass is written there.  Compiles run on up to 8
 // host threads.
 //
-// usage: jit_check n density prec arith k_req ctas tma [max_compile [source_out]]
+// usage: jit_check n density prec arith k_req ctas copy [max_compile [source_out]]
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -37,12 +37,12 @@ KTimer::~KTimer() {}
 
 int main(int argc, char** argv) {
   if (argc < 8) {
-    std::fprintf(stderr, "usage: jit_check n density prec arith k_req ctas tma [max_compile [source_out]]\n");
+    std::fprintf(stderr, "usage: jit_check n density prec arith k_req ctas copy [max_compile [source_out]]\n");
     return 2;
   }
   const int n = std::atoi(argv[1]), density = std::atoi(argv[2]), prec = std::atoi(argv[3]);
   const int arith = std::atoi(argv[4]), k_req = std::atoi(argv[5]), ctas = std::atoi(argv[6]);
-  const bool tma = std::atoi(argv[7]) != 0;
+  const int copy = std::atoi(argv[7]);
   Env env;
   env.arith = arith;
   Reg r;
@@ -67,7 +67,7 @@ int main(int argc, char** argv) {
   const int R = pl.arith == Arith::F32 ? 5 : 4;
   const int max_compile = argc > 8 ? std::atoi(argv[8]) : 1 << 30;
   JitShape shape{pl.arith, R, ctas};
-  shape.tma = tma;
+  shape.copy = static_cast<JitCopy>(copy);
   std::set<std::string> distinct;
   std::vector<std::string> todo;
   for (size_t i = 0; i < pl.fps.size(); ++i) {

@@ -132,3 +132,50 @@ def test_invalid_requests_and_bounded_poll(Q, env):
         assert e.value.name == "QS_E_HANDLE"
     finally:
         Q.serveDestroy(srv)
+
+
+def test_admission_policy_sheds_and_refuses(Q, env):
+    """Past saturation: with a queue-wait bound, requests stuck behind a long
+    one are shed (QS_E_BUSY) instead of waiting; with a queue-length bound,
+    submissions are refused while the queue is full.  The long request and
+    the ones admitted in time still complete correctly."""
+    long_ops = C.random_circuit(27, 40, 77, extras=True)
+    short = [C.random_circuit(10, 6, 900 + i) for i in range(6)]
+    srv = Q.serveCreate(env, slots=1, budgetBytes=1 << 34)
+    try:
+        Q.serveSetOption(srv, "max_queue_us", 20_000)
+        t_long = Q.serveSubmit(srv, long_ops, 27, 128)
+        ts = [Q.serveSubmit(srv, ops, 10, 64) for ops in short]
+        r_long = Q.servePoll(srv, t_long, timeoutUs=120_000_000)
+        rs = [Q.servePoll(srv, t, timeoutUs=120_000_000) for t in ts]
+        assert r_long["status"] == 0 and abs(r_long["totalProb"] - 1) <= PROB_TOL
+        names = [Q.ERRORS[r["status"]] for r in rs]
+        assert "QS_E_BUSY" in names, names
+        assert Q.serveGetOption(srv, "shed") == names.count("QS_E_BUSY")
+        for r, ops in zip(rs, short):
+            if r["status"] == 0:
+                assert abs(r["totalProb"] - 1) <= 1e-5
+            else:
+                assert r["slot"] == -1 and r["queuedUs"] >= 20_000
+        # back-pressure: two may wait, the third is refused at submission
+        Q.serveSetOption(srv, "max_queue_us", 0)
+        Q.serveSetOption(srv, "max_queue", 2)
+        t_long = Q.serveSubmit(srv, long_ops, 27, 128)
+        import time
+        deadline = time.time() + 30
+        while Q.serveGetOption(srv, "queued") > 0 and time.time() < deadline:
+            time.sleep(0.001)          # the long one is admitted (leaves the queue)
+        t1 = Q.serveSubmit(srv, short[0], 10, 64)
+        t2 = Q.serveSubmit(srv, short[1], 10, 64)
+        if Q.serveGetOption(srv, "queued") == 2:
+            with pytest.raises(Q.QSimError) as e:
+                Q.serveSubmit(srv, short[2], 10, 64)
+            assert e.value.name == "QS_E_BUSY"
+            assert Q.serveGetOption(srv, "refused") == 1
+        for t in (t_long, t1, t2):
+            assert Q.servePoll(srv, t, timeoutUs=120_000_000)["status"] == 0
+        with pytest.raises(Q.QSimError) as e:
+            Q.serveSetOption(srv, "max_queue", -1)
+        assert e.value.name == "QS_E_ARG"
+    finally:
+        Q.serveDestroy(srv)

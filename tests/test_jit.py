@@ -42,13 +42,13 @@ def harness(tmp_path_factory):
     return exe
 
 
-def run(exe, n, ops, density=False, prec=128, arith=0, k_req=0, ctas=2, max_compile=4, tma=0):
+def run(exe, n, ops, density=False, prec=128, arith=0, k_req=0, ctas=2, max_compile=4, copy=0):
     arr, cnt = Q.to_qsops(ops)
     data = ctypes.string_at(ctypes.addressof(arr), ctypes.sizeof(Q.QSOp) * cnt)
     env = dict(os.environ)
     env["LD_LIBRARY_PATH"] = os.path.join(CUDA, "lib64") + ":" + env.get("LD_LIBRARY_PATH", "")
     r = subprocess.run([exe, str(n), str(int(density)), str(prec), str(arith), str(k_req), str(ctas),
-                        str(tma), str(max_compile)], input=data, capture_output=True, timeout=600, env=env)
+                        str(copy), str(max_compile)], input=data, capture_output=True, timeout=600, env=env)
     out = r.stdout.decode(errors="replace")
     assert r.returncode == 0, out[-3000:] + r.stderr.decode(errors="replace")[-2000:]
     head = out.strip().splitlines()[-1]
@@ -102,16 +102,18 @@ def test_three_ctas_per_sm_compiles(harness):
     assert compiled == 2
 
 
+@pytest.mark.parametrize("copy", [1, 2])
 @pytest.mark.parametrize("prec,arith,k", [(64, 0, 12), (64, 0, 13), (128, 0, 11), (128, 1, 11)])
-def test_bulk_copy_pipeline_compiles(harness, prec, arith, k):
-    """The bulk-copy (TMA) double-buffered form of the generated kernels."""
-    passes, compiled, _ = run(harness, 26, C.workload_30q(26), prec=prec, arith=arith, k_req=k, tma=1,
+def test_copy_pipelines_compile(harness, prec, arith, k, copy):
+    """The bulk-copy (TMA) and async-copy double-buffered forms."""
+    passes, compiled, _ = run(harness, 26, C.workload_30q(26), prec=prec, arith=arith, k_req=k, copy=copy,
                               max_compile=2)
     assert compiled == 2
 
 
-def test_bulk_copy_pipeline_density_small_tiles(harness):
+@pytest.mark.parametrize("copy", [1, 2])
+def test_copy_pipelines_density_small_tiles(harness, copy):
     N = 7
     ops = C.with_noise(C.random_circuit(N, 10, 31, extras=True) + extras(N, 3), 0.3, 0.6)
-    passes, compiled, _ = run(harness, N, ops, density=True, k_req=9, tma=1, max_compile=2)
+    passes, compiled, _ = run(harness, N, ops, density=True, k_req=9, copy=copy, max_compile=2)
     assert compiled >= 1
