@@ -144,8 +144,19 @@ int qsDiagBoundedWait(QuESTEnv env, int timeoutUs);
  *                   use the interpreting kernel until ready (default).  Both
  *                   kernels give bit-identical amplitudes.  Applies to
  *                   complex64 and double-float passes; IEEE-FP64 passes
- *                   only with "jit_fp64" = 1.  "jit_ctas": resident CTAs per
- *                   SM the generated kernels are built for (1..4, default 2).
+ *                   only with "jit_fp64" = 1 (they are FP64-pipe bound,
+ *                   where the interpreting kernel measured faster).
+ *                   "jit_copy": how the generated kernels move tiles between
+ *                   HBM and shared memory: 0 = coalesced loads and stores,
+ *                   1 = bulk (TMA) copies of the tile's contiguous chunks,
+ *                   double-buffered (the next tile's copy overlaps the
+ *                   current tile's work; waits bounded, QS_E_TIMEOUT), 2 =
+ *                   16-byte async copies (cp.async), double-buffered, -1 =
+ *                   by arithmetic (default: 2 for complex64, with tiles of
+ *                   2^12 amplitudes, 0 otherwise).  "jit_ctas": resident
+ *                   CTAs per SM the generated kernels are built for (1..4,
+ *                   0 = by shape, the default: 3 for double-buffered 2^12
+ *                   complex64 tiles, else 2).
  *                   Read-only counters: "jit_launches", "jit_rejected",
  *                   "jit_ready", "jit_pending", "jit_failed",
  *                   "jit_compile_ms".

@@ -320,13 +320,14 @@ int setEnvOption(QuESTEnv e, const char* key, int64_t value) {
       env.plan_cache_on = value;
       if (!value) env.plan_cache.reset();
     } else if (k == "jit_copy") {
-      if (value < 0 || value > 2) fail(QS_E_ARG, "jit_copy must be 0 (plain), 1 (bulk) or 2 (async)");
+      if (value < -1 || value > 2)
+        fail(QS_E_ARG, "jit_copy must be -1 (by arithmetic), 0 (plain), 1 (bulk) or 2 (async)");
       env.jit_copy = value;
     } else if (k == "jit_fp64") {
       if (value != 0 && value != 1) fail(QS_E_ARG, "jit_fp64 must be 0 or 1");
       env.jit_fp64 = value;
     } else if (k == "jit_ctas") {
-      if (value < 1 || value > 4) fail(QS_E_ARG, "jit_ctas must be in 1..4");
+      if (value < 0 || value > 4) fail(QS_E_ARG, "jit_ctas must be 0 (by shape) or 1..4");
       env.jit_ctas = value;
     } else {
       fail(QS_E_ARG, "unknown option " + k);

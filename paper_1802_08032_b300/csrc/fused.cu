@@ -74,10 +74,12 @@ void put(std::string& k, const T& v) {
   k.append(reinterpret_cast<const char*>(&v), sizeof(T));
 }
 
-std::string plan_key(const Reg& r, const std::vector<GateOp>& seg, uint64_t zero_in, std::complex<double> scale) {
+std::string plan_key(const Reg& r, const std::vector<GateOp>& seg, int k_req, uint64_t zero_in,
+                     std::complex<double> scale) {
   const Env& env = *r.env;
   std::string k;
   k.reserve(64 + seg.size() * 96);
+  put(k, k_req);
   put(k, r.nq);
   put(k, r.n);
   put(k, r.density);
@@ -97,17 +99,20 @@ std::string plan_key(const Reg& r, const std::vector<GateOp>& seg, uint64_t zero
   return k;
 }
 
-// build_plan through the env's plan cache.
+// build_plan through the env's plan cache.  Passes that will run as
+// generated kernels with a copy pipeline get tiles that leave room for two
+// buffers (unless the env fixes the tile size).
 void cached_plan(Reg& r, const std::vector<GateOp>& seg, uint64_t zero_in, std::complex<double> scale,
                  RegPlan& out) {
   Env& env = *r.env;
+  const int k_req = env.tile_qubits > 0 ? 0 : jit_tile_cap(env, r, arith_of(r));
   if (!env.plan_cache_on) {
-    build_plan(r, seg, 0, zero_in, scale, out);
+    build_plan(r, seg, k_req, zero_in, scale, out);
     return;
   }
   if (!env.plan_cache) env.plan_cache = std::make_shared<PlanCacheImpl>();
   PlanCacheImpl& c = *static_cast<PlanCacheImpl*>(env.plan_cache.get());
-  std::string key = plan_key(r, seg, zero_in, scale);
+  std::string key = plan_key(r, seg, k_req, zero_in, scale);
   auto it = c.map.find(key);
   if (it != c.map.end()) {
     it->second.used = ++c.tick;
@@ -116,7 +121,7 @@ void cached_plan(Reg& r, const std::vector<GateOp>& seg, uint64_t zero_in, std::
     ++env.plan_cache_hits;
     return;
   }
-  build_plan(r, seg, 0, zero_in, scale, out);
+  build_plan(r, seg, k_req, zero_in, scale, out);
   if (c.map.size() >= PlanCacheImpl::kEntries) {
     auto lru = c.map.begin();
     for (auto e = c.map.begin(); e != c.map.end(); ++e)

@@ -219,11 +219,11 @@ bool jit_compile_cubin(const std::string& src, std::vector<char>& cubin, std::st
 
 bool jit_try_launch(Env& env, Reg& r, const FPass& fp, const FStage* st, const FOp* ops, Arith arith, int R,
                     double flops, double alu, const char* name) {
-  if (env.jit == 0 || r.nq < env.jit_min_qubits || fp.init) return false;
-  if (arith == Arith::F64 && env.jit_fp64 == 0) return false;
+  if (!jit_wanted(env, r, arith) || fp.init) return false;
   if (fp.op_count <= 0 || fp.op_count > kMaxPassOps) return false;
-  JitShape sh{arith, R, int(env.jit_ctas)};
-  sh.copy = static_cast<JitCopy>(env.jit_copy);
+  const JitCopy copy = jit_copy_mode(env, arith);
+  JitShape sh{arith, R, jit_ctas_for(env, fp, arith, copy)};
+  sh.copy = copy;
   std::string src;
   try {
     src = jit_source(fp, st, ops, sh);
@@ -245,7 +245,7 @@ bool jit_try_launch(Env& env, Reg& r, const FPass& fp, const FStage* st, const F
   void* args_bulk[4] = {&g, &ntiles, &status, const_cast<FOp*>(popv)};
   void** args = sh.copy == JitCopy::Bulk ? args_bulk : args_plain;
   const int threads = 1 << (fp.k - R);
-  const int64_t grid = std::min<int64_t>(fp.ntiles, int64_t(env.sms) * env.jit_ctas);
+  const int64_t grid = std::min<int64_t>(fp.ntiles, int64_t(env.sms) * sh.ctas);
   const double bytes = std::ldexp(2.0 * (arith == Arith::F32 ? 8.0 : 16.0), r.nq);
   KTimer kt(env, name, bytes, flops, 1, alu);
   QS_CUDA(cudaLaunchKernel(reinterpret_cast<const void*>(e->kern), dim3(unsigned(grid)), dim3(unsigned(threads)),

@@ -132,10 +132,11 @@ struct Env {
   // registers of at least jit_min_qubits stored qubits; CTAs per SM
   int64_t jit = 2;
   int64_t jit_min_qubits = 20;
-  int64_t jit_ctas = 2;
+  int64_t jit_ctas = 0;  // 0 = by shape (see jit_shape_for)
   // how generated kernels move tiles: 0 coalesced loads / stores, 1 bulk
-  // (TMA) copies double-buffered, 2 asynchronous copies double-buffered
-  int64_t jit_copy = 0;
+  // (TMA) copies double-buffered, 2 asynchronous copies double-buffered,
+  // -1 = by arithmetic (2 for complex64, 0 otherwise)
+  int64_t jit_copy = -1;
   // IEEE-FP64 passes are bound by the FP64 pipe, where the interpreting
   // kernel measured faster (30 qubits: 83.4 vs 88.3 ms a pass): they use
   // generated kernels only when this is 1

@@ -68,8 +68,8 @@ def run_both(Q, env, n, ops, prec, arith=0, density=False, tile=0, min_q=None, c
     finally:
         Q.setEnvOption(env, "jit", 2)
         Q.setEnvOption(env, "jit_fp64", 0)
-        Q.setEnvOption(env, "jit_copy", 0)
-        Q.setEnvOption(env, "jit_ctas", 2)
+        Q.setEnvOption(env, "jit_copy", -1)
+        Q.setEnvOption(env, "jit_ctas", 0)
         Q.setEnvOption(env, "arith", 0)
         Q.setEnvOption(env, "tile_qubits", 0)
         Q.setEnvOption(env, "jit_min_qubits", 20)
@@ -119,7 +119,7 @@ def test_compiled_density_matrix(Q, env, arith, p, copy):
     assert np.max(np.abs(b - ref)) <= AMP_TOL[128]
 
 
-@pytest.mark.parametrize("copy,tile", [(0, 0), (1, 12), (2, 12), (2, 13)])
+@pytest.mark.parametrize("copy,tile", [(0, 0), (1, 12), (2, 12), (2, 13), (-1, 0)])
 def test_compiled_26_qubit_workload_reductions(Q, env, copy, tile):
     """The depth-40 workload layering at 26 qubits (default threshold, so the
     generated kernels are the ones a user gets): complex64 amplitudes and FP64
@@ -142,9 +142,9 @@ def test_compiled_26_qubit_workload_reductions(Q, env, copy, tile):
             Q.destroyQureg(q)
         out.append((tot, p, amps))
     Q.setEnvOption(env, "jit", 2)
-    Q.setEnvOption(env, "jit_copy", 0)
+    Q.setEnvOption(env, "jit_copy", -1)
     Q.setEnvOption(env, "tile_qubits", 0)
-    Q.setEnvOption(env, "jit_ctas", 2)
+    Q.setEnvOption(env, "jit_ctas", 0)
     assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
     assert np.array_equal(out[0][2], out[1][2])
     assert abs(out[1][0] - 1) <= 1e-5
