@@ -64,6 +64,8 @@ def parse():
                     help="generated pass kernels move tiles by coalesced loads (0), bulk (TMA) copies "
                          "double-buffered (1) or async copies double-buffered (2)")
     ap.add_argument("--jit-ctas", type=int, default=None, help="resident CTAs per SM of generated kernels")
+    ap.add_argument("--jit-direct", type=int, default=None, choices=[0, 1],
+                    help="the last stage of a generated pass stores straight to HBM")
     ap.add_argument("--tile-qubits", type=int, default=None, help="fused tile size k (0 = automatic)")
     ap.add_argument("--jit", type=int, default=1, choices=[0, 1, 2],
                     help="fused passes: 0 interpreting kernel, 1 runtime-compiled kernels "
@@ -321,7 +323,8 @@ def main():
     # fused passes as runtime-compiled kernels, compiled during the warm-up
     # (the first step waits for them; timed steps reuse the cached kernels)
     Q.setEnvOption(env, "jit", args.jit)
-    for opt, val in (("jit_copy", args.jit_copy), ("jit_ctas", args.jit_ctas), ("tile_qubits", args.tile_qubits)):
+    for opt, val in (("jit_copy", args.jit_copy), ("jit_ctas", args.jit_ctas), ("tile_qubits", args.tile_qubits),
+                     ("jit_direct", args.jit_direct)):
         if val is not None:
             Q.setEnvOption(env, opt, val)
     stream = torch.cuda.Stream()

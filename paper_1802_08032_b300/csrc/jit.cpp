@@ -224,6 +224,7 @@ bool jit_try_launch(Env& env, Reg& r, const FPass& fp, const FStage* st, const F
   const JitCopy copy = jit_copy_mode(env, arith);
   JitShape sh{arith, R, jit_ctas_for(env, fp, arith, copy)};
   sh.copy = copy;
+  sh.direct_store = env.jit_direct != 0;
   std::string src;
   try {
     src = jit_source(fp, st, ops, sh);

@@ -36,6 +36,9 @@ struct JitShape {
   // of the GPU's global timer); Async = the same double buffering with
   // 16-byte asynchronous copies (cp.async) in the plain access pattern.
   JitCopy copy = JitCopy::Plain;
+  // the last stage of a pass writes its register amplitudes straight to
+  // HBM instead of through shared memory (not with JitCopy::Bulk)
+  bool direct_store = false;
 };
 
 // CUDA source of the pass kernel `qs_pass` for pass fp of a plan whose

@@ -172,6 +172,9 @@ std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const 
     return off;
   };
   const int nstage = fp.stage_end - fp.stage_begin;
+  // the last stage stores to HBM itself (no shared-memory round trip and
+  // store phase); the bulk form stores whole chunks from shared memory
+  const bool direct_last = sh.direct_store && !bulk && nstage > 0;
   std::ostringstream s;
   s << "// fused pass: k " << k << " L " << L << " R " << R << " ops " << fp.op_count << " stages " << nstage
     << (bulk ? " (bulk-copy pipeline)" : async ? " (async-copy pipeline)" : "") << "\n";
@@ -422,6 +425,39 @@ std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const 
     }
     apply_unc();
     for (size_t i = 0; i < pend.size(); ++i) apply_pend(i);
+    const bool direct = direct_last && si == fp.stage_end - 1;
+    if (direct) {
+      // The last stage writes its amplitudes straight to HBM: local index
+      // tl | off maps to the global offset D(tl) + D(off) (the low L bits
+      // in place, bit i >= L at tile qubit q[i]); a warp's stores of one
+      // register amplitude cover whole sectors once its other amplitudes
+      // are written, which L2 merges before they reach DRAM.
+      auto dmap = [&](uint32_t l) {
+        uint64_t d = l & ((1u << L) - 1u);
+        for (int b = L; b < k; ++b)
+          if ((l >> b) & 1u) d |= uint64_t(1) << fp.q[b];
+        return d;
+      };
+      s << "      int64_t dtl = int64_t(tl & " << hex32((1u << L) - 1u) << ");\n";
+      for (int b = L; b < k; ++b) {
+        bool reg = false;
+        for (int i = 0; i < R; ++i) reg = reg || S.pbits[i] == b;
+        if (!reg) s << "      dtl |= int64_t((tl >> " << b << ") & 1u) << " << int(fp.q[b]) << ";\n";
+      }
+      s << "      Store* const gt = g + base + dtl;\n";
+      for (int j = 0; j < (1 << R); ++j) {
+        const uint64_t d = dmap(off[size_t(j)]);
+        if (vec2) {
+          if (j & 1) continue;
+          s << "      *reinterpret_cast<float4*>(gt + " << hex64(d) << ") = make_float4(v[" << j << "].x, v[" << j
+            << "].y, v[" << j + 1 << "].x, v[" << j + 1 << "].y);\n";
+        } else {
+          s << "      gt[" << hex64(d) << "] = A::to_store(v[" << j << "]);\n";
+        }
+      }
+      s << "    }\n    __syncthreads();\n";
+      continue;
+    }
     // (each thread writes exactly the slots it read: converting in place
     // needs no barrier)
     for (int j = 0; j < (1 << R); ++j) {
@@ -452,6 +488,10 @@ std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const 
       << "  }\n"
       << "  mb::bulk_wait();\n"
       << "}\n";
+    return s.str();
+  }
+  if (direct_last) {
+    s << "  }\n}\n";
     return s.str();
   }
   s << "    // tile store\n";

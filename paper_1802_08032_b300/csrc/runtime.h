@@ -137,6 +137,7 @@ struct Env {
   // (TMA) copies double-buffered, 2 asynchronous copies double-buffered,
   // -1 = by arithmetic (2 for complex64, 0 otherwise)
   int64_t jit_copy = -1;
+  int64_t jit_direct = 0;  // the last stage stores straight to HBM
   // IEEE-FP64 passes are bound by the FP64 pipe, where the interpreting
   // kernel measured faster (30 qubits: 83.4 vs 88.3 ms a pass): they use
   // generated kernels only when this is 1

@@ -67,7 +67,8 @@ int main(int argc, char** argv) {
   const int R = pl.arith == Arith::F32 ? 5 : 4;
   const int max_compile = argc > 8 ? std::atoi(argv[8]) : 1 << 30;
   JitShape shape{pl.arith, R, ctas};
-  shape.copy = static_cast<JitCopy>(copy);
+  shape.copy = static_cast<JitCopy>(copy % 4);
+  shape.direct_store = copy >= 4;  // copy + 4: the last stage stores to HBM
   std::set<std::string> distinct;
   std::vector<std::string> todo;
   for (size_t i = 0; i < pl.fps.size(); ++i) {

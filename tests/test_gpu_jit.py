@@ -47,7 +47,7 @@ def controlled_extras(n, seed):
     return ops
 
 
-def run_both(Q, env, n, ops, prec, arith=0, density=False, tile=0, min_q=None, copy=0, ctas=2):
+def run_both(Q, env, n, ops, prec, arith=0, density=False, tile=0, min_q=None, copy=0, ctas=2, direct=0):
     """(interpreted, compiled) final states; checks the compiled run really
     launched generated kernels and none failed.  copy = 1 / 2: the bulk-copy
     (TMA) / async-copy pipeline forms of the generated kernels."""
@@ -56,6 +56,7 @@ def run_both(Q, env, n, ops, prec, arith=0, density=False, tile=0, min_q=None, c
     Q.setEnvOption(env, "jit_fp64", 1)
     Q.setEnvOption(env, "jit_copy", copy)
     Q.setEnvOption(env, "jit_ctas", ctas)
+    Q.setEnvOption(env, "jit_direct", direct)
     if min_q is not None:
         Q.setEnvOption(env, "jit_min_qubits", min_q)
     try:
@@ -70,6 +71,7 @@ def run_both(Q, env, n, ops, prec, arith=0, density=False, tile=0, min_q=None, c
         Q.setEnvOption(env, "jit_fp64", 0)
         Q.setEnvOption(env, "jit_copy", -1)
         Q.setEnvOption(env, "jit_ctas", 0)
+        Q.setEnvOption(env, "jit_direct", 0)
         Q.setEnvOption(env, "arith", 0)
         Q.setEnvOption(env, "tile_qubits", 0)
         Q.setEnvOption(env, "jit_min_qubits", 20)
@@ -79,48 +81,50 @@ def run_both(Q, env, n, ops, prec, arith=0, density=False, tile=0, min_q=None, c
     return a, b
 
 
-@pytest.mark.parametrize("copy", [0, 1, 2])
+@pytest.mark.parametrize("copy,direct", [(0, 0), (1, 0), (2, 0), (0, 1), (2, 1)])
 @pytest.mark.parametrize("prec,arith", [(64, 0), (128, 0), (128, 1)])
 @pytest.mark.parametrize("n", [12, 16, 21])
-def test_compiled_passes_match_interpreter_and_oracle(Q, env, prec, arith, n, copy):
+def test_compiled_passes_match_interpreter_and_oracle(Q, env, prec, arith, n, copy, direct):
     ops = C.random_circuit(n, 14, 900 + n, extras=True)
     ops = ops[: len(ops) // 2] + controlled_extras(n, n) + ops[len(ops) // 2:]
-    a, b = run_both(Q, env, n, ops, prec, arith, min_q=1, copy=copy)
+    a, b = run_both(Q, env, n, ops, prec, arith, min_q=1, copy=copy, direct=direct)
     assert np.array_equal(a, b), float(np.max(np.abs(a - b)))
     ref = O.run_circuit(n, ops).a
     assert np.max(np.abs(b - ref)) <= AMP_TOL[prec]
 
 
-@pytest.mark.parametrize("copy,ctas", [(0, 2), (1, 2), (1, 3), (2, 2), (2, 3)])
+@pytest.mark.parametrize("copy,ctas,direct", [(0, 2, 0), (1, 2, 0), (1, 3, 0), (2, 2, 0), (2, 3, 0), (2, 3, 1),
+                                              (0, 2, 1)])
 @pytest.mark.parametrize("prec,arith", [(64, 0), (128, 0), (128, 1)])
 @pytest.mark.parametrize("tile", [9, 11])
-def test_compiled_passes_with_small_tiles(Q, env, prec, arith, tile, copy, ctas):
+def test_compiled_passes_with_small_tiles(Q, env, prec, arith, tile, copy, ctas, direct):
     """Tiles smaller than the register: conditions on global bits (the tile
     base) and on local bits outside the stage's register bits; with the
     bulk-copy pipeline, several tiles per CTA (both buffers in turn)."""
     n = 15
     ops = C.random_circuit(n, 12, 77 + tile, extras=True) + controlled_extras(n, tile)
     ops = ops[len(ops) // 4:]  # a suffix: phases land on qubits outside the first tile
-    a, b = run_both(Q, env, n, ops, prec, arith, tile=tile, min_q=1, copy=copy, ctas=ctas)
+    a, b = run_both(Q, env, n, ops, prec, arith, tile=tile, min_q=1, copy=copy, ctas=ctas, direct=direct)
     assert np.array_equal(a, b), float(np.max(np.abs(a - b)))
     ref = O.run_circuit(n, ops).a
     assert np.max(np.abs(b - ref)) <= AMP_TOL[prec]
 
 
-@pytest.mark.parametrize("copy", [0, 1, 2])
+@pytest.mark.parametrize("copy,direct", [(0, 0), (1, 0), (2, 0), (2, 1)])
 @pytest.mark.parametrize("arith", [0, 1])
 @pytest.mark.parametrize("p", [(0.01, 0.005), (0.3, 0.6)])
-def test_compiled_density_matrix(Q, env, arith, p, copy):
+def test_compiled_density_matrix(Q, env, arith, p, copy, direct):
     N = 7
     ops = C.with_noise(C.random_circuit(N, 10, 31, extras=True) + controlled_extras(N, 3), *p)
-    a, b = run_both(Q, env, N, ops, 128, arith, density=True, min_q=1, copy=copy)
+    a, b = run_both(Q, env, N, ops, 128, arith, density=True, min_q=1, copy=copy, direct=direct)
     assert np.array_equal(a, b), float(np.max(np.abs(a - b)))
     ref = O.run_circuit(N, ops, density=True).a
     assert np.max(np.abs(b - ref)) <= AMP_TOL[128]
 
 
-@pytest.mark.parametrize("copy,tile", [(0, 0), (1, 12), (2, 12), (2, 13), (-1, 0)])
-def test_compiled_26_qubit_workload_reductions(Q, env, copy, tile):
+@pytest.mark.parametrize("copy,tile,direct", [(0, 0, 0), (1, 12, 0), (2, 12, 0), (2, 13, 0), (-1, 0, 0),
+                                              (-1, 0, 1)])
+def test_compiled_26_qubit_workload_reductions(Q, env, copy, tile, direct):
     """The depth-40 workload layering at 26 qubits (default threshold, so the
     generated kernels are the ones a user gets): complex64 amplitudes and FP64
     reductions equal to the interpreted run's."""
@@ -129,7 +133,8 @@ def test_compiled_26_qubit_workload_reductions(Q, env, copy, tile):
     out = []
     Q.setEnvOption(env, "jit_copy", copy)
     Q.setEnvOption(env, "tile_qubits", tile)
-    Q.setEnvOption(env, "jit_ctas", 3 if tile == 12 else (1 if copy else 2))
+    Q.setEnvOption(env, "jit_ctas", 3 if tile == 12 else (1 if copy > 0 else 0))
+    Q.setEnvOption(env, "jit_direct", direct)
     for jit in (0, 1):
         Q.setEnvOption(env, "jit", jit)
         q = Q.createQureg(n, 64, env)
@@ -145,6 +150,7 @@ def test_compiled_26_qubit_workload_reductions(Q, env, copy, tile):
     Q.setEnvOption(env, "jit_copy", -1)
     Q.setEnvOption(env, "tile_qubits", 0)
     Q.setEnvOption(env, "jit_ctas", 0)
+    Q.setEnvOption(env, "jit_direct", 0)
     assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
     assert np.array_equal(out[0][2], out[1][2])
     assert abs(out[1][0] - 1) <= 1e-5
