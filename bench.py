@@ -643,10 +643,20 @@ def variants(Q, env, torch, stream, only=(), qubits=30, serve=(60, 0.0)):
             for _ in range(reps):
                 run()
             us = (time.perf_counter() - t0) / reps * 1e6
+            # where the time goes: kernel time per circuit (CUDA events)
+            Q.resetKernelStats(env)
+            Q.setEnvOption(env, "profile", 1)
+            for _ in range(20):
+                run()
+            Q.setEnvOption(env, "profile", 0)
+            kstats = Q.getKernelStats(env)
         finally:
             Q.destroyQureg(q)
+        gpu_us = sum(k["total_ms"] for k in kstats) * 1e3 / 20
         return {"qubits": 12, "gates": ops12[1], "us_per_circuit": us,
-                "gates_per_s": ops12[1] / us * 1e6, "circuits_per_s": 1e6 / us}
+                "gates_per_s": ops12[1] / us * 1e6, "circuits_per_s": 1e6 / us,
+                "kernel_us_per_circuit": gpu_us,
+                "kernels": {k["name"]: round(k["total_ms"] * 1e3 / 20, 2) for k in kstats}}
 
     for name, fn in (("sv12_c128", sv12), ("_ref30", fp64_reference(30, ref30)),
                      ("sv30_c64", sv(64, 0, ref=ref30)), ("_rel30", release(ref30)),

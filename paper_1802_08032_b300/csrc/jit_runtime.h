@@ -40,11 +40,14 @@ inline int jit_ctas_for(const Env& env, const FPass& fp, Arith arith, JitCopy co
   return 2;
 }
 
-// Tile size cap of plans whose passes run as generated kernels: complex64
-// tiles of 2^12 amplitudes (32 KiB) with a copy pipeline, so that two
-// buffers each for three CTAs fit an SM's shared memory; 0 = no cap.
+// Tile size cap of plans whose passes may run as generated kernels:
+// complex64 tiles of 2^12 amplitudes (32 KiB) with a copy pipeline, so that
+// two buffers each for three CTAs fit an SM's shared memory; 0 = no cap.
+// It does not depend on whether generated kernels are on, or compiled yet:
+// a register's plan, and so its rounding, is the same either way (the
+// interpreting and generated kernels then agree bit for bit).
 inline int jit_tile_cap(const Env& env, const Reg& r, Arith arith) {
-  if (!jit_wanted(env, r, arith)) return 0;
+  if (r.nq < env.jit_min_qubits) return 0;
   return arith == Arith::F32 && jit_copy_mode(env, arith) != JitCopy::Plain ? 12 : 0;
 }
 
