@@ -625,7 +625,7 @@ def variants(Q, env, torch, stream, only=(), qubits=30, serve=(60, 0.0)):
             Q.destroyQureg(d)
         return {"ops_per_s": len(dops) / ms * 1e3, "ms_per_circuit": ms, "ops": len(dops)}
 
-    def sv12(reps=300):
+    def sv12(reps=300, tiles=(0, 9, 10)):
         # the 12-qubit complex128 depth-20 circuit (64 KiB: one fused tile):
         # latency-bound, so whole circuits are timed on the host clock, each
         # reset, planned, run and reduced (calcTotalProb reads its result)
@@ -637,12 +637,17 @@ def variants(Q, env, torch, stream, only=(), qubits=30, serve=(60, 0.0)):
                 Q.initZeroState(q)
                 Q.applyCircuit(q, ops12)
                 return Q.calcTotalProb(q)
-            for _ in range(10):
-                run()
-            t0 = time.perf_counter()
-            for _ in range(reps):
-                run()
-            us = (time.perf_counter() - t0) / reps * 1e6
+            by_tile = {}
+            for k in tiles:   # tile size: 0 = the planner's choice
+                Q.setEnvOption(env, "tile_qubits", k)
+                for _ in range(10):
+                    run()
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    run()
+                by_tile[k] = (time.perf_counter() - t0) / reps * 1e6
+            Q.setEnvOption(env, "tile_qubits", 0)
+            us = by_tile[0]
             # where the time goes: kernel time per circuit (CUDA events)
             Q.resetKernelStats(env)
             Q.setEnvOption(env, "profile", 1)
@@ -656,6 +661,7 @@ def variants(Q, env, torch, stream, only=(), qubits=30, serve=(60, 0.0)):
         return {"qubits": 12, "gates": ops12[1], "us_per_circuit": us,
                 "gates_per_s": ops12[1] / us * 1e6, "circuits_per_s": 1e6 / us,
                 "kernel_us_per_circuit": gpu_us,
+                "us_per_circuit_by_tile_qubits": {str(k): round(v, 1) for k, v in by_tile.items()},
                 "kernels": {k["name"]: round(k["total_ms"] * 1e3 / 20, 2) for k in kstats}}
 
     for name, fn in (("sv12_c128", sv12), ("_ref30", fp64_reference(30, ref30)),

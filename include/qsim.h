@@ -156,7 +156,10 @@ int qsDiagBoundedWait(QuESTEnv env, int timeoutUs);
  *                   2^12 amplitudes, 0 otherwise).  "jit_ctas": resident
  *                   CTAs per SM the generated kernels are built for (1..4,
  *                   0 = by shape, the default: 3 for double-buffered 2^12
- *                   complex64 tiles, else 2).
+ *                   complex64 tiles, else 2).  "jit_direct": 1 (default)
+ *                   = the last stage of a generated pass writes its
+ *                   amplitudes straight to HBM instead of through shared
+ *                   memory (not with bulk copies); 0 = through the tile.
  *                   Read-only counters: "jit_launches", "jit_rejected",
  *                   "jit_ready", "jit_pending", "jit_failed",
  *                   "jit_compile_ms".
@@ -415,6 +418,56 @@ int servePoll(QSServer server, int64_t ticket, QSResult *out, int64_t timeoutUs)
 int serveSetOption(QSServer server, const char *key, int64_t value);
 int serveGetOption(QSServer server, const char *key, int64_t *value);
 int serveDestroy(QSServer server);
+
+/* ------------------------------------------------ partitioned registers */
+/* The paper's distributed state vector (Sec. II.B.2): an n-qubit state vector
+ * split into P = 2^k parts of 2^(n-k) amplitudes by its top k index bits (in
+ * the paper, one part per node).  Gates that move amplitudes along a qubit
+ * held in the part index ("global") need other parts' amplitudes; the paper
+ * exchanges whole parts between pairs of nodes.  Here a global qubit about
+ * to be moved is first swapped with a local one (each pair of parts
+ * differing in that bit exchanges half of its amplitudes through send and
+ * receive buffers), after which the gate, and the fused tiles that follow,
+ * run inside every part; the qubit map is kept.  Diagonal gates and
+ * controls on global qubits need no exchange (a part knows its global
+ * bits).  In this library all parts live on the env's GPU and the exchange
+ * is a device-to-device copy between the buffers, the step a deployment
+ * with one part per GPU would carry out as point-to-point transfers; the
+ * swap schedule and the reductions are the same.
+ * createPartitionedQureg: numQubits 2..40, globalQubits k 1..min(6, n-1)
+ *   (P = 2^k parts), QS_C64 / QS_C128; starts in |0...0>.  Memory: the
+ *   parts plus four half-part buffers.
+ * partApplyCircuit: single-target gates, controlled gates, phases and sign
+ *   flips (QS_OP_H .. QS_OP_MCPF; channels and multi-target gates give
+ *   QS_E_ARG), validated as applyCircuit does; queued like applyCircuit,
+ *   with swaps where the schedule needs them.
+ * partCalcTotalProb / partCalcProbOfOutcome: each part reduces in FP64, the
+ *   part sums add in part order (the all-reduce of a distributed run).
+ * partCopyStateToHost: the whole 2^n state in logical index order (the
+ *   qubit map undone), into dst (caller-owned, 2^n Complex).
+ * partGetInfo: sizes, the logical -> physical qubit map (n ints), swaps run
+ *   and bytes exchanged between parts so far (any pointer may be null).
+ * partPlanSchedule (host only, no GPU): the schedule partApplyCircuit runs
+ *   for ops on a fresh register: steps of kind 0 (apply op `op` in every
+ *   part) or 1 (swap physical global position globalPos with local position
+ *   localPos), and the final qubit map; maxSteps 0 only counts. */
+typedef struct { int64_t id; } QSPartReg;
+typedef struct {
+    int32_t kind;       /* 0: local op, 1: qubit swap        */
+    int32_t op;         /* kind 0: index into the op list    */
+    int32_t globalPos;  /* kind 1: physical position >= n-k  */
+    int32_t localPos;   /* kind 1: physical position < n-k   */
+} QSPartStep;
+int createPartitionedQureg(int numQubits, int globalQubits, int precision, QuESTEnv env, QSPartReg *out);
+int destroyPartitionedQureg(QSPartReg reg);
+int partApplyCircuit(QSPartReg reg, const QSOp *ops, int64_t numOps);
+int partCalcTotalProb(QSPartReg reg, double *out);
+int partCalcProbOfOutcome(QSPartReg reg, int qubit, int outcome, double *out);
+int partCopyStateToHost(QSPartReg reg, Complex *dst);
+int partGetInfo(QSPartReg reg, int *numQubits, int *globalQubits, int *perm, int64_t *swaps,
+                double *exchangedBytes);
+int partPlanSchedule(int numQubits, int globalQubits, const QSOp *ops, int64_t numOps, QSPartStep *steps,
+                     int64_t maxSteps, int64_t *numSteps, int *finalPerm);
 
 /* ------------------------------------------------- allocation-free norm */
 /* calcTotalProbNoAlloc: sum over j of |amps[j]|^2 in FP64, for callers that

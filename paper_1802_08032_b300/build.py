@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libqsim.so")
 SOURCES = ["api.cu", "oplist.cpp", "launch.cu", "planner.cpp", "fused.cu", "profiler.cu", "noalloc.cu",
-           "batch.cu", "serve.cu", "jit.cpp", "jit_gen.cpp"]
+           "batch.cu", "serve.cu", "jit.cpp", "jit_gen.cpp", "partition.cpp", "partition.cu"]
 # device headers the runtime-compiled pass kernels include (embedded in the
 # library for NVRTC)
 JIT_HEADERS = ["common.cuh", "dfloat.cuh", "fused_types.h", "pair_arith.cuh", "fused_arith.cuh", "mbarrier.cuh"]
@@ -62,23 +62,26 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     common = [nvcc(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
               "-I", os.path.join(ROOT, "include"), "-I", GEN, *extra]
     tag = f"{os.getpid()}"
-    objs = [os.path.join(GEN, f"{os.path.splitext(s)[0]}.{tag}.o") for s in SOURCES]
+    objs = [os.path.join(GEN, f"{s.replace('.', '_')}.{tag}.o") for s in SOURCES]
     cmds = [common + ["-c", "-o", o, os.path.join(CSRC, s)] for s, o in zip(SOURCES, objs)]
     if verbose:
         for c in cmds:
             print(" ".join(c), file=sys.stderr)
     from concurrent.futures import ThreadPoolExecutor
-    with ThreadPoolExecutor(max_workers=max(1, min(len(cmds), os.cpu_count() or 1))) as ex:
-        for f in [ex.submit(subprocess.check_call, c) for c in cmds]:
-            f.result()
     tmp = LIB + f".tmp{tag}"
-    link = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-lnvrtc"]
-    if verbose:
-        print(" ".join(link), file=sys.stderr)
-    subprocess.check_call(link)
-    for o in objs:
-        os.remove(o)
-    os.replace(tmp, LIB)
+    try:
+        with ThreadPoolExecutor(max_workers=max(1, min(len(cmds), os.cpu_count() or 1))) as ex:
+            for f in [ex.submit(subprocess.check_call, c) for c in cmds]:
+                f.result()
+        link = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-lnvrtc"]
+        if verbose:
+            print(" ".join(link), file=sys.stderr)
+        subprocess.check_call(link)
+        os.replace(tmp, LIB)
+    finally:
+        for o in objs + [tmp]:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB
 
 

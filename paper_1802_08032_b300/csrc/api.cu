@@ -186,6 +186,7 @@ void set_last_error(const std::string& msg) { t_err = msg; }
 int guarded_call(const std::function<void()>& f) { return guarded(f); }
 Env& lookup_env(int64_t id) { return env_of(QuESTEnv{id}); }
 Reg& lookup_reg(int64_t id) { return reg_of(Qureg{id}); }
+void apply_op(Reg& r, const GateOp& op) { apply(r, op); }
 }
 
 extern "C" {

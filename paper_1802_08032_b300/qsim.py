@@ -73,6 +73,15 @@ class QSServer(ctypes.Structure):
     _fields_ = [("id", ctypes.c_int64)]
 
 
+class QSPartReg(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64)]
+
+
+class QSPartStep(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("op", ctypes.c_int32), ("globalPos", ctypes.c_int32),
+                ("localPos", ctypes.c_int32)]
+
+
 class QSRequest(ctypes.Structure):
     _fields_ = [("isDensity", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("numQubits", ctypes.c_int32), ("measureQubit", ctypes.c_int32),
@@ -160,6 +169,14 @@ EXTRA_SIGNATURES: dict = {
     "serveSetOption": [QSServer, ctypes.c_char_p, _I64],
     "serveGetOption": [QSServer, ctypes.c_char_p, _P(_I64)],
     "serveDestroy": [QSServer],
+    "createPartitionedQureg": [_I, _I, _I, QuESTEnv, _P(QSPartReg)],
+    "destroyPartitionedQureg": [QSPartReg],
+    "partApplyCircuit": [QSPartReg, _P(QSOp), _I64],
+    "partCalcTotalProb": [QSPartReg, _P(_D)],
+    "partCalcProbOfOutcome": [QSPartReg, _I, _I, _P(_D)],
+    "partCopyStateToHost": [QSPartReg, _VP],
+    "partGetInfo": [QSPartReg, _P(_I), _P(_I), _P(_I), _P(_I64), _P(_D)],
+    "partPlanSchedule": [_I, _I, _P(QSOp), _I64, _P(QSPartStep), _I64, _P(_I64), _P(_I)],
 }
 
 
@@ -598,3 +615,61 @@ def serveGetOption(server, key: str) -> int:
 
 def serveDestroy(server):
     _check(LIB.serveDestroy(server))
+
+
+# ------------------------------------------------ partitioned registers
+def createPartitionedQureg(numQubits: int, globalQubits: int, precision: int, env) -> QSPartReg:
+    r = QSPartReg()
+    _check(LIB.createPartitionedQureg(int(numQubits), int(globalQubits), int(precision), env, ctypes.byref(r)))
+    return r
+
+
+def destroyPartitionedQureg(r):
+    _check(LIB.destroyPartitionedQureg(r))
+
+
+def partApplyCircuit(r, ops):
+    arr, n = ops if (isinstance(ops, tuple) and len(ops) == 2 and isinstance(ops[1], int)) else to_qsops(ops)
+    _check(LIB.partApplyCircuit(r, arr, n))
+
+
+def partCalcTotalProb(r) -> float:
+    out = ctypes.c_double()
+    _check(LIB.partCalcTotalProb(r, ctypes.byref(out)))
+    return out.value
+
+
+def partCalcProbOfOutcome(r, qubit: int, outcome: int) -> float:
+    out = ctypes.c_double()
+    _check(LIB.partCalcProbOfOutcome(r, int(qubit), int(outcome), ctypes.byref(out)))
+    return out.value
+
+
+def partCopyStateToHost(r):
+    import numpy as np
+    info = partGetInfo(r)
+    out = np.empty(1 << info["numQubits"], dtype=np.complex128)
+    _check(LIB.partCopyStateToHost(r, out.ctypes.data))
+    return out
+
+
+def partGetInfo(r) -> dict:
+    n, k = ctypes.c_int(), ctypes.c_int()
+    _check(LIB.partGetInfo(r, ctypes.byref(n), ctypes.byref(k), None, None, None))
+    perm = (ctypes.c_int * n.value)()
+    sw, ex = ctypes.c_int64(), ctypes.c_double()
+    _check(LIB.partGetInfo(r, None, None, perm, ctypes.byref(sw), ctypes.byref(ex)))
+    return {"numQubits": n.value, "globalQubits": k.value, "perm": list(perm), "swaps": sw.value,
+            "exchangedBytes": ex.value}
+
+
+def partPlanSchedule(numQubits: int, globalQubits: int, ops):
+    """Host-only schedule: ([(kind, op, globalPos, localPos)], final qubit map)."""
+    arr, n = ops if (isinstance(ops, tuple) and len(ops) == 2 and isinstance(ops[1], int)) else to_qsops(ops)
+    cnt = ctypes.c_int64()
+    perm = (ctypes.c_int * numQubits)()
+    _check(LIB.partPlanSchedule(int(numQubits), int(globalQubits), arr, n, None, 0, ctypes.byref(cnt), perm))
+    steps = (QSPartStep * max(1, cnt.value))()
+    _check(LIB.partPlanSchedule(int(numQubits), int(globalQubits), arr, n, steps, cnt.value, ctypes.byref(cnt),
+                                perm))
+    return [(s.kind, s.op, s.globalPos, s.localPos) for s in steps[:cnt.value]], list(perm)

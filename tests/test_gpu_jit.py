@@ -71,7 +71,7 @@ def run_both(Q, env, n, ops, prec, arith=0, density=False, tile=0, min_q=None, c
         Q.setEnvOption(env, "jit_fp64", 0)
         Q.setEnvOption(env, "jit_copy", -1)
         Q.setEnvOption(env, "jit_ctas", 0)
-        Q.setEnvOption(env, "jit_direct", 0)
+        Q.setEnvOption(env, "jit_direct", 1)
         Q.setEnvOption(env, "arith", 0)
         Q.setEnvOption(env, "tile_qubits", 0)
         Q.setEnvOption(env, "jit_min_qubits", 20)
@@ -150,7 +150,7 @@ def test_compiled_26_qubit_workload_reductions(Q, env, copy, tile, direct):
     Q.setEnvOption(env, "jit_copy", -1)
     Q.setEnvOption(env, "tile_qubits", 0)
     Q.setEnvOption(env, "jit_ctas", 0)
-    Q.setEnvOption(env, "jit_direct", 0)
+    Q.setEnvOption(env, "jit_direct", 1)
     assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
     assert np.array_equal(out[0][2], out[1][2])
     assert abs(out[1][0] - 1) <= 1e-5
