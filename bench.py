@@ -673,6 +673,7 @@ def variants(Q, env, torch, stream, only=(), qubits=30, serve=(60, 0.0)):
                      ("single_gate_sweep_33q", lambda: sweep(33, range(33))),
                      ("dm14_c128", dm14),
                      ("batch4096_c64", lambda: batch_variant(Q, env, torch, stream)),
+                     ("partitioned_28q_4parts", lambda: partition_variant(Q, env, torch, stream)),
                      ("multi_target_passes", lambda: multi_sweep(Q, env, torch, stream, qubits)),
                      # last: after a serving sweep's many large allocations the process's later
                      # registers measured up to 15 % slower in latency-bound passes
@@ -775,6 +776,38 @@ def batch_variant(Q, env, torch, stream, count=4096, depth=30):
             "norm_max_dev": float(np.max(np.abs(norms - 1))),
             "plain_c128_circuits_per_s": len(sub) / ms_plain * 1e3,
             "plain_c128_subset": f"{len(sub)} of the same registers, one at a time, one kernel per gate"}
+
+
+def partition_variant(Q, env, torch, stream, n=28, k=2, prec=64):
+    """The paper's distribution scheme with every part on this GPU: the
+    28-qubit depth-40 workload over 4 parts of 26 qubits, qubit swaps as
+    device-to-device exchanges between send and receive buffers.  Stated
+    beside the same circuit on one 28-qubit register; a deployment with one
+    part per GPU is not built (one GPU per run), so this is no multi-GPU
+    figure."""
+    ops = Q.to_qsops(C.workload_30q(n))
+    r = Q.createPartitionedQureg(n, k, prec, env)
+    try:
+        Q.partApplyCircuit(r, ops)            # warm-up (compiles the pass kernels)
+        Q.partCalcTotalProb(r)
+        Q.destroyPartitionedQureg(r)
+        r = Q.createPartitionedQureg(n, k, prec, env)
+        info0 = Q.partGetInfo(r)
+        ms = timed(torch, stream, lambda: (Q.partApplyCircuit(r, ops), Q.partCalcTotalProb(r)), 1)
+        info = Q.partGetInfo(r)
+    finally:
+        Q.destroyPartitionedQureg(r)
+    q = Q.createQureg(n, prec, env)
+    try:
+        ms1 = timed(torch, stream, lambda: (Q.initZeroState(q), Q.applyCircuit(q, ops), Q.calcTotalProb(q)), 1)
+    finally:
+        Q.destroyQureg(q)
+    swaps = (info["swaps"] - info0["swaps"]) / 2   # timed() runs the step twice
+    return {"qubits": n, "parts": 1 << k, "precision": f"complex{prec}", "gates": ops[1],
+            "ms_per_circuit": ms, "gates_per_s": ops[1] / ms * 1e3, "swaps_per_circuit": swaps,
+            "exchanged_GB_per_circuit": (info["exchangedBytes"] - info0["exchangedBytes"]) / 2 / 1e9,
+            "one_register_ms_per_circuit": ms1,
+            "note": "all parts on one GPU: the exchange is a device-to-device copy"}
 
 
 def multi_sweep(Q, env, torch, stream, n=30):
