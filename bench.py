@@ -648,6 +648,20 @@ def variants(Q, env, torch, stream, only=(), qubits=30, serve=(60, 0.0)):
                 by_tile[k] = (time.perf_counter() - t0) / reps * 1e6
             Q.setEnvOption(env, "tile_qubits", 0)
             us = by_tile[0]
+            # the same with generated pass kernels (compiled in the first
+            # run; the 12-qubit passes run on 2 SMs, latency- not FP64-bound)
+            for opt, val in (("jit", 1), ("jit_fp64", 1), ("jit_min_qubits", 1)):
+                Q.setEnvOption(env, opt, val)
+            try:
+                for _ in range(10):
+                    run()
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    run()
+                us_jit = (time.perf_counter() - t0) / reps * 1e6
+            finally:
+                for opt, val in (("jit", 2), ("jit_fp64", 0), ("jit_min_qubits", 20)):
+                    Q.setEnvOption(env, opt, val)
             # where the time goes: kernel time per circuit (CUDA events)
             Q.resetKernelStats(env)
             Q.setEnvOption(env, "profile", 1)
@@ -662,6 +676,7 @@ def variants(Q, env, torch, stream, only=(), qubits=30, serve=(60, 0.0)):
                 "gates_per_s": ops12[1] / us * 1e6, "circuits_per_s": 1e6 / us,
                 "kernel_us_per_circuit": gpu_us,
                 "us_per_circuit_by_tile_qubits": {str(k): round(v, 1) for k, v in by_tile.items()},
+                "us_per_circuit_generated_kernels": us_jit,
                 "kernels": {k["name"]: round(k["total_ms"] * 1e3 / 20, 2) for k in kstats}}
 
     for name, fn in (("sv12_c128", sv12), ("_ref30", fp64_reference(30, ref30)),

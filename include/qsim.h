@@ -140,8 +140,10 @@ int qsDiagBoundedWait(QuESTEnv env, int timeoutUs);
  *                   for the process by the pass's structure (coefficients
  *                   are kernel parameters, so other angles reuse them):
  *                   0 = never (the interpreting fused kernel), 1 = compile
- *                   on first use and wait, 2 = compile in the background and
- *                   use the interpreting kernel until ready (default).  Both
+ *                   on first use and wait, 2 = compile in the background once
+ *                   a pass structure is met a second time, and use the
+ *                   interpreting kernel until ready (default: circuits that
+ *                   are never rerun cost no compile).  Both
  *                   kernels give bit-identical amplitudes.  Applies to
  *                   complex64 and double-float passes; IEEE-FP64 passes
  *                   only with "jit_fp64" = 1 (they are FP64-pipe bound,

@@ -132,7 +132,8 @@ T* upload(const std::vector<T>& v, cudaStream_t s) {
 template <class A, int R>
 void launch_wave(const Batch& b, const Wave& w, cudaStream_t s) {
   const size_t smem = fused_smem_bytes<A>(w.kmax, w.Lmin, w.opmax, w.stmax);
-  const int grid = int(std::min<int64_t>(w.nitems, int64_t(b.env->sms) * fused_ctas_per_sm(R)));
+  const int64_t chunks = (w.nitems + kBatchChunk - 1) / kBatchChunk;
+  const int grid = int(std::min<int64_t>(chunks, int64_t(b.env->sms) * fused_ctas_per_sm(R)));
   k_fused_batch<A, R><<<grid, kFusedThreads, smem, s>>>(b.d_items + w.first_item, w.nitems, b.d_passes,
                                                         b.d_ops, b.d_st, w.kmax, w.Lmin, w.opmax);
 }

@@ -391,6 +391,9 @@ __global__ void __launch_bounds__(kFusedThreads, fused_ctas_per_sm(R))
   for (int64_t tau = blockIdx.x; tau < P.ntiles; tau += gridDim.x) process_tile<A, R, false>(g, P, tau, m);
 }
 
+// Consecutive work items a CTA of the batched kernel takes at a time.
+constexpr int kBatchChunk = 8;
+
 // Batched: the work items of one wave (tiles of passes of many registers,
 // each pass with its own register pointer).  Shared memory is laid out for
 // the largest tile (kmax, Lmin) and op list (opmax) of the wave.
@@ -406,7 +409,11 @@ __global__ void __launch_bounds__(kFusedThreads, fused_ctas_per_sm(R))
   __shared__ FPass sP;
   PassSmem<A> m = pass_smem<A>(smem_raw, kmax, Lmin, opmax);
   int cur = -1;
-  for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+  // runs of kBatchChunk consecutive items per CTA (block-cyclic): the items
+  // of one pass are consecutive, so a CTA reloads a pass's op list once per
+  // run instead of once per item
+  for (int c = blockIdx.x; c * kBatchChunk < nitems; c += gridDim.x)
+  for (int i = c * kBatchChunk, iend = min(nitems, (c + 1) * kBatchChunk); i < iend; ++i) {
     const BItem it = items[i];
     if (it.pass != cur) {
       cur = it.pass;

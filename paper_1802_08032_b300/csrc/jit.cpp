@@ -7,6 +7,10 @@
 // host threads: with the "jit" option 2 (asynchronous) a flush launches the
 // interpreting kernel for any pass whose kernel is not ready yet and queues
 // its compilation; with 1 (synchronous) the flush waits for the compile.
+// The compile threads make no CUDA calls: a compiled cubin is loaded by the
+// next flush that needs it, on the caller's thread, so nothing in the
+// background touches the CUDA runtime (a compile still running when the
+// process exits is waited for and discarded).
 #include <nvrtc.h>
 
 #include <algorithm>
@@ -42,13 +46,15 @@ const char* jit_header_text(int i) { return kJitHeaders[i].text; }
 
 namespace {
 
-enum JitState : int { JS_QUEUED = 0, JS_READY = 1, JS_FAILED = 2 };
+// SEEN (met once, not compiled) -> QUEUED -> COMPILED (cubin ready, by a
+// compile thread) -> READY (loaded, by a caller's thread); or FAILED.
+enum JitState : int { JS_QUEUED = 0, JS_READY = 1, JS_FAILED = 2, JS_COMPILED = 3, JS_SEEN = 4 };
 
 struct JitEntry {
   std::string src;
-  int device = 0;
   size_t smem = 0;
   std::atomic<int> state{JS_QUEUED};
+  std::vector<char> cubin;
   cudaLibrary_t lib = nullptr;
   cudaKernel_t kern = nullptr;
   double compile_s = 0;
@@ -72,19 +78,33 @@ class JitCache {
       if (t.joinable()) t.join();
   }
 
-  // The entry of this source, created (and queued for compilation) if new.
-  std::shared_ptr<JitEntry> find_or_queue(const std::string& src, int device, size_t smem, bool& created) {
+  // The entry of this source.  A structure is queued for compilation the
+  // second time it is met (or at once with now = true): circuits that are
+  // never rerun (serving, one-off circuits) cost no compile.  At most
+  // kSeenMax structures met only once are remembered (oldest forgotten).
+  std::shared_ptr<JitEntry> find_or_queue(const std::string& src, size_t smem, bool now) {
     std::lock_guard<std::mutex> lk(mu_);
     auto it = map_.find(src);
-    created = false;
-    if (it != map_.end()) return it->second;
-    auto e = std::make_shared<JitEntry>();
-    e->src = src;
-    e->device = device;
-    e->smem = smem;
-    map_.emplace(src, e);
+    std::shared_ptr<JitEntry> e;
+    if (it != map_.end()) {
+      e = it->second;
+      if (e->state.load() != JS_SEEN) return e;
+    } else {
+      e = std::make_shared<JitEntry>();
+      e->src = src;
+      e->smem = smem;
+      e->state.store(JS_SEEN);
+      map_.emplace(src, e);
+      seen_.push_back(src);
+      if (seen_.size() > kSeenMax) {
+        auto old = map_.find(seen_.front());
+        if (old != map_.end() && old->second->state.load() == JS_SEEN) map_.erase(old);
+        seen_.pop_front();
+      }
+      if (!now) return e;
+    }
+    e->state.store(JS_QUEUED);
     queue_.push_back(e);
-    created = true;
     start_workers_locked();
     cv_.notify_one();
     return e;
@@ -96,17 +116,40 @@ class JitCache {
     done_cv_.wait(lk, [&] { return e->state.load() != JS_QUEUED || stop_; });
   }
 
+  // Loads a compiled cubin (caller's thread, the device current); true
+  // when e is ready to launch.
+  bool load(JitEntry& e) {
+    std::lock_guard<std::mutex> lk(load_mu_);
+    if (e.state.load() == JS_READY) return true;
+    if (e.state.load() != JS_COMPILED) return false;
+    cudaError_t err = cudaLibraryLoadData(&e.lib, e.cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (err == cudaSuccess) err = cudaLibraryGetKernel(&e.kern, e.lib, "qs_pass");
+    if (err == cudaSuccess)
+      err = cudaFuncSetAttribute(reinterpret_cast<const void*>(e.kern), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(e.smem));
+    if (err != cudaSuccess) {
+      cudaGetLastError();
+      e.log = std::string("load: ") + cudaGetErrorString(err);
+      e.state.store(JS_FAILED);
+      return false;
+    }
+    e.cubin.clear();
+    e.cubin.shrink_to_fit();
+    e.state.store(JS_READY);
+    return true;
+  }
+
   JitStats stats() {
     std::lock_guard<std::mutex> lk(mu_);
     JitStats s{};
     for (auto& kv : map_) {
       const int st = kv.second->state.load();
-      if (st == JS_READY) {
+      if (st == JS_READY || st == JS_COMPILED) {
         ++s.ready;
         s.compile_s += kv.second->compile_s;
       } else if (st == JS_FAILED) {
         ++s.failed;
-      } else {
+      } else if (st == JS_QUEUED) {
         ++s.pending;
       }
     }
@@ -140,42 +183,34 @@ class JitCache {
       }
       compile(*e);
       {
-        std::lock_guard<std::mutex> lk(mu_);
+        std::lock_guard<std::mutex> lk(mu_);  // (orders the state change before waiters check it)
       }
       done_cv_.notify_all();
     }
   }
 
+  // NVRTC only: no CUDA runtime call on a compile thread.
   static void compile(JitEntry& e) {
     const auto t0 = std::chrono::steady_clock::now();
     std::string log;
     std::vector<char> cubin;
     const bool ok = jit_compile_cubin(e.src, cubin, log);
     if (ok) {
-      cudaError_t err = cudaSetDevice(e.device);
-      if (err == cudaSuccess)
-        err = cudaLibraryLoadData(&e.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
-      if (err == cudaSuccess) err = cudaLibraryGetKernel(&e.kern, e.lib, "qs_pass");
-      if (err == cudaSuccess)
-        err = cudaFuncSetAttribute(reinterpret_cast<const void*>(e.kern),
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(e.smem));
-      if (err != cudaSuccess) {
-        e.log = std::string("load: ") + cudaGetErrorString(err);
-        e.state.store(JS_FAILED);
-        return;
-      }
+      e.cubin = std::move(cubin);
       e.compile_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-      e.state.store(JS_READY);
+      e.state.store(JS_COMPILED);
     } else {
       e.log = log;
       e.state.store(JS_FAILED);
     }
   }
 
-  std::mutex mu_;
+  std::mutex mu_, load_mu_;
   std::condition_variable cv_, done_cv_;
   bool stop_ = false;
   std::deque<std::shared_ptr<JitEntry>> queue_;
+  std::deque<std::string> seen_;  // structures met once, oldest first
+  static constexpr size_t kSeenMax = 1024;
   std::unordered_map<std::string, std::shared_ptr<JitEntry>> map_;
   std::vector<std::thread> workers_;
 };
@@ -233,10 +268,9 @@ bool jit_try_launch(Env& env, Reg& r, const FPass& fp, const FStage* st, const F
     return false;
   }
   const size_t smem = jit_smem_bytes(fp, sh);
-  bool created = false;
-  std::shared_ptr<JitEntry> e = JitCache::get().find_or_queue(src, env.device, smem, created);
+  std::shared_ptr<JitEntry> e = JitCache::get().find_or_queue(src, smem, env.jit == 1);
   if (env.jit == 1 && e->state.load() == JS_QUEUED) JitCache::get().wait(e);
-  if (e->state.load() != JS_READY) return false;
+  if (!JitCache::get().load(*e)) return false;
   // parameters: g, ntiles, then the pass's FOp records (constant bank)
   void* g = r.d;
   long long ntiles = fp.ntiles;

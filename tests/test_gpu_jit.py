@@ -157,8 +157,9 @@ def test_compiled_26_qubit_workload_reductions(Q, env, copy, tile, direct):
 
 
 def test_background_compile_then_reuse(Q, env):
-    """Option 2: a new pass structure runs on the interpreting kernel while
-    its kernels compile in the background.  Once compiled, the same circuit
+    """Option 2: a pass structure met for the first time runs on the
+    interpreting kernel and is not compiled; met again, it is compiled in the
+    background while the interpreting kernel runs it.  Once compiled, the same circuit
     structure with other angles launches only cached kernels (coefficients
     are kernel parameters, not part of the compiled code) and matches the
     oracle."""
@@ -179,6 +180,9 @@ def test_background_compile_then_reuse(Q, env):
     try:
         _, jl, passes = counted(circuit(1), 2)
         assert passes > 0 and jl == 0        # nothing compiled yet: all interpreted
+        known = Q.getEnvOption(env, "jit_pending") + Q.getEnvOption(env, "jit_ready")
+        _, jl, passes = counted(circuit(1), 2)  # met a second time: queued, still interpreted
+        assert Q.getEnvOption(env, "jit_pending") + Q.getEnvOption(env, "jit_ready") > known
         _, jl, passes = counted(circuit(1), 1)
         assert jl == passes                   # waited for the compiles
         ops = circuit(2)
