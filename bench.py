@@ -40,7 +40,10 @@ FP32_ISSUE_TINSTR = 148 * 128 * 2.032e9 / 1e12   # FP32 instructions/s at the 20
 # DRAM bytes (read + write) per amplitude per launch, from one ncu capture of
 # the kernel as built (profiles/<kernel>_*_ncu_full.md); scaled by the
 # amplitudes a launch processes.  Entries are removed when a kernel changes.
-MEASURED_TRAFFIC_PER_AMP = {}
+MEASURED_TRAFFIC_PER_AMP = {
+    # generated complex64 pass kernel, async-copy pipeline
+    "fused_c64": 1.014e9 / (1 << 26),       # profiles/qs_pass_c64_async_sv26_ncu_full.md
+}
 
 
 def parse():
