@@ -73,6 +73,14 @@ enum {
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *qsLastError(void);
+/* qsJitShutdown: waits for the background compiles of generated pass
+ * kernels that are in flight, drops the queued ones and stops the compile
+ * threads (compiled kernels stay cached; the threads start again when
+ * needed).  Destroying the last environment does this; a program that exits
+ * with environments alive calls it first (the Python binding does so at
+ * interpreter exit): a compile still running while the process tears down
+ * can crash it. */
+int qsJitShutdown(void);
 
 /* ------------------------------------------------------------ environment */
 /* createQuESTEnv: binds the current CUDA device, creates a stream owned by

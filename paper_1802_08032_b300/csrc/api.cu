@@ -249,7 +249,14 @@ int destroyQuESTEnv(QuESTEnv e) {
     cudaStreamDestroy(env.own);
     g_envs.erase(env.id);
     delete &env;
+    // the last environment: no background compile may outlive the library's
+    // users (a compile running while the process exits can crash it)
+    if (g_envs.empty()) jit_shutdown();
   });
+}
+
+int qsJitShutdown(void) {
+  return guarded([&] { jit_shutdown(); });
 }
 
 int syncQuESTEnv(QuESTEnv e) {

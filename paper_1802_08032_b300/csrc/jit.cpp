@@ -67,15 +67,27 @@ class JitCache {
     static JitCache c;
     return c;
   }
-  ~JitCache() {
+  ~JitCache() { shutdown(); }
+
+  // Drops queued compiles, waits for the ones in flight and ends the
+  // compile threads (they start again on the next queued compile).  Must
+  // run before the process exits: NVRTC's own static data may be torn down
+  // before this object's destructor, under a compile still running.
+  void shutdown() {
+    std::vector<std::thread> ws;
     {
       std::lock_guard<std::mutex> lk(mu_);
       stop_ = true;
+      for (auto& e : queue_) e->state.store(JS_SEEN);  // not compiled: met again, queued again
       queue_.clear();
+      ws.swap(workers_);
     }
     cv_.notify_all();
-    for (std::thread& t : workers_)
+    for (std::thread& t : ws)
       if (t.joinable()) t.join();
+    std::lock_guard<std::mutex> lk(mu_);
+    stop_ = false;
+    done_cv_.notify_all();
   }
 
   // The entry of this source.  A structure is queued for compilation the
@@ -290,6 +302,7 @@ bool jit_try_launch(Env& env, Reg& r, const FPass& fp, const FStage* st, const F
 }
 
 JitStats jit_stats() { return JitCache::get().stats(); }
+void jit_shutdown() { JitCache::get().shutdown(); }
 std::string jit_first_failure() { return JitCache::get().first_failure(); }
 
 }  // namespace qs

@@ -59,6 +59,9 @@ struct JitStats {
   double compile_s;  // summed compile + load time of the ready kernels
 };
 JitStats jit_stats();
+// Stops the background compile threads after the compiles in flight (called
+// when the last environment is destroyed, and by qsJitShutdown).
+void jit_shutdown();
 std::string jit_first_failure();
 
 }  // namespace qs

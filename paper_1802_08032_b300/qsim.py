@@ -12,6 +12,7 @@ arguments accept Python complex numbers and 2x2 nested sequences.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
 from typing import Iterable, Sequence
@@ -109,6 +110,7 @@ _I, _I64, _D, _VP = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void
 # name -> argtypes (every function returns int status, except qsLastError)
 SIGNATURES = {
     "createQuESTEnv": [_P(QuESTEnv)],
+    "qsJitShutdown": [],
     "destroyQuESTEnv": [QuESTEnv],
     "syncQuESTEnv": [QuESTEnv],
     "qsDiagBoundedWait": [QuESTEnv, ctypes.c_int],
@@ -195,6 +197,15 @@ def _load():
 
 
 LIB = _load()
+
+
+def qsJitShutdown():
+    """Waits for background kernel compiles in flight and stops the compile
+    threads (runs at interpreter exit, before the process tears down)."""
+    _check(LIB.qsJitShutdown())
+
+
+atexit.register(qsJitShutdown)
 
 
 def _check(code: int):
