@@ -653,6 +653,7 @@ def variants(Q, env, torch, stream, only=(), qubits=30, serve=(60, 0.0)):
             us = by_tile[0]
             # the same with generated pass kernels (compiled in the first
             # run; the 12-qubit passes run on 2 SMs, latency- not FP64-bound)
+            saved = {o: Q.getEnvOption(env, o) for o in ("jit", "jit_fp64", "jit_min_qubits")}
             for opt, val in (("jit", 1), ("jit_fp64", 1), ("jit_min_qubits", 1)):
                 Q.setEnvOption(env, opt, val)
             try:
@@ -663,7 +664,7 @@ def variants(Q, env, torch, stream, only=(), qubits=30, serve=(60, 0.0)):
                     run()
                 us_jit = (time.perf_counter() - t0) / reps * 1e6
             finally:
-                for opt, val in (("jit", 2), ("jit_fp64", 0), ("jit_min_qubits", 20)):
+                for opt, val in saved.items():
                     Q.setEnvOption(env, opt, val)
             # where the time goes: kernel time per circuit (CUDA events)
             Q.resetKernelStats(env)
