@@ -551,10 +551,13 @@ template <typename R>
 void sumsq(Env& env, const Reg& r, const Fixed& fx, int64_t nsel, double* out) {
   const int blocks = int(std::max<int64_t>(
       1, std::min<int64_t>(kRedMaxBlocks, (nsel + kRedThreads * 4 - 1) / (kRedThreads * 4))));
-  KTimer kt(env, kname<R>("reduce_sumsq").c_str(), double(nsel) * amp_bytes<R>(), double(nsel) * 4, 2);
+  // one block (small registers): its partial is the result, so the second
+  // stage (which would add zeros to it) is skipped, saving a launch
+  KTimer kt(env, kname<R>("reduce_sumsq").c_str(), double(nsel) * amp_bytes<R>(), double(nsel) * 4,
+            blocks == 1 ? 1 : 2);
   k_sumsq<R, 4><<<blocks, kRedThreads, 0, env.stream>>>(static_cast<const cvec<R>*>(r.d), nsel, fx,
-                                                        env.d_partial);
-  k_sum_partials<<<1, 1024, 0, env.stream>>>(env.d_partial, blocks, out);
+                                                        blocks == 1 ? out : env.d_partial);
+  if (blocks > 1) k_sum_partials<<<1, 1024, 0, env.stream>>>(env.d_partial, blocks, out);
 }
 
 template <typename R>
@@ -562,10 +565,10 @@ void sumdiag(Env& env, const Reg& r, int q, int o, double* out) {
   const int64_t d = int64_t(1) << r.n;
   const int blocks = int(std::max<int64_t>(
       1, std::min<int64_t>(kRedMaxBlocks, (d + kRedThreads - 1) / kRedThreads)));
-  KTimer kt(env, kname<R>("reduce_diag").c_str(), double(d) * amp_bytes<R>(), double(d), 2);
+  KTimer kt(env, kname<R>("reduce_diag").c_str(), double(d) * amp_bytes<R>(), double(d), blocks == 1 ? 1 : 2);
   k_sumdiag<R><<<blocks, kRedThreads, 0, env.stream>>>(static_cast<const cvec<R>*>(r.d), r.n, q, o,
-                                                       env.d_partial);
-  k_sum_partials<<<1, 1024, 0, env.stream>>>(env.d_partial, blocks, out);
+                                                       blocks == 1 ? out : env.d_partial);
+  if (blocks > 1) k_sum_partials<<<1, 1024, 0, env.stream>>>(env.d_partial, blocks, out);
 }
 
 double fetch_result(Env& env) {
