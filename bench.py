@@ -41,6 +41,7 @@ FP32_ISSUE_TINSTR = 148 * 128 * 2.032e9 / 1e12   # FP32 instructions/s at the 20
 # the kernel as built (profiles/<kernel>_*_ncu_full.md); scaled by the
 # amplitudes a launch processes.  Entries are removed when a kernel changes.
 MEASURED_TRAFFIC_PER_AMP = {
+    "fused_c128": 2.088e9 / (1 << 26),      # profiles/fused_c128_fp64_sv26_ncu_full.md
     # generated complex64 pass kernel, async-copy pipeline
     "fused_c64": 1.014e9 / (1 << 26),       # profiles/qs_pass_c64_async_sv26_ncu_full.md
 }
@@ -800,33 +801,38 @@ def batch_variant(Q, env, torch, stream, count=4096, depth=30):
 def partition_variant(Q, env, torch, stream, n=28, k=2, prec=64):
     """The paper's distribution scheme with every part on this GPU: the
     28-qubit depth-40 workload over 4 parts of 26 qubits, qubit swaps as
-    device-to-device exchanges between send and receive buffers.  Stated
-    beside the same circuit on one 28-qubit register; a deployment with one
-    part per GPU is not built (one GPU per run), so this is no multi-GPU
-    figure."""
+    device-to-device exchanges between send and receive buffers.  Each run
+    starts from a fresh register (the same swap schedule, so the warm-up run
+    compiled every pass kernel the timed one needs).  Stated beside the same
+    circuit on one 28-qubit register; a deployment with one part per GPU is
+    not built (one GPU per run), so this is no multi-GPU figure."""
+    import time
     ops = Q.to_qsops(C.workload_30q(n))
-    r = Q.createPartitionedQureg(n, k, prec, env)
-    try:
-        Q.partApplyCircuit(r, ops)            # warm-up (compiles the pass kernels)
-        Q.partCalcTotalProb(r)
-        Q.destroyPartitionedQureg(r)
+
+    def one_run():
         r = Q.createPartitionedQureg(n, k, prec, env)
-        info0 = Q.partGetInfo(r)
-        ms = timed(torch, stream, lambda: (Q.partApplyCircuit(r, ops), Q.partCalcTotalProb(r)), 1)
-        info = Q.partGetInfo(r)
-    finally:
-        Q.destroyPartitionedQureg(r)
+        try:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Q.partApplyCircuit(r, ops)
+            Q.partCalcTotalProb(r)            # waits for the parts
+            return (time.perf_counter() - t0) * 1e3, Q.partGetInfo(r)
+        finally:
+            Q.destroyPartitionedQureg(r)
+
+    one_run()                                 # warm-up (compiles the pass kernels)
+    ms, info = one_run()
     q = Q.createQureg(n, prec, env)
     try:
         ms1 = timed(torch, stream, lambda: (Q.initZeroState(q), Q.applyCircuit(q, ops), Q.calcTotalProb(q)), 1)
     finally:
         Q.destroyQureg(q)
-    swaps = (info["swaps"] - info0["swaps"]) / 2   # timed() runs the step twice
     return {"qubits": n, "parts": 1 << k, "precision": f"complex{prec}", "gates": ops[1],
-            "ms_per_circuit": ms, "gates_per_s": ops[1] / ms * 1e3, "swaps_per_circuit": swaps,
-            "exchanged_GB_per_circuit": (info["exchangedBytes"] - info0["exchangedBytes"]) / 2 / 1e9,
+            "ms_per_circuit": ms, "gates_per_s": ops[1] / ms * 1e3, "swaps_per_circuit": info["swaps"],
+            "exchanged_GB_per_circuit": info["exchangedBytes"] / 1e9,
             "one_register_ms_per_circuit": ms1,
-            "note": "all parts on one GPU: the exchange is a device-to-device copy"}
+            "note": "all parts on one GPU: the exchange is a device-to-device copy (host clock, "
+                    "fresh register per run)"}
 
 
 def multi_sweep(Q, env, torch, stream, n=30):
