@@ -234,7 +234,8 @@ void flush(Reg& r) {
       // the pass as its own compiled kernel when one is ready (jit.cpp)
       const int R = pl.arith == Arith::F32 ? 5 : 4;
       const char* name = pl.arith == Arith::DF ? "fused_c128_df" : pl.arith == Arith::F64 ? "fused_c128" : "fused_c64";
-      if (jit_try_launch(env, r, pl.fps[i], pl.fst.data(), pl.fops.data(), pl.arith, R, pl.flops[i], pl.alu[i], name))
+      if (jit_try_launch(env, r, pl.fps[i], pl.fst.data(), pl.fops.data(), pl.arith, R, pl.flops[i], pl.alu[i], name,
+                         pl.jit_memo.get(), i))
         continue;
       if (pl.arith == Arith::DF)
         launch_pass<DFArith, 4>(env, r, fp, d_ops, d_st, pl.flops[i], pl.alu[i], "fused_c128_df");

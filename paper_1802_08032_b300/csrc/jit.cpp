@@ -265,22 +265,39 @@ bool jit_compile_cubin(const std::string& src, std::vector<char>& cubin, std::st
 }
 
 bool jit_try_launch(Env& env, Reg& r, const FPass& fp, const FStage* st, const FOp* ops, Arith arith, int R,
-                    double flops, double alu, const char* name) {
+                    double flops, double alu, const char* name, RegPlan::JitMemo* memo, size_t pass_index) {
   if (!jit_wanted(env, r, arith) || fp.init) return false;
   if (fp.op_count <= 0 || fp.op_count > kMaxPassOps) return false;
   const JitCopy copy = jit_copy_mode(env, arith);
   JitShape sh{arith, R, jit_ctas_for(env, fp, arith, copy)};
   sh.copy = copy;
   sh.direct_store = env.jit_direct != 0;
-  std::string src;
-  try {
-    src = jit_source(fp, st, ops, sh);
-  } catch (const Error&) {
-    ++env.jit_rejected;
-    return false;
-  }
   const size_t smem = jit_smem_bytes(fp, sh);
-  std::shared_ptr<JitEntry> e = JitCache::get().find_or_queue(src, smem, env.jit == 1);
+  // a plan met before with this kernel shape: its entry, without
+  // generating the source again
+  const uint64_t sig = (uint64_t(arith) << 0) | (uint64_t(R) << 4) | (uint64_t(sh.ctas) << 8) |
+                       (uint64_t(int(copy)) << 12) | (uint64_t(sh.direct_store) << 16) | (uint64_t(1) << 20);
+  std::shared_ptr<JitEntry> e;
+  if (memo) {
+    if (memo->sig != sig) {
+      memo->sig = sig;
+      memo->kernels.clear();
+    }
+    if (memo->kernels.size() <= pass_index) memo->kernels.resize(pass_index + 1);
+    e = std::static_pointer_cast<JitEntry>(memo->kernels[pass_index]);
+    if (e && e->state.load() == JS_SEEN) e = nullptr;  // met once: look it up (and queue it) again
+  }
+  if (!e) {
+    std::string src;
+    try {
+      src = jit_source(fp, st, ops, sh);
+    } catch (const Error&) {
+      ++env.jit_rejected;
+      return false;
+    }
+    e = JitCache::get().find_or_queue(src, smem, env.jit == 1);
+    if (memo) memo->kernels[pass_index] = e;
+  }
   if (env.jit == 1 && e->state.load() == JS_QUEUED) JitCache::get().wait(e);
   if (!JitCache::get().load(*e)) return false;
   // parameters: g, ntiles, then the pass's FOp records (constant bank)

@@ -15,7 +15,8 @@ namespace qs {
 // ops are the plan's host arrays (fp's indices relative to them).  Returns
 // false when the caller must launch the interpreting kernel instead.
 bool jit_try_launch(Env& env, Reg& r, const FPass& fp, const FStage* st, const FOp* ops, Arith arith, int R,
-                    double flops, double alu, const char* name);
+                    double flops, double alu, const char* name, RegPlan::JitMemo* memo = nullptr,
+                    size_t pass_index = 0);
 
 // True when passes of register r are to run as generated kernels (the
 // env's "jit" options), so that the planner can size tiles for them.

@@ -1,5 +1,6 @@
 // Fusion plan of one register's queued gates (internal; planner.cpp).
 #pragma once
+#include <memory>
 #include <vector>
 
 #include "fused_types.h"
@@ -22,6 +23,14 @@ struct RegPlan {
   std::vector<double> alu;    // arithmetic instructions per pass (kernel precision)
   int64_t vops = 0;           // vector operations planned
   uint64_t zero_out = 0;      // bits known to hold only zeros after the plan
+  // generated kernels found for this plan's passes (jit.cpp), shared by the
+  // copies the plan cache hands out, so a repeated plan skips generating
+  // and looking up their sources; valid for the kernel shape `sig`
+  struct JitMemo {
+    uint64_t sig = 0;
+    std::vector<std::shared_ptr<void>> kernels;
+  };
+  std::shared_ptr<JitMemo> jit_memo = std::make_shared<JitMemo>();
 };
 
 // Tile parameters per precision: R register bits, maximum k, low qubits L.
