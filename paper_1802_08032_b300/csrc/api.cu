@@ -331,6 +331,9 @@ int setEnvOption(QuESTEnv e, const char* key, int64_t value) {
       if (value < -1 || value > 2)
         fail(QS_E_ARG, "jit_copy must be -1 (by arithmetic), 0 (plain), 1 (bulk) or 2 (async)");
       env.jit_copy = value;
+    } else if (k == "jit_swizzle") {
+      if (value != 0 && value != 1) fail(QS_E_ARG, "jit_swizzle must be 0 or 1");
+      env.jit_swizzle = value;
     } else if (k == "jit_direct") {
       if (value != 0 && value != 1) fail(QS_E_ARG, "jit_direct must be 0 or 1");
       env.jit_direct = value;
@@ -366,6 +369,7 @@ int getEnvOption(QuESTEnv e, const char* key, int64_t* value) {
     else if (k == "jit_fp64") *value = env.jit_fp64;
     else if (k == "jit_copy") *value = env.jit_copy;
     else if (k == "jit_direct") *value = env.jit_direct;
+    else if (k == "jit_swizzle") *value = env.jit_swizzle;
     else if (k == "plan_cache") *value = env.plan_cache_on;
     else if (k == "plan_cache_hits") *value = env.plan_cache_hits;
     else if (k == "jit_launches") *value = env.jit_launches;

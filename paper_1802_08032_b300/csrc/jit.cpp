@@ -272,11 +272,13 @@ bool jit_try_launch(Env& env, Reg& r, const FPass& fp, const FStage* st, const F
   JitShape sh{arith, R, jit_ctas_for(env, fp, arith, copy)};
   sh.copy = copy;
   sh.direct_store = env.jit_direct != 0;
+  sh.swizzle = env.jit_swizzle != 0;
   const size_t smem = jit_smem_bytes(fp, sh);
   // a plan met before with this kernel shape: its entry, without
   // generating the source again
   const uint64_t sig = (uint64_t(arith) << 0) | (uint64_t(R) << 4) | (uint64_t(sh.ctas) << 8) |
-                       (uint64_t(int(copy)) << 12) | (uint64_t(sh.direct_store) << 16) | (uint64_t(1) << 20);
+                       (uint64_t(int(copy)) << 12) | (uint64_t(sh.direct_store) << 16) |
+                       (uint64_t(sh.swizzle) << 17) | (uint64_t(1) << 20);
   std::shared_ptr<JitEntry> e;
   if (memo) {
     if (memo->sig != sig) {

@@ -39,6 +39,9 @@ struct JitShape {
   // the last stage of a pass writes its register amplitudes straight to
   // HBM instead of through shared memory (not with JitCopy::Bulk)
   bool direct_store = false;
+  // the tile's shared-memory layout is XOR-swizzled against bank conflicts
+  // (not with JitCopy::Bulk, whose chunks are copied whole)
+  bool swizzle = false;
 };
 
 // CUDA source of the pass kernel `qs_pass` for pass fp of a plan whose

@@ -171,6 +171,26 @@ std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const 
       if ((c >> i) & 1u) off |= uint64_t(1) << fp.q[L + i];
     return off;
   };
+  // Shared-memory swizzle: amplitude l of the tile lives at sw(l) = l ^ h(l),
+  // h XOR-ing the amplitude's slot within a 128-byte row with a fold of the
+  // index bits above the row, so that a warp whose 32 threads differ only
+  // in high local positions (a stage whose register bits hold the low ones)
+  // spreads over the banks instead of hitting one.  h is linear over XOR, so
+  // sw(tl | c) = sw(tl) ^ sw(c) for disjoint bits: one per-thread term and
+  // one constant per access.  Complex64 keeps amplitude pairs (2i, 2i + 1)
+  // together (16-byte accesses).  Off for bulk copies (whole chunks).
+  const bool swz = sh.swizzle && !bulk;
+  auto hsw = [&](uint64_t x) -> uint64_t {
+    if (!swz) return 0;
+    if (pack2) return (((x >> 4) ^ (x >> 7) ^ (x >> 10)) & 7u) << 1;
+    return ((x >> 3) ^ (x >> 6) ^ (x >> 9)) & 7u;
+  };
+  auto sw = [&](uint64_t x) { return x ^ hsw(x); };
+  auto hsw_expr = [&](const std::string& v) -> std::string {
+    if (!swz) return "0u";
+    if (pack2) return "(((((" + v + ") >> 4) ^ ((" + v + ") >> 7) ^ ((" + v + ") >> 10)) & 7u) << 1)";
+    return "((((" + v + ") >> 3) ^ ((" + v + ") >> 6) ^ ((" + v + ") >> 9)) & 7u)";
+  };
   const int nstage = fp.stage_end - fp.stage_begin;
   // the last stage stores to HBM itself (no shared-memory round trip and
   // store phase); the bulk form stores whole chunks from shared memory
@@ -211,6 +231,8 @@ std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const 
       << "  int64_t toff = int64_t(lt & " << hex32((1u << L) - 1u) << ");\n";
     for (int i = 0; i < cbits; ++i)
       s << "  toff |= int64_t((lt >> " << (L + i) << ") & 1u) << " << int(fp.q[L + i]) << ";\n";
+    // shared-memory index of its accesses (amplitude units; swizzled)
+    s << "  const uint32_t slt = lt ^ " << hsw_expr("lt") << ";\n";
   }
   // (global offset, shared index) of this thread's u-th coalesced access
   auto acc_goff = [&](int u) { return hex64(deposit(uint64_t(u) << cbits)); };
@@ -276,11 +298,11 @@ std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const 
       << "    const int64_t gb = b + toff;\n";
     for (int u = 0; u < depth; ++u) {
       if (pack2)
-        s << "    mb::async_copy16(reinterpret_cast<float4*>(dst) + (tid + " << u * T
-          << "u), reinterpret_cast<const float4*>(g) + ((gb + " << acc_goff(u) << ") >> 1));\n";
+        s << "    mb::async_copy16(reinterpret_cast<float4*>(dst) + ((slt ^ " << hex32(uint32_t(sw(uint64_t(2 * u * T))))
+          << ") >> 1), reinterpret_cast<const float4*>(g) + ((gb + " << acc_goff(u) << ") >> 1));\n";
       else
-        s << "    mb::async_copy16(reinterpret_cast<Store*>(dst) + (tid + " << u * T << "u), g + gb + " << acc_goff(u)
-          << ");\n";
+        s << "    mb::async_copy16(reinterpret_cast<Store*>(dst) + (slt ^ " << hex32(uint32_t(sw(uint64_t(u * T))))
+          << "), g + gb + " << acc_goff(u) << ");\n";
     }
     s << "    asm volatile(\"cp.async.commit_group;\" ::: \"memory\");\n  };\n"
       << "  int64_t tau = blockIdx.x;\n"
@@ -307,12 +329,14 @@ std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const 
         << "      const int64_t gb = base + toff;\n";
       for (int u = 0; u < depth; ++u)
         s << "      const float4 ld" << u << " = g4[(gb + " << acc_goff(u) << ") >> 1];\n";
-      for (int u = 0; u < depth; ++u) s << "      t4[tid + " << u * T << "u] = ld" << u << ";\n";
+      for (int u = 0; u < depth; ++u)
+        s << "      t4[(slt ^ " << hex32(uint32_t(sw(uint64_t(2 * u * T)))) << ") >> 1] = ld" << u << ";\n";
       s << "    }\n";
     } else {
       s << "    {\n      const int64_t gb = base + toff;\n";
       for (int u = 0; u < depth; ++u) s << "      const double2 ld" << u << " = g[gb + " << acc_goff(u) << "];\n";
-      for (int u = 0; u < depth; ++u) s << "      tile[tid + " << u * T << "u] = A::from_store(ld" << u << ");\n";
+      for (int u = 0; u < depth; ++u)
+        s << "      tile[slt ^ " << hex32(uint32_t(sw(uint64_t(u * T)))) << "] = A::from_store(ld" << u << ");\n";
       s << "    }\n";
     }
     s << "    __syncthreads();\n";
@@ -337,6 +361,7 @@ std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const 
       const int p = S.pbits[i];
       s << "      tl = ((tl >> " << p << ") << " << (p + 1) << ") | (tl & " << hex32((1u << p) - 1u) << ");\n";
     }
+    s << "      const uint32_t stl = tl ^ " << hsw_expr("tl") << ";\n";
     s << "      Cplx v[" << (1 << R) << "];\n";
     std::vector<uint32_t> off(size_t(1) << R);
     for (int j = 0; j < (1 << R); ++j) {
@@ -349,14 +374,14 @@ std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const 
       const uint32_t o = off[size_t(j)];
       if (vec2) {
         if (j & 1) continue;
-        s << "      {\n        const float4 w = *reinterpret_cast<const float4*>(tile + (tl | " << hex32(o & ~cpm)
-          << "));\n        v[" << j << "] = make_float2(w.x, w.y);\n        v[" << j + 1
+        s << "      {\n        const float4 w = *reinterpret_cast<const float4*>(tile + (stl ^ "
+          << hex32(uint32_t(sw(o & ~cpm))) << "));\n        v[" << j << "] = make_float2(w.x, w.y);\n        v[" << j + 1
           << "] = make_float2(w.z, w.w);\n      }\n";
       } else if (first_io) {
-        s << "      v[" << j << "] = A::from_store(reinterpret_cast<const Store*>(tile)[tl | " << hex32(o & ~cpm)
-          << "]);\n";
+        s << "      v[" << j << "] = A::from_store(reinterpret_cast<const Store*>(tile)[stl ^ "
+          << hex32(uint32_t(sw(o & ~cpm))) << "]);\n";
       } else {
-        s << "      v[" << j << "] = tile[tl | " << hex32(o & ~cpm) << "];\n";
+        s << "      v[" << j << "] = tile[stl ^ " << hex32(uint32_t(sw(o & ~cpm))) << "];\n";
       }
     }
     // Sign flips (CZ, multi-controlled phase flips) are kept pending, as
@@ -464,12 +489,12 @@ std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const 
       const uint32_t o = off[size_t(j)];
       if (vec2) {
         if (j & 1) continue;
-        s << "      *reinterpret_cast<float4*>(tile + (tl | " << hex32(o) << ")) = make_float4(v[" << j << "].x, v["
+        s << "      *reinterpret_cast<float4*>(tile + (stl ^ " << hex32(uint32_t(sw(o))) << ")) = make_float4(v[" << j << "].x, v["
           << j << "].y, v[" << j + 1 << "].x, v[" << j + 1 << "].y);\n";
       } else if (last_io) {
-        s << "      reinterpret_cast<Store*>(tile)[tl | " << hex32(o) << "] = A::to_store(v[" << j << "]);\n";
+        s << "      reinterpret_cast<Store*>(tile)[stl ^ " << hex32(uint32_t(sw(o))) << "] = A::to_store(v[" << j << "]);\n";
       } else {
-        s << "      tile[tl | " << hex32(o) << "] = v[" << j << "];\n";
+        s << "      tile[stl ^ " << hex32(uint32_t(sw(o))) << "] = v[" << j << "];\n";
       }
     }
     s << "    }\n    __syncthreads();\n";
@@ -500,15 +525,18 @@ std::string jit_source(const FPass& fp, const FStage* st, const FOp* ops, const 
       << "      const float4* t4 = reinterpret_cast<const float4*>(tile);\n"
       << "      const int64_t gb = base + toff;\n";
     for (int u = 0; u < depth; ++u)
-      s << "      g4[(gb + " << acc_goff(u) << ") >> 1] = t4[tid + " << u * T << "u];\n";
+      s << "      g4[(gb + " << acc_goff(u) << ") >> 1] = t4[(slt ^ " << hex32(uint32_t(sw(uint64_t(2 * u * T))))
+        << ") >> 1];\n";
     s << "    }\n";
   } else {
     s << "    {\n      const int64_t gb = base + toff;\n";
     for (int u = 0; u < depth; ++u) {
       if (async)  // already in the storage format
-        s << "      g[gb + " << acc_goff(u) << "] = reinterpret_cast<const Store*>(tile)[tid + " << u * T << "u];\n";
+        s << "      g[gb + " << acc_goff(u) << "] = reinterpret_cast<const Store*>(tile)[slt ^ "
+          << hex32(uint32_t(sw(uint64_t(u * T)))) << "];\n";
       else
-        s << "      g[gb + " << acc_goff(u) << "] = A::to_store(tile[tid + " << u * T << "u]);\n";
+        s << "      g[gb + " << acc_goff(u) << "] = A::to_store(tile[slt ^ " << hex32(uint32_t(sw(uint64_t(u * T))))
+          << "]);\n";
     }
     s << "    }\n";
   }

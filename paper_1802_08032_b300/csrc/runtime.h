@@ -141,6 +141,9 @@ struct Env {
   // 30-qubit workload: complex64 9743 -> 10155 gates/s, double-float 1601
   // -> 1697)
   int64_t jit_direct = 1;
+  // generated kernels swizzle the tile in shared memory (bank conflicts of
+  // stages whose register bits hold the low local positions)
+  int64_t jit_swizzle = 1;
   // IEEE-FP64 passes are bound by the FP64 pipe, where the interpreting
   // kernel measured faster (30 qubits: 83.4 vs 88.3 ms a pass): they use
   // generated kernels only when this is 1

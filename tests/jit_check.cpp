@@ -68,7 +68,8 @@ int main(int argc, char** argv) {
   const int max_compile = argc > 8 ? std::atoi(argv[8]) : 1 << 30;
   JitShape shape{pl.arith, R, ctas};
   shape.copy = static_cast<JitCopy>(copy % 4);
-  shape.direct_store = copy >= 4;  // copy + 4: the last stage stores to HBM
+  shape.direct_store = (copy & 4) != 0;  // copy + 4: the last stage stores to HBM
+  shape.swizzle = (copy & 8) == 0;       // copy + 8: no shared-memory swizzle
   std::set<std::string> distinct;
   std::vector<std::string> todo;
   for (size_t i = 0; i < pl.fps.size(); ++i) {
@@ -79,8 +80,9 @@ int main(int argc, char** argv) {
       std::printf("GENFAIL pass %zu: %s\n", i, e.msg.c_str());
       return 3;
     }
-    if (i == 0 && argc > 9) {
-      FILE* f = std::fopen(argv[9], "w");
+    if (argc > 9 && (i == 0 || std::getenv("JIT_CHECK_ALL"))) {
+      const std::string name = std::string(argv[9]) + (i == 0 ? "" : "." + std::to_string(i));
+      FILE* f = std::fopen(name.c_str(), "w");
       if (f) {
         std::fputs(src.c_str(), f);
         std::fclose(f);

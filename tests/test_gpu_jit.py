@@ -47,7 +47,8 @@ def controlled_extras(n, seed):
     return ops
 
 
-def run_both(Q, env, n, ops, prec, arith=0, density=False, tile=0, min_q=None, copy=0, ctas=2, direct=0):
+def run_both(Q, env, n, ops, prec, arith=0, density=False, tile=0, min_q=None, copy=0, ctas=2, direct=0,
+             swizzle=1):
     """(interpreted, compiled) final states; checks the compiled run really
     launched generated kernels and none failed.  copy = 1 / 2: the bulk-copy
     (TMA) / async-copy pipeline forms of the generated kernels."""
@@ -57,6 +58,7 @@ def run_both(Q, env, n, ops, prec, arith=0, density=False, tile=0, min_q=None, c
     Q.setEnvOption(env, "jit_copy", copy)
     Q.setEnvOption(env, "jit_ctas", ctas)
     Q.setEnvOption(env, "jit_direct", direct)
+    Q.setEnvOption(env, "jit_swizzle", swizzle)
     if min_q is not None:
         Q.setEnvOption(env, "jit_min_qubits", min_q)
     try:
@@ -72,6 +74,7 @@ def run_both(Q, env, n, ops, prec, arith=0, density=False, tile=0, min_q=None, c
         Q.setEnvOption(env, "jit_copy", -1)
         Q.setEnvOption(env, "jit_ctas", 0)
         Q.setEnvOption(env, "jit_direct", 1)
+        Q.setEnvOption(env, "jit_swizzle", 1)
         Q.setEnvOption(env, "arith", 0)
         Q.setEnvOption(env, "tile_qubits", 0)
         Q.setEnvOption(env, "jit_min_qubits", 20)
@@ -93,17 +96,19 @@ def test_compiled_passes_match_interpreter_and_oracle(Q, env, prec, arith, n, co
     assert np.max(np.abs(b - ref)) <= AMP_TOL[prec]
 
 
-@pytest.mark.parametrize("copy,ctas,direct", [(0, 2, 0), (1, 3, 0), (2, 3, 0), (2, 3, 1), (0, 2, 1)])
+@pytest.mark.parametrize("copy,ctas,direct,swizzle", [(0, 2, 0, 1), (1, 3, 0, 1), (2, 3, 0, 1), (2, 3, 1, 1),
+                                                      (0, 2, 1, 1), (2, 3, 1, 0)])
 @pytest.mark.parametrize("prec,arith", [(64, 0), (128, 0), (128, 1)])
 @pytest.mark.parametrize("tile", [9, 11])
-def test_compiled_passes_with_small_tiles(Q, env, prec, arith, tile, copy, ctas, direct):
+def test_compiled_passes_with_small_tiles(Q, env, prec, arith, tile, copy, ctas, direct, swizzle):
     """Tiles smaller than the register: conditions on global bits (the tile
     base) and on local bits outside the stage's register bits; with the
     bulk-copy pipeline, several tiles per CTA (both buffers in turn)."""
     n = 15
     ops = C.random_circuit(n, 12, 77 + tile, extras=True) + controlled_extras(n, tile)
     ops = ops[len(ops) // 4:]  # a suffix: phases land on qubits outside the first tile
-    a, b = run_both(Q, env, n, ops, prec, arith, tile=tile, min_q=1, copy=copy, ctas=ctas, direct=direct)
+    a, b = run_both(Q, env, n, ops, prec, arith, tile=tile, min_q=1, copy=copy, ctas=ctas, direct=direct,
+                    swizzle=swizzle)
     assert np.array_equal(a, b), float(np.max(np.abs(a - b)))
     ref = O.run_circuit(n, ops).a
     assert np.max(np.abs(b - ref)) <= AMP_TOL[prec]

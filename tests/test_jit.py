@@ -102,11 +102,12 @@ def test_three_ctas_per_sm_compiles(harness):
     assert compiled == 2
 
 
-@pytest.mark.parametrize("copy", [1, 2, 4, 6])
+@pytest.mark.parametrize("copy", [1, 2, 4, 6, 8, 14])
 @pytest.mark.parametrize("prec,arith,k", [(64, 0, 12), (64, 0, 13), (128, 0, 11), (128, 1, 11)])
 def test_copy_pipelines_compile(harness, prec, arith, k, copy):
-    """The bulk-copy (TMA) and async-copy double-buffered forms, and (copy + 4)
-    the last stage storing straight to HBM."""
+    """The bulk-copy (TMA) and async-copy double-buffered forms, (copy + 4)
+    the last stage storing straight to HBM, (copy + 8) without the
+    shared-memory swizzle."""
     passes, compiled, _ = run(harness, 26, C.workload_30q(26), prec=prec, arith=arith, k_req=k, copy=copy,
                               max_compile=2)
     assert compiled == 2
