@@ -170,6 +170,13 @@ int qsDiagBoundedWait(QuESTEnv env, int timeoutUs);
  *                   = the last stage of a generated pass writes its
  *                   amplitudes straight to HBM instead of through shared
  *                   memory (not with bulk copies); 0 = through the tile.
+ *                   "jit_swizzle": 1 (default) = the generated kernels
+ *                   place a tile's amplitudes in shared memory under an
+ *                   XOR swizzle of the 16-byte chunk index (so stages whose
+ *                   register bits hold the low positions spread a warp over
+ *                   the banks; not with bulk copies, which land chunks
+ *                   unpermuted); 0 = plain layout.  Amplitudes are the
+ *                   same either way.
  *                   Read-only counters: "jit_launches", "jit_rejected",
  *                   "jit_ready", "jit_pending", "jit_failed",
  *                   "jit_compile_ms".
