@@ -875,8 +875,10 @@ def multi_sweep(Q, env, torch, stream, n=30):
                         # the same pass on the CUDA cores, and with the targets on the lowest bits
                         low = tuple(range(m))
                         try:
-                            for mode, name in ((0, "cuda_cores"), (2, "tensor_cores")):
+                            for mode, stage, name in ((0, 1, "cuda_cores"), (2, 1, "tensor_cores"),
+                                                      (2, 0, "tensor_cores_gather")):
                                 Q.setEnvOption(env, "multi_tc", mode)
+                                Q.setEnvOption(env, "multi_tc_stage", stage)
                                 ms = timed(torch, stream, lambda: Q.multiQubitUnitary(q, tg, U), 2)
                                 out[f"c64_m{m}_{name}"] = {"ms": ms, "GBps": 2 * (1 << n) * S / ms / 1e6}
                                 ms = timed(torch, stream, lambda: Q.multiQubitUnitary(q, low, U), 2)
@@ -884,6 +886,7 @@ def multi_sweep(Q, env, torch, stream, n=30):
                                                                        "GBps": 2 * (1 << n) * S / ms / 1e6}
                         finally:
                             Q.setEnvOption(env, "multi_tc", 1)
+                            Q.setEnvOption(env, "multi_tc_stage", 1)
                         ms = timed(torch, stream, lambda: Q.multiQubitUnitary(q, low, U), 2)
                         out[f"c64_m{m}_low_targets"] = {"ms": ms, "GBps": 2 * (1 << n) * S / ms / 1e6}
             finally:

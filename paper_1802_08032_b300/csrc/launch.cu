@@ -216,29 +216,76 @@ void launch_tc(Env& env, Reg& r, const TcParams<M>& p, const Fixed& fx, int64_t 
                                                                env.d_status);
 }
 
+// The staged tensor-core pass (k_sv_multi_tcs): a persistent grid of CTAs
+// (128 threads for 4 targets, 256 for 5), as many per SM as registers,
+// shared memory and tensor memory (512 columns) allow.
+template <int M, bool PAIR>
+void launch_tcs(Env& env, Reg& r, const TcParams<M>& p, const Fixed& fx, int64_t nsel) {
+  constexpr size_t smem = tcs_smem_bytes<M>();
+  static const int per_sm = [] {
+    QS_CUDA(cudaFuncSetAttribute(k_sv_multi_tcs<M, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    cudaFuncAttributes fa{};
+    QS_CUDA(cudaFuncGetAttributes(&fa, k_sv_multi_tcs<M, PAIR>));
+    const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+    const int by_regs = 65536 / std::max(1, regs_warp * (kTcRows * tcs_group<M>() / 32));
+    const int by_smem = int((228 * 1024) / (smem + fa.sharedSizeBytes + 1024));
+    return std::max(1, std::min({by_regs, by_smem, int(512 / tcs_tmem_cols<M>()), 8}));
+  }();
+  const int64_t ntiles = nsel / kTcRows;
+  const int grid = int(std::min<int64_t>(ntiles, int64_t(env.sms) * per_sm));
+  KTimer kt(env, "sv_multi_tc_c64", double(nsel) * 2 * (1 << M) * sizeof(float2),
+            double(nsel) * (1 << (2 * M)) * 8);
+  k_sv_multi_tcs<M, PAIR><<<grid, kTcRows * tcs_group<M>(), smem, env.stream>>>(static_cast<float2*>(r.d), nsel, fx, p,
+                                                                env.d_status);
+}
+
 template <int M>
 void multi_pass_tc(Env& env, Reg& r, const MultiParams<float, M>& mp, const Fixed& fx, int64_t nsel) {
+  constexpr int D2 = 1 << M;
   TcParams<M> p{};
-  for (int k = 0; k < 8; ++k) p.t[k] = mp.t[k];
-  for (int e = 0; e < (1 << (2 * M)); ++e) p.u[e] = make_float2(mp.u[e].x, mp.u[e].y);
-  int tmin = 64;
-  for (int k = 0; k < M; ++k) tmin = std::min(tmin, int(mp.t[k]));
-  // targets among the five lowest qubits: a thread's block would be runs of
-  // contiguous amplitudes, so load the tile in address order instead; the
-  // enumeration takes the 7 lowest free qubits and the targets, ascending
-  if (tmin < 5 && nsel >= kTcRows) {
+  // targets ascending: target k of the kernel is mp.t[order[k]], so bit k
+  // of a kernel block index is bit order[k] of the matrix's index
+  int order[M];
+  for (int k = 0; k < M; ++k) order[k] = k;
+  std::sort(order, order + M, [&](int x, int y) { return mp.t[x] < mp.t[y]; });
+  for (int k = 0; k < M; ++k) p.t[k] = mp.t[order[k]];
+  auto orig = [&](int i) {
+    int o = 0;
+    for (int k = 0; k < M; ++k)
+      if ((i >> k) & 1) o |= 1 << order[k];
+    return o;
+  };
+  for (int n = 0; n < D2; ++n)
+    for (int l = 0; l < D2; ++l) {
+      const auto& u = mp.u[orig(n) * D2 + orig(l)];
+      p.u[n * D2 + l] = make_float2(u.x, u.y);
+    }
+  const int tmin = p.t[0];
+  const bool staged = env.multi_tc_stage != 0 && nsel >= kTcRows;
+  // tiles in address order (the staged kernel, or targets among the five
+  // lowest qubits, where a thread's block would be runs of contiguous
+  // amplitudes): the enumeration takes the 7 lowest free qubits and the
+  // targets, ascending
+  if ((staged || tmin < 5) && nsel >= kTcRows) {
     uint64_t fixed = 0;
     for (int k = 0; k < fx.n; ++k) fixed |= uint64_t(1) << fx.pos[k];
     std::vector<std::pair<int, int>> en;  // (qubit, role)
     for (int q = 0, j = 0; q < r.nq && j < 7; ++q)
       if (!((fixed >> q) & 1)) en.push_back({q, j++});
-    for (int k = 0; k < M; ++k) en.push_back({int(mp.t[k]), 0x80 | k});
+    for (int k = 0; k < M; ++k) en.push_back({int(p.t[k]), 0x80 | k});
     std::sort(en.begin(), en.end());
     for (size_t k = 0; k < en.size(); ++k) {
       p.pos[k] = uint8_t(en[k].first);
       p.role[k] = uint8_t(en[k].second);
     }
-    launch_tc<M, true>(env, r, p, fx, nsel);
+    if (staged) {
+      p.split = p.pos[0] != 0;  // qubit 0 is a control
+      // target 0 (the lowest) at qubit 0: a row's elements 2l, 2l + 1 adjacent
+      if (p.pos[0] == 0 && p.role[0] == 0x80) launch_tcs<M, true>(env, r, p, fx, nsel);
+      else launch_tcs<M, false>(env, r, p, fx, nsel);
+    } else {
+      launch_tc<M, true>(env, r, p, fx, nsel);
+    }
   } else {
     launch_tc<M, false>(env, r, p, fx, nsel);
   }

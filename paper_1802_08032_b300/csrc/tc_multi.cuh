@@ -40,6 +40,7 @@ struct TcParams {
   // t[u], else the block-index bit it carries
   uint8_t pos[16];
   uint8_t role[16];
+  uint8_t split;                    // staged kernel: qubit 0 is a control (pairs copied as two 8 B halves)
   float2 u[1 << (2 * MT)];          // row-major matrix
 };
 
@@ -149,6 +150,77 @@ __device__ __forceinline__ void wait_ld(uint32_t (&r)[N]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" : QS_R32(QS_INOUT, r, 0)::"memory");
   if constexpr (N > 32) asm volatile("" : QS_R32(QS_INOUT, r, 32));
 }
+
+// Columns [O, O + 32) of this warp's 32 lanes written from r[0 .. 32)
+// (thread i: lane 32 * warp + i).  Asynchronous: complete after wait_st.
+template <int N>
+__device__ __forceinline__ void st32(uint32_t taddr, const uint32_t (&r)[N]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+      "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+      "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+
+// 16-column forms: columns [taddr, taddr + 16) of this warp's lanes into
+// r[O .. O + 16) (ld16) or from r[0 .. 16) (st16).
+template <int O, int N>
+__device__ __forceinline__ void ld16(uint32_t taddr, uint32_t (&r)[N]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[O + 0]), "=r"(r[O + 1]), "=r"(r[O + 2]), "=r"(r[O + 3]), "=r"(r[O + 4]), "=r"(r[O + 5]),
+        "=r"(r[O + 6]), "=r"(r[O + 7]), "=r"(r[O + 8]), "=r"(r[O + 9]), "=r"(r[O + 10]), "=r"(r[O + 11]),
+        "=r"(r[O + 12]), "=r"(r[O + 13]), "=r"(r[O + 14]), "=r"(r[O + 15])
+      : "r"(taddr));
+}
+
+template <int N>
+__device__ __forceinline__ void st16(uint32_t taddr, const uint32_t (&r)[N]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+
+__device__ __forceinline__ void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// D (tensor memory) (+)= A (tensor memory, 128 lanes = rows, one TF32 per
+// column) x B (shared-memory descriptor).
+__device__ __forceinline__ void mma_tf32_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+// Asynchronous global -> shared copies (cp.async; this thread's groups).
+__device__ __forceinline__ void cp16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp8(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Shared-memory position (in 8-byte elements) of tile element e in the
+// staged kernel: its 16-byte chunk c = e >> 1 moves to c ^ h(c >> 3), h the
+// XOR of c's 3-bit groups, so that the rows a warp reads (any five of the
+// enumeration bits) spread over the banks; linear over GF(2), so the
+// position of a union of disjoint bit sets is the XOR of their positions.
+__host__ __device__ constexpr uint32_t chunk_swz(uint32_t c) {
+  return c ^ (((c >> 3) ^ (c >> 6) ^ (c >> 9)) & 7u);
+}
+__host__ __device__ constexpr uint32_t elem_pos(uint32_t e) { return (chunk_swz(e >> 1) << 1) | (e & 1u); }
 
 }  // namespace tc
 
@@ -359,6 +431,284 @@ __global__ void __launch_bounds__(kTcRows) k_sv_multi_tc(float2* __restrict__ a,
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(ND)));
+}
+
+// ------------------------------------------------------------ staged form
+// The staged kernel (registers with at least 7 free qubits, nsel >= 128):
+// a tile is the 128 x 2^m amplitudes whose enumeration bits (the 7 lowest
+// free qubits and the targets, ascending: pos[], role[]) vary, i.e. the
+// address pattern tile base + dep(e), e < 2^(7+m).  Tiles are copied in
+// address order (16-byte cp.async chunks, coalesced whatever the targets)
+// into one of two shared-memory stages, two tiles ahead of the one being
+// worked.  G threads share a block (row): each reads its 2^m / G elements
+// out of the stage, splits them into TF32 hi and lo and writes them to the
+// row's tensor-memory lane as its columns of the A operand (tcgen05.st);
+// the MMAs read A from tensor memory and B from shared memory, and each
+// thread stores its 2^m / G outputs straight from registers.  Shared
+// memory: the two stages and B hi / lo; tensor memory: the accumulator
+// (2^(m+1) columns) and A hi / lo (2^(m+1) each).  With 2^m / G = 16
+// elements a thread, m = 5 runs 256 threads (two CTAs, 16 warps an SM; the
+// tensor memory holds two) and m = 4 runs 128 (four CTAs an SM).
+template <int MT>
+__host__ __device__ constexpr int tcs_group() {
+  return MT == 5 ? 2 : 1;
+}
+
+template <int MT>
+__host__ __device__ constexpr uint32_t tcs_tmem_cols() {
+  return (6u << MT) <= 32u ? 32u : (6u << MT) <= 64u ? 64u : (6u << MT) <= 128u ? 128u : (6u << MT) <= 256u ? 256u : 512u;
+}
+
+template <int MT>
+__host__ __device__ constexpr size_t tcs_stage_bytes() {
+  return size_t(kTcRows) * (1 << MT) * 8;
+}
+
+// Copy chunks (16 bytes) per thread per tile.
+template <int MT>
+__host__ __device__ constexpr int tcs_rounds() {
+  return (1 << MT) / (2 * tcs_group<MT>());
+}
+
+// Shared memory of the staged kernel: two stages, B hi / lo, the target
+// offsets (int64 per combination), the address offsets and chunk positions
+// of the copy rounds (int64, uint16), the mbarrier and the tensor-memory
+// slot.
+template <int MT>
+__host__ __device__ constexpr size_t tcs_smem_bytes() {
+  return 2 * tcs_stage_bytes<MT>() + size_t(2) * (2 << MT) * (2 << MT) * 4 + 8 * (1 << MT) + 10 * tcs_rounds<MT>() + 64;
+}
+
+// PAIR: enumeration bit 0 is target 0 at qubit 0 (targets sorted
+// ascending), so elements 2l, 2l + 1 of a row are adjacent in memory and in
+// the stage: read and stored as one 16-byte access.
+template <int MT, bool PAIR>
+__global__ void __launch_bounds__(kTcRows * tcs_group<MT>())
+    k_sv_multi_tcs(float2* __restrict__ a, int64_t nsel, const __grid_constant__ Fixed fx,
+                   const __grid_constant__ TcParams<MT> p, unsigned* status) {
+  constexpr int D2 = 1 << MT, KD = 2 * D2, ND = 2 * D2, E = 7 + MT;
+  constexpr int G = tcs_group<MT>(), T = kTcRows * G, LT = G == 2 ? 8 : 7;  // T = 2^LT threads
+  constexpr int LH = D2 / G;       // elements (and outputs) of a row per thread
+  constexpr int NR = tcs_rounds<MT>();
+  static_assert(MT >= 4 && MT <= 5 && LH == 16, "16 columns a thread per tensor-memory access");
+  static_assert(NR == 1 << (E - 1 - LT), "copy rounds");
+  constexpr uint32_t kStage = uint32_t(tcs_stage_bytes<MT>()), kB = ND * KD * 4;
+  constexpr uint32_t kCols = tcs_tmem_cols<MT>();
+  constexpr uint32_t kIdesc = tc::idesc_tf32(kTcRows, ND);
+  static_assert(ND + 2 * KD <= int(kCols), "tensor-memory layout");
+  extern __shared__ __align__(1024) uint8_t smem[];
+  float* sBh = reinterpret_cast<float*>(smem + 2 * kStage);
+  float* sBl = reinterpret_cast<float*>(smem + 2 * kStage + kB);
+  int64_t* ldep = reinterpret_cast<int64_t*>(smem + 2 * kStage + 2 * kB);  // [D2] address offset of combination l
+  int64_t* cdep = ldep + D2;                                               // [NR] address offset of round i
+  uint16_t* cpos = reinterpret_cast<uint16_t*>(cdep + NR);                 // [NR] chunk position of round i
+  constexpr uint32_t kBar = (2 * kStage + 2 * kB + 8 * D2 + 10 * NR + 7) / 8 * 8;
+  static_assert(kBar + 16 <= tcs_smem_bytes<MT>(), "shared-memory layout");
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kBar);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, row = tid & (kTcRows - 1), hf = tid / kTcRows;
+
+  // enumeration index of row bit b and of target u
+  int krow[7], ktg[MT];
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    const int r = p.role[k];
+#pragma unroll
+    for (int u = 0; u < MT; ++u)
+      if (r == (0x80 | u)) ktg[u] = k;
+#pragma unroll
+    for (int b = 0; b < 7; ++b)
+      if (r == b) krow[b] = k;
+  }
+  // this thread's row: element bits (erow), their stage position and their
+  // address offset; its elements hf * LH + i: stage positions lp[i]
+  uint32_t erow = 0;
+  int64_t rdep = 0;
+#pragma unroll
+  for (int b = 0; b < 7; ++b)
+    if ((row >> b) & 1) {
+      erow |= 1u << krow[b];
+      rdep += int64_t(1) << p.pos[krow[b]];
+    }
+  const uint32_t prow = tc::elem_pos(erow);
+  uint32_t lp[LH];
+#pragma unroll
+  for (int i = 0; i < LH; ++i) {
+    const int l = hf * LH + i;
+    uint32_t el = 0;
+#pragma unroll
+    for (int u = 0; u < MT; ++u)
+      if ((l >> u) & 1) el |= 1u << ktg[u];
+    lp[i] = prow ^ tc::elem_pos(el);
+  }
+  // copy chunks tid + T i: element bits 1..LT from tid (address ctdep,
+  // position chunk_swz(tid)), bits LT + 1.. from i (cdep[i], cpos[i])
+  int64_t ctdep = 0;
+#pragma unroll
+  for (int k = 1; k <= LT; ++k)
+    if ((tid >> (k - 1)) & 1) ctdep += int64_t(1) << p.pos[k];
+  const uint32_t ctpos = tc::chunk_swz(uint32_t(tid));
+  const int64_t half = int64_t(1) << p.pos[0];  // address step of element bit 0 (split copies)
+
+  // B = [[Re U^T, Im U^T], [-Im U^T, Re U^T]] stored N x K (row n = output
+  // column): row n < D2 gives Re w[n], row D2 + n gives Im w[n].
+  for (int e = tid; e < ND * KD; e += T) {
+    const int n = e / KD, k = e % KD;
+    const float2 u = p.u[(n & (D2 - 1)) * D2 + (k & (D2 - 1))];
+    const float v = n < D2 ? (k < D2 ? u.x : -u.y) : (k < D2 ? u.y : u.x);
+    const float h = tc::tf32_hi(v);
+    sBh[tc::at<ND>(n, k)] = h;
+    sBl[tc::at<ND>(n, k)] = v - h;
+  }
+  if (tid < D2) {
+    int64_t d = 0;
+#pragma unroll
+    for (int u = 0; u < MT; ++u)
+      if ((tid >> u) & 1) d += int64_t(1) << p.pos[ktg[u]];
+    ldep[tid] = d;
+  }
+  if (tid < NR) {
+    int64_t d = 0;
+    for (int k = LT + 1; k < E; ++k)
+      if ((tid >> (k - LT - 1)) & 1) d += int64_t(1) << p.pos[k];
+    cdep[tid] = d;
+    cpos[tid] = uint16_t(tc::chunk_swz(uint32_t(tid) << LT));
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tslot)),
+                 "r"(kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;");  // B, written by the threads, read by the MMAs
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+  const uint32_t bar_a = tc::smem_u32(bar);
+  const uint32_t bh = tc::smem_u32(sBh), bl = tc::smem_u32(sBl);
+  const uint32_t stage0 = tc::smem_u32(smem);
+  const uint32_t trow = tmem + (uint32_t((warp & 3) * 32) << 16);  // this warp's lanes (its rows)
+  const uint32_t cre = uint32_t(hf * LH), cim = uint32_t(D2 + hf * LH);  // this thread's columns
+  const bool split = p.split != 0;
+
+  const int64_t ntiles = nsel / kTcRows;  // nsel is a power of two >= 128
+  // copies of tile t into stage s (every thread its NR chunks)
+  auto issue = [&](int64_t t, int s) {
+    const float2* src = a + deposit(t * kTcRows, fx) + ctdep;
+    const uint32_t dst = stage0 + uint32_t(s) * kStage;
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+      const uint32_t d = dst + ((ctpos ^ cpos[i]) << 4);
+      const float2* sp = src + cdep[i];
+      if (!split) {
+        tc::cp16(d, sp);
+      } else {
+        tc::cp8(d, sp);
+        tc::cp8(d + 8, sp + half);
+      }
+    }
+  };
+  int64_t tile = blockIdx.x;
+  const int64_t step = gridDim.x;
+  if (tile < ntiles) issue(tile, 0);
+  tc::cp_commit();
+  if (tile + step < ntiles) issue(tile + step, 1);
+  tc::cp_commit();
+  uint32_t parity = 0;
+  bool ok = true;
+  int s = 0;
+  for (; tile < ntiles; tile += step, s ^= 1) {
+    tc::cp_wait<1>();  // this thread's copies of this tile
+    __syncthreads();   // everyone's
+    const float2* st = reinterpret_cast<const float2*>(smem + uint32_t(s) * kStage);
+    float2 v[LH];
+    if constexpr (PAIR) {
+#pragma unroll
+      for (int i = 0; i < LH; i += 2) {
+        const float4 q = *reinterpret_cast<const float4*>(st + lp[i]);
+        v[i] = make_float2(q.x, q.y);
+        v[i + 1] = make_float2(q.z, q.w);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < LH; ++i) v[i] = st[lp[i]];
+    }
+    // this thread's columns of A = [Re v, Im v] as TF32 hi and lo: hi at
+    // ND.., lo at ND + KD..
+    {
+      uint32_t h[16], lo[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const float hx = tc::tf32_hi(v[i].x);
+        h[i] = __float_as_uint(hx);
+        lo[i] = __float_as_uint(v[i].x - hx);
+      }
+      tc::st16(trow + uint32_t(ND) + cre, h);
+      tc::st16(trow + uint32_t(ND + KD) + cre, lo);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const float hy = tc::tf32_hi(v[i].y);
+        h[i] = __float_as_uint(hy);
+        lo[i] = __float_as_uint(v[i].y - hy);
+      }
+      tc::st16(trow + uint32_t(ND) + cim, h);
+      tc::st16(trow + uint32_t(ND + KD) + cim, lo);
+    }
+    tc::wait_st();
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();  // A complete; the stage is free; last tile's accumulator reads done
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tile + 2 * step < ntiles) issue(tile + 2 * step, s);
+    tc::cp_commit();
+    if (tid == 0) {
+      // lo*hi + hi*lo + hi*hi; K advances 8 columns (two core matrices of B)
+      const uint32_t as[3] = {uint32_t(ND + KD), uint32_t(ND), uint32_t(ND)}, bs[3] = {bh, bl, bh};
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int kk = 0; kk < KD / 8; ++kk)
+          tc::mma_tf32_ts(tmem, tmem + as[q] + uint32_t(kk * 8), tc::desc(bs[q] + kk * 2 * (ND * 16), ND * 16, 128),
+                          kIdesc, (q | kk) != 0);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_a));
+    }
+    const int64_t j = deposit(tile * kTcRows, fx) + rdep;
+    const bool done = tc::mbar_wait(bar_a, parity);
+    parity ^= 1u;
+    if (__syncthreads_or(!done)) {
+      ok = false;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    uint32_t r[32];
+    tc::ld16<0>(trow + cre, r);
+    tc::ld16<16>(trow + cim, r);
+    tc::wait_ld(r);
+    float2* dst = a + j;
+    if constexpr (PAIR) {
+#pragma unroll
+      for (int i = 0; i < LH; i += 2)
+        *reinterpret_cast<float4*>(dst + ldep[hf * LH + i]) =
+            make_float4(__uint_as_float(r[i]), __uint_as_float(r[16 + i]), __uint_as_float(r[i + 1]),
+                        __uint_as_float(r[16 + i + 1]));
+    } else {
+#pragma unroll
+      for (int i = 0; i < LH; ++i)
+        dst[ldep[hf * LH + i]] = make_float2(__uint_as_float(r[i]), __uint_as_float(r[16 + i]));
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+  }
+  tc::cp_wait<0>();  // no copy still in flight when the CTA ends
+  if (!ok) {
+    if (tid == 0) atomicOr(status, 1u);
+    tc::mbar_wait(bar_a, parity ^ 1u);  // the outstanding commit, bounded
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
 }
 
 // Diagnostic: the bounded wait of k_sv_multi_tc on an mbarrier that nothing

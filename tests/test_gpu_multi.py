@@ -148,23 +148,55 @@ def test_multi_target_tensor_cores(Q, env, m, ctrls, tset):
     ref = O.State(n, amps=psi)
     ref.multi(targets, U, ctrls)
     out = {}
-    for tc in (2, 1, 0):
-        Q.setEnvOption(env, "multi_tc", tc)
-        q = Q.createQureg(n, 64, env)
-        Q.setAmps(q, psi)
-        Q.multiControlledMultiQubitUnitary(q, ctrls, targets, U)
-        Q.multiControlledMultiQubitUnitary(q, ctrls, targets, U.conj().T)
-        Q.multiControlledMultiQubitUnitary(q, ctrls, targets, U)
-        out[tc] = Q.copyStateToHost(q)
-        Q.destroyQureg(q)
-    Q.setEnvOption(env, "multi_tc", 1)
+    try:
+        for tc, stage in ((2, 1), (1, 1), (2, 0), (0, 1)):
+            Q.setEnvOption(env, "multi_tc", tc)
+            Q.setEnvOption(env, "multi_tc_stage", stage)
+            q = Q.createQureg(n, 64, env)
+            Q.setAmps(q, psi)
+            Q.multiControlledMultiQubitUnitary(q, ctrls, targets, U)
+            Q.multiControlledMultiQubitUnitary(q, ctrls, targets, U.conj().T)
+            Q.multiControlledMultiQubitUnitary(q, ctrls, targets, U)
+            out[(tc, stage)] = Q.copyStateToHost(q)
+            Q.destroyQureg(q)
+    finally:
+        Q.setEnvOption(env, "multi_tc", 1)
+        Q.setEnvOption(env, "multi_tc_stage", 1)
     # three gates of 2^(m+1)-term FP32 sums whose products carry about 2^-23
     # relative error each (the TF32 split): bound 5e-6 of the largest
     # amplitude, well inside the complex64 bar of 1e-5 absolute
     scale = np.max(np.abs(ref.a))
-    for tc in (2, 1):
-        assert np.max(np.abs(out[tc] - ref.a)) <= 5e-6 * scale
-        assert np.max(np.abs(out[tc] - out[0])) <= 5e-6 * scale
+    for key in ((2, 1), (1, 1), (2, 0)):
+        assert np.max(np.abs(out[key] - ref.a)) <= 5e-6 * scale, key
+        assert np.max(np.abs(out[key] - out[(0, 1)])) <= 5e-6 * scale, key
+    # staged tiles (A in tensor memory) and register gathers (A in shared
+    # memory) feed the same TF32 operands to the same products
+    assert np.max(np.abs(out[(2, 1)] - out[(2, 0)])) <= 1e-6 * scale
+
+
+@pytest.mark.parametrize("n", [10, 11, 12, 13])
+def test_multi_target_tensor_cores_small_registers(Q, env, n):
+    """Five targets on 10-13 qubits on the tensor cores: fewer than seven
+    free qubits (one partial 128-block tile, the register-gather kernel) up
+    to one and two full staged tiles, with the lowest target at qubit 0 and
+    a control on qubit 0."""
+    psi = rand_state(n, 80 + n)
+    U = rand_u(32, 90 + n)
+    Q.setEnvOption(env, "multi_tc", 2)
+    try:
+        for targets, ctrls in (((0, 3, n - 1, 5, 2), ()), ((4, 1, 6, 2, 7), (0,))):
+            if n - len(targets) - len(ctrls) < 1:
+                continue
+            ref = O.State(n, amps=psi)
+            ref.multi(targets, U, ctrls)
+            q = Q.createQureg(n, 64, env)
+            Q.setAmps(q, psi)
+            Q.multiControlledMultiQubitUnitary(q, ctrls, targets, U)
+            got = Q.copyStateToHost(q)
+            Q.destroyQureg(q)
+            assert np.max(np.abs(got - ref.a)) <= 5e-6 * np.max(np.abs(ref.a)), (targets, ctrls)
+    finally:
+        Q.setEnvOption(env, "multi_tc", 1)
 
 
 def test_multi_target_tensor_cores_density_matrix(Q, env):
@@ -322,8 +354,8 @@ def test_multi_target_density_matrix_14_qubits(Q, env, prec, m, targets, ctrls):
         assert abs(tr - 1.0) <= 1e-5
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
-def test_multi_target_random_placements(Q, env, mode):
+@pytest.mark.parametrize("mode,stage", [(0, 1), (1, 1), (2, 1), (2, 0)])
+def test_multi_target_random_placements(Q, env, mode, stage):
     """Complex64 gates on 2-5 targets at seeded random positions, most with a
     target among the five lowest qubits and some with controls there too
     (every table the shared-memory tile and tensor-core paths derive from
@@ -332,6 +364,7 @@ def test_multi_target_random_placements(Q, env, mode):
     rng = np.random.default_rng(500 + mode)
     psi = rand_state(n, 61)
     Q.setEnvOption(env, "multi_tc", mode)
+    Q.setEnvOption(env, "multi_tc_stage", stage)
     try:
         for case in range(24):
             m = int(rng.integers(2, 6))
@@ -354,3 +387,4 @@ def test_multi_target_random_placements(Q, env, mode):
             assert np.max(np.abs(got - ref.a)) <= 5e-6 * np.max(np.abs(ref.a)), (m, targets, ctrls)
     finally:
         Q.setEnvOption(env, "multi_tc", 1)
+        Q.setEnvOption(env, "multi_tc_stage", 1)
