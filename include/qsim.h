@@ -139,9 +139,19 @@ int qsDiagBoundedWait(QuESTEnv env, int timeoutUs);
  *                   pairs, three products accumulated in FP32: a few units of
  *                   1e-7 of the largest amplitude per gate), 0 = FP32 on the
  *                   CUDA cores, 1 = by shape (default): 5 targets on the
- *                   tensor cores, 4 on the CUDA cores (paired FP32 FMAs,
- *                   faster there; through shared-memory tiles when a target
- *                   is below qubit 5)
+ *                   tensor cores, 4 on the tensor cores when at least 7
+ *                   qubits are neither target nor control (the staged
+ *                   kernel) and on the CUDA cores otherwise (paired FP32
+ *                   FMAs; through shared-memory tiles when a target is
+ *                   below qubit 5)
+ *   "multi_tc_stage" tensor-core passes on registers with at least 7 free
+ *                   qubits: 1 (default) = staged kernel (tiles copied in
+ *                   address order into shared memory two ahead, the A
+ *                   operand written to tensor memory, coalesced stores
+ *                   whatever the targets); 0 = the register-gather kernel
+ *                   (A staged in shared memory; fewer than 7 free qubits
+ *                   always use it).  Same products, amplitudes within a
+ *                   few units of 1e-7.
  *   "jit"           fused passes of registers of at least "jit_min_qubits"
  *                   stored qubits (default 20) as kernels generated for the
  *                   pass and compiled at run time (NVRTC, sm_103a), cached

@@ -219,13 +219,13 @@ void launch_tc(Env& env, Reg& r, const TcParams<M>& p, const Fixed& fx, int64_t 
 // The staged tensor-core pass (k_sv_multi_tcs): a persistent grid of CTAs
 // (128 threads for 4 targets, 256 for 5), as many per SM as registers,
 // shared memory and tensor memory (512 columns) allow.
-template <int M, bool PAIR>
+template <int M, int MODE>
 void launch_tcs(Env& env, Reg& r, const TcParams<M>& p, const Fixed& fx, int64_t nsel) {
   constexpr size_t smem = tcs_smem_bytes<M>();
   static const int per_sm = [] {
-    QS_CUDA(cudaFuncSetAttribute(k_sv_multi_tcs<M, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    QS_CUDA(cudaFuncSetAttribute(k_sv_multi_tcs<M, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     cudaFuncAttributes fa{};
-    QS_CUDA(cudaFuncGetAttributes(&fa, k_sv_multi_tcs<M, PAIR>));
+    QS_CUDA(cudaFuncGetAttributes(&fa, k_sv_multi_tcs<M, MODE>));
     const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;
     const int by_regs = 65536 / std::max(1, regs_warp * (kTcRows * tcs_group<M>() / 32));
     const int by_smem = int((228 * 1024) / (smem + fa.sharedSizeBytes + 1024));
@@ -235,7 +235,7 @@ void launch_tcs(Env& env, Reg& r, const TcParams<M>& p, const Fixed& fx, int64_t
   const int grid = int(std::min<int64_t>(ntiles, int64_t(env.sms) * per_sm));
   KTimer kt(env, "sv_multi_tc_c64", double(nsel) * 2 * (1 << M) * sizeof(float2),
             double(nsel) * (1 << (2 * M)) * 8);
-  k_sv_multi_tcs<M, PAIR><<<grid, kTcRows * tcs_group<M>(), smem, env.stream>>>(static_cast<float2*>(r.d), nsel, fx, p,
+  k_sv_multi_tcs<M, MODE><<<grid, kTcRows * tcs_group<M>(), smem, env.stream>>>(static_cast<float2*>(r.d), nsel, fx, p,
                                                                 env.d_status);
 }
 
@@ -280,9 +280,17 @@ void multi_pass_tc(Env& env, Reg& r, const MultiParams<float, M>& mp, const Fixe
     }
     if (staged) {
       p.split = p.pos[0] != 0;  // qubit 0 is a control
-      // target 0 (the lowest) at qubit 0: a row's elements 2l, 2l + 1 adjacent
-      if (p.pos[0] == 0 && p.role[0] == 0x80) launch_tcs<M, true>(env, r, p, fx, nsel);
-      else launch_tcs<M, false>(env, r, p, fx, nsel);
+      // row bits 0..4 at qubits 0..4: a warp's rows are consecutive
+      // amplitudes, stores straight from registers (5 targets; with 4, the
+      // four CTAs an SM measured faster storing through the stage, 0.92 vs
+      // 0.85 of HBM at 30 qubits); else results leave through the stage,
+      // read in pairs when target 0 is at qubit 0
+      bool direct = M == 5;
+      for (int k = 0; k < 5; ++k) direct = direct && p.pos[k] == k && p.role[k] == k;
+      const bool pair = p.pos[0] == 0 && p.role[0] == 0x80;
+      if (direct) launch_tcs<M, 0>(env, r, p, fx, nsel);
+      else if (pair) launch_tcs<M, 2>(env, r, p, fx, nsel);
+      else launch_tcs<M, 1>(env, r, p, fx, nsel);
     } else {
       launch_tc<M, true>(env, r, p, fx, nsel);
     }
@@ -374,14 +382,16 @@ void multi_pass(Env& env, Reg& r, const GateOp& op, int shift, uint64_t cmask, b
   const Fixed fx = make_fixed(bits);
   const int64_t nsel = r.dim >> fx.n;
   if constexpr (std::is_same<R, float>::value) {
-    // by shape: 5 targets on the tensor cores; up to 4 on the CUDA cores
-    // (paired FMAs), at 3-4 through shared-memory tiles when a target is
-    // among the five lowest qubits (a thread's block would be short
-    // contiguous runs)
+    // by shape: 5 targets on the tensor cores, and 4 where the staged
+    // tensor-core kernel runs (at least 7 free qubits); else up to 4 on the
+    // CUDA cores (paired FMAs), at 3-4 through shared-memory tiles when a
+    // target is among the five lowest qubits (a thread's block would be
+    // short contiguous runs)
     int tmin = 64;
     for (int k = 0; k < M; ++k) tmin = std::min(tmin, int(p.t[k]));
     if constexpr (M >= 4) {
-      if (env.multi_tc == 2 || (env.multi_tc == 1 && M == 5)) {
+      const bool staged = env.multi_tc_stage != 0 && nsel >= kTcRows;
+      if (env.multi_tc == 2 || (env.multi_tc == 1 && (M == 5 || staged))) {
         multi_pass_tc<M>(env, r, p, fx, nsel);
         return;
       }

@@ -14,14 +14,20 @@
 // FP32 accuracy (measured: a few units of 1e-7 of the largest amplitude per
 // gate).
 //
-// Per CTA: 128 threads, one block (GEMM row) per thread.  Operands in
-// shared memory in the no-swizzle K-major core-matrix layout (8 rows x 16
-// bytes per core matrix; consecutive core matrices 128 bytes apart along
-// the rows, R*16 bytes apart along K), the accumulator (128 lanes x
-// 2^(m+1) FP32 columns) in tensor memory.  One thread issues the MMAs and
-// commits them to an mbarrier; every thread waits (bounded), reads its row
-// back with tcgen05.ld and scatters it.  The next tile's gather is issued
-// before the wait, so global loads overlap the MMAs and the stores.
+// Two kernels.  The staged one (k_sv_multi_tcs, below) serves registers
+// with at least seven qubits that are neither target nor control: tiles
+// copied in address order into shared memory two tiles ahead, A written to
+// tensor memory, results stored coalesced.  The register-gather one
+// (k_sv_multi_tc) serves the rest and the "multi_tc_stage" 0 option: per
+// CTA 128 threads, one block (GEMM row) per thread, gathered into
+// registers; operands in shared memory in the no-swizzle K-major
+// core-matrix layout (8 rows x 16 bytes per core matrix; consecutive core
+// matrices 128 bytes apart along the rows, R*16 bytes apart along K), the
+// accumulator (128 lanes x 2^(m+1) FP32 columns) in tensor memory.  In
+// both, one thread issues the MMAs and commits them to an mbarrier; every
+// thread waits (bounded) and reads its row back with tcgen05.ld.  Here the
+// next tile's gather is issued before the wait, so global loads overlap
+// the MMAs and the stores.
 #pragma once
 #include <cstdint>
 
@@ -479,13 +485,21 @@ __host__ __device__ constexpr size_t tcs_smem_bytes() {
   return 2 * tcs_stage_bytes<MT>() + size_t(2) * (2 << MT) * (2 << MT) * 4 + 8 * (1 << MT) + 10 * tcs_rounds<MT>() + 64;
 }
 
-// PAIR: enumeration bit 0 is target 0 at qubit 0 (targets sorted
-// ascending), so elements 2l, 2l + 1 of a row are adjacent in memory and in
-// the stage: read and stored as one 16-byte access.
-template <int MT, bool PAIR>
+// MODE 0: the lowest five row bits are qubits 0..4 (targets and controls
+// above them), so a warp's 32 rows are 32 consecutive amplitudes: results
+// are stored straight from registers, coalesced, and the stage is refilled
+// as soon as A is in tensor memory.  MODE 1 and 2: a warp's rows are far
+// apart, so direct stores would touch up to 32 lines an instruction: the
+// results go back into the tile's stage (to the positions their inputs
+// came from) and leave it in address order, 16-byte chunks, the mirror of
+// the copy in; the stage is refilled after that.  MODE 2: enumeration bit
+// 0 is target 0 at qubit 0 (targets sorted ascending), so elements 2l,
+// 2l + 1 of a row are adjacent: read and written as one 16-byte access.
+template <int MT, int MODE>
 __global__ void __launch_bounds__(kTcRows * tcs_group<MT>())
     k_sv_multi_tcs(float2* __restrict__ a, int64_t nsel, const __grid_constant__ Fixed fx,
                    const __grid_constant__ TcParams<MT> p, unsigned* status) {
+  constexpr bool PAIR = MODE == 2, DIRECT = MODE == 0;
   constexpr int D2 = 1 << MT, KD = 2 * D2, ND = 2 * D2, E = 7 + MT;
   constexpr int G = tcs_group<MT>(), T = kTcRows * G, LT = G == 2 ? 8 : 7;  // T = 2^LT threads
   constexpr int LH = D2 / G;       // elements (and outputs) of a row per thread
@@ -662,8 +676,10 @@ __global__ void __launch_bounds__(kTcRows * tcs_group<MT>())
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();  // A complete; the stage is free; last tile's accumulator reads done
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (tile + 2 * step < ntiles) issue(tile + 2 * step, s);
-    tc::cp_commit();
+    if constexpr (DIRECT) {
+      if (tile + 2 * step < ntiles) issue(tile + 2 * step, s);
+      tc::cp_commit();
+    }
     if (tid == 0) {
       // lo*hi + hi*lo + hi*hi; K advances 8 columns (two core matrices of B)
       const uint32_t as[3] = {uint32_t(ND + KD), uint32_t(ND), uint32_t(ND)}, bs[3] = {bh, bl, bh};
@@ -687,17 +703,38 @@ __global__ void __launch_bounds__(kTcRows * tcs_group<MT>())
     tc::ld16<0>(trow + cre, r);
     tc::ld16<16>(trow + cim, r);
     tc::wait_ld(r);
-    float2* dst = a + j;
-    if constexpr (PAIR) {
-#pragma unroll
-      for (int i = 0; i < LH; i += 2)
-        *reinterpret_cast<float4*>(dst + ldep[hf * LH + i]) =
-            make_float4(__uint_as_float(r[i]), __uint_as_float(r[16 + i]), __uint_as_float(r[i + 1]),
-                        __uint_as_float(r[16 + i + 1]));
-    } else {
+    if constexpr (DIRECT) {
+      float2* dst = a + j;
 #pragma unroll
       for (int i = 0; i < LH; ++i)
         dst[ldep[hf * LH + i]] = make_float2(__uint_as_float(r[i]), __uint_as_float(r[16 + i]));
+    } else {
+      float2* so = reinterpret_cast<float2*>(smem + uint32_t(s) * kStage);
+      if constexpr (PAIR) {
+#pragma unroll
+        for (int i = 0; i < LH; i += 2)
+          *reinterpret_cast<float4*>(so + lp[i]) = make_float4(__uint_as_float(r[i]), __uint_as_float(r[16 + i]),
+                                                               __uint_as_float(r[i + 1]), __uint_as_float(r[16 + i + 1]));
+      } else {
+#pragma unroll
+        for (int i = 0; i < LH; ++i) so[lp[i]] = make_float2(__uint_as_float(r[i]), __uint_as_float(r[16 + i]));
+      }
+      __syncthreads();
+      float2* dst = a + (j - rdep) + ctdep;  // the tile's base + this thread's chunk bits
+#pragma unroll
+      for (int i = 0; i < NR; ++i) {
+        const float4 q = *reinterpret_cast<const float4*>(so + 2 * (ctpos ^ cpos[i]));
+        float2* dp = dst + cdep[i];
+        if (!split) {
+          *reinterpret_cast<float4*>(dp) = q;
+        } else {
+          dp[0] = make_float2(q.x, q.y);
+          dp[half] = make_float2(q.z, q.w);
+        }
+      }
+      __syncthreads();  // the stage is read out: refill it
+      if (tile + 2 * step < ntiles) issue(tile + 2 * step, s);
+      tc::cp_commit();
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
   }

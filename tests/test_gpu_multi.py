@@ -137,10 +137,11 @@ def test_multi_target_errors(Q, env):
 def test_multi_target_tensor_cores(Q, env, m, ctrls, tset):
     """Complex64 gates on 4-5 targets on the tensor cores (three TF32
     products per FP32 operand pair; forced, and chosen by shape): many
-    128-block tiles per CTA, targets mixed low and high or all among the
-    lowest qubits (tiles loaded in address order through shared memory) or
-    all above them (one block per thread), with and without controls, against
-    the CUDA-core kernel and the oracle."""
+    128-block tiles per CTA, targets mixed low and high, all among the
+    lowest qubits or all above them, with and without controls; the staged
+    kernel (every store form: straight from registers, through the stage
+    in pairs or in single elements) and the register-gather kernel, against
+    each other, the CUDA-core kernel and the oracle."""
     n = 20
     psi = rand_state(n, 40 + m)
     targets = tset[:m]
