@@ -632,9 +632,10 @@ def variants(Q, env, torch, stream, only=(), qubits=30, serve=(60, 0.0)):
         return {"ops_per_s": len(dops) / ms * 1e3, "ms_per_circuit": ms, "ops": len(dops)}
 
     def sv12(reps=300, tiles=(0, 9, 10)):
-        # the 12-qubit complex128 depth-20 circuit (64 KiB: one fused tile):
-        # latency-bound, so whole circuits are timed on the host clock, each
-        # reset, planned, run and reduced (calcTotalProb reads its result)
+        # the 12-qubit complex128 depth-20 circuit (64 KiB: one fused tile,
+        # spread over a cluster of 8 CTAs): latency-bound, so whole circuits
+        # are timed on the host clock, each reset, planned, run and reduced
+        # (calcTotalProb reads its result)
         import time
         ops12 = Q.to_qsops(C.workload_12q())
         q = Q.createQureg(12, 128, env)
@@ -654,10 +655,21 @@ def variants(Q, env, torch, stream, only=(), qubits=30, serve=(60, 0.0)):
                 by_tile[k] = (time.perf_counter() - t0) / reps * 1e6
             Q.setEnvOption(env, "tile_qubits", 0)
             us = by_tile[0]
+            # without thread-block clusters (two tiles of 2^11 on two CTAs)
+            Q.setEnvOption(env, "fused_cluster", 0)
+            try:
+                for _ in range(10):
+                    run()
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    run()
+                us_one_cta = (time.perf_counter() - t0) / reps * 1e6
+            finally:
+                Q.setEnvOption(env, "fused_cluster", 8)
             # the same with generated pass kernels (compiled in the first
             # run; the 12-qubit passes run on 2 SMs, latency- not FP64-bound)
-            saved = {o: Q.getEnvOption(env, o) for o in ("jit", "jit_fp64", "jit_min_qubits")}
-            for opt, val in (("jit", 1), ("jit_fp64", 1), ("jit_min_qubits", 1)):
+            saved = {o: Q.getEnvOption(env, o) for o in ("jit", "jit_fp64", "jit_min_qubits", "fused_cluster")}
+            for opt, val in (("jit", 1), ("jit_fp64", 1), ("jit_min_qubits", 1), ("fused_cluster", 0)):
                 Q.setEnvOption(env, opt, val)
             try:
                 for _ in range(10):
@@ -683,6 +695,7 @@ def variants(Q, env, torch, stream, only=(), qubits=30, serve=(60, 0.0)):
                 "gates_per_s": ops12[1] / us * 1e6, "circuits_per_s": 1e6 / us,
                 "kernel_us_per_circuit": gpu_us,
                 "us_per_circuit_by_tile_qubits": {str(k): round(v, 1) for k, v in by_tile.items()},
+                "us_per_circuit_one_cta": us_one_cta,
                 "us_per_circuit_generated_kernels": us_jit,
                 "kernels": {k["name"]: round(k["total_ms"] * 1e3 / 20, 2) for k in kstats}}
 

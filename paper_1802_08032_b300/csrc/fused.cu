@@ -6,6 +6,7 @@
 #include <cstring>
 #include <memory>
 #include <string>
+#include <type_traits>
 #include <unordered_map>
 
 #include "fused_kernel.cuh"
@@ -16,6 +17,53 @@
 namespace qs {
 
 namespace {
+
+// A single-tile pass on a cluster of C CTAs (k_fused_cluster).
+template <class A, int R, int C>
+void launch_cluster(Env& env, Reg& r, const FPass& fp, const FOp* d_ops, const FStage* d_st) {
+  constexpr int c = C == 2 ? 1 : C == 4 ? 2 : 3;
+  const size_t smem = cluster_smem_bytes<A>(fp.k, c, fp.L, fp.op_count, fp.stage_end - fp.stage_begin);
+  static const bool attr_set = [] {
+    QS_CUDA(cudaFuncSetAttribute(k_fused_cluster<A, R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 110 * 1024));
+    return true;
+  }();
+  (void)attr_set;
+  k_fused_cluster<A, R, C><<<C, (1 << (fp.k - R)) / C, smem, env.stream>>>(static_cast<typename A::Store*>(r.d), fp,
+                                                                          d_ops, d_st);
+}
+
+template <class A, int R>
+void launch_cluster_r(Env& env, Reg& r, const FPass& fp, const FOp* d_ops, const FStage* d_st, int ctas) {
+  if (ctas == 8) launch_cluster<A, R, 8>(env, r, fp, d_ops, d_st);
+  else if (ctas == 4) launch_cluster<A, R, 4>(env, r, fp, d_ops, d_st);
+  else launch_cluster<A, R, 2>(env, r, fp, d_ops, d_st);
+}
+
+// A pass of a cluster plan (RegPlan::cluster > 1; plain arithmetic, R of
+// the plan).
+void launch_cluster_pass(Env& env, Reg& r, const RegPlan& pl, const FPass& fp, const FOp* d_ops,
+                         const FStage* d_st, double flops, double alu, const char* name) {
+  const double bytes = std::ldexp(2.0 * (pl.arith == Arith::F32 ? 8 : 16), r.nq);
+  KTimer kt(env, name, bytes, flops, 1, alu);
+  if (pl.arith == Arith::F64) {
+    switch (pl.R) {
+      case 2: return launch_cluster_r<PlainArith<double>, 2>(env, r, fp, d_ops, d_st, pl.cluster);
+      case 3: return launch_cluster_r<PlainArith<double>, 3>(env, r, fp, d_ops, d_st, pl.cluster);
+      case 4: return launch_cluster_r<PlainArith<double>, 4>(env, r, fp, d_ops, d_st, pl.cluster);
+      default: break;
+    }
+  } else if (pl.arith == Arith::F32) {
+    switch (pl.R) {
+      case 2: return launch_cluster_r<PlainArith<float>, 2>(env, r, fp, d_ops, d_st, pl.cluster);
+      case 3: return launch_cluster_r<PlainArith<float>, 3>(env, r, fp, d_ops, d_st, pl.cluster);
+      case 4: return launch_cluster_r<PlainArith<float>, 4>(env, r, fp, d_ops, d_st, pl.cluster);
+      case 5: return launch_cluster_r<PlainArith<float>, 5>(env, r, fp, d_ops, d_st, pl.cluster);
+      default: break;
+    }
+  }
+  fail(QS_E_ARG, "cluster plan with an unsupported arithmetic or register-bit count");
+}
 
 template <class A, int R>
 void launch_pass(Env& env, Reg& r, const FPass& fp, const FOp* d_ops, const FStage* d_st,
@@ -87,6 +135,7 @@ std::string plan_key(const Reg& r, const std::vector<GateOp>& seg, int k_req, ui
   put(k, int(arith_of(r)));
   put(k, env.tile_qubits);
   put(k, env.max_fused_ops);
+  put(k, env.fused_cluster);
   put(k, zero_in);
   put(k, scale.real());
   put(k, scale.imag());
@@ -231,9 +280,13 @@ void flush(Reg& r) {
       fp.stage_end += int(st0[pi]);
       const FOp* d_ops = static_cast<const FOp*>(env.d_fops);
       const FStage* d_st = static_cast<const FStage*>(env.d_fst);
+      const char* name = pl.arith == Arith::DF ? "fused_c128_df" : pl.arith == Arith::F64 ? "fused_c128" : "fused_c64";
+      if (pl.cluster > 1) {  // one tile on a thread-block cluster
+        launch_cluster_pass(env, r, pl, fp, d_ops, d_st, pl.flops[i], pl.alu[i], name);
+        continue;
+      }
       // the pass as its own compiled kernel when one is ready (jit.cpp)
       const int R = pl.arith == Arith::F32 ? 5 : 4;
-      const char* name = pl.arith == Arith::DF ? "fused_c128_df" : pl.arith == Arith::F64 ? "fused_c128" : "fused_c64";
       if (jit_try_launch(env, r, pl.fps[i], pl.fst.data(), pl.fops.data(), pl.arith, R, pl.flops[i], pl.alu[i], name,
                          pl.jit_memo.get(), i))
         continue;

@@ -143,6 +143,98 @@ __device__ __forceinline__ void run_op(typename A::Cplx (&v)[1 << R], const FOp&
   }
 }
 
+// A tile held in the CTA's own shared memory: element l at t[l].
+template <class A>
+struct LocalTile {
+  typename A::Cplx* t;
+  __device__ __forceinline__ typename A::Cplx load(uint32_t l) const { return t[l]; }
+  __device__ __forceinline__ void store(uint32_t l, const typename A::Cplx& v) const { t[l] = v; }
+};
+
+// One stage of a pass for one thread: its 2^R register amplitudes from the
+// tile, the stage's operations, and back.  tidx: the thread's index among
+// the tile's 2^(k-R) stage threads; base: the tile's global base (tile bits
+// zero); ops: the pass's op list.
+template <class A, int R, class Tile>
+__device__ __forceinline__ void run_stage(const Tile& tile, const FStage& st, const FOp* ops, uint32_t tidx,
+                                          uint64_t base) {
+  using Cplx = typename A::Cplx;
+  uint32_t poff[R];
+  uint32_t pm = 0, cpm = 0;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    poff[i] = 1u << st.pbits[i];
+    pm |= poff[i];
+    // register bits in st.copy start as copies of their bit-0 half
+    if ((st.copy >> i) & 1u) cpm |= poff[i];
+  }
+  // tlocal: tidx with a zero bit inserted at each register-bit
+  // position (positions ascending), i.e. its bits spread over the local
+  // positions not in pm
+  uint32_t tlocal = tidx;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const uint32_t p = st.pbits[i];
+    tlocal = ((tlocal >> p) << (p + 1)) | (tlocal & ((1u << p) - 1u));
+  }
+  Cplx v[1 << R];
+#pragma unroll
+  for (int j = 0; j < (1 << R); ++j) {
+    uint32_t off = 0;
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+      if (j & (1 << i)) off |= poff[i];
+    v[j] = tile.load(tlocal | (off & ~cpm));
+  }
+  // Sign flips (CZ, multi-controlled phase flips) commute with every
+  // diagonal op, and with a pair update on register bit i whenever the
+  // flipped set is symmetric under toggling bit i; so they are collected
+  // as a per-thread mask over the register amplitudes and applied only
+  // before an op they do not commute with, or at the end of the stage.
+  uint32_t flips = 0;
+  // code, flags and rmask share one word (read one op ahead); kind,
+  // conj, i0, i1 another
+  const int oe = st.op_end;
+  uint32_t wnext = st.op_begin < oe ? *reinterpret_cast<const uint32_t*>(&ops[st.op_begin].code) : 0u;
+  for (int o = st.op_begin; o < oe; ++o) {
+    const FOp& op = ops[o];
+    const uint32_t w = wnext;
+    wnext = o + 1 < oe ? *reinterpret_cast<const uint32_t*>(&ops[o + 1].code) : 0u;
+    const uint32_t flags = (w >> 16) & 0xFFu;
+    if ((flags & FF_COND) &&
+        ((tlocal & op.lmask) != op.lmask || (base & op.gmask) != op.gmask))
+      continue;
+    if ((flags & FF_FLIP) && flips) {
+      const uint32_t w0 = *reinterpret_cast<const uint32_t*>(&op);
+      if (depends_on_bit(flips, (w0 >> 16) & 0xFFu) ||
+          ((flags & FF_TWO) && depends_on_bit(flips, w0 >> 24))) {
+#pragma unroll
+        for (int j = 0; j < (1 << R); ++j)
+          if ((flips >> j) & 1u) v[j] = A::negate(v[j]);
+        flips = 0;
+      }
+    }
+    if ((w & 0xFFFFu) == FC_SIGN * kCodeSlots) {
+      flips ^= op.c.u[15];
+      continue;
+    }
+    run_op<A, R>(v, op, w & 0xFFFFu, op.rmask, tlocal, base, flips);
+  }
+  if (flips) {
+#pragma unroll
+    for (int j = 0; j < (1 << R); ++j)
+      if ((flips >> j) & 1u) v[j] = A::negate(v[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < (1 << R); ++j) {
+    uint32_t off = 0;
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+      if (j & (1 << i)) off |= poff[i];
+    tile.store(tlocal | off, v[j]);
+  }
+}
+
 // Shared-memory bytes of a pass launch.
 template <class A>
 __host__ __device__ inline size_t fused_smem_bytes(int k, int L, int nops, int nstages) {
@@ -276,83 +368,8 @@ __device__ __forceinline__ void process_tile(typename A::Store* __restrict__ g, 
   }
   __syncthreads();
   for (int s = 0; s < nst; ++s) {
-    if (!GENERAL || int(threadIdx.x) < active) {
-      const FStage& st = m.st[s];
-      uint32_t poff[R];
-      uint32_t pm = 0, cpm = 0;
-#pragma unroll
-      for (int i = 0; i < R; ++i) {
-        poff[i] = 1u << st.pbits[i];
-        pm |= poff[i];
-        // register bits in st.copy start as copies of their bit-0 half
-        if ((st.copy >> i) & 1u) cpm |= poff[i];
-      }
-      // tlocal: threadIdx with a zero bit inserted at each register-bit
-      // position (positions ascending), i.e. its bits spread over the local
-      // positions not in pm
-      uint32_t tlocal = threadIdx.x;
-#pragma unroll
-      for (int i = 0; i < R; ++i) {
-        const uint32_t p = st.pbits[i];
-        tlocal = ((tlocal >> p) << (p + 1)) | (tlocal & ((1u << p) - 1u));
-      }
-      Cplx v[1 << R];
-#pragma unroll
-      for (int j = 0; j < (1 << R); ++j) {
-        uint32_t off = 0;
-#pragma unroll
-        for (int i = 0; i < R; ++i)
-          if (j & (1 << i)) off |= poff[i];
-        v[j] = m.tile[tlocal | (off & ~cpm)];
-      }
-      // Sign flips (CZ, multi-controlled phase flips) commute with every
-      // diagonal op, and with a pair update on register bit i whenever the
-      // flipped set is symmetric under toggling bit i; so they are collected
-      // as a per-thread mask over the register amplitudes and applied only
-      // before an op they do not commute with, or at the end of the stage.
-      uint32_t flips = 0;
-      // code, flags and rmask share one word (read one op ahead); kind,
-      // conj, i0, i1 another
-      const int oe = st.op_end;
-      uint32_t wnext = st.op_begin < oe ? *reinterpret_cast<const uint32_t*>(&m.ops[st.op_begin].code) : 0u;
-      for (int o = st.op_begin; o < oe; ++o) {
-        const FOp& op = m.ops[o];
-        const uint32_t w = wnext;
-        wnext = o + 1 < oe ? *reinterpret_cast<const uint32_t*>(&m.ops[o + 1].code) : 0u;
-        const uint32_t flags = (w >> 16) & 0xFFu;
-        if ((flags & FF_COND) &&
-            ((tlocal & op.lmask) != op.lmask || (uint64_t(base) & op.gmask) != op.gmask))
-          continue;
-        if ((flags & FF_FLIP) && flips) {
-          const uint32_t w0 = *reinterpret_cast<const uint32_t*>(&op);
-          if (depends_on_bit(flips, (w0 >> 16) & 0xFFu) ||
-              ((flags & FF_TWO) && depends_on_bit(flips, w0 >> 24))) {
-#pragma unroll
-            for (int j = 0; j < (1 << R); ++j)
-              if ((flips >> j) & 1u) v[j] = A::negate(v[j]);
-            flips = 0;
-          }
-        }
-        if ((w & 0xFFFFu) == FC_SIGN * kCodeSlots) {
-          flips ^= op.c.u[15];
-          continue;
-        }
-        run_op<A, R>(v, op, w & 0xFFFFu, op.rmask, tlocal, uint64_t(base), flips);
-      }
-      if (flips) {
-#pragma unroll
-        for (int j = 0; j < (1 << R); ++j)
-          if ((flips >> j) & 1u) v[j] = A::negate(v[j]);
-      }
-#pragma unroll
-      for (int j = 0; j < (1 << R); ++j) {
-        uint32_t off = 0;
-#pragma unroll
-        for (int i = 0; i < R; ++i)
-          if (j & (1 << i)) off |= poff[i];
-        m.tile[tlocal | off] = v[j];
-      }
-    }
+    if (!GENERAL || int(threadIdx.x) < active)
+      run_stage<A, R>(LocalTile<A>{m.tile}, m.st[s], m.ops, threadIdx.x, uint64_t(base));
     __syncthreads();
   }
   // store
@@ -389,6 +406,156 @@ __global__ void __launch_bounds__(kFusedThreads, fused_ctas_per_sm(R))
   load_pass<A>(P, ops, stages, m);
   __syncthreads();
   for (int64_t tau = blockIdx.x; tau < P.ntiles; tau += gridDim.x) process_tile<A, R, false>(g, P, tau, m);
+}
+
+// ------------------------------------------------------------ cluster form
+// A pass over a register that is a single tile (2^k amplitudes) runs on one
+// CTA in the kernel above, i.e. on one SM.  Here it runs on a cluster of C
+// CTAs (C SMs): CTA r of the cluster holds tile elements r 2^(k-c) ..
+// (r + 1) 2^(k-c) - 1 (c = log2 C) in its shared memory and runs stage
+// threads r T .. (r + 1) T - 1 (T = 2^(k-R-c)).  A stage whose register
+// bits all lie below bit k - c keeps every thread's amplitudes in its own
+// CTA (the thread's top c index bits are its rank): shared-memory accesses
+// and a CTA barrier.  A stage with a register bit among the top c reads and
+// writes other CTAs' slices through distributed shared memory
+// (ld / st.shared::cluster), with cluster barriers before and after it.
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// Barrier over every thread of the cluster; orders the shared-memory
+// accesses (local and distributed) before it against those after it.
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_map(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void ld_cluster(uint32_t a, double2& v) {
+  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a) : "memory");
+}
+__device__ __forceinline__ void ld_cluster(uint32_t a, float2& v) {
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+}
+__device__ __forceinline__ void st_cluster(uint32_t a, const double2& v) {
+  asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"(v.x), "d"(v.y) : "memory");
+}
+__device__ __forceinline__ void st_cluster(uint32_t a, const float2& v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+
+// This CTA's slice of a cluster tile, addressed by tile index (the rank
+// bits, all equal to this CTA's in a local stage, are dropped).
+template <class A>
+struct SliceTile {
+  typename A::Cplx* t;
+  uint32_t mask;  // 2^(k-c) - 1
+  __device__ __forceinline__ typename A::Cplx load(uint32_t l) const { return t[l & mask]; }
+  __device__ __forceinline__ void store(uint32_t l, const typename A::Cplx& v) const { t[l & mask] = v; }
+};
+
+// The whole cluster tile: element l in the slice of rank l >> shift.
+template <class A>
+struct ClusterTile {
+  uint32_t base;  // shared address of the slice (the same offset in every CTA)
+  uint32_t shift;
+  __device__ __forceinline__ typename A::Cplx load(uint32_t l) const {
+    typename A::Cplx v;
+    ld_cluster(cluster_map(base + (l & ((1u << shift) - 1u)) * uint32_t(sizeof(v)), l >> shift), v);
+    return v;
+  }
+  __device__ __forceinline__ void store(uint32_t l, const typename A::Cplx& v) const {
+    st_cluster(cluster_map(base + (l & ((1u << shift) - 1u)) * uint32_t(sizeof(v)), l >> shift), v);
+  }
+};
+
+// Shared-memory bytes of a cluster launch: the slice, chunk offsets, op
+// list, stage list.
+template <class A>
+__host__ __device__ inline size_t cluster_smem_bytes(int k, int c, int L, int nops, int nstages) {
+  return sizeof(typename A::Cplx) * (size_t(1) << (k - c)) + sizeof(int64_t) * (size_t(1) << (k - L)) +
+         sizeof(FOp) * size_t(nops) + sizeof(FStage) * size_t(nstages);
+}
+
+// One pass over a single-tile register (P.ntiles == 1) on a cluster of C
+// CTAs of 2^(k-R)/C threads.  Plain arithmetic only (float2 / double2).
+template <class A, int R, int C>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kFusedThreads)
+    k_fused_cluster(typename A::Store* __restrict__ g, const __grid_constant__ FPass P,
+                    const FOp* __restrict__ ops, const FStage* __restrict__ stages) {
+  using Cplx = typename A::Cplx;
+  constexpr uint32_t c = C == 2 ? 1 : C == 4 ? 2 : 3;
+  static_assert(C == 2 || C == 4 || C == 8, "cluster of 2, 4 or 8 CTAs");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int k = P.k, L = P.L;
+  const uint32_t ks = uint32_t(k) - c;  // index bits of a slice
+  PassSmem<A> m;
+  m.tile = reinterpret_cast<Cplx*>(smem_raw);
+  m.choff = reinterpret_cast<int64_t*>(smem_raw + sizeof(Cplx) * (size_t(1) << ks));
+  m.ops = reinterpret_cast<FOp*>(m.choff + (1 << (k - L)));
+  m.st = reinterpret_cast<FStage*>(m.ops + P.op_count);
+  load_pass<A>(P, ops, stages, m);
+  __syncthreads();
+  const uint32_t rank = cluster_rank();
+  const uint32_t nslice = 1u << ks, l0 = rank << ks;
+  const uint32_t lmask_low = (1u << L) - 1u;
+  // this CTA's slice from HBM (the register is one tile: base 0)
+  if constexpr (sizeof(typename A::Store) == 8) {
+    const float4* g4 = reinterpret_cast<const float4*>(g);
+    float4* t4 = reinterpret_cast<float4*>(m.tile);
+    for (uint32_t e = threadIdx.x; e < nslice / 2; e += blockDim.x) {
+      const uint32_t l = l0 + 2 * e;
+      t4[e] = g4[(m.choff[l >> L] + (l & lmask_low)) >> 1];
+    }
+  } else {
+    for (uint32_t o = threadIdx.x; o < nslice; o += blockDim.x) {
+      const uint32_t l = l0 + o;
+      m.tile[o] = A::from_store(g[m.choff[l >> L] + (l & lmask_low)]);
+    }
+  }
+  const SliceTile<A> slice{m.tile, nslice - 1u};
+  const ClusterTile<A> whole{static_cast<uint32_t>(__cvta_generic_to_shared(m.tile)), ks};
+  const uint32_t tidx = rank * blockDim.x + threadIdx.x;
+  const int nst = P.stage_end - P.stage_begin;
+  auto distributed = [&](int s) {
+    bool d = false;
+#pragma unroll
+    for (int i = 0; i < R; ++i) d = d || m.st[s].pbits[i] >= ks;
+    return d;
+  };
+  bool cur = nst > 0 && distributed(0);
+  if (cur) cluster_sync();
+  else __syncthreads();
+  for (int s = 0; s < nst; ++s) {
+    if (cur) run_stage<A, R>(whole, m.st[s], m.ops, tidx, 0);
+    else run_stage<A, R>(slice, m.st[s], m.ops, tidx, 0);
+    const bool next = s + 1 < nst && distributed(s + 1);
+    if (cur || next) cluster_sync();  // other CTAs' slices read or written on either side
+    else __syncthreads();
+    cur = next;
+  }
+  // this CTA's slice back to HBM
+  if constexpr (sizeof(typename A::Store) == 8) {
+    float4* g4 = reinterpret_cast<float4*>(g);
+    const float4* t4 = reinterpret_cast<const float4*>(m.tile);
+    for (uint32_t e = threadIdx.x; e < nslice / 2; e += blockDim.x) {
+      const uint32_t l = l0 + 2 * e;
+      g4[(m.choff[l >> L] + (l & lmask_low)) >> 1] = t4[e];
+    }
+  } else {
+    for (uint32_t o = threadIdx.x; o < nslice; o += blockDim.x) {
+      const uint32_t l = l0 + o;
+      g[m.choff[l >> L] + (l & lmask_low)] = A::to_store(m.tile[o]);
+    }
+  }
+  cluster_sync();  // no CTA leaves while another could still address its slice
 }
 
 // Consecutive work items a CTA of the batched kernel takes at a time.

@@ -606,10 +606,12 @@ void check_launch() { QS_CUDA(cudaGetLastError()); }
 
 template <typename R>
 void sumsq(Env& env, const Reg& r, const Fixed& fx, int64_t nsel, double* out) {
-  const int blocks = int(std::max<int64_t>(
-      1, std::min<int64_t>(kRedMaxBlocks, (nsel + kRedThreads * 4 - 1) / (kRedThreads * 4))));
-  // one block (small registers): its partial is the result, so the second
-  // stage (which would add zeros to it) is skipped, saving a launch
+  // one block up to 16 amplitudes a thread (registers of up to 2^13
+  // amplitudes): its partial is the result, so the second stage (which would
+  // add zeros to it) is skipped, saving a launch
+  const int blocks = nsel <= int64_t(kRedThreads) * 16
+                         ? 1
+                         : int(std::min<int64_t>(kRedMaxBlocks, (nsel + kRedThreads * 4 - 1) / (kRedThreads * 4)));
   KTimer kt(env, kname<R>("reduce_sumsq").c_str(), double(nsel) * amp_bytes<R>(), double(nsel) * 4,
             blocks == 1 ? 1 : 2);
   k_sumsq<R, 4><<<blocks, kRedThreads, 0, env.stream>>>(static_cast<const cvec<R>*>(r.d), nsel, fx,

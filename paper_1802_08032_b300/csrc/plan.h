@@ -15,6 +15,9 @@ enum class Arith { F32, F64, DF };
 // indices are relative to this plan's own arrays.
 struct RegPlan {
   int k = 0, L = 0, R = 0;
+  // > 1: the register is one tile, spread over a thread-block cluster of
+  // this many CTAs (k_fused_cluster), with R chosen for 4 warps a CTA
+  int cluster = 0;
   Arith arith = Arith::F64;
   std::vector<FPass> fps;
   std::vector<FOp> fops;

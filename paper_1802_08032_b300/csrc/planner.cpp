@@ -927,9 +927,27 @@ Arith arith_of(const Reg& r) {
 void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, uint64_t zero_in,
                 std::complex<double> scale_in, RegPlan& out) {
   const Env& env = *r.env;
-  const TileCfg cfg = tile_cfg(r);
+  TileCfg cfg = tile_cfg(r);
+  // A register that fits one tile, in plain arithmetic, runs as one tile on
+  // a thread-block cluster of up to "fused_cluster" CTAs (k_fused_cluster)
+  // when the tile size is free or set to the register: 2^c CTAs of 4 warps,
+  // i.e. R = k - 7 - c register bits (at least 2, at most the default), so
+  // that 4c warps share the FP pipes of 4c SM sub-partitions instead of
+  // 2^(k-R-5) warps on one SM.
+  int cluster_c = 0;
+  if (k_req == 0 && (env.tile_qubits == 0 || env.tile_qubits >= r.nq) && r.nq <= cfg.kmax &&
+      arith_of(r) != Arith::DF && env.fused_cluster > 1) {
+    int c = env.fused_cluster >= 8 ? 3 : env.fused_cluster >= 4 ? 2 : 1;
+    const int Rc = std::max(2, std::min(cfg.R, r.nq - 7 - c));
+    while (c > 0 && r.nq - Rc - 5 - c < 2) --c;
+    if (c > 0) {
+      cluster_c = c;
+      cfg.R = Rc;
+    }
+  }
   int k = std::min(cfg.kmax, r.nq);
-  if (k_req > 0) k = std::min(k_req, r.nq);
+  if (cluster_c > 0) k = r.nq;
+  else if (k_req > 0) k = std::min(k_req, r.nq);
   else if (env.tile_qubits > 0) k = std::min<int>(int(env.tile_qubits), r.nq);
   // a register of at most 18 qubits has too few tiles to fill the GPU: one
   // qubit less per tile doubles the tiles (SMs at work) for a few more
@@ -937,13 +955,16 @@ void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, uint64_t 
   // 372-528 / 497 / 563 -> 283 / 369 / 405 us; complex64 16 / 18 qubits
   // 255 / 288 -> 232 / 265 us)
   else if (r.nq <= 18) k = std::min(k, cfg.kmax - 1);
-  k = std::max(k, std::min(cfg.R + 5, r.nq));
-  k = std::min(k, cfg.R + 8);
+  if (cluster_c == 0) {
+    k = std::max(k, std::min(cfg.R + 5, r.nq));
+    k = std::min(k, cfg.R + 8);  // at most 256 threads on one CTA
+  }
   const int L = std::min(cfg.L, k);
   out = RegPlan{};
   out.k = k;
   out.L = L;
   out.R = cfg.R;
+  out.cluster = cluster_c > 0 ? 1 << cluster_c : 0;
   out.arith = arith_of(r);
 
   std::vector<VOp> vops;

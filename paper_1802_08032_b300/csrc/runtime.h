@@ -127,6 +127,7 @@ struct Env {
   int64_t profile = 0;
   int64_t arith = 0;         // complex128 arithmetic of fused passes: 0 = IEEE FP64, 1 = double-float
   int64_t multi_tc = 1;      // complex64 dense gates on 4-5 targets: 0 CUDA cores, 1 by shape (5 on the tensor cores), 2 tensor cores
+  int64_t fused_cluster = 8;   // single-tile fused passes: largest thread-block cluster (CTAs, 2/4/8) they spread over, 0 or 1 = one CTA
   int64_t multi_tc_stage = 1;  // tensor-core multi-target passes with >= 7 free qubits: 1 staged (cp.async tiles, A in tensor memory), 0 register gather
   // fused passes as runtime-compiled kernels (jit.cpp): 0 off, 1 compile and
   // wait, 2 compile in the background (interpreting kernel until ready);
