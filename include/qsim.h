@@ -118,6 +118,18 @@ int qsDiagBoundedWait(QuESTEnv env, int timeoutUs);
  *                   entries only): results equal applying the gates one by
  *                   one up to rounding.
  *   "tile_qubits"   k of a fused tile, 0 = automatic
+ *   "fused_cluster" registers that fit one fused tile (complex128 up to 12
+ *                   stored qubits, complex64 up to 13; plain arithmetic)
+ *                   run it on a thread-block cluster of up to this many CTAs
+ *                   (2, 4 or 8; default 8): each CTA holds a slice of the
+ *                   tile in shared memory and stages reach the others'
+ *                   slices through distributed shared memory, with fewer
+ *                   register amplitudes a thread so that every CTA runs 4
+ *                   warps.  0 or 1 = one CTA (tiles one qubit smaller on
+ *                   registers of at most 18 qubits).  Amplitudes equal the
+ *                   one-CTA plan's up to rounding (bitwise for state
+ *                   vectors).  Applies when "tile_qubits" is 0 or at least
+ *                   the register's qubits.
  *   "max_fused_ops" cap on operations per fused pass (0 = automatic)
  *   "budget_bytes"  cap on the register memory of this env (0 = none)
  *   "arith"         complex128 arithmetic of fused passes and multi-target
