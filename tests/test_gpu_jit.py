@@ -59,6 +59,9 @@ def run_both(Q, env, n, ops, prec, arith=0, density=False, tile=0, min_q=None, c
     Q.setEnvOption(env, "jit_ctas", ctas)
     Q.setEnvOption(env, "jit_direct", direct)
     Q.setEnvOption(env, "jit_swizzle", swizzle)
+    # a single-tile register would otherwise run on a thread-block cluster
+    # (the interpreting cluster kernel), which generated kernels do not replace
+    Q.setEnvOption(env, "fused_cluster", 0)
     if min_q is not None:
         Q.setEnvOption(env, "jit_min_qubits", min_q)
     try:
@@ -78,6 +81,7 @@ def run_both(Q, env, n, ops, prec, arith=0, density=False, tile=0, min_q=None, c
         Q.setEnvOption(env, "arith", 0)
         Q.setEnvOption(env, "tile_qubits", 0)
         Q.setEnvOption(env, "jit_min_qubits", 20)
+        Q.setEnvOption(env, "fused_cluster", 8)
     assert Q.getEnvOption(env, "jit_failed") == 0
     assert Q.getEnvOption(env, "jit_rejected") == 0
     assert launched > 0
