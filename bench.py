@@ -755,6 +755,18 @@ def batch_variant(Q, env, torch, stream, count=4096, depth=30):
         # on registers of 10 or more qubits: a complex64 tile holds at least
         # 2^(R + 5) amplitudes, R = 5)
         k, depth = Q.tuneBatchJoint(b, [8, 10, 11, 12, 13], [0, 32, 64, 128], replays=1)
+        # both schedules at the tuned plan: one launch per wave (graph of
+        # waves) and one persistent launch over every wave; the batch keeps
+        # the faster one
+        form_ms = {}
+        for persistent in (0, 1):
+            Q.setEnvOption(env, "batch_persistent", persistent)
+            Q.tuneBatchJoint(b, [k], [depth], replays=1)    # re-plans in this form
+            form_ms[persistent] = timed(torch, stream, lambda: Q.runBatch(b), 3)
+        best_form = min(form_ms, key=form_ms.get)
+        Q.setEnvOption(env, "batch_persistent", best_form)
+        Q.tuneBatchJoint(b, [k], [depth], replays=1)
+        Q.setEnvOption(env, "batch_persistent", 1)
         ms = timed(torch, stream, lambda: Q.runBatch(b), 3)
         info = Q.getBatchInfo(b)
         norms = Q.getBatchNorms(b)
@@ -797,6 +809,8 @@ def batch_variant(Q, env, torch, stream, count=4096, depth=30):
     return {"circuits_per_s": count / ms * 1e3, "ms_per_batch": ms, "tile_qubits": k,
             "fusion_depth": depth or "planner default (256 ops per pass)",
             "tuned_over": {"tile_qubits": [8, 10, 11, 12, 13], "fusion_depth": [0, 32, 64, 128]},
+            "schedule": "persistent launch" if best_form else "one launch per wave (graph)",
+            "ms_per_batch_by_schedule": {"graph_of_waves": form_ms[0], "persistent": form_ms[1]},
             "registers": count, "amplitudes": int(sum(1 << n for n in sizes)),
             "gates": int(sum(len(c) for c in circs)), "passes": info["passes"],
             "waves": info["waves"], "alg_GBps": info["bytes"] / ms / 1e6,

@@ -129,7 +129,23 @@ int qsDiagBoundedWait(QuESTEnv env, int timeoutUs);
  *                   registers of at most 18 qubits).  Amplitudes equal the
  *                   one-CTA plan's up to rounding (bitwise for state
  *                   vectors).  Applies when "tile_qubits" is 0 or at least
- *                   the register's qubits.
+ *                   the register's qubits.  Batches never use clusters.
+ *   "batch_persistent" batches created (or re-tuned) from now on: 0 = one
+ *                   launch per wave, captured in the batch's graph; 1 = one
+ *                   persistent launch over every wave (default):
+ *                   CTAs claim runs of work items from a global ticket in
+ *                   wave order and, before a register's next pass, wait
+ *                   until every tile of its previous pass is done (waits
+ *                   bounded by 1 s of the GPU's global timer; a wait that
+ *                   runs out stops the launch and the next getBatchNorms,
+ *                   syncQuESTEnv or reduction returns QS_E_TIMEOUT).  The
+ *                   amplitudes are the same bit for bit.
+ *   "batch_diag_stall" diagnostic of that bounded wait: batches built while
+ *                   it is 1 (persistent form) wait for one tile more than
+ *                   each previous pass has, with a 2 ms bound instead of
+ *                   1 s, so the first such wait runs out; the next
+ *                   getBatchNorms returns QS_E_TIMEOUT and the context stays
+ *                   usable.  Default 0.
  *   "max_fused_ops" cap on operations per fused pass (0 = automatic)
  *   "budget_bytes"  cap on the register memory of this env (0 = none)
  *   "arith"         complex128 arithmetic of fused passes and multi-target

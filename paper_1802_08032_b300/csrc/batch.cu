@@ -84,6 +84,10 @@ struct Batch {
   FOp* d_ops = nullptr;
   FStage* d_st = nullptr;
   BItem* d_items = nullptr;
+  BDep* d_deps = nullptr;     // persistent form: each pass's predecessor
+  int* d_done = nullptr;      // persistent form: tiles done per pass, then the ticket
+  bool persistent = false;
+  bool diag_stall = false;    // every wait needs one tile too many (diagnostic)
   NormDesc* d_norms = nullptr;
   double* d_out = nullptr;
   double* h_out = nullptr;
@@ -105,6 +109,8 @@ void free_plan(Batch& b) {
   cudaFree(b.d_ops);
   cudaFree(b.d_st);
   cudaFree(b.d_items);
+  cudaFree(b.d_deps);
+  cudaFree(b.d_done);
   cudaFree(b.d_norms);
   cudaFree(b.d_out);
   if (b.h_out) cudaFreeHost(b.h_out);
@@ -114,6 +120,8 @@ void free_plan(Batch& b) {
   b.d_ops = nullptr;
   b.d_st = nullptr;
   b.d_items = nullptr;
+  b.d_deps = nullptr;
+  b.d_done = nullptr;
   b.d_norms = nullptr;
   b.d_out = nullptr;
   b.h_out = nullptr;
@@ -138,11 +146,27 @@ void launch_wave(const Batch& b, const Wave& w, cudaStream_t s) {
                                                         b.d_ops, b.d_st, w.kmax, w.Lmin, w.opmax);
 }
 
+// Every wave in one launch: CTAs claim item runs in list order and wait
+// (bounded) for a register's previous pass (k_fused_batch_persist).
+template <class A, int R>
+void launch_persistent(const Batch& b, int nitems, int kmax, int Lmin, int opmax, int stmax, cudaStream_t s) {
+  const size_t smem = fused_smem_bytes<A>(kmax, Lmin, opmax, stmax);
+  const int64_t chunks = (nitems + kBatchChunk - 1) / kBatchChunk;
+  const int grid = int(std::min<int64_t>(chunks, int64_t(b.env->sms) * fused_ctas_per_sm(R)));
+  const int npass = int(b.passes);
+  k_fused_batch_persist<A, R><<<grid, kFusedThreads, smem, s>>>(
+      b.d_items, nitems, b.d_passes, b.d_ops, b.d_st, b.d_deps, b.d_done,
+      reinterpret_cast<unsigned*>(b.d_done + npass), b.env->d_status, kmax, Lmin, opmax,
+      b.diag_stall ? 2000000ull : 1000000000ull);
+}
+
 template <class A, int R>
 void set_batch_attr() {
   // once per instantiation (thread-safe static initialisation)
   static const bool done = [] {
     QS_CUDA(cudaFuncSetAttribute(k_fused_batch<A, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 110 * 1024));
+    QS_CUDA(cudaFuncSetAttribute(k_fused_batch_persist<A, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  110 * 1024));
     return true;
   }();
@@ -162,6 +186,16 @@ void build(Batch& b) {
     DepthScope(Env& env_, int64_t d) : e(env_), saved(env_.max_fused_ops) { e.max_fused_ops = d; }
     ~DepthScope() { e.max_fused_ops = saved; }
   } depth_scope(env, b.max_ops > 0 ? b.max_ops : env.max_fused_ops);
+  // k_fused_batch runs every tile on one CTA with a fixed number of register
+  // bits per stage, so the batch's plans never spread a single-tile register
+  // over a thread-block cluster (whose plans take fewer register bits)
+  struct ClusterScope {
+    Env& e;
+    int64_t saved;
+    explicit ClusterScope(Env& env_) : e(env_), saved(env_.fused_cluster) { e.fused_cluster = 0; }
+    ~ClusterScope() { e.fused_cluster = saved; }
+  } cluster_scope(env);
+  const int kernel_R = b.arith == Arith::F32 ? 5 : 4;
   for (size_t r = 0; r < b.regs.size(); ++r) {
     // every replay starts from |0...0> (the first pass generates it)
     const int nq = b.regs[r]->nq;
@@ -170,6 +204,9 @@ void build(Batch& b) {
     b.regs[r]->zero_bits = 0;  // the register's contents are the batch's from now on
     b.regs[r]->pend_scale = 1.0;
     b.regs[r]->reset_qscale();
+    if (plans[r].R != kernel_R || plans[r].cluster > 1)
+      fail(QS_E_ARG, "batch plan with " + std::to_string(plans[r].R) + " register bits (kernel takes " +
+                         std::to_string(kernel_R) + ")");
     if (!plans[r].fps.empty()) plans[r].fps[0].init = 1;
     maxp = std::max(maxp, plans[r].fps.size());
   }
@@ -227,6 +264,14 @@ void build(Batch& b) {
     b.alu += wave.alu;
     b.waves.push_back(wave);
   }
+  // predecessor of every pass (persistent form): the register's previous pass
+  std::vector<BDep> deps(passes.size(), BDep{-1, 0});
+  for (size_t r = 0; r < b.regs.size(); ++r)
+    for (size_t w = 1; w < pass_index[r].size(); ++w) {
+      const int prev = pass_index[r][w - 1];
+      deps[size_t(pass_index[r][w])] =
+          BDep{prev, int(passes[size_t(prev)].ntiles) + (env.batch_diag_stall ? 1 : 0)};
+    }
   std::vector<NormDesc> nd;
   for (Reg* r : b.regs) {
     nd.push_back(NormDesc{r->d, r->dim});
@@ -238,6 +283,12 @@ void build(Batch& b) {
   b.d_st = upload(st, s);
   b.d_items = upload(items, s);
   b.d_norms = upload(nd, s);
+  b.persistent = env.batch_persistent != 0;
+  b.diag_stall = env.batch_diag_stall != 0;
+  if (b.persistent) {
+    b.d_deps = upload(deps, s);
+    QS_CUDA(cudaMalloc(&b.d_done, sizeof(int) * (passes.size() + 1)));
+  }
   QS_CUDA(cudaMalloc(&b.d_out, sizeof(double) * b.regs.size()));
   QS_CUDA(cudaMallocHost(&b.h_out, sizeof(double) * b.regs.size()));
   QS_CUDA(cudaStreamSynchronize(s));
@@ -245,20 +296,53 @@ void build(Batch& b) {
   else if (b.arith == Arith::F64) set_batch_attr<PlainArith<double>, 4>();
   else set_batch_attr<PlainArith<float>, 5>();
 
-  // capture: the waves, then the norms
+  // capture: the waves, then the norms.  The first call that fails inside
+  // the capture is named in the error (later ones only report the
+  // invalidated capture).
+  std::string first_err;
+  auto note = [&](cudaError_t e, const std::string& what) {
+    if (e != cudaSuccess && first_err.empty()) first_err = what + ": " + cudaGetErrorString(e);
+  };
   QS_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  for (const Wave& w : b.waves) {
-    if (b.arith == Arith::DF) launch_wave<DFArith, 4>(b, w, s);
-    else if (b.arith == Arith::F64) launch_wave<PlainArith<double>, 4>(b, w, s);
-    else launch_wave<PlainArith<float>, 5>(b, w, s);
+  if (b.persistent) {
+    int kmax = 0, Lmin = 64, opmax = 0, stmax = 0;
+    for (const Wave& w : b.waves) {
+      kmax = std::max(kmax, w.kmax);
+      Lmin = std::min(Lmin, w.Lmin);
+      opmax = std::max(opmax, w.opmax);
+      stmax = std::max(stmax, w.stmax);
+    }
+    const int nitems = int(items.size());
+    note(cudaMemsetAsync(b.d_done, 0, sizeof(int) * (passes.size() + 1), s), "clearing the pass counters");
+    if (nitems == 0) {
+      // registers with no queued gates: nothing to launch (as with no waves)
+    } else if (b.arith == Arith::DF) launch_persistent<DFArith, 4>(b, nitems, kmax, Lmin, opmax, stmax, s);
+    else if (b.arith == Arith::F64) launch_persistent<PlainArith<double>, 4>(b, nitems, kmax, Lmin, opmax, stmax, s);
+    else launch_persistent<PlainArith<float>, 5>(b, nitems, kmax, Lmin, opmax, stmax, s);
+    note(cudaGetLastError(), "persistent launch (items " + std::to_string(nitems) + ", k " + std::to_string(kmax) +
+                                 ", L " + std::to_string(Lmin) + ", ops " + std::to_string(opmax) + ", stages " +
+                                 std::to_string(stmax) + ")");
+  } else {
+    for (size_t wi = 0; wi < b.waves.size(); ++wi) {
+      const Wave& w = b.waves[wi];
+      if (b.arith == Arith::DF) launch_wave<DFArith, 4>(b, w, s);
+      else if (b.arith == Arith::F64) launch_wave<PlainArith<double>, 4>(b, w, s);
+      else launch_wave<PlainArith<float>, 5>(b, w, s);
+      note(cudaGetLastError(), "wave " + std::to_string(wi) + " launch (items " + std::to_string(w.nitems) +
+                                   ", k " + std::to_string(w.kmax) + ", L " + std::to_string(w.Lmin) + ", ops " +
+                                   std::to_string(w.opmax) + ", stages " + std::to_string(w.stmax) + ")");
+    }
   }
   const int nreg = int(b.regs.size());
   if (b.prec == QS_C128) k_batch_norms<double2><<<nreg, kNormThreads, 0, s>>>(b.d_norms, b.d_out);
   else k_batch_norms<float2><<<nreg, kNormThreads, 0, s>>>(b.d_norms, b.d_out);
-  const cudaError_t le = cudaGetLastError();
+  note(cudaGetLastError(), "norms launch");
   cudaGraph_t g = nullptr;
   const cudaError_t ce = cudaStreamEndCapture(s, &g);
-  if (le != cudaSuccess) fail(QS_E_CUDA, std::string("batch launch: ") + cudaGetErrorString(le));
+  if (!first_err.empty()) {
+    if (g) cudaGraphDestroy(g);
+    fail(QS_E_CUDA, "batch " + first_err);
+  }
   if (ce != cudaSuccess) fail(QS_E_CUDA, std::string("batch capture: ") + cudaGetErrorString(ce));
   b.graph = g;
   QS_CUDA(cudaGraphInstantiate(&b.exec, b.graph, 0));
@@ -354,7 +438,9 @@ int getBatchNorms(QSBatch h, double* out) {
     if (!out) fail(QS_E_ARG, "null output");
     cudaStream_t s = b.env->stream;
     QS_CUDA(cudaMemcpyAsync(b.h_out, b.d_out, sizeof(double) * b.regs.size(), cudaMemcpyDeviceToHost, s));
+    QS_CUDA(cudaMemcpyAsync(b.env->h_status, b.env->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     QS_CUDA(cudaStreamSynchronize(s));
+    check_status(*b.env);  // a bounded wait of the persistent form that ran out
     std::memcpy(out, b.h_out, sizeof(double) * b.regs.size());
   });
 }

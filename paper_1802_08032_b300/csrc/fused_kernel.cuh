@@ -306,7 +306,10 @@ __device__ __forceinline__ void load_pass(const FPass& P, const FOp* __restrict_
 // the block take part in loads, stores and barriers.  GENERAL = false is the
 // single-register launch, where blockDim = 2^(k-R) and no pass generates
 // |0...0>, so those checks compile away.
-template <class A, int R, bool GENERAL>
+// CG: tile loads bypass L1 (ld.global.cg), for a kernel that reads
+// amplitudes other CTAs wrote earlier in the same launch (L1 is not coherent
+// across SMs, and this SM may hold older copies of the same lines).
+template <class A, int R, bool GENERAL, bool CG = false>
 __device__ __forceinline__ void process_tile(typename A::Store* __restrict__ g, const FPass& P,
                                              int64_t tau, PassSmem<A>& m) {
   using Cplx = typename A::Cplx;
@@ -342,7 +345,11 @@ __device__ __forceinline__ void process_tile(typename A::Store* __restrict__ g, 
 #pragma unroll
       for (int u = 0; u < kDepth; ++u) {
         const int l = 2 * (e0 + u * blockDim.x);
-        if (!GENERAL || l < ntile) t[u] = g4[(base + m.choff[l >> L] + (l & lmask_low)) >> 1];
+        if (!GENERAL || l < ntile) {
+          const float4* src = g4 + ((base + m.choff[l >> L] + (l & lmask_low)) >> 1);
+          if constexpr (CG) t[u] = __ldcg(src);
+          else t[u] = *src;
+        }
       }
 #pragma unroll
       for (int u = 0; u < kDepth; ++u) {
@@ -357,7 +364,11 @@ __device__ __forceinline__ void process_tile(typename A::Store* __restrict__ g, 
 #pragma unroll
       for (int u = 0; u < kDepth; ++u) {
         const int l = l0 + u * blockDim.x;
-        if (!GENERAL || l < ntile) t[u] = g[base + m.choff[l >> L] + (l & lmask_low)];
+        if (!GENERAL || l < ntile) {
+          const Store* src = g + (base + m.choff[l >> L] + (l & lmask_low));
+          if constexpr (CG) t[u] = __ldcg(src);
+          else t[u] = *src;
+        }
       }
 #pragma unroll
       for (int u = 0; u < kDepth; ++u) {
@@ -592,6 +603,103 @@ __global__ void __launch_bounds__(kFusedThreads, fused_ctas_per_sm(R))
       __syncthreads();
     }
     process_tile<A, R, true>(static_cast<typename A::Store*>(sP.amps), sP, it.tile, m);
+  }
+}
+
+// Persistent batched form: one launch runs every wave.  The items of all
+// waves are listed in wave order (pass w of a register before pass w + 1)
+// and CTAs claim runs of kBatchChunk consecutive items from a global ticket,
+// so the runs are claimed in list order.  Before the first item of a pass,
+// thread 0 waits until every tile of the register's previous pass is done
+// (done[prev] == need).  A waited-on item has a smaller index than the
+// waiting one, so it was claimed earlier by a CTA that is running and never
+// waits on a later item: the lowest unfinished claimed item can always
+// proceed, and the launch cannot deadlock.  Each wait is still bounded by
+// the global timer (max_ns); when one runs out the CTA sets bit 2 of the
+// status word and stops claiming, and CTAs waiting on its items run out in
+// turn.  done[] and the ticket are zeroed before every launch.
+struct BDep {
+  int32_t prev;  // pass whose tiles must all be done first (-1: none)
+  int32_t need;  // its tile count
+};
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint64_t batch_globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_volatile_u32(const unsigned* p) {
+  return *reinterpret_cast<const volatile unsigned*>(p);
+}
+
+// True once *count reaches need; false after max_ns of the global timer, or
+// as soon as another CTA has reported a wait that ran out (status bit 2).
+__device__ __forceinline__ bool batch_wait_count(const int* count, int need, const unsigned* status,
+                                                 uint64_t max_ns) {
+  if (ld_acquire_gpu(count) >= need) return true;
+  const uint64_t t0 = batch_globaltimer();
+  for (;;) {
+    __nanosleep(100);
+    if (ld_acquire_gpu(count) >= need) return true;
+    if ((ld_volatile_u32(status) & 4u) || batch_globaltimer() - t0 > max_ns) return false;
+  }
+}
+
+template <class A, int R>
+__global__ void __launch_bounds__(kFusedThreads, fused_ctas_per_sm(R))
+    k_fused_batch_persist(const BItem* __restrict__ items, int nitems, const FPass* __restrict__ passes,
+                          const FOp* __restrict__ ops, const FStage* __restrict__ stages,
+                          const BDep* __restrict__ deps, int* done, unsigned* ticket, unsigned* status,
+                          int kmax, int Lmin, int opmax, uint64_t max_ns) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ FPass sP;
+  __shared__ int s_chunk, s_ok;
+  PassSmem<A> m = pass_smem<A>(smem_raw, kmax, Lmin, opmax);
+  int cur = -1;
+  for (;;) {
+    // after a wait ran out anywhere, stop claiming (the launch ends soon)
+    if (threadIdx.x == 0) s_chunk = (ld_volatile_u32(status) & 4u) ? 0x7FFFFFFF / kBatchChunk : int(atomicAdd(ticket, 1u));
+    __syncthreads();
+    const int c = s_chunk;
+    __syncthreads();  // every thread has read s_chunk before it is claimed again
+    if (int64_t(c) * kBatchChunk >= nitems) return;
+    const int iend = min(nitems, (c + 1) * kBatchChunk);
+    for (int i = c * kBatchChunk; i < iend; ++i) {
+      const BItem it = items[i];
+      if (it.pass != cur) {
+        cur = it.pass;
+        if (threadIdx.x == 0) {
+          const BDep d = deps[cur];
+          bool ok = d.prev < 0 || batch_wait_count(done + d.prev, d.need, status, max_ns);
+          if (!ok) atomicOr(status, 4u);
+          __threadfence();
+          s_ok = ok;
+        }
+        if (threadIdx.x < sizeof(FPass) / 8)
+          reinterpret_cast<uint64_t*>(&sP)[threadIdx.x] =
+              reinterpret_cast<const uint64_t*>(passes + cur)[threadIdx.x];
+        __syncthreads();
+        if (!s_ok) return;  // every thread leaves together; nothing is in flight
+        load_pass<A>(sP, ops, stages, m);
+        __syncthreads();
+      }
+      process_tile<A, R, true, true>(static_cast<typename A::Store*>(sP.amps), sP, it.tile, m);
+      // the tile's stores, then its count (process_tile ends with a barrier
+      // after the stores; each thread fences its own)
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(done + cur, 1);
+      }
+    }
   }
 }
 

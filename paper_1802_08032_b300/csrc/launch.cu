@@ -661,7 +661,9 @@ void check_status(Env& env) {
   *env.h_status = 0;
   QS_CUDA(cudaMemsetAsync(env.d_status, 0, sizeof(unsigned), env.stream));
   fail(QS_E_TIMEOUT, std::string("a bounded device wait ran out (") +
-                         ((s & 1u) ? "tensor-core multi-target pass" : "bulk tile copy of a fused pass") +
+                         ((s & 1u)   ? "tensor-core multi-target pass"
+                          : (s & 2u) ? "bulk tile copy of a fused pass"
+                                     : "persistent batch: a register's previous pass") +
                          "); amplitudes are unreliable");
 }
 

@@ -127,6 +127,14 @@ struct Env {
   int64_t profile = 0;
   int64_t arith = 0;         // complex128 arithmetic of fused passes: 0 = IEEE FP64, 1 = double-float
   int64_t multi_tc = 1;      // complex64 dense gates on 4-5 targets: 0 CUDA cores, 1 by shape (5 on the tensor cores), 2 tensor cores
+  // batches built from now on: 0 = one launch per wave (graph of waves),
+  // 1 = one persistent launch over every wave (k_fused_batch_persist; 88.6
+  // against 94.0 ms for the 4096-register workload)
+  int64_t batch_persistent = 1;
+  // diagnostic of the persistent form's bounded wait: batches built while it
+  // is 1 wait for one tile more than every previous pass has, with a 2 ms
+  // bound, so every such wait runs out (QS_E_TIMEOUT at getBatchNorms)
+  int64_t batch_diag_stall = 0;
   int64_t fused_cluster = 8;   // single-tile fused passes: largest thread-block cluster (CTAs, 2/4/8) they spread over, 0 or 1 = one CTA
   int64_t multi_tc_stage = 1;  // tensor-core multi-target passes with >= 7 free qubits: 1 staged (cp.async tiles, A in tensor memory), 0 register gather
   // fused passes as runtime-compiled kernels (jit.cpp): 0 off, 1 compile and

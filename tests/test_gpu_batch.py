@@ -34,9 +34,11 @@ def make_regs(Q, env, sizes, prec, seed0, depth=10):
     return regs, circs
 
 
+@pytest.mark.parametrize("persistent", [0, 1])
 @pytest.mark.parametrize("prec,arith", [(64, 0), (128, 0), (128, 1)])
-def test_batch_matches_oracle(Q, env, prec, arith):
+def test_batch_matches_oracle(Q, env, prec, arith, persistent):
     Q.setEnvOption(env, "arith", arith)
+    Q.setEnvOption(env, "batch_persistent", persistent)
     sizes = [5, 6, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17] * 2
     regs, circs = make_regs(Q, env, sizes, prec, 4096)
     try:
@@ -57,6 +59,47 @@ def test_batch_matches_oracle(Q, env, prec, arith):
         for q in regs:
             Q.destroyQureg(q)
         Q.setEnvOption(env, "arith", 0)
+        Q.setEnvOption(env, "batch_persistent", 1)
+
+
+@pytest.mark.parametrize("prec", [64, 128])
+def test_persistent_batch_equals_wave_launches_bitwise(Q, env, prec):
+    """The persistent form (one launch; CTAs claim items in wave order and
+    wait for a register's previous pass) gives the amplitudes of the
+    one-launch-per-wave graph bit for bit: the same tiles with the same
+    arithmetic, only scheduled differently.  Many registers with several
+    passes each, so passes of different registers overlap; two replays."""
+    rng = C.SplitMix64(2024)
+    sizes = [8 + rng.below(11) for _ in range(160)]
+    regs, circs = make_regs(Q, env, sizes, prec, 9000, depth=16)
+    out = {}
+    try:
+        for persistent in (0, 1):
+            Q.setEnvOption(env, "batch_persistent", persistent)
+            if persistent:   # the first batch took the registers' queued gates
+                for q, ops in zip(regs, circs):
+                    Q.applyCircuit(q, ops)
+            b = Q.createBatch(env, regs, tileQubits=10)
+            assert Q.getBatchInfo(b)["waves"] >= 3
+            states = []
+            for _ in range(2):
+                Q.runBatch(b)
+                norms = Q.getBatchNorms(b)
+                states.append([Q.copyStateToHost(q) for q in regs])
+            for x, y in zip(*states):
+                assert np.array_equal(x, y)
+            out[persistent] = (states[0], norms)
+            Q.destroyBatch(b)
+        for n, x, y in zip(sizes, out[0][0], out[1][0]):
+            assert np.array_equal(x, y), n
+        assert np.array_equal(out[0][1], out[1][1])
+        for i in range(0, len(sizes), 23):
+            ref = O.run_circuit(sizes[i], circs[i])
+            assert np.max(np.abs(out[1][0][i] - ref.a)) <= AMP_TOL[prec]
+    finally:
+        Q.setEnvOption(env, "batch_persistent", 1)
+        for q in regs:
+            Q.destroyQureg(q)
 
 
 @pytest.mark.parametrize("prec", [64, 128])
@@ -125,6 +168,60 @@ def test_batch_joint_tuner(Q, env):
         assert e.value.name == "QS_E_ARG"
         Q.destroyBatch(b)
     finally:
+        for q in regs:
+            Q.destroyQureg(q)
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_batch_of_registers_without_gates(Q, env, persistent):
+    """Registers with nothing queued: the replay launches no pass (and the
+    persistent form no empty launch) and every register reads |0...0>."""
+    Q.setEnvOption(env, "batch_persistent", persistent)
+    regs = [Q.createQureg(n, 64, env) for n in (6, 9, 12)]
+    try:
+        b = Q.createBatch(env, regs)
+        Q.runBatch(b)
+        assert np.array_equal(Q.getBatchNorms(b), np.ones(3))
+        for q in regs:
+            a = Q.copyStateToHost(q)
+            assert a[0] == 1 and not np.any(a[1:])
+        Q.destroyBatch(b)
+    finally:
+        Q.setEnvOption(env, "batch_persistent", 1)
+        for q in regs:
+            Q.destroyQureg(q)
+
+
+def test_persistent_batch_bounded_wait_reports_timeout(Q, env):
+    """The persistent form's wait for a register's previous pass is bounded:
+    with every dependency one tile short (diagnostic option, 2 ms bound) the
+    wait runs out, the launch ends, getBatchNorms reports QS_E_TIMEOUT once,
+    and the context keeps working (a normal batch afterwards matches the
+    oracle).  No fault and no unbounded wait."""
+    sizes = [12, 15, 17]
+    regs, circs = make_regs(Q, env, sizes, 64, 71, depth=12)
+    try:
+        Q.setEnvOption(env, "batch_diag_stall", 1)
+        b = Q.createBatch(env, regs, tileQubits=10)
+        Q.setEnvOption(env, "batch_diag_stall", 0)
+        assert Q.getBatchInfo(b)["waves"] >= 2
+        Q.runBatch(b)
+        with pytest.raises(Q.QSimError) as e:
+            Q.getBatchNorms(b)
+        assert e.value.name == "QS_E_TIMEOUT"
+        Q.destroyBatch(b)
+        Q.syncQuESTEnv(env)   # the status word was cleared: no second report
+        for q, ops in zip(regs, circs):
+            Q.applyCircuit(q, ops)
+        b = Q.createBatch(env, regs, tileQubits=10)
+        Q.runBatch(b)
+        Q.getBatchNorms(b)
+        for q, n, ops in zip(regs, sizes, circs):
+            ref = O.run_circuit(n, ops)
+            assert np.max(np.abs(Q.copyStateToHost(q) - ref.a)) <= AMP_TOL[64]
+        Q.destroyBatch(b)
+    finally:
+        Q.setEnvOption(env, "batch_diag_stall", 0)
         for q in regs:
             Q.destroyQureg(q)
 
