@@ -424,6 +424,10 @@ def main():
         except Exception as e:  # host without room for the sample
             line["cpu_baseline"] = {"value": None, "unavailable": str(e)}
     Q.destroyQuESTEnv(env)
+    if "variants" in line:
+        # last key of the line: the figures stay in view when only the end
+        # of the output is kept
+        line["summary"] = compact_summary(line["variants"])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -498,6 +502,90 @@ def timed(torch, stream, fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
+def pass_kernel_roofline(Q, env, run):
+    """One more run with per-kernel CUDA events: the fused pass kernels'
+    algorithmic bytes (one read and one write of the register per pass) over
+    their summed kernel time, against the measured HBM copy bandwidth."""
+    Q.resetKernelStats(env)
+    Q.setEnvOption(env, "profile", 1)
+    try:
+        run()
+    finally:
+        Q.setEnvOption(env, "profile", 0)
+    ks = [k for k in Q.getKernelStats(env) if k["name"].startswith(("fused", "jit", "qs_pass", "sv_fused"))]
+    ms = sum(k["total_ms"] for k in ks)
+    if ms <= 0:
+        return {}
+    gbs = sum(k["bytes"] for k in ks) / ms / 1e6
+    return {"pass_kernel_ms": ms, "pass_kernel_launches": sum(k["launches"] for k in ks),
+            "pass_kernel_GBps": gbs, "pass_kernel_hbm_frac_of_measured": gbs / peaks()[0]}
+
+
+def compact_summary(v):
+    """The variants' headline figures in a few hundred characters (the
+    full detail is under "variants"), rounded, in the units of their
+    sources: gates/s, circuits/s, GB/s, ms, us."""
+    import statistics
+    out = {}
+
+    def g(d, *ks):
+        for k in ks:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return d
+
+    def r(x, nd=3):
+        return None if x is None else float(f"{x:.{nd}g}")
+
+    if "sv12_c128" in v:
+        out["sv12_us"] = r(g(v, "sv12_c128", "us_per_circuit"))
+    for name in ("sv30_c64", "sv33_c128", "sv33_c64", "sv30_df64_out_of_spec"):
+        if name in v:
+            out[name] = [r(g(v, name, "gates_per_s")), r(g(v, name, "pass_kernel_hbm_frac_of_measured"), 2),
+                         r(g(v, name, "error_vs_fp64", "max_abs_err"), 2),
+                         r(g(v, name, "error_vs_fp64", "one_minus_fidelity"), 2)]
+    if "dm14_c128" in v:
+        out["dm14_ops_s"] = r(g(v, "dm14_c128", "ops_per_s"))
+    for name, key in (("single_gate_sweep", "sweep30"), ("single_gate_sweep_33q", "sweep33")):
+        sw = v.get(name)
+        if isinstance(sw, dict) and "targets" in sw:
+            row = {}
+            for kind in ("H", "U", "T", "CZ", "MCPF"):
+                for prec in (64, 128):
+                    vals = sw.get(f"{kind}_c{prec}_GBps_by_target")
+                    if vals:
+                        hi = vals[5:-3] or vals   # bits the sector rule does not touch
+                        row[f"{kind}{prec}"] = [round(min(hi)), round(statistics.median(hi))]
+            out[key + "_bits5up_min_med_GBps"] = row
+    b = v.get("batch4096_c64")
+    if isinstance(b, dict) and "circuits_per_s" in b:
+        out["batch"] = {"c_s": r(b["circuits_per_s"]), "plain_c128_c_s": r(b.get("plain_c128_circuits_per_s")),
+                        "k": b.get("tile_qubits"), "sched": "persist" if "persist" in str(b.get("schedule")) else "waves",
+                        "err": r(g(b, "error_vs_fp64_all_registers", "max_abs_err"), 2),
+                        "1-F": r(g(b, "error_vs_fp64_all_registers", "max_one_minus_fidelity"), 2)}
+    m = v.get("multi_target_passes")
+    if isinstance(m, dict):
+        out["multi_GBps"] = {k: round(x["GBps"]) for k, x in m.items()
+                             if isinstance(x, dict) and "GBps" in x and k in (
+                                 "c64_m4", "c64_m5", "c64_m5_low_targets_tensor_cores",
+                                 "c64_m4_low_targets", "c128_m2")}
+    sv = v.get("serving")
+    if isinstance(sv, dict):
+        rows = {}
+        for rate, d in sv.items():
+            if isinstance(d, dict) and "served" in d:
+                rows[rate.split("_")[0]] = [r(g(d, "served", "circuits_per_s")), r(g(d, "served", "p50_ms")),
+                                            r(g(d, "served", "p99_ms")),
+                                            r(g(d, "served_shed_after_1s", "p99_ms")),
+                                            r(g(d, "plain_c128_one_at_a_time", "circuits_per_s"))]
+        out["serve_c_s_p50ms_p99ms_p99shedms_plainc128"] = rows
+    p = v.get("partitioned_28q_4parts")
+    if isinstance(p, dict) and "gates_per_s" in p:
+        out["part28_4_gates_s"] = r(p["gates_per_s"])
+    return out
+
+
 def variants(Q, env, torch, stream, only=(), qubits=30, serve=(60, 0.0)):
     """Other configurations of the same metric, measured outside the timed
     region: the 12-qubit circuit (latency), complex64 and double-float
@@ -527,6 +615,7 @@ def variants(Q, env, torch, stream, only=(), qubits=30, serve=(60, 0.0)):
                 ms = timed(torch, stream, run, reps)
                 res = {"qubits": n, "gates": len(circ), "gates_per_s": len(circ) / ms * 1e3,
                        "ms_per_circuit": ms}
+                res.update(pass_kernel_roofline(Q, env, run))
                 if prec == 64 and ref is not None and ref.get("q") is not None:
                     res["error_vs_fp64"] = c64_error(Q, torch, q, ref["q"])
                 if n == 30:
