@@ -127,8 +127,9 @@ int qsDiagBoundedWait(QuESTEnv env, int timeoutUs);
  *                   register amplitudes a thread so that every CTA runs 4
  *                   warps.  0 or 1 = one CTA (tiles one qubit smaller on
  *                   registers of at most 18 qubits).  Amplitudes equal the
- *                   one-CTA plan's up to rounding (bitwise for state
- *                   vectors).  Applies when "tile_qubits" is 0 or at least
+ *                   one-CTA plan's up to rounding (commuting operations may
+ *                   be grouped into stages in another order); each plan is
+ *                   deterministic.  Applies when "tile_qubits" is 0 or at least
  *                   the register's qubits.  Batches never use clusters.
  *   "batch_persistent" batches created (or re-tuned) from now on: 0 = one
  *                   launch per wave, captured in the batch's graph; 1 = one

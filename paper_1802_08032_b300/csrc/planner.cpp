@@ -757,25 +757,53 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
     if (v.kind == FK_DEPH) need |= local_mask(v.zmask());
     return need;
   };
-  size_t i = 0;
-  while (i < p.ops.size()) {
-    // grow the stage's register set while the needed bits fit in R
+  // Two ops commute when no bit either moves amplitudes along is a bit the
+  // other touches (the pass builder's rule).
+  auto commute = [](const VOp& a, const VOp& b) {
+    const uint64_t xa = a.xmask(), xb = b.xmask();
+    return (xa & (xb | b.zmask())) == 0 && (xb & (xa | a.zmask())) == 0;
+  };
+  // Ops not yet in a stage, in pass order.  A stage takes them in order
+  // while their needed bits fit in R register bits; an op that does not fit
+  // is deferred to a later stage, and a later op still joins this stage if
+  // its bits fit and it commutes with every op deferred so far (so moving
+  // it ahead of them changes nothing).  The ops of a stage keep their pass
+  // order, and every op placed ahead of a deferred one commutes with it:
+  // the result is that of the pass order.
+  std::vector<size_t> rem(p.ops.size());
+  for (size_t o = 0; o < rem.size(); ++o) rem[o] = o;
+  while (!rem.empty()) {
     uint32_t P = 0;
-    size_t j = i;
-    while (j < p.ops.size()) {
-      const uint32_t need = needed(p.ops[j]);
-      if (j > i && popc(P | need) > R) break;
-      P |= need;
-      ++j;
+    std::vector<size_t> take, defer;
+    for (size_t o : rem) {
+      const VOp& v = p.ops[o];
+      bool free = true;
+      for (size_t d : defer)
+        if (!commute(v, p.ops[d])) {
+          free = false;
+          break;
+        }
+      if (free) {
+        const uint32_t need = needed(v);
+        if (take.empty() || popc(P | need) <= R) {
+          P |= need;
+          take.push_back(o);
+          continue;
+        }
+      }
+      defer.push_back(o);
     }
+    rem.swap(defer);
     // spare register slots go first to the single bits the stage's phases
     // condition on (a phase on a lane bit runs on half-idle lanes), then to
     // the highest unused local bits (keeps low bits on lanes)
-    for (size_t o = i; o < j && popc(P) < R; ++o)
+    for (size_t o : take) {
+      if (popc(P) >= R) break;
       if (p.ops[o].kind == FK_PHASE || p.ops[o].kind == FK_PHASEU) {
         const uint32_t c = local_mask(p.ops[o].cond);
         if (popc(c) == 1) P |= c;
       }
+    }
     for (int b = k - 1; b >= 0 && popc(P) < R; --b) P |= 1u << b;
     FStage st{};
     int idx[32];
@@ -789,7 +817,7 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
     if (n != R || (P >> k) != 0) fail(QS_E_ARG, "fused planner: stage register set is not R tile bits");
     st.op_begin = int32_t(fops.size()) - first;
     bool sign_seen = false;
-    for (size_t o = i; o < j; ++o) {
+    for (size_t o : take) {
       const VOp& v = p.ops[o];
       if (v.spread) {  // a copy made when the stage loads its amplitudes
         st.copy |= uint8_t(1u << idx[lpos[v.b0]]);
@@ -851,7 +879,6 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
     }
     st.op_end = int32_t(fops.size()) - first;
     fst.push_back(st);
-    i = j;
   }
 }
 

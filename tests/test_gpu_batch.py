@@ -105,7 +105,9 @@ def test_persistent_batch_equals_wave_launches_bitwise(Q, env, prec):
 @pytest.mark.parametrize("prec", [64, 128])
 def test_batch_result_equals_alone_bitwise(Q, env, prec):
     """Each register's amplitudes after the batched replay are bit-identical
-    to running the same circuit on its own (same planner, same tile size)."""
+    to running the same circuit on its own (same planner, same tile size;
+    one CTA per tile, as in the batch: a thread-block cluster plan groups
+    its stages by fewer register bits)."""
     sizes = [7, 11, 14, 18, 12, 16]
     regs, circs = make_regs(Q, env, sizes, prec, 777, depth=14)
     try:
@@ -114,6 +116,7 @@ def test_batch_result_equals_alone_bitwise(Q, env, prec):
         mixed = [Q.copyStateToHost(q) for q in regs]
         Q.destroyBatch(b)
         Q.setEnvOption(env, "tile_qubits", 11)
+        Q.setEnvOption(env, "fused_cluster", 0)
         for n, ops, m in zip(sizes, circs, mixed):
             q = Q.createQureg(n, prec, env)
             Q.applyCircuit(q, ops)
@@ -122,6 +125,7 @@ def test_batch_result_equals_alone_bitwise(Q, env, prec):
             assert np.array_equal(alone, m), n
     finally:
         Q.setEnvOption(env, "tile_qubits", 0)
+        Q.setEnvOption(env, "fused_cluster", 8)
         for q in regs:
             Q.destroyQureg(q)
 

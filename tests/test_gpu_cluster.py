@@ -5,9 +5,13 @@ A register of at most 13 qubits is one fused tile.  With "fused_cluster" C
 its tile is spread over the shared memory of C CTAs, stages whose register
 bits include the top log2(C) tile bits read and write the other CTAs'
 slices through distributed shared memory, and the rest stay in the CTA's
-own slice.  Every amplitude sees the same operations in the same order as on
-one CTA, so the results are compared bit for bit; the oracle holds both to
-the parity bars."""
+own slice.  A cluster plan has fewer register bits per stage than the
+one-CTA plan, and the planner groups commuting operations into stages by
+those bits, so an amplitude may see commuting operations in another order:
+the two plans agree to rounding (compared at PLAN_TOL), each is
+deterministic (a rerun is bit-identical), and the oracle holds both to the
+parity bars."""
+
 import numpy as np
 import pytest
 
@@ -16,6 +20,10 @@ from paper_1802_08032_b300 import circuits as C
 from gpu_helpers import AMP_TOL, PROB_TOL
 
 pytestmark = pytest.mark.gpu
+
+# two plans of one circuit (other stage groupings of commuting operations):
+# far below the oracle bars (1e-12 / 1e-5)
+PLAN_TOL = {128: 1e-13, 64: 1e-6}
 
 
 @pytest.fixture(scope="module")
@@ -63,8 +71,10 @@ def test_cluster_state_vector(Q, env, prec, n):
     one, tr1 = run(Q, env, make, ops, 0, tile=n)
     for c in (2, 4, 8):
         got, tr = run(Q, env, make, ops, c, tile=n)
-        assert np.array_equal(got, one), (c, float(np.max(np.abs(got - one))))
-        assert tr == tr1
+        assert np.max(np.abs(got - one)) <= PLAN_TOL[prec], (c, float(np.max(np.abs(got - one))))
+        assert abs(tr - tr1) <= (PLAN_TOL[prec] if prec == 128 else 1e-6)
+        again, tr_again = run(Q, env, make, ops, c, tile=n)
+        assert np.array_equal(again, got) and tr_again == tr
     ref = O.run_circuit(n, ops)
     default, trd = run(Q, env, make, ops, 8)
     for a, t in ((one, tr1), (default, trd)):
@@ -83,16 +93,11 @@ def test_cluster_density_matrix(Q, env, prec, N):
     one, tr1 = run(Q, env, make, ops, 0, tile=2 * N)
     for c in (2, 4, 8):
         got, tr = run(Q, env, make, ops, c, tile=2 * N)
-        if prec == 64:
-            assert np.array_equal(got, one), (c, float(np.max(np.abs(got - one))))
-            assert tr == tr1
-        else:
-            # complex128 density plans with 4 register bits (one CTA) fold
-            # the channels' off-diagonal factors into side operations, the
-            # cluster plans' 2-3 register bits do not: the same products in
-            # another order, equal to rounding
-            assert np.max(np.abs(got - one)) <= 1e-15, c
-            assert abs(tr - tr1) <= 1e-15
+        # other stage groupings, and for complex128 the one-CTA plan's 4
+        # register bits fold the channels' off-diagonal factors into side
+        # operations where the cluster plans' 2-3 do not: equal to rounding
+        assert np.max(np.abs(got - one)) <= PLAN_TOL[prec], (c, float(np.max(np.abs(got - one))))
+        assert abs(tr - tr1) <= (PLAN_TOL[prec] if prec == 128 else 1e-6)
     ref = O.run_circuit(N, ops, density=True)
     default, trd = run(Q, env, make, ops, 8)
     for a, t in ((one, tr1), (default, trd)):
@@ -107,7 +112,7 @@ def test_cluster_12_qubit_workload(Q, env):
     ops = C.workload_12q()
     one, _ = run(Q, env, lambda: Q.createQureg(12, 128, env), ops, 0, tile=12)
     got, tr = run(Q, env, lambda: Q.createQureg(12, 128, env), ops, 8)
-    assert np.array_equal(got, one)
+    assert np.max(np.abs(got - one)) <= PLAN_TOL[128]
     ref = O.run_circuit(12, ops)
     assert np.max(np.abs(got - ref.a)) <= AMP_TOL[128]
     assert abs(tr - ref.total_prob()) <= PROB_TOL
