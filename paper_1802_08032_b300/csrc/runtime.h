@@ -128,8 +128,8 @@ struct Env {
   int64_t arith = 0;         // complex128 arithmetic of fused passes: 0 = IEEE FP64, 1 = double-float
   int64_t multi_tc = 1;      // complex64 dense gates on 4-5 targets: 0 CUDA cores, 1 by shape (5 on the tensor cores), 2 tensor cores
   // batches built from now on: 0 = one launch per wave (graph of waves),
-  // 1 = one persistent launch over every wave (k_fused_batch_persist; 88.6
-  // against 94.0 ms for the 4096-register workload)
+  // 1 = one persistent launch over every wave (k_fused_batch_persist; 69.0
+  // against 73.1 ms for the 4096-register workload)
   int64_t batch_persistent = 1;
   // diagnostic of the persistent form's bounded wait: batches built while it
   // is 1 wait for one tile more than every previous pass has, with a 2 ms
