@@ -757,41 +757,75 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
     if (v.kind == FK_DEPH) need |= local_mask(v.zmask());
     return need;
   };
-  // Two ops commute when no bit either moves amplitudes along is a bit the
-  // other touches (the pass builder's rule).
-  auto commute = [](const VOp& a, const VOp& b) {
-    const uint64_t xa = a.xmask(), xb = b.xmask();
-    return (xa & (xb | b.zmask())) == 0 && (xb & (xa | a.zmask())) == 0;
-  };
   // Ops not yet in a stage, in pass order.  A stage takes them in order
-  // while their needed bits fit in R register bits; an op that does not fit
-  // is deferred to a later stage, and a later op still joins this stage if
-  // its bits fit and it commutes with every op deferred so far (so moving
-  // it ahead of them changes nothing).  The ops of a stage keep their pass
-  // order, and every op placed ahead of a deferred one commutes with it:
-  // the result is that of the pass order.
+  // while their needed bits fit in its R register bits; an op that does not
+  // fit is deferred to a later stage, and a later op still joins this stage
+  // if its bits fit and it commutes with every op deferred so far (no bit
+  // either moves amplitudes along is a bit the other touches: the pass
+  // builder's rule; against all deferred ops at once through the union of
+  // their moved bits DX and of their touched bits DZ).  The ops of a stage
+  // keep their pass order, and every op placed ahead of a deferred one
+  // commutes with it: the result is that of the pass order.
   std::vector<size_t> rem(p.ops.size());
   for (size_t o = 0; o < rem.size(); ++o) rem[o] = o;
-  while (!rem.empty()) {
-    uint32_t P = 0;
-    std::vector<size_t> take, defer;
+  // One candidate register set: start from P0 and, with grow, add the bits
+  // of each op that still fits; returns the ops taken (in pass order).
+  auto simulate = [&](uint32_t P0, bool grow, uint32_t& P, std::vector<size_t>& take,
+                      std::vector<size_t>& defer) {
+    P = P0;
+    take.clear();
+    defer.clear();
+    uint64_t DX = 0, DZ = 0;
     for (size_t o : rem) {
       const VOp& v = p.ops[o];
-      bool free = true;
-      for (size_t d : defer)
-        if (!commute(v, p.ops[d])) {
-          free = false;
-          break;
-        }
-      if (free) {
+      const uint64_t xv = v.xmask(), zv = v.zmask();
+      if ((xv & (DX | DZ)) == 0 && (DX & (xv | zv)) == 0) {
         const uint32_t need = needed(v);
-        if (take.empty() || popc(P | need) <= R) {
+        if ((need & ~P) == 0 || (grow && (take.empty() || popc(P | need) <= R))) {
           P |= need;
           take.push_back(o);
           continue;
         }
       }
       defer.push_back(o);
+      DX |= xv;
+      DZ |= zv;
+    }
+  };
+  // ops that move amplitudes (the ones register bits are for)
+  auto moving = [&](const std::vector<size_t>& t) {
+    int c = 0;
+    for (size_t o : t) c += needed(p.ops[o]) != 0;
+    return c;
+  };
+  std::vector<size_t> take, defer, ctake, cdefer;
+  while (!rem.empty()) {
+    // Candidates: the in-order greedy set and, with at least 4 register
+    // bits, every window of R adjacent tile positions (on layered circuits a
+    // block of neighbouring qubits can advance several layers in one stage,
+    // bounded by its neighbours, where the first ops' bits are scattered
+    // across a layer).  The one taking the most moving ops wins (ties: the
+    // greedy set, then the lower window); a candidate must take the first
+    // op (progress).  Cluster plans (2-3 register bits, many cheap stages)
+    // keep the greedy set: there the search costs more planning time than
+    // it saves.
+    uint32_t P = 0;
+    simulate(0, true, P, take, defer);
+    if (R >= 4) {
+      int best = moving(take);
+      for (int w = 0; w + R <= k; ++w) {
+        const uint32_t W = ((1u << R) - 1u) << w;
+        uint32_t Pw = 0;
+        simulate(W, false, Pw, ctake, cdefer);
+        if (ctake.empty() || ctake[0] != rem[0]) continue;
+        const int m = moving(ctake);
+        if (m > best) {
+          best = m;
+          P = Pw;
+          take.swap(ctake);
+          defer.swap(cdefer);
+        }
+      }
     }
     rem.swap(defer);
     // spare register slots go first to the single bits the stage's phases
