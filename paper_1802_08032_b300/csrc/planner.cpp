@@ -9,7 +9,8 @@
 // bits fit in the k tile qubits; an operation that does not fit is
 // deferred, and a later operation may move ahead of deferred ones only if
 // it commutes with all of them (no X bit of either touches a bit of the
-// other).  Passes repeat until the queue is empty.
+// other).  Several candidate tiles compete for each pass (see plan()).
+// Passes repeat until the queue is empty.
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -616,7 +617,7 @@ double defer_offdiag(std::vector<VOp>& ops, int N, bool side_factors) {
 int popc(uint64_t x) { return __builtin_popcountll(x); }
 
 std::vector<Pass> plan(const std::vector<VOp>& ops, int nq, int k, int L, int64_t max_ops,
-                       int scale_limit, std::complex<double> scale_in) {
+                       int scale_limit, std::complex<double> scale_in, int dm_n) {
   std::vector<Pass> passes;
   std::vector<VOp> rem = ops;
   ScaleState scale;
@@ -624,10 +625,14 @@ std::vector<Pass> plan(const std::vector<VOp>& ops, int nq, int k, int L, int64_
   scale.g = scale_in;
   const uint64_t low = (uint64_t(1) << L) - 1;
   const uint64_t all = nq >= 64 ? ~uint64_t(0) : (uint64_t(1) << nq) - 1;
-  while (!rem.empty()) {
-    Pass p;
-    uint64_t tile = low, bx = 0, ball = 0;
-    std::vector<VOp> deferred;
+  // One candidate pass: the tile starts as T0 and, with grow, takes the X
+  // bits of each op that still fits in k qubits; an op is taken if its X
+  // bits are in the tile and it commutes with every op deferred so far.
+  auto simulate = [&](uint64_t T0, bool grow, Pass& p, std::vector<VOp>& deferred, uint64_t& tile) {
+    tile = T0;
+    uint64_t bx = 0, ball = 0;
+    p.ops.clear();
+    deferred.clear();
     for (const VOp& v : rem) {
       const uint64_t x = v.xmask(), z = v.zmask();
       // A mid-plan scale (a density matrix's deferred channel factor)
@@ -642,7 +647,7 @@ std::vector<Pass> plan(const std::vector<VOp>& ops, int nq, int k, int L, int64_
         continue;
       }
       const bool commutes = (x & ball) == 0 && ((x | z) & bx) == 0;
-      const bool fits = popc(tile | x) <= k;
+      const bool fits = grow ? popc(tile | x) <= k : (x & ~tile) == 0;
       const bool room = int64_t(p.ops.size()) < max_ops;
       if (commutes && fits && room) {
         tile |= x;
@@ -651,6 +656,51 @@ std::vector<Pass> plan(const std::vector<VOp>& ops, int nq, int k, int L, int64_
         deferred.push_back(v);
         bx |= x;
         ball |= x | z;
+      }
+    }
+  };
+  auto moving = [](const Pass& p) {
+    int c = 0;
+    for (const VOp& v : p.ops) c += v.xmask() != 0;
+    return c;
+  };
+  while (!rem.empty()) {
+    Pass p, cp;
+    std::vector<VOp> deferred, cdef;
+    uint64_t tile = 0, ctile = 0;
+    // Candidate tiles: the one grown from the ops in order, and the low L
+    // qubits plus a window of adjacent qubits (a density matrix: a block of
+    // rows with its column partners, bit t + N, topped up from the ops).
+    // On layered circuits a block of neighbouring qubits can advance several
+    // layers in one pass, bounded by its neighbours, where the first ops'
+    // qubits are scattered across a layer.  The candidate taking the most
+    // ops that move amplitudes wins (ties: the grown tile, then the lower
+    // window).  30-qubit workload: 28 -> 19 passes (complex64, k = 12),
+    // 26 -> 19 (complex128); 14-qubit noisy density matrix 18 -> 15.
+    simulate(low, true, p, deferred, tile);
+    int best = moving(p);
+    std::vector<uint64_t> cands;
+    const int w = k - L;
+    if (dm_n == 0) {
+      for (int b = L; w > 0 && b + w <= nq; ++b) cands.push_back(low | (((uint64_t(1) << w) - 1) << b));
+    } else {
+      // a block of rows with its column partners (bit t + N)
+      for (int h = 1; 2 * h <= k; ++h)
+        for (int b = 0; b + h <= dm_n; ++b) {
+          const uint64_t rows = ((uint64_t(1) << h) - 1) << b;
+          const uint64_t T = low | rows | (rows << dm_n);
+          if (popc(T) <= k) cands.push_back(T);
+        }
+    }
+    for (uint64_t T : cands) {
+      simulate(T, popc(T) < k, cp, cdef, ctile);
+      if (cp.ops.empty()) continue;  // (each pass must take an op)
+      const int m = moving(cp);
+      if (m > best) {
+        best = m;
+        std::swap(p, cp);
+        deferred.swap(cdef);
+        tile = ctile;
       }
     }
     // pad the tile to exactly k qubits with the lowest unused ones
@@ -1047,7 +1097,7 @@ void build_plan(const Reg& r, const std::vector<GateOp>& q, int k_req, uint64_t 
   const int64_t cap = env.max_fused_ops > 0 ? std::min<int64_t>(env.max_fused_ops, kMaxPassOps)
                                             : kMaxPassOps;
   const std::vector<Pass> passes =
-      plan(vops, r.nq, k, L, cap, out.arith == Arith::F64 ? 1000 : 80, scale_in);
+      plan(vops, r.nq, k, L, cap, out.arith == Arith::F64 ? 1000 : 80, scale_in, r.density ? r.n : 0);
   for (const Pass& p : passes) {
     FPass fp{};
     fp.k = k;
