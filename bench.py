@@ -41,7 +41,7 @@ FP32_ISSUE_TINSTR = 148 * 128 * 2.032e9 / 1e12   # FP32 instructions/s at the 20
 # the kernel as built (profiles/<kernel>_*_ncu_full.md); scaled by the
 # amplitudes a launch processes.  Entries are removed when a kernel changes.
 MEASURED_TRAFFIC_PER_AMP = {
-    "fused_c128": 2.088e9 / (1 << 26),      # profiles/fused_c128_fp64_sv26_ncu_full.md
+    "fused_c128": 2.089e9 / (1 << 26),      # profiles/fused_c128_fp64_sv26_ncu_full.md
     # generated complex64 pass kernel, async-copy pipeline
     "fused_c64": 1.014e9 / (1 << 26),       # profiles/qs_pass_c64_async_sv26_ncu_full.md
 }
