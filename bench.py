@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--jit-swizzle", type=int, default=None, choices=[0, 1],
                     help="generated kernels swizzle the tile in shared memory")
     ap.add_argument("--tile-qubits", type=int, default=None, help="fused tile size k (0 = automatic)")
+    ap.add_argument("--tile-low", type=int, default=None,
+                    help="lowest qubits every fused tile holds (0 = automatic: 4 complex64, 3 complex128)")
     ap.add_argument("--jit", type=int, default=1, choices=[0, 1, 2],
                     help="fused passes: 0 interpreting kernel, 1 runtime-compiled kernels "
                          "(compiled in the warm-up), 2 compiled in the background")
@@ -330,6 +332,7 @@ def main():
     # (the first step waits for them; timed steps reuse the cached kernels)
     Q.setEnvOption(env, "jit", args.jit)
     for opt, val in (("jit_copy", args.jit_copy), ("jit_ctas", args.jit_ctas), ("tile_qubits", args.tile_qubits),
+                     ("tile_low_qubits", args.tile_low),
                      ("jit_direct", args.jit_direct), ("jit_swizzle", args.jit_swizzle)):
         if val is not None:
             Q.setEnvOption(env, opt, val)

@@ -147,6 +147,11 @@ int qsDiagBoundedWait(QuESTEnv env, int timeoutUs);
  *                   1 s, so the first such wait runs out; the next
  *                   getBatchNorms returns QS_E_TIMEOUT and the context stays
  *                   usable.  Default 0.
+ *   "tile_low_qubits" lowest qubits every fused tile holds: HBM chunks of
+ *                   2^L contiguous amplitudes (0 = automatic: 4 for
+ *                   complex64, 3 for complex128; else 2..6).  Fewer leave
+ *                   more tile qubits to a pass, with shorter chunks
+ *                   (measured slower below the default).
  *   "max_fused_ops" cap on operations per fused pass (0 = automatic)
  *   "budget_bytes"  cap on the register memory of this env (0 = none)
  *   "arith"         complex128 arithmetic of fused passes and multi-target

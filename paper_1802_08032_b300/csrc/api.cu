@@ -318,6 +318,9 @@ int setEnvOption(QuESTEnv e, const char* key, int64_t value) {
       if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8)
         fail(QS_E_ARG, "fused_cluster must be 0, 1, 2, 4 or 8");
       env.fused_cluster = value;
+    } else if (k == "tile_low_qubits") {
+      if (value != 0 && (value < 2 || value > 6)) fail(QS_E_ARG, "tile_low_qubits must be 0 (default) or 2..6");
+      env.tile_low_qubits = value;
     } else if (k == "batch_persistent") {
       if (value != 0 && value != 1) fail(QS_E_ARG, "batch_persistent must be 0 or 1");
       env.batch_persistent = value;
@@ -379,6 +382,7 @@ int getEnvOption(QuESTEnv e, const char* key, int64_t* value) {
     else if (k == "multi_tc_stage") *value = env.multi_tc_stage;
     else if (k == "fused_cluster") *value = env.fused_cluster;
     else if (k == "batch_persistent") *value = env.batch_persistent;
+    else if (k == "tile_low_qubits") *value = env.tile_low_qubits;
     else if (k == "batch_diag_stall") *value = env.batch_diag_stall;
     else if (k == "jit") *value = env.jit;
     else if (k == "jit_min_qubits") *value = env.jit_min_qubits;

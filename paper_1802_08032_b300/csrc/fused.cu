@@ -136,6 +136,7 @@ std::string plan_key(const Reg& r, const std::vector<GateOp>& seg, int k_req, ui
   put(k, env.tile_qubits);
   put(k, env.max_fused_ops);
   put(k, env.fused_cluster);
+  put(k, env.tile_low_qubits);
   put(k, zero_in);
   put(k, scale.real());
   put(k, scale.imag());

@@ -1023,7 +1023,13 @@ void note_mixing(Reg& r, const GateOp& op) {
   r.zero_bits &= ~x;
 }
 
-TileCfg tile_cfg(const Reg& r) { return r.prec == QS_C128 ? TileCfg{4, 12, 3} : TileCfg{5, 13, 4}; }
+TileCfg tile_cfg(const Reg& r) {
+  TileCfg c = r.prec == QS_C128 ? TileCfg{4, 12, 3} : TileCfg{5, 13, 4};
+  // the env's "tile_low_qubits": fewer contiguous low qubits per tile leave
+  // more tile qubits for the passes' windows, with shorter HBM chunks
+  if (r.env && r.env->tile_low_qubits > 0) c.L = int(r.env->tile_low_qubits);
+  return c;
+}
 
 bool fusable(const Reg& r) {
   const TileCfg c = tile_cfg(r);

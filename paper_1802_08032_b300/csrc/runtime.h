@@ -131,6 +131,9 @@ struct Env {
   // 1 = one persistent launch over every wave (k_fused_batch_persist; 69.0
   // against 73.1 ms for the 4096-register workload)
   int64_t batch_persistent = 1;
+  // fused tiles: the lowest qubits every tile holds, i.e. the contiguous
+  // HBM chunk of 2^L amplitudes (0 = 4 for complex64, 3 for complex128)
+  int64_t tile_low_qubits = 0;
   // diagnostic of the persistent form's bounded wait: batches built while it
   // is 1 wait for one tile more than every previous pass has, with a 2 ms
   // bound, so every such wait runs out (QS_E_TIMEOUT at getBatchNorms)
