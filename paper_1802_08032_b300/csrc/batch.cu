@@ -56,8 +56,9 @@ __global__ void __launch_bounds__(kNormThreads) k_batch_norms(const NormDesc* __
   double acc = 0.0;
   for (int64_t j = threadIdx.x; j < d.dim; j += kNormThreads) {
     const V v = a[j];
-    acc = fma(double(v.x), double(v.x), acc);
-    acc = fma(double(v.y), double(v.y), acc);
+    const double re = widen(v.x), im = widen(v.y);
+    acc = fma(re, re, acc);
+    acc = fma(im, im, acc);
   }
   const double s = norm_block_sum(acc, sh);
   if (threadIdx.x == 0) out[blockIdx.x] = s;

@@ -45,4 +45,24 @@ __device__ __forceinline__ float neg_bits(float x) {
   return __int_as_float(__float_as_int(x) ^ 0x80000000);
 }
 
+// float -> double, exactly, without the FP64 pipe: the double has the
+// float's sign, its exponent rebiased by 1023 - 127 = 896 and its 23-bit
+// significand followed by 29 zero bits (IEEE 754 binary32 / binary64
+// layouts).  A subnormal is first scaled by 2^64 on the FP32 pipe (exact:
+// a power of two, into the normal range) and its exponent lowered by 64;
+// zero keeps exponent 0, infinities and NaN take 2047 with their
+// significand bits.  Selects, not branches: on B300 a conversion
+// instruction, even predicated off, occupies the FP64 pipe that the FMAs of
+// the FP64 reductions need (2 conversions and 2 FMAs per complex64
+// amplitude).  The value is the conversion's, so results do not change.
+__device__ __forceinline__ double widen(float x) {
+  const uint32_t f0 = __float_as_uint(x);
+  const bool sub = (f0 & 0x7F800000u) == 0u && (f0 & 0x007FFFFFu) != 0u;
+  const uint32_t f = __float_as_uint(sub ? x * 18446744073709551616.0f : x);  // x 2^64
+  const uint32_t e = (f >> 23) & 0xFFu, m = f & 0x007FFFFFu;
+  const uint32_t ed = e == 0u ? 0u : (e == 0xFFu ? 0x7FFu : e + 896u - (sub ? 64u : 0u));
+  return __hiloint2double(int((f & 0x80000000u) | (ed << 20) | (m >> 3)), int(m << 29));
+}
+__device__ __forceinline__ double widen(double x) { return x; }
+
 }  // namespace qs

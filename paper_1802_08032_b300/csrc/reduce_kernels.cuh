@@ -11,6 +11,7 @@
 namespace qs {
 
 constexpr int kRedThreads = 512;
+
 constexpr int kRedMaxBlocks = 1184;  // 148 SMs x 8
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -47,7 +48,7 @@ __global__ void __launch_bounds__(kRedThreads) k_sumsq(const cvec<R>* __restrict
     }
 #pragma unroll
     for (int u = 0; u < UNROLL; ++u) {
-      const double re = double(x[u].x), im = double(x[u].y);
+      const double re = widen(x[u].x), im = widen(x[u].y);
       acc = fma(re, re, acc);
       acc = fma(im, im, acc);
     }
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(kRedThreads) k_inner(const cvec<RA>* __restric
     }
 #pragma unroll
     for (int u = 0; u < UNROLL; ++u) {
-      const double ar = double(x[u].x), ai = double(x[u].y), br = double(y[u].x), bi = double(y[u].y);
+      const double ar = widen(x[u].x), ai = widen(x[u].y), br = widen(y[u].x), bi = widen(y[u].y);
       re = fma(ar, br, re);
       re = fma(ai, bi, re);
       im = fma(ar, bi, im);

@@ -89,3 +89,31 @@ def test_inner_product_errors(Q, env):
     finally:
         for q in (qa, qb, d):
             Q.destroyQureg(q)
+
+
+# float32 values whose widening to FP64 has to be exact: normal ones of
+# every size (taken by the integer-pipe widening), the smallest normal, and
+# the ones that take the conversion instruction (subnormals, zeros)
+EDGE_F32 = [1.0, -0.1, 3.0e-20, -1.17549435e-38, 1.0e-40, -1.4e-45, 1.5e18, 0.0, -0.0, 2.0 ** -126,
+            0.7071067811865476, 123456.789]
+
+
+@pytest.mark.parametrize("re", EDGE_F32)
+def test_complex64_reductions_widen_exactly(Q, env, re):
+    """One nonzero complex64 amplitude (re, im): the total probability is
+    re^2 + im^2 rounded once (the FMA of im^2 onto the exact re^2; every
+    other term adds zero), and <a|a> the same, for edge float32 values."""
+    im = np.float32(-0.375)
+    re32 = np.float32(re)
+    a = np.zeros(1 << 4, dtype=np.complex64)
+    a[5] = complex(re32, im)
+    q = Q.createQureg(4, 64, env)
+    try:
+        Q.setAmps(q, a.astype(np.complex128))
+        got = Q.calcTotalProb(q)
+        want = float(np.float64(re32) ** 2 + np.float64(im) ** 2)   # re^2 exact in FP64, one rounding
+        assert got == want, (re, got, want)
+        ip = Q.calcInnerProduct(q, q)
+        assert ip.real == want and ip.imag == 0.0
+    finally:
+        Q.destroyQureg(q)
