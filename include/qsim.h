@@ -161,11 +161,13 @@ int qsDiagBoundedWait(QuESTEnv env, int timeoutUs);
  *                   48-bit significand: a few units of 2^-48 of error per
  *                   update instead of 2^-53; a multi-target pass on m
  *                   targets up to 2^m units of 2^-48 of the norm).  Storage
- *                   stays complex128 and amplitudes meet the 1e-12 bar, but
- *                   FP64-reduced probabilities after long circuits drift by
- *                   up to ~5e-13 (30 qubits, 1259 gates), outside the 1e-13
- *                   complex128 bar.  Single-gate passes, reductions and
- *                   measurement always use FP64.
+ *                   stays complex128; amplitudes meet the 1e-12 bar and the
+ *                   FP64-reduced probabilities of the 30-qubit 1259-gate
+ *                   circuit stay within 6e-14 of an FP64 oracle, but every
+ *                   pass boundary rounds the float pairs to doubles, so
+ *                   longer circuits with more passes drift further than IEEE
+ *                   FP64.  Single-gate passes, reductions and measurement
+ *                   always use FP64.
  *   "profile"       1 = time every kernel launch with CUDA events (see
  *                   getKernelStats), 0 = off (default)
  *   "multi_tc"      where complex64 multi-target gates on 4-5 targets run:

@@ -8,11 +8,6 @@ from paper_1802_08032_b300 import circuits as C
 # Parity bars: max |amplitude difference| after the circuit.
 AMP_TOL = {128: 1e-12, 64: 1e-5}
 PROB_TOL = 1e-13
-# Probability bar of the opt-in double-float arithmetic ("arith" 1), an
-# out-of-spec precision form: complex128 storage, but 48-bit significands in
-# the updates (a few units of 2^-48 instead of 2^-53), so its FP64-reduced
-# probabilities are held to this bar, not the complex128 one (PROB_TOL).
-DF_PROB_TOL = 5e-13
 
 
 def rand_state(nq, seed):

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from paper_1802_08032_b300 import circuits as C
-from gpu_helpers import AMP_TOL, DF_PROB_TOL, PROB_TOL, inverse
+from gpu_helpers import AMP_TOL, PROB_TOL, inverse
 
 pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
@@ -152,10 +152,11 @@ def test_30_qubit_depth40_workload(Q, env, prec, arith):
     finally:
         Q.setEnvOption(env, "arith", 0)
     assert np.max(np.abs(got - as_complex(g["amps"]))) <= AMP_TOL[prec]
-    # Double-float updates carry ~2^-47 relative error each; over 1259 gates
-    # on 2^30 amplitudes the FP64-reduced probabilities drift by ~1e-13, so
-    # that opt-in mode is held to 5e-13 (the IEEE-FP64 default to 1e-13).
-    tol = (PROB_TOL if arith == 0 else DF_PROB_TOL) if prec == 128 else 1e-5
+    # Double-float (an out-of-spec precision form: 48-bit significands, a few
+    # units of 2^-48 per update) is held to the complex128 bar as well: with
+    # 19 passes (each pass boundary rounds the float pairs to doubles) its
+    # FP64-reduced probabilities stay within 6e-14 of the oracle here.
+    tol = PROB_TOL if prec == 128 else 1e-5
     assert abs(tot - g["total_prob"]) <= tol
     assert np.max(np.abs(np.array(probs) - g["prob_outcome_1"])) <= tol
 
