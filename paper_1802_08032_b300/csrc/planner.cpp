@@ -818,8 +818,16 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
   // commutes with it: the result is that of the pass order.
   std::vector<size_t> rem(p.ops.size());
   for (size_t o = 0; o < rem.size(); ++o) rem[o] = o;
+  // Per op: moved bits, touched bits, needed register positions.
+  std::vector<uint64_t> ox(p.ops.size()), oz(p.ops.size());
+  std::vector<uint32_t> oneed(p.ops.size());
+  for (size_t o = 0; o < p.ops.size(); ++o) {
+    ox[o] = p.ops[o].xmask();
+    oz[o] = p.ops[o].zmask();
+    oneed[o] = needed(p.ops[o]);
+  }
   // One candidate register set: start from P0 and, with grow, add the bits
-  // of each op that still fits; returns the ops taken (in pass order).
+  // of each op that still fits; the ops taken, in pass order.
   auto simulate = [&](uint32_t P0, bool grow, uint32_t& P, std::vector<size_t>& take,
                       std::vector<size_t>& defer) {
     P = P0;
@@ -827,10 +835,9 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
     defer.clear();
     uint64_t DX = 0, DZ = 0;
     for (size_t o : rem) {
-      const VOp& v = p.ops[o];
-      const uint64_t xv = v.xmask(), zv = v.zmask();
+      const uint64_t xv = ox[o], zv = oz[o];
       if ((xv & (DX | DZ)) == 0 && (DX & (xv | zv)) == 0) {
-        const uint32_t need = needed(v);
+        const uint32_t need = oneed[o];
         if ((need & ~P) == 0 || (grow && (take.empty() || popc(P | need) <= R))) {
           P |= need;
           take.push_back(o);
@@ -842,41 +849,57 @@ void encode_pass(const Pass& p, int R, int k, Arith arith, std::vector<FOp>& fop
       DZ |= zv;
     }
   };
-  // ops that move amplitudes (the ones register bits are for)
-  auto moving = [&](const std::vector<size_t>& t) {
-    int c = 0;
-    for (size_t o : t) c += needed(p.ops[o]) != 0;
-    return c;
-  };
-  std::vector<size_t> take, defer, ctake, cdefer;
-  while (!rem.empty()) {
-    // Candidates: the in-order greedy set and, with at least 4 register
-    // bits, every window of R adjacent tile positions (on layered circuits a
-    // block of neighbouring qubits can advance several layers in one stage,
-    // bounded by its neighbours, where the first ops' bits are scattered
-    // across a layer).  The one taking the most moving ops wins (ties: the
-    // greedy set, then the lower window); a candidate must take the first
-    // op (progress).  Cluster plans (2-3 register bits, many cheap stages)
-    // keep the greedy set: there the search costs more planning time than
-    // it saves.
-    uint32_t P = 0;
-    simulate(0, true, P, take, defer);
-    if (R >= 4) {
-      int best = moving(take);
-      for (int w = 0; w + R <= k; ++w) {
-        const uint32_t W = ((1u << R) - 1u) << w;
-        uint32_t Pw = 0;
-        simulate(W, false, Pw, ctake, cdefer);
-        if (ctake.empty() || ctake[0] != rem[0]) continue;
-        const int m = moving(ctake);
-        if (m > best) {
-          best = m;
-          P = Pw;
-          take.swap(ctake);
-          defer.swap(cdefer);
+  // The same scan over the first `limit` remaining ops only, counting the
+  // moving ops (those needing register bits) it takes; -1 when it does not
+  // take the first op (every stage must make progress).
+  auto score = [&](uint32_t P0, bool grow, size_t limit) {
+    uint32_t P = P0;
+    uint64_t DX = 0, DZ = 0;
+    int moved = 0;
+    bool any = false;
+    const size_t n = std::min(limit, rem.size());
+    for (size_t i = 0; i < n; ++i) {
+      const size_t o = rem[i];
+      const uint64_t xv = ox[o], zv = oz[o];
+      if ((xv & (DX | DZ)) == 0 && (DX & (xv | zv)) == 0) {
+        const uint32_t need = oneed[o];
+        if ((need & ~P) == 0 || (grow && (!any || popc(P | need) <= R))) {
+          P |= need;
+          any = true;
+          moved += need != 0;
+          continue;
         }
       }
+      if (i == 0) return -1;
+      DX |= xv;
+      DZ |= zv;
     }
+    return moved;
+  };
+  constexpr size_t kScoreOps = 128;
+  std::vector<size_t> take, defer;
+  while (!rem.empty()) {
+    // Candidates: the in-order greedy set and every window of R adjacent
+    // tile positions (on layered circuits a block of neighbouring qubits
+    // can advance several layers in one stage, bounded by its neighbours,
+    // where the first ops' bits are scattered across a layer).  Each is
+    // scored on the next kScoreOps remaining ops by the moving ops it takes;
+    // the highest wins (ties: the greedy set, then the lower window) and
+    // only the winner scans every remaining op.
+    uint32_t P0 = 0;
+    bool grow = true;
+    int best = score(0, true, kScoreOps);
+    for (int w = 0; w + R <= k; ++w) {
+      const uint32_t W = ((1u << R) - 1u) << w;
+      const int m = score(W, false, kScoreOps);
+      if (m > best) {
+        best = m;
+        P0 = W;
+        grow = false;
+      }
+    }
+    uint32_t P = 0;
+    simulate(P0, grow, P, take, defer);
     rem.swap(defer);
     // spare register slots go first to the single bits the stage's phases
     // condition on (a phase on a lane bit runs on half-idle lanes), then to
