@@ -10,7 +10,7 @@
 // writes the final 2^nq amplitudes (re, im doubles) to stdout after a line
 // "STATE".  The test compares that state with the oracle.
 //
-// usage: planner_check n density prec arith k_req emulate [fresh]
+// usage: planner_check n density prec arith k_req emulate [fresh [tile_low_qubits]]
 #include <algorithm>
 #include <complex>
 #include <cstdio>
@@ -300,8 +300,10 @@ int main(int argc, char** argv) {
   const int n = std::atoi(argv[1]), density = std::atoi(argv[2]), prec = std::atoi(argv[3]);
   const int arith = std::atoi(argv[4]), k_req = std::atoi(argv[5]), emu = std::atoi(argv[6]);
   const int fresh = argc > 7 ? std::atoi(argv[7]) : 1;
+  const int tile_low = argc > 8 ? std::atoi(argv[8]) : 0;
   Env env;
   env.arith = arith;
+  env.tile_low_qubits = tile_low;
   Reg r;
   r.env = &env;
   r.n = n;

@@ -46,11 +46,11 @@ def harness(tmp_path_factory):
     return exe
 
 
-def run(exe, n, ops, density=False, prec=128, arith=0, k_req=0, emulate=True):
+def run(exe, n, ops, density=False, prec=128, arith=0, k_req=0, emulate=True, tile_low=0):
     arr, cnt = Q.to_qsops(ops)
     data = ctypes.string_at(ctypes.addressof(arr), ctypes.sizeof(QSOp) * cnt)
     r = subprocess.run([exe, str(n), str(int(density)), str(prec), str(arith), str(k_req),
-                        str(int(emulate))], input=data, capture_output=True, timeout=120)
+                        str(int(emulate)), "1", str(tile_low)], input=data, capture_output=True, timeout=120)
     out = r.stdout
     head, _, rest = out.partition(b"\n")
     assert r.returncode == 0, (head.decode(), r.stderr.decode()[-2000:])
@@ -187,3 +187,20 @@ def test_planned_density_matrix_heavy_noise(harness, p_depol, arith):
     head, rho = run(harness, N, ops, density=True, arith=arith)
     ref = O.run_circuit(N, ops, density=True).a
     assert np.max(np.abs(rho - ref)) <= 1e-12, head
+
+
+@pytest.mark.parametrize("tile_low", [2, 3, 5])
+def test_tile_low_qubits_option_plans_match_oracle(harness, tile_low):
+    """Plans whose tiles hold other numbers of contiguous low qubits (the
+    "tile_low_qubits" option: shorter HBM chunks, more tile qubits for the
+    pass windows) still give the oracle's state: state vectors in both
+    precisions and double-float, tiles smaller than the register, noisy
+    density matrices."""
+    for n, k, prec, arith in ((12, 0, 128, 0), (14, 9, 64, 0), (15, 10, 128, 1), (16, 12, 64, 0)):
+        ops = C.random_circuit(n, 12, 500 + n + tile_low, extras=True)
+        head, st = run(harness, n, ops, prec=prec, arith=arith, k_req=k, tile_low=tile_low)
+        assert np.max(np.abs(st - O.run_circuit(n, ops).a)) <= TOL[(prec, arith)], head
+    for N, k, arith in ((5, 8, 0), (6, 0, 1), (6, 10, 0)):
+        ops = C.with_noise(C.random_circuit(N, 8, 31 + N, extras=True), 0.05, 0.02)
+        head, rho = run(harness, N, ops, density=True, k_req=k, arith=arith, tile_low=tile_low)
+        assert np.max(np.abs(rho - O.run_circuit(N, ops, density=True).a)) <= 1e-12, head
