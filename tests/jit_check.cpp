@@ -45,6 +45,8 @@ int main(int argc, char** argv) {
   const int copy = std::atoi(argv[7]);
   Env env;
   env.arith = arith;
+  // the "tile_low_qubits" option (contiguous low qubits per tile), if set
+  if (const char* t = std::getenv("JIT_CHECK_TILE_LOW")) env.tile_low_qubits = std::atoi(t);
   Reg r;
   r.env = &env;
   r.n = n;

@@ -42,10 +42,11 @@ def harness(tmp_path_factory):
     return exe
 
 
-def run(exe, n, ops, density=False, prec=128, arith=0, k_req=0, ctas=2, max_compile=4, copy=0):
+def run(exe, n, ops, density=False, prec=128, arith=0, k_req=0, ctas=2, max_compile=4, copy=0, tile_low=0):
     arr, cnt = Q.to_qsops(ops)
     data = ctypes.string_at(ctypes.addressof(arr), ctypes.sizeof(Q.QSOp) * cnt)
     env = dict(os.environ)
+    env["JIT_CHECK_TILE_LOW"] = str(tile_low)
     env["LD_LIBRARY_PATH"] = os.path.join(CUDA, "lib64") + ":" + env.get("LD_LIBRARY_PATH", "")
     r = subprocess.run([exe, str(n), str(int(density)), str(prec), str(arith), str(k_req), str(ctas),
                         str(copy), str(max_compile)], input=data, capture_output=True, timeout=600, env=env)
@@ -119,3 +120,15 @@ def test_copy_pipelines_density_small_tiles(harness, copy):
     ops = C.with_noise(C.random_circuit(N, 10, 31, extras=True) + extras(N, 3), 0.3, 0.6)
     passes, compiled, _ = run(harness, N, ops, density=True, k_req=9, copy=copy, max_compile=2)
     assert compiled >= 1
+
+
+@pytest.mark.parametrize("tile_low", [2, 3])
+@pytest.mark.parametrize("prec,arith,copy", [(64, 0, 2), (64, 0, 6), (64, 0, 1), (128, 0, 0), (128, 1, 4)])
+def test_passes_with_fewer_low_tile_qubits_compile(harness, tile_low, prec, arith, copy):
+    """Plans whose tiles hold 2 or 3 contiguous low qubits ("tile_low_qubits":
+    HBM chunks of 32 / 64 bytes for complex64) generate kernels that compile
+    in every copy form, the bulk copies included (chunks stay a multiple of
+    16 bytes)."""
+    passes, compiled, _ = run(harness, 26, C.workload_30q(26), prec=prec, arith=arith,
+                              k_req=12 if prec == 64 else 0, copy=copy, max_compile=2, tile_low=tile_low)
+    assert passes > 0 and compiled == 2
