@@ -204,3 +204,46 @@ def test_tile_low_qubits_option_plans_match_oracle(harness, tile_low):
         ops = C.with_noise(C.random_circuit(N, 8, 31 + N, extras=True), 0.05, 0.02)
         head, rho = run(harness, N, ops, density=True, k_req=k, arith=arith, tile_low=tile_low)
         assert np.max(np.abs(rho - O.run_circuit(N, ops, density=True).a)) <= 1e-12, head
+
+
+def _edge_circuits(n):
+    """Shapes at the planner's corners: only diagonal operations (phases,
+    CZ, multi-controlled flips: no pass needs a moved bit), every gate on the
+    top qubit, alternating top and bottom qubits, a ladder of CNOTs."""
+    rng = C.SplitMix64(4000 + n)
+    diag = [C.Op(C.H, (q,)) for q in range(n)]
+    for i in range(40):
+        a, b = C.distinct_qubits(rng, n, 2)
+        diag.append([C.Op(C.T_GATE, (a,)), C.Op(C.CZ, (a, b)), C.Op(C.PHASE, (b,), (), (0.1 + rng.uniform(),)),
+                     C.Op(C.MCPF, (), tuple(C.distinct_qubits(rng, n, 3)))][i % 4])
+    top = [C.Op(C.H, (n - 1,))] + [C.Op([C.SQRT_X, C.SQRT_Y, C.T_GATE][i % 3], (n - 1,)) for i in range(30)]
+    alt = [C.Op(C.H, (q,)) for q in range(n)] + \
+        [C.Op([C.SQRT_X, C.SQRT_Y][i % 2], ((n - 1) if i % 2 else 0,)) for i in range(30)] + \
+        [C.Op(C.CZ, (0, n - 1))]
+    ladder = [C.Op(C.H, (0,))] + [C.Op(C.CNOT, (q + 1,), (q,)) for q in range(n - 1)] + \
+        [C.Op(C.SQRT_Y, (q,)) for q in range(0, n, 3)]
+    return {"diagonal": diag, "top": top, "alternate": alt, "ladder": ladder}
+
+
+@pytest.mark.parametrize("prec,arith", [(128, 0), (64, 0), (128, 1)])
+@pytest.mark.parametrize("n,k", [(13, 0), (14, 13), (16, 10), (18, 12)])
+def test_planner_edge_circuits_match_oracle(harness, n, k, prec, arith):
+    """The candidate tiles and stage windows on circuits at the planner's
+    corners (tile one qubit short of the register, tiles of 2^10 on 16
+    qubits, one-tile registers on clusters) still give the oracle's state."""
+    for name, ops in _edge_circuits(n).items():
+        head, st = run(harness, n, ops, prec=prec, arith=arith, k_req=k)
+        err = np.max(np.abs(st - O.run_circuit(n, ops).a))
+        assert err <= TOL[(prec, arith)], (name, head, err)
+
+
+@pytest.mark.parametrize("arith", [0, 1])
+def test_planner_density_matrix_channels_only(harness, arith):
+    """A density matrix with channels and no gates after a layer of H:
+    only deferred off-diagonal factors and diagonal mixes in the passes."""
+    N = 6
+    ops = [C.Op(C.H, (q,)) for q in range(N)]
+    for i in range(24):
+        ops.append(C.Op(C.DEPHASE if i % 2 else C.DEPOL, (i % N,), (), (0.02 + 0.01 * (i % 5),)))
+    head, rho = run(harness, N, ops, density=True, arith=arith, k_req=8)
+    assert np.max(np.abs(rho - O.run_circuit(N, ops, density=True).a)) <= 1e-12, head
